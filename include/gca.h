@@ -1,0 +1,221 @@
+/*
+ * gca.h -- C-ABI of the B300 GCA-H^2 library.
+ *
+ * Green cross approximation (GCA) H^2-matrix compression of the Galerkin
+ * single-layer Laplace matrix (Boerm & Christophersen, "GCA-H^2 matrix
+ * compression for electrostatic simulations"), built and applied on one GPU.
+ *
+ *   g(x, y) = 1 / (4 pi |x - y|)                                  (Sect. 1)
+ *   g_ij    = int phi_i(x) int g(x, y) phi_j(y) dy dx             (Eq. (1))
+ *
+ * with piecewise constant phi_i = indicator of triangle i.  The library
+ * builds the H^2 representation
+ *
+ *   G|tau x sigma ~ V_tau S_{tau sigma} V_sigma^*      admissible blocks,
+ *   G|tau x sigma   exactly                            inadmissible leaves,
+ *
+ * with nested bases V_tau = [V_1 E_1; V_2 E_2] obtained by cross
+ * approximation of Green quadrature matrices (Sect. 2 - Sect. 4), and
+ * applies it (and its transpose) to blocks of vectors.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: 0 (GCA_OK) on success, a negative gca_status otherwise;
+ *     gca_strerror() gives a one-line text.  On error, outputs are left
+ *     unspecified and no handle is returned.
+ *   - Host pointers (meshes, trees, parameter structs, export buffers) are
+ *     owned by the caller and only read/written during the call.
+ *   - Device pointers (x, y of the products) are owned by the caller and
+ *     must be valid device memory of the current device.
+ *   - Handles own all of their device memory until gca_free().
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Products are stream ordered and do not synchronise.
+ *     gca_build synchronises the stream (it sizes its outputs from ranks
+ *     found on the device).
+ *   - Every index is 0-based; triangles are referred to by their position
+ *     in the caller's triangle array ("original order").
+ */
+#ifndef GCA_H
+#define GCA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GCA_OK = 0,
+  GCA_ERR_INVALID_ARG = -1, /* bad mesh, tree, parameter or size          */
+  GCA_ERR_CUDA = -2,        /* a CUDA runtime call failed                 */
+  GCA_ERR_OOM = -3,         /* device or host allocation failed           */
+  GCA_ERR_NUMERIC = -4,     /* NaN/Inf in the input or in an intermediate */
+  GCA_ERR_TIMEOUT = -5,     /* a bounded device-side wait expired         */
+  GCA_ERR_UNSUPPORTED = -6  /* valid request outside the built limits     */
+} gca_status;
+
+/* Surface mesh (Sect. 2): nv vertices, nt flat triangles.  vertices is
+ * [nv][3] float64 row-major, triangles [nt][3] int32 row-major with vertex
+ * ids in [0, nv).  The mesh must be conforming (neighbouring triangles
+ * share vertex ids): the singular quadrature picks its rule by counting
+ * shared ids (Sect. 8).  Degenerate (zero-area) triangles are rejected. */
+typedef struct {
+  int32_t nv;
+  int32_t nt;
+  const double* vertices;
+  const int32_t* triangles;
+} gca_mesh;
+
+/* Cluster tree (Sect. 2): clusters are index sets tau-hat of triangles,
+ * stored as ranges [begin, end) of `perm`, which lists triangle ids in
+ * cluster order.  Cluster 0 is the root ([0, nt), level 0).  A cluster is
+ * a leaf iff child0 == child1 == -1; otherwise child0 covers
+ * [begin, m) and child1 [m, end) for some begin < m < end, and
+ * level[child] = level[parent] + 1.  All arrays are host int32 of length
+ * nclusters (perm: nt). */
+typedef struct {
+  int32_t nclusters;
+  const int32_t* perm;
+  const int32_t* begin;
+  const int32_t* end;
+  const int32_t* child0;
+  const int32_t* child1;
+  const int32_t* level;
+} gca_tree;
+
+/* Parameters of the construction.
+ *   leaf_size    only used by gca_tree_build; gca_build accepts any valid
+ *                tree whose leaves hold at most GCA_MAX_LEAF triangles.
+ *   eta          admissibility max(diam tau, diam sigma) <= 2 eta dist
+ *                (Sect. 2), eta > 0.
+ *   box_gauss_m  m: Gauss-Legendre points per direction on each face of
+ *                the box omega; k = 6 m^2 quadrature points (Eq. (2)).
+ *                1 <= m <= GCA_MAX_BOX_M.
+ *   aca_tol      relative stopping tolerance of the cross approximation
+ *                (Sect. 3): stop before a pivot <= aca_tol * |first pivot|.
+ *   tri_rule     triangle rule for regular integrals; only 7 (the
+ *                degree-5 seven-point rule) is implemented.
+ *   sauter_q     Gauss order per variable of the Sauter-Schwab rules for
+ *                touching pairs (Sect. 8), 1 <= q <= GCA_MAX_SAUTER_Q.
+ *   omega_margin omega = box(tau) widened by omega_margin * diam(tau) on
+ *                each side; a value < 0 selects 1 / (4 eta).
+ *   flags        reserved, must be 0. */
+typedef struct {
+  int32_t leaf_size;
+  double eta;
+  int32_t box_gauss_m;
+  double aca_tol;
+  int32_t tri_rule;
+  int32_t sauter_q;
+  double omega_margin;
+  uint32_t flags;
+} gca_params;
+
+enum {
+  GCA_MAX_LEAF = 128,
+  GCA_MAX_BOX_M = 6,
+  GCA_MAX_SAUTER_Q = 16
+};
+
+/* Arithmetic of a product.  GCA_F64: everything in float64, x and y are
+ * float64.  GCA_F32: bases, transfers, couplings and near field in
+ * float32, float32 x and y.  GCA_BF16: bases, transfers and couplings in
+ * bfloat16 with float32 accumulation, near field float32; x, y float32. */
+typedef enum { GCA_F64 = 0, GCA_F32 = 1, GCA_BF16 = 2 } gca_prec;
+
+typedef struct gca_h2 gca_h2; /* opaque handle */
+
+/* Sizes and counters of a built handle. */
+typedef struct {
+  int32_t n;            /* triangles                                      */
+  int32_t nclusters;
+  int32_t depth;        /* deepest level                                  */
+  int32_t k;            /* quadrature points per box, 6 m^2               */
+  int32_t nfar;         /* admissible (coupling) blocks                   */
+  int32_t nnear;        /* inadmissible leaf (near-field) blocks          */
+  int32_t max_rank;
+  int32_t reserved;
+  int64_t rank_sum;     /* sum of r_tau over all clusters (root: 0)       */
+  int64_t v_entries;    /* coefficients of the leaf bases V_tau           */
+  int64_t e_entries;    /* coefficients of the transfer matrices E_tau    */
+  int64_t s_entries;    /* coefficients of the coupling matrices S        */
+  int64_t n_entries;    /* coefficients of the near-field blocks          */
+  int64_t n_singular[4];/* near entries by shared vertices: 0,1,2,3       */
+  double build_seconds; /* wall time of gca_build (host clock)            */
+} gca_stats;
+
+/* Host copy of a built handle, for inspection and tests.  The caller
+ * allocates every array with the sizes from gca_h2_stats:
+ *   rank   [nclusters]     r_tau (0 for the root)
+ *   pivots [rank_sum]      tilde-tau as triangle ids in selection order,
+ *                          clusters in increasing id
+ *   far    [2*nfar]        (tau, sigma) pairs, sorted by tau then sigma
+ *   near   [2*nnear]       (tau, sigma) pairs, sorted by tau then sigma
+ *   V      [v_entries]     for each leaf in increasing id: |tau-hat| x r
+ *                          row-major, rows in cluster (perm) order
+ *   E      [e_entries]     for each cluster whose parent is not the root,
+ *                          in increasing id: r_child x r_parent row-major
+ *   S      [s_entries]     for each far block in the order of `far`:
+ *                          r_tau x r_sigma row-major
+ *   N      [n_entries]     for each near block in the order of `near`:
+ *                          |tau-hat| x |sigma-hat| row-major, cluster order
+ * Any pointer may be NULL to skip that array. */
+typedef struct {
+  int32_t* rank;
+  int32_t* pivots;
+  int32_t* far;
+  int32_t* near;
+  double* V;
+  double* E;
+  double* S;
+  double* N;
+} gca_host_dump;
+
+/* Cluster tree by recursive bisection (helper; the tree stays an input of
+ * gca_build).  The bounding box of the triangle centroids (a+b+c)/3 is
+ * split at its midpoint across its longest axis (ties: lowest axis);
+ * centroids below the midpoint go to child0, keeping their order.  If a
+ * side would be empty, the set is sorted stably by that coordinate and
+ * halved (child0 gets the lower floor(size/2)).  Sets of at most
+ * leaf_size triangles are leaves; clusters are numbered breadth first.
+ * Output arrays are caller-allocated host int32: perm [nt], the others
+ * [max_clusters] (2*nt - 1 always suffices).  *nclusters receives the
+ * count.  Errors: INVALID_ARG (bad mesh, leaf_size < 1, too small
+ * max_clusters). */
+int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t max_clusters,
+                   int32_t* perm, int32_t* begin, int32_t* end, int32_t* child0,
+                   int32_t* child1, int32_t* level, int32_t* nclusters);
+
+/* Build the GCA-H^2 representation of G on the current device (Sect. 2 -
+ * Sect. 4, Sect. 8): cluster boxes, box quadrature, Green quadrature
+ * matrices, complete-pivoting cross approximation level by level from the
+ * leaves (leaf bases V_tau, transfer matrices E_tau, pivot sets tilde-tau),
+ * coupling matrices S = G|tilde-tau x tilde-sigma and near-field blocks
+ * G|tau-hat x sigma-hat, plus float32 / bfloat16 copies for the reduced
+ * precision products.  mesh/tree/params are copied; *out receives a new
+ * handle.  Synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA, NUMERIC. */
+int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
+              void* stream, gca_h2** out);
+
+/* y = G_H2 x for nrhs right-hand sides.  x: device, column-major n x nrhs
+ * with leading dimension ldx >= n, rows in original triangle order; y:
+ * device, same layout with ldy >= n, overwritten.  Element type float64
+ * for GCA_F64, float32 otherwise.  x and y must not overlap.  The handle
+ * keeps internal work buffers: calls on the same handle must be ordered on
+ * one stream.  1 <= nrhs <= 4096.  Errors: INVALID_ARG, CUDA, OOM. */
+int h2_matvec(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx,
+              void* y, int64_t ldy, void* stream);
+
+/* y = G_H2^T x, same conventions as h2_matvec. */
+int h2_matvec_transpose(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x,
+                        int64_t ldx, void* y, int64_t ldy, void* stream);
+
+int gca_h2_stats(const gca_h2* h, gca_stats* out);
+int gca_h2_export(const gca_h2* h, gca_host_dump* out);
+void gca_free(gca_h2* h);
+const char* gca_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCA_H */

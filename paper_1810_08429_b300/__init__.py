@@ -1,0 +1,250 @@
+"""Python binding of the B300 GCA-H^2 library (``include/gca.h``).
+
+Argument marshalling only: every step of the construction and of the
+products runs in the CUDA kernels of ``libgca.so``.  PyTorch supplies
+device memory and streams.  The library must be built first
+(``python -m paper_1810_08429_b300._build`` or ``__graft_entry__.build()``);
+importing this package without it raises immediately.
+
+    import paper_1810_08429_b300 as gca
+    tree = gca.tree_build(vertices, triangles, leaf_size=32)
+    h = gca.build(vertices, triangles, tree, gca.Params(leaf_size=32, ...))
+    y = h.matvec(x)                     # x: CUDA tensor (n,) or (n, R)
+    yt = h.matvec(x, transpose=True)
+"""
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgca.so")
+
+F64, F32, BF16 = 0, 1, 2
+_PREC = {"f64": F64, "f32": F32, "bf16": BF16, F64: F64, F32: F32, BF16: BF16}
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int32), ("nt", ctypes.c_int32),
+                ("vertices", _f64p), ("triangles", _i32p)]
+
+
+class _Tree(ctypes.Structure):
+    _fields_ = [("nclusters", ctypes.c_int32), ("perm", _i32p), ("begin", _i32p),
+                ("end", _i32p), ("child0", _i32p), ("child1", _i32p), ("level", _i32p)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("eta", ctypes.c_double),
+                ("box_gauss_m", ctypes.c_int32), ("aca_tol", ctypes.c_double),
+                ("tri_rule", ctypes.c_int32), ("sauter_q", ctypes.c_int32),
+                ("omega_margin", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nclusters", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("nfar", ctypes.c_int32), ("nnear", ctypes.c_int32),
+                ("max_rank", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rank_sum", ctypes.c_int64), ("v_entries", ctypes.c_int64),
+                ("e_entries", ctypes.c_int64), ("s_entries", ctypes.c_int64),
+                ("n_entries", ctypes.c_int64), ("n_singular", ctypes.c_int64 * 4),
+                ("build_seconds", ctypes.c_double)]
+
+
+class _Dump(ctypes.Structure):
+    _fields_ = [("rank", _i32p), ("pivots", _i32p), ("far", _i32p), ("near", _i32p),
+                ("V", _f64p), ("E", _f64p), ("S", _f64p), ("N", _f64p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -m paper_1810_08429_b300._build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    sig = {
+        "gca_tree_build": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.c_int32, ctypes.c_int32,
+                                          _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
+        "gca_build": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
+                                     ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+        "h2_matvec": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int32, vp, ctypes.c_int64, vp,
+                                     ctypes.c_int64, vp]),
+        "h2_matvec_transpose": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int32, vp,
+                                               ctypes.c_int64, vp, ctypes.c_int64, vp]),
+        "gca_h2_stats": (ctypes.c_int, [vp, ctypes.POINTER(_Stats)]),
+        "gca_h2_export": (ctypes.c_int, [vp, ctypes.POINTER(_Dump)]),
+        "gca_free": (None, [vp]),
+        "gca_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "gca_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class GCAError(RuntimeError):
+    pass
+
+
+def _check(status, what):
+    if status != 0:
+        msg = lib.gca_last_error().decode(errors="replace")
+        raise GCAError(f"{what}: {lib.gca_strerror(status).decode()} ({status}): {msg}")
+
+
+@dataclass
+class Params:
+    """Construction parameters (mirrors ``gca_params``)."""
+    leaf_size: int = 32
+    eta: float = 2.0
+    box_gauss_m: int = 3
+    aca_tol: float = 1e-6
+    tri_rule: int = 7
+    sauter_q: int = 5
+    omega_margin: float = -1.0
+    flags: int = 0
+
+    def _c(self):
+        return _Params(self.leaf_size, self.eta, self.box_gauss_m, self.aca_tol, self.tri_rule,
+                       self.sauter_q, self.omega_margin, self.flags)
+
+
+def _mesh(vertices, triangles):
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    t = np.ascontiguousarray(triangles, dtype=np.int32)
+    if v.ndim != 2 or v.shape[1] != 3 or t.ndim != 2 or t.shape[1] != 3:
+        raise ValueError("vertices must be (nv, 3) and triangles (nt, 3)")
+    m = _Mesh(v.shape[0], t.shape[0], v.ctypes.data_as(_f64p), t.ctypes.data_as(_i32p))
+    return m, (v, t)
+
+
+def tree_build(vertices, triangles, leaf_size):
+    """Cluster tree by recursive bisection (``gca_tree_build``), as numpy arrays."""
+    m, keep = _mesh(vertices, triangles)
+    n = m.nt
+    cap = max(2 * n - 1, 1)
+    out = {k: np.zeros(n if k == "perm" else cap, dtype=np.int32)
+           for k in ("perm", "begin", "end", "child0", "child1", "level")}
+    nc = ctypes.c_int32(0)
+    st = lib.gca_tree_build(ctypes.byref(m), leaf_size, cap,
+                            *[out[k].ctypes.data_as(_i32p)
+                              for k in ("perm", "begin", "end", "child0", "child1", "level")],
+                            ctypes.byref(nc))
+    _check(st, "gca_tree_build")
+    for k in ("begin", "end", "child0", "child1", "level"):
+        out[k] = out[k][:nc.value].copy()
+    return out
+
+
+def _tree(tree):
+    arrs = {k: np.ascontiguousarray(tree[k], dtype=np.int32)
+            for k in ("perm", "begin", "end", "child0", "child1", "level")}
+    t = _Tree(len(arrs["begin"]), *[arrs[k].ctypes.data_as(_i32p)
+                                     for k in ("perm", "begin", "end", "child0", "child1", "level")])
+    return t, arrs
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class H2:
+    """A built GCA-H^2 matrix on the current CUDA device (owns a gca_h2 handle)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib.gca_free(h)
+            self._h = ctypes.c_void_p(None)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self):
+        s = _Stats()
+        _check(lib.gca_h2_stats(self._h, ctypes.byref(s)), "gca_h2_stats")
+        out = {name: getattr(s, name) for name, _ in _Stats._fields_ if name != "n_singular"}
+        out["n_singular"] = list(s.n_singular)
+        return out
+
+    def export(self):
+        """Host copy of the representation (layout documented in gca.h)."""
+        s = self.stats()
+        d = {
+            "rank": np.zeros(s["nclusters"], dtype=np.int32),
+            "pivots": np.zeros(max(s["rank_sum"], 1), dtype=np.int32),
+            "far": np.zeros(2 * max(s["nfar"], 1), dtype=np.int32),
+            "near": np.zeros(2 * max(s["nnear"], 1), dtype=np.int32),
+            "V": np.zeros(max(s["v_entries"], 1)),
+            "E": np.zeros(max(s["e_entries"], 1)),
+            "S": np.zeros(max(s["s_entries"], 1)),
+            "N": np.zeros(max(s["n_entries"], 1)),
+        }
+        dump = _Dump(*[d[k].ctypes.data_as(_i32p if d[k].dtype == np.int32 else _f64p)
+                       for k in ("rank", "pivots", "far", "near", "V", "E", "S", "N")])
+        _check(lib.gca_h2_export(self._h, ctypes.byref(dump)), "gca_h2_export")
+        d["pivots"] = d["pivots"][:s["rank_sum"]]
+        d["far"] = d["far"][:2 * s["nfar"]].reshape(-1, 2)
+        d["near"] = d["near"][:2 * s["nnear"]].reshape(-1, 2)
+        for k, key in (("V", "v_entries"), ("E", "e_entries"), ("S", "s_entries"),
+                       ("N", "n_entries")):
+            d[k] = d[k][:s[key]]
+        return d
+
+    def matvec_raw(self, prec, nrhs, x_ptr, ldx, y_ptr, ldy, stream_ptr, transpose=False):
+        fn = lib.h2_matvec_transpose if transpose else lib.h2_matvec
+        _check(fn(self._h, _PREC.get(prec, prec), nrhs, x_ptr, ldx, y_ptr, ldy, stream_ptr),
+               "h2_matvec_transpose" if transpose else "h2_matvec")
+
+    def matvec(self, x, prec="f64", transpose=False, out=None, stream=None):
+        """y = G_H2 x (or G_H2^T x) for a CUDA tensor x of shape (n,) or (n, R)."""
+        import torch
+        p = _PREC[prec]
+        dt = torch.float64 if p == F64 else torch.float32
+        vec = x.dim() == 1
+        x2 = x[:, None] if vec else x
+        if x2.dtype != dt or not x2.is_cuda:
+            raise TypeError(f"x must be a CUDA {dt} tensor")
+        if x2.stride(0) != 1:
+            x2 = x2.t().contiguous().t()
+        n, R = x2.shape
+        if out is None:
+            out = torch.empty((R, n), dtype=dt, device=x2.device).t()
+        y2 = out[:, None] if out.dim() == 1 else out
+        if y2.stride(0) != 1 or y2.shape != (n, R):
+            raise ValueError("out must be column-major (n, R)")
+        self.matvec_raw(p, R, ctypes.c_void_p(x2.data_ptr()), x2.stride(1) if R > 1 else n,
+                        ctypes.c_void_p(y2.data_ptr()), y2.stride(1) if R > 1 else n,
+                        _stream_ptr(stream), transpose)
+        return out[:, 0] if vec and out.dim() == 2 else out
+
+
+def build(vertices, triangles, tree, params, stream=None):
+    """gca_build on the current CUDA device; returns an ``H2``."""
+    m, keep_m = _mesh(vertices, triangles)
+    t, keep_t = _tree(tree)
+    p = params._c()
+    h = ctypes.c_void_p(None)
+    _check(lib.gca_build(ctypes.byref(m), ctypes.byref(t), ctypes.byref(p), _stream_ptr(stream),
+                         ctypes.byref(h)), "gca_build")
+    return H2(h.value)

@@ -1,0 +1,126 @@
+// Extern "C" entry points declared in gca.h: argument checks and dispatch
+// to the build / product translation units, statistics, export and error
+// text.
+
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.hpp"
+
+namespace gca {
+namespace {
+thread_local std::string g_last_error;
+}
+void set_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace gca
+
+extern "C" {
+
+const char* gca_last_error(void) { return gca::g_last_error.c_str(); }
+
+int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params, void* stream,
+              gca_h2** out) {
+  if (!out) {
+    gca::set_error("gca_build: out is NULL");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    return gca::build(mesh, tree, params, static_cast<cudaStream_t>(stream), out);
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_build: host allocation failed");
+    return GCA_ERR_OOM;
+  }
+}
+
+int h2_matvec(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx, void* y,
+              int64_t ldy, void* stream) {
+  return gca::matvec(h, prec, false, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream));
+}
+
+int h2_matvec_transpose(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx,
+                        void* y, int64_t ldy, void* stream) {
+  return gca::matvec(h, prec, true, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream));
+}
+
+int gca_h2_stats(const gca_h2* h, gca_stats* o) {
+  if (!h || !o) {
+    gca::set_error("gca_h2_stats: NULL argument");
+    return GCA_ERR_INVALID_ARG;
+  }
+  std::memset(o, 0, sizeof(*o));
+  o->n = h->n;
+  o->nclusters = h->nc;
+  o->depth = h->depth;
+  o->k = h->k;
+  o->nfar = (int32_t)h->far_t.size();
+  o->nnear = (int32_t)h->near_t.size();
+  o->max_rank = h->max_rank;
+  o->rank_sum = h->rank_sum;
+  o->v_entries = h->v_entries;
+  o->e_entries = h->e_entries;
+  o->s_entries = h->s_entries;
+  o->n_entries = h->n_entries;
+  for (int c = 0; c < 4; ++c) o->n_singular[c] = h->n_singular[c];
+  o->build_seconds = h->build_seconds;
+  return GCA_OK;
+}
+
+int gca_h2_export(const gca_h2* h, gca_host_dump* o) {
+  if (!h || !o) {
+    gca::set_error("gca_h2_export: NULL argument");
+    return GCA_ERR_INVALID_ARG;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    gca::set_error("gca_h2_export: device error before export");
+    return GCA_ERR_CUDA;
+  }
+  if (o->rank) std::memcpy(o->rank, h->rank.data(), sizeof(int) * h->nc);
+  if (o->pivots) {
+    int64_t at = 0;
+    for (int c = 0; c < h->nc; ++c)
+      for (int t = 0; t < h->rank[c]; ++t) o->pivots[at++] = h->piv[h->poff[c] + t];
+  }
+  if (o->far)
+    for (size_t b = 0; b < h->far_t.size(); ++b) {
+      o->far[2 * b] = h->far_t[b];
+      o->far[2 * b + 1] = h->far_s[b];
+    }
+  if (o->near)
+    for (size_t b = 0; b < h->near_t.size(); ++b) {
+      o->near[2 * b] = h->near_t[b];
+      o->near[2 * b + 1] = h->near_s[b];
+    }
+  struct Item { double* dst; const gca::DevMem* src; int64_t n; };
+  const Item items[4] = {{o->V, &h->V64, h->v_entries}, {o->E, &h->E64, h->e_entries},
+                         {o->S, &h->S64, h->s_entries}, {o->N, &h->N64, h->n_entries}};
+  for (const auto& it : items)
+    if (it.dst && it.n > 0) {
+      cudaError_t e = cudaMemcpy(it.dst, it.src->p, sizeof(double) * it.n, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        gca::set_error(std::string("gca_h2_export: ") + cudaGetErrorString(e));
+        return GCA_ERR_CUDA;
+      }
+    }
+  return GCA_OK;
+}
+
+void gca_free(gca_h2* h) { delete h; }
+
+const char* gca_strerror(int status) {
+  switch (status) {
+    case GCA_OK: return "ok";
+    case GCA_ERR_INVALID_ARG: return "invalid argument";
+    case GCA_ERR_CUDA: return "CUDA runtime error";
+    case GCA_ERR_OOM: return "out of memory";
+    case GCA_ERR_NUMERIC: return "non-finite value";
+    case GCA_ERR_TIMEOUT: return "device wait timed out";
+    case GCA_ERR_UNSUPPORTED: return "unsupported size or option";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

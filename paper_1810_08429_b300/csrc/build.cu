@@ -1,0 +1,899 @@
+// GCA-H^2 construction on the GPU (Sect. 2 - Sect. 4, Sect. 8).
+//
+// Pipeline of gca_build (all arithmetic in float64 on the device):
+//   1. k_tri_geom       7-point rule nodes and weights of every triangle
+//   2. k_cluster_boxes  bounding box of each cluster's vertices
+//      host             diameters, admissibility, block tree (tree.cpp)
+//   3. k_box_quad       Gauss rule on the faces of omega_tau (Eq. (2))
+//   4. k_green_aca      per tree level, deepest first, one CTA per cluster:
+//                       the Green quadrature matrix A_tau (leaves: all
+//                       triangles; parents: the children's pivot rows) is
+//                       formed in shared memory (or global scratch when it
+//                       does not fit), cross-approximated with complete
+//                       pivoting (Sect. 3), and V^ = U L^{-1} is written.
+//                       The host reads the level's ranks back to size the
+//                       next level.
+//   5. k_pack           leaf bases V_tau and transfer matrices E_tau
+//                       (Sect. 4) in float64 / float32 / bfloat16
+//   6. k_couple_entries S_{tau sigma} = G|tilde-tau x tilde-sigma (7 x 7
+//                       point rule: pivots of admissible blocks never touch)
+//   7. k_near_entries   G|tau-hat x sigma-hat for inadmissible leaf pairs;
+//                       disjoint pairs directly, touching pairs appended to
+//                       one list per Sauter-Schwab case (Sect. 8), which
+//      k_singular<case> then integrate with one warp per entry.
+//   8. reduced-precision copies of S and N.
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "internal.hpp"
+#include "rules.hpp"
+
+namespace gca {
+
+namespace {
+
+constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
+
+// a point and a weight, 32-byte aligned for single vector loads
+struct __align__(32) P4 {
+  double x, y, z, w;
+};
+constexpr int kAcaThreads = 256;
+constexpr int kStatusNumeric = 1;
+constexpr int kStatusOverflow = 2;
+
+// ------------------------------------------------------------------ geometry
+
+__global__ void k_tri_geom(int nt, const double* __restrict__ vert, const int* __restrict__ tri,
+                           Rules rules, P4* __restrict__ tq) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const int ia = tri[3 * t], ib = tri[3 * t + 1], ic = tri[3 * t + 2];
+  double a[3], b[3], c[3];
+  for (int d = 0; d < 3; ++d) {
+    a[d] = vert[3 * ia + d];
+    b[d] = vert[3 * ib + d];
+    c[d] = vert[3 * ic + d];
+  }
+  double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double cx = u[1] * v[2] - u[2] * v[1];
+  double cy = u[2] * v[0] - u[0] * v[2];
+  double cz = u[0] * v[1] - u[1] * v[0];
+  double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+  for (int q = 0; q < 7; ++q) {
+    double l0 = rules.bary[q][0], l1 = rules.bary[q][1], l2 = rules.bary[q][2];
+    tq[7 * t + q] = P4{l0 * a[0] + l1 * b[0] + l2 * c[0], l0 * a[1] + l1 * b[1] + l2 * c[1],
+                       l0 * a[2] + l1 * b[2] + l2 * c[2], rules.w7[q] * area};
+  }
+}
+
+// one warp per cluster: min / max over the vertices of its triangles
+__global__ void k_cluster_boxes(int nc, const int* __restrict__ begin, const int* __restrict__ end,
+                                const int* __restrict__ perm, const int* __restrict__ tri,
+                                const double* __restrict__ vert, double* __restrict__ box) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nc) return;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = begin[warp] + lane; i < end[warp]; i += 32) {
+    const int t = perm[i];
+    for (int a = 0; a < 3; ++a) {
+      const int v = tri[3 * t + a];
+      for (int d = 0; d < 3; ++d) {
+        double x = vert[3 * v + d];
+        lo[d] = fmin(lo[d], x);
+        hi[d] = fmax(hi[d], x);
+      }
+    }
+  }
+  for (int off = 16; off; off >>= 1)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
+      hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+    }
+  if (lane == 0)
+    for (int d = 0; d < 3; ++d) {
+      box[6 * warp + d] = lo[d];
+      box[6 * warp + 3 + d] = hi[d];
+    }
+}
+
+// Gauss rule on the six faces of omega = box widened by margin * diam.
+// Point nu = face * m^2 + a * m + b; faces -x, +x, -y, +y, -z, +z; on each
+// face the lower remaining axis carries the index a.  Output (x, y, z,
+// sqrt(w)) per point; the outward normal is implied by the face.
+__global__ void k_box_quad(int nc, Rules rules, const double* __restrict__ box,
+                           const double* __restrict__ diam, double margin,
+                           P4* __restrict__ zq) {
+  const int m = rules.m, k = 6 * m * m;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nc * k) return;
+  const int c = idx / k, nu = idx % k;
+  const int face = nu / (m * m), a = (nu / m) % m, b = nu % m;
+  const int d = face >> 1, side = face & 1;
+  const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+  const double delta = margin * diam[c];
+  double lo[3], hi[3];
+  for (int e = 0; e < 3; ++e) {
+    lo[e] = box[6 * c + e] - delta;
+    hi[e] = box[6 * c + 3 + e] + delta;
+  }
+  const double mid1 = 0.5 * (lo[d1] + hi[d1]), half1 = 0.5 * (hi[d1] - lo[d1]);
+  const double mid2 = 0.5 * (lo[d2] + hi[d2]), half2 = 0.5 * (hi[d2] - lo[d2]);
+  double z[3];
+  z[d] = side ? hi[d] : lo[d];
+  z[d1] = mid1 + half1 * rules.box_t[a];
+  z[d2] = mid2 + half2 * rules.box_t[b];
+  const double w = rules.box_w[a] * rules.box_w[b] * half1 * half2;
+  zq[idx] = P4{z[0], z[1], z[2], sqrt(w)};
+}
+
+// ------------------------------------------------------ Green matrix + ACA
+
+struct AcaJob {
+  int c;          // cluster
+  int rows;       // rows of A^
+  int leaf;       // rows are the cluster's triangles (1) or the children's pivots (0)
+  int rmax;       // min(rows, 2k)
+  int tbegin;     // leaf: first position in perm
+  int r0;         // non-leaf: rank of child0 (its pivots come first)
+  int r1;
+  int pad;
+  int64_t piv0;   // non-leaf: pivot pool offsets of the children
+  int64_t piv1;
+  int64_t m_off;  // matrix offset in global scratch (when not in shared memory)
+  int64_t u_off;  // column factors U (rows x rmax, column-major) in scratch
+  int64_t vh_off; // V^ (rows x r, row-major) in the V^ pool
+  int64_t p_off;  // this cluster's pivots in the pivot pool
+  double diam;    // d_tau
+};
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = lane < nw ? red[lane] : 0.0;
+  for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+__device__ __forceinline__ int block_min_int(int v, int* red) {
+  for (int off = 16; off; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = lane < nw ? red[lane] : INT_MAX;
+  for (int off = 16; off; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+__device__ __forceinline__ int block_or(int v, int* red) {
+  v = __any_sync(0xffffffffu, v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = lane < nw ? red[lane] : 0;
+  return __any_sync(0xffffffffu, v);
+}
+
+// Shared memory: row ids [rows_cap] int, pivot rows [rows_cap] int, u [rows_cap],
+// v [2k], reduction scratch [64], then (optionally) the matrix [rows_cap * 2k].
+__global__ void __launch_bounds__(kAcaThreads)
+k_green_aca(const AcaJob* __restrict__ jobs, int k, int rows_cap, int mat_in_smem,
+            const int* __restrict__ perm, const P4* __restrict__ tq,
+            const P4* __restrict__ zq, int* __restrict__ piv_pool,
+            double* __restrict__ mscratch, double* __restrict__ uscratch,
+            double* __restrict__ vh_pool, int* __restrict__ rank_out, double tol, double tie,
+            int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const AcaJob job = jobs[blockIdx.x];
+  const int twok = 2 * k;
+  int* s_rows = reinterpret_cast<int*>(smem_raw);
+  int* s_prow = s_rows + rows_cap;
+  double* s_u = reinterpret_cast<double*>(s_prow + rows_cap + ((2 * rows_cap) & 1));
+  double* s_v = s_u + rows_cap;
+  double* s_red = s_v + twok;
+  int* s_ired = reinterpret_cast<int*>(s_red + 32);
+  double* M = mat_in_smem ? reinterpret_cast<double*>(s_red + 64) : mscratch + job.m_off;
+  double* U = uscratch + job.u_off;
+  const int rows = job.rows;
+  const int tid = threadIdx.x, nth = blockDim.x;
+
+  for (int i = tid; i < rows; i += nth) {
+    int t;
+    if (job.leaf)
+      t = perm[job.tbegin + i];
+    else
+      t = i < job.r0 ? piv_pool[job.piv0 + i] : piv_pool[job.piv1 + (i - job.r0)];
+    s_rows[i] = t;
+  }
+  __syncthreads();
+
+  // A^[i, nu] = sqrt(w) int g(x, z_nu); A^[i, nu + k] = -d sqrt(w) int dg/dn_z(x, z_nu)
+  const P4* z = zq + (int64_t)job.c * k;
+  const int m2 = k / 6;
+  for (int idx = tid; idx < rows * k; idx += nth) {
+    const int i = idx % rows, nu = idx / rows;
+    const P4 zz = z[nu];
+    const int face = nu / m2, d = face >> 1;
+    const double sgn = (face & 1) ? 1.0 : -1.0;
+    const P4* xq = tq + 7 * (int64_t)s_rows[i];
+    double gs = 0.0, ds = 0.0;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const P4 x = xq[q];
+      const double dx = x.x - zz.x, dy = x.y - zz.y, dz = x.z - zz.z;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      const double ir = rsqrt(r2);
+      const double dn = sgn * (d == 0 ? dx : (d == 1 ? dy : dz));
+      gs += x.w * ir;
+      ds += x.w * dn * ir * ir * ir;
+    }
+    M[(int64_t)nu * rows + i] = zz.w * gs * kInv4Pi;
+    M[(int64_t)(nu + k) * rows + i] = -job.diam * zz.w * ds * kInv4Pi;
+  }
+  __syncthreads();
+
+  // cross approximation with complete pivoting (Sect. 3)
+  const int total = rows * twok;
+  int r = 0;
+  double first = 0.0;
+  bool have_update = false;
+  for (;;) {
+    double lmax = 0.0;
+    int lnan = 0;
+    for (int idx = tid; idx < total; idx += nth) {
+      double val = M[idx];
+      if (have_update) {
+        const int i = idx % rows, j = idx / rows;
+        val = __dsub_rn(val, __dmul_rn(s_u[i], s_v[j]));
+        M[idx] = val;
+      }
+      lmax = fmax(lmax, fabs(val));
+      lnan |= (val != val);
+    }
+    const double big = block_max(lmax, s_red);
+    const int anynan = block_or(lnan, s_ired);
+    if (anynan) {
+      if (tid == 0) atomicOr(status, kStatusNumeric);
+      break;
+    }
+    if (r == 0) first = big;
+    if (big == 0.0 || (r > 0 && big <= tol * first)) break;
+    const double thr = big * (1.0 - tie);
+    int lidx = INT_MAX;
+    for (int idx = tid; idx < total; idx += nth)
+      if (fabs(M[idx]) >= thr) {
+        lidx = idx;
+        break;
+      }
+    const int gidx = block_min_int(lidx, s_ired);
+    const int ip = gidx % rows, jp = gidx / rows;
+    const double p = M[gidx];
+    for (int i = tid; i < rows; i += nth) {
+      const double u = __ddiv_rn(M[(int64_t)jp * rows + i], p);
+      s_u[i] = u;
+      U[(int64_t)r * rows + i] = u;
+    }
+    for (int j = tid; j < twok; j += nth) s_v[j] = M[(int64_t)j * rows + ip];
+    if (tid == 0) s_prow[r] = ip;
+    __syncthreads();
+    ++r;
+    have_update = true;
+    if (r == job.rmax) break;
+  }
+  __syncthreads();
+
+  // V^ = U L^{-1}, L = U[P, :] unit lower triangular; V^ row-major rows x r
+  double* Vh = vh_pool + job.vh_off;
+  for (int a = tid; a < rows; a += nth) {
+    for (int c = r - 1; c >= 0; --c) {
+      double s = U[(int64_t)c * rows + a];
+      for (int d = c + 1; d < r; ++d) s -= Vh[(int64_t)a * r + d] * U[(int64_t)c * rows + s_prow[d]];
+      Vh[(int64_t)a * r + c] = s;
+    }
+  }
+  for (int t = tid; t < r; t += nth) piv_pool[job.p_off + t] = s_rows[s_prow[t]];
+  if (tid == 0) rank_out[job.c] = r;
+}
+
+// --------------------------------------------------------------- packing
+
+struct Segment {
+  int64_t src;
+  int64_t dst;
+  int64_t len;
+};
+
+__global__ void k_pack(const Segment* __restrict__ seg, const double* __restrict__ src,
+                       double* __restrict__ d64, float* __restrict__ d32,
+                       __nv_bfloat16* __restrict__ d16) {
+  const Segment s = seg[blockIdx.x];
+  for (int64_t i = threadIdx.x; i < s.len; i += blockDim.x) {
+    const double v = src[s.src + i];
+    d64[s.dst + i] = v;
+    d32[s.dst + i] = (float)v;
+    d16[s.dst + i] = __double2bfloat16(v);
+  }
+}
+
+__global__ void k_convert(int64_t n, const double* __restrict__ src, float* __restrict__ d32,
+                          __nv_bfloat16* __restrict__ d16) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = src[i];
+    d32[i] = (float)v;
+    if (d16) d16[i] = __double2bfloat16(v);
+  }
+}
+
+// ------------------------------------------------------ regular entries
+
+// 7 x 7 rule: sum_p sum_q w_p w_q / (4 pi |x_p - y_q|)
+__device__ __forceinline__ double regular_entry(const P4* __restrict__ xq,
+                                                const P4* __restrict__ yq) {
+  double s = 0.0;
+#pragma unroll
+  for (int p = 0; p < 7; ++p) {
+    const P4 x = xq[p];
+    double sp = 0.0;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const P4 y = yq[q];
+      const double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+      sp += y.w * rsqrt(dx * dx + dy * dy + dz * dz);
+    }
+    s += x.w * sp;
+  }
+  return s * kInv4Pi;
+}
+
+// One CTA per admissible block; the column pivots' nodes are staged in
+// shared memory.  S is row-major r_tau x r_sigma.
+__global__ void k_couple_entries(const int* __restrict__ far_t, const int* __restrict__ far_s,
+                                 const int64_t* __restrict__ soff, const int* __restrict__ rank,
+                                 const int64_t* __restrict__ poff, const int* __restrict__ piv,
+                                 const P4* __restrict__ tq, double* __restrict__ S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  P4* ys = reinterpret_cast<P4*>(smem_raw);
+  const int b = blockIdx.x;
+  const int t = far_t[b], s = far_s[b];
+  const int rt = rank[t], rs = rank[s];
+  const int* pt = piv + poff[t];
+  const int* ps = piv + poff[s];
+  for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) ys[i] = tq[7 * (int64_t)ps[i / 7] + i % 7];
+  __syncthreads();
+  double* out = S + soff[b];
+  for (int idx = threadIdx.x; idx < rt * rs; idx += blockDim.x) {
+    const int a = idx / rs, c = idx % rs;
+    out[idx] = regular_entry(tq + 7 * (int64_t)pt[a], ys + 7 * c);
+  }
+}
+
+struct SingularItem {
+  int64_t pos;  // position in N
+  int ti;
+  int tj;
+};
+
+// One CTA per near block: disjoint pairs by the 7 x 7 rule, touching pairs
+// appended to the list of their case (1 common vertex, 2 common edge,
+// 3 identical).
+__global__ void k_near_entries(const int* __restrict__ near_t, const int* __restrict__ near_s,
+                               const int64_t* __restrict__ noff, const int* __restrict__ begin,
+                               const int* __restrict__ end, const int* __restrict__ perm,
+                               const int* __restrict__ tri, const P4* __restrict__ tq,
+                               double* __restrict__ N, SingularItem* __restrict__ lists,
+                               int64_t cap, unsigned long long* __restrict__ counts,
+                               int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  P4* ys = reinterpret_cast<P4*>(smem_raw);
+  const int b = blockIdx.x;
+  const int t = near_t[b], s = near_s[b];
+  const int bt = begin[t], nt = end[t] - bt, bs = begin[s], ns = end[s] - bs;
+  for (int i = threadIdx.x; i < ns * 7; i += blockDim.x)
+    ys[i] = tq[7 * (int64_t)perm[bs + i / 7] + i % 7];
+  __syncthreads();
+  const int64_t base = noff[b];
+  for (int idx = threadIdx.x; idx < nt * ns; idx += blockDim.x) {
+    const int i = idx / ns, j = idx % ns;
+    const int ti = perm[bt + i], tj = perm[bs + j];
+    int shared = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int va = tri[3 * ti + a];
+      shared += (va == tri[3 * tj]) + (va == tri[3 * tj + 1]) + (va == tri[3 * tj + 2]);
+    }
+    if (shared == 0) {
+      N[base + idx] = regular_entry(tq + 7 * (int64_t)ti, ys + 7 * j);
+    } else {
+      const unsigned long long slot = atomicAdd(&counts[shared], 1ull);
+      if (slot < (unsigned long long)cap) {
+        lists[(shared - 1) * cap + slot] = SingularItem{base + idx, ti, tj};
+      } else {
+        atomicOr(status, kStatusOverflow);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------- Sauter-Schwab (Sect. 8)
+//
+// Both triangles are parametrised over {0 <= u2 <= u1 <= 1} by
+// x(u) = P0 + u1 (P1 - P0) + u2 (P2 - P1) with the shared vertex (or the
+// first shared edge vertex) at P0 = Q0.  The substitutions map [0,1]^4 onto
+// T x T in 6 (identical), 5 (common edge) or 2 (common vertex) pieces; on
+// each piece u = xi * u^(eta), v = xi * v^(eta), so x - y = xi h(eta) and,
+// with the Jacobian xi^3 w^(eta), the integrand is xi^2 w^(eta) / |h(eta)|.
+// The xi-integral is therefore exactly 1/3 and only eta is sampled (q^3
+// Gauss points per piece).
+
+template <int CASE>
+__device__ __forceinline__ double sauter_piece(int piece, double e1, double e2, double e3,
+                                               double& u1, double& u2, double& v1, double& v2) {
+  if (CASE == 3) {
+    const double w = e1 * e1 * e2;
+    switch (piece) {
+      case 0: u1 = 1.0; u2 = 1.0 - e1 + e1 * e2; v1 = 1.0 - e1 * e2 * e3; v2 = 1.0 - e1; break;
+      case 1: v1 = 1.0; v2 = 1.0 - e1 + e1 * e2; u1 = 1.0 - e1 * e2 * e3; u2 = 1.0 - e1; break;
+      case 2: u1 = 1.0; u2 = e1 * (1.0 - e2 + e2 * e3); v1 = 1.0 - e1 * e2; v2 = e1 * (1.0 - e2); break;
+      case 3: v1 = 1.0; v2 = e1 * (1.0 - e2 + e2 * e3); u1 = 1.0 - e1 * e2; u2 = e1 * (1.0 - e2); break;
+      case 4: u1 = 1.0 - e1 * e2 * e3; u2 = e1 * (1.0 - e2 * e3); v1 = 1.0; v2 = e1 * (1.0 - e2); break;
+      default: v1 = 1.0 - e1 * e2 * e3; v2 = e1 * (1.0 - e2 * e3); u1 = 1.0; u2 = e1 * (1.0 - e2); break;
+    }
+    return w;
+  } else if (CASE == 2) {
+    switch (piece) {
+      case 0: u1 = 1.0; u2 = e1 * e3; v1 = 1.0 - e1 * e2; v2 = e1 * (1.0 - e2); return e1 * e1;
+      case 1: u1 = 1.0; u2 = e1; v1 = 1.0 - e1 * e2 * e3; v2 = e1 * e2 * (1.0 - e3); break;
+      case 2: u1 = 1.0 - e1 * e2; u2 = e1 * (1.0 - e2); v1 = 1.0; v2 = e1 * e2 * e3; break;
+      case 3: u1 = 1.0 - e1 * e2 * e3; u2 = e1 * e2 * (1.0 - e3); v1 = 1.0; v2 = e1; break;
+      default: u1 = 1.0 - e1 * e2 * e3; u2 = e1 * (1.0 - e2 * e3); v1 = 1.0; v2 = e1 * e2; break;
+    }
+    return e1 * e1 * e2;
+  } else {
+    if (piece == 0) {
+      u1 = 1.0; u2 = e1; v1 = e2; v2 = e2 * e3;
+    } else {
+      v1 = 1.0; v2 = e1; u1 = e2; u2 = e2 * e3;
+    }
+    return e2;
+  }
+}
+
+// one warp per touching pair
+template <int CASE>
+__global__ void k_singular(const SingularItem* __restrict__ items,
+                           const unsigned long long* __restrict__ counts, int64_t cap,
+                           const int* __restrict__ tri, const double* __restrict__ vert, Rules rules,
+                           double* __restrict__ N) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t count = min((long long)counts[CASE], (long long)cap);
+  if (w >= count) return;
+  const SingularItem it = items[w];
+  int ti[3], tj[3];
+  for (int a = 0; a < 3; ++a) {
+    ti[a] = tri[3 * it.ti + a];
+    tj[a] = tri[3 * it.tj + a];
+  }
+  int P[3], Q[3];
+  if (CASE == 3) {
+    for (int a = 0; a < 3; ++a) P[a] = Q[a] = ti[a];
+  } else if (CASE == 2) {
+    // shared ids in the order they occur in triangle i, then the others
+    int sh[2], ns = 0, oi = -1, oj = -1;
+    for (int a = 0; a < 3; ++a) {
+      const bool in_j = ti[a] == tj[0] || ti[a] == tj[1] || ti[a] == tj[2];
+      if (in_j) sh[ns++] = ti[a]; else oi = ti[a];
+    }
+    for (int a = 0; a < 3; ++a)
+      if (tj[a] != sh[0] && tj[a] != sh[1]) oj = tj[a];
+    P[0] = Q[0] = sh[0];
+    P[1] = Q[1] = sh[1];
+    P[2] = oi;
+    Q[2] = oj;
+  } else {
+    int pi = 0, pj = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (ti[a] == tj[b]) { pi = a; pj = b; }
+    for (int a = 0; a < 3; ++a) {
+      P[a] = ti[(pi + a) % 3];
+      Q[a] = tj[(pj + a) % 3];
+    }
+  }
+  double p[3][3], qv[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) {
+      p[a][d] = vert[3 * P[a] + d];
+      qv[a][d] = vert[3 * Q[a] + d];
+    }
+  double e1v[3], e2v[3], f1v[3], f2v[3];
+  for (int d = 0; d < 3; ++d) {
+    e1v[d] = p[1][d] - p[0][d];
+    e2v[d] = p[2][d] - p[1][d];
+    f1v[d] = qv[1][d] - qv[0][d];
+    f2v[d] = qv[2][d] - qv[1][d];
+  }
+  const int q = rules.q, q3 = q * q * q;
+  constexpr int pieces = CASE == 3 ? 6 : (CASE == 2 ? 5 : 2);
+  double acc = 0.0;
+  for (int s = lane; s < pieces * q3; s += 32) {
+    const int piece = s / q3, r = s % q3;
+    const int a = r / (q * q), b = (r / q) % q, c = r % q;
+    const double e1 = rules.ss_t[a], e2 = rules.ss_t[b], e3 = rules.ss_t[c];
+    double u1, u2, v1, v2;
+    const double wj = sauter_piece<CASE>(piece, e1, e2, e3, u1, u2, v1, v2);
+    double h[3];
+    for (int d = 0; d < 3; ++d) h[d] = u1 * e1v[d] + u2 * e2v[d] - v1 * f1v[d] - v2 * f2v[d];
+    const double r2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
+    acc += rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * wj * rsqrt(r2);
+  }
+  for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) {
+    double jp[3], jq[3];
+    jp[0] = e1v[1] * e2v[2] - e1v[2] * e2v[1];
+    jp[1] = e1v[2] * e2v[0] - e1v[0] * e2v[2];
+    jp[2] = e1v[0] * e2v[1] - e1v[1] * e2v[0];
+    jq[0] = f1v[1] * f2v[2] - f1v[2] * f2v[1];
+    jq[1] = f1v[2] * f2v[0] - f1v[0] * f2v[2];
+    jq[2] = f1v[0] * f2v[1] - f1v[1] * f2v[0];
+    const double JP = sqrt(jp[0] * jp[0] + jp[1] * jp[1] + jp[2] * jp[2]);
+    const double JQ = sqrt(jq[0] * jq[0] + jq[1] * jq[1] + jq[2] * jq[2]);
+    N[it.pos] = acc * JP * JQ * (kInv4Pi / 3.0);
+  }
+}
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+int check_status(DevMem& st, cudaStream_t s, const char* where) {
+  int h = 0;
+  GCA_TRY_CUDA(cudaMemcpyAsync(&h, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GCA_TRY_CUDA(cudaStreamSynchronize(s));
+  if (h & kStatusNumeric) {
+    set_error(std::string(where) + ": NaN in the Green quadrature matrix");
+    return GCA_ERR_NUMERIC;
+  }
+  if (h & kStatusOverflow) {
+    set_error(std::string(where) + ": singular-pair list overflow (mesh not conforming?)");
+    return GCA_ERR_INVALID_ARG;
+  }
+  return GCA_OK;
+}
+
+}  // namespace
+
+// The whole construction; see the header of this file.
+int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
+          gca_h2** out) {
+  auto t0 = std::chrono::steady_clock::now();
+  GCA_TRY(validate_mesh(mesh));
+  GCA_TRY(validate_tree(mesh, tree, GCA_MAX_LEAF));
+  if (!prm || !(prm->eta > 0.0) || prm->box_gauss_m < 1 || prm->box_gauss_m > GCA_MAX_BOX_M ||
+      !(prm->aca_tol >= 0.0) || prm->tri_rule != 7 || prm->sauter_q < 1 ||
+      prm->sauter_q > GCA_MAX_SAUTER_Q || prm->flags != 0) {
+    set_error("gca_build: invalid parameters");
+    return GCA_ERR_INVALID_ARG;
+  }
+  auto h = std::make_unique<gca_h2>();
+  h->params = *prm;
+  h->n = mesh->nt;
+  h->nv = mesh->nv;
+  h->nc = tree->nclusters;
+  h->m = prm->box_gauss_m;
+  h->k = 6 * h->m * h->m;
+  const int n = h->n, nc = h->nc, k = h->k;
+  const double margin = prm->omega_margin < 0.0 ? 1.0 / (4.0 * prm->eta) : prm->omega_margin;
+  const Rules rules = make_rules(h->m, prm->sauter_q);
+
+  h->perm.assign(tree->perm, tree->perm + n);
+  h->begin.assign(tree->begin, tree->begin + nc);
+  h->end.assign(tree->end, tree->end + nc);
+  h->child0.assign(tree->child0, tree->child0 + nc);
+  h->child1.assign(tree->child1, tree->child1 + nc);
+  h->level.assign(tree->level, tree->level + nc);
+  h->parent.assign(nc, -1);
+  for (int c = 0; c < nc; ++c)
+    if (h->child0[c] >= 0) h->parent[h->child0[c]] = h->parent[h->child1[c]] = c;
+  h->depth = *std::max_element(h->level.begin(), h->level.end());
+  h->by_level.assign(h->depth + 1, {});
+  for (int c = 0; c < nc; ++c) {
+    h->by_level[h->level[c]].push_back(c);
+    if (h->child0[c] < 0) {
+      h->leaves.push_back(c);
+      h->max_leaf = std::max(h->max_leaf, h->end[c] - h->begin[c]);
+    }
+  }
+
+  // geometry upload
+  std::vector<double> vert(mesh->vertices, mesh->vertices + 3LL * mesh->nv);
+  std::vector<int> tri(mesh->triangles, mesh->triangles + 3LL * n);
+  GCA_TRY(upload(h->d_vert, vert, st));
+  GCA_TRY(upload(h->d_tri, tri, st));
+  GCA_TRY(upload(h->d_perm, h->perm, st));
+  GCA_TRY(upload(h->d_begin, h->begin, st));
+  GCA_TRY(upload(h->d_end, h->end, st));
+  DevMem d_tq, d_box, d_diam, d_zq, d_status;
+  GCA_TRY(d_tq.alloc(sizeof(P4) * 7 * (size_t)n));
+  GCA_TRY(d_box.alloc(sizeof(double) * 6 * (size_t)nc));
+  GCA_TRY(d_status.alloc(sizeof(int)));
+  GCA_TRY_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), st));
+  k_tri_geom<<<blocks_for(n, 128), 128, 0, st>>>(n, h->d_vert.as<double>(), h->d_tri.as<int>(), rules,
+                                                d_tq.as<P4>());
+  k_cluster_boxes<<<blocks_for(32LL * nc, 128), 128, 0, st>>>(
+      nc, h->d_begin.as<int>(), h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(),
+      h->d_vert.as<double>(), d_box.as<double>());
+  GCA_TRY_CUDA(cudaGetLastError());
+  std::vector<double> box(6 * (size_t)nc), diam;
+  GCA_TRY_CUDA(cudaMemcpyAsync(box.data(), d_box.p, box.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GCA_TRY_CUDA(cudaStreamSynchronize(st));
+  box_diameters(box, diam);
+  block_tree(h->child0, h->child1, box, diam, prm->eta, h->far_t, h->far_s, h->near_t, h->near_s);
+  GCA_TRY(upload(d_diam, diam, st));
+
+  // box quadrature
+  GCA_TRY(d_zq.alloc(sizeof(P4) * (size_t)nc * k));
+  k_box_quad<<<blocks_for((int64_t)nc * k, 128), 128, 0, st>>>(nc, rules, d_box.as<double>(),
+                                                               d_diam.as<double>(), margin,
+                                                               d_zq.as<P4>());
+  GCA_TRY_CUDA(cudaGetLastError());
+
+  // nested bases, level by level from the deepest
+  h->rank.assign(nc, 0);
+  h->poff.assign(nc, -1);
+  std::vector<int64_t> vh_off(nc, -1);
+  std::vector<int> rows_of(nc, 0);
+  int64_t piv_cap = 0, vh_cap = 0;
+  for (int c = 1; c < nc; ++c) {
+    // upper bounds, refined per level below
+    piv_cap += std::min<int64_t>(h->end[c] - h->begin[c], 2 * k);
+  }
+  DevMem d_piv, d_rank, d_vh, d_mscr, d_uscr, d_jobs;
+  GCA_TRY(d_piv.alloc(sizeof(int) * (size_t)std::max<int64_t>(piv_cap, 1)));
+  GCA_TRY(d_rank.alloc(sizeof(int) * (size_t)nc));
+  GCA_TRY_CUDA(cudaMemsetAsync(d_rank.p, 0, sizeof(int) * nc, st));
+  // V^ pool: rows <= min(|tau-hat|, 4k) for every cluster bounds its size
+  int64_t piv_used = 0, vh_used = 0;
+  for (int c = 1; c < nc; ++c) {
+    int64_t rows = h->child0[c] < 0 ? (h->end[c] - h->begin[c])
+                                    : std::min<int64_t>(h->end[c] - h->begin[c], 4 * k);
+    vh_cap += rows * std::min<int64_t>(rows, 2 * k);
+  }
+  GCA_TRY(d_vh.alloc(sizeof(double) * (size_t)std::max<int64_t>(vh_cap, 1)));
+  int dev = 0;
+  GCA_TRY_CUDA(cudaGetDevice(&dev));
+  int smem_optin = 0;
+  GCA_TRY_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  GCA_TRY_CUDA(cudaFuncSetAttribute(k_green_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+  const double tie = std::ldexp(1.0, -40);
+  for (int L = h->depth; L >= 1; --L) {
+    std::vector<AcaJob> jobs;
+    int rows_cap = 0;
+    for (int c : h->by_level[L]) {
+      AcaJob j{};
+      j.c = c;
+      j.leaf = h->child0[c] < 0;
+      if (j.leaf) {
+        j.rows = h->end[c] - h->begin[c];
+        j.tbegin = h->begin[c];
+      } else {
+        const int c0 = h->child0[c], c1 = h->child1[c];
+        j.r0 = h->rank[c0];
+        j.r1 = h->rank[c1];
+        j.rows = j.r0 + j.r1;
+        j.piv0 = h->poff[c0];
+        j.piv1 = h->poff[c1];
+      }
+      j.rmax = std::min(j.rows, 2 * k);
+      j.diam = diam[c];
+      j.p_off = piv_used;
+      h->poff[c] = piv_used;
+      piv_used += j.rmax;
+      j.vh_off = vh_used;
+      vh_off[c] = vh_used;
+      vh_used += (int64_t)j.rows * j.rmax;
+      rows_of[c] = j.rows;
+      rows_cap = std::max(rows_cap, j.rows);
+      jobs.push_back(j);
+    }
+    if (jobs.empty()) continue;
+    if (piv_used > piv_cap || vh_used > vh_cap) {
+      set_error("gca_build: internal pool bound exceeded");
+      return GCA_ERR_INVALID_ARG;
+    }
+    rows_cap = std::max(rows_cap, 1);
+    const size_t head = (size_t)2 * rows_cap * sizeof(int) + ((2 * rows_cap) & 1) * sizeof(int) +
+                        sizeof(double) * ((size_t)rows_cap + 2 * k + 64);
+    const size_t mat = sizeof(double) * (size_t)rows_cap * 2 * k;
+    const bool in_smem = head + mat <= (size_t)smem_optin;
+    int64_t m_used = 0, u_used = 0;
+    for (auto& j : jobs) {
+      j.m_off = m_used;
+      if (!in_smem) m_used += (int64_t)j.rows * 2 * k;
+      j.u_off = u_used;
+      u_used += (int64_t)j.rows * j.rmax;
+    }
+    GCA_TRY(d_mscr.reserve(sizeof(double) * (size_t)std::max<int64_t>(m_used, 1)));
+    GCA_TRY(d_uscr.reserve(sizeof(double) * (size_t)std::max<int64_t>(u_used, 1)));
+    GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * jobs.size()));
+    GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, jobs.data(), sizeof(AcaJob) * jobs.size(),
+                                 cudaMemcpyHostToDevice, st));
+    const size_t smem = head + (in_smem ? mat : 0);
+    k_green_aca<<<(unsigned)jobs.size(), kAcaThreads, smem, st>>>(
+        d_jobs.as<AcaJob>(), k, rows_cap, in_smem ? 1 : 0, h->d_perm.as<int>(), d_tq.as<P4>(),
+        d_zq.as<P4>(), d_piv.as<int>(), d_mscr.as<double>(), d_uscr.as<double>(),
+        d_vh.as<double>(), d_rank.as<int>(), prm->aca_tol, tie, d_status.as<int>());
+    GCA_TRY_CUDA(cudaGetLastError());
+    GCA_TRY(check_status(d_status, st, "cross approximation"));
+    GCA_TRY_CUDA(cudaMemcpyAsync(h->rank.data(), d_rank.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));
+  }
+  d_mscr.release();
+  d_uscr.release();
+
+  // offsets of the stored coefficients
+  h->xoff.assign(nc + 1, 0);
+  for (int c = 0; c < nc; ++c) h->xoff[c + 1] = h->xoff[c] + h->rank[c];
+  h->rank_sum = h->xoff[nc];
+  h->max_rank = *std::max_element(h->rank.begin(), h->rank.end());
+  h->voff.assign(nc, -1);
+  h->eoff.assign(nc, -1);
+  std::vector<Segment> segs;
+  for (int c = 1; c < nc; ++c) {
+    if (h->child0[c] < 0) {
+      h->voff[c] = h->v_entries;
+      const int64_t len = (int64_t)(h->end[c] - h->begin[c]) * h->rank[c];
+      h->v_entries += len;
+    }
+  }
+  for (int c = 1; c < nc; ++c)
+    if (h->parent[c] > 0) {
+      h->eoff[c] = h->e_entries;
+      h->e_entries += (int64_t)h->rank[c] * h->rank[h->parent[c]];
+    }
+  std::vector<Segment> vseg, eseg;
+  for (int c = 1; c < nc; ++c) {
+    const int r = h->rank[c];
+    if (h->child0[c] < 0) {
+      vseg.push_back({vh_off[c], h->voff[c], (int64_t)rows_of[c] * r});
+    } else if (c != 0) {
+      const int c0 = h->child0[c], c1 = h->child1[c];
+      eseg.push_back({vh_off[c], h->eoff[c0], (int64_t)h->rank[c0] * r});
+      eseg.push_back({vh_off[c] + (int64_t)h->rank[c0] * r, h->eoff[c1], (int64_t)h->rank[c1] * r});
+    }
+  }
+  GCA_TRY(h->V64.alloc(sizeof(double) * h->v_entries));
+  GCA_TRY(h->V32.alloc(sizeof(float) * h->v_entries));
+  GCA_TRY(h->V16.alloc(sizeof(__nv_bfloat16) * h->v_entries));
+  GCA_TRY(h->E64.alloc(sizeof(double) * h->e_entries));
+  GCA_TRY(h->E32.alloc(sizeof(float) * h->e_entries));
+  GCA_TRY(h->E16.alloc(sizeof(__nv_bfloat16) * h->e_entries));
+  DevMem d_seg;
+  for (auto* sv : {&vseg, &eseg}) {
+    if (sv->empty()) continue;
+    GCA_TRY(d_seg.reserve(sizeof(Segment) * sv->size()));
+    GCA_TRY_CUDA(cudaMemcpyAsync(d_seg.p, sv->data(), sizeof(Segment) * sv->size(),
+                                 cudaMemcpyHostToDevice, st));
+    const bool isv = sv == &vseg;
+    k_pack<<<(unsigned)sv->size(), 256, 0, st>>>(
+        d_seg.as<Segment>(), d_vh.as<double>(), isv ? h->V64.as<double>() : h->E64.as<double>(),
+        isv ? h->V32.as<float>() : h->E32.as<float>(),
+        isv ? h->V16.as<__nv_bfloat16>() : h->E16.as<__nv_bfloat16>());
+    GCA_TRY_CUDA(cudaGetLastError());
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_seg is reused
+  }
+  d_vh.release();
+
+  // pivots (host copy) and the pivot pool for the entry kernels
+  h->piv.resize(std::max<int64_t>(piv_used, 1));
+  GCA_TRY_CUDA(cudaMemcpyAsync(h->piv.data(), d_piv.p, sizeof(int) * piv_used, cudaMemcpyDeviceToHost, st));
+  GCA_TRY(upload(h->d_rank, h->rank, st));
+  DevMem d_poff;
+  GCA_TRY(upload(d_poff, h->poff, st));
+
+  // coupling matrices
+  const int nfar = (int)h->far_t.size(), nnear = (int)h->near_t.size();
+  h->soff.assign(nfar + 1, 0);
+  for (int b = 0; b < nfar; ++b)
+    h->soff[b + 1] = h->soff[b] + (int64_t)h->rank[h->far_t[b]] * h->rank[h->far_s[b]];
+  h->s_entries = h->soff[nfar];
+  GCA_TRY(upload(h->d_far_t, h->far_t, st));
+  GCA_TRY(upload(h->d_far_s, h->far_s, st));
+  GCA_TRY(upload(h->d_soff, h->soff, st));
+  GCA_TRY(h->S64.alloc(sizeof(double) * h->s_entries));
+  if (nfar > 0) {
+    const size_t smem = sizeof(P4) * 7 * (size_t)std::max(h->max_rank, 1);
+    GCA_TRY_CUDA(cudaFuncSetAttribute(k_couple_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_couple_entries<<<nfar, 256, smem, st>>>(h->d_far_t.as<int>(), h->d_far_s.as<int>(),
+                                             h->d_soff.as<int64_t>(), h->d_rank.as<int>(),
+                                             d_poff.as<int64_t>(), d_piv.as<int>(), d_tq.as<P4>(),
+                                             h->S64.as<double>());
+    GCA_TRY_CUDA(cudaGetLastError());
+  }
+
+  // near field
+  h->noff.assign(nnear + 1, 0);
+  for (int b = 0; b < nnear; ++b) {
+    const int t = h->near_t[b], s = h->near_s[b];
+    h->noff[b + 1] = h->noff[b] + (int64_t)(h->end[t] - h->begin[t]) * (h->end[s] - h->begin[s]);
+  }
+  h->n_entries = h->noff[nnear];
+  GCA_TRY(upload(h->d_near_t, h->near_t, st));
+  GCA_TRY(upload(h->d_near_s, h->near_s, st));
+  GCA_TRY(upload(h->d_noff, h->noff, st));
+  GCA_TRY(h->N64.alloc(sizeof(double) * h->n_entries));
+  // bound on touching ordered pairs: sum over vertices of (triangles at v)^2
+  std::vector<int64_t> valence(mesh->nv, 0);
+  for (int t = 0; t < 3 * n; ++t) valence[tri[t]]++;
+  int64_t cap = 0;
+  for (auto v : valence) cap += v * v;
+  DevMem d_items, d_counts;
+  GCA_TRY(d_items.alloc(sizeof(SingularItem) * 3 * (size_t)cap));
+  GCA_TRY(d_counts.alloc(sizeof(unsigned long long) * 4));
+  GCA_TRY_CUDA(cudaMemsetAsync(d_counts.p, 0, sizeof(unsigned long long) * 4, st));
+  if (nnear > 0) {
+    const size_t smem = sizeof(P4) * 7 * (size_t)h->max_leaf;
+    GCA_TRY_CUDA(cudaFuncSetAttribute(k_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_near_entries<<<nnear, 256, smem, st>>>(
+        h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
+        h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), d_tq.as<P4>(),
+        h->N64.as<double>(), d_items.as<SingularItem>(), cap, d_counts.as<unsigned long long>(),
+        d_status.as<int>());
+    GCA_TRY_CUDA(cudaGetLastError());
+    GCA_TRY(check_status(d_status, st, "near field"));
+    unsigned long long counts[4];
+    GCA_TRY_CUDA(cudaMemcpyAsync(counts, d_counts.p, sizeof(counts), cudaMemcpyDeviceToHost, st));
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));
+    for (int c = 1; c <= 3; ++c) h->n_singular[c] = (int64_t)counts[c];
+    h->n_singular[0] = h->n_entries - (h->n_singular[1] + h->n_singular[2] + h->n_singular[3]);
+    const SingularItem* items = d_items.as<SingularItem>();
+    const unsigned long long* cnt = d_counts.as<unsigned long long>();
+    if (counts[1])
+      k_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
+          items, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), rules, h->N64.as<double>());
+    if (counts[2])
+      k_singular<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
+          items + cap, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), rules, h->N64.as<double>());
+    if (counts[3])
+      k_singular<3><<<blocks_for(32LL * counts[3], 256), 256, 0, st>>>(
+          items + 2 * cap, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), rules,
+          h->N64.as<double>());
+    GCA_TRY_CUDA(cudaGetLastError());
+  }
+
+  // reduced-precision copies
+  GCA_TRY(h->S32.alloc(sizeof(float) * h->s_entries));
+  GCA_TRY(h->S16.alloc(sizeof(__nv_bfloat16) * h->s_entries));
+  GCA_TRY(h->N32.alloc(sizeof(float) * h->n_entries));
+  if (h->s_entries)
+    k_convert<<<1184, 256, 0, st>>>(h->s_entries, h->S64.as<double>(), h->S32.as<float>(),
+                                    h->S16.as<__nv_bfloat16>());
+  if (h->n_entries)
+    k_convert<<<1184, 256, 0, st>>>(h->n_entries, h->N64.as<double>(), h->N32.as<float>(), nullptr);
+  GCA_TRY_CUDA(cudaGetLastError());
+
+  GCA_TRY(finish_plan(h.get(), st));
+  GCA_TRY_CUDA(cudaStreamSynchronize(st));
+  h->build_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = h.release();
+  return GCA_OK;
+}
+
+}  // namespace gca

@@ -1,0 +1,128 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point declared in include/gca.h, its structs have the layout the header
+gives them, the cluster-tree helper matches the oracle bit for bit, and
+invalid input is rejected before any device work."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+import paper_1810_08429_b300 as gca
+from oracle import cluster
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gca.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:int|void|const char\*)\s+(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("gca_build", "h2_matvec", "h2_matvec_transpose", "gca_tree_build",
+                     "gca_h2_stats", "gca_h2_export", "gca_free", "gca_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(gca.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layout_matches_header(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "gca.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\","
+        "sizeof(gca_mesh),sizeof(gca_tree),sizeof(gca_params),sizeof(gca_stats),"
+        "sizeof(gca_host_dump),offsetof(gca_stats,rank_sum),offsetof(gca_params,omega_margin));"
+        "return 0;}\n")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [ctypes.sizeof(gca._Mesh), ctypes.sizeof(gca._Tree), ctypes.sizeof(gca._Params),
+            ctypes.sizeof(gca._Stats), ctypes.sizeof(gca._Dump), gca._Stats.rank_sum.offset,
+            gca._Params.omega_margin.offset]
+    assert got == want
+
+
+@pytest.mark.parametrize("name,leaf", [("sphere80", 8), ("sphere1280", 32), ("perturbed1280", 32),
+                                       ("sphere20480", 64), ("perturbed20480", 64),
+                                       ("ellipsoid1280", 16)])
+def test_tree_build_matches_oracle(name, leaf):
+    v, t = synth.mesh_for_config(name)
+    ours = gca.tree_build(v, t, leaf)
+    ref = cluster.build_tree(v, t, leaf)
+    for key in ("perm", "begin", "end", "child0", "child1", "level"):
+        assert np.array_equal(ours[key], ref[key]), key
+
+
+def test_tree_build_degenerate_split():
+    # all centroids share x and y: the median rule must kick in
+    n = 40
+    v = np.zeros((3 * n, 3))
+    t = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    for i in range(n):
+        v[3 * i] = [0.0, 0.0, 0.0]
+        v[3 * i + 1] = [1.0, 0.0, 0.0]
+        v[3 * i + 2] = [0.0, 1.0, float(i % 3)]
+    ours = gca.tree_build(v, t, 4)
+    ref = cluster.build_tree(v, t, 4)
+    for key in ("perm", "begin", "end", "child0", "child1", "level"):
+        assert np.array_equal(ours[key], ref[key]), key
+
+
+def test_tree_build_single_leaf():
+    v, t = synth.icosahedron()
+    tr = gca.tree_build(v, t, 64)
+    assert len(tr["begin"]) == 1 and tr["child0"][0] == -1
+
+
+def _raw_build(v, t, tree, params):
+    m, keep_m = gca._mesh(v, t)
+    tr, keep_t = gca._tree(tree)
+    p = params._c()
+    h = ctypes.c_void_p(None)
+    return gca.lib.gca_build(ctypes.byref(m), ctypes.byref(tr), ctypes.byref(p), None,
+                             ctypes.byref(h)), h
+
+
+def test_invalid_input_rejected_on_host():
+    v, t = synth.icosphere(1)
+    tree = gca.tree_build(v, t, 8)
+    p = gca.Params(leaf_size=8)
+    # bad vertex id
+    bad = t.copy()
+    bad[3, 1] = 10_000
+    st, h = _raw_build(v, bad, tree, p)
+    assert st == -1 and not h.value
+    # NaN coordinate
+    vn = v.copy()
+    vn[5, 2] = np.nan
+    st, h = _raw_build(vn, t, tree, p)
+    assert st == -4 and not h.value
+    # broken tree: children do not split the parent range
+    tb = {k: a.copy() for k, a in tree.items()}
+    tb["end"][tb["child0"][0]] -= 1
+    st, h = _raw_build(v, t, tb, p)
+    assert st == -1 and not h.value
+    # unsupported parameter
+    st, h = _raw_build(v, t, tree, gca.Params(leaf_size=8, box_gauss_m=7))
+    assert st == -1 and not h.value
+    st, h = _raw_build(v, t, tree, gca.Params(leaf_size=8, tri_rule=6))
+    assert st == -1 and not h.value
+    with pytest.raises(gca.GCAError):
+        gca.tree_build(v, bad, 8)
+    assert "vertex id" in gca.lib.gca_last_error().decode()

@@ -160,6 +160,34 @@ def test_aca_stopping_rule():
     assert np.abs(res.V @ A[res.rows, :] - A).max() < 1e-4
 
 
+def test_interpolation_sensitivity_at_tight_tolerance(monkeypatch):
+    """Why bases are compared more loosely than products at tol 1e-8.
+
+    One rounding error of noise on the Green matrices (relative 2e-16) moves
+    the transfer matrices E by up to ~1e-9, while the pivots stay the same and
+    the H^2 product moves by ~1e-15: V^ = A[:, Q] A[P, Q]^{-1} is
+    ill-conditioned along directions that A[P, :] maps to almost nothing.
+    """
+    v, t = synth.mesh_for_config("ellipsoid1280")
+    p = Params(leaf_size=24, eta=2.0, box_gauss_m=3, aca_tol=1e-8, sauter_q=4)
+    H0 = gca.build_h2(v, t, p)
+    orig = gca.green_matrix
+    rng = np.random.default_rng(0)
+    monkeypatch.setattr(gca, "green_matrix",
+                        lambda *a, **k: (lambda A: A * (1 + 2e-16 * rng.standard_normal(A.shape)))(
+                            orig(*a, **k)))
+    H1 = gca.build_h2(v, t, p)
+    for c in range(1, len(H0.bases.pivots)):
+        assert np.array_equal(H0.bases.pivots[c], H1.bases.pivots[c])
+    dE = max(np.abs(H0.bases.E[c] - H1.bases.E[c]).max() for c in H0.bases.E)
+    x = synth.normal_rhs(len(t), 4, 1)
+    y0, y1 = h2.matvec(H0, x), h2.matvec(H1, x)
+    dy = (np.linalg.norm(y0 - y1, axis=0) / np.linalg.norm(y0, axis=0)).max()
+    assert dy < 1e-13
+    assert dE < 1e-8
+    assert dE > 100 * dy
+
+
 # ---------------------------------------------------------------- Sect. 4
 
 def test_nested_bases_interpolate(h2_1280):
