@@ -1,0 +1,404 @@
+"""Benchmark of the GCA-H^2 hot path on one B300 (or N replicas).
+
+Workload: the 20480-triangle unit sphere (icosahedron refined five times)
+and the same sphere radially perturbed by 0.1 sin(3 theta) cos(2 phi);
+leaf size 64, eta = 2, 4 x 4 Gauss points per box face (k = 96), ACA
+tolerance 1e-8, Sauter-Schwab order 5; 16 right-hand sides N(0, 1), seed 0.
+
+One step = the whole hot path on both meshes: gca_build (boxes, box
+quadrature, Green matrices + ACA per level, nested bases, coupling and
+near-field entries, reduced-precision copies) followed by the H^2 products
+y = G_H2 x in float64, float32 and bfloat16 and the transposed product in
+float32.  Inputs are resident in HBM when the timed region starts; the
+stored matrices (>= 480 MB per mesh in float32) exceed the 126 MB L2, so
+no flush is needed between products.
+
+The headline `value` is the algorithmic HBM throughput of the float32
+product (bytes of V, E, S, N once plus x read and y written, divided by the
+product's device time).  `build_s` is the device time of building both
+meshes.  Under torchrun every rank runs the same workload on its own GPU
+(weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = ("GCA-H² build s & matvec GB/s (frac HBM peak), FP32/BF16 vs FP64 at stated err")
+MESHES = ("sphere20480", "perturbed20480")
+PARAMS = dict(leaf_size=64, eta=2.0, box_gauss_m=4, aca_tol=1e-8, sauter_q=5)
+NRHS = 16
+FLOPS_PER_EVAL = 11  # 3 differences, 5 for |d|^2, 1 rsqrt, 2 multiply-accumulate
+
+
+def config(extra=None):
+    c = {"workload": "sphere20480+perturbed20480 (2 meshes x 20480 triangles)",
+         "leaf_size": 64, "eta": 2.0, "box_gauss_m": 4, "aca_tol": 1e-8, "sauter_q": 5,
+         "nrhs": NRHS, "l2": "no flush: stored matrices exceed the 126 MB L2",
+         "step": "gca_build x2 + h2_matvec f64/f32/bf16 + h2_matvec_transpose f32, per mesh"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def product_bytes(st, prec, n, R):
+    sm = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+    sv = 8 if prec == "f64" else 4
+    return (sm * (st["v_entries"] + st["e_entries"] + st["s_entries"])
+            + sv * st["n_entries"] + 2 * sv * n * R)
+
+
+def build_evals(st, q):
+    regular = 49 * (st["s_entries"] + st["n_singular"][0])
+    singular = q ** 3 * (2 * st["n_singular"][1] + 5 * st["n_singular"][2]
+                         + 6 * st["n_singular"][3])
+    return {"couple_entries": 49 * st["s_entries"], "near_entries": 49 * st["n_singular"][0],
+            "singular": singular, "total": regular + singular}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6400.0)), "measured"
+    return 6400.0, "fallback"
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(mesh="sphere1280", reps=5):
+    """The oracle on a bounded sample: its own GCA-H^2 of a smaller sphere with
+    the workload's parameters, then timed float64 products with 16 RHS."""
+    from oracle import gca as ogca, h2 as oh2
+    from oracle.params import Params as OParams
+    v, t = synth.mesh_for_config(mesh)
+    p = OParams(**PARAMS)
+    t0 = time.perf_counter()
+    H = ogca.build_h2(v, t, p)
+    tb = time.perf_counter() - t0
+    st = oh2.storage(H)
+    x = synth.normal_rhs(len(t), NRHS, seed=0)
+    oh2.matvec(H, x)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oh2.matvec(H, x)
+        times.append(time.perf_counter() - t0)
+    byt = 8 * st["total"] + 2 * 8 * len(t) * NRHS
+    return {"gbs": byt / statistics.median(times) / 1e9, "build_s": tb,
+            "matvec_s": statistics.median(times), "n": len(t), "mesh": mesh,
+            "cores": blas_threads()}
+
+
+def run_reference(args):
+    """CPU oracle arm: same metric, unit and config; bounded oracle samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    mesh = "sphere1280"
+    from oracle import gca as ogca, h2 as oh2
+    from oracle.params import Params as OParams
+    v, t = synth.mesh_for_config(mesh)
+    H = ogca.build_h2(v, t, OParams(**PARAMS))
+    st = oh2.storage(H)
+    x = synth.normal_rhs(len(t), NRHS, seed=0)
+    byt = 8 * st["total"] + 2 * 8 * len(t) * NRHS
+    for _ in range(args.warmup):
+        oh2.matvec(H, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oh2.matvec(H, x)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = byt / dt / 1e9
+    sample = (f"oracle float64 H2 product, 16 RHS, on its own GCA-H2 of the {len(t)}-triangle "
+              f"sphere built with the workload's parameters (build not timed)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"sample_mesh": mesh}),
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": blas_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1810_08429_b300 as gca
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # workload, host side
+    meshes, trees = [], []
+    for name in MESHES:
+        v, t = synth.mesh_for_config(name)
+        meshes.append((v, t))
+        trees.append(gca.tree_build(v, t, PARAMS["leaf_size"]))
+    n = meshes[0][1].shape[0]
+    prm = gca.Params(**PARAMS)
+    xs64 = [torch.from_numpy(synth.normal_rhs(len(t), NRHS, seed=0)).to(dev) for _, t in meshes]
+    xs32 = [x.float() for x in xs64]
+    ys = {p: [torch.empty((NRHS, len(t)), dtype=torch.float64 if p == "f64" else torch.float32,
+                          device=dev).t() for _, t in meshes] for p in ("f64", "f32", "bf16", "f32T")}
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    marks = []
+
+    def step(record):
+        hs = []
+        for (v, t), tr in zip(meshes, trees):
+            a = ev()
+            hs.append(gca.build(v, t, tr, prm))
+            if record:
+                marks.append(("build", a, ev()))
+        for i, h in enumerate(hs):
+            for p, x, tr_ in (("f64", xs64[i], False), ("f32", xs32[i], False),
+                              ("bf16", xs32[i], False), ("f32T", xs32[i], True)):
+                a = ev()
+                h.matvec(x, "f32" if p == "f32T" else p, transpose=tr_, out=ys[p][i])
+                if record:
+                    marks.append((p + f".{i}", a, ev()))
+        return hs
+
+    hs = None
+    for _ in range(args.warmup):
+        hs = step(False)
+    stats = [h.stats() for h in hs]
+    fp64_peak, fp32_peak = gca.peak_probe()
+    torch.cuda.synchronize()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    gca.profile_enable(True)
+    with ClockSampler(local) as clocks:
+        t_start = ev()
+        for _ in range(args.steps):
+            hs = step(True)
+        t_end = ev()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    gca.profile_enable(False)
+    phases = gca.profile_read()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    clk = clocks.summary()
+
+    agg = {}
+    for name, a, b in marks:
+        key = name.split(".")[0]
+        agg.setdefault(key, 0.0)
+        agg[key] += a.elapsed_time(b)
+    K = args.steps
+    nm = len(MESHES)
+    bytes_by = {p: sum(product_bytes(s, p if p != "f32T" else "f32", n, NRHS) for s in stats)
+                for p in ("f64", "f32", "bf16", "f32T")}
+    gbs = {p: bytes_by[p] * K / (agg[p] * 1e-3) / 1e9 for p in bytes_by}
+    hbm_peak, peak_kind = measured_peaks()
+
+    # accuracy of the reduced-precision products against the float64 product
+    errs = {}
+    for p in ("f32", "bf16"):
+        e = 0.0
+        for i in range(nm):
+            ref = ys["f64"][i]
+            e = max(e, float(((ys[p][i].double() - ref).norm(dim=0) / ref.norm(dim=0)).max()))
+        errs[p] = e
+
+    # dominant kernel of the step, and of the product: algorithmic work of the
+    # phase over the timed region divided by the phase's device time
+    dom = max(phases, key=lambda k: phases[k][1])
+    evals = [build_evals(s, PARAMS["sauter_q"]) for s in stats]
+
+    def roofline_for(name):
+        launches, ms = phases[name]
+        if name.startswith("mv_"):
+            stage, prec = name.split(".")[0], name.split(".")[1]
+            sm = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+            sv = 8 if prec == "f64" else 4
+            per = {"mv_couple": lambda s: sm * s["s_entries"],
+                   "mv_leaf_out": lambda s: sm * s["v_entries"] + sv * s["n_entries"] + sv * n * NRHS,
+                   "mv_forward_up": lambda s: sm * s["e_entries"],
+                   "mv_backward": lambda s: sm * s["e_entries"],
+                   "mv_forward_leaf": lambda s: sm * s["v_entries"],
+                   "mv_gather": lambda s: 2 * sv * n * NRHS}[stage]
+            byt = K * sum(per(s) for s in stats)
+            ach = byt / (ms * 1e-3) / 1e9
+            return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                    "launches_per_step": launches / K, "peak_kind": peak_kind}
+        if name in evals[0]:
+            flops = K * FLOPS_PER_EVAL * sum(e[name] for e in evals)
+            ach = flops / (ms * 1e-3) / 1e12
+        else:
+            ach = None
+        pk = fp64_peak / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": pk,
+                "unit": "TFLOP/s (fp64)", "frac": (ach / pk) if ach else None, "traffic": None,
+                "launches_per_step": launches / K,
+                "peak_kind": "measured by gca_peak_probe (fp64 FMA chains)"}
+
+    mv_dom = max((k for k in phases if k.startswith("mv_") and ".f32" in k and not k.endswith(".T")),
+                 key=lambda k: phases[k][1])
+
+    # end to end through the public API with host buffers (f32 product)
+    e2e_ms = []
+    h2d = d2h = 0
+    pin_x = [x.cpu().pin_memory() for x in xs32]
+    pin_y = [torch.empty((NRHS, len(t)), dtype=torch.float32).pin_memory().t() for _, t in meshes]
+    dx = [torch.empty((NRHS, len(t)), dtype=torch.float32, device=dev).t() for _, t in meshes]
+    for it in range(args.warmup + K):
+        a = ev()
+        for i, h in enumerate(hs):
+            dx[i].copy_(pin_x[i], non_blocking=True)
+            h.matvec(dx[i], "f32", out=ys["f32"][i])
+            pin_y[i].copy_(ys["f32"][i], non_blocking=True)
+        b = ev()
+        b.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    h2d = sum(x.numel() * 4 for x in xs32)
+    d2h = h2d
+    e2e_val = bytes_by["f32"] / (statistics.median(e2e_ms) * 1e-3) / 1e9
+
+    launches_per_step = sum(l for (l, _) in phases.values()) / K
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        o = oracle_sample()
+        cpu = {"value": o["gbs"], "unit": "GB/s", "cores": o["cores"], "kind": "oracle",
+               "sample": (f"oracle float64 H2 product (16 RHS) on its own GCA-H2 of the "
+                          f"{o['n']}-triangle sphere built with the workload's parameters; "
+                          f"oracle build {o['build_s']:.1f} s, product {o['matvec_s']*1e3:.0f} ms")}
+    line = {
+        "metric": METRIC, "value": gbs["f32"] * world, "unit": "GB/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": total_ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config({"parallelism": f"replicas{world}"}),
+        "build_s": agg["build"] / K * 1e-3,
+        "matvec": {p: {"GB/s": gbs[p], "frac_hbm": gbs[p] / hbm_peak,
+                       "ms": agg[p] / K / nm} for p in gbs},
+        "err_vs_f64": errs,
+        "roofline": roofline_for(dom),
+        "roofline_matvec": roofline_for(mv_dom),
+        "peaks": {"hbm_gbs": hbm_peak, "hbm_kind": peak_kind, "fp64_tflops": fp64_peak / 1e12,
+                  "fp32_tflops": fp32_peak / 1e12},
+        "phases_ms_per_step": {k: v[1] / K for k, v in sorted(phases.items())},
+        "clocks": clk,
+        "e2e": {"value": e2e_val * world, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * K,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

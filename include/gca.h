@@ -209,6 +209,31 @@ int h2_matvec(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64
 int h2_matvec_transpose(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x,
                         int64_t ldx, void* y, int64_t ldy, void* stream);
 
+/* Tracing (process wide, for one thread).  While enabled, every phase of
+ * gca_build and of the products records a pair of CUDA events on its stream.
+ * gca_profile_read synchronises those events, writes the accumulated GPU
+ * time and launch count per phase name (at most cap entries; *count gets
+ * the number of phases) and clears the accumulators.  Phase names: build
+ * phases ("green_aca", "couple_entries", ...) and product phases
+ * "mv_<stage>.<f64|f32|bf16>[.T]". */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+} gca_phase;
+int gca_profile_enable(int on);
+int gca_profile_read(gca_phase* out, int32_t cap, int32_t* count);
+
+/* Arithmetic throughput probe (not part of the method): chains of fused
+ * multiply-adds on every SM; FLOP/s in float64 and float32, 2 per FMA.
+ * Used as the denominator of the ALU roofline of the build kernels. */
+int gca_peak_probe(double* fp64_flops, double* fp32_flops);
+
+/* Sticky error bits of the products run on this handle so far (0: none;
+ * 1: a bounded device-side wait of the persistent product kernel expired,
+ * the results of that product are unreliable).  Synchronises the device. */
+int gca_h2_status(const gca_h2* h, int32_t* status);
+
 int gca_h2_stats(const gca_h2* h, gca_stats* out);
 int gca_h2_export(const gca_h2* h, gca_host_dump* out);
 void gca_free(gca_h2* h);

@@ -56,6 +56,11 @@ class _Stats(ctypes.Structure):
                 ("build_seconds", ctypes.c_double)]
 
 
+class _Phase(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("ms", ctypes.c_double)]
+
+
 class _Dump(ctypes.Structure):
     _fields_ = [("rank", _i32p), ("pivots", _i32p), ("far", _i32p), ("near", _i32p),
                 ("V", _f64p), ("E", _f64p), ("S", _f64p), ("N", _f64p)]
@@ -78,9 +83,14 @@ def _load():
                                                ctypes.c_int64, vp, ctypes.c_int64, vp]),
         "gca_h2_stats": (ctypes.c_int, [vp, ctypes.POINTER(_Stats)]),
         "gca_h2_export": (ctypes.c_int, [vp, ctypes.POINTER(_Dump)]),
+        "gca_h2_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32)]),
         "gca_free": (None, [vp]),
         "gca_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "gca_last_error": (ctypes.c_char_p, []),
+        "gca_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+        "gca_profile_read": (ctypes.c_int, [ctypes.POINTER(_Phase), ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_int32)]),
+        "gca_peak_probe": (ctypes.c_int, [_f64p, _f64p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -187,6 +197,12 @@ class H2:
         out["n_singular"] = list(s.n_singular)
         return out
 
+    def status(self):
+        """Sticky error bits of the products so far (0: none); synchronises."""
+        v = ctypes.c_int32(0)
+        _check(lib.gca_h2_status(self._h, ctypes.byref(v)), "gca_h2_status")
+        return v.value
+
     def export(self):
         """Host copy of the representation (layout documented in gca.h)."""
         s = self.stats()
@@ -237,6 +253,27 @@ class H2:
                         ctypes.c_void_p(y2.data_ptr()), y2.stride(1) if R > 1 else n,
                         _stream_ptr(stream), transpose)
         return out[:, 0] if vec and out.dim() == 2 else out
+
+
+def profile_enable(on=True):
+    """Start / stop per-phase GPU event timing (gca_profile_enable)."""
+    _check(lib.gca_profile_enable(1 if on else 0), "gca_profile_enable")
+
+
+def profile_read():
+    """{phase: (launches, ms)} accumulated since the last read (gca_profile_read)."""
+    cap = 256
+    buf = (_Phase * cap)()
+    cnt = ctypes.c_int32(0)
+    _check(lib.gca_profile_read(buf, cap, ctypes.byref(cnt)), "gca_profile_read")
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].ms) for i in range(min(cnt.value, cap))}
+
+
+def peak_probe():
+    """(float64, float32) FMA throughput of the current device in FLOP/s."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check(lib.gca_peak_probe(ctypes.byref(a), ctypes.byref(b)), "gca_peak_probe")
+    return a.value, b.value
 
 
 def build(vertices, triangles, tree, params, stream=None):

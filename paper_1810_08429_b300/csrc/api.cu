@@ -108,6 +108,18 @@ int gca_h2_export(const gca_h2* h, gca_host_dump* o) {
   return GCA_OK;
 }
 
+int gca_h2_status(const gca_h2* h, int32_t* status) {
+  if (!h || !status) {
+    gca::set_error("gca_h2_status: NULL argument");
+    return GCA_ERR_INVALID_ARG;
+  }
+  int v = 0;
+  int st = gca::product_status(h, &v);
+  if (st != GCA_OK) return st;
+  *status = v;
+  return GCA_OK;
+}
+
 void gca_free(gca_h2* h) { delete h; }
 
 const char* gca_strerror(int status) {

@@ -33,6 +33,7 @@
 #include <numeric>
 
 #include "internal.hpp"
+#include "panel.cuh"
 #include "rules.hpp"
 
 namespace gca {
@@ -321,26 +322,121 @@ struct Segment {
 };
 
 __global__ void k_pack(const Segment* __restrict__ seg, const double* __restrict__ src,
-                       double* __restrict__ d64, float* __restrict__ d32,
-                       __nv_bfloat16* __restrict__ d16) {
+                       double* __restrict__ d64) {
   const Segment s = seg[blockIdx.x];
-  for (int64_t i = threadIdx.x; i < s.len; i += blockDim.x) {
-    const double v = src[s.src + i];
-    d64[s.dst + i] = v;
-    d32[s.dst + i] = (float)v;
-    d16[s.dst + i] = __double2bfloat16(v);
+  for (int64_t i = threadIdx.x; i < s.len; i += blockDim.x) d64[s.dst + i] = src[s.src + i];
+}
+
+}  // namespace
+
+// Row-major float64 blocks -> panel layout (panel.cuh) in float64, float32
+// and (optionally) bfloat16; one CTA per block.  With `trans` the panel
+// holds the transposed block (m x k panel of a k x m row-major source).
+struct PanelJob {
+  int64_t src;
+  int64_t dst;
+  int m;
+  int k;
+  int trans;
+  int pad;
+};
+
+__global__ void k_to_panel(const PanelJob* __restrict__ jobs, const double* __restrict__ src,
+                           double* __restrict__ d64, float* __restrict__ d32,
+                           __nv_bfloat16* __restrict__ d16) {
+  const PanelJob j = jobs[blockIdx.x];
+  const int kp = pad8(j.k);
+  const int64_t total = (int64_t)j.m * kp;
+  auto at = [&](int a, int kk) -> double {
+    if (kk >= j.k) return 0.0;
+    return j.trans ? src[j.src + (int64_t)kk * j.m + a] : src[j.src + (int64_t)a * j.k + kk];
+  };
+  for (int64_t d = threadIdx.x; d < total; d += blockDim.x) {
+    {
+      const int64_t pw = (int64_t)j.m * 2;
+      const int p = (int)(d / pw), rem = (int)(d % pw);
+      d64[j.dst + d] = at(rem / 2, p * 2 + rem % 2);
+    }
+    {
+      const int64_t pw = (int64_t)j.m * 4;
+      const int p = (int)(d / pw), rem = (int)(d % pw);
+      d32[j.dst + d] = (float)at(rem / 4, p * 4 + rem % 4);
+    }
+    if (d16) {
+      const int64_t pw = (int64_t)j.m * 8;
+      const int p = (int)(d / pw), rem = (int)(d % pw);
+      d16[j.dst + d] = __double2bfloat16(at(rem / 8, p * 8 + rem % 8));
+    }
   }
 }
 
-__global__ void k_convert(int64_t n, const double* __restrict__ src, float* __restrict__ d32,
-                          __nv_bfloat16* __restrict__ d16) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = src[i];
-    d32[i] = (float)v;
-    if (d16) d16[i] = __double2bfloat16(v);
+// Panels of V, V^T, E, E^T, S, S^T, N, N^T (index PanelKind) with their
+// element offsets per block (the same for all precisions).
+int make_panels(gca_h2* h, cudaStream_t st) {
+  const int nc = h->nc;
+  const int nfar = (int)h->far_t.size(), nnear = (int)h->near_t.size();
+  std::vector<PanelJob> jobs[kPanelKinds];
+  int64_t size[kPanelKinds] = {0};
+  for (int q = 0; q < kPanelKinds; ++q) h->panel_off[q].clear();
+  h->panel_off[kV].assign(nc, -1);
+  h->panel_off[kVt].assign(nc, -1);
+  h->panel_off[kE].assign(nc, -1);
+  h->panel_off[kEt].assign(nc, -1);
+  h->panel_off[kS].assign(nfar, -1);
+  h->panel_off[kSt].assign(nfar, -1);
+  h->panel_off[kN].assign(nnear, -1);
+  h->panel_off[kNt].assign(nnear, -1);
+  auto add = [&](int kind, int idx, int64_t src, int m, int k, int trans) {
+    h->panel_off[kind][idx] = size[kind];
+    jobs[kind].push_back({src, size[kind], m, k, trans, 0});
+    size[kind] += (int64_t)m * pad8(k);
+  };
+  for (int c = 1; c < nc; ++c) {
+    if (h->child0[c] < 0) {
+      const int nr = h->end[c] - h->begin[c], r = h->rank[c];
+      add(kV, c, h->voff[c], nr, r, 0);
+      add(kVt, c, h->voff[c], r, nr, 1);
+    }
+    if (h->parent[c] > 0) {
+      const int r = h->rank[c], rp = h->rank[h->parent[c]];
+      add(kE, c, h->eoff[c], r, rp, 0);
+      add(kEt, c, h->eoff[c], rp, r, 1);
+    }
   }
+  for (int b = 0; b < nfar; ++b) {
+    const int rt = h->rank[h->far_t[b]], rs = h->rank[h->far_s[b]];
+    add(kS, b, h->soff[b], rt, rs, 0);
+    add(kSt, b, h->soff[b], rs, rt, 1);
+  }
+  for (int b = 0; b < nnear; ++b) {
+    const int t = h->near_t[b], s = h->near_s[b];
+    const int mt = h->end[t] - h->begin[t], ms = h->end[s] - h->begin[s];
+    add(kN, b, h->noff[b], mt, ms, 0);
+    add(kNt, b, h->noff[b], ms, mt, 1);
+  }
+  const DevMem* srcs[kPanelKinds] = {&h->V64, &h->V64, &h->E64, &h->E64,
+                                     &h->S64, &h->S64, &h->N64, &h->N64};
+  DevMem d_jobs;
+  for (int q = 0; q < kPanelKinds; ++q) {
+    const bool near = q == kN || q == kNt;
+    GCA_TRY(h->P64[q].alloc(sizeof(double) * size[q]));
+    GCA_TRY(h->P32[q].alloc(sizeof(float) * size[q]));
+    if (!near) GCA_TRY(h->P16[q].alloc(sizeof(__nv_bfloat16) * size[q]));
+    h->psize[q] = size[q];
+    if (jobs[q].empty()) continue;
+    GCA_TRY(d_jobs.reserve(sizeof(PanelJob) * jobs[q].size()));
+    GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, jobs[q].data(), sizeof(PanelJob) * jobs[q].size(),
+                                 cudaMemcpyHostToDevice, st));
+    k_to_panel<<<(unsigned)jobs[q].size(), 256, 0, st>>>(
+        d_jobs.as<PanelJob>(), srcs[q]->as<double>(), h->P64[q].as<double>(), h->P32[q].as<float>(),
+        near ? nullptr : h->P16[q].as<__nv_bfloat16>());
+    GCA_TRY_CUDA(cudaGetLastError());
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_jobs is reused
+  }
+  return GCA_OK;
 }
+
+namespace {
 
 // ------------------------------------------------------ regular entries
 
@@ -634,11 +730,17 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY(d_box.alloc(sizeof(double) * 6 * (size_t)nc));
   GCA_TRY(d_status.alloc(sizeof(int)));
   GCA_TRY_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), st));
-  k_tri_geom<<<blocks_for(n, 128), 128, 0, st>>>(n, h->d_vert.as<double>(), h->d_tri.as<int>(), rules,
-                                                d_tq.as<P4>());
-  k_cluster_boxes<<<blocks_for(32LL * nc, 128), 128, 0, st>>>(
-      nc, h->d_begin.as<int>(), h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(),
-      h->d_vert.as<double>(), d_box.as<double>());
+  {
+    PhaseScope ps__("tri_geom", st);
+    k_tri_geom<<<blocks_for(n, 128), 128, 0, st>>>(n, h->d_vert.as<double>(), h->d_tri.as<int>(), rules,
+                                                  d_tq.as<P4>());
+  }
+  {
+    PhaseScope ps__("cluster_boxes", st);
+    k_cluster_boxes<<<blocks_for(32LL * nc, 128), 128, 0, st>>>(
+        nc, h->d_begin.as<int>(), h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(),
+        h->d_vert.as<double>(), d_box.as<double>());
+  }
   GCA_TRY_CUDA(cudaGetLastError());
   std::vector<double> box(6 * (size_t)nc), diam;
   GCA_TRY_CUDA(cudaMemcpyAsync(box.data(), d_box.p, box.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -649,9 +751,12 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
 
   // box quadrature
   GCA_TRY(d_zq.alloc(sizeof(P4) * (size_t)nc * k));
-  k_box_quad<<<blocks_for((int64_t)nc * k, 128), 128, 0, st>>>(nc, rules, d_box.as<double>(),
-                                                               d_diam.as<double>(), margin,
-                                                               d_zq.as<P4>());
+  {
+    PhaseScope ps__("box_quad", st);
+    k_box_quad<<<blocks_for((int64_t)nc * k, 128), 128, 0, st>>>(nc, rules, d_box.as<double>(),
+                                                                 d_diam.as<double>(), margin,
+                                                                 d_zq.as<P4>());
+  }
   GCA_TRY_CUDA(cudaGetLastError());
 
   // nested bases, level by level from the deepest
@@ -735,10 +840,13 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, jobs.data(), sizeof(AcaJob) * jobs.size(),
                                  cudaMemcpyHostToDevice, st));
     const size_t smem = head + (in_smem ? mat : 0);
-    k_green_aca<<<(unsigned)jobs.size(), kAcaThreads, smem, st>>>(
-        d_jobs.as<AcaJob>(), k, rows_cap, in_smem ? 1 : 0, h->d_perm.as<int>(), d_tq.as<P4>(),
-        d_zq.as<P4>(), d_piv.as<int>(), d_mscr.as<double>(), d_uscr.as<double>(),
-        d_vh.as<double>(), d_rank.as<int>(), prm->aca_tol, tie, d_status.as<int>());
+    {
+      PhaseScope ps__("green_aca", st);
+      k_green_aca<<<(unsigned)jobs.size(), kAcaThreads, smem, st>>>(
+          d_jobs.as<AcaJob>(), k, rows_cap, in_smem ? 1 : 0, h->d_perm.as<int>(), d_tq.as<P4>(),
+          d_zq.as<P4>(), d_piv.as<int>(), d_mscr.as<double>(), d_uscr.as<double>(),
+          d_vh.as<double>(), d_rank.as<int>(), prm->aca_tol, tie, d_status.as<int>());
+    }
     GCA_TRY_CUDA(cudaGetLastError());
     GCA_TRY(check_status(d_status, st, "cross approximation"));
     GCA_TRY_CUDA(cudaMemcpyAsync(h->rank.data(), d_rank.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
@@ -779,11 +887,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     }
   }
   GCA_TRY(h->V64.alloc(sizeof(double) * h->v_entries));
-  GCA_TRY(h->V32.alloc(sizeof(float) * h->v_entries));
-  GCA_TRY(h->V16.alloc(sizeof(__nv_bfloat16) * h->v_entries));
   GCA_TRY(h->E64.alloc(sizeof(double) * h->e_entries));
-  GCA_TRY(h->E32.alloc(sizeof(float) * h->e_entries));
-  GCA_TRY(h->E16.alloc(sizeof(__nv_bfloat16) * h->e_entries));
   DevMem d_seg;
   for (auto* sv : {&vseg, &eseg}) {
     if (sv->empty()) continue;
@@ -791,10 +895,11 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     GCA_TRY_CUDA(cudaMemcpyAsync(d_seg.p, sv->data(), sizeof(Segment) * sv->size(),
                                  cudaMemcpyHostToDevice, st));
     const bool isv = sv == &vseg;
-    k_pack<<<(unsigned)sv->size(), 256, 0, st>>>(
-        d_seg.as<Segment>(), d_vh.as<double>(), isv ? h->V64.as<double>() : h->E64.as<double>(),
-        isv ? h->V32.as<float>() : h->E32.as<float>(),
-        isv ? h->V16.as<__nv_bfloat16>() : h->E16.as<__nv_bfloat16>());
+    {
+      PhaseScope ps__("pack", st);
+      k_pack<<<(unsigned)sv->size(), 256, 0, st>>>(
+          d_seg.as<Segment>(), d_vh.as<double>(), isv ? h->V64.as<double>() : h->E64.as<double>());
+    }
     GCA_TRY_CUDA(cudaGetLastError());
     GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_seg is reused
   }
@@ -820,10 +925,13 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   if (nfar > 0) {
     const size_t smem = sizeof(P4) * 7 * (size_t)std::max(h->max_rank, 1);
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_couple_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_couple_entries<<<nfar, 256, smem, st>>>(h->d_far_t.as<int>(), h->d_far_s.as<int>(),
-                                             h->d_soff.as<int64_t>(), h->d_rank.as<int>(),
-                                             d_poff.as<int64_t>(), d_piv.as<int>(), d_tq.as<P4>(),
-                                             h->S64.as<double>());
+    {
+      PhaseScope ps__("couple_entries", st);
+      k_couple_entries<<<nfar, 256, smem, st>>>(h->d_far_t.as<int>(), h->d_far_s.as<int>(),
+                                               h->d_soff.as<int64_t>(), h->d_rank.as<int>(),
+                                               d_poff.as<int64_t>(), d_piv.as<int>(), d_tq.as<P4>(),
+                                               h->S64.as<double>());
+    }
     GCA_TRY_CUDA(cudaGetLastError());
   }
 
@@ -850,11 +958,14 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   if (nnear > 0) {
     const size_t smem = sizeof(P4) * 7 * (size_t)h->max_leaf;
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_near_entries<<<nnear, 256, smem, st>>>(
-        h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
-        h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), d_tq.as<P4>(),
-        h->N64.as<double>(), d_items.as<SingularItem>(), cap, d_counts.as<unsigned long long>(),
-        d_status.as<int>());
+    {
+      PhaseScope ps__("near_entries", st);
+      k_near_entries<<<nnear, 256, smem, st>>>(
+          h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
+          h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), d_tq.as<P4>(),
+          h->N64.as<double>(), d_items.as<SingularItem>(), cap, d_counts.as<unsigned long long>(),
+          d_status.as<int>());
+    }
     GCA_TRY_CUDA(cudaGetLastError());
     GCA_TRY(check_status(d_status, st, "near field"));
     unsigned long long counts[4];
@@ -864,6 +975,8 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     h->n_singular[0] = h->n_entries - (h->n_singular[1] + h->n_singular[2] + h->n_singular[3]);
     const SingularItem* items = d_items.as<SingularItem>();
     const unsigned long long* cnt = d_counts.as<unsigned long long>();
+    PhaseScope ps_sing("singular", st);
+    ps_sing.launches((counts[1] > 0) + (counts[2] > 0) + (counts[3] > 0));
     if (counts[1])
       k_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
           items, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), rules, h->N64.as<double>());
@@ -877,16 +990,12 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     GCA_TRY_CUDA(cudaGetLastError());
   }
 
-  // reduced-precision copies
-  GCA_TRY(h->S32.alloc(sizeof(float) * h->s_entries));
-  GCA_TRY(h->S16.alloc(sizeof(__nv_bfloat16) * h->s_entries));
-  GCA_TRY(h->N32.alloc(sizeof(float) * h->n_entries));
-  if (h->s_entries)
-    k_convert<<<1184, 256, 0, st>>>(h->s_entries, h->S64.as<double>(), h->S32.as<float>(),
-                                    h->S16.as<__nv_bfloat16>());
-  if (h->n_entries)
-    k_convert<<<1184, 256, 0, st>>>(h->n_entries, h->N64.as<double>(), h->N32.as<float>(), nullptr);
-  GCA_TRY_CUDA(cudaGetLastError());
+  // panel layout for the products, three precisions
+  {
+    PhaseScope ps_conv("to_panel", st);
+    ps_conv.launches(kPanelKinds);
+    GCA_TRY(make_panels(h.get(), st));
+  }
 
   GCA_TRY(finish_plan(h.get(), st));
   GCA_TRY_CUDA(cudaStreamSynchronize(st));

@@ -14,6 +14,10 @@
 
 namespace gca {
 
+// Stored blocks in panel layout: leaf bases, transfers, couplings, near field,
+// each also transposed.
+enum PanelKind { kV = 0, kVt, kE, kEt, kS, kSt, kN, kNt, kPanelKinds };
+
 // Last error text of the calling thread (returned by gca_last_error()).
 void set_error(const std::string& msg);
 
@@ -83,10 +87,32 @@ void block_tree(const std::vector<int>& child0, const std::vector<int>& child1,
                 std::vector<int>& far_t, std::vector<int>& far_s, std::vector<int>& near_t,
                 std::vector<int>& near_s);
 
+// Event pair around a phase when profiling is enabled (profile.cu).
+class PhaseScope {
+ public:
+  PhaseScope(const char* name, cudaStream_t s);
+  PhaseScope(const std::string& name, cudaStream_t s) : PhaseScope(name.c_str(), s) {}
+  ~PhaseScope();
+  // kernel launches inside the phase (default 1)
+  void launches(int k) { launches_ = k; }
+  PhaseScope(const PhaseScope&) = delete;
+  PhaseScope& operator=(const PhaseScope&) = delete;
+
+ private:
+  std::string name_;
+  cudaStream_t s_;
+  void* a_ = nullptr;
+  void* b_ = nullptr;
+  bool active_ = false;
+  int launches_ = 1;
+};
+
 // Entry points of the translation units.
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
           gca_h2** out);
 int finish_plan(gca_h2* h, cudaStream_t st);
+int make_panels(gca_h2* h, cudaStream_t st);
+int product_status(const gca_h2* h, int* out);
 int matvec(const gca_h2* h, gca_prec prec, bool trans, int32_t nrhs, const void* x, int64_t ldx,
            void* y, int64_t ldy, cudaStream_t st);
 
@@ -124,27 +150,26 @@ struct gca_h2 {
   std::vector<int64_t> eoff;           // per cluster with a non-root parent, -1 otherwise
   int64_t v_entries = 0, e_entries = 0, s_entries = 0, n_entries = 0;
   int64_t n_singular[4] = {0, 0, 0, 0};
-  gca::BlockIndex far_row, far_col, near_row, near_col;
 
   // device: geometry and tree
-  gca::DevMem d_vert, d_tri, d_perm, d_begin, d_end, d_rank, d_xoff;
-  // device: coefficients, three precisions
-  gca::DevMem V64, E64, S64, N64, V32, E32, S32, N32, V16, E16, S16;
-  // device: product plans
-  gca::DevMem d_leaves, d_voff, d_eoff, d_parent, d_child0, d_child1;
+  gca::DevMem d_vert, d_tri, d_perm, d_begin, d_end, d_rank;
+  // device: block lists (build kernels)
   gca::DevMem d_far_t, d_far_s, d_soff, d_near_t, d_near_s, d_noff;
-  gca::DevMem d_far_row_ptr, d_far_row_blk, d_far_col_ptr, d_far_col_blk;
-  gca::DevMem d_near_row_ptr, d_near_row_blk, d_near_col_ptr, d_near_col_blk;
-  std::vector<gca::DevMem*> level_lists_owner;
-  std::vector<gca::DevMem> d_up_level;    // per level: non-leaf clusters (forward/up)
-  std::vector<int> n_up_level;
-  std::vector<gca::DevMem> d_down_level;  // per level: clusters whose parent is at this level - 1
-  std::vector<int> n_down_level;
-  gca::DevMem d_far_rows;                 // clusters with >= 1 far block as row
-  gca::DevMem d_far_cols;                 // clusters with >= 1 far block as column
-  int n_far_rows = 0, n_far_cols = 0;
+  // device: coefficients, row-major float64 (as exported)
+  gca::DevMem V64, E64, S64, N64;
+  // device: coefficients in panel layout (panel.cuh) for the products, in
+  // both orientations, three precisions (near field: float64 / float32)
+  gca::DevMem P64[gca::kPanelKinds], P32[gca::kPanelKinds], P16[gca::kPanelKinds];
+  std::vector<int64_t> panel_off[gca::kPanelKinds];  // per block, elements (all precisions)
+  int64_t psize[gca::kPanelKinds] = {0};
+  // persistent product: work items in dependency order, per direction
+  gca::DevMem d_items[2];
+  int64_t n_items[2] = {0, 0};
   int max_leaf = 0;
 
-  // device: product work buffers (grown on demand)
-  mutable gca::DevMem w_xp, w_xh, w_yh;
+  // device: product workspace (grown on demand): x-hat, y-hat, dependency
+  // counters and the work-claim counter, zeroed by one memset per product
+  mutable gca::DevMem w_ws;
+  mutable gca::DevMem d_status;  // sticky error bits of the products
+  int max_rows = 0;              // largest block dimension (bounds the staged X)
 };

@@ -150,6 +150,7 @@ def test_matvec_f64(gpu_1280, h2_1280, nrhs):
     assert rel_cols(y, ref) <= TOL64
     yt = h.matvec(xt, "f64", transpose=True).cpu().numpy()
     assert rel_cols(yt, oh2.matvec_t(h2_1280, x)) <= TOL64
+    assert h.status() == 0
 
 
 @pytest.mark.parametrize("prec,tol", [("f32", TOL32), ("bf16", TOL16)])
@@ -163,6 +164,7 @@ def test_matvec_reduced(gpu_1280, h2_1280, prec, tol):
     yt = h.matvec(xt, prec, transpose=True).double().cpu().numpy()
     assert rel_cols(y, ref) <= tol
     assert rel_cols(yt, refT) <= tol
+    assert h.status() == 0
 
 
 def test_matvec_leading_dimension(gpu_1280, h2_1280):
