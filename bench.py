@@ -5,11 +5,11 @@ and the same sphere radially perturbed by 0.1 sin(3 theta) cos(2 phi);
 leaf size 64, eta = 2, 4 x 4 Gauss points per box face (k = 96), ACA
 tolerance 1e-8, Sauter-Schwab order 5; 16 right-hand sides N(0, 1), seed 0.
 
-One step = the whole hot path on both meshes: gca_build (boxes, box
+One step = the whole hot path on both meshes: gca_build_batch (boxes, box
 quadrature, Green matrices + ACA per level, nested bases, coupling and
-near-field entries, reduced-precision copies) followed by the H^2 products
-y = G_H2 x in float64, float32 and bfloat16 and the transposed product in
-float32.  Inputs are resident in HBM when the timed region starts; the
+near-field entries, panel copies in three precisions) followed by the
+batched H^2 products y_i = G_i x_i (both meshes in one persistent launch)
+in float64, float32 and bfloat16 and the transposed product in float32.  Inputs are resident in HBM when the timed region starts; the
 stored matrices (>= 480 MB per mesh in float32) exceed the 126 MB L2, so
 no flush is needed between products.
 
@@ -49,7 +49,7 @@ def config(extra=None):
     c = {"workload": "sphere20480+perturbed20480 (2 meshes x 20480 triangles)",
          "leaf_size": 64, "eta": 2.0, "box_gauss_m": 4, "aca_tol": 1e-8, "sauter_q": 5,
          "nrhs": NRHS, "l2": "no flush: stored matrices exceed the 126 MB L2",
-         "step": "gca_build x2 + h2_matvec f64/f32/bf16 + h2_matvec_transpose f32, per mesh"}
+         "step": "gca_build_batch (2 meshes) + h2_matvec_batch f64/f32/bf16 + h2_matvec_transpose_batch f32"}
     if extra:
         c.update(extra)
     return c
@@ -241,22 +241,21 @@ def main():
         return e
 
     marks = []
+    batch = None
 
     def step(record):
-        hs = []
-        for (v, t), tr in zip(meshes, trees):
+        nonlocal batch
+        a = ev()
+        batch = gca.build_batch(meshes, trees, prm)
+        if record:
+            marks.append(("build", a, ev()))
+        for p, xs, tr_ in (("f64", xs64, False), ("f32", xs32, False), ("bf16", xs32, False),
+                           ("f32T", xs32, True)):
             a = ev()
-            hs.append(gca.build(v, t, tr, prm))
+            batch.matvec(xs, "f32" if p == "f32T" else p, transpose=tr_, outs=ys[p])
             if record:
-                marks.append(("build", a, ev()))
-        for i, h in enumerate(hs):
-            for p, x, tr_ in (("f64", xs64[i], False), ("f32", xs32[i], False),
-                              ("bf16", xs32[i], False), ("f32T", xs32[i], True)):
-                a = ev()
-                h.matvec(x, "f32" if p == "f32T" else p, transpose=tr_, out=ys[p][i])
-                if record:
-                    marks.append((p + f".{i}", a, ev()))
-        return hs
+                marks.append((p, a, ev()))
+        return batch.handles
 
     hs = None
     for _ in range(args.warmup):
@@ -319,12 +318,7 @@ def main():
             stage, prec = name.split(".")[0], name.split(".")[1]
             sm = {"f64": 8, "f32": 4, "bf16": 2}[prec]
             sv = 8 if prec == "f64" else 4
-            per = {"mv_couple": lambda s: sm * s["s_entries"],
-                   "mv_leaf_out": lambda s: sm * s["v_entries"] + sv * s["n_entries"] + sv * n * NRHS,
-                   "mv_forward_up": lambda s: sm * s["e_entries"],
-                   "mv_backward": lambda s: sm * s["e_entries"],
-                   "mv_forward_leaf": lambda s: sm * s["v_entries"],
-                   "mv_gather": lambda s: 2 * sv * n * NRHS}[stage]
+            per = {"mv_persistent": lambda s: product_bytes(s, prec, n, NRHS)}[stage]
             byt = K * sum(per(s) for s in stats)
             ach = byt / (ms * 1e-3) / 1e9
             return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
@@ -352,9 +346,10 @@ def main():
     dx = [torch.empty((NRHS, len(t)), dtype=torch.float32, device=dev).t() for _, t in meshes]
     for it in range(args.warmup + K):
         a = ev()
-        for i, h in enumerate(hs):
+        for i in range(nm):
             dx[i].copy_(pin_x[i], non_blocking=True)
-            h.matvec(dx[i], "f32", out=ys["f32"][i])
+        batch.matvec(dx, "f32", outs=ys["f32"])
+        for i in range(nm):
             pin_y[i].copy_(ys["f32"][i], non_blocking=True)
         b = ev()
         b.synchronize()
@@ -382,7 +377,7 @@ def main():
         "data": "synthetic", "config": config({"parallelism": f"replicas{world}"}),
         "build_s": agg["build"] / K * 1e-3,
         "matvec": {p: {"GB/s": gbs[p], "frac_hbm": gbs[p] / hbm_peak,
-                       "ms": agg[p] / K / nm} for p in gbs},
+                       "ms_both_meshes": agg[p] / K} for p in gbs},
         "err_vs_f64": errs,
         "roofline": roofline_for(dom),
         "roofline_matvec": roofline_for(mv_dom),

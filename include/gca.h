@@ -122,7 +122,8 @@ enum {
  * bfloat16 with float32 accumulation, near field float32; x, y float32. */
 typedef enum { GCA_F64 = 0, GCA_F32 = 1, GCA_BF16 = 2 } gca_prec;
 
-typedef struct gca_h2 gca_h2; /* opaque handle */
+typedef struct gca_h2 gca_h2;             /* opaque handle */
+typedef struct gca_h2_batch gca_h2_batch; /* opaque batch of handles */
 
 /* Sizes and counters of a built handle. */
 typedef struct {
@@ -228,6 +229,28 @@ int gca_profile_read(gca_phase* out, int32_t cap, int32_t* count);
  * multiply-adds on every SM; FLOP/s in float64 and float32, 2 per FMA.
  * Used as the denominator of the ALU roofline of the build kernels. */
 int gca_peak_probe(double* fp64_flops, double* fp32_flops);
+
+/* Batches: independent GCA-H^2 matrices (one per mesh) built with the same
+ * parameters and applied together in one persistent launch, which lets the
+ * dependency chains of the meshes' tree recursions overlap each other's
+ * streaming work.  gca_build_batch builds every mesh like gca_build (count
+ * >= 1, meshes[i] with trees[i]); the batch owns the handles (read them with
+ * gca_batch_handle, never free them individually).  The batched products take
+ * per-mesh nrhs, x, ldx, y, ldy arrays (host arrays of length count; x, y
+ * device pointers with the conventions of h2_matvec).  Calls on one batch must
+ * be ordered on one stream.  Errors: as gca_build / h2_matvec. */
+int gca_build_batch(int32_t count, const gca_mesh* meshes, const gca_tree* trees,
+                    const gca_params* params, void* stream, gca_h2_batch** out);
+int gca_batch_size(const gca_h2_batch* b, int32_t* count);
+int gca_batch_handle(const gca_h2_batch* b, int32_t i, const gca_h2** h);
+int h2_matvec_batch(const gca_h2_batch* b, gca_prec prec, const int32_t* nrhs, const void* const* x,
+                    const int64_t* ldx, void* const* y, const int64_t* ldy, void* stream);
+int h2_matvec_transpose_batch(const gca_h2_batch* b, gca_prec prec, const int32_t* nrhs,
+                              const void* const* x, const int64_t* ldx, void* const* y,
+                              const int64_t* ldy, void* stream);
+/* Sticky error bits of the batched products (see gca_h2_status). */
+int gca_batch_status(const gca_h2_batch* b, int32_t* status);
+void gca_free_batch(gca_h2_batch* b);
 
 /* Sticky error bits of the products run on this handle so far (0: none;
  * 1: a bounded device-side wait of the persistent product kernel expired,

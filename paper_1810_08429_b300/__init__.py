@@ -87,6 +87,19 @@ def _load():
         "gca_free": (None, [vp]),
         "gca_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "gca_last_error": (ctypes.c_char_p, []),
+        "gca_build_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
+                                           ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+        "gca_batch_size": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32)]),
+        "gca_batch_handle": (ctypes.c_int, [vp, ctypes.c_int32, ctypes.POINTER(vp)]),
+        "h2_matvec_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64), vp]),
+        "h2_matvec_transpose_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                                     ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64),
+                                                     ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64),
+                                                     vp]),
+        "gca_batch_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32)]),
+        "gca_free_batch": (None, [vp]),
         "gca_profile_enable": (ctypes.c_int, [ctypes.c_int]),
         "gca_profile_read": (ctypes.c_int, [ctypes.POINTER(_Phase), ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int32)]),
@@ -172,19 +185,23 @@ def _stream_ptr(stream):
 
 
 class H2:
-    """A built GCA-H^2 matrix on the current CUDA device (owns a gca_h2 handle)."""
+    """A built GCA-H^2 matrix on the current CUDA device (a gca_h2 handle).
 
-    def __init__(self, handle):
+    Handles returned by ``build`` own their device memory; handles of a
+    ``Batch`` are views that the batch owns."""
+
+    def __init__(self, handle, owner=None):
         self._h = ctypes.c_void_p(handle)
+        self._owner = owner
 
     def __del__(self):
         self.free()
 
     def free(self):
         h = getattr(self, "_h", None)
-        if h is not None and h.value:
+        if h is not None and h.value and getattr(self, "_owner", None) is None:
             lib.gca_free(h)
-            self._h = ctypes.c_void_p(None)
+        self._h = ctypes.c_void_p(None)
 
     @property
     def handle(self):
@@ -231,6 +248,10 @@ class H2:
         fn = lib.h2_matvec_transpose if transpose else lib.h2_matvec
         _check(fn(self._h, _PREC.get(prec, prec), nrhs, x_ptr, ldx, y_ptr, ldy, stream_ptr),
                "h2_matvec_transpose" if transpose else "h2_matvec")
+
+    @property
+    def n(self):
+        return self.stats()["n"]
 
     def matvec(self, x, prec="f64", transpose=False, out=None, stream=None):
         """y = G_H2 x (or G_H2^T x) for a CUDA tensor x of shape (n,) or (n, R)."""
@@ -285,3 +306,89 @@ def build(vertices, triangles, tree, params, stream=None):
     _check(lib.gca_build(ctypes.byref(m), ctypes.byref(t), ctypes.byref(p), _stream_ptr(stream),
                          ctypes.byref(h)), "gca_build")
     return H2(h.value)
+
+
+def _as_colmajor(x, dt):
+    vec = x.dim() == 1
+    x2 = x[:, None] if vec else x
+    if x2.dtype != dt or not x2.is_cuda:
+        raise TypeError(f"x must be a CUDA {dt} tensor")
+    if x2.stride(0) != 1:
+        x2 = x2.t().contiguous().t()
+    return x2, vec
+
+
+class Batch:
+    """Several GCA-H^2 matrices applied in one persistent launch (gca_h2_batch)."""
+
+    def __init__(self, ptr):
+        self._b = ctypes.c_void_p(ptr)
+        cnt = ctypes.c_int32(0)
+        _check(lib.gca_batch_size(self._b, ctypes.byref(cnt)), "gca_batch_size")
+        self.handles = []
+        for i in range(cnt.value):
+            h = ctypes.c_void_p(None)
+            _check(lib.gca_batch_handle(self._b, i, ctypes.byref(h)), "gca_batch_handle")
+            self.handles.append(H2(h.value, owner=self))
+
+    def __len__(self):
+        return len(self.handles)
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        b = getattr(self, "_b", None)
+        if b is not None and b.value:
+            for h in self.handles:
+                h._h = ctypes.c_void_p(None)
+            lib.gca_free_batch(b)
+            self._b = ctypes.c_void_p(None)
+
+    def status(self):
+        v = ctypes.c_int32(0)
+        _check(lib.gca_batch_status(self._b, ctypes.byref(v)), "gca_batch_status")
+        return v.value
+
+    def matvec(self, xs, prec="f32", transpose=False, outs=None, stream=None):
+        """[G_i x_i] (or transposes) for CUDA tensors x_i of shape (n_i,) or (n_i, R_i)."""
+        import torch
+        p = _PREC[prec]
+        dt = torch.float64 if p == F64 else torch.float32
+        k = len(self.handles)
+        if len(xs) != k:
+            raise ValueError("one right-hand side block per mesh")
+        xs2, vecs = zip(*[_as_colmajor(x, dt) for x in xs])
+        if outs is None:
+            outs = [torch.empty((x2.shape[1], x2.shape[0]), dtype=dt, device=x2.device).t() for x2 in xs2]
+        ys2 = [o[:, None] if o.dim() == 1 else o for o in outs]
+        nrhs = (ctypes.c_int32 * k)(*[x2.shape[1] for x2 in xs2])
+        xp = (ctypes.c_void_p * k)(*[x2.data_ptr() for x2 in xs2])
+        yp = (ctypes.c_void_p * k)(*[y2.data_ptr() for y2 in ys2])
+        ldx = (ctypes.c_int64 * k)(*[x2.stride(1) if x2.shape[1] > 1 else x2.shape[0] for x2 in xs2])
+        ldy = (ctypes.c_int64 * k)(*[y2.stride(1) if y2.shape[1] > 1 else y2.shape[0] for y2 in ys2])
+        fn = lib.h2_matvec_transpose_batch if transpose else lib.h2_matvec_batch
+        _check(fn(self._b, p, nrhs, xp, ldx, yp, ldy, _stream_ptr(stream)), "h2_matvec_batch")
+        return [o[:, 0] if v and o.dim() == 2 else o for o, v in zip(outs, vecs)]
+
+
+def build_batch(meshes, trees, params, stream=None):
+    """gca_build_batch over [(vertices, triangles)] with matching trees; returns a ``Batch``."""
+    k = len(meshes)
+    ms, keep = [], []
+    for v, t in meshes:
+        m, kp = _mesh(v, t)
+        ms.append(m)
+        keep.append(kp)
+    trs = []
+    for tr in trees:
+        t, kp = _tree(tr)
+        trs.append(t)
+        keep.append(kp)
+    marr = (_Mesh * k)(*ms)
+    tarr = (_Tree * k)(*trs)
+    p = params._c()
+    b = ctypes.c_void_p(None)
+    _check(lib.gca_build_batch(k, marr, tarr, ctypes.byref(p), _stream_ptr(stream), ctypes.byref(b)),
+           "gca_build_batch")
+    return Batch(b.value)

@@ -6,6 +6,7 @@
 
 #include <cstring>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "internal.hpp"
@@ -121,6 +122,84 @@ int gca_h2_status(const gca_h2* h, int32_t* status) {
 }
 
 void gca_free(gca_h2* h) { delete h; }
+
+int gca_build_batch(int32_t count, const gca_mesh* meshes, const gca_tree* trees,
+                    const gca_params* params, void* stream, gca_h2_batch** out) {
+  if (!out || count < 1 || !meshes || !trees) {
+    gca::set_error("gca_build_batch: invalid arguments");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    auto b = std::make_unique<gca_h2_batch>();
+    for (int32_t i = 0; i < count; ++i) {
+      gca_h2* h = nullptr;
+      int st = gca::build(meshes + i, trees + i, params, static_cast<cudaStream_t>(stream), &h);
+      if (st != GCA_OK) {
+        gca::set_error("gca_build_batch: mesh " + std::to_string(i) + ": " + gca_last_error());
+        return st;
+      }
+      b->h.push_back(h);
+    }
+    int st = b->d_status.alloc(sizeof(int));
+    if (st != GCA_OK) return st;
+    if (cudaMemset(b->d_status.p, 0, sizeof(int)) != cudaSuccess) {
+      gca::set_error("gca_build_batch: cudaMemset failed");
+      return GCA_ERR_CUDA;
+    }
+    *out = b.release();
+    return GCA_OK;
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_build_batch: host allocation failed");
+    return GCA_ERR_OOM;
+  }
+}
+
+int gca_batch_size(const gca_h2_batch* b, int32_t* count) {
+  if (!b || !count) {
+    gca::set_error("gca_batch_size: NULL argument");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *count = (int32_t)b->h.size();
+  return GCA_OK;
+}
+
+int gca_batch_handle(const gca_h2_batch* b, int32_t i, const gca_h2** h) {
+  if (!b || !h || i < 0 || i >= (int32_t)b->h.size()) {
+    gca::set_error("gca_batch_handle: invalid arguments");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *h = b->h[i];
+  return GCA_OK;
+}
+
+int h2_matvec_batch(const gca_h2_batch* b, gca_prec prec, const int32_t* nrhs, const void* const* x,
+                    const int64_t* ldx, void* const* y, const int64_t* ldy, void* stream) {
+  return gca::matvec_batch(b, prec, false, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream));
+}
+
+int h2_matvec_transpose_batch(const gca_h2_batch* b, gca_prec prec, const int32_t* nrhs,
+                              const void* const* x, const int64_t* ldx, void* const* y,
+                              const int64_t* ldy, void* stream) {
+  return gca::matvec_batch(b, prec, true, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream));
+}
+
+int gca_batch_status(const gca_h2_batch* b, int32_t* status) {
+  if (!b || !status) {
+    gca::set_error("gca_batch_status: NULL argument");
+    return GCA_ERR_INVALID_ARG;
+  }
+  int v = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(&v, b->d_status.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    gca::set_error("gca_batch_status: CUDA error");
+    return GCA_ERR_CUDA;
+  }
+  *status = v;
+  return GCA_OK;
+}
+
+void gca_free_batch(gca_h2_batch* b) { delete b; }
 
 const char* gca_strerror(int status) {
   switch (status) {

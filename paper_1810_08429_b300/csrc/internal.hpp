@@ -113,6 +113,9 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
 int finish_plan(gca_h2* h, cudaStream_t st);
 int make_panels(gca_h2* h, cudaStream_t st);
 int product_status(const gca_h2* h, int* out);
+int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* nrhs,
+                 const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy,
+                 cudaStream_t st);
 int matvec(const gca_h2* h, gca_prec prec, bool trans, int32_t nrhs, const void* x, int64_t ldx,
            void* y, int64_t ldy, cudaStream_t st);
 
@@ -163,13 +166,25 @@ struct gca_h2 {
   std::vector<int64_t> panel_off[gca::kPanelKinds];  // per block, elements (all precisions)
   int64_t psize[gca::kPanelKinds] = {0};
   // persistent product: work items in dependency order, per direction
-  gca::DevMem d_items[2];
+  gca::DevMem d_items[2], d_groups[2];
   int64_t n_items[2] = {0, 0};
   int max_leaf = 0;
 
   // device: product workspace (grown on demand): x-hat, y-hat, dependency
   // counters and the work-claim counter, zeroed by one memset per product
   mutable gca::DevMem w_ws;
+  mutable std::vector<unsigned char> w_cache;  // slot descriptors the workspace holds
   mutable gca::DevMem d_status;  // sticky error bits of the products
   int max_rows = 0;              // largest block dimension (bounds the staged X)
+};
+
+// A batch of handles applied in one persistent launch.
+struct gca_h2_batch {
+  std::vector<gca_h2*> h;          // owned
+  mutable gca::DevMem ws;          // shared product workspace
+  mutable std::vector<unsigned char> w_cache;
+  mutable gca::DevMem d_status;
+  ~gca_h2_batch() {
+    for (auto* p : h) delete p;
+  }
 };

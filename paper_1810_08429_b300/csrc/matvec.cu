@@ -33,6 +33,8 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <queue>
+#include <cstring>
 #include <string>
 
 #include "internal.hpp"
@@ -42,7 +44,7 @@ namespace gca {
 
 namespace {
 
-constexpr int kBatch = 2;            // items claimed per atomic
+constexpr int kBatch = 1;            // groups claimed per atomic
 constexpr int kSpinLimit = 1 << 20;  // bounded wait: well under a second with the back-off below
 constexpr int kStatusTimeout = 1;
 
@@ -52,28 +54,36 @@ struct MvItem {
   int64_t x_row;  // first row of the input vector block
   int64_t o_row;  // output row of lane 0
   int m;          // rows of the stored block (panel stride)
-  int k;          // columns of the stored block = rows of the input block
+  int k;          // columns of this item's column chunk (<= kChunk)
   int a0;         // first block row handled by this item
+  int k0;         // first block column of the chunk
   int kind;       // panel kind | (input << 4) | (output << 8)
   int wait_idx;   // counter that must reach wait_cnt * nchunk first (-1: none)
   int wait_cnt;
   int sig_idx;    // counter bumped after the outputs are added (-1: none)
-  int pad;
+  int flush;      // last segment of its group: add the accumulated rows to the output
 };
 
 enum { kInXh = 0, kInYh = 1, kInX = 2 };
 enum { kOutXh = 0, kOutYh = 1, kOutY = 2 };
 
-template <typename T, typename TV>
-struct MvArgs {
-  const void* A[kPanelKinds];  // panel arrays (near-field kinds hold TN)
+// Everything one mesh (slot) of a launch needs; a launch runs the work of
+// any number of slots, each slot's work list in dependency order, slot after
+// slot in claim order.
+template <typename TV>
+struct SlotArgs {
+  const void* A[kPanelKinds];  // panel arrays (near-field kinds hold the near storage type)
   const MvItem* items;
-  int64_t n_items;
+  const int2* groups;          // [begin, end) segment ranges claimed as a unit
+  int64_t work_begin;          // first claim index of this slot
+  int64_t n_work;              // groups * nchunk
   int nchunk;
   int R;
+  int n;
+  int pad;
   const TV* x;                 // caller's x, original order, column-major
   int64_t ldx;
-  TV* y;                       // caller's y, original order, column-major (zeroed)
+  TV* y;                       // caller's y, original order, column-major
   int64_t ldy;
   const int* perm;
   const TV* xp;                // x in cluster order [n][R]
@@ -81,9 +91,26 @@ struct MvArgs {
   TV* xh;                      // [rank_sum][R]
   TV* yh;
   int* counters;               // [2 nc]
+};
+
+struct LaunchArgs {
+  const void* slots;           // SlotArgs<TV>[nslots]
+  int nslots;
+  int64_t total;               // claims over all slots
   unsigned long long* next;    // work-claim counter
   int* status;
+  int* abort_flag;             // raised by any timed-out wait; every wait gives up
 };
+
+template <typename TV>
+__device__ __forceinline__ int find_slot(const SlotArgs<TV>* sl, int nslots, int64_t w) {
+  int lo = 0, hi = nslots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sl[mid].work_begin <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -91,273 +118,653 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+// ---------------------------------------------------------------- pipeline
+//
+// CTA = kConsumers consumer warps + 1 producer warp.  The producer claims
+// items (claim-ahead), waits for their input vector, and issues 1-D bulk
+// copies (TMA) of the input block and of the item's block panels into
+// mbarrier-guarded rings; the consumers compute continuously.  Item = a
+// slice of kItemRows rows x kChunk columns of one stored block; consumer
+// warp w owns rows [64 w, 64 w + 64) of it (see Tile).
+constexpr int kConsumers = 2;
+constexpr int kThreads = 32 * (kConsumers + 1);
+constexpr int kItemRows = 64 * kConsumers;  // 128: 64 rows per consumer warp
+constexpr int kChunk = 64;                                 // columns per item
+constexpr int kStagePanels = 4;
+constexpr int kStageBytes = kStagePanels * kItemRows * 16;  // 8 KB
+constexpr int kStages = 4;
+constexpr int kXSlots = 4;
+constexpr int kMbarLimit = 1 << 20;
+
+struct Meta {
+  int64_t o_row;  // output row of item row 0
+  int rows;       // valid rows of the item
+  int np;         // panels of the chunk
+  int out;        // output array, -1: end of work
+  int sig_idx;
+  int c0;         // first right-hand side of this pass
+  int near;       // near-field panels (storage type TN)
+  int flush;      // last segment of the group
+  int slot;       // mesh of the launch
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
-// 16-byte copy that reads src_bytes (0 or 16) and zero-fills the rest
-__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, int src_bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes)
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b))
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait_group() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, unsigned tx) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_u32(b)),
+               "r"(tx)
+               : "memory");
 }
-
-// Ring of the per-warp block stream: kStages stages of kStagePanels panels,
-// each panel 32 rows x 16 bytes.
-constexpr int kStagePanels = 8;
-constexpr int kStages = 4;
-constexpr int kRingBytes = kStages * kStagePanels * 32 * 16;
-
-// acc[c] += sum_k A[a0 + lane, k] Xs[k, c] over the 32-row slice of a panel
-// block, streamed through the warp's shared-memory ring with cp.async.
-template <typename T, typename TA, int RC>
-__device__ __forceinline__ void stream_block(const T* __restrict__ A, int M, int a0, int kp,
-                                             const TA* __restrict__ Xs, unsigned char* ring,
-                                             int lane, TA (&acc)[RC]) {
-  constexpr int P = Panel<T>::P;
-  const int np = kp / P;
-  const int nst = (np + kStagePanels - 1) / kStagePanels;
-  const bool valid = a0 + lane < M;
-  const uint4* src = reinterpret_cast<const uint4*>(A) + a0 + lane;
-  auto issue = [&](int s) {
-    if (s < nst) {
-      unsigned char* slot = ring + (s % kStages) * (kStagePanels * 512) + lane * 16;
-#pragma unroll
-      for (int g = 0; g < kStagePanels; ++g) {
-        const int p = s * kStagePanels + g;
-        if (p < np)
-          cp_async16_zfill(slot + g * 512, valid ? src + (int64_t)p * M : reinterpret_cast<const uint4*>(A),
-                           valid ? 16 : 0);
-      }
-    }
-    cp_async_commit();
-  };
-#pragma unroll
-  for (int s = 0; s < kStages - 1; ++s) issue(s);
-  for (int s = 0; s < nst; ++s) {
-    issue(s + kStages - 1);
-    cp_async_wait_group<kStages - 1>();
-    __syncwarp();
-    const unsigned char* slot = ring + (s % kStages) * (kStagePanels * 512) + lane * 16;
-#pragma unroll
-    for (int g = 0; g < kStagePanels; ++g) {
-      const int p = s * kStagePanels + g;
-      if (p >= np) break;
-      TA v[P];
-      unpack(*reinterpret_cast<const uint4*>(slot + g * 512), v);
-#pragma unroll
-      for (int kk = 0; kk < P; ++kk) {
-        const TA* xr = Xs + (p * P + kk) * RC;
-#pragma unroll
-        for (int c = 0; c < RC; ++c) acc[c] = fma(v[kk], xr[c], acc[c]);
-      }
-    }
-    __syncwarp();
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of parity `parity`; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag,
+                                          int* status) {
+  for (int i = 0; i < kMbarLimit; ++i) {
+    if (mbar_try_wait(b, parity)) return true;
+    if ((i & 63) == 63 && *abort_flag) return false;
   }
+  atomicOr(status, kStatusTimeout);
+  *abort_flag = 1;
+  return false;
+}
+// Bounded wait used only while draining copies before exit (ignores the
+// abort flag, so that no copy is still landing when the CTA retires).
+__device__ __forceinline__ void mbar_drain(uint64_t* b, unsigned parity) {
+  for (int i = 0; i < kMbarLimit; ++i)
+    if (mbar_try_wait(b, parity)) return;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// add RC consecutive values of one output row (16-byte vector atomics when
-// the row segment is 16-byte aligned: R and c0 multiples of 4)
-template <int RC>
-__device__ __forceinline__ void add_row(float* p, const float (&v)[RC], int valid_cols, bool aligned) {
-  if (RC % 4 == 0 && valid_cols == RC && aligned) {
+// Fire-and-forget reductions into global memory (no return value, so the
+// issuing warp does not wait for the L2 round trip).
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
+// add N consecutive values of one output row (16-byte vector reductions
+// when the segment is 16-byte aligned)
+template <int N>
+__device__ __forceinline__ void add_row(float* p, const float* v, int valid_cols, bool aligned) {
+  if (N % 4 == 0 && valid_cols >= N && aligned) {
 #pragma unroll
-    for (int c = 0; c < RC; c += 4)
-      atomicAdd(reinterpret_cast<float4*>(p + c), make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]));
+    for (int c = 0; c < N; c += 4) red_add4(p + c, v[c], v[c + 1], v[c + 2], v[c + 3]);
   } else {
 #pragma unroll
-    for (int c = 0; c < RC; ++c)
-      if (c < valid_cols) atomicAdd(p + c, v[c]);
+    for (int c = 0; c < N; ++c)
+      if (c < valid_cols) red_add(p + c, v[c]);
   }
 }
-template <int RC>
-__device__ __forceinline__ void add_row(double* p, const double (&v)[RC], int valid_cols, bool) {
+template <int N>
+__device__ __forceinline__ void add_row(double* p, const double* v, int valid_cols, bool) {
 #pragma unroll
-  for (int c = 0; c < RC; ++c)
-    if (c < valid_cols) atomicAdd(p + c, v[c]);
+  for (int c = 0; c < N; ++c)
+    if (c < valid_cols) red_add(p + c, v[c]);
 }
 
+// x (original order) -> x in cluster order, all slots of a launch
+// (blockIdx.y = slot)
 template <typename TV>
-__global__ void k_gather(int n, int R, const int* __restrict__ perm, const TV* __restrict__ x,
-                         int64_t ldx, TV* __restrict__ xp) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * R) return;
-  const int i = (int)(idx / R), c = (int)(idx % R);
-  xp[idx] = x[perm[i] + c * ldx];
+__global__ void k_gather(const SlotArgs<TV>* __restrict__ slots) {
+  const SlotArgs<TV>& sa = slots[blockIdx.y];
+  const int64_t tot = (int64_t)sa.n * sa.R;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / sa.R), c = (int)(idx % sa.R);
+    const_cast<TV*>(sa.xp)[idx] = sa.x[sa.perm[i] + c * sa.ldx];
+  }
 }
 
+// y in cluster order -> caller's y (original order)
 template <typename TV>
-__global__ void k_scatter(int n, int R, const int* __restrict__ perm, const TV* __restrict__ yp,
-                          TV* __restrict__ y, int64_t ldy) {
-  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)n * R) return;
-  const int c = (int)(idx / n), i = (int)(idx % n);
-  y[perm[i] + c * ldy] = yp[(int64_t)i * R + c];
+__global__ void k_scatter(const SlotArgs<TV>* __restrict__ slots) {
+  const SlotArgs<TV>& sa = slots[blockIdx.y];
+  const int64_t tot = (int64_t)sa.n * sa.R;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / sa.n), i = (int)(idx % sa.n);
+    sa.y[sa.perm[i] + c * sa.ldy] = sa.yp[(int64_t)i * sa.R + c];
+  }
+}
+
+// Consumer register tile.  A warp covers 64 rows x RC right-hand sides:
+// CPL = min(RC, 8) columns per lane, NCG = RC / CPL column groups,
+// RG = 32 / NCG row groups, RPL = 64 / RG rows per lane; lane (rg, cg) owns
+// rows rg + RG * i (i < RPL) and columns cg * CPL + [0, CPL).  Rows of one
+// load instruction are consecutive (conflict-free 16-byte shared loads).
+template <int RC>
+struct Tile {
+  static constexpr int CPL = RC < 8 ? RC : 8;
+  static constexpr int NCG = RC / CPL;
+  static constexpr int RG = 32 / NCG;
+  static constexpr int RPL = 64 / RG;
+};
+
+// One ring stage: np_stage panels of P columns of the lane's rows.
+template <typename T, typename TA, int RC>
+__device__ __forceinline__ void consume_stage(const unsigned char* slot, int np_stage, int p0,
+                                              const TA* __restrict__ Xs, int rowbase, int cg,
+                                              TA (&acc)[Tile<RC>::RPL][Tile<RC>::CPL]) {
+  using Tl = Tile<RC>;
+  constexpr int P = Panel<T>::P;
+#pragma unroll
+  for (int g = 0; g < kStagePanels; ++g) {
+    if (g >= np_stage) break;
+    TA v[Tl::RPL][P];
+#pragma unroll
+    for (int i = 0; i < Tl::RPL; ++i)
+      unpack(*reinterpret_cast<const uint4*>(slot + g * (kItemRows * 16) + (rowbase + Tl::RG * i) * 16),
+             v[i]);
+#pragma unroll
+    for (int kk = 0; kk < P; ++kk) {
+      const TA* xr = Xs + ((p0 + g) * P + kk) * RC + cg * Tl::CPL;
+      TA x[Tl::CPL];
+#pragma unroll
+      for (int c = 0; c < Tl::CPL; ++c) x[c] = xr[c];
+#pragma unroll
+      for (int i = 0; i < Tl::RPL; ++i)
+#pragma unroll
+        for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = fma(v[i][kk], x[c], acc[i][c]);
+    }
+  }
 }
 
 template <typename T, typename TN, typename TA, typename TV, int RC>
-__global__ void __launch_bounds__(32) k_h2_persistent(MvArgs<T, TV> g) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(kThreads) k_h2_persistent(LaunchArgs L) {
+  const SlotArgs<TV>* slots = static_cast<const SlotArgs<TV>*>(L.slots);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned char* ring = smem_raw;
-  TA* Xs = reinterpret_cast<TA*>(smem_raw + kRingBytes);
-  const int lane = threadIdx.x;
-  const int64_t total = g.n_items * g.nchunk;
-  for (;;) {
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(g.next, (unsigned long long)kBatch);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if ((int64_t)base >= total) break;
-    const int64_t stop = min((int64_t)base + kBatch, total);
-    for (int64_t w = (int64_t)base; w < stop; ++w) {
-      const MvItem it = g.items[w / g.nchunk];
-      const int c0 = (int)(w % g.nchunk) * RC;
-      const int ain = it.kind & 15, xin = (it.kind >> 4) & 15, out = (it.kind >> 8) & 15;
+  TA* xs_base = reinterpret_cast<TA*>(smem_raw + kStages * kStageBytes);
+  constexpr int kXsElems = kChunk * RC;
+  Meta* meta = reinterpret_cast<Meta*>(xs_base + kXSlots * kXsElems);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(meta + kXSlots);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kStages;
+  uint64_t* xfull = bars + 2 * kStages;
+  uint64_t* xempty = bars + 2 * kStages + kXSlots;
+  volatile int* abort_flag = L.abort_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, kConsumers);
+    }
+    for (int i = 0; i < kXSlots; ++i) {
+      mbar_init(xfull + i, 1);
+      mbar_init(xempty + i, kConsumers);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
 
-      // wait until the input vector block is complete
-      if (it.wait_idx >= 0) {
-        const int need = it.wait_cnt * g.nchunk;
-        int spins = 0;
-        while (ld_acquire(g.counters + it.wait_idx) < need) {
-          if (++spins > kSpinLimit) {
-            if (lane == 0) atomicOr(g.status, kStatusTimeout);
+  if (warp == kConsumers) {
+    // ------------------------------------------------------------ producer
+    const int64_t total = L.total;
+    int seq = 0;
+    int64_t pstage = 0;
+    bool dead = false;
+    unsigned long long nxt = 0;
+    if (lane == 0) nxt = atomicAdd(L.next, (unsigned long long)kBatch);
+    nxt = __shfl_sync(0xffffffffu, nxt, 0);
+    int xuses[kXSlots] = {0, 0};
+    while (!dead && (int64_t)nxt < total) {
+      const unsigned long long base = nxt;
+      unsigned long long ahead = 0;
+      if (lane == 0) ahead = atomicAdd(L.next, (unsigned long long)kBatch);  // claim ahead
+      const int64_t stop = min((int64_t)base + kBatch, total);
+      for (int64_t wseg = 0, w = (int64_t)base; w < stop && !dead;) {
+        const int slot = find_slot(slots, L.nslots, w);
+        const SlotArgs<TV>& sa = slots[slot];
+        const int64_t lw = w - sa.work_begin;
+        const int2 grp = sa.groups[lw / sa.nchunk];
+        const int64_t segi = grp.x + wseg;
+        const MvItem it = sa.items[segi];
+        const int c0 = (int)(lw % sa.nchunk) * RC;
+        if (segi + 1 >= grp.y) {
+          wseg = 0;
+          ++w;
+        } else {
+          ++wseg;
+        }
+        const int ain = it.kind & 15, xin = (it.kind >> 4) & 15, out = (it.kind >> 8) & 15;
+        const bool is_near = ain == kN || ain == kNt;
+        const int P = is_near ? Panel<TN>::P : Panel<T>::P;
+        const int esz = is_near ? (int)sizeof(TN) : (int)sizeof(T);
+        const int kp = pad8(it.k);
+        const int np = kp / P;
+        const int rows = min(kItemRows, it.m - it.a0);
+        const int xs = seq % kXSlots;
+        TA* Xs = xs_base + xs * kXsElems;
+        if (seq >= kXSlots && !mbar_wait(xempty + xs, ((seq / kXSlots) - 1) & 1, abort_flag, L.status)) {
+          dead = true;
+          break;
+        }
+        if (*abort_flag) {
+          dead = true;
+          break;
+        }
+        // the item's block panels do not depend on anything: issue up to a
+        // ring's worth now, the rest after the input block is staged (the
+        // consumers can only drain this item's stages once its input is in)
+        const unsigned char* Ab = static_cast<const unsigned char*>(sa.A[ain]) + it.a_off * esz;
+        const int pbase = it.k0 / P;
+        auto issue_stage = [&](int s0) -> bool {
+          const int slot = (int)(pstage % kStages);
+          if (pstage >= kStages &&
+              !mbar_wait(empty + slot, (unsigned)(((pstage / kStages) - 1) & 1), abort_flag, L.status))
+            return false;
+          if (lane == 0) {
+            const int npst = min(kStagePanels, np - s0);
+            mbar_arrive_tx(full + slot, (unsigned)(npst * rows * 16));
+            for (int q = 0; q < npst; ++q) {
+              const int64_t pan = pbase + s0 + q;
+              bulk_g2s(ring + slot * kStageBytes + q * (kItemRows * 16), Ab + (pan * it.m + it.a0) * 16,
+                       (unsigned)(rows * 16), full + slot);
+            }
+          }
+          __syncwarp();
+          ++pstage;
+          return true;
+        };
+        int s0 = 0;
+        for (int n = 0; s0 < np && n < kStages; s0 += kStagePanels, ++n)
+          if (!issue_stage(s0)) {
+            dead = true;
             break;
           }
-          __nanosleep(128);
-        }
-      }
-
-      // stage the input rows (zero beyond k up to pad8(k)) for RHS c0 .. c0+RC
-      const int kp = pad8(it.k);
-      {
-        const TV* X = (xin == kInXh ? g.xh : (xin == kInYh ? g.yh : g.xp)) + it.x_row * g.R + c0;
-        constexpr int V = 16 / (int)sizeof(TA);  // values per 16-byte copy
-        if (RC % V == 0 && g.R % V == 0 && c0 + RC <= g.R) {
-          for (int i = lane; i < it.k * (RC / V); i += 32) {
-            const int r = i / (RC / V), c = (i % (RC / V)) * V;
-            cp_async16(Xs + r * RC + c, X + (int64_t)r * g.R + c);
+        if (dead) break;
+        // input vector block complete?
+        if (it.wait_idx >= 0) {
+          const int need = it.wait_cnt * sa.nchunk * kConsumers;  // each consumer warp signals
+          int spins = 0;
+          while (ld_acquire(sa.counters + it.wait_idx) < need) {
+            if (++spins > kSpinLimit) {
+              if (lane == 0) atomicOr(L.status, kStatusTimeout);
+              *abort_flag = 1;
+              break;
+            }
+            if (*abort_flag) break;
+            __nanosleep(32);
           }
-          cp_async_commit();
+        }
+        if (lane == 0) {
+          Meta mt;
+          mt.o_row = it.o_row;
+          mt.rows = rows;
+          mt.np = np;
+          mt.out = out;
+          mt.sig_idx = it.sig_idx;
+          mt.c0 = c0;
+          mt.near = is_near ? 1 : 0;
+          mt.flush = it.flush;
+          mt.slot = slot;
+          meta[xs] = mt;
+        }
+        // stage the input rows k0 .. k0+kp (zero beyond the block's columns)
+        const TV* X = (xin == kInXh ? sa.xh : (xin == kInYh ? sa.yh : sa.xp)) + it.x_row * sa.R + c0;
+        const bool bulk = RC == sa.R && (RC * sizeof(TV)) % 16 == 0 && sizeof(TA) == sizeof(TV);
+        if (bulk) {
           for (int i = it.k * RC + lane; i < kp * RC; i += 32) Xs[i] = (TA)0;
+          __syncwarp();
+          if (lane == 0) {
+            const unsigned bytes = (unsigned)(it.k * RC * sizeof(TV));
+            fence_proxy_async();
+            if (bytes > 0) {
+              mbar_arrive_tx(xfull + xs, bytes);
+              bulk_g2s(Xs, X, bytes, xfull + xs);
+            } else {
+              mbar_arrive(xfull + xs);
+            }
+          }
         } else {
           for (int i = lane; i < kp * RC; i += 32) {
             const int r = i / RC, c = i % RC;
-            Xs[i] = (r < it.k && c0 + c < g.R) ? (TA)__ldcg(X + (int64_t)r * g.R + c) : (TA)0;
+            Xs[i] = (r < it.k && c0 + c < sa.R) ? (TA)__ldcg(X + (int64_t)r * sa.R + c) : (TA)0;
           }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(xfull + xs);
         }
+        for (; s0 < np; s0 += kStagePanels)
+          if (!issue_stage(s0)) {
+            dead = true;
+            break;
+          }
+        ++xuses[xs];
+        ++seq;
       }
-      __syncwarp();
-
-      // 32 rows of the block times the staged vector block (the vector's
-      // cp.async group completes with the block's first stage)
-      const bool valid = it.a0 + lane < it.m;
-      TA acc[RC];
+      nxt = __shfl_sync(0xffffffffu, ahead, 0);
+      dead = __any_sync(0xffffffffu, dead);
+    }
+    // end of work for the consumers
+    {
+      const int xs = seq % kXSlots;
+      bool ok = true;
+      if (seq >= kXSlots) ok = mbar_wait(xempty + xs, ((seq / kXSlots) - 1) & 1, abort_flag, L.status);
+      if (lane == 0) {
+        Meta mt{};
+        mt.out = -1;
+        meta[xs] = mt;
+        mbar_arrive(xfull + xs);  // release: consumers see the end marker
+      }
+      ++xuses[xs];
+      (void)ok;
+    }
+    // drain: every issued stage's copy has landed before the CTA can exit
+    if (lane == 0) {
+      for (int slot = 0; slot < kStages; ++slot) {
+        const int64_t uses = pstage > slot ? (pstage - slot + kStages - 1) / kStages : 0;
+        if (uses > 0) mbar_drain(full + slot, (unsigned)((uses - 1) & 1));
+      }
+      for (int xsl = 0; xsl < kXSlots; ++xsl)
+        if (xuses[xsl] > 0) mbar_drain(xfull + xsl, (unsigned)((xuses[xsl] - 1) & 1));
+    }
+  } else {
+    // ------------------------------------------------------------ consumers
+    using Tl = Tile<RC>;
+    int seq = 0;
+    int64_t cstage = 0;
+    const int rg = lane % Tl::RG, cg = lane / Tl::RG;
+    const int rowbase = warp * 64 + rg;  // item rows of this lane: rowbase + RG * i
+    TA acc[Tl::RPL][Tl::CPL];
 #pragma unroll
-      for (int c = 0; c < RC; ++c) acc[c] = (TA)0;
-      if (ain == kN || ain == kNt)
-        stream_block<TN, TA, RC>(static_cast<const TN*>(g.A[ain]) + it.a_off, it.m, it.a0, kp, Xs,
-                                 ring, lane, acc);
-      else
-        stream_block<T, TA, RC>(static_cast<const T*>(g.A[ain]) + it.a_off, it.m, it.a0, kp, Xs, ring,
-                                lane, acc);
-
-      if (valid) {
-        TV* orow = (out == kOutXh ? g.xh : (out == kOutYh ? g.yh : g.yp)) + (it.o_row + lane) * g.R + c0;
-        add_row<RC>(orow, acc, min(RC, g.R - c0), (g.R % 4) == 0 && (c0 % 4) == 0);
+    for (int i = 0; i < Tl::RPL; ++i)
+#pragma unroll
+      for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
+    for (;;) {
+      const int xs = seq % kXSlots;
+      if (!mbar_wait(xfull + xs, (unsigned)((seq / kXSlots) & 1), abort_flag, L.status)) break;
+      const Meta mt = meta[xs];
+      if (mt.out < 0) break;
+      const TA* Xs = xs_base + xs * kXsElems;
+      bool dead = false;
+      for (int s0 = 0; s0 < mt.np; s0 += kStagePanels, ++cstage) {
+        const int slot = (int)(cstage % kStages);
+        if (!mbar_wait(full + slot, (unsigned)((cstage / kStages) & 1), abort_flag, L.status)) {
+          dead = true;
+          break;
+        }
+        const unsigned char* sl = ring + slot * kStageBytes;
+        const int npst = min(kStagePanels, mt.np - s0);
+        if (mt.near)
+          consume_stage<TN, TA, RC>(sl, npst, s0, Xs, rowbase, cg, acc);
+        else
+          consume_stage<T, TA, RC>(sl, npst, s0, Xs, rowbase, cg, acc);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + slot);
       }
-      if (it.sig_idx >= 0) {
+      if (dead) break;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(xempty + xs);
+      ++seq;
+      if (!mt.flush) continue;
+      const SlotArgs<TV>& sa = slots[mt.slot];
+      TV* obase = mt.out == kOutXh ? sa.xh : (mt.out == kOutYh ? sa.yh : sa.yp);
+      const int R = sa.R;
+      const int col0 = mt.c0 + cg * Tl::CPL;
+      const int vc = min(Tl::CPL, R - col0);
+      const bool aligned = (R % 4) == 0 && (col0 % 4) == 0;
+#pragma unroll
+      for (int i = 0; i < Tl::RPL; ++i) {
+        const int r = rowbase + Tl::RG * i;
+        if (r < mt.rows && vc > 0) add_row<Tl::CPL>(obase + (mt.o_row + r) * R + col0, acc[i], vc, aligned);
+      }
+#pragma unroll
+      for (int i = 0; i < Tl::RPL; ++i)
+#pragma unroll
+        for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
+      if (mt.sig_idx >= 0) {
         __threadfence();
         __syncwarp();
-        if (lane == 0) atomicAdd(g.counters + it.sig_idx, 1);
+        if (lane == 0) atomicAdd(sa.counters + mt.sig_idx, 1);
       }
-      __syncwarp();
     }
   }
 }
 
 }  // namespace
 
+// Claim order of the groups.  The emission order below is a valid
+// dependency order but makes CTAs claim groups long before their inputs
+// exist.  This list scheduler simulates the launch: kWorkers CTAs, a group
+// costs a fixed latency plus its bytes at a CTA's share of HBM bandwidth, a
+// group is ready once every counter it waits for has seen all of its
+// contributions, and among ready groups the one with the longest remaining
+// dependency path (upward rank) starts first.  Groups are then claimed in
+// simulated start order, which is again a dependency order (a group starts
+// only after everything it waits for has finished), so the launch stays
+// deadlock free.
+void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups, int ncounters) {
+  const int ng = (int)groups.size();
+  if (ng < 2) return;
+  constexpr double kWorkers = 148 * 4, kLatency = 2.0e-6, kBandwidth = 6.0e12;  // s, B/s
+  std::vector<double> cost(ng);
+  std::vector<int> sig(ng, -1);
+  std::vector<std::vector<std::pair<int, int>>> waits(ng);
+  std::vector<std::vector<int>> waiters(ncounters);
+  std::vector<int> total(ncounters, 0);
+  for (int gi = 0; gi < ng; ++gi) {
+    double bytes = 0;
+    for (int sgi = groups[gi].x; sgi < groups[gi].y; ++sgi) {
+      const MvItem& it = items[sgi];
+      bytes += 16.0 * std::min(kItemRows, it.m - it.a0) * (pad8(it.k) / 4);  // float panels
+      if (it.wait_idx >= 0) waits[gi].push_back({it.wait_idx, it.wait_cnt});
+    }
+    cost[gi] = kLatency + bytes / (kBandwidth / kWorkers);
+    sig[gi] = items[groups[gi].y - 1].sig_idx;
+    if (sig[gi] >= 0) total[sig[gi]]++;
+    std::sort(waits[gi].begin(), waits[gi].end());
+    waits[gi].erase(std::unique(waits[gi].begin(), waits[gi].end()), waits[gi].end());
+    for (auto& w : waits[gi]) waiters[w.first].push_back(gi);
+  }
+  // upward rank: emission order is topological, so one reverse sweep suffices
+  std::vector<double> rank(ng, 0.0), cmax(ncounters, 0.0);
+  for (int gi = ng - 1; gi >= 0; --gi) {
+    rank[gi] = cost[gi] + (sig[gi] >= 0 ? cmax[sig[gi]] : 0.0);
+    for (auto& w : waits[gi]) cmax[w.first] = std::max(cmax[w.first], rank[gi]);
+  }
+  std::vector<int> pending(ng), done(ncounters, 0);
+  using Ready = std::pair<double, int>;  // (rank, group)
+  std::priority_queue<Ready> ready;
+  for (int gi = 0; gi < ng; ++gi) {
+    pending[gi] = (int)waits[gi].size();
+    if (pending[gi] == 0) ready.push({rank[gi], gi});
+  }
+  using Run = std::pair<double, int>;  // (finish, group), earliest first
+  std::priority_queue<Run, std::vector<Run>, std::greater<Run>> running;
+  std::vector<int> order;
+  order.reserve(ng);
+  double t = 0.0;
+  int free_workers = (int)kWorkers;
+  while ((int)order.size() < ng) {
+    while (free_workers > 0 && !ready.empty()) {
+      const int gi = ready.top().second;
+      ready.pop();
+      order.push_back(gi);
+      running.push({t + cost[gi], gi});
+      --free_workers;
+    }
+    if (running.empty()) break;  // cannot happen for a dependency-ordered list
+    const Run r = running.top();
+    running.pop();
+    t = r.first;
+    ++free_workers;
+    const int c = sig[r.second];
+    if (c >= 0 && ++done[c] == total[c])
+      for (int gw : waiters[c]) {
+        // a group waits for the counter to reach its full count
+        if (--pending[gw] == 0) ready.push({rank[gw], gw});
+      }
+  }
+  if ((int)order.size() != ng) return;  // keep the emission order
+  std::vector<int2> out(ng);
+  for (int i = 0; i < ng; ++i) out[i] = groups[order[i]];
+  groups.swap(out);
+}
+
 // Work items of one direction (0: product, 1: transposed product).
+// Segments = (block, 128-row slice, 64-column chunk); groups = runs of
+// segments with the same output rows claimed and accumulated together.
 int build_items(gca_h2* h, int dir, cudaStream_t st) {
   const int nc = h->nc;
   const bool trans = dir == 1;
   std::vector<MvItem> items;
-  std::vector<int> cx(nc, 0), cy(nc, 0);  // contributions to x-hat_c, y-hat_c
-  auto chunks = [&](int kind, int in, int out, int64_t a_off, int m, int k, int64_t x_row,
-                    int64_t o_row0, int wait_idx, int wait_cnt, int sig_idx, int* sig_cnt) {
-    for (int a0 = 0; a0 < m; a0 += 32) {
-      MvItem it{};
-      it.a_off = a_off;
-      it.x_row = x_row;
-      it.o_row = o_row0 + a0;
-      it.m = m;
-      it.k = k;
-      it.a0 = a0;
-      it.kind = kind | (in << 4) | (out << 8);
-      it.wait_idx = wait_cnt > 0 ? wait_idx : -1;
-      it.wait_cnt = wait_cnt;
-      it.sig_idx = sig_idx;
-      items.push_back(it);
-      if (sig_cnt) ++*sig_cnt;
+  std::vector<int2> groups;
+  std::vector<int> cx(nc, 0), cy(nc, 0);  // contributions (groups) to x-hat_c, y-hat_c
+  struct Blk {
+    int kind;
+    int64_t a_off;
+    int m, k;
+    int64_t x_row;
+    int wait_idx, wait_cnt;
+  };
+  // one group per slice of rows [a0, a0 + 128) over a list of blocks sharing output rows
+  auto emit = [&](const std::vector<Blk>& blks, int in, int out, int64_t o_row0, int m, int sig_idx,
+                  int* sig_cnt, int max_segs) {
+    for (int a0 = 0; a0 < m; a0 += kItemRows) {
+      int start = (int)items.size();
+      int segs = 0;
+      auto close = [&]() {
+        if ((int)items.size() == start) return;
+        items.back().flush = 1;
+        items.back().sig_idx = sig_idx;
+        groups.push_back(make_int2(start, (int)items.size()));
+        if (sig_cnt) ++*sig_cnt;
+        start = (int)items.size();
+        segs = 0;
+      };
+      for (const Blk& b : blks)
+        for (int k0 = 0; k0 < b.k; k0 += kChunk) {
+          if (segs == max_segs) close();
+          MvItem it{};
+          it.a_off = b.a_off;
+          it.x_row = b.x_row + k0;
+          it.o_row = o_row0 + a0;
+          it.m = m;
+          it.k = std::min(kChunk, b.k - k0);
+          it.a0 = a0;
+          it.k0 = k0;
+          it.kind = b.kind | (in << 4) | (out << 8);
+          it.wait_idx = b.wait_cnt > 0 ? b.wait_idx : -1;
+          it.wait_cnt = b.wait_cnt;
+          it.sig_idx = -1;
+          it.flush = 0;
+          items.push_back(it);
+          ++segs;
+        }
+      close();
     }
   };
   const auto& O = h->panel_off;
+  const int kCoupleSegs = 4, kNearSegs = 8;
   // forward transform: leaves
   for (int c : h->leaves)
     if (c > 0 && h->rank[c] > 0)
-      chunks(kVt, kInX, kOutXh, O[kVt][c], h->rank[c], h->end[c] - h->begin[c], h->begin[c],
-             h->xoff[c], -1, 0, c, &cx[c]);
-  // forward transform: up the tree, deepest level first
+      emit({{kVt, O[kVt][c], h->rank[c], h->end[c] - h->begin[c], h->begin[c], -1, 0}}, kInX, kOutXh,
+           h->xoff[c], h->rank[c], c, &cx[c], 1);
+  // forward transform: up the tree, deepest level first (one segment per group:
+  // the chain is latency bound, so its work is spread over many CTAs)
   for (int L = h->depth - 1; L >= 1; --L)
     for (int p : h->by_level[L]) {
       if (h->child0[p] < 0) continue;
       for (int ch : {h->child0[p], h->child1[p]})
-        chunks(kEt, kInXh, kOutXh, O[kEt][ch], h->rank[p], h->rank[ch], h->xoff[ch], h->xoff[p], ch,
-               cx[ch], p, &cx[p]);
+        emit({{kEt, O[kEt][ch], h->rank[p], h->rank[ch], h->xoff[ch], ch, cx[ch]}}, kInXh, kOutXh,
+             h->xoff[p], h->rank[p], p, &cx[p], 1);
     }
-  // coupling, blocks whose input cluster is deepest first
-  const int nfar = (int)h->far_t.size();
-  std::vector<int> order(nfar);
-  for (int b = 0; b < nfar; ++b) order[b] = b;
-  std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
-    const int iu = trans ? h->far_t[u] : h->far_s[u], iv = trans ? h->far_t[v] : h->far_s[v];
-    return h->level[iu] > h->level[iv];
-  });
-  for (int b : order) {
-    const int t = h->far_t[b], s = h->far_s[b];
-    const int own = trans ? s : t, in = trans ? t : s;
-    chunks(trans ? kSt : kS, kInXh, kOutYh, O[trans ? kSt : kS][b], h->rank[own], h->rank[in],
-           h->xoff[in], h->xoff[own], in, cx[in], nc + own, &cy[own]);
+  // coupling: per output cluster, its blocks (deepest input first) in groups
+  // of a few segments; clusters deepest first, since their inputs are ready
+  // first.  The near field has no dependencies and is placed after the
+  // couplings of the two deepest levels, as work for the CTAs while the
+  // forward transform climbs the tree.
+  std::vector<std::vector<int>> far_by_own(nc);
+  for (int b = 0; b < (int)h->far_t.size(); ++b)
+    far_by_own[trans ? h->far_s[b] : h->far_t[b]].push_back(b);
+  std::vector<int> owners;
+  for (int c = 0; c < nc; ++c)
+    if (!far_by_own[c].empty()) owners.push_back(c);
+  std::stable_sort(owners.begin(), owners.end(), [&](int u, int v) { return h->level[u] > h->level[v]; });
+  auto emit_couple = [&](int own) {
+    auto& bl = far_by_own[own];
+    std::stable_sort(bl.begin(), bl.end(), [&](int u, int v) {
+      const int iu = trans ? h->far_t[u] : h->far_s[u], iv = trans ? h->far_t[v] : h->far_s[v];
+      return h->level[iu] > h->level[iv];
+    });
+    std::vector<Blk> blks;
+    for (int b : bl) {
+      const int in = trans ? h->far_t[b] : h->far_s[b];
+      blks.push_back({trans ? kSt : kS, O[trans ? kSt : kS][b], h->rank[own], h->rank[in], h->xoff[in], in,
+                      cx[in]});
+    }
+    emit(blks, kInXh, kOutYh, h->xoff[own], h->rank[own], nc + own, &cy[own], kCoupleSegs);
+  };
+  size_t oi = 0;
+  for (; oi < owners.size() && h->level[owners[oi]] >= h->depth - 1; ++oi) emit_couple(owners[oi]);
+  {
+    std::vector<std::vector<int>> by_own(nc);
+    for (int b = 0; b < (int)h->near_t.size(); ++b) by_own[trans ? h->near_s[b] : h->near_t[b]].push_back(b);
+    for (int own = 0; own < nc; ++own) {
+      if (by_own[own].empty()) continue;
+      std::vector<Blk> blks;
+      for (int b : by_own[own]) {
+        const int in = trans ? h->near_t[b] : h->near_s[b];
+        blks.push_back({trans ? kNt : kN, O[trans ? kNt : kN][b], h->end[own] - h->begin[own],
+                        h->end[in] - h->begin[in], h->begin[in], -1, 0});
+      }
+      emit(blks, kInX, kOutY, h->begin[own], h->end[own] - h->begin[own], -1, nullptr, kNearSegs);
+    }
   }
-  // near field (no dependencies)
-  for (int b = 0; b < (int)h->near_t.size(); ++b) {
-    const int t = h->near_t[b], s = h->near_s[b];
-    const int own = trans ? s : t, in = trans ? t : s;
-    chunks(trans ? kNt : kN, kInX, kOutY, O[trans ? kNt : kN][b], h->end[own] - h->begin[own],
-           h->end[in] - h->begin[in], h->begin[in], h->begin[own], -1, 0, -1, nullptr);
-  }
+  for (; oi < owners.size(); ++oi) emit_couple(owners[oi]);
   // backward transform, level by level down (y-hat of the parent must be final)
   for (int L = 2; L <= h->depth; ++L)
     for (int c : h->by_level[L]) {
       const int p = h->parent[c];
       if (cy[p] == 0 || h->rank[c] == 0) continue;  // y-hat_p = 0
-      chunks(kE, kInYh, kOutYh, O[kE][c], h->rank[c], h->rank[p], h->xoff[p], h->xoff[c], nc + p,
-             cy[p], nc + c, &cy[c]);
+      emit({{kE, O[kE][c], h->rank[c], h->rank[p], h->xoff[p], nc + p, cy[p]}}, kInYh, kOutYh,
+           h->xoff[c], h->rank[c], nc + c, &cy[c], 1);
     }
   // leaf bases
   for (int c : h->leaves)
     if (c > 0 && h->rank[c] > 0 && cy[c] > 0)
-      chunks(kV, kInYh, kOutY, O[kV][c], h->end[c] - h->begin[c], h->rank[c], h->xoff[c],
-             h->begin[c], nc + c, cy[c], -1, nullptr);
-  h->n_items[dir] = (int64_t)items.size();
+      emit({{kV, O[kV][c], h->end[c] - h->begin[c], h->rank[c], h->xoff[c], nc + c, cy[c]}}, kInYh,
+           kOutY, h->begin[c], h->end[c] - h->begin[c], -1, nullptr, 1);
+  schedule_groups(items, groups, 2 * nc);
+  h->n_items[dir] = (int64_t)groups.size();
   GCA_TRY(upload(h->d_items[dir], items, st));
+  GCA_TRY(upload(h->d_groups[dir], groups, st));
   return GCA_OK;
 }
 
@@ -372,93 +779,176 @@ int finish_plan(gca_h2* h, cudaStream_t st) {
 
 namespace {
 
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }  // keeps every region aligned
+
+// One persistent launch over `count` handles (slots).  Workspace layout:
+// [claim counter, abort flag | per slot: x-hat, y-hat, y (cluster order),
+// counters] zeroed by one memset, then per slot x (cluster order), then the
+// slot descriptors.
 template <typename T, typename TN, typename TA, typename TV, int RC>
-int run_rc(const gca_h2* h, const DevMem* P, const DevMem* PN, bool trans, int R, const TV* x,
-           int64_t ldx, TV* y, int64_t ldy, cudaStream_t st) {
+int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, const void* const* x,
+              const int64_t* ldx, void* const* y, const int64_t* ldy, DevMem& ws,
+              std::vector<unsigned char>& ws_cache, int* status, cudaStream_t st) {
   const char* pn = sizeof(T) == 8 ? ".f64" : (sizeof(T) == 4 ? ".f32" : ".bf16");
-  PhaseScope ps(std::string("mv_persistent") + pn + (trans ? ".T" : ""), st);
+  PhaseScope ps(std::string("mv_persistent") + pn + (dir ? ".T" : ""), st);
   ps.launches(4);
-  const int dir = trans ? 1 : 0;
-  const int nchunk = (R + RC - 1) / RC;
-  // workspace: x-hat | y-hat | y (cluster order) | counters | claim counter | x (cluster order)
-  auto up256 = [](size_t b) { return (b + 255) & ~(size_t)255; };  // keeps every region aligned
-  const size_t vec_bytes = up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * R);
-  const size_t n_bytes = up256(sizeof(TV) * (size_t)h->n * R);
-  const size_t cnt_bytes = up256(sizeof(int) * 2 * (size_t)h->nc);
-  const size_t zeroed = 2 * vec_bytes + n_bytes + cnt_bytes + 256;
-  GCA_TRY(h->w_ws.reserve(zeroed + n_bytes));
-  unsigned char* base = h->w_ws.as<unsigned char>();
-  MvArgs<T, TV> g{};
-  for (int q = 0; q < kPanelKinds; ++q) g.A[q] = (q == kN || q == kNt) ? PN[q].p : P[q].p;
-  g.items = h->d_items[dir].as<MvItem>();
-  g.n_items = h->n_items[dir];
-  g.nchunk = nchunk;
-  g.R = R;
-  g.x = x;
-  g.ldx = ldx;
-  g.y = y;
-  g.ldy = ldy;
-  g.perm = h->d_perm.as<int>();
-  g.xh = reinterpret_cast<TV*>(base);
-  g.yh = reinterpret_cast<TV*>(base + vec_bytes);
-  g.yp = reinterpret_cast<TV*>(base + 2 * vec_bytes);
-  g.counters = reinterpret_cast<int*>(base + 2 * vec_bytes + n_bytes);
-  g.next = reinterpret_cast<unsigned long long*>(base + 2 * vec_bytes + n_bytes + cnt_bytes);
-  TV* xp = reinterpret_cast<TV*>(base + zeroed);
-  g.xp = xp;
-  g.status = h->d_status.as<int>();
+  std::vector<SlotArgs<TV>> sl(count);
+  size_t off = 256;  // claim counter + abort flag
+  std::vector<size_t> o_xh(count), o_yh(count), o_yp(count), o_cnt(count), o_xp(count);
+  for (int i = 0; i < count; ++i) {
+    const gca_h2* h = hs[i];
+    const int R = nrhs[i];
+    o_xh[i] = off;
+    off += up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * R);
+    o_yh[i] = off;
+    off += up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * R);
+    o_yp[i] = off;
+    off += up256(sizeof(TV) * (size_t)h->n * R);
+    o_cnt[i] = off;
+    off += up256(sizeof(int) * 2 * (size_t)h->nc);
+  }
+  const size_t zeroed = off;
+  for (int i = 0; i < count; ++i) {
+    o_xp[i] = off;
+    off += up256(sizeof(TV) * (size_t)hs[i]->n * nrhs[i]);
+  }
+  const size_t o_slots = off;
+  off += up256(sizeof(SlotArgs<TV>) * count);
+  if (off > ws.bytes) ws_cache.clear();
+  GCA_TRY(ws.reserve(off));
+  unsigned char* base = ws.as<unsigned char>();
+  int64_t work = 0;
+  int max_n = 0;
+  for (int i = 0; i < count; ++i) {
+    const gca_h2* h = hs[i];
+    SlotArgs<TV>& a = sl[i];
+    const DevMem* P = sizeof(T) == 8 ? h->P64 : (sizeof(T) == 4 ? h->P32 : h->P16);
+    const DevMem* PN = sizeof(TN) == 8 ? h->P64 : h->P32;
+    for (int q = 0; q < kPanelKinds; ++q) a.A[q] = (q == kN || q == kNt) ? PN[q].p : P[q].p;
+    a.items = h->d_items[dir].as<MvItem>();
+    a.groups = h->d_groups[dir].as<int2>();
+    a.R = nrhs[i];
+    a.nchunk = (a.R + RC - 1) / RC;
+    a.n_work = h->n_items[dir] * a.nchunk;
+    a.work_begin = work;
+    work += a.n_work;
+    a.n = h->n;
+    a.x = static_cast<const TV*>(x[i]);
+    a.ldx = ldx[i];
+    a.y = static_cast<TV*>(y[i]);
+    a.ldy = ldy[i];
+    a.perm = h->d_perm.as<int>();
+    a.xh = reinterpret_cast<TV*>(base + o_xh[i]);
+    a.yh = reinterpret_cast<TV*>(base + o_yh[i]);
+    a.yp = reinterpret_cast<TV*>(base + o_yp[i]);
+    a.counters = reinterpret_cast<int*>(base + o_cnt[i]);
+    a.xp = reinterpret_cast<TV*>(base + o_xp[i]);
+    max_n = std::max(max_n, h->n * a.R);
+  }
+  LaunchArgs L;
+  L.slots = base + o_slots;
+  L.nslots = count;
+  L.total = work;
+  L.next = reinterpret_cast<unsigned long long*>(base);
+  L.abort_flag = reinterpret_cast<int*>(base + 16);
+  L.status = status;
+  // the descriptors change only with the arguments: upload when they differ
+  // from what the workspace already holds
+  const size_t sbytes = sizeof(SlotArgs<TV>) * count;
+  if (ws_cache.size() != sbytes + sizeof(void*) ||
+      std::memcmp(ws_cache.data(), sl.data(), sbytes) != 0 ||
+      std::memcmp(ws_cache.data() + sbytes, &base, sizeof(void*)) != 0) {
+    GCA_TRY_CUDA(cudaMemcpyAsync(base + o_slots, sl.data(), sbytes, cudaMemcpyHostToDevice, st));
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // sl is a stack vector
+    ws_cache.assign(reinterpret_cast<const unsigned char*>(sl.data()),
+                    reinterpret_cast<const unsigned char*>(sl.data()) + sbytes);
+    ws_cache.insert(ws_cache.end(), reinterpret_cast<const unsigned char*>(&base),
+                    reinterpret_cast<const unsigned char*>(&base) + sizeof(void*));
+  }
   GCA_TRY_CUDA(cudaMemsetAsync(base, 0, zeroed, st));
-  const int nt = 256;
-  const unsigned nb = (unsigned)(((int64_t)h->n * R + nt - 1) / nt);
-  k_gather<TV><<<nb, nt, 0, st>>>(h->n, R, h->d_perm.as<int>(), x, ldx, xp);
-  const size_t smem = kRingBytes + sizeof(TA) * (size_t)pad8(h->max_rows) * RC;
-  auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
-  if (smem > 48 * 1024)
-    GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int dev = 0, sms = 0, per_sm = 0;
-  GCA_TRY_CUDA(cudaGetDevice(&dev));
-  GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  GCA_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem));
-  const int64_t want = (g.n_items * nchunk + kBatch - 1) / kBatch;
-  const int64_t cap = (int64_t)sms * std::max(per_sm, 1);
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, cap));
-  if (g.n_items > 0) kern<<<grid, 32, smem, st>>>(g);
-  k_scatter<TV><<<nb, nt, 0, st>>>(h->n, R, h->d_perm.as<int>(), g.yp, y, ldy);
+  const auto* d_slots = reinterpret_cast<const SlotArgs<TV>*>(base + o_slots);
+  const unsigned gx = (unsigned)std::min<int64_t>(1024, (max_n + 255) / 256);
+  k_gather<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots);
+  if (work > 0) {
+    const size_t smem = (size_t)kStages * kStageBytes + sizeof(TA) * (size_t)kXSlots * kChunk * RC +
+                        kXSlots * sizeof(Meta) + (2 * kStages + 2 * kXSlots) * sizeof(uint64_t);
+    auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
+    if (smem > 48 * 1024)
+      GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    GCA_TRY_CUDA(cudaGetDevice(&dev));
+    GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GCA_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    const int64_t cap = (int64_t)sms * std::max(per_sm, 1);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(work, cap));
+    kern<<<grid, kThreads, smem, st>>>(L);
+  }
+  k_scatter<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots);
   GCA_TRY_CUDA(cudaGetLastError());
   return GCA_OK;
 }
 
 template <typename T, typename TN, typename TA, typename TV>
-int run(const gca_h2* h, const DevMem* P, const DevMem* PN, bool trans, int R, const TV* x,
-        int64_t ldx, TV* y, int64_t ldy, cudaStream_t st) {
-  if (R >= 16) return run_rc<T, TN, TA, TV, 16>(h, P, PN, trans, R, x, ldx, y, ldy, st);
-  if (R > 4) return run_rc<T, TN, TA, TV, 8>(h, P, PN, trans, R, x, ldx, y, ldy, st);
-  if (R > 2) return run_rc<T, TN, TA, TV, 4>(h, P, PN, trans, R, x, ldx, y, ldy, st);
-  if (R > 1) return run_rc<T, TN, TA, TV, 2>(h, P, PN, trans, R, x, ldx, y, ldy, st);
-  return run_rc<T, TN, TA, TV, 1>(h, P, PN, trans, R, x, ldx, y, ldy, st);
+int launch(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, const void* const* x,
+           const int64_t* ldx, void* const* y, const int64_t* ldy, DevMem& ws,
+           std::vector<unsigned char>& wc, int* status, cudaStream_t st) {
+  int R = 1;
+  for (int i = 0; i < count; ++i) R = std::max(R, (int)nrhs[i]);
+  if (R >= 16) return launch_rc<T, TN, TA, TV, 16>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+  if (R > 4) return launch_rc<T, TN, TA, TV, 8>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+  if (R > 2) return launch_rc<T, TN, TA, TV, 4>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+  if (R > 1) return launch_rc<T, TN, TA, TV, 2>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+  return launch_rc<T, TN, TA, TV, 1>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+}
+
+int launch_any(const gca_h2* const* hs, int count, gca_prec prec, bool trans, const int32_t* nrhs,
+               const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy, DevMem& ws,
+               std::vector<unsigned char>& wc, int* status, cudaStream_t st) {
+  for (int i = 0; i < count; ++i)
+    if (!hs[i] || !x[i] || !y[i] || nrhs[i] < 1 || nrhs[i] > 4096 || ldx[i] < hs[i]->n ||
+        ldy[i] < hs[i]->n) {
+      set_error("h2_matvec: invalid arguments (handle " + std::to_string(i) + ")");
+      return GCA_ERR_INVALID_ARG;
+    }
+  const int dir = trans ? 1 : 0;
+  switch (prec) {
+    case GCA_F64:
+      return launch<double, double, double, double>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+    case GCA_F32:
+      return launch<float, float, float, float>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+    case GCA_BF16:
+      return launch<__nv_bfloat16, float, float, float>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc,
+                                                        status, st);
+  }
+  set_error("h2_matvec: unknown precision");
+  return GCA_ERR_INVALID_ARG;
 }
 
 }  // namespace
 
 int matvec(const gca_h2* h, gca_prec prec, bool trans, int32_t nrhs, const void* x, int64_t ldx,
            void* y, int64_t ldy, cudaStream_t st) {
-  if (!h || !x || !y || nrhs < 1 || nrhs > 4096 || ldx < h->n || ldy < h->n) {
-    set_error("h2_matvec: invalid arguments");
+  if (!h) {
+    set_error("h2_matvec: NULL handle");
     return GCA_ERR_INVALID_ARG;
   }
-  switch (prec) {
-    case GCA_F64:
-      return run<double, double, double, double>(h, h->P64, h->P64, trans, nrhs, (const double*)x,
-                                                 ldx, (double*)y, ldy, st);
-    case GCA_F32:
-      return run<float, float, float, float>(h, h->P32, h->P32, trans, nrhs, (const float*)x, ldx,
-                                             (float*)y, ldy, st);
-    case GCA_BF16:
-      return run<__nv_bfloat16, float, float, float>(h, h->P16, h->P32, trans, nrhs,
-                                                     (const float*)x, ldx, (float*)y, ldy, st);
+  const gca_h2* hs[1] = {h};
+  const void* xs[1] = {x};
+  void* ys[1] = {y};
+  return launch_any(hs, 1, prec, trans, &nrhs, xs, &ldx, ys, &ldy, h->w_ws, h->w_cache,
+                    h->d_status.as<int>(), st);
+}
+
+int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* nrhs,
+                 const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy,
+                 cudaStream_t st) {
+  if (!b || b->h.empty() || !nrhs || !x || !ldx || !y || !ldy) {
+    set_error("h2_matvec_batch: invalid arguments");
+    return GCA_ERR_INVALID_ARG;
   }
-  set_error("h2_matvec: unknown precision");
-  return GCA_ERR_INVALID_ARG;
+  std::vector<const gca_h2*> hs(b->h.begin(), b->h.end());
+  return launch_any(hs.data(), (int)hs.size(), prec, trans, nrhs, x, ldx, y, ldy, b->ws, b->w_cache,
+                    b->d_status.as<int>(), st);
 }
 
 int product_status(const gca_h2* h, int* out) {
