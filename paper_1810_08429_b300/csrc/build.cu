@@ -5,14 +5,14 @@
 //   2. k_cluster_boxes  bounding box of each cluster's vertices
 //      host             diameters, admissibility, block tree (tree.cpp)
 //   3. k_box_quad       Gauss rule on the faces of omega_tau (Eq. (2))
-//   4. k_green_aca      per tree level, deepest first, one CTA per cluster:
-//                       the Green quadrature matrix A_tau (leaves: all
-//                       triangles; parents: the children's pivot rows) is
-//                       formed in shared memory (or global scratch when it
-//                       does not fit), cross-approximated with complete
-//                       pivoting (Sect. 3), and V^ = U L^{-1} is written.
-//                       The host reads the level's ranks back to size the
-//                       next level.
+//   4. k_aca            per tree level, deepest first, one CTA (small
+//                       matrices) or one thread-block cluster of 8/16 CTAs
+//                       (large ones) per cluster: the Green quadrature matrix
+//                       A_tau (leaves: all triangles; parents: the children's
+//                       pivot rows) is formed in shared memory, cross-
+//                       approximated with complete pivoting (Sect. 3), and
+//                       V^ = U L^{-1} is written.  The host reads the level's
+//                       ranks back to size the next level.
 //   5. k_pack           leaf bases V_tau and transfer matrices E_tau
 //                       (Sect. 4) in float64 / float32 / bfloat16
 //   6. k_couple_entries S_{tau sigma} = G|tilde-tau x tilde-sigma (7 x 7
@@ -23,6 +23,7 @@
 //      k_singular<case> then integrate with one warp per entry.
 //   8. reduced-precision copies of S and N.
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -157,160 +158,196 @@ struct AcaJob {
   double diam;    // d_tau
 };
 
-__device__ __forceinline__ double block_max(double v, double* red) {
-  for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-  v = lane < nw ? red[lane] : 0.0;
-  for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-  return v;
-}
+// Cross approximation of one job on a thread-block cluster of C CTAs
+// (C = 1 for small jobs).  CTA q owns the box points nu in [q kw, q kw + kw)
+// and keeps both of their columns of A^ (nu: g-column, nu + k: dg-column)
+// in shared memory, column-major.  One ACA step (Sect. 3):
+//   1. apply the previous rank-one update (one FMA per entry) while taking
+//      the largest |entry| as an IEEE bit pattern (integer max is exact for
+//      non-negative doubles and keeps the slow FP64 pipe free);
+//   2. cluster max -> stopping rule; threshold max (1 - tie);
+//   3. smallest column-major global index at or above the threshold
+//      (columns of a CTA are in increasing global order, so the first hit of
+//      each thread's strided sweep is its minimum) -> cluster min;
+//   4. the owner of the pivot column forms u = R[:, j*] / p, writes it to the
+//      U scratch and the other CTAs copy it through distributed shared memory;
+//      every CTA keeps its slice of the pivot row as v.
+// Afterwards V^ = U L^{-1} (L = U[P, :], unit lower triangular) is solved
+// row by row, the rows spread over the cluster.
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
-__device__ __forceinline__ int block_min_int(int v, int* red) {
-  for (int off = 16; off; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-  v = lane < nw ? red[lane] : INT_MAX;
-  for (int off = 16; off; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
-  return v;
-}
-
-__device__ __forceinline__ int block_or(int v, int* red) {
-  v = __any_sync(0xffffffffu, v);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  const int nw = blockDim.x >> 5;
-  v = lane < nw ? red[lane] : 0;
-  return __any_sync(0xffffffffu, v);
-}
-
-// Shared memory: row ids [rows_cap] int, pivot rows [rows_cap] int, u [rows_cap],
-// v [2k], reduction scratch [64], then (optionally) the matrix [rows_cap * 2k].
-__global__ void __launch_bounds__(kAcaThreads)
-k_green_aca(const AcaJob* __restrict__ jobs, int k, int rows_cap, int mat_in_smem,
-            const int* __restrict__ perm, const P4* __restrict__ tq,
-            const P4* __restrict__ zq, int* __restrict__ piv_pool,
-            double* __restrict__ mscratch, double* __restrict__ uscratch,
-            double* __restrict__ vh_pool, int* __restrict__ rank_out, double tol, double tie,
-            int* __restrict__ status) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const AcaJob job = jobs[blockIdx.x];
-  const int twok = 2 * k;
-  int* s_rows = reinterpret_cast<int*>(smem_raw);
-  int* s_prow = s_rows + rows_cap;
-  double* s_u = reinterpret_cast<double*>(s_prow + rows_cap + ((2 * rows_cap) & 1));
-  double* s_v = s_u + rows_cap;
-  double* s_red = s_v + twok;
-  int* s_ired = reinterpret_cast<int*>(s_red + 32);
-  double* M = mat_in_smem ? reinterpret_cast<double*>(s_red + 64) : mscratch + job.m_off;
-  double* U = uscratch + job.u_off;
-  const int rows = job.rows;
-  const int tid = threadIdx.x, nth = blockDim.x;
-
-  for (int i = tid; i < rows; i += nth) {
-    int t;
-    if (job.leaf)
-      t = perm[job.tbegin + i];
-    else
-      t = i < job.r0 ? piv_pool[job.piv0 + i] : piv_pool[job.piv1 + (i - job.r0)];
-    s_rows[i] = t;
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  for (int off = 16; off; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = o > v ? o : v;
   }
+  return v;
+}
+__device__ __forceinline__ int warp_min_int(int v) {
+  for (int off = 16; off; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
+  return v;
+}
+
+__global__ void __launch_bounds__(kAcaThreads)
+k_aca(const AcaJob* __restrict__ jobs, int k, int rows_cap, int kw_cap, const int* __restrict__ perm,
+      const P4* __restrict__ tq, const P4* __restrict__ zq, int* __restrict__ piv_pool,
+      double* __restrict__ uscratch, double* __restrict__ vh_pool, int* __restrict__ rank_out,
+      double tol, double tie, int* __restrict__ status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int q = (int)cluster.block_rank();
+  const AcaJob job = jobs[blockIdx.x / C];
+  const int rows = job.rows;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  const int kw = (k + C - 1) / C;
+  const int nu0 = q * kw;
+  const int nk = max(0, min(kw, k - nu0));  // box points of this CTA
+  const int ncol = 2 * nk;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* S = reinterpret_cast<double*>(smem_raw);                  // rows_cap x 2 kw_cap
+  double* s_u = S + (size_t)rows_cap * 2 * kw_cap;                    // rows_cap
+  double* s_v = s_u + rows_cap;                                       // 2 kw_cap
+  int* s_rows = reinterpret_cast<int*>(s_v + 2 * kw_cap);             // rows_cap
+  int* s_prow = s_rows + rows_cap;                                    // rows_cap
+  __shared__ unsigned long long s_wmax[32];
+  __shared__ int s_wmin[32];
+  __shared__ unsigned long long s_max;  // cluster visible
+  __shared__ int s_idx;                 // cluster visible
+
+  for (int i = tid; i < rows; i += nth)
+    s_rows[i] = job.leaf ? perm[job.tbegin + i]
+                         : (i < job.r0 ? piv_pool[job.piv0 + i] : piv_pool[job.piv1 + (i - job.r0)]);
   __syncthreads();
 
-  // A^[i, nu] = sqrt(w) int g(x, z_nu); A^[i, nu + k] = -d sqrt(w) int dg/dn_z(x, z_nu)
+  // this CTA's columns of A^: nu (g) and nu + k (dg) for its box points
   const P4* z = zq + (int64_t)job.c * k;
   const int m2 = k / 6;
-  for (int idx = tid; idx < rows * k; idx += nth) {
-    const int i = idx % rows, nu = idx / rows;
+  for (int idx = tid; idx < rows * nk; idx += nth) {
+    const int i = idx % rows, a = idx / rows, nu = nu0 + a;
     const P4 zz = z[nu];
     const int face = nu / m2, d = face >> 1;
     const double sgn = (face & 1) ? 1.0 : -1.0;
     const P4* xq = tq + 7 * (int64_t)s_rows[i];
     double gs = 0.0, ds = 0.0;
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const P4 x = xq[q];
+    for (int qq = 0; qq < 7; ++qq) {
+      const P4 x = xq[qq];
       const double dx = x.x - zz.x, dy = x.y - zz.y, dz = x.z - zz.z;
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      const double ir = rsqrt(r2);
+      const double ir = rsqrt(dx * dx + dy * dy + dz * dz);
       const double dn = sgn * (d == 0 ? dx : (d == 1 ? dy : dz));
       gs += x.w * ir;
       ds += x.w * dn * ir * ir * ir;
     }
-    M[(int64_t)nu * rows + i] = zz.w * gs * kInv4Pi;
-    M[(int64_t)(nu + k) * rows + i] = -job.diam * zz.w * ds * kInv4Pi;
+    S[(int64_t)a * rows + i] = zz.w * gs * kInv4Pi;
+    S[(int64_t)(nk + a) * rows + i] = -job.diam * zz.w * ds * kInv4Pi;
   }
   __syncthreads();
 
-  // cross approximation with complete pivoting (Sect. 3)
-  const int total = rows * twok;
+  const int total = rows * ncol;
+  double* U = uscratch + job.u_off;
   int r = 0;
   double first = 0.0;
   bool have_update = false;
   for (;;) {
-    double lmax = 0.0;
-    int lnan = 0;
+    // 1. update + local max of |R| (bit patterns)
+    unsigned long long lmax = 0;
     for (int idx = tid; idx < total; idx += nth) {
-      double val = M[idx];
+      double val = S[idx];
       if (have_update) {
-        const int i = idx % rows, j = idx / rows;
-        val = __dsub_rn(val, __dmul_rn(s_u[i], s_v[j]));
-        M[idx] = val;
+        val = fma(-s_u[idx % rows], s_v[idx / rows], val);
+        S[idx] = val;
       }
-      lmax = fmax(lmax, fabs(val));
-      lnan |= (val != val);
+      const unsigned long long b = (unsigned long long)__double_as_longlong(val) & kAbsMask;
+      lmax = b > lmax ? b : lmax;
     }
-    const double big = block_max(lmax, s_red);
-    const int anynan = block_or(lnan, s_ired);
-    if (anynan) {
-      if (tid == 0) atomicOr(status, kStatusNumeric);
+    lmax = warp_max_u64(lmax);
+    if (lane == 0) s_wmax[wid] = lmax;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long m = 0;
+      for (int w = 0; w < nth / 32; ++w) m = s_wmax[w] > m ? s_wmax[w] : m;
+      s_max = m;
+    }
+    cluster.sync();
+    // 2. cluster max (each warp reads the C CTAs' maxima)
+    unsigned long long gmax = 0;
+    if (lane < C) gmax = *cluster.map_shared_rank(&s_max, lane);
+    gmax = warp_max_u64(gmax);
+    if (gmax > kInfBits) {
+      if (tid == 0 && q == 0) atomicOr(status, kStatusNumeric);
       break;
     }
+    const double big = __longlong_as_double((long long)gmax);
     if (r == 0) first = big;
     if (big == 0.0 || (r > 0 && big <= tol * first)) break;
-    const double thr = big * (1.0 - tie);
+    const unsigned long long thr = (unsigned long long)__double_as_longlong(big * (1.0 - tie));
+    // 3. smallest global column-major index at or above the threshold
     int lidx = INT_MAX;
-    for (int idx = tid; idx < total; idx += nth)
-      if (fabs(M[idx]) >= thr) {
-        lidx = idx;
+    for (int idx = tid; idx < total; idx += nth) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(S[idx]) & kAbsMask;
+      if (b >= thr) {
+        const int i = idx % rows, jj = idx / rows;
+        const int j = jj < nk ? nu0 + jj : k + nu0 + (jj - nk);
+        lidx = j * rows + i;
         break;
       }
-    const int gidx = block_min_int(lidx, s_ired);
-    const int ip = gidx % rows, jp = gidx / rows;
-    const double p = M[gidx];
-    for (int i = tid; i < rows; i += nth) {
-      const double u = __ddiv_rn(M[(int64_t)jp * rows + i], p);
-      s_u[i] = u;
-      U[(int64_t)r * rows + i] = u;
     }
-    for (int j = tid; j < twok; j += nth) s_v[j] = M[(int64_t)j * rows + ip];
+    lidx = warp_min_int(lidx);
+    if (lane == 0) s_wmin[wid] = lidx;
+    __syncthreads();
+    if (tid == 0) {
+      int m = INT_MAX;
+      for (int w = 0; w < nth / 32; ++w) m = min(m, s_wmin[w]);
+      s_idx = m;
+    }
+    cluster.sync();
+    int gidx = INT_MAX;
+    if (lane < C) gidx = *cluster.map_shared_rank(&s_idx, lane);
+    gidx = warp_min_int(gidx);
+    const int ip = gidx % rows, jp = gidx / rows;
+    const int nup = jp < k ? jp : jp - k;
+    const int owner = nup / kw;
+    // 4. pivot row slice, pivot column from its owner
+    for (int jj = tid; jj < ncol; jj += nth) s_v[jj] = S[(int64_t)jj * rows + ip];
+    if (q == owner) {
+      const int ajj = jp < k ? (nup - nu0) : (nk + nup - nu0);
+      const double p = S[(int64_t)ajj * rows + ip];
+      for (int i = tid; i < rows; i += nth) {
+        const double u = S[(int64_t)ajj * rows + i] / p;
+        s_u[i] = u;
+        U[(int64_t)r * rows + i] = u;
+      }
+    }
     if (tid == 0) s_prow[r] = ip;
+    cluster.sync();
+    if (q != owner) {
+      const double* ru = cluster.map_shared_rank(s_u, owner);
+      for (int i = tid; i < rows; i += nth) s_u[i] = ru[i];
+    }
     __syncthreads();
     ++r;
     have_update = true;
     if (r == job.rmax) break;
   }
-  __syncthreads();
+  cluster.sync();  // every U column written, no CTA still reads a peer's u
 
-  // V^ = U L^{-1}, L = U[P, :] unit lower triangular; V^ row-major rows x r
+  // V^ = U L^{-1}, rows spread over the cluster; V^ row-major rows x r
   double* Vh = vh_pool + job.vh_off;
-  for (int a = tid; a < rows; a += nth) {
+  const int rpc = (rows + C - 1) / C;
+  for (int a = q * rpc + tid; a < min(rows, (q + 1) * rpc); a += nth) {
     for (int c = r - 1; c >= 0; --c) {
-      double s = U[(int64_t)c * rows + a];
-      for (int d = c + 1; d < r; ++d) s -= Vh[(int64_t)a * r + d] * U[(int64_t)c * rows + s_prow[d]];
-      Vh[(int64_t)a * r + c] = s;
+      double sacc = U[(int64_t)c * rows + a];
+      for (int d = c + 1; d < r; ++d) sacc -= Vh[(int64_t)a * r + d] * U[(int64_t)c * rows + s_prow[d]];
+      Vh[(int64_t)a * r + c] = sacc;
     }
   }
-  for (int t = tid; t < r; t += nth) piv_pool[job.p_off + t] = s_rows[s_prow[t]];
-  if (tid == 0) rank_out[job.c] = r;
+  if (q == 0) {
+    for (int t = tid; t < r; t += nth) piv_pool[job.p_off + t] = s_rows[s_prow[t]];
+    if (tid == 0) rank_out[job.c] = r;
+  }
 }
 
 // --------------------------------------------------------------- packing
@@ -769,7 +806,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     // upper bounds, refined per level below
     piv_cap += std::min<int64_t>(h->end[c] - h->begin[c], 2 * k);
   }
-  DevMem d_piv, d_rank, d_vh, d_mscr, d_uscr, d_jobs;
+  DevMem d_piv, d_rank, d_vh, d_uscr, d_jobs;
   GCA_TRY(d_piv.alloc(sizeof(int) * (size_t)std::max<int64_t>(piv_cap, 1)));
   GCA_TRY(d_rank.alloc(sizeof(int) * (size_t)nc));
   GCA_TRY_CUDA(cudaMemsetAsync(d_rank.p, 0, sizeof(int) * nc, st));
@@ -785,11 +822,20 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY_CUDA(cudaGetDevice(&dev));
   int smem_optin = 0;
   GCA_TRY_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  GCA_TRY_CUDA(cudaFuncSetAttribute(k_green_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+  cudaFuncAttributes aca_attr{};
+  GCA_TRY_CUDA(cudaFuncGetAttributes(&aca_attr, k_aca));
+  const int aca_dyn_max = smem_optin - (int)aca_attr.sharedSizeBytes;
+  GCA_TRY_CUDA(cudaFuncSetAttribute(k_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, aca_dyn_max));
+  GCA_TRY_CUDA(cudaFuncSetAttribute(k_aca, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   const double tie = std::ldexp(1.0, -40);
+  // shared memory of one CTA of k_aca for a job of `rows` rows on a C-CTA cluster
+  auto aca_smem = [&](int rows, int C) -> size_t {
+    const int kw = (k + C - 1) / C;
+    return sizeof(double) * ((size_t)rows * 2 * kw + rows + 2 * kw) + sizeof(int) * 2 * (size_t)rows;
+  };
+  const size_t smem_budget = (size_t)aca_dyn_max;
   for (int L = h->depth; L >= 1; --L) {
     std::vector<AcaJob> jobs;
-    int rows_cap = 0;
     for (int c : h->by_level[L]) {
       AcaJob j{};
       j.c = c;
@@ -814,7 +860,6 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
       vh_off[c] = vh_used;
       vh_used += (int64_t)j.rows * j.rmax;
       rows_of[c] = j.rows;
-      rows_cap = std::max(rows_cap, j.rows);
       jobs.push_back(j);
     }
     if (jobs.empty()) continue;
@@ -822,37 +867,66 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
       set_error("gca_build: internal pool bound exceeded");
       return GCA_ERR_INVALID_ARG;
     }
-    rows_cap = std::max(rows_cap, 1);
-    const size_t head = (size_t)2 * rows_cap * sizeof(int) + ((2 * rows_cap) & 1) * sizeof(int) +
-                        sizeof(double) * ((size_t)rows_cap + 2 * k + 64);
-    const size_t mat = sizeof(double) * (size_t)rows_cap * 2 * k;
-    const bool in_smem = head + mat <= (size_t)smem_optin;
-    int64_t m_used = 0, u_used = 0;
+    int64_t u_used = 0;
     for (auto& j : jobs) {
-      j.m_off = m_used;
-      if (!in_smem) m_used += (int64_t)j.rows * 2 * k;
       j.u_off = u_used;
       u_used += (int64_t)j.rows * j.rmax;
     }
-    GCA_TRY(d_mscr.reserve(sizeof(double) * (size_t)std::max<int64_t>(m_used, 1)));
     GCA_TRY(d_uscr.reserve(sizeof(double) * (size_t)std::max<int64_t>(u_used, 1)));
-    GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * jobs.size()));
-    GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, jobs.data(), sizeof(AcaJob) * jobs.size(),
-                                 cudaMemcpyHostToDevice, st));
-    const size_t smem = head + (in_smem ? mat : 0);
-    {
-      PhaseScope ps__("green_aca", st);
-      k_green_aca<<<(unsigned)jobs.size(), kAcaThreads, smem, st>>>(
-          d_jobs.as<AcaJob>(), k, rows_cap, in_smem ? 1 : 0, h->d_perm.as<int>(), d_tq.as<P4>(),
-          d_zq.as<P4>(), d_piv.as<int>(), d_mscr.as<double>(), d_uscr.as<double>(),
-          d_vh.as<double>(), d_rank.as<int>(), prm->aca_tol, tie, d_status.as<int>());
+    // small jobs on one CTA, large ones on clusters of 8 or 16 CTAs whose
+    // column slices fit in shared memory
+    std::vector<AcaJob> by_c[3];
+    const int csize[3] = {1, 8, 16};
+    for (const auto& j : jobs) {
+      int pick = -1;
+      if ((size_t)j.rows * 2 * k * sizeof(double) <= 96 * 1024 && aca_smem(j.rows, 1) <= smem_budget)
+        pick = 0;
+      else if (aca_smem(j.rows, 8) <= smem_budget)
+        pick = 1;
+      else if (aca_smem(j.rows, 16) <= smem_budget)
+        pick = 2;
+      if (pick < 0) {
+        set_error("gca_build: cross approximation matrix too large for the cluster kernel");
+        return GCA_ERR_UNSUPPORTED;
+      }
+      by_c[pick].push_back(j);
     }
-    GCA_TRY_CUDA(cudaGetLastError());
+    GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * jobs.size()));
+    size_t at = 0;
+    for (int g = 0; g < 3; ++g) {
+      if (by_c[g].empty()) continue;
+      const int C = csize[g];
+      int rows_cap = 1;
+      for (const auto& j : by_c[g]) rows_cap = std::max(rows_cap, j.rows);
+      const int kw = (k + C - 1) / C;
+      const size_t smem = aca_smem(rows_cap, C);
+      AcaJob* dj = d_jobs.as<AcaJob>() + at;
+      GCA_TRY_CUDA(cudaMemcpyAsync(dj, by_c[g].data(), sizeof(AcaJob) * by_c[g].size(),
+                                   cudaMemcpyHostToDevice, st));
+      at += by_c[g].size();
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(by_c[g].size() * C));
+      cfg.blockDim = dim3(kAcaThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      PhaseScope ps__("green_aca", st);
+      GCA_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_aca, (const AcaJob*)dj, k, rows_cap, kw,
+                                      (const int*)h->d_perm.as<int>(), (const P4*)d_tq.as<P4>(),
+                                      (const P4*)d_zq.as<P4>(), d_piv.as<int>(), d_uscr.as<double>(),
+                                      d_vh.as<double>(), d_rank.as<int>(), prm->aca_tol, tie,
+                                      d_status.as<int>()));
+    }
     GCA_TRY(check_status(d_status, st, "cross approximation"));
     GCA_TRY_CUDA(cudaMemcpyAsync(h->rank.data(), d_rank.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
     GCA_TRY_CUDA(cudaStreamSynchronize(st));
   }
-  d_mscr.release();
   d_uscr.release();
 
   // offsets of the stored coefficients
