@@ -1,6 +1,6 @@
 """Compile the CUDA sources of the package into an in-tree shared library.
 
-    python -m paper_1810_08429_b300._build
+    python paper_1810_08429_b300/_build.py
 
 produces ``paper_1810_08429_b300/libgca.so`` for sm_103a (B300).  Host code
 is compiled without floating-point contraction so that the cluster tree and
