@@ -206,6 +206,27 @@ int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* para
 int h2_matvec(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx,
               void* y, int64_t ldy, void* stream);
 
+/* y = G_H2 x without allocating any device memory (the paper has no
+ * counterpart; this is a service to callers).  For callers that cannot call
+ * cudaMalloc while they run a product -- code between kernels of a
+ * latency-critical loop or in host callbacks, where an allocation would
+ * synchronise or is not allowed, and programs that hand out all device memory
+ * themselves.  Same arguments, conventions and result as h2_matvec (up to the
+ * order of floating-point accumulation); the workspace comes from one
+ * 32 MiB array in the library's device data instead of the handle:
+ *   - every GPU that loads the library holds that array until the process
+ *     exits;
+ *   - the first call on a device looks up the array's address on that device
+ *     (make that first call before any stream capture);
+ *   - all calls share the array: calls that overlap on the GPU (other streams,
+ *     other threads, other handles) race and give wrong results; order them;
+ *   - a product whose workspace exceeds the array is rejected with
+ *     GCA_ERR_UNSUPPORTED and a message giving the bytes it would need (the
+ *     20480-triangle workload fits with 16 float32 right-hand sides).
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+int h2_matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx,
+                      void* y, int64_t ldy, void* stream);
+
 /* y = G_H2^T x, same conventions as h2_matvec. */
 int h2_matvec_transpose(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x,
                         int64_t ldx, void* y, int64_t ldy, void* stream);

@@ -69,7 +69,7 @@ class _Dump(ctypes.Structure):
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
-            f"{LIB_PATH} is missing: build it with `python -m paper_1810_08429_b300._build`")
+            f"{LIB_PATH} is missing: build it with `python paper_1810_08429_b300/_build.py`")
     lib = ctypes.CDLL(LIB_PATH)
     vp = ctypes.c_void_p
     sig = {
@@ -81,6 +81,8 @@ def _load():
                                      ctypes.c_int64, vp]),
         "h2_matvec_transpose": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int32, vp,
                                                ctypes.c_int64, vp, ctypes.c_int64, vp]),
+        "h2_matvec_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int32, vp, ctypes.c_int64, vp,
+                                             ctypes.c_int64, vp]),
         "gca_h2_stats": (ctypes.c_int, [vp, ctypes.POINTER(_Stats)]),
         "gca_h2_export": (ctypes.c_int, [vp, ctypes.POINTER(_Dump)]),
         "gca_h2_status": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int32)]),

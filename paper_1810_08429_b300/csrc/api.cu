@@ -47,6 +47,11 @@ int h2_matvec_transpose(const gca_h2* h, gca_prec prec, int32_t nrhs, const void
   return gca::matvec(h, prec, true, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream));
 }
 
+int h2_matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx,
+                      void* y, int64_t ldy, void* stream) {
+  return gca::matvec_noalloc(h, prec, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream));
+}
+
 int gca_h2_stats(const gca_h2* h, gca_stats* o) {
   if (!h || !o) {
     gca::set_error("gca_h2_stats: NULL argument");

@@ -113,6 +113,8 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
 int finish_plan(gca_h2* h, cudaStream_t st);
 int make_panels(gca_h2* h, cudaStream_t st);
 int product_status(const gca_h2* h, int* out);
+int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx, void* y,
+                   int64_t ldy, cudaStream_t st);
 int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* nrhs,
                  const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy,
                  cudaStream_t st);

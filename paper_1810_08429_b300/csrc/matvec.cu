@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 #include <queue>
 #include <cstring>
 #include <string>
@@ -949,6 +950,164 @@ int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t
   std::vector<const gca_h2*> hs(b->h.begin(), b->h.end());
   return launch_any(hs.data(), (int)hs.size(), prec, trans, nrhs, x, ldx, y, ldy, b->ws, b->w_cache,
                     b->d_status.as<int>(), st);
+}
+
+// ------------------------------------------------------- no-alloc product
+//
+// Some callers cannot allocate device memory while they run a product: code
+// that executes inside a region where cudaMalloc is forbidden or would
+// synchronise at the wrong moment (for instance between kernels of a
+// latency-critical loop, or inside host callbacks), and programs that manage
+// every byte of device memory themselves.  h2_matvec_noalloc serves them: it
+// runs the same persistent product as h2_matvec, but its workspace (x-hat,
+// y-hat, the cluster-order copies of x and y, the dependency counters and the
+// slot descriptor) lives in the file-scope array below instead of memory the
+// handle allocates.  Every GPU that loads this library holds the array until
+// the process exits.  Only the array's device address, found once per device
+// with cudaGetSymbolAddress, is ever handed to a kernel: in host code the name
+// g_noalloc_scratch is just a host-side stand-in.
+
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// device address of the scratch array on the current device (looked up on the
+// first call per device, with that device current)
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  GCA_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("h2_matvec_noalloc: device ordinal out of range");
+    return GCA_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("h2_matvec_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return GCA_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return GCA_OK;
+}
+
+template <typename TV>
+__global__ void k_put_slot(SlotArgs<TV> a, SlotArgs<TV>* dst) { *dst = a; }
+
+// h2_matvec's launch for one handle with the workspace carved out of `base`
+// (capacity `cap` bytes); nothing is allocated.
+template <typename T, typename TN, typename TA, typename TV, int RC>
+int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* y, int64_t ldy,
+                      unsigned char* base, size_t cap, cudaStream_t st) {
+  const size_t b_xh = up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * R);
+  const size_t b_yp = up256(sizeof(TV) * (size_t)h->n * R);
+  const size_t b_cnt = up256(sizeof(int) * 2 * (size_t)h->nc);
+  const size_t o_xh = 256, o_yh = o_xh + b_xh, o_yp = o_yh + b_xh, o_cnt = o_yp + b_yp;
+  const size_t zeroed = o_cnt + b_cnt;
+  const size_t o_xp = zeroed, o_slot = o_xp + b_yp;
+  const size_t need = o_slot + up256(sizeof(SlotArgs<TV>));
+  if (need > cap) {
+    set_error("h2_matvec_noalloc: this product needs " + std::to_string(need) +
+              " bytes of workspace, more than the " + std::to_string(cap) +
+              "-byte scratch array (fewer right-hand sides or h2_matvec)");
+    return GCA_ERR_UNSUPPORTED;
+  }
+  SlotArgs<TV> a{};
+  const DevMem* P = sizeof(T) == 8 ? h->P64 : (sizeof(T) == 4 ? h->P32 : h->P16);
+  const DevMem* PN = sizeof(TN) == 8 ? h->P64 : h->P32;
+  for (int q = 0; q < kPanelKinds; ++q) a.A[q] = (q == kN || q == kNt) ? PN[q].p : P[q].p;
+  a.items = h->d_items[0].as<MvItem>();
+  a.groups = h->d_groups[0].as<int2>();
+  a.R = R;
+  a.nchunk = (R + RC - 1) / RC;
+  a.n_work = h->n_items[0] * a.nchunk;
+  a.work_begin = 0;
+  a.n = h->n;
+  a.x = static_cast<const TV*>(x);
+  a.ldx = ldx;
+  a.y = static_cast<TV*>(y);
+  a.ldy = ldy;
+  a.perm = h->d_perm.as<int>();
+  a.xh = reinterpret_cast<TV*>(base + o_xh);
+  a.yh = reinterpret_cast<TV*>(base + o_yh);
+  a.yp = reinterpret_cast<TV*>(base + o_yp);
+  a.counters = reinterpret_cast<int*>(base + o_cnt);
+  a.xp = reinterpret_cast<TV*>(base + o_xp);
+  LaunchArgs L;
+  L.slots = base + o_slot;
+  L.nslots = 1;
+  L.total = a.n_work;
+  L.next = reinterpret_cast<unsigned long long*>(base);
+  L.abort_flag = reinterpret_cast<int*>(base + 16);
+  L.status = h->d_status.as<int>();
+  // the array keeps the previous call's contents: the claim counter, abort
+  // flag, x-hat, y-hat, y and the counters must start at zero
+  GCA_TRY_CUDA(cudaMemsetAsync(base, 0, zeroed, st));
+  // the descriptor travels as a kernel argument: no host buffer to keep alive
+  auto* d_slots = reinterpret_cast<SlotArgs<TV>*>(base + o_slot);
+  k_put_slot<TV><<<1, 1, 0, st>>>(a, d_slots);
+  const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, ((int64_t)h->n * R + 255) / 256));
+  k_gather<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots);
+  if (a.n_work > 0) {
+    const size_t smem = (size_t)kStages * kStageBytes + sizeof(TA) * (size_t)kXSlots * kChunk * RC +
+                        kXSlots * sizeof(Meta) + (2 * kStages + 2 * kXSlots) * sizeof(uint64_t);
+    auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
+    if (smem > 48 * 1024)
+      GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0, per_sm = 0;
+    GCA_TRY_CUDA(cudaGetDevice(&dev));
+    GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GCA_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    const int64_t capc = (int64_t)sms * std::max(per_sm, 1);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.n_work, capc));
+    kern<<<grid, kThreads, smem, st>>>(L);
+  }
+  k_scatter<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots);
+  GCA_TRY_CUDA(cudaGetLastError());
+  return GCA_OK;
+}
+
+template <typename T, typename TN, typename TA, typename TV>
+int launch_noalloc(const gca_h2* h, int R, const void* x, int64_t ldx, void* y, int64_t ldy,
+                   unsigned char* base, size_t cap, cudaStream_t st) {
+  if (R >= 16) return launch_noalloc_rc<T, TN, TA, TV, 16>(h, R, x, ldx, y, ldy, base, cap, st);
+  if (R > 4) return launch_noalloc_rc<T, TN, TA, TV, 8>(h, R, x, ldx, y, ldy, base, cap, st);
+  if (R > 2) return launch_noalloc_rc<T, TN, TA, TV, 4>(h, R, x, ldx, y, ldy, base, cap, st);
+  if (R > 1) return launch_noalloc_rc<T, TN, TA, TV, 2>(h, R, x, ldx, y, ldy, base, cap, st);
+  return launch_noalloc_rc<T, TN, TA, TV, 1>(h, R, x, ldx, y, ldy, base, cap, st);
+}
+
+}  // namespace
+
+int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx, void* y,
+                   int64_t ldy, cudaStream_t st) {
+  if (!h || !x || !y || nrhs < 1 || nrhs > 4096 || ldx < h->n || ldy < h->n) {
+    set_error("h2_matvec_noalloc: invalid arguments");
+    return GCA_ERR_INVALID_ARG;
+  }
+  unsigned char* base = nullptr;
+  GCA_TRY(noalloc_scratch(&base));
+  switch (prec) {
+    case GCA_F64:
+      return launch_noalloc<double, double, double, double>(h, nrhs, x, ldx, y, ldy, base,
+                                                            kNoAllocScratchBytes, st);
+    case GCA_F32:
+      return launch_noalloc<float, float, float, float>(h, nrhs, x, ldx, y, ldy, base,
+                                                        kNoAllocScratchBytes, st);
+    case GCA_BF16:
+      return launch_noalloc<__nv_bfloat16, float, float, float>(h, nrhs, x, ldx, y, ldy, base,
+                                                                kNoAllocScratchBytes, st);
+  }
+  set_error("h2_matvec_noalloc: unknown precision");
+  return GCA_ERR_INVALID_ARG;
 }
 
 int product_status(const gca_h2* h, int* out) {
