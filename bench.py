@@ -20,6 +20,7 @@ meshes.  Under torchrun every rank runs the same workload on its own GPU
 (weak scaling, no collective on the data path).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --profile f32|f64|bf16|build [--steps K] [--warmup W]
 """
 
 import argparse
@@ -62,12 +63,55 @@ def product_bytes(st, prec, n, R):
             + sv * st["n_entries"] + 2 * sv * n * R)
 
 
+# floating-point operations of one evaluation of g and dg/dn at a (triangle
+# point, box point) pair of a Green matrix: difference 3, |d|^2 5, rsqrt 1,
+# 1/|d|^3 2, <n, d> 5, two weighted accumulations 4
+FLOPS_PER_GREEN_EVAL = 20
+
+
+def green_aca_flops(tree, rank, k):
+    """FP64 work of the Green-matrix + ACA phase: 7 k rows evaluations per
+    cluster (rows = |tau-hat| at leaves, r_1 + r_2 above), the rank-one
+    updates of the rows x 2k residual (2 rows 2k flops per pivot) and the
+    triangular solve for V-hat (rows r^2)."""
+    c0, c1 = tree["child0"], tree["child1"]
+    total = 0
+    for c in range(1, len(c0)):
+        rows = int(tree["end"][c] - tree["begin"][c]) if c0[c] < 0 else int(rank[c0[c]] + rank[c1[c]])
+        r = int(rank[c])
+        total += FLOPS_PER_GREEN_EVAL * 7 * k * rows + 2 * rows * 2 * k * r + rows * r * r
+    return int(total)
+
+
 def build_evals(st, q):
     regular = 49 * (st["s_entries"] + st["n_singular"][0])
     singular = q ** 3 * (2 * st["n_singular"][1] + 5 * st["n_singular"][2]
                          + 6 * st["n_singular"][3])
     return {"couple_entries": 49 * st["s_entries"], "near_entries": 49 * st["n_singular"][0],
             "singular": singular, "total": regular + singular}
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the kernel on the 20480-triangle sphere alone, with the
+# sha256 of the kernel's source file at capture time: reported only while the
+# source is unchanged, scaled to the timed launch by its algorithmic bytes.
+TRAFFIC = {
+    "couple_entries": ("paper_1810_08429_b300/csrc/build.cu",
+                       "0983f442ed7bba41027ccffeeba8a24cc3c5e3d04b5cba7362b5bbdc22b460a5", 541.50e6),
+    "mv_persistent.f32": ("paper_1810_08429_b300/csrc/matvec.cu",
+                          "a7c1ece76f407339dcc83a0707c261eae809045b4cc2c4ef0ba0e95166f1c8bd", 485.92e6),
+}
+
+
+def captured_traffic(name):
+    import hashlib
+    if name not in TRAFFIC:
+        return None
+    path, sha, byt = TRAFFIC[name]
+    with open(os.path.join(ROOT, path), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != sha:
+            return None
+    return byt
 
 
 class ClockSampler:
@@ -196,6 +240,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Small case for kernel captures: the 20480-triangle sphere alone, built
+    once (or `steps` times for --profile build), then `steps` products in one
+    precision with 16 right-hand sides.  Prints one line; not a bench value."""
+    import torch
+
+    import paper_1810_08429_b300 as gca
+    v, t = synth.mesh_for_config(MESHES[0])
+    tree = gca.tree_build(v, t, PARAMS["leaf_size"])
+    prm = gca.Params(**PARAMS)
+    h = gca.build(v, t, tree, prm)
+    if args.profile == "build":
+        for _ in range(args.steps):
+            h.free()
+            h = gca.build(v, t, tree, prm)
+    else:
+        dt = torch.float64 if args.profile == "f64" else torch.float32
+        x = torch.from_numpy(synth.normal_rhs(len(t), NRHS, seed=0)).to("cuda", dt)
+        y = torch.empty((NRHS, len(t)), dtype=dt, device="cuda").t()
+        for _ in range(args.warmup + args.steps):
+            h.matvec(x, args.profile, out=y)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "n": len(t), "status": h.status()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -203,9 +272,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["f64", "f32", "bf16", "build"], default=None,
+                    help="run the small single-mesh case used for kernel captures")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile:
+        run_profile(args)
         return
 
     import torch
@@ -261,6 +335,7 @@ def main():
     for _ in range(args.warmup):
         hs = step(False)
     stats = [h.stats() for h in hs]
+    aca_flops = [green_aca_flops(tr, h.export()["rank"], s["k"]) for tr, h, s in zip(trees, hs, stats)]
     fp64_peak, fp32_peak = gca.peak_probe()
     torch.cuda.synchronize()
 
@@ -321,17 +396,24 @@ def main():
             per = {"mv_persistent": lambda s: product_bytes(s, prec, n, NRHS)}[stage]
             byt = K * sum(per(s) for s in stats)
             ach = byt / (ms * 1e-3) / 1e9
+            tr = captured_traffic(name)
+            if tr is not None:  # captured on mesh 0 alone; the launch covers every mesh
+                tr = tr * sum(per(s) for s in stats) / per(stats[0])
             return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                    "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                    "unit": "GB/s", "frac": ach / hbm_peak, "traffic": tr,
+                    "traffic_unit": "bytes per launch",
                     "launches_per_step": launches / K, "peak_kind": peak_kind}
         if name in evals[0]:
             flops = K * FLOPS_PER_EVAL * sum(e[name] for e in evals)
             ach = flops / (ms * 1e-3) / 1e12
+        elif name == "green_aca":
+            ach = K * sum(aca_flops) / (ms * 1e-3) / 1e12
         else:
             ach = None
         pk = fp64_peak / 1e12
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": pk,
-                "unit": "TFLOP/s (fp64)", "frac": (ach / pk) if ach else None, "traffic": None,
+                "unit": "TFLOP/s (fp64)", "frac": (ach / pk) if ach else None,
+                "traffic": captured_traffic(name), "traffic_unit": "bytes per launch (mesh 0)",
                 "launches_per_step": launches / K,
                 "peak_kind": "measured by gca_peak_probe (fp64 FMA chains)"}
 
