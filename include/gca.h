@@ -98,7 +98,12 @@ typedef struct {
  *                touching pairs (Sect. 8), 1 <= q <= GCA_MAX_SAUTER_Q.
  *   omega_margin omega = box(tau) widened by omega_margin * diam(tau) on
  *                each side; a value < 0 selects 1 / (4 eta).
- *   flags        reserved, must be 0. */
+ *   flags        what the handle keeps after the build, a bit set of
+ *                GCA_DROP_* (0 keeps everything).  Dropping the copies a
+ *                caller never uses cuts the handle's device memory (for
+ *                many meshes in one batch); a product in a dropped
+ *                precision, or an export of dropped coefficients, then
+ *                fails with GCA_ERR_UNSUPPORTED. */
 typedef struct {
   int32_t leaf_size;
   double eta;
@@ -109,6 +114,16 @@ typedef struct {
   double omega_margin;
   uint32_t flags;
 } gca_params;
+
+enum {
+  GCA_DROP_F64 = 1,    /* no float64 panels: GCA_F64 products rejected      */
+  GCA_DROP_F32 = 2,    /* no float32 V, E, S panels: GCA_F32 products
+                          rejected (the float32 near field stays while
+                          GCA_BF16 products are kept)                      */
+  GCA_DROP_BF16 = 4,   /* no bfloat16 panels: GCA_BF16 products rejected    */
+  GCA_DROP_EXPORT = 8  /* free the row-major float64 V, E, S, N after the
+                          build: gca_h2_export of them is rejected          */
+};
 
 enum {
   GCA_MAX_LEAF = 128,

@@ -23,6 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgca.so")
 
 F64, F32, BF16 = 0, 1, 2
+DROP_F64, DROP_F32, DROP_BF16, DROP_EXPORT = 1, 2, 4, 8  # gca_params.flags
 _PREC = {"f64": F64, "f32": F32, "bf16": BF16, F64: F64, F32: F32, BF16: BF16}
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -394,3 +395,46 @@ def build_batch(meshes, trees, params, stream=None):
     _check(lib.gca_build_batch(k, marr, tarr, ctypes.byref(p), _stream_ptr(stream), ctypes.byref(b)),
            "gca_build_batch")
     return Batch(b.value)
+
+
+_AUTOGRAD = None
+
+
+def _autograd_class():
+    global _AUTOGRAD
+    if _AUTOGRAD is None:
+        import torch
+
+        class H2Matvec(torch.autograd.Function):
+            """y = G_H2 u as a differentiable torch operation.
+
+            ``H2Matvec.apply(h, u, prec)`` runs ``h2_matvec``; the backward
+            is the transposed H^2 product, dL/du = G_H2^T dL/dy
+            (``h2_matvec_transpose``), so gradients of losses such as
+            ||P G_H2 u - f||^2 cost one more product.  u is a CUDA tensor of
+            shape (n,) or (n, R): float64 for prec "f64", float32 otherwise.
+            """
+
+            @staticmethod
+            def forward(ctx, h, u, prec="f32"):
+                ctx.h = h
+                ctx.prec = prec
+                return h.matvec(u, prec)
+
+            @staticmethod
+            def backward(ctx, gy):
+                return None, ctx.h.matvec(gy, ctx.prec, transpose=True), None
+
+        _AUTOGRAD = H2Matvec
+    return _AUTOGRAD
+
+
+def __getattr__(name):
+    if name == "H2Matvec":
+        return _autograd_class()
+    raise AttributeError(name)
+
+
+def h2_matvec_autograd(h, u, prec="f32"):
+    """Differentiable y = G_H2 u (backward: the transposed product)."""
+    return _autograd_class().apply(h, u, prec)

@@ -100,6 +100,10 @@ int gca_h2_export(const gca_h2* h, gca_host_dump* o) {
       o->near[2 * b] = h->near_t[b];
       o->near[2 * b + 1] = h->near_s[b];
     }
+  if ((h->params.flags & GCA_DROP_EXPORT) && (o->V || o->E || o->S || o->N)) {
+    gca::set_error("gca_h2_export: the handle was built with GCA_DROP_EXPORT");
+    return GCA_ERR_UNSUPPORTED;
+  }
   struct Item { double* dst; const gca::DevMem* src; int64_t n; };
   const Item items[4] = {{o->V, &h->V64, h->v_entries}, {o->E, &h->E64, h->e_entries},
                          {o->S, &h->S64, h->s_entries}, {o->N, &h->N64, h->n_entries}};

@@ -389,12 +389,12 @@ __global__ void k_to_panel(const PanelJob* __restrict__ jobs, const double* __re
     return j.trans ? src[j.src + (int64_t)kk * j.m + a] : src[j.src + (int64_t)a * j.k + kk];
   };
   for (int64_t d = threadIdx.x; d < total; d += blockDim.x) {
-    {
+    if (d64) {
       const int64_t pw = (int64_t)j.m * 2;
       const int p = (int)(d / pw), rem = (int)(d % pw);
       d64[j.dst + d] = at(rem / 2, p * 2 + rem % 2);
     }
-    {
+    if (d32) {
       const int64_t pw = (int64_t)j.m * 4;
       const int p = (int)(d / pw), rem = (int)(d % pw);
       d32[j.dst + d] = (float)at(rem / 4, p * 4 + rem % 4);
@@ -454,19 +454,24 @@ int make_panels(gca_h2* h, cudaStream_t st) {
   const DevMem* srcs[kPanelKinds] = {&h->V64, &h->V64, &h->E64, &h->E64,
                                      &h->S64, &h->S64, &h->N64, &h->N64};
   DevMem d_jobs;
+  const uint32_t fl = h->params.flags;
   for (int q = 0; q < kPanelKinds; ++q) {
     const bool near = q == kN || q == kNt;
-    GCA_TRY(h->P64[q].alloc(sizeof(double) * size[q]));
-    GCA_TRY(h->P32[q].alloc(sizeof(float) * size[q]));
-    if (!near) GCA_TRY(h->P16[q].alloc(sizeof(__nv_bfloat16) * size[q]));
+    const bool k64 = !(fl & GCA_DROP_F64);
+    // the float32 near field also serves the bfloat16 products
+    const bool k32 = !(fl & GCA_DROP_F32) || (near && !(fl & GCA_DROP_BF16));
+    const bool k16 = !near && !(fl & GCA_DROP_BF16);
+    if (k64) GCA_TRY(h->P64[q].alloc(sizeof(double) * size[q]));
+    if (k32) GCA_TRY(h->P32[q].alloc(sizeof(float) * size[q]));
+    if (k16) GCA_TRY(h->P16[q].alloc(sizeof(__nv_bfloat16) * size[q]));
     h->psize[q] = size[q];
-    if (jobs[q].empty()) continue;
+    if (jobs[q].empty() || !(k64 || k32 || k16)) continue;
     GCA_TRY(d_jobs.reserve(sizeof(PanelJob) * jobs[q].size()));
     GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, jobs[q].data(), sizeof(PanelJob) * jobs[q].size(),
                                  cudaMemcpyHostToDevice, st));
     k_to_panel<<<(unsigned)jobs[q].size(), 256, 0, st>>>(
-        d_jobs.as<PanelJob>(), srcs[q]->as<double>(), h->P64[q].as<double>(), h->P32[q].as<float>(),
-        near ? nullptr : h->P16[q].as<__nv_bfloat16>());
+        d_jobs.as<PanelJob>(), srcs[q]->as<double>(), k64 ? h->P64[q].as<double>() : nullptr,
+        k32 ? h->P32[q].as<float>() : nullptr, k16 ? h->P16[q].as<__nv_bfloat16>() : nullptr);
     GCA_TRY_CUDA(cudaGetLastError());
     GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_jobs is reused
   }
@@ -720,7 +725,8 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY(validate_tree(mesh, tree, GCA_MAX_LEAF));
   if (!prm || !(prm->eta > 0.0) || prm->box_gauss_m < 1 || prm->box_gauss_m > GCA_MAX_BOX_M ||
       !(prm->aca_tol >= 0.0) || prm->tri_rule != 7 || prm->sauter_q < 1 ||
-      prm->sauter_q > GCA_MAX_SAUTER_Q || prm->flags != 0) {
+      prm->sauter_q > GCA_MAX_SAUTER_Q ||
+      (prm->flags & ~(uint32_t)(GCA_DROP_F64 | GCA_DROP_F32 | GCA_DROP_BF16 | GCA_DROP_EXPORT)) != 0) {
     set_error("gca_build: invalid parameters");
     return GCA_ERR_INVALID_ARG;
   }
@@ -1073,6 +1079,12 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
 
   GCA_TRY(finish_plan(h.get(), st));
   GCA_TRY_CUDA(cudaStreamSynchronize(st));
+  if (prm->flags & GCA_DROP_EXPORT) {
+    h->V64.release();
+    h->E64.release();
+    h->S64.release();
+    h->N64.release();
+  }
   h->build_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = h.release();

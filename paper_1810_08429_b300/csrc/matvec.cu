@@ -874,13 +874,27 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
     const size_t smem = (size_t)kStages * kStageBytes + sizeof(TA) * (size_t)kXSlots * kChunk * RC +
                         kXSlots * sizeof(Meta) + (2 * kStages + 2 * kXSlots) * sizeof(uint64_t);
     auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
-    if (smem > 48 * 1024)
-      GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
+    // resident CTAs on the device, found once per device (later launches
+    // make no attribute or occupancy calls, so they can be graph captured)
+    static std::mutex mu;
+    static int64_t cap_by_dev[64] = {};
+    int dev = 0;
     GCA_TRY_CUDA(cudaGetDevice(&dev));
-    GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GCA_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    const int64_t cap = (int64_t)sms * std::max(per_sm, 1);
+    int64_t cap = 0;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      cap = dev >= 0 && dev < 64 ? cap_by_dev[dev] : 0;
+    }
+    if (cap == 0) {
+      if (smem > 48 * 1024)
+        GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int sms = 0, per_sm = 0;
+      GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      GCA_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+      cap = (int64_t)sms * std::max(per_sm, 1);
+      std::lock_guard<std::mutex> lk(mu);
+      if (dev >= 0 && dev < 64) cap_by_dev[dev] = cap;
+    }
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(work, cap));
     kern<<<grid, kThreads, smem, st>>>(L);
   }
@@ -902,15 +916,31 @@ int launch(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, con
   return launch_rc<T, TN, TA, TV, 1>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
 }
 
+// the handle kept the panels of this precision (gca_params.flags)
+bool has_precision(const gca_h2* h, gca_prec prec) {
+  const uint32_t fl = h->params.flags;
+  switch (prec) {
+    case GCA_F64: return !(fl & GCA_DROP_F64);
+    case GCA_F32: return !(fl & GCA_DROP_F32);
+    case GCA_BF16: return !(fl & GCA_DROP_BF16);
+  }
+  return false;
+}
+
 int launch_any(const gca_h2* const* hs, int count, gca_prec prec, bool trans, const int32_t* nrhs,
                const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy, DevMem& ws,
                std::vector<unsigned char>& wc, int* status, cudaStream_t st) {
-  for (int i = 0; i < count; ++i)
+  for (int i = 0; i < count; ++i) {
     if (!hs[i] || !x[i] || !y[i] || nrhs[i] < 1 || nrhs[i] > 4096 || ldx[i] < hs[i]->n ||
         ldy[i] < hs[i]->n) {
       set_error("h2_matvec: invalid arguments (handle " + std::to_string(i) + ")");
       return GCA_ERR_INVALID_ARG;
     }
+    if (!has_precision(hs[i], prec)) {
+      set_error("h2_matvec: handle " + std::to_string(i) + " was built without this precision");
+      return GCA_ERR_UNSUPPORTED;
+    }
+  }
   const int dir = trans ? 1 : 0;
   switch (prec) {
     case GCA_F64:
@@ -1092,6 +1122,10 @@ int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, 
   if (!h || !x || !y || nrhs < 1 || nrhs > 4096 || ldx < h->n || ldy < h->n) {
     set_error("h2_matvec_noalloc: invalid arguments");
     return GCA_ERR_INVALID_ARG;
+  }
+  if (!has_precision(h, prec)) {
+    set_error("h2_matvec_noalloc: the handle was built without this precision");
+    return GCA_ERR_UNSUPPORTED;
   }
   unsigned char* base = nullptr;
   GCA_TRY(noalloc_scratch(&base));
