@@ -378,6 +378,28 @@ struct PanelJob {
   int pad;
 };
 
+// Tiled panel layout of one M x K block (K_pad = pad8(K)): row slices of
+// kTileRows rows, each slice split into column chunks of kTileCols columns,
+// every (slice, chunk) tile stored contiguously as column panels of P
+// entries per row.  Tile (a0, k0) with ms = min(kTileRows, M - a0) rows
+// starts at element a0 * K_pad + ms * k0; inside it entry (a, kk) sits at
+// (kk / P) * ms * P + a * P + kk % P.  A product segment is one tile, so it
+// moves with one contiguous copy.
+constexpr int kTileRows = 64, kTileCols = 64;
+
+__host__ __device__ inline int64_t tile_index(int m, int kp, int P, int64_t d, int* row, int* col) {
+  const int64_t slice_elems = (int64_t)kTileRows * kp;
+  const int i = (int)(d / slice_elems);
+  const int64_t e = d - i * slice_elems;
+  const int ms = min(kTileRows, m - i * kTileRows);
+  const int j = (int)(e / ((int64_t)ms * kTileCols));
+  const int64_t f = e - (int64_t)j * ms * kTileCols;
+  const int p = (int)(f / (ms * P)), g = (int)(f % (ms * P));
+  *row = i * kTileRows + g / P;
+  *col = j * kTileCols + p * P + g % P;
+  return d;
+}
+
 __global__ void k_to_panel(const PanelJob* __restrict__ jobs, const double* __restrict__ src,
                            double* __restrict__ d64, float* __restrict__ d32,
                            __nv_bfloat16* __restrict__ d16) {
@@ -389,20 +411,18 @@ __global__ void k_to_panel(const PanelJob* __restrict__ jobs, const double* __re
     return j.trans ? src[j.src + (int64_t)kk * j.m + a] : src[j.src + (int64_t)a * j.k + kk];
   };
   for (int64_t d = threadIdx.x; d < total; d += blockDim.x) {
+    int a, kk;
     if (d64) {
-      const int64_t pw = (int64_t)j.m * 2;
-      const int p = (int)(d / pw), rem = (int)(d % pw);
-      d64[j.dst + d] = at(rem / 2, p * 2 + rem % 2);
+      tile_index(j.m, kp, 2, d, &a, &kk);
+      d64[j.dst + d] = at(a, kk);
     }
     if (d32) {
-      const int64_t pw = (int64_t)j.m * 4;
-      const int p = (int)(d / pw), rem = (int)(d % pw);
-      d32[j.dst + d] = (float)at(rem / 4, p * 4 + rem % 4);
+      tile_index(j.m, kp, 4, d, &a, &kk);
+      d32[j.dst + d] = (float)at(a, kk);
     }
     if (d16) {
-      const int64_t pw = (int64_t)j.m * 8;
-      const int p = (int)(d / pw), rem = (int)(d % pw);
-      d16[j.dst + d] = __double2bfloat16(at(rem / 8, p * 8 + rem % 8));
+      tile_index(j.m, kp, 8, d, &a, &kk);
+      d16[j.dst + d] = __double2bfloat16(at(a, kk));
     }
   }
 }

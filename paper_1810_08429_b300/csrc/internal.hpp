@@ -169,7 +169,8 @@ struct gca_h2 {
   int64_t psize[gca::kPanelKinds] = {0};
   // persistent product: work items in dependency order, per direction
   gca::DevMem d_items[2], d_groups[2];
-  int64_t n_items[2] = {0, 0};
+  int64_t n_items[2] = {0, 0};  // chain groups per direction (the free groups follow them)
+  int64_t n_free[2] = {0, 0};   // free (near-field) groups per direction
   int max_leaf = 0;
 
   // device: product workspace (grown on demand): x-hat, y-hat, dependency

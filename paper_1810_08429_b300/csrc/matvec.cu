@@ -45,7 +45,6 @@ namespace gca {
 
 namespace {
 
-constexpr int kBatch = 1;            // groups claimed per atomic
 constexpr int kSpinLimit = 1 << 20;  // bounded wait: well under a second with the back-off below
 constexpr int kStatusTimeout = 1;
 
@@ -75,9 +74,12 @@ template <typename TV>
 struct SlotArgs {
   const void* A[kPanelKinds];  // panel arrays (near-field kinds hold the near storage type)
   const MvItem* items;
-  const int2* groups;          // [begin, end) segment ranges claimed as a unit
-  int64_t work_begin;          // first claim index of this slot
-  int64_t n_work;              // groups * nchunk
+  const int2* groups;          // chain list: [begin, end) segment ranges claimed as a unit
+  const int2* free_groups;     // free list (no dependencies)
+  int64_t work_begin;          // first chain claim index of this slot
+  int64_t n_work;              // chain groups * nchunk
+  int64_t free_begin;          // first free claim index of this slot
+  int64_t n_free;              // free groups * nchunk
   int nchunk;
   int R;
   int n;
@@ -97,8 +99,10 @@ struct SlotArgs {
 struct LaunchArgs {
   const void* slots;           // SlotArgs<TV>[nslots]
   int nslots;
-  int64_t total;               // claims over all slots
-  unsigned long long* next;    // work-claim counter
+  int64_t total;               // chain claims over all slots
+  int64_t total_free;          // free claims over all slots
+  unsigned long long* next;    // chain claim counter
+  unsigned long long* next_free;  // free claim counter
   int* status;
   int* abort_flag;             // raised by any timed-out wait; every wait gives up
 };
@@ -113,6 +117,16 @@ __device__ __forceinline__ int find_slot(const SlotArgs<TV>* sl, int nslots, int
   return lo;
 }
 
+template <typename TV>
+__device__ __forceinline__ int find_free_slot(const SlotArgs<TV>* sl, int nslots, int64_t w) {
+  int lo = 0, hi = nslots - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sl[mid].free_begin <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -121,43 +135,41 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 
 // ---------------------------------------------------------------- pipeline
 //
-// CTA = kConsumers consumer warps + 1 producer warp.  The producer claims
-// items (claim-ahead), waits for their input vector, and issues 1-D bulk
-// copies (TMA) of the input block and of the item's block panels into
-// mbarrier-guarded rings; the consumers compute continuously.  Item = a
-// slice of kItemRows rows x kChunk columns of one stored block; consumer
-// warp w owns rows [64 w, 64 w + 64) of it (see Tile).
-constexpr int kConsumers = 2;
-constexpr int kThreads = 32 * (kConsumers + 1);
-constexpr int kItemRows = 64 * kConsumers;  // 128: 64 rows per consumer warp
-constexpr int kChunk = 64;                                 // columns per item
+// Every warp of the persistent launch works on its own: it claims a group
+// (claim-ahead), streams the group's block panels into its private ring of
+// shared-memory stages with 1-D bulk copies (TMA) completing on per-stage
+// mbarriers, waits for the segment's input vector block (bounded spin on the
+// dependency counter), stages it, and accumulates in registers.  A segment =
+// kItemRows rows x kChunk columns of one stored block; the stages of the
+// group's segments form one stream, so the next segment's panels are in
+// flight while the current one is computed.  A warp stalled on a dependency
+// stalls nobody else.
+constexpr int kWarps = 4;                                   // independent warps per CTA
+constexpr int kThreads = 32 * kWarps;
+constexpr int kItemRows = 64;                               // rows per segment (one warp tile)
+constexpr int kChunk = 64;                                  // columns per segment
 constexpr int kStagePanels = 4;
-constexpr int kStageBytes = kStagePanels * kItemRows * 16;  // 8 KB
-constexpr int kStages = 4;
-constexpr int kXSlots = 4;
+constexpr int kStageBytes = kStagePanels * kItemRows * 16;  // 4 KB: one contiguous copy
+constexpr int kStages = 3;
 constexpr int kMbarLimit = 1 << 20;
+constexpr int kMaxGroupSegs = 8;  // segments of a group
 
-struct Meta {
-  int64_t o_row;  // output row of item row 0
-  int rows;       // valid rows of the item
-  int np;         // panels of the chunk
-  int out;        // output array, -1: end of work
-  int sig_idx;
-  int c0;         // first right-hand side of this pass
-  int near;       // near-field panels (storage type TN)
-  int flush;      // last segment of the group
-  int slot;       // mesh of the launch
-};
+// shared memory of one warp: ring, input block, mbarriers (kStages + 1)
+template <typename TA, int RC>
+__host__ __device__ constexpr size_t warp_smem() {
+  return ((size_t)kStages * kStageBytes + sizeof(TA) * (size_t)kChunk * RC + (kStages + 1) * 8 + 127) /
+         128 * 128;
+}
+template <typename TA, int RC>
+__host__ __device__ constexpr size_t cta_smem() {
+  return kWarps * warp_smem<TA, RC>();
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 __device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b))
-               : "memory");
 }
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, unsigned tx) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
@@ -186,7 +198,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile
   return false;
 }
 // Bounded wait used only while draining copies before exit (ignores the
-// abort flag, so that no copy is still landing when the CTA retires).
+// abort flag, so that no copy is still landing when the warp retires).
 __device__ __forceinline__ void mbar_drain(uint64_t* b, unsigned parity) {
   for (int i = 0; i < kMbarLimit; ++i)
     if (mbar_try_wait(b, parity)) return;
@@ -198,8 +210,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// orders this thread's generic-proxy shared-memory accesses before later
+// bulk copies (async proxy) into the same buffers
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// orders global-memory writes seen through an acquire before later bulk
+// copies (async proxy) that read them
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -263,11 +282,11 @@ __global__ void k_scatter(const SlotArgs<TV>* __restrict__ slots) {
   }
 }
 
-// Consumer register tile.  A warp covers 64 rows x RC right-hand sides:
-// CPL = min(RC, 8) columns per lane, NCG = RC / CPL column groups,
-// RG = 32 / NCG row groups, RPL = 64 / RG rows per lane; lane (rg, cg) owns
-// rows rg + RG * i (i < RPL) and columns cg * CPL + [0, CPL).  Rows of one
-// load instruction are consecutive (conflict-free 16-byte shared loads).
+// Register tile of a warp: 64 rows x RC right-hand sides.  CPL = min(RC, 8)
+// columns per lane, NCG = RC / CPL column groups, RG = 32 / NCG row groups,
+// RPL = 64 / RG rows per lane; lane (rg, cg) owns rows rg + RG * i (i < RPL)
+// and columns cg * CPL + [0, CPL).  Rows of one load instruction are
+// consecutive (conflict-free 16-byte shared loads).
 template <int RC>
 struct Tile {
   static constexpr int CPL = RC < 8 ? RC : 8;
@@ -276,21 +295,29 @@ struct Tile {
   static constexpr int RPL = 64 / RG;
 };
 
-// One ring stage: np_stage panels of P columns of the lane's rows.
+// One ring stage: npst panels (P columns each, `pst` bytes apart) of the
+// lane's rows.
 template <typename T, typename TA, int RC>
-__device__ __forceinline__ void consume_stage(const unsigned char* slot, int np_stage, int p0,
-                                              const TA* __restrict__ Xs, int rowbase, int cg,
+__device__ __forceinline__ void consume_stage(const unsigned char* stage, int pst, int npst, int p0,
+                                              const TA* __restrict__ Xs, int rg, int cg,
                                               TA (&acc)[Tile<RC>::RPL][Tile<RC>::CPL]) {
   using Tl = Tile<RC>;
   constexpr int P = Panel<T>::P;
+  // the stage's sum (at most kStagePanels * P terms) is formed on its own
+  // and then added: two-level summation keeps the rounding error of the
+  // long sums over a group's segments near that of a few short chains
+  TA part[Tl::RPL][Tl::CPL];
+#pragma unroll
+  for (int i = 0; i < Tl::RPL; ++i)
+#pragma unroll
+    for (int c = 0; c < Tl::CPL; ++c) part[i][c] = (TA)0;
 #pragma unroll
   for (int g = 0; g < kStagePanels; ++g) {
-    if (g >= np_stage) break;
+    if (g >= npst) break;
     TA v[Tl::RPL][P];
 #pragma unroll
     for (int i = 0; i < Tl::RPL; ++i)
-      unpack(*reinterpret_cast<const uint4*>(slot + g * (kItemRows * 16) + (rowbase + Tl::RG * i) * 16),
-             v[i]);
+      unpack(*reinterpret_cast<const uint4*>(stage + g * pst + (rg + Tl::RG * i) * 16), v[i]);
 #pragma unroll
     for (int kk = 0; kk < P; ++kk) {
       const TA* xr = Xs + ((p0 + g) * P + kk) * RC + cg * Tl::CPL;
@@ -300,268 +327,261 @@ __device__ __forceinline__ void consume_stage(const unsigned char* slot, int np_
 #pragma unroll
       for (int i = 0; i < Tl::RPL; ++i)
 #pragma unroll
-        for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = fma(v[i][kk], x[c], acc[i][c]);
+        for (int c = 0; c < Tl::CPL; ++c) part[i][c] = fma(v[i][kk], x[c], part[i][c]);
     }
   }
+#pragma unroll
+  for (int i = 0; i < Tl::RPL; ++i)
+#pragma unroll
+    for (int c = 0; c < Tl::CPL; ++c) acc[i][c] += part[i][c];
 }
 
-template <typename T, typename TN, typename TA, typename TV, int RC>
-__global__ void __launch_bounds__(kThreads) k_h2_persistent(LaunchArgs L) {
-  const SlotArgs<TV>* slots = static_cast<const SlotArgs<TV>*>(L.slots);
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned char* ring = smem_raw;
-  TA* xs_base = reinterpret_cast<TA*>(smem_raw + kStages * kStageBytes);
-  constexpr int kXsElems = kChunk * RC;
-  Meta* meta = reinterpret_cast<Meta*>(xs_base + kXSlots * kXsElems);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(meta + kXSlots);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + kStages;
-  uint64_t* xfull = bars + 2 * kStages;
-  uint64_t* xempty = bars + 2 * kStages + kXSlots;
-  volatile int* abort_flag = L.abort_flag;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    for (int i = 0; i < kStages; ++i) {
-      mbar_init(full + i, 1);
-      mbar_init(empty + i, kConsumers);
-    }
-    for (int i = 0; i < kXSlots; ++i) {
-      mbar_init(xfull + i, 1);
-      mbar_init(xempty + i, kConsumers);
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
+// A segment (one tile of a stored block) as the issuing side sees it.
+struct SegSrc {
+  const unsigned char* A;  // the tile
+  int rows;                // rows of the tile: panels are rows * 16 bytes apart
+  int np;                  // panels of the tile
+};
 
-  if (warp == kConsumers) {
-    // ------------------------------------------------------------ producer
-    const int64_t total = L.total;
-    int seq = 0;
-    int64_t pstage = 0;
-    bool dead = false;
-    unsigned long long nxt = 0;
-    if (lane == 0) nxt = atomicAdd(L.next, (unsigned long long)kBatch);
-    nxt = __shfl_sync(0xffffffffu, nxt, 0);
-    int xuses[kXSlots] = {0, 0};
-    while (!dead && (int64_t)nxt < total) {
-      const unsigned long long base = nxt;
-      unsigned long long ahead = 0;
-      if (lane == 0) ahead = atomicAdd(L.next, (unsigned long long)kBatch);  // claim ahead
-      const int64_t stop = min((int64_t)base + kBatch, total);
-      for (int64_t wseg = 0, w = (int64_t)base; w < stop && !dead;) {
-        const int slot = find_slot(slots, L.nslots, w);
-        const SlotArgs<TV>& sa = slots[slot];
-        const int64_t lw = w - sa.work_begin;
-        const int2 grp = sa.groups[lw / sa.nchunk];
-        const int64_t segi = grp.x + wseg;
-        const MvItem it = sa.items[segi];
-        const int c0 = (int)(lw % sa.nchunk) * RC;
-        if (segi + 1 >= grp.y) {
-          wseg = 0;
-          ++w;
-        } else {
-          ++wseg;
-        }
-        const int ain = it.kind & 15, xin = (it.kind >> 4) & 15, out = (it.kind >> 8) & 15;
-        const bool is_near = ain == kN || ain == kNt;
-        const int P = is_near ? Panel<TN>::P : Panel<T>::P;
-        const int esz = is_near ? (int)sizeof(TN) : (int)sizeof(T);
-        const int kp = pad8(it.k);
-        const int np = kp / P;
-        const int rows = min(kItemRows, it.m - it.a0);
-        const int xs = seq % kXSlots;
-        TA* Xs = xs_base + xs * kXsElems;
-        if (seq >= kXSlots && !mbar_wait(xempty + xs, ((seq / kXSlots) - 1) & 1, abort_flag, L.status)) {
-          dead = true;
-          break;
-        }
-        if (*abort_flag) {
-          dead = true;
-          break;
-        }
-        // the item's block panels do not depend on anything: issue up to a
-        // ring's worth now, the rest after the input block is staged (the
-        // consumers can only drain this item's stages once its input is in)
-        const unsigned char* Ab = static_cast<const unsigned char*>(sa.A[ain]) + it.a_off * esz;
-        const int pbase = it.k0 / P;
-        auto issue_stage = [&](int s0) -> bool {
-          const int slot = (int)(pstage % kStages);
-          if (pstage >= kStages &&
-              !mbar_wait(empty + slot, (unsigned)(((pstage / kStages) - 1) & 1), abort_flag, L.status))
-            return false;
-          if (lane == 0) {
-            const int npst = min(kStagePanels, np - s0);
-            mbar_arrive_tx(full + slot, (unsigned)(npst * rows * 16));
-            for (int q = 0; q < npst; ++q) {
-              const int64_t pan = pbase + s0 + q;
-              bulk_g2s(ring + slot * kStageBytes + q * (kItemRows * 16), Ab + (pan * it.m + it.a0) * 16,
-                       (unsigned)(rows * 16), full + slot);
-            }
-          }
-          __syncwarp();
-          ++pstage;
-          return true;
-        };
-        int s0 = 0;
-        for (int n = 0; s0 < np && n < kStages; s0 += kStagePanels, ++n)
-          if (!issue_stage(s0)) {
-            dead = true;
-            break;
-          }
-        if (dead) break;
-        // input vector block complete?
-        if (it.wait_idx >= 0) {
-          const int need = it.wait_cnt * sa.nchunk * kConsumers;  // each consumer warp signals
-          int spins = 0;
-          while (ld_acquire(sa.counters + it.wait_idx) < need) {
-            if (++spins > kSpinLimit) {
-              if (lane == 0) atomicOr(L.status, kStatusTimeout);
-              *abort_flag = 1;
-              break;
-            }
-            if (*abort_flag) break;
-            __nanosleep(32);
-          }
-        }
-        if (lane == 0) {
-          Meta mt;
-          mt.o_row = it.o_row;
-          mt.rows = rows;
-          mt.np = np;
-          mt.out = out;
-          mt.sig_idx = it.sig_idx;
-          mt.c0 = c0;
-          mt.near = is_near ? 1 : 0;
-          mt.flush = it.flush;
-          mt.slot = slot;
-          meta[xs] = mt;
-        }
-        // stage the input rows k0 .. k0+kp (zero beyond the block's columns)
-        const TV* X = (xin == kInXh ? sa.xh : (xin == kInYh ? sa.yh : sa.xp)) + it.x_row * sa.R + c0;
-        const bool bulk = RC == sa.R && (RC * sizeof(TV)) % 16 == 0 && sizeof(TA) == sizeof(TV);
-        if (bulk) {
-          for (int i = it.k * RC + lane; i < kp * RC; i += 32) Xs[i] = (TA)0;
-          __syncwarp();
-          if (lane == 0) {
-            const unsigned bytes = (unsigned)(it.k * RC * sizeof(TV));
-            fence_proxy_async();
-            if (bytes > 0) {
-              mbar_arrive_tx(xfull + xs, bytes);
-              bulk_g2s(Xs, X, bytes, xfull + xs);
-            } else {
-              mbar_arrive(xfull + xs);
-            }
-          }
-        } else {
-          for (int i = lane; i < kp * RC; i += 32) {
-            const int r = i / RC, c = i % RC;
-            Xs[i] = (r < it.k && c0 + c < sa.R) ? (TA)__ldcg(X + (int64_t)r * sa.R + c) : (TA)0;
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(xfull + xs);
-        }
-        for (; s0 < np; s0 += kStagePanels)
-          if (!issue_stage(s0)) {
-            dead = true;
-            break;
-          }
-        ++xuses[xs];
-        ++seq;
-      }
-      nxt = __shfl_sync(0xffffffffu, ahead, 0);
-      dead = __any_sync(0xffffffffu, dead);
-    }
-    // end of work for the consumers
-    {
-      const int xs = seq % kXSlots;
-      bool ok = true;
-      if (seq >= kXSlots) ok = mbar_wait(xempty + xs, ((seq / kXSlots) - 1) & 1, abort_flag, L.status);
-      if (lane == 0) {
-        Meta mt{};
-        mt.out = -1;
-        meta[xs] = mt;
-        mbar_arrive(xfull + xs);  // release: consumers see the end marker
-      }
-      ++xuses[xs];
-      (void)ok;
-    }
-    // drain: every issued stage's copy has landed before the CTA can exit
+template <typename T, typename TN, typename TV>
+__device__ __forceinline__ SegSrc seg_src(const SlotArgs<TV>& sa, const MvItem& it) {
+  const int ain = it.kind & 15;
+  const bool is_near = ain == kN || ain == kNt;
+  const int P = is_near ? Panel<TN>::P : Panel<T>::P;
+  const int esz = is_near ? (int)sizeof(TN) : (int)sizeof(T);
+  SegSrc s;
+  s.A = static_cast<const unsigned char*>(sa.A[ain]) + it.a_off * esz;
+  s.rows = min(kItemRows, it.m - it.a0);
+  s.np = pad8(it.k) / P;
+  return s;
+}
+
+// Per-warp state of the stage ring (shared memory of the warp).
+template <typename TA, int RC>
+struct WarpRing {
+  unsigned char* ring;
+  TA* Xs;
+  uint64_t* full;
+  uint64_t* xbar;
+  uint32_t fill, use, xuse;  // stages issued / consumed, input blocks copied
+};
+
+// Every segment of group [grp.x, grp.y) has its input block complete.
+template <typename TV>
+__device__ __forceinline__ bool group_ready(const SlotArgs<TV>& sa, int2 grp, int lane) {
+  bool ok = true;
+  for (int s = grp.x + lane; s < grp.y; s += 32) {
+    const MvItem& it = sa.items[s];
+    if (it.wait_idx >= 0 && ld_acquire(sa.counters + it.wait_idx) < it.wait_cnt * sa.nchunk) ok = false;
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+// One claimed unit: the segments of one group for right-hand sides
+// [c0, c0 + RC).  Returns false when a wait timed out or the launch aborted.
+template <typename T, typename TN, typename TA, typename TV, int RC>
+__device__ bool run_group(const SlotArgs<TV>& sa, int2 grp, int c0, WarpRing<TA, RC>& w,
+                          TA (&acc)[Tile<RC>::RPL][Tile<RC>::CPL], const LaunchArgs& L, int lane) {
+  using Tl = Tile<RC>;
+  volatile int* abort_flag = L.abort_flag;
+  const int rg = lane % Tl::RG, cg = lane / Tl::RG;
+  // issuing cursor: segment `is`, its stage `ist`; stages of consecutive
+  // segments form one stream through the ring
+  int is = grp.x, ist = 0;
+  SegSrc src = seg_src<T, TN, TV>(sa, sa.items[is]);
+  auto issue = [&]() {
+    if (is >= grp.y || w.fill - w.use >= (uint32_t)kStages) return;
+    const int s = (int)(w.fill % kStages);
     if (lane == 0) {
-      for (int slot = 0; slot < kStages; ++slot) {
-        const int64_t uses = pstage > slot ? (pstage - slot + kStages - 1) / kStages : 0;
-        if (uses > 0) mbar_drain(full + slot, (unsigned)((uses - 1) & 1));
-      }
-      for (int xsl = 0; xsl < kXSlots; ++xsl)
-        if (xuses[xsl] > 0) mbar_drain(xfull + xsl, (unsigned)((xuses[xsl] - 1) & 1));
+      const int p0 = ist * kStagePanels;
+      const int npst = min(kStagePanels, src.np - p0);
+      const unsigned bytes = (unsigned)(npst * src.rows * 16);  // contiguous panels of the tile
+      mbar_arrive_tx(w.full + s, bytes);
+      bulk_g2s(w.ring + s * kStageBytes, src.A + (int64_t)p0 * src.rows * 16, bytes, w.full + s);
     }
-  } else {
-    // ------------------------------------------------------------ consumers
-    using Tl = Tile<RC>;
-    int seq = 0;
-    int64_t cstage = 0;
-    const int rg = lane % Tl::RG, cg = lane / Tl::RG;
-    const int rowbase = warp * 64 + rg;  // item rows of this lane: rowbase + RG * i
-    TA acc[Tl::RPL][Tl::CPL];
+    ++w.fill;
+    if (++ist * kStagePanels >= src.np) {
+      ist = 0;
+      if (++is < grp.y) src = seg_src<T, TN, TV>(sa, sa.items[is]);
+    }
+  };
+  for (int q = 0; q < kStages; ++q) issue();
+
+  for (int us = grp.x; us < grp.y; ++us) {
+    const MvItem it = sa.items[us];
+    const int xin = (it.kind >> 4) & 15, out = (it.kind >> 8) & 15;
+    const int rows = min(kItemRows, it.m - it.a0);
+    const int ain = it.kind & 15;
+    const bool is_near = ain == kN || ain == kNt;
+    const int np = pad8(it.k) / (is_near ? Panel<TN>::P : Panel<T>::P);
+    const int kp = pad8(it.k);
+    // input vector block complete?
+    if (it.wait_idx >= 0) {
+      const int need = it.wait_cnt * sa.nchunk;
+      int timeout = 0;
+      if (lane == 0) {
+        int spins = 0;
+        while (ld_acquire(sa.counters + it.wait_idx) < need) {
+          if (++spins > kSpinLimit) {
+            atomicOr(L.status, kStatusTimeout);
+            *abort_flag = 1;
+            timeout = 1;
+            break;
+          }
+          if (*abort_flag) {
+            timeout = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      if (__shfl_sync(0xffffffffu, timeout, 0)) return false;
+    }
+    // stage the input rows k0 .. k0 + kp (zero beyond the block's columns);
+    // every lane is done reading the previous block (__syncwarp)
+    const TV* X = (xin == kInXh ? sa.xh : (xin == kInYh ? sa.yh : sa.xp)) + it.x_row * sa.R + c0;
+    const bool bulk = RC == sa.R && (RC * sizeof(TV)) % 16 == 0 && sizeof(TA) == sizeof(TV);
+    fence_proxy_async();
+    if (it.wait_idx >= 0) fence_proxy_async_global();  // the block was written by other warps
+    __syncwarp();
+    if (bulk) {
+      for (int i = it.k * RC + lane; i < kp * RC; i += 32) w.Xs[i] = (TA)0;
+      if (lane == 0) {
+        const unsigned bytes = (unsigned)(it.k * RC * sizeof(TV));
+        mbar_arrive_tx(w.xbar, bytes);
+        bulk_g2s(w.Xs, X, bytes, w.xbar);
+      }
+      ++w.xuse;
+      if (!mbar_wait(w.xbar, (w.xuse - 1) & 1, abort_flag, L.status)) return false;
+    } else {
+      for (int i = lane; i < kp * RC; i += 32) {
+        const int r = i / RC, c = i % RC;
+        w.Xs[i] = (r < it.k && c0 + c < sa.R) ? (TA)__ldcg(X + (int64_t)r * sa.R + c) : (TA)0;
+      }
+    }
+    __syncwarp();
+    for (int p0 = 0; p0 < np; p0 += kStagePanels) {
+      const int s = (int)(w.use % kStages);
+      if (!mbar_wait(w.full + s, (w.use / kStages) & 1, abort_flag, L.status)) return false;
+      const unsigned char* stg = w.ring + s * kStageBytes;
+      const int npst = min(kStagePanels, np - p0);
+      if (is_near)
+        consume_stage<TN, TA, RC>(stg, rows * 16, npst, p0, w.Xs, rg, cg, acc);
+      else
+        consume_stage<T, TA, RC>(stg, rows * 16, npst, p0, w.Xs, rg, cg, acc);
+      ++w.use;
+      fence_proxy_async();
+      __syncwarp();
+      issue();  // refill the freed stage (possibly with the next segment's panels)
+    }
+    if (!it.flush) continue;
+    TV* obase = out == kOutXh ? sa.xh : (out == kOutYh ? sa.yh : sa.yp);
+    const int R = sa.R;
+    const int col0 = c0 + cg * Tl::CPL;
+    const int vc = min(Tl::CPL, R - col0);
+    const bool aligned = (R % 4) == 0 && (col0 % 4) == 0;
+#pragma unroll
+    for (int i = 0; i < Tl::RPL; ++i) {
+      const int r = rg + Tl::RG * i;
+      if (r < rows && vc > 0) add_row<Tl::CPL>(obase + (it.o_row + r) * R + col0, acc[i], vc, aligned);
+    }
 #pragma unroll
     for (int i = 0; i < Tl::RPL; ++i)
 #pragma unroll
       for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
-    for (;;) {
-      const int xs = seq % kXSlots;
-      if (!mbar_wait(xfull + xs, (unsigned)((seq / kXSlots) & 1), abort_flag, L.status)) break;
-      const Meta mt = meta[xs];
-      if (mt.out < 0) break;
-      const TA* Xs = xs_base + xs * kXsElems;
-      bool dead = false;
-      for (int s0 = 0; s0 < mt.np; s0 += kStagePanels, ++cstage) {
-        const int slot = (int)(cstage % kStages);
-        if (!mbar_wait(full + slot, (unsigned)((cstage / kStages) & 1), abort_flag, L.status)) {
-          dead = true;
-          break;
-        }
-        const unsigned char* sl = ring + slot * kStageBytes;
-        const int npst = min(kStagePanels, mt.np - s0);
-        if (mt.near)
-          consume_stage<TN, TA, RC>(sl, npst, s0, Xs, rowbase, cg, acc);
-        else
-          consume_stage<T, TA, RC>(sl, npst, s0, Xs, rowbase, cg, acc);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(empty + slot);
-      }
-      if (dead) break;
+    if (it.sig_idx >= 0) {
+      __threadfence();
       __syncwarp();
-      if (lane == 0) mbar_arrive(xempty + xs);
-      ++seq;
-      if (!mt.flush) continue;
-      const SlotArgs<TV>& sa = slots[mt.slot];
-      TV* obase = mt.out == kOutXh ? sa.xh : (mt.out == kOutYh ? sa.yh : sa.yp);
-      const int R = sa.R;
-      const int col0 = mt.c0 + cg * Tl::CPL;
-      const int vc = min(Tl::CPL, R - col0);
-      const bool aligned = (R % 4) == 0 && (col0 % 4) == 0;
-#pragma unroll
-      for (int i = 0; i < Tl::RPL; ++i) {
-        const int r = rowbase + Tl::RG * i;
-        if (r < mt.rows && vc > 0) add_row<Tl::CPL>(obase + (mt.o_row + r) * R + col0, acc[i], vc, aligned);
-      }
-#pragma unroll
-      for (int i = 0; i < Tl::RPL; ++i)
-#pragma unroll
-        for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
-      if (mt.sig_idx >= 0) {
-        __threadfence();
-        __syncwarp();
-        if (lane == 0) atomicAdd(sa.counters + mt.sig_idx, 1);
-      }
+      if (lane == 0) atomicAdd(sa.counters + it.sig_idx, 1);
     }
   }
+  return true;
+}
+
+// Claim the next unit of a list; -1 once the list is exhausted.
+__device__ __forceinline__ int64_t claim(unsigned long long* next, int64_t total, int lane) {
+  unsigned long long v = 0;
+  if (lane == 0) v = atomicAdd(next, 1ull);
+  v = __shfl_sync(0xffffffffu, v, 0);
+  return (int64_t)v < total ? (int64_t)v : -1;
+}
+
+// Persistent product over all slots of a launch.  Two work lists: the
+// dependency chain (forward and backward transforms, couplings), claimed in
+// a dependency order, and the free list (near field), which waits for
+// nothing.  A warp whose chain group is not ready yet does free work
+// meanwhile, and blocks on the chain only when the free list is exhausted.
+template <typename T, typename TN, typename TA, typename TV, int RC>
+__global__ void __launch_bounds__(kThreads) k_h2_persistent(LaunchArgs L) {
+  using Tl = Tile<RC>;
+  const SlotArgs<TV>* slots = static_cast<const SlotArgs<TV>*>(L.slots);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr size_t kRingBytes = (size_t)kStages * kStageBytes;
+  constexpr size_t kXBytes = sizeof(TA) * (size_t)kChunk * RC;
+  WarpRing<TA, RC> w;
+  w.ring = smem_raw + warp * warp_smem<TA, RC>();
+  w.Xs = reinterpret_cast<TA*>(w.ring + kRingBytes);
+  w.full = reinterpret_cast<uint64_t*>(w.ring + kRingBytes + kXBytes);
+  w.xbar = w.full + kStages;
+  w.fill = w.use = w.xuse = 0;
+  if (lane == 0) {
+    for (int i = 0; i < kStages; ++i) mbar_init(w.full + i, 1);
+    mbar_init(w.xbar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+
+  TA acc[Tl::RPL][Tl::CPL];
+#pragma unroll
+  for (int i = 0; i < Tl::RPL; ++i)
+#pragma unroll
+    for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
+
+  bool ok = true;
+  int64_t cu = claim(L.next, L.total, lane);
+  bool free_left = true;
+  while (ok) {
+    if (cu >= 0) {
+      const SlotArgs<TV>& sa = slots[find_slot(slots, L.nslots, cu)];
+      const int64_t lw = cu - sa.work_begin;
+      const int2 grp = sa.groups[lw / sa.nchunk];
+      if (free_left && !group_ready(sa, grp, lane)) {
+        const int64_t fu = claim(L.next_free, L.total_free, lane);
+        if (fu >= 0) {
+          const SlotArgs<TV>& sf = slots[find_free_slot(slots, L.nslots, fu)];
+          const int64_t lf = fu - sf.free_begin;
+          ok = run_group<T, TN, TA, TV, RC>(sf, sf.free_groups[lf / sf.nchunk], (int)(lf % sf.nchunk) * RC, w,
+                                            acc, L, lane);
+          continue;
+        }
+        free_left = false;
+      }
+      ok = run_group<T, TN, TA, TV, RC>(sa, grp, (int)(lw % sa.nchunk) * RC, w, acc, L, lane);
+      cu = claim(L.next, L.total, lane);
+      continue;
+    }
+    if (!free_left) break;
+    const int64_t fu = claim(L.next_free, L.total_free, lane);
+    if (fu < 0) break;
+    const SlotArgs<TV>& sf = slots[find_free_slot(slots, L.nslots, fu)];
+    const int64_t lf = fu - sf.free_begin;
+    ok = run_group<T, TN, TA, TV, RC>(sf, sf.free_groups[lf / sf.nchunk], (int)(lf % sf.nchunk) * RC, w, acc,
+                                      L, lane);
+  }
+  // drain: every issued copy has landed before the warp exits
+  if (lane == 0) {
+    for (uint32_t u = w.use; u < w.fill; ++u) mbar_drain(w.full + (u % kStages), (u / kStages) & 1);
+    if (w.xuse > 0) mbar_drain(w.xbar, (w.xuse - 1) & 1);
+  }
+  __syncwarp();
 }
 
 }  // namespace
 
 // Claim order of the groups.  The emission order below is a valid
 // dependency order but makes CTAs claim groups long before their inputs
-// exist.  This list scheduler simulates the launch: kWorkers CTAs, a group
+// exist.  This list scheduler simulates the launch: kWorkers warps, a group
 // costs a fixed latency plus its bytes at a CTA's share of HBM bandwidth, a
 // group is ready once every counter it waits for has seen all of its
 // contributions, and among ready groups the one with the longest remaining
@@ -572,7 +592,7 @@ __global__ void __launch_bounds__(kThreads) k_h2_persistent(LaunchArgs L) {
 void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups, int ncounters) {
   const int ng = (int)groups.size();
   if (ng < 2) return;
-  constexpr double kWorkers = 148 * 4, kLatency = 2.0e-6, kBandwidth = 6.0e12;  // s, B/s
+  constexpr double kWorkers = 148 * 16, kLatency = 2.0e-6, kBandwidth = 6.0e12;  // s, B/s
   std::vector<double> cost(ng);
   std::vector<int> sig(ng, -1);
   std::vector<std::vector<std::pair<int, int>>> waits(ng);
@@ -644,7 +664,8 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
   const int nc = h->nc;
   const bool trans = dir == 1;
   std::vector<MvItem> items;
-  std::vector<int2> groups;
+  std::vector<int2> groups, free_groups;
+  std::vector<int2>* target = &groups;  // list the groups being emitted go to
   std::vector<int> cx(nc, 0), cy(nc, 0);  // contributions (groups) to x-hat_c, y-hat_c
   struct Blk {
     int kind;
@@ -663,7 +684,7 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
         if ((int)items.size() == start) return;
         items.back().flush = 1;
         items.back().sig_idx = sig_idx;
-        groups.push_back(make_int2(start, (int)items.size()));
+        target->push_back(make_int2(start, (int)items.size()));
         if (sig_cnt) ++*sig_cnt;
         start = (int)items.size();
         segs = 0;
@@ -672,7 +693,8 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
         for (int k0 = 0; k0 < b.k; k0 += kChunk) {
           if (segs == max_segs) close();
           MvItem it{};
-          it.a_off = b.a_off;
+          // the tile (a0, k0) of the block (tiled panel layout, panel.cuh)
+          it.a_off = b.a_off + (int64_t)a0 * pad8(b.k) + (int64_t)std::min(kItemRows, m - a0) * k0;
           it.x_row = b.x_row + k0;
           it.o_row = o_row0 + a0;
           it.m = m;
@@ -735,6 +757,9 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
   size_t oi = 0;
   for (; oi < owners.size() && h->level[owners[oi]] >= h->depth - 1; ++oi) emit_couple(owners[oi]);
   {
+    // the near field waits for nothing: its own list, which warps work on
+    // while their chain groups wait for inputs
+    target = &free_groups;
     std::vector<std::vector<int>> by_own(nc);
     for (int b = 0; b < (int)h->near_t.size(); ++b) by_own[trans ? h->near_s[b] : h->near_t[b]].push_back(b);
     for (int own = 0; own < nc; ++own) {
@@ -747,6 +772,7 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
       }
       emit(blks, kInX, kOutY, h->begin[own], h->end[own] - h->begin[own], -1, nullptr, kNearSegs);
     }
+    target = &groups;
   }
   for (; oi < owners.size(); ++oi) emit_couple(owners[oi]);
   // backward transform, level by level down (y-hat of the parent must be final)
@@ -762,8 +788,20 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
     if (c > 0 && h->rank[c] > 0 && cy[c] > 0)
       emit({{kV, O[kV][c], h->end[c] - h->begin[c], h->rank[c], h->xoff[c], nc + c, cy[c]}}, kInYh,
            kOutY, h->begin[c], h->end[c] - h->begin[c], -1, nullptr, 1);
+  for (const int2& g : groups)
+    if (g.y - g.x > kMaxGroupSegs) {
+      set_error("internal: work group longer than the per-warp descriptor cache");
+      return GCA_ERR_UNSUPPORTED;
+    }
+  for (const int2& g : free_groups)
+    if (g.y - g.x > kMaxGroupSegs) {
+      set_error("internal: work group longer than the per-warp descriptor cache");
+      return GCA_ERR_UNSUPPORTED;
+    }
   schedule_groups(items, groups, 2 * nc);
   h->n_items[dir] = (int64_t)groups.size();
+  h->n_free[dir] = (int64_t)free_groups.size();
+  groups.insert(groups.end(), free_groups.begin(), free_groups.end());
   GCA_TRY(upload(h->d_items[dir], items, st));
   GCA_TRY(upload(h->d_groups[dir], groups, st));
   return GCA_OK;
@@ -818,7 +856,7 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   if (off > ws.bytes) ws_cache.clear();
   GCA_TRY(ws.reserve(off));
   unsigned char* base = ws.as<unsigned char>();
-  int64_t work = 0;
+  int64_t work = 0, free_work = 0;
   int max_n = 0;
   for (int i = 0; i < count; ++i) {
     const gca_h2* h = hs[i];
@@ -828,11 +866,15 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
     for (int q = 0; q < kPanelKinds; ++q) a.A[q] = (q == kN || q == kNt) ? PN[q].p : P[q].p;
     a.items = h->d_items[dir].as<MvItem>();
     a.groups = h->d_groups[dir].as<int2>();
+    a.free_groups = a.groups + h->n_items[dir];
     a.R = nrhs[i];
     a.nchunk = (a.R + RC - 1) / RC;
     a.n_work = h->n_items[dir] * a.nchunk;
     a.work_begin = work;
     work += a.n_work;
+    a.n_free = h->n_free[dir] * a.nchunk;
+    a.free_begin = free_work;
+    free_work += a.n_free;
     a.n = h->n;
     a.x = static_cast<const TV*>(x[i]);
     a.ldx = ldx[i];
@@ -850,7 +892,9 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   L.slots = base + o_slots;
   L.nslots = count;
   L.total = work;
+  L.total_free = free_work;
   L.next = reinterpret_cast<unsigned long long*>(base);
+  L.next_free = reinterpret_cast<unsigned long long*>(base + 8);
   L.abort_flag = reinterpret_cast<int*>(base + 16);
   L.status = status;
   // the descriptors change only with the arguments: upload when they differ
@@ -870,9 +914,8 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   const auto* d_slots = reinterpret_cast<const SlotArgs<TV>*>(base + o_slots);
   const unsigned gx = (unsigned)std::min<int64_t>(1024, (max_n + 255) / 256);
   k_gather<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots);
-  if (work > 0) {
-    const size_t smem = (size_t)kStages * kStageBytes + sizeof(TA) * (size_t)kXSlots * kChunk * RC +
-                        kXSlots * sizeof(Meta) + (2 * kStages + 2 * kXSlots) * sizeof(uint64_t);
+  if (work + free_work > 0) {
+    const size_t smem = cta_smem<TA, RC>();
     auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
     // resident CTAs on the device, found once per device (later launches
     // make no attribute or occupancy calls, so they can be graph captured)
@@ -895,7 +938,8 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
       std::lock_guard<std::mutex> lk(mu);
       if (dev >= 0 && dev < 64) cap_by_dev[dev] = cap;
     }
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(work, cap));
+    const unsigned grid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + free_work + kWarps - 1) / kWarps, cap));
     kern<<<grid, kThreads, smem, st>>>(L);
   }
   k_scatter<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots);
@@ -1056,10 +1100,13 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   for (int q = 0; q < kPanelKinds; ++q) a.A[q] = (q == kN || q == kNt) ? PN[q].p : P[q].p;
   a.items = h->d_items[0].as<MvItem>();
   a.groups = h->d_groups[0].as<int2>();
+  a.free_groups = a.groups + h->n_items[0];
   a.R = R;
   a.nchunk = (R + RC - 1) / RC;
   a.n_work = h->n_items[0] * a.nchunk;
   a.work_begin = 0;
+  a.n_free = h->n_free[0] * a.nchunk;
+  a.free_begin = 0;
   a.n = h->n;
   a.x = static_cast<const TV*>(x);
   a.ldx = ldx;
@@ -1075,7 +1122,9 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   L.slots = base + o_slot;
   L.nslots = 1;
   L.total = a.n_work;
+  L.total_free = a.n_free;
   L.next = reinterpret_cast<unsigned long long*>(base);
+  L.next_free = reinterpret_cast<unsigned long long*>(base + 8);
   L.abort_flag = reinterpret_cast<int*>(base + 16);
   L.status = h->d_status.as<int>();
   // the array keeps the previous call's contents: the claim counter, abort
@@ -1086,9 +1135,8 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   k_put_slot<TV><<<1, 1, 0, st>>>(a, d_slots);
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, ((int64_t)h->n * R + 255) / 256));
   k_gather<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots);
-  if (a.n_work > 0) {
-    const size_t smem = (size_t)kStages * kStageBytes + sizeof(TA) * (size_t)kXSlots * kChunk * RC +
-                        kXSlots * sizeof(Meta) + (2 * kStages + 2 * kXSlots) * sizeof(uint64_t);
+  if (a.n_work + a.n_free > 0) {
+    const size_t smem = cta_smem<TA, RC>();
     auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
     if (smem > 48 * 1024)
       GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1097,7 +1145,8 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
     GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     GCA_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     const int64_t capc = (int64_t)sms * std::max(per_sm, 1);
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(a.n_work, capc));
+    const unsigned grid =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.n_work + a.n_free + kWarps - 1) / kWarps, capc));
     kern<<<grid, kThreads, smem, st>>>(L);
   }
   k_scatter<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots);
