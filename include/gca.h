@@ -289,8 +289,9 @@ int gca_batch_status(const gca_h2_batch* b, int32_t* status);
 void gca_free_batch(gca_h2_batch* b);
 
 /* Sticky error bits of the products run on this handle so far (0: none;
- * 1: a bounded device-side wait of the persistent product kernel expired,
- * the results of that product are unreliable).  Synchronises the device. */
+ * 1: a bounded device-side wait of the persistent product kernel expired;
+ * 2: the kernel met a malformed work record).  With any bit set the results
+ * of that product are unreliable.  Synchronises the device. */
 int gca_h2_status(const gca_h2* h, int32_t* status);
 
 int gca_h2_stats(const gca_h2* h, gca_stats* out);

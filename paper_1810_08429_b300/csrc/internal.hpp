@@ -167,10 +167,15 @@ struct gca_h2 {
   gca::DevMem P64[gca::kPanelKinds], P32[gca::kPanelKinds], P16[gca::kPanelKinds];
   std::vector<int64_t> panel_off[gca::kPanelKinds];  // per block, elements (all precisions)
   int64_t psize[gca::kPanelKinds] = {0};
-  // persistent product: work items in dependency order, per direction
-  gca::DevMem d_items[2], d_groups[2];
-  int64_t n_items[2] = {0, 0};  // chain groups per direction (the free groups follow them)
-  int64_t n_free[2] = {0, 0};   // free (near-field) groups per direction
+  // persistent product, per direction: group records of up to 8 segment
+  // descriptors each, the chain groups in claim order followed by the free
+  // (near-field) groups, and the simulated start time of every chain group
+  // (used to interleave the claim orders of the meshes of a batch)
+  gca::DevMem d_segs[2];
+  int64_t n_chain[2] = {0, 0};  // chain groups per direction
+  int64_t n_free[2] = {0, 0};   // free groups per direction
+  std::vector<float> chain_t[2];
+  float makespan[2] = {0.f, 0.f};
   int max_leaf = 0;
 
   // device: product workspace (grown on demand): x-hat, y-hat, dependency

@@ -9,22 +9,31 @@
 // product swaps S, N for S^T, N^T.
 //
 // Every stage is a small dense product with a stored block in panel layout
-// (panel.cuh).  The whole recursion is cut into warp work items of 32
-// output rows x one block, listed in a dependency-respecting order:
+// (panel.cuh).  The recursion is cut into segments (one tile of a block:
+// up to 64 output rows x 64 input rows) and segments sharing output rows
+// into groups of at most 8, the unit a warp claims.  Two lists:
 //
-//   forward (leaves, then level by level up) -> coupling -> near field
-//   -> backward (level by level down) -> leaf bases
+//   chain: leaf forward -> upward transfers -> couplings -> downward
+//          transfers -> leaf bases, in a dependency order fixed by a list
+//          scheduler on the host;
+//   free:  the near field, which depends on nothing.
 //
-// and executed by one persistent kernel whose warps claim items with an
-// atomic counter.  An item waits (bounded spin, acquire) until the vector it
-// reads is complete, i.e. until a per-cluster counter has seen every item
-// that contributes to it, then stages that vector in shared memory, streams
-// its block from HBM and adds its 32 x RC results with atomics; items that
-// complete a vector other items read bump that vector's counter (release).
-// Items are claimed in list order and only wait for earlier items, so the
-// earliest unfinished item always has its inputs and the launch cannot
+// One persistent kernel runs both lists; its warps work independently.  A
+// group waits (bounded spin, acquire) until every vector it reads is
+// complete, i.e. until a per-cluster counter has seen every group that adds
+// to it; a warp whose chain group is not ready runs a free group meanwhile.
+// Groups are claimed in list order and only wait for earlier groups, so the
+// earliest unfinished group always has its inputs and the launch cannot
 // deadlock however many warps are resident.  A wait that exceeds its bound
-// sets a timeout bit in the handle's status word and goes on (no hang).
+// sets a timeout bit in the handle's status word and the launch winds down
+// (no hang).
+//
+// Per warp, everything that can be fetched ahead is: the next group's claim
+// (an atomic issued when the current group starts) and its descriptors (one
+// bulk copy into shared memory), the block tiles (a ring of bulk copies on
+// mbarriers that runs across the segments of a group) and each segment's
+// input vector block (two buffers, the next segment's block in flight while
+// the current one is used).
 //
 // x is gathered into cluster order first and y scattered back to the
 // caller's order last; x-hat, y-hat, y (cluster order) and the counters are
@@ -33,9 +42,9 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <queue>
-#include <cstring>
 #include <string>
 
 #include "internal.hpp"
@@ -45,18 +54,18 @@ namespace gca {
 
 namespace {
 
-constexpr int kSpinLimit = 1 << 20;  // bounded wait: well under a second with the back-off below
 constexpr int kStatusTimeout = 1;
+constexpr int kStatusBadPlan = 2;
 
-// One warp work item (host builds them, device executes them).
+// Work item of the host-side plan (one segment).
 struct MvItem {
-  int64_t a_off;  // element offset of the block in its panel array
+  int64_t a_off;  // element offset of the tile in its panel array
   int64_t x_row;  // first row of the input vector block
-  int64_t o_row;  // output row of lane 0
-  int m;          // rows of the stored block (panel stride)
-  int k;          // columns of this item's column chunk (<= kChunk)
-  int a0;         // first block row handled by this item
-  int k0;         // first block column of the chunk
+  int64_t o_row;  // output row of the tile's first row
+  int m;          // rows of the stored block
+  int k;          // columns of this tile (<= kChunk)
+  int a0;         // first block row of the tile
+  int k0;         // first block column of the tile
   int kind;       // panel kind | (input << 4) | (output << 8)
   int wait_idx;   // counter that must reach wait_cnt * nchunk first (-1: none)
   int wait_cnt;
@@ -64,23 +73,33 @@ struct MvItem {
   int flush;      // last segment of its group: add the accumulated rows to the output
 };
 
+// Device descriptor of a segment: 32 bytes, 8 per group record.
+struct MvSeg {
+  uint32_t a8;       // tile offset in units of 8 elements of its panel array
+  int32_t x_row;     // first row of the input vector block
+  int32_t o_row;     // output row of the tile's first row
+  uint32_t rk;       // tile rows | columns << 16
+  uint32_t flags;    // panel kind | input << 8 | output << 16 | last << 24
+  int32_t wait_idx;  // -1: none
+  int32_t wait_cnt;
+  int32_t sig_idx;   // -1: none
+};
+static_assert(sizeof(MvSeg) == 32, "segment descriptor must be 32 bytes");
+
+constexpr int kMaxGroupSegs = 8;                            // segments of a group
+constexpr int kRecordBytes = kMaxGroupSegs * (int)sizeof(MvSeg);  // one group record
+
 enum { kInXh = 0, kInYh = 1, kInX = 2 };
 enum { kOutXh = 0, kOutYh = 1, kOutY = 2 };
 
-// Everything one mesh (slot) of a launch needs; a launch runs the work of
-// any number of slots, each slot's work list in dependency order, slot after
-// slot in claim order.
+// Everything one mesh (slot) of a launch needs.
 template <typename TV>
 struct SlotArgs {
   const void* A[kPanelKinds];  // panel arrays (near-field kinds hold the near storage type)
-  const MvItem* items;
-  const int2* groups;          // chain list: [begin, end) segment ranges claimed as a unit
-  const int2* free_groups;     // free list (no dependencies)
-  int64_t work_begin;          // first chain claim index of this slot
-  int64_t n_work;              // chain groups * nchunk
-  int64_t free_begin;          // first free claim index of this slot
-  int64_t n_free;              // free groups * nchunk
-  int nchunk;
+  const MvSeg* segs;           // group records: chain groups, then free groups
+  int64_t n_chain;             // chain groups
+  int64_t n_free;              // free groups
+  int nchunk;                  // right-hand-side chunks of RC columns
   int R;
   int n;
   int pad;
@@ -99,6 +118,8 @@ struct SlotArgs {
 struct LaunchArgs {
   const void* slots;           // SlotArgs<TV>[nslots]
   int nslots;
+  const int2* chain_map;       // claim -> (slot, claim within the slot); null: one slot
+  const int2* free_map;
   int64_t total;               // chain claims over all slots
   int64_t total_free;          // free claims over all slots
   unsigned long long* next;    // chain claim counter
@@ -106,26 +127,6 @@ struct LaunchArgs {
   int* status;
   int* abort_flag;             // raised by any timed-out wait; every wait gives up
 };
-
-template <typename TV>
-__device__ __forceinline__ int find_slot(const SlotArgs<TV>* sl, int nslots, int64_t w) {
-  int lo = 0, hi = nslots - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (sl[mid].work_begin <= w) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <typename TV>
-__device__ __forceinline__ int find_free_slot(const SlotArgs<TV>* sl, int nslots, int64_t w) {
-  int lo = 0, hi = nslots - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (sl[mid].free_begin <= w) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -135,34 +136,51 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 
 // ---------------------------------------------------------------- pipeline
 //
-// Every warp of the persistent launch works on its own: it claims a group
-// (claim-ahead), streams the group's block panels into its private ring of
-// shared-memory stages with 1-D bulk copies (TMA) completing on per-stage
-// mbarriers, waits for the segment's input vector block (bounded spin on the
-// dependency counter), stages it, and accumulates in registers.  A segment =
-// kItemRows rows x kChunk columns of one stored block; the stages of the
-// group's segments form one stream, so the next segment's panels are in
-// flight while the current one is computed.  A warp stalled on a dependency
-// stalls nobody else.
-constexpr int kWarps = 4;                                   // independent warps per CTA
-constexpr int kThreads = 32 * kWarps;
+// A CTA holds kPairs pairs of warps.  In each pair a consumer warp only
+// computes: it waits on mbarriers for the group its producer hands it, for
+// each segment's input vector block and for each ring stage of block panels,
+// multiplies, and adds its results to the output.  The producer warp does
+// everything that waits on memory: it claims groups (one ahead), copies
+// their descriptor records, waits for the counters of chain inputs, and
+// issues the bulk copies (TMA, 1-D) of the panels and input blocks into the
+// consumer's buffers, running ahead of the consumer by the ring's depth.
+constexpr int kPairs = 4;                                   // producer/consumer pairs per CTA
+// register split between the warpgroups (float products, two CTAs per SM):
+// launched with kLaunchRegs a thread, producers give up what consumers take
+constexpr int kLaunchRegs = 128, kProducerRegs = 80, kConsumerRegs = 176;
+static_assert(kProducerRegs + kConsumerRegs == 2 * kLaunchRegs, "register split must balance");
+template <typename TA>
+constexpr bool kSplitRegs = sizeof(TA) == 4;
+constexpr int kThreads = 64 * kPairs;                       // consumers: warps 0..3, producers: 4..7
 constexpr int kItemRows = 64;                               // rows per segment (one warp tile)
 constexpr int kChunk = 64;                                  // columns per segment
 constexpr int kStagePanels = 4;
 constexpr int kStageBytes = kStagePanels * kItemRows * 16;  // 4 KB: one contiguous copy
-constexpr int kStages = 3;
-constexpr int kMbarLimit = 1 << 20;
-constexpr int kMaxGroupSegs = 8;  // segments of a group
+constexpr int kStages = 4;
+constexpr int kDescSlots = 4;                               // records: chain 0, 1; free 2, 3
+// bound of every mbarrier wait, in SM clock cycles (about a second)
+constexpr long long kWaitCycles = 1LL << 31;
+// a waiting warp sleeps until the phase completes or this many ns pass
+constexpr unsigned kSuspendNs = 20000;
 
-// shared memory of one warp: ring, input block, mbarriers (kStages + 1)
+// Shared memory of one pair: ring, two input blocks, four descriptor
+// records, the two-entry group queue, mbarriers.
 template <typename TA, int RC>
-__host__ __device__ constexpr size_t warp_smem() {
-  return ((size_t)kStages * kStageBytes + sizeof(TA) * (size_t)kChunk * RC + (kStages + 1) * 8 + 127) /
-         128 * 128;
-}
+struct PairSmem {
+  static constexpr size_t kXSlot = sizeof(TA) * (size_t)kChunk * RC;
+  static constexpr size_t kRing = 0;
+  static constexpr size_t kX = (size_t)kStages * kStageBytes;
+  static constexpr size_t kDesc = kX + 2 * kXSlot;
+  static constexpr size_t kQueue = kDesc + (size_t)kDescSlots * kRecordBytes;
+  static constexpr size_t kBar = kQueue + 2 * sizeof(int4);
+  // full/empty per stage, xfull/xempty per block, ufull/uempty per queue
+  // entry, dland/dfree per record
+  static constexpr int kBars = 2 * kStages + 4 + 4 + 2 * kDescSlots;
+  static constexpr size_t kBytes = (kBar + 8 * kBars + 127) / 128 * 128;
+};
 template <typename TA, int RC>
 __host__ __device__ constexpr size_t cta_smem() {
-  return kWarps * warp_smem<TA, RC>();
+  return kPairs * PairSmem<TA, RC>::kBytes;
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -171,27 +189,56 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 __device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(b)) : "memory");
+}
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, unsigned tx) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
                    smem_u32(b)),
                "r"(tx)
                : "memory");
 }
+// potentially blocking test: the warp is suspended until the phase
+// completes or kSuspendNs pass, so waiting warps take no issue slots from
+// the computing ones
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity), "n"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
+// non-blocking: has the phase of parity `parity` completed?
+__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(smem_u32(b)), "r"(parity)
       : "memory");
   return ok != 0;
 }
 // Bounded wait for the phase of parity `parity`; false on timeout or abort.
+// Between polls the warp sleeps (doubling up to kMaxSleep ns), so that a
+// waiting warp takes almost no issue slots from the computing warps of its
+// SM sub-partition; the abort flag and the deadline are checked every 16th
+// poll.
+template <unsigned kMaxSleep = 128>
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag,
                                           int* status) {
-  for (int i = 0; i < kMbarLimit; ++i) {
+  if (mbar_try_wait(b, parity)) return true;
+  const long long t0 = clock64();
+  unsigned ns = 16;
+  for (unsigned it = 1;; ++it) {
+    __nanosleep(ns);
+    ns = ns < kMaxSleep ? 2 * ns : kMaxSleep;
     if (mbar_try_wait(b, parity)) return true;
-    if ((i & 63) == 63 && *abort_flag) return false;
+    if ((it & 15) == 0) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kWaitCycles) break;
+    }
   }
   atomicOr(status, kStatusTimeout);
   *abort_flag = 1;
@@ -200,8 +247,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile
 // Bounded wait used only while draining copies before exit (ignores the
 // abort flag, so that no copy is still landing when the warp retires).
 __device__ __forceinline__ void mbar_drain(uint64_t* b, unsigned parity) {
-  for (int i = 0; i < kMbarLimit; ++i)
-    if (mbar_try_wait(b, parity)) return;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, parity)) {
+    __nanosleep(256);
+    if (clock64() - t0 > kWaitCycles) return;
+  }
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile(
@@ -223,6 +273,13 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// claim counter increment whose result is read later (the warp runs on
+// until the value is used)
+__device__ __forceinline__ unsigned long long atom_add_u64(unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("atom.relaxed.gpu.global.add.u64 %0, [%1], 1;" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
 // Fire-and-forget reductions into global memory (no return value, so the
 // issuing warp does not wait for the L2 round trip).
@@ -235,6 +292,12 @@ __device__ __forceinline__ void red_add4(float* p, float a, float b, float c, fl
 }
 __device__ __forceinline__ void red_add(double* p, double v) {
   asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+// counter increment with release semantics at GPU scope: writes that happen
+// before it (this thread's, and other lanes' ordered by a warp barrier) are
+// visible to a thread that reads the new value with an acquire
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // add N consecutive values of one output row (16-byte vector reductions
@@ -282,11 +345,11 @@ __global__ void k_scatter(const SlotArgs<TV>* __restrict__ slots) {
   }
 }
 
-// Register tile of a warp: 64 rows x RC right-hand sides.  CPL = min(RC, 8)
-// columns per lane, NCG = RC / CPL column groups, RG = 32 / NCG row groups,
-// RPL = 64 / RG rows per lane; lane (rg, cg) owns rows rg + RG * i (i < RPL)
-// and columns cg * CPL + [0, CPL).  Rows of one load instruction are
-// consecutive (conflict-free 16-byte shared loads).
+// Register tile of a consumer: 64 rows x RC right-hand sides.  CPL =
+// min(RC, 8) columns per lane, NCG = RC / CPL column groups, RG = 32 / NCG
+// row groups, RPL = 64 / RG rows per lane; lane (rg, cg) owns rows
+// rg + RG * i (i < RPL) and columns cg * CPL + [0, CPL).  Rows of one load
+// instruction are consecutive (conflict-free 16-byte shared loads).
 template <int RC>
 struct Tile {
   static constexpr int CPL = RC < 8 ? RC : 8;
@@ -295,304 +358,620 @@ struct Tile {
   static constexpr int RPL = 64 / RG;
 };
 
-// One ring stage: npst panels (P columns each, `pst` bytes apart) of the
-// lane's rows.
-template <typename T, typename TA, int RC>
-__device__ __forceinline__ void consume_stage(const unsigned char* stage, int pst, int npst, int p0,
-                                              const TA* __restrict__ Xs, int rg, int cg,
-                                              TA (&acc)[Tile<RC>::RPL][Tile<RC>::CPL]) {
+// 16-byte load from a shared-memory address (an explicit shared-space load:
+// the buffers reach the inner loop through a struct, and a generic load
+// would go through the address-space check of the load/store unit).  The
+// memory clobber keeps it after the mbarrier wait that makes the data valid.
+__device__ __forceinline__ uint4 lds128(unsigned addr) {
+  uint4 u;
+  asm("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(u.x), "=r"(u.y), "=r"(u.z), "=r"(u.w) : "r"(addr)
+      : "memory");
+  return u;
+}
+
+// CPL consecutive values of a staged input row: 16-byte shared loads where
+// the row segment is 16-byte aligned (CPL * sizeof(TA) a multiple of 16;
+// every buffer and row start is)
+template <typename TA, int CPL>
+__device__ __forceinline__ void load_row(const TA* __restrict__ p, TA (&x)[CPL]) {
+  if constexpr ((CPL * sizeof(TA)) % 16 == 0) {
+    constexpr int V = 16 / (int)sizeof(TA);
+    const unsigned a = smem_u32(p);
+#pragma unroll
+    for (int c = 0; c < CPL; c += V) {
+      const uint4 u = lds128(a + c * (unsigned)sizeof(TA));
+      if constexpr (sizeof(TA) == 4) {
+        x[c] = __uint_as_float(u.x);
+        x[c + 1] = __uint_as_float(u.y);
+        x[c + 2] = __uint_as_float(u.z);
+        x[c + 3] = __uint_as_float(u.w);
+      } else {
+        x[c] = __hiloint2double((int)u.y, (int)u.x);
+        x[c + 1] = __hiloint2double((int)u.w, (int)u.z);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) x[c] = p[c];
+  }
+}
+
+// One panel (P columns) of the lane's rows in the first NI row groups times
+// the staged input rows.
+template <typename T, typename TA, int RC, int NI>
+__device__ __forceinline__ void panel_fma(const unsigned char* panel, const TA* __restrict__ xr, int rg, int cg,
+                                          TA (&part)[Tile<RC>::RPL][Tile<RC>::CPL]) {
   using Tl = Tile<RC>;
   constexpr int P = Panel<T>::P;
-  // the stage's sum (at most kStagePanels * P terms) is formed on its own
-  // and then added: two-level summation keeps the rounding error of the
-  // long sums over a group's segments near that of a few short chains
+  TA v[NI][P];
+  const unsigned pa = smem_u32(panel) + rg * 16;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) unpack(lds128(pa + Tl::RG * i * 16), v[i]);
+#pragma unroll
+  for (int kk = 0; kk < P; ++kk) {
+    TA x[Tl::CPL];
+    load_row<TA, Tl::CPL>(xr + kk * RC + cg * Tl::CPL, x);
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+#pragma unroll
+      for (int c = 0; c < Tl::CPL; ++c) part[i][c] = fma(v[i][kk], x[c], part[i][c]);
+  }
+}
+
+// One ring stage: npst panels (`pst` bytes apart) of the lane's rows in the
+// first NI row groups (the groups beyond the tile's rows are skipped: the
+// condition is the same for every lane).  The stage's sum (at most
+// kStagePanels * P terms) is formed on its own and then added: two-level
+// summation keeps the rounding error of the long sums over a group's
+// segments near that of a few short chains.
+template <typename T, typename TA, int RC, int NI>
+__device__ __forceinline__ void consume_rows(const unsigned char* stage, int pst, int npst, int p0,
+                                             const TA* __restrict__ Xs, int rg, int cg,
+                                             TA (&acc)[Tile<RC>::RPL][Tile<RC>::CPL]) {
+  using Tl = Tile<RC>;
+  constexpr int P = Panel<T>::P;
   TA part[Tl::RPL][Tl::CPL];
 #pragma unroll
-  for (int i = 0; i < Tl::RPL; ++i)
+  for (int i = 0; i < NI; ++i)
 #pragma unroll
     for (int c = 0; c < Tl::CPL; ++c) part[i][c] = (TA)0;
+#pragma unroll 1
+  for (int g = 0; g < npst; ++g) panel_fma<T, TA, RC, NI>(stage + g * pst, Xs + (p0 + g) * P * RC, rg, cg, part);
 #pragma unroll
-  for (int g = 0; g < kStagePanels; ++g) {
-    if (g >= npst) break;
-    TA v[Tl::RPL][P];
-#pragma unroll
-    for (int i = 0; i < Tl::RPL; ++i)
-      unpack(*reinterpret_cast<const uint4*>(stage + g * pst + (rg + Tl::RG * i) * 16), v[i]);
-#pragma unroll
-    for (int kk = 0; kk < P; ++kk) {
-      const TA* xr = Xs + ((p0 + g) * P + kk) * RC + cg * Tl::CPL;
-      TA x[Tl::CPL];
-#pragma unroll
-      for (int c = 0; c < Tl::CPL; ++c) x[c] = xr[c];
-#pragma unroll
-      for (int i = 0; i < Tl::RPL; ++i)
-#pragma unroll
-        for (int c = 0; c < Tl::CPL; ++c) part[i][c] = fma(v[i][kk], x[c], part[i][c]);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < Tl::RPL; ++i)
+  for (int i = 0; i < NI; ++i)
 #pragma unroll
     for (int c = 0; c < Tl::CPL; ++c) acc[i][c] += part[i][c];
 }
 
-// A segment (one tile of a stored block) as the issuing side sees it.
-struct SegSrc {
-  const unsigned char* A;  // the tile
-  int rows;                // rows of the tile: panels are rows * 16 bytes apart
-  int np;                  // panels of the tile
+template <typename T, typename TA, int RC>
+__device__ __forceinline__ void consume_stage(const unsigned char* stage, int rows, int npst, int p0,
+                                              const TA* __restrict__ Xs, int rg, int cg,
+                                              TA (&acc)[Tile<RC>::RPL][Tile<RC>::CPL]) {
+  using Tl = Tile<RC>;
+  const int pst = rows * 16;
+  const int ni = (rows + Tl::RG - 1) / Tl::RG;  // row groups holding rows of the tile
+  if constexpr (Tl::RPL == 4) {
+    if (ni >= 4)
+      consume_rows<T, TA, RC, 4>(stage, pst, npst, p0, Xs, rg, cg, acc);
+    else if (ni == 3)
+      consume_rows<T, TA, RC, 3>(stage, pst, npst, p0, Xs, rg, cg, acc);
+    else if (ni == 2)
+      consume_rows<T, TA, RC, 2>(stage, pst, npst, p0, Xs, rg, cg, acc);
+    else
+      consume_rows<T, TA, RC, 1>(stage, pst, npst, p0, Xs, rg, cg, acc);
+  } else {
+    static_assert(Tl::RPL == 2, "row groups per lane");
+    if (ni >= 2)
+      consume_rows<T, TA, RC, 2>(stage, pst, npst, p0, Xs, rg, cg, acc);
+    else
+      consume_rows<T, TA, RC, 1>(stage, pst, npst, p0, Xs, rg, cg, acc);
+  }
+}
+
+// Shared-memory regions and mbarriers of one pair.
+template <typename TA, int RC>
+struct Pair {
+  unsigned char* ring;
+  TA* xb;
+  MvSeg* rec;
+  int4* queue;  // {slot (-1: no more groups), first right-hand side, record, 0}
+  uint64_t* bar;
+  __device__ uint64_t* full(int s) const { return bar + s; }
+  __device__ uint64_t* empty(int s) const { return bar + kStages + s; }
+  __device__ uint64_t* xfull(int j) const { return bar + 2 * kStages + j; }
+  __device__ uint64_t* xempty(int j) const { return bar + 2 * kStages + 2 + j; }
+  __device__ uint64_t* ufull(int q) const { return bar + 2 * kStages + 4 + q; }
+  __device__ uint64_t* uempty(int q) const { return bar + 2 * kStages + 6 + q; }
+  __device__ uint64_t* dland(int d) const { return bar + 2 * kStages + 8 + d; }
+  __device__ uint64_t* dfree(int d) const { return bar + 2 * kStages + 8 + kDescSlots + d; }
+  __device__ TA* xslot(int j) const { return xb + (size_t)j * kChunk * RC; }
 };
 
+// A group held by a producer: its slot, the right-hand-side chunk and the
+// descriptor record it was copied to.
+struct Unit {
+  int slot;    // -1: none
+  int c0;      // first right-hand side
+  int dslot;   // descriptor record of the pair
+};
+
+// The segments of a group: lane j < nseg holds the descriptor of segment j;
+// `notready` marks segments whose input vector block is not complete yet,
+// `haswait` those that depend on other groups.
+struct Probe {
+  MvSeg d;
+  int nseg;
+  unsigned notready;
+  unsigned haswait;
+};
+
+__device__ __forceinline__ MvSeg read_seg(const MvSeg* rec, int lane) {
+  MvSeg d{};
+  if (lane < kMaxGroupSegs) {
+    const uint4* q = reinterpret_cast<const uint4*>(rec + lane);
+    const uint4 a = q[0], b = q[1];
+    d.a8 = a.x;
+    d.x_row = (int)a.y;
+    d.o_row = (int)a.z;
+    d.rk = a.w;
+    d.flags = b.x;
+    d.wait_idx = (int)b.y;
+    d.wait_cnt = (int)b.z;
+    d.sig_idx = (int)b.w;
+  }
+  return d;
+}
+
+__device__ __forceinline__ int count_segs(const MvSeg& d, int lane) {
+  const unsigned lastmask = __ballot_sync(0xffffffffu, lane < kMaxGroupSegs && ((d.flags >> 24) & 1));
+  return lastmask ? __ffs(lastmask) : 0;
+}
+
 template <typename T, typename TN, typename TV>
-__device__ __forceinline__ SegSrc seg_src(const SlotArgs<TV>& sa, const MvItem& it) {
-  const int ain = it.kind & 15;
+__device__ __forceinline__ void seg_geom(const SlotArgs<TV>& sa, uint32_t a8, uint32_t rk, uint32_t flags,
+                                         const unsigned char*& A, int& rows, int& np) {
+  const int ain = flags & 0xff;
   const bool is_near = ain == kN || ain == kNt;
   const int P = is_near ? Panel<TN>::P : Panel<T>::P;
   const int esz = is_near ? (int)sizeof(TN) : (int)sizeof(T);
-  SegSrc s;
-  s.A = static_cast<const unsigned char*>(sa.A[ain]) + it.a_off * esz;
-  s.rows = min(kItemRows, it.m - it.a0);
-  s.np = pad8(it.k) / P;
-  return s;
+  A = static_cast<const unsigned char*>(sa.A[ain]) + (int64_t)a8 * 8 * esz;
+  rows = (int)(rk & 0xffff);
+  np = pad8((int)(rk >> 16)) / P;
 }
 
-// Per-warp state of the stage ring (shared memory of the warp).
-template <typename TA, int RC>
-struct WarpRing {
-  unsigned char* ring;
-  TA* Xs;
-  uint64_t* full;
-  uint64_t* xbar;
-  uint32_t fill, use, xuse;  // stages issued / consumed, input blocks copied
-};
-
-// Every segment of group [grp.x, grp.y) has its input block complete.
-template <typename TV>
-__device__ __forceinline__ bool group_ready(const SlotArgs<TV>& sa, int2 grp, int lane) {
-  bool ok = true;
-  for (int s = grp.x + lane; s < grp.y; s += 32) {
-    const MvItem& it = sa.items[s];
-    if (it.wait_idx >= 0 && ld_acquire(sa.counters + it.wait_idx) < it.wait_cnt * sa.nchunk) ok = false;
-  }
-  return __all_sync(0xffffffffu, ok);
+template <typename TV, int RC>
+__device__ __forceinline__ bool bulk_inputs(const SlotArgs<TV>& sa) {
+  return RC == sa.R && (RC * sizeof(TV)) % 16 == 0;
 }
 
-// One claimed unit: the segments of one group for right-hand sides
-// [c0, c0 + RC).  Returns false when a wait timed out or the launch aborted.
+// ------------------------------------------------------------- producer
 template <typename T, typename TN, typename TA, typename TV, int RC>
-__device__ bool run_group(const SlotArgs<TV>& sa, int2 grp, int c0, WarpRing<TA, RC>& w,
-                          TA (&acc)[Tile<RC>::RPL][Tile<RC>::CPL], const LaunchArgs& L, int lane) {
-  using Tl = Tile<RC>;
+__device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, const Pair<TA, RC>& P, int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
   volatile int* abort_flag = L.abort_flag;
-  const int rg = lane % Tl::RG, cg = lane / Tl::RG;
-  // issuing cursor: segment `is`, its stage `ist`; stages of consecutive
-  // segments form one stream through the ring
-  int is = grp.x, ist = 0;
-  SegSrc src = seg_src<T, TN, TV>(sa, sa.items[is]);
-  auto issue = [&]() {
-    if (is >= grp.y || w.fill - w.use >= (uint32_t)kStages) return;
-    const int s = (int)(w.fill % kStages);
-    if (lane == 0) {
-      const int p0 = ist * kStagePanels;
-      const int npst = min(kStagePanels, src.np - p0);
-      const unsigned bytes = (unsigned)(npst * src.rows * 16);  // contiguous panels of the tile
-      mbar_arrive_tx(w.full + s, bytes);
-      bulk_g2s(w.ring + s * kStageBytes, src.A + (int64_t)p0 * src.rows * 16, bytes, w.full + s);
-    }
-    ++w.fill;
-    if (++ist * kStagePanels >= src.np) {
-      ist = 0;
-      if (++is < grp.y) src = seg_src<T, TN, TV>(sa, sa.items[is]);
-    }
-  };
-  for (int q = 0; q < kStages; ++q) issue();
+  uint32_t fill = 0, xfill = 0, uhand = 0;
+  uint32_t dland_par = 0, dland_pend = 0, dfree_par = 0, dused = 0;
+  bool ok = true;
+  auto wait = [&](uint64_t* b, unsigned par) { return mbar_wait<512>(b, par, abort_flag, L.status); };
 
-  for (int us = grp.x; us < grp.y; ++us) {
-    const MvItem it = sa.items[us];
-    const int xin = (it.kind >> 4) & 15, out = (it.kind >> 8) & 15;
-    const int rows = min(kItemRows, it.m - it.a0);
-    const int ain = it.kind & 15;
-    const bool is_near = ain == kN || ain == kNt;
-    const int np = pad8(it.k) / (is_near ? Panel<TN>::P : Panel<T>::P);
-    const int kp = pad8(it.k);
-    // input vector block complete?
-    if (it.wait_idx >= 0) {
-      const int need = it.wait_cnt * sa.nchunk;
-      int timeout = 0;
-      if (lane == 0) {
-        int spins = 0;
-        while (ld_acquire(sa.counters + it.wait_idx) < need) {
-          if (++spins > kSpinLimit) {
-            atomicOr(L.status, kStatusTimeout);
-            *abort_flag = 1;
-            timeout = 1;
-            break;
-          }
-          if (*abort_flag) {
-            timeout = 1;
-            break;
-          }
-          __nanosleep(32);
+  // copy the record of claim c of a list into record d (after the consumer
+  // has released d's previous record)
+  auto fetch = [&](int64_t c, bool chain, int d) -> Unit {
+    Unit u{-1, 0, d};
+    if (c < 0 || !ok) return u;
+    if ((dused >> d) & 1) {
+      if (!wait(P.dfree(d), (dfree_par >> d) & 1)) {
+        ok = false;
+        return u;
+      }
+      dfree_par ^= 1u << d;
+    }
+    int s = 0;
+    int64_t loc = c;
+    const int2* map = chain ? L.chain_map : L.free_map;
+    if (map) {
+      const int2 m = map[c];
+      s = m.x;
+      loc = m.y;
+    }
+    const SlotArgs<TV>& sa = slots[s];
+    const int64_t g = loc / sa.nchunk + (chain ? 0 : sa.n_chain);
+    u.slot = s;
+    u.c0 = (int)(loc % sa.nchunk) * RC;
+    if (lane == 0) {
+      mbar_arrive_tx(P.dland(d), kRecordBytes);
+      bulk_g2s(P.rec + d * kMaxGroupSegs, sa.segs + g * kMaxGroupSegs, kRecordBytes, P.dland(d));
+    }
+    dland_pend |= 1u << d;
+    dused |= 1u << d;
+    return u;
+  };
+  auto land = [&](int d) -> bool {
+    if (!((dland_pend >> d) & 1)) return true;
+    if (!wait(P.dland(d), (dland_par >> d) & 1)) return false;
+    dland_par ^= 1u << d;
+    dland_pend &= ~(1u << d);
+    return true;
+  };
+  auto probe = [&](const SlotArgs<TV>& sa, int d, Probe& pr) -> bool {
+    pr.d = read_seg(P.rec + d * kMaxGroupSegs, lane);
+    pr.nseg = count_segs(pr.d, lane);
+    const bool w = lane < pr.nseg && pr.d.wait_idx >= 0;
+    bool nr = false;
+    if (w) nr = ld_acquire(sa.counters + pr.d.wait_idx) < pr.d.wait_cnt * sa.nchunk;
+    pr.notready = __ballot_sync(FULL, nr);
+    pr.haswait = __ballot_sync(FULL, w);
+    __syncwarp();
+    return pr.nseg > 0;
+  };
+  auto claim_now = [&](unsigned long long* ctr, int64_t total) -> int64_t {
+    unsigned long long v = 0;
+    if (lane == 0) v = atomicAdd(ctr, 1ull);
+    v = __shfl_sync(FULL, v, 0);
+    return (int64_t)v < total ? (int64_t)v : -1;
+  };
+  // hand group (slot, c0, record d) to the consumer
+  auto hand = [&](int slot, int c0, int d) -> bool {
+    const int q = (int)(uhand & 1);
+    if (uhand >= 2 && !wait(P.uempty(q), ((uhand >> 1) - 1) & 1)) return false;
+    if (lane == 0) {
+      P.queue[q] = make_int4(slot, c0, d, 0);
+      mbar_arrive(P.ufull(q));
+    }
+    __syncwarp();
+    ++uhand;
+    return true;
+  };
+
+  Unit cu = fetch(claim_now(L.next, L.total), true, 0);
+  Unit fu = fetch(claim_now(L.next_free, L.total_free), false, 2);
+  while (ok) {
+    Unit u;
+    bool chain;
+    Probe pr;
+    if (cu.slot >= 0) {
+      if (!(ok = land(cu.dslot))) break;
+      if (!probe(slots[cu.slot], cu.dslot, pr)) {
+        atomicOr(L.status, kStatusBadPlan);
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      chain = !(pr.notready && fu.slot >= 0);
+      if (!chain) {
+        // the chain group waits for inputs: hand the held free group first
+        if (!(ok = land(fu.dslot))) break;
+        if (!probe(slots[fu.slot], fu.dslot, pr)) {
+          atomicOr(L.status, kStatusBadPlan);
+          *abort_flag = 1;
+          ok = false;
+          break;
         }
       }
-      if (__shfl_sync(0xffffffffu, timeout, 0)) return false;
-    }
-    // stage the input rows k0 .. k0 + kp (zero beyond the block's columns);
-    // every lane is done reading the previous block (__syncwarp)
-    const TV* X = (xin == kInXh ? sa.xh : (xin == kInYh ? sa.yh : sa.xp)) + it.x_row * sa.R + c0;
-    const bool bulk = RC == sa.R && (RC * sizeof(TV)) % 16 == 0 && sizeof(TA) == sizeof(TV);
-    fence_proxy_async();
-    if (it.wait_idx >= 0) fence_proxy_async_global();  // the block was written by other warps
-    __syncwarp();
-    if (bulk) {
-      for (int i = it.k * RC + lane; i < kp * RC; i += 32) w.Xs[i] = (TA)0;
-      if (lane == 0) {
-        const unsigned bytes = (unsigned)(it.k * RC * sizeof(TV));
-        mbar_arrive_tx(w.xbar, bytes);
-        bulk_g2s(w.Xs, X, bytes, w.xbar);
+      u = chain ? cu : fu;
+    } else if (fu.slot >= 0) {
+      if (!(ok = land(fu.dslot))) break;
+      if (!probe(slots[fu.slot], fu.dslot, pr)) {
+        atomicOr(L.status, kStatusBadPlan);
+        *abort_flag = 1;
+        ok = false;
+        break;
       }
-      ++w.xuse;
-      if (!mbar_wait(w.xbar, (w.xuse - 1) & 1, abort_flag, L.status)) return false;
+      chain = false;
+      u = fu;
     } else {
-      for (int i = lane; i < kp * RC; i += 32) {
-        const int r = i / RC, c = i % RC;
-        w.Xs[i] = (r < it.k && c0 + c < sa.R) ? (TA)__ldcg(X + (int64_t)r * sa.R + c) : (TA)0;
+      break;
+    }
+    const SlotArgs<TV>& sa = slots[u.slot];
+    if (!(ok = hand(u.slot, u.c0, u.dslot))) break;
+    // claim the successor on the same list; its record is fetched once the
+    // first data of this group is on its way
+    unsigned long long* ctr = chain ? L.next : L.next_free;
+    const int64_t total = chain ? L.total : L.total_free;
+    unsigned long long token = 0;
+    if (lane == 0) token = atom_add_u64(ctr);
+    bool fetched = false;
+    Unit next{-1, 0, u.dslot ^ 1};
+    auto fetch_next = [&]() {
+      if (fetched) return;
+      fetched = true;
+      const int64_t c = (int64_t)__shfl_sync(FULL, token, 0);
+      next = fetch(c < total ? c : -1, chain, u.dslot ^ 1);
+    };
+    const bool bulk = bulk_inputs<TV, RC>(sa);
+    const MvSeg& d = pr.d;
+    for (int s = 0; s < pr.nseg && ok; ++s) {
+      const uint32_t fl = __shfl_sync(FULL, d.flags, s);
+      const uint32_t rk = __shfl_sync(FULL, d.rk, s);
+      const unsigned char* A;
+      int rows, np;
+      seg_geom<T, TN, TV>(sa, __shfl_sync(FULL, d.a8, s), rk, fl, A, rows, np);
+      int p0 = 0;  // panels of this segment issued so far
+      auto issue_stage = [&]() {
+        const int st = (int)(fill % kStages);
+        if (lane == 0) {
+          const int npst = min(kStagePanels, np - p0);
+          const unsigned bytes = (unsigned)(npst * rows * 16);  // contiguous panels of the tile
+          mbar_arrive_tx(P.full(st), bytes);
+          bulk_g2s(P.ring + st * kStageBytes, A + (int64_t)p0 * rows * 16, bytes, P.full(st));
+        }
+        ++fill;
+        p0 += kStagePanels;
+      };
+      auto stage_free_now = [&]() {
+        return fill < (uint32_t)kStages ||
+               mbar_test(P.empty((int)(fill % kStages)), ((fill / kStages) - 1) & 1);
+      };
+      if ((pr.notready >> s) & 1) {
+        // the block's panels do not depend on the input: put what fits in
+        // flight, then wait for the input vector block to be complete
+        while (p0 < np && stage_free_now()) issue_stage();
+        const int widx = __shfl_sync(FULL, d.wait_idx, s);
+        const int need = __shfl_sync(FULL, d.wait_cnt, s) * sa.nchunk;
+        int timeout = 0;
+        if (lane == 0) {
+          const long long t0 = clock64();
+          unsigned ns = 32;
+          for (unsigned spins = 1; ld_acquire(sa.counters + widx) < need; ++spins) {
+            if ((spins & 7) == 0) {
+              if (*abort_flag) {
+                timeout = 1;
+                break;
+              }
+              if (clock64() - t0 > kWaitCycles) {
+                atomicOr(L.status, kStatusTimeout);
+                *abort_flag = 1;
+                timeout = 1;
+                break;
+              }
+            }
+            __nanosleep(ns);
+            ns = ns < 256 ? 2 * ns : 256;
+          }
+        }
+        if (__shfl_sync(FULL, timeout, 0)) {
+          ok = false;
+          break;
+        }
       }
+      // the segment's input vector block
+      {
+        const int j = (int)(xfill & 1);
+        if (xfill >= 2 && !wait(P.xempty(j), ((xfill >> 1) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        const int xin = (fl >> 8) & 0xff;
+        const int k = (int)(rk >> 16);
+        const int xrow = __shfl_sync(FULL, d.x_row, s);
+        const TV* X = (xin == kInXh ? sa.xh : (xin == kInYh ? sa.yh : sa.xp)) + (int64_t)xrow * sa.R;
+        if (bulk) {
+          if (lane == 0) {
+            if ((pr.haswait >> s) & 1) fence_proxy_async_global();  // written by other warps
+            const unsigned bytes = (unsigned)(k * RC * sizeof(TV));
+            mbar_arrive_tx(P.xfull(j), bytes);
+            bulk_g2s(P.xslot(j), X, bytes, P.xfull(j));
+          }
+        } else {
+          TA* Xs = P.xslot(j);
+          const int c0 = u.c0;
+          const int kp = pad8(k);
+          for (int i = lane; i < kp * RC; i += 32) {
+            const int r = i / RC, c = i % RC;
+            Xs[i] = (r < k && c0 + c < sa.R) ? (TA)__ldcg(X + (int64_t)r * sa.R + c0 + c) : (TA)0;
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(P.xfull(j));
+        }
+        ++xfill;
+      }
+      // the rest of the segment's panels
+      while (p0 < np) {
+        if (fill >= (uint32_t)kStages &&
+            !wait(P.empty((int)(fill % kStages)), ((fill / kStages) - 1) & 1)) {
+          ok = false;
+          break;
+        }
+        issue_stage();
+        if (s == 0) fetch_next();
+      }
+      if (!ok) break;
     }
-    __syncwarp();
-    for (int p0 = 0; p0 < np; p0 += kStagePanels) {
-      const int s = (int)(w.use % kStages);
-      if (!mbar_wait(w.full + s, (w.use / kStages) & 1, abort_flag, L.status)) return false;
-      const unsigned char* stg = w.ring + s * kStageBytes;
-      const int npst = min(kStagePanels, np - p0);
-      if (is_near)
-        consume_stage<TN, TA, RC>(stg, rows * 16, npst, p0, w.Xs, rg, cg, acc);
-      else
-        consume_stage<T, TA, RC>(stg, rows * 16, npst, p0, w.Xs, rg, cg, acc);
-      ++w.use;
-      fence_proxy_async();
-      __syncwarp();
-      issue();  // refill the freed stage (possibly with the next segment's panels)
-    }
-    if (!it.flush) continue;
-    TV* obase = out == kOutXh ? sa.xh : (out == kOutYh ? sa.yh : sa.yp);
-    const int R = sa.R;
-    const int col0 = c0 + cg * Tl::CPL;
-    const int vc = min(Tl::CPL, R - col0);
-    const bool aligned = (R % 4) == 0 && (col0 % 4) == 0;
-#pragma unroll
-    for (int i = 0; i < Tl::RPL; ++i) {
-      const int r = rg + Tl::RG * i;
-      if (r < rows && vc > 0) add_row<Tl::CPL>(obase + (it.o_row + r) * R + col0, acc[i], vc, aligned);
-    }
-#pragma unroll
-    for (int i = 0; i < Tl::RPL; ++i)
-#pragma unroll
-      for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
-    if (it.sig_idx >= 0) {
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) atomicAdd(sa.counters + it.sig_idx, 1);
-    }
+    fetch_next();
+    if (chain)
+      cu = next;
+    else
+      fu = next;
   }
-  return true;
-}
-
-// Claim the next unit of a list; -1 once the list is exhausted.
-__device__ __forceinline__ int64_t claim(unsigned long long* next, int64_t total, int lane) {
-  unsigned long long v = 0;
-  if (lane == 0) v = atomicAdd(next, 1ull);
-  v = __shfl_sync(0xffffffffu, v, 0);
-  return (int64_t)v < total ? (int64_t)v : -1;
-}
-
-// Persistent product over all slots of a launch.  Two work lists: the
-// dependency chain (forward and backward transforms, couplings), claimed in
-// a dependency order, and the free list (near field), which waits for
-// nothing.  A warp whose chain group is not ready yet does free work
-// meanwhile, and blocks on the chain only when the free list is exhausted.
-template <typename T, typename TN, typename TA, typename TV, int RC>
-__global__ void __launch_bounds__(kThreads) k_h2_persistent(LaunchArgs L) {
-  using Tl = Tile<RC>;
-  const SlotArgs<TV>* slots = static_cast<const SlotArgs<TV>*>(L.slots);
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr size_t kRingBytes = (size_t)kStages * kStageBytes;
-  constexpr size_t kXBytes = sizeof(TA) * (size_t)kChunk * RC;
-  WarpRing<TA, RC> w;
-  w.ring = smem_raw + warp * warp_smem<TA, RC>();
-  w.Xs = reinterpret_cast<TA*>(w.ring + kRingBytes);
-  w.full = reinterpret_cast<uint64_t*>(w.ring + kRingBytes + kXBytes);
-  w.xbar = w.full + kStages;
-  w.fill = w.use = w.xuse = 0;
+  if (ok) ok = hand(-1, 0, 0);  // no more groups
+  // drain: every issued copy has landed before the warp exits
   if (lane == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(w.full + i, 1);
-    mbar_init(w.xbar, 1);
-    fence_mbar_init();
+    for (uint32_t f = fill > (uint32_t)kStages ? fill - kStages : 0; f < fill; ++f)
+      mbar_drain(P.full((int)(f % kStages)), (f / kStages) & 1);
+    for (uint32_t f = xfill > 2u ? xfill - 2 : 0; f < xfill; ++f) mbar_drain(P.xfull((int)(f & 1)), (f >> 1) & 1);
+    for (int dd = 0; dd < kDescSlots; ++dd)
+      if ((dland_pend >> dd) & 1) mbar_drain(P.dland(dd), (dland_par >> dd) & 1);
   }
   __syncwarp();
+}
 
+// ------------------------------------------------------------- consumer
+template <typename T, typename TN, typename TA, typename TV, int RC>
+__device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, const Pair<TA, RC>& P, int lane) {
+  using Tl = Tile<RC>;
+  constexpr unsigned FULL = 0xffffffffu;
+  volatile int* abort_flag = L.abort_flag;
+  const int rg = lane % Tl::RG, cg = lane / Tl::RG;
+  uint32_t use = 0, xuse = 0, ucnt = 0;
+  // A group that completes a vector bumps its counter with a release
+  // reduction, ordered after every lane's output reductions by the warp
+  // barrier (release is cumulative).  It is deferred to after the next
+  // stage or to before any wait that may depend on it, whichever comes
+  // first, so that it seldom waits for the reductions to be performed.
+  int* pending = nullptr;
+  auto signal = [&]() {
+    if (!pending) return;
+    __syncwarp();
+    if (lane == 0) red_release_add(pending, 1);
+    pending = nullptr;
+  };
   TA acc[Tl::RPL][Tl::CPL];
 #pragma unroll
   for (int i = 0; i < Tl::RPL; ++i)
 #pragma unroll
     for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
-
-  bool ok = true;
-  int64_t cu = claim(L.next, L.total, lane);
-  bool free_left = true;
-  while (ok) {
-    if (cu >= 0) {
-      const SlotArgs<TV>& sa = slots[find_slot(slots, L.nslots, cu)];
-      const int64_t lw = cu - sa.work_begin;
-      const int2 grp = sa.groups[lw / sa.nchunk];
-      if (free_left && !group_ready(sa, grp, lane)) {
-        const int64_t fu = claim(L.next_free, L.total_free, lane);
-        if (fu >= 0) {
-          const SlotArgs<TV>& sf = slots[find_free_slot(slots, L.nslots, fu)];
-          const int64_t lf = fu - sf.free_begin;
-          ok = run_group<T, TN, TA, TV, RC>(sf, sf.free_groups[lf / sf.nchunk], (int)(lf % sf.nchunk) * RC, w,
-                                            acc, L, lane);
-          continue;
-        }
-        free_left = false;
-      }
-      ok = run_group<T, TN, TA, TV, RC>(sa, grp, (int)(lw % sa.nchunk) * RC, w, acc, L, lane);
-      cu = claim(L.next, L.total, lane);
-      continue;
+  while (true) {
+    const int q = (int)(ucnt & 1);
+    if (pending && !mbar_test(P.ufull(q), (ucnt >> 1) & 1)) signal();
+    if (!mbar_wait(P.ufull(q), (ucnt >> 1) & 1, abort_flag, L.status)) return;
+    const int4 msg = P.queue[q];
+    ++ucnt;
+    if (msg.x < 0) {
+      signal();
+      return;
     }
-    if (!free_left) break;
-    const int64_t fu = claim(L.next_free, L.total_free, lane);
-    if (fu < 0) break;
-    const SlotArgs<TV>& sf = slots[find_free_slot(slots, L.nslots, fu)];
-    const int64_t lf = fu - sf.free_begin;
-    ok = run_group<T, TN, TA, TV, RC>(sf, sf.free_groups[lf / sf.nchunk], (int)(lf % sf.nchunk) * RC, w, acc,
-                                      L, lane);
+    const SlotArgs<TV>& sa = slots[msg.x];
+    const int c0 = msg.y;
+    const MvSeg d = read_seg(P.rec + msg.z * kMaxGroupSegs, lane);
+    const int nseg = count_segs(d, lane);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(P.dfree(msg.z));  // the record may be reused
+    const bool bulk = bulk_inputs<TV, RC>(sa);
+    for (int s = 0; s < nseg; ++s) {
+      const uint32_t fl = __shfl_sync(FULL, d.flags, s);
+      const uint32_t rk = __shfl_sync(FULL, d.rk, s);
+      const int rows = (int)(rk & 0xffff);
+      const int k = (int)(rk >> 16);
+      const int kp = pad8(k);
+      const int ain = fl & 0xff;
+      const bool is_near = ain == kN || ain == kNt;
+      const int np = kp / (is_near ? Panel<TN>::P : Panel<T>::P);
+      const int j = (int)(xuse & 1);
+      if (pending && !mbar_test(P.xfull(j), (xuse >> 1) & 1)) signal();
+      if (!mbar_wait(P.xfull(j), (xuse >> 1) & 1, abort_flag, L.status)) return;
+      TA* Xs = P.xslot(j);
+      if (bulk)  // rows beyond the block's columns meet zero panel columns: make them zero
+        for (int i = k * RC + lane; i < kp * RC; i += 32) Xs[i] = (TA)0;
+      __syncwarp();
+      for (int p0 = 0; p0 < np; p0 += kStagePanels) {
+        const int st = (int)(use % kStages);
+        if (pending && !mbar_test(P.full(st), (use / kStages) & 1)) signal();
+        if (!mbar_wait(P.full(st), (use / kStages) & 1, abort_flag, L.status)) return;
+        const unsigned char* stg = P.ring + st * kStageBytes;
+        const int npst = min(kStagePanels, np - p0);
+        if constexpr (sizeof(T) == sizeof(TN)) {
+          consume_stage<T, TA, RC>(stg, rows, npst, p0, Xs, rg, cg, acc);
+        } else {
+          if (is_near)
+            consume_stage<TN, TA, RC>(stg, rows, npst, p0, Xs, rg, cg, acc);
+          else
+            consume_stage<T, TA, RC>(stg, rows, npst, p0, Xs, rg, cg, acc);
+        }
+        ++use;
+        __syncwarp();  // every lane's reads of the stage have returned
+        if (lane == 0) mbar_arrive(P.empty(st));
+        signal();
+      }
+      // zero rows written above come before the producer's next copy into
+      // this buffer
+      if (bulk && k < kp) fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(P.xempty(j));
+      ++xuse;
+      if (!((fl >> 24) & 1)) continue;
+      // last segment: add the accumulated rows to the output
+      const int out = (fl >> 16) & 0xff;
+      TV* obase = out == kOutXh ? sa.xh : (out == kOutYh ? sa.yh : sa.yp);
+      const int o_row = __shfl_sync(FULL, d.o_row, s);
+      const int sig = __shfl_sync(FULL, d.sig_idx, s);
+      const int R = sa.R;
+      const int col0 = c0 + cg * Tl::CPL;
+      const int vc = min(Tl::CPL, R - col0);
+      const bool aligned = (R % 4) == 0 && (col0 % 4) == 0;
+#pragma unroll
+      for (int i = 0; i < Tl::RPL; ++i) {
+        const int r = rg + Tl::RG * i;
+        if (r < rows && vc > 0) add_row<Tl::CPL>(obase + ((int64_t)o_row + r) * R + col0, acc[i], vc, aligned);
+      }
+#pragma unroll
+      for (int i = 0; i < Tl::RPL; ++i)
+#pragma unroll
+        for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
+      if (sig >= 0) pending = sa.counters + sig;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(P.uempty(q));
   }
-  // drain: every issued copy has landed before the warp exits
-  if (lane == 0) {
-    for (uint32_t u = w.use; u < w.fill; ++u) mbar_drain(w.full + (u % kStages), (u / kStages) & 1);
-    if (w.xuse > 0) mbar_drain(w.xbar, (w.xuse - 1) & 1);
+}
+
+// Persistent product over all slots of a launch.  Two lists: the dependency
+// chain (forward and backward transforms, couplings), claimed in a
+// dependency order, and the free list (near field), which waits for
+// nothing.  A producer holds at most one chain group and one free group; it
+// hands its consumer the chain group when that is ready (or the free list is
+// used up) and the free group otherwise, and claims the successor on the
+// same list while it streams a group.
+// (float: two CTAs per SM within 128 registers a thread; double: one CTA,
+// whose buffers fill the shared memory and whose accumulators need more)
+template <typename T, typename TN, typename TA, typename TV, int RC>
+__global__ void __launch_bounds__(kThreads, sizeof(TA) == 8 ? 1 : 2) k_h2_persistent(LaunchArgs L) {
+  using PS = PairSmem<TA, RC>;
+  const SlotArgs<TV>* slots = static_cast<const SlotArgs<TV>*>(L.slots);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int pair = warp % kPairs;
+  unsigned char* base = smem_raw + pair * PS::kBytes;
+  Pair<TA, RC> P;
+  P.ring = base + PS::kRing;
+  P.xb = reinterpret_cast<TA*>(base + PS::kX);
+  P.rec = reinterpret_cast<MvSeg*>(base + PS::kDesc);
+  P.queue = reinterpret_cast<int4*>(base + PS::kQueue);
+  P.bar = reinterpret_cast<uint64_t*>(base + PS::kBar);
+  if (warp < kPairs && lane == 0) {
+    for (int i = 0; i < PS::kBars; ++i) mbar_init(P.bar + i, 1);
+    fence_mbar_init();
   }
-  __syncwarp();
+  __syncthreads();
+  if constexpr (kSplitRegs<TA>) {
+    // the producers need few registers, the consumers' tiles many: move
+    // registers from the producer warpgroup to the consumer warpgroup
+    // (kProducerRegs + kConsumerRegs = 2 * kLaunchRegs, checked on the host
+    // against the launch's register count)
+    if (warp >= kPairs) {
+      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
+      producer_loop<T, TN, TA, TV, RC>(L, slots, P, lane);
+    } else {
+      asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
+      consumer_loop<T, TN, TA, TV, RC>(L, slots, P, lane);
+    }
+  } else {
+    if (warp >= kPairs)
+      producer_loop<T, TN, TA, TV, RC>(L, slots, P, lane);
+    else
+      consumer_loop<T, TN, TA, TV, RC>(L, slots, P, lane);
+  }
 }
 
 }  // namespace
 
 // Claim order of the groups.  The emission order below is a valid
-// dependency order but makes CTAs claim groups long before their inputs
+// dependency order but makes warps claim groups long before their inputs
 // exist.  This list scheduler simulates the launch: kWorkers warps, a group
-// costs a fixed latency plus its bytes at a CTA's share of HBM bandwidth, a
+// costs a fixed latency plus its bytes at a warp's share of HBM bandwidth, a
 // group is ready once every counter it waits for has seen all of its
 // contributions, and among ready groups the one with the longest remaining
 // dependency path (upward rank) starts first.  Groups are then claimed in
 // simulated start order, which is again a dependency order (a group starts
 // only after everything it waits for has finished), so the launch stays
-// deadlock free.
-void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups, int ncounters) {
+// deadlock free.  The simulated start times are returned in `start` (claim
+// order) and the simulated end of the last group in `makespan`.
+void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups, int ncounters,
+                     std::vector<float>& start, float& makespan) {
   const int ng = (int)groups.size();
-  if (ng < 2) return;
-  constexpr double kWorkers = 148 * 16, kLatency = 2.0e-6, kBandwidth = 6.0e12;  // s, B/s
+  start.assign(ng, 0.f);
+  makespan = 0.f;
+  if (ng < 1) return;
+  constexpr double kWorkers = 148 * 8, kLatency = 2.0e-6, kBandwidth = 6.0e12;  // s, B/s
   std::vector<double> cost(ng);
   std::vector<int> sig(ng, -1);
   std::vector<std::vector<std::pair<int, int>>> waits(ng);
@@ -628,7 +1007,9 @@ void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups
   using Run = std::pair<double, int>;  // (finish, group), earliest first
   std::priority_queue<Run, std::vector<Run>, std::greater<Run>> running;
   std::vector<int> order;
+  std::vector<float> t_order;
   order.reserve(ng);
+  t_order.reserve(ng);
   double t = 0.0;
   int free_workers = (int)kWorkers;
   while ((int)order.size() < ng) {
@@ -636,6 +1017,7 @@ void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups
       const int gi = ready.top().second;
       ready.pop();
       order.push_back(gi);
+      t_order.push_back((float)t);
       running.push({t + cost[gi], gi});
       --free_workers;
     }
@@ -651,14 +1033,46 @@ void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups
         if (--pending[gw] == 0) ready.push({rank[gw], gw});
       }
   }
-  if ((int)order.size() != ng) return;  // keep the emission order
+  if ((int)order.size() != ng) {  // keep the emission order
+    for (int i = 0; i < ng; ++i) start[i] = (float)i / ng;
+    makespan = 1.f;
+    return;
+  }
+  while (!running.empty()) {
+    t = running.top().first;
+    running.pop();
+  }
   std::vector<int2> out(ng);
   for (int i = 0; i < ng; ++i) out[i] = groups[order[i]];
   groups.swap(out);
+  start.swap(t_order);
+  makespan = (float)t;
 }
 
+namespace {
+
+// host descriptor of a plan item
+int to_seg(const MvItem& it, MvSeg& s) {
+  if (it.a_off % 8 != 0 || it.a_off / 8 > 0xffffffffLL || it.x_row > INT32_MAX || it.o_row > INT32_MAX) {
+    set_error("internal: product plan offsets exceed the descriptor range");
+    return GCA_ERR_UNSUPPORTED;
+  }
+  s.a8 = (uint32_t)(it.a_off / 8);
+  s.x_row = (int32_t)it.x_row;
+  s.o_row = (int32_t)it.o_row;
+  s.rk = (uint32_t)std::min(kItemRows, it.m - it.a0) | ((uint32_t)it.k << 16);
+  s.flags = (uint32_t)(it.kind & 15) | ((uint32_t)((it.kind >> 4) & 15) << 8) |
+            ((uint32_t)((it.kind >> 8) & 15) << 16) | ((uint32_t)(it.flush ? 1 : 0) << 24);
+  s.wait_idx = it.wait_idx;
+  s.wait_cnt = it.wait_cnt;
+  s.sig_idx = it.sig_idx;
+  return GCA_OK;
+}
+
+}  // namespace
+
 // Work items of one direction (0: product, 1: transposed product).
-// Segments = (block, 128-row slice, 64-column chunk); groups = runs of
+// Segments = (block, 64-row slice, 64-column chunk); groups = runs of
 // segments with the same output rows claimed and accumulated together.
 int build_items(gca_h2* h, int dir, cudaStream_t st) {
   const int nc = h->nc;
@@ -674,9 +1088,12 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
     int64_t x_row;
     int wait_idx, wait_cnt;
   };
-  // one group per slice of rows [a0, a0 + 128) over a list of blocks sharing output rows
+  // one group per slice of rows [a0, a0 + 64) over a list of blocks sharing
+  // output rows; a segment covers `piece` columns of one tile (a multiple of
+  // 8 dividing kChunk: column kc of a tile starts at element kc * rows in
+  // every precision, so a piece is one contiguous run of panels)
   auto emit = [&](const std::vector<Blk>& blks, int in, int out, int64_t o_row0, int m, int sig_idx,
-                  int* sig_cnt, int max_segs) {
+                  int* sig_cnt, int max_segs, int piece) {
     for (int a0 = 0; a0 < m; a0 += kItemRows) {
       int start = (int)items.size();
       int segs = 0;
@@ -690,15 +1107,16 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
         segs = 0;
       };
       for (const Blk& b : blks)
-        for (int k0 = 0; k0 < b.k; k0 += kChunk) {
+        for (int k0 = 0; k0 < b.k; k0 += piece) {
           if (segs == max_segs) close();
           MvItem it{};
-          // the tile (a0, k0) of the block (tiled panel layout, panel.cuh)
+          // columns [k0, k0 + piece) of row slice a0 of the block (tiled
+          // panel layout, panel.cuh)
           it.a_off = b.a_off + (int64_t)a0 * pad8(b.k) + (int64_t)std::min(kItemRows, m - a0) * k0;
           it.x_row = b.x_row + k0;
           it.o_row = o_row0 + a0;
           it.m = m;
-          it.k = std::min(kChunk, b.k - k0);
+          it.k = std::min(piece, b.k - k0);
           it.a0 = a0;
           it.k0 = k0;
           it.kind = b.kind | (in << 4) | (out << 8);
@@ -713,26 +1131,28 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
     }
   };
   const auto& O = h->panel_off;
-  const int kCoupleSegs = 4, kNearSegs = 8;
+  const int kCoupleSegs = 8, kNearSegs = 8;
+  // segments of the transforms (the critical path of the product): one tile
+  // each, every tile of a transfer block in a group of its own, so that each
+  // step of the tree recursion is spread over many warps
+  const int kChainPiece = kChunk;
   // forward transform: leaves
   for (int c : h->leaves)
     if (c > 0 && h->rank[c] > 0)
       emit({{kVt, O[kVt][c], h->rank[c], h->end[c] - h->begin[c], h->begin[c], -1, 0}}, kInX, kOutXh,
-           h->xoff[c], h->rank[c], c, &cx[c], 1);
+           h->xoff[c], h->rank[c], c, &cx[c], 1, kChainPiece);
   // forward transform: up the tree, deepest level first (one segment per group:
-  // the chain is latency bound, so its work is spread over many CTAs)
+  // the chain is latency bound, so its work is spread over many warps)
   for (int L = h->depth - 1; L >= 1; --L)
     for (int p : h->by_level[L]) {
       if (h->child0[p] < 0) continue;
       for (int ch : {h->child0[p], h->child1[p]})
         emit({{kEt, O[kEt][ch], h->rank[p], h->rank[ch], h->xoff[ch], ch, cx[ch]}}, kInXh, kOutXh,
-             h->xoff[p], h->rank[p], p, &cx[p], 1);
+             h->xoff[p], h->rank[p], p, &cx[p], 1, kChainPiece);
     }
   // coupling: per output cluster, its blocks (deepest input first) in groups
   // of a few segments; clusters deepest first, since their inputs are ready
-  // first.  The near field has no dependencies and is placed after the
-  // couplings of the two deepest levels, as work for the CTAs while the
-  // forward transform climbs the tree.
+  // first.  The near field has no dependencies and goes to the free list.
   std::vector<std::vector<int>> far_by_own(nc);
   for (int b = 0; b < (int)h->far_t.size(); ++b)
     far_by_own[trans ? h->far_s[b] : h->far_t[b]].push_back(b);
@@ -740,7 +1160,7 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
   for (int c = 0; c < nc; ++c)
     if (!far_by_own[c].empty()) owners.push_back(c);
   std::stable_sort(owners.begin(), owners.end(), [&](int u, int v) { return h->level[u] > h->level[v]; });
-  auto emit_couple = [&](int own) {
+  for (int own : owners) {
     auto& bl = far_by_own[own];
     std::stable_sort(bl.begin(), bl.end(), [&](int u, int v) {
       const int iu = trans ? h->far_t[u] : h->far_s[u], iv = trans ? h->far_t[v] : h->far_s[v];
@@ -752,13 +1172,9 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
       blks.push_back({trans ? kSt : kS, O[trans ? kSt : kS][b], h->rank[own], h->rank[in], h->xoff[in], in,
                       cx[in]});
     }
-    emit(blks, kInXh, kOutYh, h->xoff[own], h->rank[own], nc + own, &cy[own], kCoupleSegs);
-  };
-  size_t oi = 0;
-  for (; oi < owners.size() && h->level[owners[oi]] >= h->depth - 1; ++oi) emit_couple(owners[oi]);
+    emit(blks, kInXh, kOutYh, h->xoff[own], h->rank[own], nc + own, &cy[own], kCoupleSegs, kChunk);
+  }
   {
-    // the near field waits for nothing: its own list, which warps work on
-    // while their chain groups wait for inputs
     target = &free_groups;
     std::vector<std::vector<int>> by_own(nc);
     for (int b = 0; b < (int)h->near_t.size(); ++b) by_own[trans ? h->near_s[b] : h->near_t[b]].push_back(b);
@@ -770,40 +1186,42 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
         blks.push_back({trans ? kNt : kN, O[trans ? kNt : kN][b], h->end[own] - h->begin[own],
                         h->end[in] - h->begin[in], h->begin[in], -1, 0});
       }
-      emit(blks, kInX, kOutY, h->begin[own], h->end[own] - h->begin[own], -1, nullptr, kNearSegs);
+      emit(blks, kInX, kOutY, h->begin[own], h->end[own] - h->begin[own], -1, nullptr, kNearSegs, kChunk);
     }
     target = &groups;
   }
-  for (; oi < owners.size(); ++oi) emit_couple(owners[oi]);
   // backward transform, level by level down (y-hat of the parent must be final)
   for (int L = 2; L <= h->depth; ++L)
     for (int c : h->by_level[L]) {
       const int p = h->parent[c];
       if (cy[p] == 0 || h->rank[c] == 0) continue;  // y-hat_p = 0
       emit({{kE, O[kE][c], h->rank[c], h->rank[p], h->xoff[p], nc + p, cy[p]}}, kInYh, kOutYh,
-           h->xoff[c], h->rank[c], nc + c, &cy[c], 1);
+           h->xoff[c], h->rank[c], nc + c, &cy[c], 1, kChainPiece);
     }
   // leaf bases
   for (int c : h->leaves)
     if (c > 0 && h->rank[c] > 0 && cy[c] > 0)
       emit({{kV, O[kV][c], h->end[c] - h->begin[c], h->rank[c], h->xoff[c], nc + c, cy[c]}}, kInYh,
-           kOutY, h->begin[c], h->end[c] - h->begin[c], -1, nullptr, 1);
-  for (const int2& g : groups)
-    if (g.y - g.x > kMaxGroupSegs) {
-      set_error("internal: work group longer than the per-warp descriptor cache");
-      return GCA_ERR_UNSUPPORTED;
-    }
-  for (const int2& g : free_groups)
-    if (g.y - g.x > kMaxGroupSegs) {
-      set_error("internal: work group longer than the per-warp descriptor cache");
-      return GCA_ERR_UNSUPPORTED;
-    }
-  schedule_groups(items, groups, 2 * nc);
-  h->n_items[dir] = (int64_t)groups.size();
+           kOutY, h->begin[c], h->end[c] - h->begin[c], -1, nullptr, 1, kChainPiece);
+  for (const auto* gl : {&groups, &free_groups})
+    for (const int2& g : *gl)
+      if (g.y - g.x > kMaxGroupSegs) {
+        set_error("internal: work group longer than a group record");
+        return GCA_ERR_UNSUPPORTED;
+      }
+  schedule_groups(items, groups, 2 * nc, h->chain_t[dir], h->makespan[dir]);
+  h->n_chain[dir] = (int64_t)groups.size();
   h->n_free[dir] = (int64_t)free_groups.size();
-  groups.insert(groups.end(), free_groups.begin(), free_groups.end());
-  GCA_TRY(upload(h->d_items[dir], items, st));
-  GCA_TRY(upload(h->d_groups[dir], groups, st));
+  // group records in claim order: chain groups, then free groups
+  std::vector<MvSeg> segs((groups.size() + free_groups.size()) * kMaxGroupSegs);
+  std::memset(segs.data(), 0, segs.size() * sizeof(MvSeg));
+  size_t gi = 0;
+  for (const auto* gl : {&groups, &free_groups})
+    for (const int2& g : *gl) {
+      for (int j = g.x; j < g.y; ++j) GCA_TRY(to_seg(items[j], segs[gi * kMaxGroupSegs + (j - g.x)]));
+      ++gi;
+    }
+  GCA_TRY(upload(h->d_segs[dir], segs, st));
   return GCA_OK;
 }
 
@@ -820,19 +1238,117 @@ namespace {
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }  // keeps every region aligned
 
+// Claim orders of a batch: every slot's list in its own order, the slots
+// interleaved by scheduled start time (chain) or by relative position
+// (free), so that all meshes progress together.
+void merge_claims(const gca_h2* const* hs, int count, int dir, const std::vector<int>& nchunk,
+                  std::vector<int2>& chain_map, std::vector<int2>& free_map) {
+  using Key = std::pair<float, int>;  // (time, slot)
+  chain_map.clear();
+  free_map.clear();
+  {
+    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> q;
+    std::vector<int64_t> pos(count, 0);
+    for (int s = 0; s < count; ++s)
+      if (hs[s]->n_chain[dir] > 0) q.push({hs[s]->chain_t[dir][0], s});
+    while (!q.empty()) {
+      const int s = q.top().second;
+      q.pop();
+      const int64_t g = pos[s]++;
+      for (int c = 0; c < nchunk[s]; ++c) chain_map.push_back(make_int2(s, (int)(g * nchunk[s] + c)));
+      if (pos[s] < hs[s]->n_chain[dir]) q.push({hs[s]->chain_t[dir][pos[s]], s});
+    }
+  }
+  {
+    std::priority_queue<Key, std::vector<Key>, std::greater<Key>> q;
+    std::vector<int64_t> pos(count, 0);
+    auto key = [&](int s) { return (float)((pos[s] + 0.5) / (double)hs[s]->n_free[dir]); };
+    for (int s = 0; s < count; ++s)
+      if (hs[s]->n_free[dir] > 0) q.push({key(s), s});
+    while (!q.empty()) {
+      const int s = q.top().second;
+      q.pop();
+      const int64_t g = pos[s]++;
+      for (int c = 0; c < nchunk[s]; ++c) free_map.push_back(make_int2(s, (int)(g * nchunk[s] + c)));
+      if (pos[s] < hs[s]->n_free[dir]) q.push({key(s), s});
+    }
+  }
+}
+
+template <typename T, typename TN, typename TV>
+void fill_slot(SlotArgs<TV>& a, const gca_h2* h, int dir, int R, int RC, const void* x, int64_t ldx,
+               void* y, int64_t ldy) {
+  const DevMem* P = sizeof(T) == 8 ? h->P64 : (sizeof(T) == 4 ? h->P32 : h->P16);
+  const DevMem* PN = sizeof(TN) == 8 ? h->P64 : h->P32;
+  for (int q = 0; q < kPanelKinds; ++q) a.A[q] = (q == kN || q == kNt) ? PN[q].p : P[q].p;
+  a.segs = h->d_segs[dir].as<MvSeg>();
+  a.n_chain = h->n_chain[dir];
+  a.n_free = h->n_free[dir];
+  a.R = R;
+  a.nchunk = (R + RC - 1) / RC;
+  a.n = h->n;
+  a.pad = 0;
+  a.x = static_cast<const TV*>(x);
+  a.ldx = ldx;
+  a.y = static_cast<TV*>(y);
+  a.ldy = ldy;
+  a.perm = h->d_perm.as<int>();
+}
+
+// Launches the persistent kernel with as many CTAs as fit on the device (found once per device and kernel, so that later launches
+// make no attribute or occupancy calls and can be graph captured).
+template <typename T, typename TN, typename TA, typename TV, int RC>
+int launch_persistent(const LaunchArgs& L, int64_t units, cudaStream_t st) {
+  const size_t smem = cta_smem<TA, RC>();
+  auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
+  static std::mutex mu;
+  static int64_t cap_by_dev[64] = {};
+  int dev = 0;
+  GCA_TRY_CUDA(cudaGetDevice(&dev));
+  int64_t cap = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    cap = dev >= 0 && dev < 64 ? cap_by_dev[dev] : 0;
+  }
+  if (cap == 0) {
+    if (smem > 48 * 1024)
+      GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if constexpr (kSplitRegs<TA>) {
+      // setmaxnreg moves registers inside the CTA's launch allocation: the
+      // split only balances if every thread was launched with kLaunchRegs
+      cudaFuncAttributes fa{};
+      GCA_TRY_CUDA(cudaFuncGetAttributes(&fa, kern));
+      if (fa.numRegs != kLaunchRegs) {
+        set_error("internal: product kernel compiled with " + std::to_string(fa.numRegs) +
+                  " registers a thread, the register split needs " + std::to_string(kLaunchRegs));
+        return GCA_ERR_UNSUPPORTED;
+      }
+    }
+    int sms = 0, per_sm = 0;
+    GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GCA_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    cap = (int64_t)sms * std::max(per_sm, 1);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64) cap_by_dev[dev] = cap;
+  }
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((units + kPairs - 1) / kPairs, cap));
+  kern<<<grid, kThreads, smem, st>>>(L);
+  return GCA_OK;
+}
+
 // One persistent launch over `count` handles (slots).  Workspace layout:
-// [claim counter, abort flag | per slot: x-hat, y-hat, y (cluster order),
+// [claim counters, abort flag | per slot: x-hat, y-hat, y (cluster order),
 // counters] zeroed by one memset, then per slot x (cluster order), then the
-// slot descriptors.
+// slot descriptors and (batches) the merged claim orders.
 template <typename T, typename TN, typename TA, typename TV, int RC>
 int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, const void* const* x,
               const int64_t* ldx, void* const* y, const int64_t* ldy, DevMem& ws,
               std::vector<unsigned char>& ws_cache, int* status, cudaStream_t st) {
   const char* pn = sizeof(T) == 8 ? ".f64" : (sizeof(T) == 4 ? ".f32" : ".bf16");
   PhaseScope ps(std::string("mv_persistent") + pn + (dir ? ".T" : ""), st);
-  ps.launches(4);
+  ps.launches(3);
   std::vector<SlotArgs<TV>> sl(count);
-  size_t off = 256;  // claim counter + abort flag
+  size_t off = 256;  // claim counters + abort flag
   std::vector<size_t> o_xh(count), o_yh(count), o_yp(count), o_cnt(count), o_xp(count);
   for (int i = 0; i < count; ++i) {
     const gca_h2* h = hs[i];
@@ -853,58 +1369,63 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   }
   const size_t o_slots = off;
   off += up256(sizeof(SlotArgs<TV>) * count);
-  if (off > ws.bytes) ws_cache.clear();
-  GCA_TRY(ws.reserve(off));
-  unsigned char* base = ws.as<unsigned char>();
+  std::vector<int> nchunk(count);
   int64_t work = 0, free_work = 0;
   int max_n = 0;
   for (int i = 0; i < count; ++i) {
-    const gca_h2* h = hs[i];
+    nchunk[i] = (nrhs[i] + RC - 1) / RC;
+    work += hs[i]->n_chain[dir] * nchunk[i];
+    free_work += hs[i]->n_free[dir] * nchunk[i];
+    max_n = std::max(max_n, hs[i]->n * nrhs[i]);
+  }
+  const size_t o_cmap = off;
+  if (count > 1) off += up256(sizeof(int2) * (size_t)std::max<int64_t>(work, 1));
+  const size_t o_fmap = off;
+  if (count > 1) off += up256(sizeof(int2) * (size_t)std::max<int64_t>(free_work, 1));
+  if (off > ws.bytes) ws_cache.clear();
+  GCA_TRY(ws.reserve(off));
+  unsigned char* base = ws.as<unsigned char>();
+  for (int i = 0; i < count; ++i) {
     SlotArgs<TV>& a = sl[i];
-    const DevMem* P = sizeof(T) == 8 ? h->P64 : (sizeof(T) == 4 ? h->P32 : h->P16);
-    const DevMem* PN = sizeof(TN) == 8 ? h->P64 : h->P32;
-    for (int q = 0; q < kPanelKinds; ++q) a.A[q] = (q == kN || q == kNt) ? PN[q].p : P[q].p;
-    a.items = h->d_items[dir].as<MvItem>();
-    a.groups = h->d_groups[dir].as<int2>();
-    a.free_groups = a.groups + h->n_items[dir];
-    a.R = nrhs[i];
-    a.nchunk = (a.R + RC - 1) / RC;
-    a.n_work = h->n_items[dir] * a.nchunk;
-    a.work_begin = work;
-    work += a.n_work;
-    a.n_free = h->n_free[dir] * a.nchunk;
-    a.free_begin = free_work;
-    free_work += a.n_free;
-    a.n = h->n;
-    a.x = static_cast<const TV*>(x[i]);
-    a.ldx = ldx[i];
-    a.y = static_cast<TV*>(y[i]);
-    a.ldy = ldy[i];
-    a.perm = h->d_perm.as<int>();
+    fill_slot<T, TN, TV>(a, hs[i], dir, nrhs[i], RC, x[i], ldx[i], y[i], ldy[i]);
     a.xh = reinterpret_cast<TV*>(base + o_xh[i]);
     a.yh = reinterpret_cast<TV*>(base + o_yh[i]);
     a.yp = reinterpret_cast<TV*>(base + o_yp[i]);
     a.counters = reinterpret_cast<int*>(base + o_cnt[i]);
     a.xp = reinterpret_cast<TV*>(base + o_xp[i]);
-    max_n = std::max(max_n, h->n * a.R);
   }
   LaunchArgs L;
   L.slots = base + o_slots;
   L.nslots = count;
+  L.chain_map = count > 1 ? reinterpret_cast<const int2*>(base + o_cmap) : nullptr;
+  L.free_map = count > 1 ? reinterpret_cast<const int2*>(base + o_fmap) : nullptr;
   L.total = work;
   L.total_free = free_work;
   L.next = reinterpret_cast<unsigned long long*>(base);
   L.next_free = reinterpret_cast<unsigned long long*>(base + 8);
   L.abort_flag = reinterpret_cast<int*>(base + 16);
   L.status = status;
-  // the descriptors change only with the arguments: upload when they differ
-  // from what the workspace already holds
+  // the descriptors (and claim orders) change only with the arguments:
+  // upload when they differ from what the workspace already holds
   const size_t sbytes = sizeof(SlotArgs<TV>) * count;
   if (ws_cache.size() != sbytes + sizeof(void*) ||
       std::memcmp(ws_cache.data(), sl.data(), sbytes) != 0 ||
       std::memcmp(ws_cache.data() + sbytes, &base, sizeof(void*)) != 0) {
     GCA_TRY_CUDA(cudaMemcpyAsync(base + o_slots, sl.data(), sbytes, cudaMemcpyHostToDevice, st));
-    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // sl is a stack vector
+    std::vector<int2> cmap, fmap;
+    if (count > 1) {
+      merge_claims(hs, count, dir, nchunk, cmap, fmap);
+      if ((int64_t)cmap.size() != work || (int64_t)fmap.size() != free_work) {
+        set_error("internal: merged claim order has the wrong length");
+        return GCA_ERR_UNSUPPORTED;
+      }
+      if (work > 0)
+        GCA_TRY_CUDA(cudaMemcpyAsync(base + o_cmap, cmap.data(), sizeof(int2) * work, cudaMemcpyHostToDevice, st));
+      if (free_work > 0)
+        GCA_TRY_CUDA(
+            cudaMemcpyAsync(base + o_fmap, fmap.data(), sizeof(int2) * free_work, cudaMemcpyHostToDevice, st));
+    }
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // sl, cmap, fmap are host vectors of this frame
     ws_cache.assign(reinterpret_cast<const unsigned char*>(sl.data()),
                     reinterpret_cast<const unsigned char*>(sl.data()) + sbytes);
     ws_cache.insert(ws_cache.end(), reinterpret_cast<const unsigned char*>(&base),
@@ -914,34 +1435,7 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   const auto* d_slots = reinterpret_cast<const SlotArgs<TV>*>(base + o_slots);
   const unsigned gx = (unsigned)std::min<int64_t>(1024, (max_n + 255) / 256);
   k_gather<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots);
-  if (work + free_work > 0) {
-    const size_t smem = cta_smem<TA, RC>();
-    auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
-    // resident CTAs on the device, found once per device (later launches
-    // make no attribute or occupancy calls, so they can be graph captured)
-    static std::mutex mu;
-    static int64_t cap_by_dev[64] = {};
-    int dev = 0;
-    GCA_TRY_CUDA(cudaGetDevice(&dev));
-    int64_t cap = 0;
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      cap = dev >= 0 && dev < 64 ? cap_by_dev[dev] : 0;
-    }
-    if (cap == 0) {
-      if (smem > 48 * 1024)
-        GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      int sms = 0, per_sm = 0;
-      GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      GCA_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-      cap = (int64_t)sms * std::max(per_sm, 1);
-      std::lock_guard<std::mutex> lk(mu);
-      if (dev >= 0 && dev < 64) cap_by_dev[dev] = cap;
-    }
-    const unsigned grid =
-        (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + free_work + kWarps - 1) / kWarps, cap));
-    kern<<<grid, kThreads, smem, st>>>(L);
-  }
+  if (work + free_work > 0) GCA_TRY((launch_persistent<T, TN, TA, TV, RC>(L, work + free_work, st)));
   k_scatter<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots);
   GCA_TRY_CUDA(cudaGetLastError());
   return GCA_OK;
@@ -1095,24 +1589,7 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
     return GCA_ERR_UNSUPPORTED;
   }
   SlotArgs<TV> a{};
-  const DevMem* P = sizeof(T) == 8 ? h->P64 : (sizeof(T) == 4 ? h->P32 : h->P16);
-  const DevMem* PN = sizeof(TN) == 8 ? h->P64 : h->P32;
-  for (int q = 0; q < kPanelKinds; ++q) a.A[q] = (q == kN || q == kNt) ? PN[q].p : P[q].p;
-  a.items = h->d_items[0].as<MvItem>();
-  a.groups = h->d_groups[0].as<int2>();
-  a.free_groups = a.groups + h->n_items[0];
-  a.R = R;
-  a.nchunk = (R + RC - 1) / RC;
-  a.n_work = h->n_items[0] * a.nchunk;
-  a.work_begin = 0;
-  a.n_free = h->n_free[0] * a.nchunk;
-  a.free_begin = 0;
-  a.n = h->n;
-  a.x = static_cast<const TV*>(x);
-  a.ldx = ldx;
-  a.y = static_cast<TV*>(y);
-  a.ldy = ldy;
-  a.perm = h->d_perm.as<int>();
+  fill_slot<T, TN, TV>(a, h, 0, R, RC, x, ldx, y, ldy);
   a.xh = reinterpret_cast<TV*>(base + o_xh);
   a.yh = reinterpret_cast<TV*>(base + o_yh);
   a.yp = reinterpret_cast<TV*>(base + o_yp);
@@ -1121,13 +1598,15 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   LaunchArgs L;
   L.slots = base + o_slot;
   L.nslots = 1;
-  L.total = a.n_work;
-  L.total_free = a.n_free;
+  L.chain_map = nullptr;
+  L.free_map = nullptr;
+  L.total = a.n_chain * a.nchunk;
+  L.total_free = a.n_free * a.nchunk;
   L.next = reinterpret_cast<unsigned long long*>(base);
   L.next_free = reinterpret_cast<unsigned long long*>(base + 8);
   L.abort_flag = reinterpret_cast<int*>(base + 16);
   L.status = h->d_status.as<int>();
-  // the array keeps the previous call's contents: the claim counter, abort
+  // the array keeps the previous call's contents: the claim counters, abort
   // flag, x-hat, y-hat, y and the counters must start at zero
   GCA_TRY_CUDA(cudaMemsetAsync(base, 0, zeroed, st));
   // the descriptor travels as a kernel argument: no host buffer to keep alive
@@ -1135,20 +1614,7 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   k_put_slot<TV><<<1, 1, 0, st>>>(a, d_slots);
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, ((int64_t)h->n * R + 255) / 256));
   k_gather<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots);
-  if (a.n_work + a.n_free > 0) {
-    const size_t smem = cta_smem<TA, RC>();
-    auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
-    if (smem > 48 * 1024)
-      GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int dev = 0, sms = 0, per_sm = 0;
-    GCA_TRY_CUDA(cudaGetDevice(&dev));
-    GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    GCA_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    const int64_t capc = (int64_t)sms * std::max(per_sm, 1);
-    const unsigned grid =
-        (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.n_work + a.n_free + kWarps - 1) / kWarps, capc));
-    kern<<<grid, kThreads, smem, st>>>(L);
-  }
+  if (L.total + L.total_free > 0) GCA_TRY((launch_persistent<T, TN, TA, TV, RC>(L, L.total + L.total_free, st)));
   k_scatter<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots);
   GCA_TRY_CUDA(cudaGetLastError());
   return GCA_OK;
