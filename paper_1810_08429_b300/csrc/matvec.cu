@@ -46,6 +46,7 @@
 #include <mutex>
 #include <queue>
 #include <string>
+#include <type_traits>
 
 #include "internal.hpp"
 #include "panel.cuh"
@@ -126,6 +127,7 @@ struct LaunchArgs {
   unsigned long long* next_free;  // free claim counter
   int* status;
   int* abort_flag;             // raised by any timed-out wait; every wait gives up
+  const void* zeros;           // kZeroBytes of zeros (pads input blocks)
 };
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -158,6 +160,7 @@ constexpr int kStagePanels = 4;
 constexpr int kStageBytes = kStagePanels * kItemRows * 16;  // 4 KB: one contiguous copy
 constexpr int kStages = 4;
 constexpr int kDescSlots = 4;                               // records: chain 0, 1; free 2, 3
+constexpr size_t kZeroBytes = (size_t)kChunk * 16 * 8;      // a full input block of doubles
 // bound of every mbarrier wait, in SM clock cycles (about a second)
 constexpr long long kWaitCycles = 1LL << 31;
 // a waiting warp sleeps until the phase completes or this many ns pass
@@ -259,11 +262,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
-}
-// orders this thread's generic-proxy shared-memory accesses before later
-// bulk copies (async proxy) into the same buffers
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 // orders global-memory writes seen through an acquire before later bulk
 // copies (async proxy) that read them
@@ -468,6 +466,88 @@ __device__ __forceinline__ void consume_stage(const unsigned char* stage, int ro
   }
 }
 
+// ------------------------------------------- bfloat16 blocks on tensor cores
+//
+// In the bfloat16 product the stored V, E and S panels are bfloat16 and the
+// products run on the tensor cores (mma.sync m16n8k16, bfloat16 operands,
+// float accumulation).  The panel layout already is the operand layout of
+// ldmatrix: a panel row is one 16-byte row of an 8 x 8 matrix, two
+// consecutive panels are the two k halves of a 16 x 16 A fragment.  The
+// staged float input rows are split into bfloat16 hi + lo parts (x = hi + lo
+// to 16 bits), so that the input is not rounded to 8 bits; each k step is
+// two products.  Warp tile: 64 rows (four m16 tiles) x RC columns (RC / 8
+// n8 tiles); lane (g, t) = (lane / 4, lane % 4) holds rows g, g + 8 and
+// columns 2t, 2t + 1 of each m16 x n8 accumulator.
+template <typename T, int RC>
+constexpr bool kTensorCore = std::is_same<T, __nv_bfloat16>::value && (RC == 8 || RC == 16);
+
+__device__ __forceinline__ void ldmatrix_x4(unsigned addr, unsigned (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// two floats as bfloat16 (round to nearest), the first in the low half
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  unsigned r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// x = hi + lo with hi, lo bfloat16 pairs
+__device__ __forceinline__ void split_bf16(float x0, float x1, unsigned& hi, unsigned& lo) {
+  hi = pack_bf16(x0, x1);
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+  lo = pack_bf16(x0 - h0, x1 - h1);
+}
+
+// One ring stage of bfloat16 panels (npst of them, `rows` rows each) on the
+// tensor cores.  p0: the stage's first panel within the segment.
+template <int RC>
+__device__ __forceinline__ void mma_stage(const unsigned char* stage, int rows, int npst, int p0,
+                                          const float* __restrict__ Xs, int lane, float (&accm)[4][RC / 8][4]) {
+  constexpr int NT = RC / 8;
+  const int g = lane >> 2, t = lane & 3;
+  const int q = lane >> 3, r8 = lane & 7;
+  const int pst = rows * 16;
+  const int mtiles = (rows + 15) >> 4;
+  const unsigned sbase = smem_u32(stage);
+  for (int pp = 0; pp < npst; pp += 2) {
+    const bool two = pp + 1 < npst;  // a last single panel is the lower k half only
+    const int kb = (p0 + pp) * 8;    // first input row of the k step
+    unsigned bh[NT][2], bl[NT][2];
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const float* xc = Xs + (kb + 2 * t) * RC + 8 * nt + g;
+      split_bf16(xc[0], xc[RC], bh[nt][0], bl[nt][0]);
+      split_bf16(xc[8 * RC], xc[9 * RC], bh[nt][1], bl[nt][1]);
+    }
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+      if (mt >= mtiles) break;
+      unsigned a[4];
+      const int row = 16 * mt + r8 + 8 * (q & 1);
+      const int panel = pp + (two ? (q >> 1) : 0);
+      ldmatrix_x4(sbase + panel * pst + row * 16, a);
+      if (!two) a[2] = a[3] = 0u;
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        mma_bf16(accm[mt][nt], a, bh[nt][0], bh[nt][1]);
+        mma_bf16(accm[mt][nt], a, bl[nt][0], bl[nt][1]);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void red_add2(float* p, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
 // Shared-memory regions and mbarriers of one pair.
 template <typename TA, int RC>
 struct Pair {
@@ -552,7 +632,60 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
   uint32_t fill = 0, xfill = 0, uhand = 0;
   uint32_t dland_par = 0, dland_pend = 0, dfree_par = 0, dused = 0;
   bool ok = true;
-  auto wait = [&](uint64_t* b, unsigned par) { return mbar_wait<512>(b, par, abort_flag, L.status); };
+  // Counter signals.  A group that completes a vector bumps the vector's
+  // counter once its consumer has added its rows to the output.  The
+  // consumer reduces, passes a warp barrier and arrives on the group's queue
+  // entry (uempty, a release at CTA scope); the producer observes that
+  // arrival and increments the counter with a release reduction at GPU
+  // scope, which is cumulative over the consumer's reductions.  The consumer
+  // never waits for its reductions to be performed; the producer does, in
+  // time it would otherwise spend waiting.
+  uint32_t usig = 0;                             // handed groups whose signal is done
+  int* sig_q0 = nullptr;                         // counter of the group in queue entry 0
+  int* sig_q1 = nullptr;                         // ... entry 1
+  auto sig_one = [&](bool block) -> bool {       // retire the oldest handed group
+    if (usig == uhand) return false;
+    const int q = (int)(usig & 1);
+    const unsigned par = (usig >> 1) & 1;
+    if (block) {
+      if (!mbar_wait<512>(P.uempty(q), par, abort_flag, L.status)) {
+        ok = false;
+        return false;
+      }
+    } else if (!mbar_test(P.uempty(q), par)) {
+      return false;
+    }
+    int* c = q ? sig_q1 : sig_q0;
+    if (c && lane == 0) red_release_add(c, 1);
+    __syncwarp();
+    ++usig;
+    return true;
+  };
+  auto sig_poll = [&]() {
+    while (sig_one(false)) {
+    }
+  };
+  // bounded wait that keeps delivering counter signals meanwhile
+  auto wait = [&](uint64_t* b, unsigned par) -> bool {
+    if (mbar_try_wait(b, par)) return true;
+    const long long t0 = clock64();
+    unsigned ns = 16;
+    for (unsigned it = 1;; ++it) {
+      sig_poll();
+      if (!ok) return false;
+      __nanosleep(ns);
+      ns = ns < 512 ? 2 * ns : 512;
+      if (mbar_try_wait(b, par)) return true;
+      if ((it & 15) == 0) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+          atomicOr(L.status, kStatusTimeout);
+          *abort_flag = 1;
+          return false;
+        }
+      }
+    }
+  };
 
   // copy the record of claim c of a list into record d (after the consumer
   // has released d's previous record)
@@ -610,10 +743,18 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
     v = __shfl_sync(FULL, v, 0);
     return (int64_t)v < total ? (int64_t)v : -1;
   };
-  // hand group (slot, c0, record d) to the consumer
-  auto hand = [&](int slot, int c0, int d) -> bool {
+  // hand group (slot, c0, record d) to the consumer; `sig`: the counter it
+  // bumps when done (null: none)
+  auto hand = [&](int slot, int c0, int d, int* sig) -> bool {
     const int q = (int)(uhand & 1);
     if (uhand >= 2 && !wait(P.uempty(q), ((uhand >> 1) - 1) & 1)) return false;
+    // the group that used this entry is done: its signal goes out first
+    while (usig + 2 <= uhand)
+      if (!sig_one(true)) return false;
+    if (q)
+      sig_q1 = sig;
+    else
+      sig_q0 = sig;
     if (lane == 0) {
       P.queue[q] = make_int4(slot, c0, d, 0);
       mbar_arrive(P.ufull(q));
@@ -663,7 +804,10 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
       break;
     }
     const SlotArgs<TV>& sa = slots[u.slot];
-    if (!(ok = hand(u.slot, u.c0, u.dslot))) break;
+    {
+      const int sig = __shfl_sync(FULL, pr.d.sig_idx, pr.nseg - 1);
+      if (!(ok = hand(u.slot, u.c0, u.dslot, sig >= 0 ? sa.counters + sig : nullptr))) break;
+    }
     // claim the successor on the same list; its record is fetched once the
     // first data of this group is on its way
     unsigned long long* ctr = chain ? L.next : L.next_free;
@@ -708,20 +852,28 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
         while (p0 < np && stage_free_now()) issue_stage();
         const int widx = __shfl_sync(FULL, d.wait_idx, s);
         const int need = __shfl_sync(FULL, d.wait_cnt, s) * sa.nchunk;
-        int timeout = 0;
-        if (lane == 0) {
+        bool timeout = false;
+        {
           const long long t0 = clock64();
           unsigned ns = 32;
-          for (unsigned spins = 1; ld_acquire(sa.counters + widx) < need; ++spins) {
+          for (unsigned spins = 1;; ++spins) {
+            int v = 0;
+            if (lane == 0) v = ld_acquire(sa.counters + widx);  // lane 0 issues the copy below
+            if (__shfl_sync(FULL, v, 0) >= need) break;
+            sig_poll();
+            if (!ok) {
+              timeout = true;
+              break;
+            }
             if ((spins & 7) == 0) {
               if (*abort_flag) {
-                timeout = 1;
+                timeout = true;
                 break;
               }
               if (clock64() - t0 > kWaitCycles) {
                 atomicOr(L.status, kStatusTimeout);
                 *abort_flag = 1;
-                timeout = 1;
+                timeout = true;
                 break;
               }
             }
@@ -729,7 +881,7 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
             ns = ns < 256 ? 2 * ns : 256;
           }
         }
-        if (__shfl_sync(FULL, timeout, 0)) {
+        if (timeout) {
           ok = false;
           break;
         }
@@ -745,17 +897,24 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
         const int k = (int)(rk >> 16);
         const int xrow = __shfl_sync(FULL, d.x_row, s);
         const TV* X = (xin == kInXh ? sa.xh : (xin == kInYh ? sa.yh : sa.xp)) + (int64_t)xrow * sa.R;
+        // rows past the block's columns meet zero panel columns (and, on the
+        // tensor cores, the zeroed upper half of a last single panel): they
+        // are copied in as zeros, so the buffer only ever gets bulk copies
+        const int ain = fl & 0xff;
+        const int kz = (kTensorCore<T, RC> && ain != kN && ain != kNt) ? (k + 15) & ~15 : pad8(k);
         if (bulk) {
           if (lane == 0) {
             if ((pr.haswait >> s) & 1) fence_proxy_async_global();  // written by other warps
             const unsigned bytes = (unsigned)(k * RC * sizeof(TV));
-            mbar_arrive_tx(P.xfull(j), bytes);
+            const unsigned zb = (unsigned)((kz - k) * RC * sizeof(TV));
+            mbar_arrive_tx(P.xfull(j), bytes + zb);
             bulk_g2s(P.xslot(j), X, bytes, P.xfull(j));
+            if (zb) bulk_g2s(P.xslot(j) + (size_t)k * RC, L.zeros, zb, P.xfull(j));
           }
         } else {
           TA* Xs = P.xslot(j);
           const int c0 = u.c0;
-          const int kp = pad8(k);
+          const int kp = kz;
           for (int i = lane; i < kp * RC; i += 32) {
             const int r = i / RC, c = i % RC;
             Xs[i] = (r < k && c0 + c < sa.R) ? (TA)__ldcg(X + (int64_t)r * sa.R + c0 + c) : (TA)0;
@@ -773,6 +932,7 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
           break;
         }
         issue_stage();
+        sig_poll();
         if (s == 0) fetch_next();
       }
       if (!ok) break;
@@ -783,7 +943,10 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
     else
       fu = next;
   }
-  if (ok) ok = hand(-1, 0, 0);  // no more groups
+  // the last signals, then: no more groups
+  while (ok && usig < uhand)
+    if (!sig_one(true)) break;
+  if (ok) ok = hand(-1, 0, 0, nullptr);
   // drain: every issued copy has landed before the warp exits
   if (lane == 0) {
     for (uint32_t f = fill > (uint32_t)kStages ? fill - kStages : 0; f < fill; ++f)
@@ -803,33 +966,26 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
   volatile int* abort_flag = L.abort_flag;
   const int rg = lane % Tl::RG, cg = lane / Tl::RG;
   uint32_t use = 0, xuse = 0, ucnt = 0;
-  // A group that completes a vector bumps its counter with a release
-  // reduction, ordered after every lane's output reductions by the warp
-  // barrier (release is cumulative).  It is deferred to after the next
-  // stage or to before any wait that may depend on it, whichever comes
-  // first, so that it seldom waits for the reductions to be performed.
-  int* pending = nullptr;
-  auto signal = [&]() {
-    if (!pending) return;
-    __syncwarp();
-    if (lane == 0) red_release_add(pending, 1);
-    pending = nullptr;
-  };
   TA acc[Tl::RPL][Tl::CPL];
 #pragma unroll
   for (int i = 0; i < Tl::RPL; ++i)
 #pragma unroll
     for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
+  constexpr bool kTC = kTensorCore<T, RC>;
+  constexpr int NT = RC >= 8 ? RC / 8 : 1;
+  float accm[4][NT][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) accm[i][nt][e] = 0.f;
   while (true) {
     const int q = (int)(ucnt & 1);
-    if (pending && !mbar_test(P.ufull(q), (ucnt >> 1) & 1)) signal();
     if (!mbar_wait(P.ufull(q), (ucnt >> 1) & 1, abort_flag, L.status)) return;
     const int4 msg = P.queue[q];
     ++ucnt;
-    if (msg.x < 0) {
-      signal();
-      return;
-    }
+    if (msg.x < 0) return;
     const SlotArgs<TV>& sa = slots[msg.x];
     const int c0 = msg.y;
     const MvSeg d = read_seg(P.rec + msg.z * kMaxGroupSegs, lane);
@@ -837,6 +993,13 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
     __syncwarp();
     if (lane == 0) mbar_arrive(P.dfree(msg.z));  // the record may be reused
     const bool bulk = bulk_inputs<TV, RC>(sa);
+    // bfloat16 far-field groups run on the tensor cores (all segments of a
+    // group are of one kind)
+    bool tc = false;
+    if constexpr (kTC) {
+      const int ain0 = __shfl_sync(FULL, d.flags, 0) & 0xff;
+      tc = ain0 != kN && ain0 != kNt;
+    }
     for (int s = 0; s < nseg; ++s) {
       const uint32_t fl = __shfl_sync(FULL, d.flags, s);
       const uint32_t rk = __shfl_sync(FULL, d.rk, s);
@@ -847,20 +1010,20 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
       const bool is_near = ain == kN || ain == kNt;
       const int np = kp / (is_near ? Panel<TN>::P : Panel<T>::P);
       const int j = (int)(xuse & 1);
-      if (pending && !mbar_test(P.xfull(j), (xuse >> 1) & 1)) signal();
       if (!mbar_wait(P.xfull(j), (xuse >> 1) & 1, abort_flag, L.status)) return;
-      TA* Xs = P.xslot(j);
-      if (bulk)  // rows beyond the block's columns meet zero panel columns: make them zero
-        for (int i = k * RC + lane; i < kp * RC; i += 32) Xs[i] = (TA)0;
-      __syncwarp();
+      const TA* Xs = P.xslot(j);  // padded with zero rows by the producer
       for (int p0 = 0; p0 < np; p0 += kStagePanels) {
         const int st = (int)(use % kStages);
-        if (pending && !mbar_test(P.full(st), (use / kStages) & 1)) signal();
         if (!mbar_wait(P.full(st), (use / kStages) & 1, abort_flag, L.status)) return;
         const unsigned char* stg = P.ring + st * kStageBytes;
         const int npst = min(kStagePanels, np - p0);
         if constexpr (sizeof(T) == sizeof(TN)) {
           consume_stage<T, TA, RC>(stg, rows, npst, p0, Xs, rg, cg, acc);
+        } else if constexpr (kTC) {
+          if (tc)
+            mma_stage<RC>(stg, rows, npst, p0, reinterpret_cast<const float*>(Xs), lane, accm);
+          else
+            consume_stage<TN, TA, RC>(stg, rows, npst, p0, Xs, rg, cg, acc);
         } else {
           if (is_near)
             consume_stage<TN, TA, RC>(stg, rows, npst, p0, Xs, rg, cg, acc);
@@ -870,11 +1033,7 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
         ++use;
         __syncwarp();  // every lane's reads of the stage have returned
         if (lane == 0) mbar_arrive(P.empty(st));
-        signal();
       }
-      // zero rows written above come before the producer's next copy into
-      // this buffer
-      if (bulk && k < kp) fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(P.xempty(j));
       ++xuse;
@@ -883,8 +1042,35 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
       const int out = (fl >> 16) & 0xff;
       TV* obase = out == kOutXh ? sa.xh : (out == kOutYh ? sa.yh : sa.yp);
       const int o_row = __shfl_sync(FULL, d.o_row, s);
-      const int sig = __shfl_sync(FULL, d.sig_idx, s);
       const int R = sa.R;
+      if constexpr (kTC) {
+        if (tc) {
+          // accumulator fragments: rows 16 mt + g (+ 8), columns 8 nt + 2t (+ 1)
+          const int g = lane >> 2, t = lane & 3;
+          const bool even = (R % 2) == 0;
+#pragma unroll
+          for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < NT; ++nt) {
+              const int col = c0 + 8 * nt + 2 * t;
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int r = 16 * mt + g + 8 * h;
+                float* o = reinterpret_cast<float*>(obase) + ((int64_t)o_row + r) * R + col;
+                if (r < rows && col < R) {
+                  if (even && col + 1 < R) {
+                    red_add2(o, accm[mt][nt][2 * h], accm[mt][nt][2 * h + 1]);
+                  } else {
+                    red_add(o, accm[mt][nt][2 * h]);
+                    if (col + 1 < R) red_add(o + 1, accm[mt][nt][2 * h + 1]);
+                  }
+                }
+                accm[mt][nt][2 * h] = accm[mt][nt][2 * h + 1] = 0.f;
+              }
+            }
+          continue;
+        }
+      }
       const int col0 = c0 + cg * Tl::CPL;
       const int vc = min(Tl::CPL, R - col0);
       const bool aligned = (R % 4) == 0 && (col0 % 4) == 0;
@@ -897,8 +1083,9 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
       for (int i = 0; i < Tl::RPL; ++i)
 #pragma unroll
         for (int c = 0; c < Tl::CPL; ++c) acc[i][c] = (TA)0;
-      if (sig >= 0) pending = sa.counters + sig;
     }
+    // every lane's output reductions come before this arrival: the producer
+    // signals the group's counter once it sees it
     __syncwarp();
     if (lane == 0) mbar_arrive(P.uempty(q));
   }
@@ -1348,7 +1535,7 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   PhaseScope ps(std::string("mv_persistent") + pn + (dir ? ".T" : ""), st);
   ps.launches(3);
   std::vector<SlotArgs<TV>> sl(count);
-  size_t off = 256;  // claim counters + abort flag
+  size_t off = 256 + kZeroBytes;  // claim counters + abort flag, zeros
   std::vector<size_t> o_xh(count), o_yh(count), o_yp(count), o_cnt(count), o_xp(count);
   for (int i = 0; i < count; ++i) {
     const gca_h2* h = hs[i];
@@ -1404,6 +1591,7 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   L.next = reinterpret_cast<unsigned long long*>(base);
   L.next_free = reinterpret_cast<unsigned long long*>(base + 8);
   L.abort_flag = reinterpret_cast<int*>(base + 16);
+  L.zeros = base + 256;
   L.status = status;
   // the descriptors (and claim orders) change only with the arguments:
   // upload when they differ from what the workspace already holds
@@ -1578,7 +1766,7 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   const size_t b_xh = up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * R);
   const size_t b_yp = up256(sizeof(TV) * (size_t)h->n * R);
   const size_t b_cnt = up256(sizeof(int) * 2 * (size_t)h->nc);
-  const size_t o_xh = 256, o_yh = o_xh + b_xh, o_yp = o_yh + b_xh, o_cnt = o_yp + b_yp;
+  const size_t o_xh = 256 + kZeroBytes, o_yh = o_xh + b_xh, o_yp = o_yh + b_xh, o_cnt = o_yp + b_yp;
   const size_t zeroed = o_cnt + b_cnt;
   const size_t o_xp = zeroed, o_slot = o_xp + b_yp;
   const size_t need = o_slot + up256(sizeof(SlotArgs<TV>));
@@ -1605,6 +1793,7 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   L.next = reinterpret_cast<unsigned long long*>(base);
   L.next_free = reinterpret_cast<unsigned long long*>(base + 8);
   L.abort_flag = reinterpret_cast<int*>(base + 16);
+  L.zeros = base + 256;
   L.status = h->d_status.as<int>();
   // the array keeps the previous call's contents: the claim counters, abort
   // flag, x-hat, y-hat, y and the counters must start at zero
