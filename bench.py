@@ -84,10 +84,12 @@ def green_aca_flops(tree, rank, k):
 
 
 def build_evals(st, q):
-    regular = 49 * (st["s_entries"] + st["n_singular"][0])
+    # coupling blocks come in mirrored pairs (S_{sigma tau} = S_{tau sigma}^T):
+    # every distinct entry is evaluated once
+    regular = 49 * (st["s_entries"] // 2 + st["n_singular"][0])
     singular = q ** 3 * (2 * st["n_singular"][1] + 5 * st["n_singular"][2]
                          + 6 * st["n_singular"][3])
-    return {"couple_entries": 49 * st["s_entries"], "near_entries": 49 * st["n_singular"][0],
+    return {"couple_entries": 49 * (st["s_entries"] // 2), "near_entries": 49 * st["n_singular"][0],
             "singular": singular, "total": regular + singular}
 
 

@@ -521,15 +521,21 @@ __device__ __forceinline__ double regular_entry(const P4* __restrict__ xq,
   return s * kInv4Pi;
 }
 
-// One CTA per admissible block; the column pivots' nodes are staged in
-// shared memory.  S is row-major r_tau x r_sigma.
-__global__ void k_couple_entries(const int* __restrict__ far_t, const int* __restrict__ far_s,
-                                 const int64_t* __restrict__ soff, const int* __restrict__ rank,
-                                 const int64_t* __restrict__ poff, const int* __restrict__ piv,
-                                 const P4* __restrict__ tq, double* __restrict__ S) {
+// One CTA per pair of mirrored admissible blocks (tau, sigma) and
+// (sigma, tau): G is symmetric (Eq. 1 with g(x, y) = g(y, x) and the same
+// rule on both triangles), so S_{sigma tau} = S_{tau sigma}^T and every
+// entry is computed once and stored twice.  pairs[i] = (b, m): block b and
+// its mirror m (-1: b is computed alone).  The column pivots' nodes are
+// staged in shared memory.  S is row-major r_tau x r_sigma per block.
+__global__ void k_couple_entries(const int2* __restrict__ pairs, const int* __restrict__ far_t,
+                                 const int* __restrict__ far_s, const int64_t* __restrict__ soff,
+                                 const int* __restrict__ rank, const int64_t* __restrict__ poff,
+                                 const int* __restrict__ piv, const P4* __restrict__ tq,
+                                 double* __restrict__ S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   P4* ys = reinterpret_cast<P4*>(smem_raw);
-  const int b = blockIdx.x;
+  const int2 bm = pairs[blockIdx.x];
+  const int b = bm.x;
   const int t = far_t[b], s = far_s[b];
   const int rt = rank[t], rs = rank[s];
   const int* pt = piv + poff[t];
@@ -537,9 +543,12 @@ __global__ void k_couple_entries(const int* __restrict__ far_t, const int* __res
   for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) ys[i] = tq[7 * (int64_t)ps[i / 7] + i % 7];
   __syncthreads();
   double* out = S + soff[b];
+  double* mir = bm.y >= 0 ? S + soff[bm.y] : nullptr;
   for (int idx = threadIdx.x; idx < rt * rs; idx += blockDim.x) {
     const int a = idx / rs, c = idx % rs;
-    out[idx] = regular_entry(tq + 7 * (int64_t)pt[a], ys + 7 * c);
+    const double v = regular_entry(tq + 7 * (int64_t)pt[a], ys + 7 * c);
+    out[idx] = v;
+    if (mir) mir[(int64_t)c * rt + a] = v;
   }
 }
 
@@ -1023,16 +1032,40 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY(upload(h->d_soff, h->soff, st));
   GCA_TRY(h->S64.alloc(sizeof(double) * h->s_entries));
   if (nfar > 0) {
+    // mirrored pairs: the block list is sorted by (row, column) cluster, and
+    // the block tree is symmetric (the admissibility condition and the
+    // splitting rule do not depend on the order of tau and sigma); a block
+    // whose mirror is missing is computed alone
+    std::vector<int2> pairs;
+    pairs.reserve(nfar / 2 + 1);
+    for (int b = 0; b < nfar; ++b) {
+      const int t = h->far_t[b], s = h->far_s[b];
+      int m = -1;
+      {
+        int lo = 0, hi = nfar;
+        while (lo < hi) {
+          const int mid = (lo + hi) / 2;
+          if (h->far_t[mid] < s || (h->far_t[mid] == s && h->far_s[mid] < t)) lo = mid + 1; else hi = mid;
+        }
+        if (lo < nfar && h->far_t[lo] == s && h->far_s[lo] == t) m = lo;
+      }
+      if (m < 0)
+        pairs.push_back(make_int2(b, -1));
+      else if (t < s)
+        pairs.push_back(make_int2(b, m));
+    }
+    DevMem d_pairs;
+    GCA_TRY(upload(d_pairs, pairs, st));
     const size_t smem = sizeof(P4) * 7 * (size_t)std::max(h->max_rank, 1);
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_couple_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
       PhaseScope ps__("couple_entries", st);
-      k_couple_entries<<<nfar, 256, smem, st>>>(h->d_far_t.as<int>(), h->d_far_s.as<int>(),
-                                               h->d_soff.as<int64_t>(), h->d_rank.as<int>(),
-                                               d_poff.as<int64_t>(), d_piv.as<int>(), d_tq.as<P4>(),
-                                               h->S64.as<double>());
+      k_couple_entries<<<(unsigned)pairs.size(), 256, smem, st>>>(
+          d_pairs.as<int2>(), h->d_far_t.as<int>(), h->d_far_s.as<int>(), h->d_soff.as<int64_t>(),
+          h->d_rank.as<int>(), d_poff.as<int64_t>(), d_piv.as<int>(), d_tq.as<P4>(), h->S64.as<double>());
     }
     GCA_TRY_CUDA(cudaGetLastError());
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_pairs is freed at the end of this scope
   }
 
   // near field

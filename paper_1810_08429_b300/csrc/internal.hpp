@@ -121,6 +121,19 @@ int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t
 int matvec(const gca_h2* h, gca_prec prec, bool trans, int32_t nrhs, const void* x, int64_t ldx,
            void* y, int64_t ldy, cudaStream_t st);
 
+// Device workspace of the products of a handle or a batch: the scratch
+// vectors (zeroed per product) and, per precision and direction, the slot
+// descriptors and merged claim orders together with the host bytes they were
+// built from, so that repeated products in any order upload nothing.
+struct DescCache {
+  DevMem mem;
+  std::vector<unsigned char> key;
+};
+struct ProductCache {
+  DevMem ws;
+  DescCache desc[6];  // (float64, float32, bfloat16) x (product, transposed product)
+};
+
 // Compressed sparse index of blocks by one of their two clusters.
 struct BlockIndex {
   std::vector<int> ptr;   // [nclusters + 1]
@@ -180,8 +193,7 @@ struct gca_h2 {
 
   // device: product workspace (grown on demand): x-hat, y-hat, dependency
   // counters and the work-claim counter, zeroed by one memset per product
-  mutable gca::DevMem w_ws;
-  mutable std::vector<unsigned char> w_cache;  // slot descriptors the workspace holds
+  mutable gca::ProductCache pc;
   mutable gca::DevMem d_status;  // sticky error bits of the products
   int max_rows = 0;              // largest block dimension (bounds the staged X)
 };
@@ -189,8 +201,7 @@ struct gca_h2 {
 // A batch of handles applied in one persistent launch.
 struct gca_h2_batch {
   std::vector<gca_h2*> h;          // owned
-  mutable gca::DevMem ws;          // shared product workspace
-  mutable std::vector<unsigned char> w_cache;
+  mutable gca::ProductCache pc;    // shared product workspace
   mutable gca::DevMem d_status;
   ~gca_h2_batch() {
     for (auto* p : h) delete p;

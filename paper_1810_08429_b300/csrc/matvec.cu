@@ -1524,13 +1524,16 @@ int launch_persistent(const LaunchArgs& L, int64_t units, cudaStream_t st) {
 }
 
 // One persistent launch over `count` handles (slots).  Workspace layout:
-// [claim counters, abort flag | per slot: x-hat, y-hat, y (cluster order),
-// counters] zeroed by one memset, then per slot x (cluster order), then the
-// slot descriptors and (batches) the merged claim orders.
+// [claim counters, abort flag, zeros | per slot: x-hat, y-hat, y (cluster
+// order), counters] zeroed by one memset, then per slot x (cluster order).
+// The slot descriptors and (batches) the merged claim orders live in the
+// descriptor cache of the precision and direction.
 template <typename T, typename TN, typename TA, typename TV, int RC>
 int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, const void* const* x,
-              const int64_t* ldx, void* const* y, const int64_t* ldy, DevMem& ws,
-              std::vector<unsigned char>& ws_cache, int* status, cudaStream_t st) {
+              const int64_t* ldx, void* const* y, const int64_t* ldy, ProductCache& pc, int* status,
+              cudaStream_t st) {
+  DevMem& ws = pc.ws;
+  DescCache& dc = pc.desc[(sizeof(T) == 8 ? 0 : (sizeof(T) == 4 ? 1 : 2)) * 2 + dir];
   const char* pn = sizeof(T) == 8 ? ".f64" : (sizeof(T) == 4 ? ".f32" : ".bf16");
   PhaseScope ps(std::string("mv_persistent") + pn + (dir ? ".T" : ""), st);
   ps.launches(3);
@@ -1554,8 +1557,6 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
     o_xp[i] = off;
     off += up256(sizeof(TV) * (size_t)hs[i]->n * nrhs[i]);
   }
-  const size_t o_slots = off;
-  off += up256(sizeof(SlotArgs<TV>) * count);
   std::vector<int> nchunk(count);
   int64_t work = 0, free_work = 0;
   int max_n = 0;
@@ -1565,13 +1566,16 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
     free_work += hs[i]->n_free[dir] * nchunk[i];
     max_n = std::max(max_n, hs[i]->n * nrhs[i]);
   }
-  const size_t o_cmap = off;
-  if (count > 1) off += up256(sizeof(int2) * (size_t)std::max<int64_t>(work, 1));
-  const size_t o_fmap = off;
-  if (count > 1) off += up256(sizeof(int2) * (size_t)std::max<int64_t>(free_work, 1));
-  if (off > ws.bytes) ws_cache.clear();
+  size_t doff = up256(sizeof(SlotArgs<TV>) * count);
+  const size_t o_cmap = doff;
+  if (count > 1) doff += up256(sizeof(int2) * (size_t)std::max<int64_t>(work, 1));
+  const size_t o_fmap = doff;
+  if (count > 1) doff += up256(sizeof(int2) * (size_t)std::max<int64_t>(free_work, 1));
   GCA_TRY(ws.reserve(off));
   unsigned char* base = ws.as<unsigned char>();
+  if (doff > dc.mem.bytes) dc.key.clear();
+  GCA_TRY(dc.mem.reserve(doff));
+  unsigned char* dbase = dc.mem.as<unsigned char>();
   for (int i = 0; i < count; ++i) {
     SlotArgs<TV>& a = sl[i];
     fill_slot<T, TN, TV>(a, hs[i], dir, nrhs[i], RC, x[i], ldx[i], y[i], ldy[i]);
@@ -1582,10 +1586,10 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
     a.xp = reinterpret_cast<TV*>(base + o_xp[i]);
   }
   LaunchArgs L;
-  L.slots = base + o_slots;
+  L.slots = dbase;
   L.nslots = count;
-  L.chain_map = count > 1 ? reinterpret_cast<const int2*>(base + o_cmap) : nullptr;
-  L.free_map = count > 1 ? reinterpret_cast<const int2*>(base + o_fmap) : nullptr;
+  L.chain_map = count > 1 ? reinterpret_cast<const int2*>(dbase + o_cmap) : nullptr;
+  L.free_map = count > 1 ? reinterpret_cast<const int2*>(dbase + o_fmap) : nullptr;
   L.total = work;
   L.total_free = free_work;
   L.next = reinterpret_cast<unsigned long long*>(base);
@@ -1594,12 +1598,11 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   L.zeros = base + 256;
   L.status = status;
   // the descriptors (and claim orders) change only with the arguments:
-  // upload when they differ from what the workspace already holds
+  // upload when they differ from what the cache already holds (the
+  // descriptors contain the workspace and the caller's vector addresses)
   const size_t sbytes = sizeof(SlotArgs<TV>) * count;
-  if (ws_cache.size() != sbytes + sizeof(void*) ||
-      std::memcmp(ws_cache.data(), sl.data(), sbytes) != 0 ||
-      std::memcmp(ws_cache.data() + sbytes, &base, sizeof(void*)) != 0) {
-    GCA_TRY_CUDA(cudaMemcpyAsync(base + o_slots, sl.data(), sbytes, cudaMemcpyHostToDevice, st));
+  if (dc.key.size() != sbytes || std::memcmp(dc.key.data(), sl.data(), sbytes) != 0) {
+    GCA_TRY_CUDA(cudaMemcpyAsync(dbase, sl.data(), sbytes, cudaMemcpyHostToDevice, st));
     std::vector<int2> cmap, fmap;
     if (count > 1) {
       merge_claims(hs, count, dir, nchunk, cmap, fmap);
@@ -1608,19 +1611,17 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
         return GCA_ERR_UNSUPPORTED;
       }
       if (work > 0)
-        GCA_TRY_CUDA(cudaMemcpyAsync(base + o_cmap, cmap.data(), sizeof(int2) * work, cudaMemcpyHostToDevice, st));
+        GCA_TRY_CUDA(cudaMemcpyAsync(dbase + o_cmap, cmap.data(), sizeof(int2) * work, cudaMemcpyHostToDevice, st));
       if (free_work > 0)
         GCA_TRY_CUDA(
-            cudaMemcpyAsync(base + o_fmap, fmap.data(), sizeof(int2) * free_work, cudaMemcpyHostToDevice, st));
+            cudaMemcpyAsync(dbase + o_fmap, fmap.data(), sizeof(int2) * free_work, cudaMemcpyHostToDevice, st));
     }
     GCA_TRY_CUDA(cudaStreamSynchronize(st));  // sl, cmap, fmap are host vectors of this frame
-    ws_cache.assign(reinterpret_cast<const unsigned char*>(sl.data()),
-                    reinterpret_cast<const unsigned char*>(sl.data()) + sbytes);
-    ws_cache.insert(ws_cache.end(), reinterpret_cast<const unsigned char*>(&base),
-                    reinterpret_cast<const unsigned char*>(&base) + sizeof(void*));
+    dc.key.assign(reinterpret_cast<const unsigned char*>(sl.data()),
+                  reinterpret_cast<const unsigned char*>(sl.data()) + sbytes);
   }
   GCA_TRY_CUDA(cudaMemsetAsync(base, 0, zeroed, st));
-  const auto* d_slots = reinterpret_cast<const SlotArgs<TV>*>(base + o_slots);
+  const auto* d_slots = reinterpret_cast<const SlotArgs<TV>*>(dbase);
   const unsigned gx = (unsigned)std::min<int64_t>(1024, (max_n + 255) / 256);
   k_gather<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots);
   if (work + free_work > 0) GCA_TRY((launch_persistent<T, TN, TA, TV, RC>(L, work + free_work, st)));
@@ -1631,15 +1632,15 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
 
 template <typename T, typename TN, typename TA, typename TV>
 int launch(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, const void* const* x,
-           const int64_t* ldx, void* const* y, const int64_t* ldy, DevMem& ws,
-           std::vector<unsigned char>& wc, int* status, cudaStream_t st) {
+           const int64_t* ldx, void* const* y, const int64_t* ldy, ProductCache& pc, int* status,
+           cudaStream_t st) {
   int R = 1;
   for (int i = 0; i < count; ++i) R = std::max(R, (int)nrhs[i]);
-  if (R >= 16) return launch_rc<T, TN, TA, TV, 16>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
-  if (R > 4) return launch_rc<T, TN, TA, TV, 8>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
-  if (R > 2) return launch_rc<T, TN, TA, TV, 4>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
-  if (R > 1) return launch_rc<T, TN, TA, TV, 2>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
-  return launch_rc<T, TN, TA, TV, 1>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+  if (R >= 16) return launch_rc<T, TN, TA, TV, 16>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+  if (R > 4) return launch_rc<T, TN, TA, TV, 8>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+  if (R > 2) return launch_rc<T, TN, TA, TV, 4>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+  if (R > 1) return launch_rc<T, TN, TA, TV, 2>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+  return launch_rc<T, TN, TA, TV, 1>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
 }
 
 // the handle kept the panels of this precision (gca_params.flags)
@@ -1654,8 +1655,8 @@ bool has_precision(const gca_h2* h, gca_prec prec) {
 }
 
 int launch_any(const gca_h2* const* hs, int count, gca_prec prec, bool trans, const int32_t* nrhs,
-               const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy, DevMem& ws,
-               std::vector<unsigned char>& wc, int* status, cudaStream_t st) {
+               const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy,
+               ProductCache& pc, int* status, cudaStream_t st) {
   for (int i = 0; i < count; ++i) {
     if (!hs[i] || !x[i] || !y[i] || nrhs[i] < 1 || nrhs[i] > 4096 || ldx[i] < hs[i]->n ||
         ldy[i] < hs[i]->n) {
@@ -1670,11 +1671,11 @@ int launch_any(const gca_h2* const* hs, int count, gca_prec prec, bool trans, co
   const int dir = trans ? 1 : 0;
   switch (prec) {
     case GCA_F64:
-      return launch<double, double, double, double>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+      return launch<double, double, double, double>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
     case GCA_F32:
-      return launch<float, float, float, float>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc, status, st);
+      return launch<float, float, float, float>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
     case GCA_BF16:
-      return launch<__nv_bfloat16, float, float, float>(hs, count, dir, nrhs, x, ldx, y, ldy, ws, wc,
+      return launch<__nv_bfloat16, float, float, float>(hs, count, dir, nrhs, x, ldx, y, ldy, pc,
                                                         status, st);
   }
   set_error("h2_matvec: unknown precision");
@@ -1692,8 +1693,7 @@ int matvec(const gca_h2* h, gca_prec prec, bool trans, int32_t nrhs, const void*
   const gca_h2* hs[1] = {h};
   const void* xs[1] = {x};
   void* ys[1] = {y};
-  return launch_any(hs, 1, prec, trans, &nrhs, xs, &ldx, ys, &ldy, h->w_ws, h->w_cache,
-                    h->d_status.as<int>(), st);
+  return launch_any(hs, 1, prec, trans, &nrhs, xs, &ldx, ys, &ldy, h->pc, h->d_status.as<int>(), st);
 }
 
 int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* nrhs,
@@ -1704,7 +1704,7 @@ int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t
     return GCA_ERR_INVALID_ARG;
   }
   std::vector<const gca_h2*> hs(b->h.begin(), b->h.end());
-  return launch_any(hs.data(), (int)hs.size(), prec, trans, nrhs, x, ldx, y, ldy, b->ws, b->w_cache,
+  return launch_any(hs.data(), (int)hs.size(), prec, trans, nrhs, x, ldx, y, ldy, b->pc,
                     b->d_status.as<int>(), st);
 }
 
