@@ -174,6 +174,15 @@ struct AcaJob {
 //      every CTA keeps its slice of the pivot row as v.
 // Afterwards V^ = U L^{-1} (L = U[P, :], unit lower triangular) is solved
 // row by row, the rows spread over the cluster.
+// doubles of the matrix region of k_aca's shared memory: the CTA's columns
+// of A^ during the cross approximation, then one row of V^ per warp (r <=
+// rows) during the triangular solve
+__host__ __device__ constexpr size_t aca_s_doubles(int rows_cap, int kw_cap) {
+  return (size_t)rows_cap * 2 * kw_cap > (size_t)(kAcaThreads / 32) * rows_cap
+             ? (size_t)rows_cap * 2 * kw_cap
+             : (size_t)(kAcaThreads / 32) * rows_cap;
+}
+
 constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
@@ -208,7 +217,7 @@ k_aca(const AcaJob* __restrict__ jobs, int k, int rows_cap, int kw_cap, const in
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* S = reinterpret_cast<double*>(smem_raw);                  // rows_cap x 2 kw_cap
-  double* s_u = S + (size_t)rows_cap * 2 * kw_cap;                    // rows_cap
+  double* s_u = S + aca_s_doubles(rows_cap, kw_cap);                  // rows_cap
   double* s_v = s_u + rows_cap;                                       // 2 kw_cap
   int* s_rows = reinterpret_cast<int*>(s_v + 2 * kw_cap);             // rows_cap
   int* s_prow = s_rows + rows_cap;                                    // rows_cap
@@ -251,17 +260,32 @@ k_aca(const AcaJob* __restrict__ jobs, int k, int rows_cap, int kw_cap, const in
   int r = 0;
   double first = 0.0;
   bool have_update = false;
+  // (row, column) of a thread's entries idx = tid + nth m, advanced without
+  // division: idx -> idx + nth moves the row by di and the column by dj
+  const int i_first = tid % rows, j_first = tid / rows;
+  const int di = nth % rows, dj = nth / rows;
   for (;;) {
     // 1. update + local max of |R| (bit patterns)
     unsigned long long lmax = 0;
-    for (int idx = tid; idx < total; idx += nth) {
-      double val = S[idx];
-      if (have_update) {
-        val = fma(-s_u[idx % rows], s_v[idx / rows], val);
+    if (have_update) {
+      int i = i_first, jj = j_first;
+      for (int idx = tid; idx < total; idx += nth) {
+        const double val = fma(-s_u[i], s_v[jj], S[idx]);
         S[idx] = val;
+        const unsigned long long b = (unsigned long long)__double_as_longlong(val) & kAbsMask;
+        lmax = b > lmax ? b : lmax;
+        i += di;
+        jj += dj;
+        if (i >= rows) {
+          i -= rows;
+          ++jj;
+        }
       }
-      const unsigned long long b = (unsigned long long)__double_as_longlong(val) & kAbsMask;
-      lmax = b > lmax ? b : lmax;
+    } else {
+      for (int idx = tid; idx < total; idx += nth) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(S[idx]) & kAbsMask;
+        lmax = b > lmax ? b : lmax;
+      }
     }
     lmax = warp_max_u64(lmax);
     if (lane == 0) s_wmax[wid] = lmax;
@@ -334,15 +358,27 @@ k_aca(const AcaJob* __restrict__ jobs, int k, int rows_cap, int kw_cap, const in
   }
   cluster.sync();  // every U column written, no CTA still reads a peer's u
 
-  // V^ = U L^{-1}, rows spread over the cluster; V^ row-major rows x r
+  // V^ = U L^{-1} (L = U[P, :], unit lower triangular): row a of V^
+  // solves v L = U[a, :] by back substitution, v_c = U[a, c] -
+  // sum_{d > c} v_d L_{dc}.  One warp per row (rows spread over the
+  // cluster), the sum over d split over the lanes; the row being solved
+  // lives in the warp's slice of S (the residual is no longer needed).
+  // V^ row-major rows x r.
   double* Vh = vh_pool + job.vh_off;
   const int rpc = (rows + C - 1) / C;
-  for (int a = q * rpc + tid; a < min(rows, (q + 1) * rpc); a += nth) {
+  const int nwarps = nth / 32;
+  double* vrow = S + (size_t)wid * rows_cap;  // r <= rows doubles per warp
+  for (int a = q * rpc + wid; a < min(rows, (q + 1) * rpc); a += nwarps) {
     for (int c = r - 1; c >= 0; --c) {
-      double sacc = U[(int64_t)c * rows + a];
-      for (int d = c + 1; d < r; ++d) sacc -= Vh[(int64_t)a * r + d] * U[(int64_t)c * rows + s_prow[d]];
-      Vh[(int64_t)a * r + c] = sacc;
+      double part = 0.0;
+      const double* Lc = U + (int64_t)c * rows;
+      for (int d = c + 1 + lane; d < r; d += 32) part = fma(vrow[d], Lc[s_prow[d]], part);
+      for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+      if (lane == 0) vrow[c] = Lc[a] - part;
+      __syncwarp();
     }
+    for (int c = lane; c < r; c += 32) Vh[(int64_t)a * r + c] = vrow[c];
+    __syncwarp();
   }
   if (q == 0) {
     for (int t = tid; t < r; t += nth) piv_pool[job.p_off + t] = s_rows[s_prow[t]];
@@ -866,7 +902,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // shared memory of one CTA of k_aca for a job of `rows` rows on a C-CTA cluster
   auto aca_smem = [&](int rows, int C) -> size_t {
     const int kw = (k + C - 1) / C;
-    return sizeof(double) * ((size_t)rows * 2 * kw + rows + 2 * kw) + sizeof(int) * 2 * (size_t)rows;
+    return sizeof(double) * (aca_s_doubles(rows, kw) + rows + 2 * kw) + sizeof(int) * 2 * (size_t)rows;
   };
   const size_t smem_budget = (size_t)aca_dyn_max;
   for (int L = h->depth; L >= 1; --L) {
