@@ -156,6 +156,8 @@ int gca_build_batch(int32_t count, const gca_mesh* meshes, const gca_tree* trees
       gca::set_error("gca_build_batch: cudaMemset failed");
       return GCA_ERR_CUDA;
     }
+    st = gca::prepare_batch(b.get(), static_cast<cudaStream_t>(stream));
+    if (st != GCA_OK) return st;
     *out = b.release();
     return GCA_OK;
   } catch (const std::bad_alloc&) {

@@ -12,6 +12,8 @@
 
 #include "gca.h"
 
+struct gca_h2_batch;
+
 namespace gca {
 
 // Stored blocks in panel layout: leaf bases, transfers, couplings, near field,
@@ -113,6 +115,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
 int finish_plan(gca_h2* h, cudaStream_t st);
 int make_panels(gca_h2* h, cudaStream_t st);
 int product_status(const gca_h2* h, int* out);
+int prepare_batch(gca_h2_batch* b, cudaStream_t st);
 int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx, void* y,
                    int64_t ldy, cudaStream_t st);
 int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* nrhs,
@@ -132,6 +135,11 @@ struct DescCache {
 struct ProductCache {
   DevMem ws;
   DescCache desc[6];  // (float64, float32, bfloat16) x (product, transposed product)
+  // merged claim orders of a batch for one right-hand-side chunk per mesh,
+  // per direction: chain claims, then free claims
+  DevMem maps1[2];
+  int64_t maps1_chain[2] = {0, 0};
+  int64_t maps1_free[2] = {0, 0};
 };
 
 // Compressed sparse index of blocks by one of their two clusters.

@@ -116,8 +116,17 @@ struct SlotArgs {
   int* counters;               // [2 nc]
 };
 
+// The slot descriptors of a launch over at most kInlineSlots meshes travel
+// as a kernel parameter (nothing to upload); larger launches read a device
+// copy.
+constexpr int kInlineSlots = 8;
+template <typename TV>
+struct SlotPack {
+  SlotArgs<TV> s[kInlineSlots];
+};
+
 struct LaunchArgs {
-  const void* slots;           // SlotArgs<TV>[nslots]
+  const void* slots;           // SlotArgs<TV>[nslots] in device memory (nslots > kInlineSlots)
   int nslots;
   const int2* chain_map;       // claim -> (slot, claim within the slot); null: one slot
   const int2* free_map;
@@ -321,8 +330,9 @@ __device__ __forceinline__ void add_row(double* p, const double* v, int valid_co
 // x (original order) -> x in cluster order, all slots of a launch
 // (blockIdx.y = slot)
 template <typename TV>
-__global__ void k_gather(const SlotArgs<TV>* __restrict__ slots) {
-  const SlotArgs<TV>& sa = slots[blockIdx.y];
+__global__ void k_gather(const SlotArgs<TV>* __restrict__ dslots, const __grid_constant__ SlotPack<TV> pack,
+                         int inline_slots) {
+  const SlotArgs<TV>& sa = inline_slots ? pack.s[blockIdx.y] : dslots[blockIdx.y];
   const int64_t tot = (int64_t)sa.n * sa.R;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -333,8 +343,9 @@ __global__ void k_gather(const SlotArgs<TV>* __restrict__ slots) {
 
 // y in cluster order -> caller's y (original order)
 template <typename TV>
-__global__ void k_scatter(const SlotArgs<TV>* __restrict__ slots) {
-  const SlotArgs<TV>& sa = slots[blockIdx.y];
+__global__ void k_scatter(const SlotArgs<TV>* __restrict__ dslots, const __grid_constant__ SlotPack<TV> pack,
+                          int inline_slots) {
+  const SlotArgs<TV>& sa = inline_slots ? pack.s[blockIdx.y] : dslots[blockIdx.y];
   const int64_t tot = (int64_t)sa.n * sa.R;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -1101,9 +1112,10 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
 // (float: two CTAs per SM within 128 registers a thread; double: one CTA,
 // whose buffers fill the shared memory and whose accumulators need more)
 template <typename T, typename TN, typename TA, typename TV, int RC>
-__global__ void __launch_bounds__(kThreads, sizeof(TA) == 8 ? 1 : 2) k_h2_persistent(LaunchArgs L) {
+__global__ void __launch_bounds__(kThreads, sizeof(TA) == 8 ? 1 : 2)
+    k_h2_persistent(const __grid_constant__ LaunchArgs L, const __grid_constant__ SlotPack<TV> pack) {
   using PS = PairSmem<TA, RC>;
-  const SlotArgs<TV>* slots = static_cast<const SlotArgs<TV>*>(L.slots);
+  const SlotArgs<TV>* slots = L.slots ? static_cast<const SlotArgs<TV>*>(L.slots) : pack.s;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int pair = warp % kPairs;
@@ -1485,7 +1497,7 @@ void fill_slot(SlotArgs<TV>& a, const gca_h2* h, int dir, int R, int RC, const v
 // Launches the persistent kernel with as many CTAs as fit on the device (found once per device and kernel, so that later launches
 // make no attribute or occupancy calls and can be graph captured).
 template <typename T, typename TN, typename TA, typename TV, int RC>
-int launch_persistent(const LaunchArgs& L, int64_t units, cudaStream_t st) {
+int launch_persistent(const LaunchArgs& L, const SlotPack<TV>& pack, int64_t units, cudaStream_t st) {
   const size_t smem = cta_smem<TA, RC>();
   auto kern = k_h2_persistent<T, TN, TA, TV, RC>;
   static std::mutex mu;
@@ -1519,24 +1531,26 @@ int launch_persistent(const LaunchArgs& L, int64_t units, cudaStream_t st) {
     if (dev >= 0 && dev < 64) cap_by_dev[dev] = cap;
   }
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((units + kPairs - 1) / kPairs, cap));
-  kern<<<grid, kThreads, smem, st>>>(L);
+  kern<<<grid, kThreads, smem, st>>>(L, pack);
   return GCA_OK;
 }
 
 // One persistent launch over `count` handles (slots).  Workspace layout:
 // [claim counters, abort flag, zeros | per slot: x-hat, y-hat, y (cluster
 // order), counters] zeroed by one memset, then per slot x (cluster order).
-// The slot descriptors and (batches) the merged claim orders live in the
-// descriptor cache of the precision and direction.
+// Up to kInlineSlots slot descriptors travel as a kernel parameter; the
+// merged claim orders of a batch come precomputed from gca_build_batch when
+// every mesh takes one right-hand-side chunk.  Other launches keep their
+// descriptors (and claim orders) in the device cache of the precision and
+// direction, uploaded when the arguments change.
 template <typename T, typename TN, typename TA, typename TV, int RC>
 int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, const void* const* x,
               const int64_t* ldx, void* const* y, const int64_t* ldy, ProductCache& pc, int* status,
               cudaStream_t st) {
-  DevMem& ws = pc.ws;
-  DescCache& dc = pc.desc[(sizeof(T) == 8 ? 0 : (sizeof(T) == 4 ? 1 : 2)) * 2 + dir];
   const char* pn = sizeof(T) == 8 ? ".f64" : (sizeof(T) == 4 ? ".f32" : ".bf16");
   PhaseScope ps(std::string("mv_persistent") + pn + (dir ? ".T" : ""), st);
   ps.launches(3);
+  DevMem& ws = pc.ws;
   std::vector<SlotArgs<TV>> sl(count);
   size_t off = 256 + kZeroBytes;  // claim counters + abort flag, zeros
   std::vector<size_t> o_xh(count), o_yh(count), o_yp(count), o_cnt(count), o_xp(count);
@@ -1560,22 +1574,16 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   std::vector<int> nchunk(count);
   int64_t work = 0, free_work = 0;
   int max_n = 0;
+  bool one_chunk = true;
   for (int i = 0; i < count; ++i) {
     nchunk[i] = (nrhs[i] + RC - 1) / RC;
+    one_chunk = one_chunk && nchunk[i] == 1;
     work += hs[i]->n_chain[dir] * nchunk[i];
     free_work += hs[i]->n_free[dir] * nchunk[i];
     max_n = std::max(max_n, hs[i]->n * nrhs[i]);
   }
-  size_t doff = up256(sizeof(SlotArgs<TV>) * count);
-  const size_t o_cmap = doff;
-  if (count > 1) doff += up256(sizeof(int2) * (size_t)std::max<int64_t>(work, 1));
-  const size_t o_fmap = doff;
-  if (count > 1) doff += up256(sizeof(int2) * (size_t)std::max<int64_t>(free_work, 1));
   GCA_TRY(ws.reserve(off));
   unsigned char* base = ws.as<unsigned char>();
-  if (doff > dc.mem.bytes) dc.key.clear();
-  GCA_TRY(dc.mem.reserve(doff));
-  unsigned char* dbase = dc.mem.as<unsigned char>();
   for (int i = 0; i < count; ++i) {
     SlotArgs<TV>& a = sl[i];
     fill_slot<T, TN, TV>(a, hs[i], dir, nrhs[i], RC, x[i], ldx[i], y[i], ldy[i]);
@@ -1585,11 +1593,66 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
     a.counters = reinterpret_cast<int*>(base + o_cnt[i]);
     a.xp = reinterpret_cast<TV*>(base + o_xp[i]);
   }
+  const bool inline_slots = count <= kInlineSlots;
+  const bool pre_maps = count > 1 && one_chunk && pc.maps1[dir].p && pc.maps1_chain[dir] == work &&
+                        pc.maps1_free[dir] == free_work;
+  const bool dev_maps = count > 1 && !pre_maps;
+  SlotPack<TV> pack;
+  std::memset(&pack, 0, sizeof(pack));
   LaunchArgs L;
-  L.slots = dbase;
+  L.slots = nullptr;
+  L.chain_map = nullptr;
+  L.free_map = nullptr;
+  if (inline_slots)
+    for (int i = 0; i < count; ++i) pack.s[i] = sl[i];
+  if (pre_maps) {
+    L.chain_map = pc.maps1[dir].as<int2>();
+    L.free_map = L.chain_map + work;
+  }
+  const SlotArgs<TV>* d_slots = nullptr;
+  if (!inline_slots || dev_maps) {
+    DescCache& dc = pc.desc[(sizeof(T) == 8 ? 0 : (sizeof(T) == 4 ? 1 : 2)) * 2 + dir];
+    size_t doff = up256(sizeof(SlotArgs<TV>) * count);
+    const size_t o_cmap = doff;
+    if (dev_maps) doff += up256(sizeof(int2) * (size_t)std::max<int64_t>(work, 1));
+    const size_t o_fmap = doff;
+    if (dev_maps) doff += up256(sizeof(int2) * (size_t)std::max<int64_t>(free_work, 1));
+    if (doff > dc.mem.bytes) dc.key.clear();
+    GCA_TRY(dc.mem.reserve(doff));
+    unsigned char* dbase = dc.mem.as<unsigned char>();
+    // the descriptors (and claim orders) change only with the arguments:
+    // upload when they differ from what the cache already holds (the
+    // descriptors contain the workspace and the caller's vector addresses)
+    const size_t sbytes = sizeof(SlotArgs<TV>) * count;
+    std::vector<unsigned char> key(sbytes + 1);
+    std::memcpy(key.data(), sl.data(), sbytes);
+    key[sbytes] = dev_maps ? 1 : 0;
+    if (dc.key != key) {
+      GCA_TRY_CUDA(cudaMemcpyAsync(dbase, sl.data(), sbytes, cudaMemcpyHostToDevice, st));
+      std::vector<int2> cmap, fmap;
+      if (dev_maps) {
+        merge_claims(hs, count, dir, nchunk, cmap, fmap);
+        if ((int64_t)cmap.size() != work || (int64_t)fmap.size() != free_work) {
+          set_error("internal: merged claim order has the wrong length");
+          return GCA_ERR_UNSUPPORTED;
+        }
+        if (work > 0)
+          GCA_TRY_CUDA(cudaMemcpyAsync(dbase + o_cmap, cmap.data(), sizeof(int2) * work, cudaMemcpyHostToDevice, st));
+        if (free_work > 0)
+          GCA_TRY_CUDA(
+              cudaMemcpyAsync(dbase + o_fmap, fmap.data(), sizeof(int2) * free_work, cudaMemcpyHostToDevice, st));
+      }
+      GCA_TRY_CUDA(cudaStreamSynchronize(st));  // sl, cmap, fmap are host vectors of this frame
+      dc.key.swap(key);
+    }
+    d_slots = reinterpret_cast<const SlotArgs<TV>*>(dbase);
+    if (!inline_slots) L.slots = dbase;
+    if (dev_maps) {
+      L.chain_map = reinterpret_cast<const int2*>(dbase + o_cmap);
+      L.free_map = reinterpret_cast<const int2*>(dbase + o_fmap);
+    }
+  }
   L.nslots = count;
-  L.chain_map = count > 1 ? reinterpret_cast<const int2*>(dbase + o_cmap) : nullptr;
-  L.free_map = count > 1 ? reinterpret_cast<const int2*>(dbase + o_fmap) : nullptr;
   L.total = work;
   L.total_free = free_work;
   L.next = reinterpret_cast<unsigned long long*>(base);
@@ -1597,35 +1660,11 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   L.abort_flag = reinterpret_cast<int*>(base + 16);
   L.zeros = base + 256;
   L.status = status;
-  // the descriptors (and claim orders) change only with the arguments:
-  // upload when they differ from what the cache already holds (the
-  // descriptors contain the workspace and the caller's vector addresses)
-  const size_t sbytes = sizeof(SlotArgs<TV>) * count;
-  if (dc.key.size() != sbytes || std::memcmp(dc.key.data(), sl.data(), sbytes) != 0) {
-    GCA_TRY_CUDA(cudaMemcpyAsync(dbase, sl.data(), sbytes, cudaMemcpyHostToDevice, st));
-    std::vector<int2> cmap, fmap;
-    if (count > 1) {
-      merge_claims(hs, count, dir, nchunk, cmap, fmap);
-      if ((int64_t)cmap.size() != work || (int64_t)fmap.size() != free_work) {
-        set_error("internal: merged claim order has the wrong length");
-        return GCA_ERR_UNSUPPORTED;
-      }
-      if (work > 0)
-        GCA_TRY_CUDA(cudaMemcpyAsync(dbase + o_cmap, cmap.data(), sizeof(int2) * work, cudaMemcpyHostToDevice, st));
-      if (free_work > 0)
-        GCA_TRY_CUDA(
-            cudaMemcpyAsync(dbase + o_fmap, fmap.data(), sizeof(int2) * free_work, cudaMemcpyHostToDevice, st));
-    }
-    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // sl, cmap, fmap are host vectors of this frame
-    dc.key.assign(reinterpret_cast<const unsigned char*>(sl.data()),
-                  reinterpret_cast<const unsigned char*>(sl.data()) + sbytes);
-  }
   GCA_TRY_CUDA(cudaMemsetAsync(base, 0, zeroed, st));
-  const auto* d_slots = reinterpret_cast<const SlotArgs<TV>*>(dbase);
   const unsigned gx = (unsigned)std::min<int64_t>(1024, (max_n + 255) / 256);
-  k_gather<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots);
-  if (work + free_work > 0) GCA_TRY((launch_persistent<T, TN, TA, TV, RC>(L, work + free_work, st)));
-  k_scatter<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots);
+  k_gather<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots, pack, inline_slots ? 1 : 0);
+  if (work + free_work > 0) GCA_TRY((launch_persistent<T, TN, TA, TV, RC>(L, pack, work + free_work, st)));
+  k_scatter<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots, pack, inline_slots ? 1 : 0);
   GCA_TRY_CUDA(cudaGetLastError());
   return GCA_OK;
 }
@@ -1681,6 +1720,30 @@ int launch_any(const gca_h2* const* hs, int count, gca_prec prec, bool trans, co
   set_error("h2_matvec: unknown precision");
   return GCA_ERR_INVALID_ARG;
 }
+
+}  // namespace
+
+// Claim orders of a batch for one right-hand-side chunk per mesh (R <= 16),
+// merged and uploaded once when the batch is built.
+int prepare_batch(gca_h2_batch* b, cudaStream_t st) {
+  const int count = (int)b->h.size();
+  if (count < 2) return GCA_OK;
+  std::vector<const gca_h2*> hs(b->h.begin(), b->h.end());
+  std::vector<int> nchunk(count, 1);
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<int2> cmap, fmap;
+    merge_claims(hs.data(), count, dir, nchunk, cmap, fmap);
+    cmap.insert(cmap.end(), fmap.begin(), fmap.end());
+    b->pc.maps1_chain[dir] = (int64_t)cmap.size() - (int64_t)fmap.size();
+    b->pc.maps1_free[dir] = (int64_t)fmap.size();
+    if (cmap.empty()) cmap.push_back(make_int2(0, 0));
+    GCA_TRY(upload(b->pc.maps1[dir], cmap, st));
+  }
+  GCA_TRY_CUDA(cudaStreamSynchronize(st));  // the host vectors go out of scope
+  return GCA_OK;
+}
+
+namespace {
 
 }  // namespace
 
@@ -1802,9 +1865,12 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   auto* d_slots = reinterpret_cast<SlotArgs<TV>*>(base + o_slot);
   k_put_slot<TV><<<1, 1, 0, st>>>(a, d_slots);
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, ((int64_t)h->n * R + 255) / 256));
-  k_gather<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots);
-  if (L.total + L.total_free > 0) GCA_TRY((launch_persistent<T, TN, TA, TV, RC>(L, L.total + L.total_free, st)));
-  k_scatter<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots);
+  SlotPack<TV> pack;
+  std::memset(&pack, 0, sizeof(pack));
+  k_gather<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots, pack, 0);
+  if (L.total + L.total_free > 0)
+    GCA_TRY((launch_persistent<T, TN, TA, TV, RC>(L, pack, L.total + L.total_free, st)));
+  k_scatter<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots, pack, 0);
   GCA_TRY_CUDA(cudaGetLastError());
   return GCA_OK;
 }
