@@ -99,9 +99,14 @@ def build_evals(st, q):
 # source is unchanged, scaled to the timed launch by its algorithmic bytes.
 TRAFFIC = {
     "couple_entries": ("paper_1810_08429_b300/csrc/build.cu",
-                       "0983f442ed7bba41027ccffeeba8a24cc3c5e3d04b5cba7362b5bbdc22b460a5", 541.50e6),
+                       "44e68fc10fa230bed4647f73cdb392b198276e1ee26b782e4c38c37513b95713", 593.84e6),
+    # 13 level launches of one mesh move 29.04 MB in all: the average per launch
+    "green_aca": ("paper_1810_08429_b300/csrc/build.cu",
+                  "44e68fc10fa230bed4647f73cdb392b198276e1ee26b782e4c38c37513b95713", 29.04e6 / 13),
     "mv_persistent.f32": ("paper_1810_08429_b300/csrc/matvec.cu",
-                          "a7c1ece76f407339dcc83a0707c261eae809045b4cc2c4ef0ba0e95166f1c8bd", 485.92e6),
+                          "90eeb48bee6df5ffa900f27387a66c7d74e28ecae1e7821bdf353a082dcff36d", 480.99e6),
+    "mv_persistent.bf16": ("paper_1810_08429_b300/csrc/matvec.cu",
+                           "90eeb48bee6df5ffa900f27387a66c7d74e28ecae1e7821bdf353a082dcff36d", 270.84e6),
 }
 
 
