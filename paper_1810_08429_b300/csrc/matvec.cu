@@ -165,9 +165,9 @@ constexpr bool kSplitRegs = sizeof(TA) == 4;
 constexpr int kThreads = 64 * kPairs;                       // consumers: warps 0..3, producers: 4..7
 constexpr int kItemRows = 64;                               // rows per segment (one warp tile)
 constexpr int kChunk = 64;                                  // columns per segment
-constexpr int kStagePanels = 4;
-constexpr int kStageBytes = kStagePanels * kItemRows * 16;  // 4 KB: one contiguous copy
-constexpr int kStages = 4;
+constexpr int kStagePanels = 8;
+constexpr int kStageBytes = kStagePanels * kItemRows * 16;  // 8 KB: one contiguous copy
+constexpr int kStages = 2;
 constexpr int kDescSlots = 4;                               // records: chain 0, 1; free 2, 3
 constexpr size_t kZeroBytes = (size_t)kChunk * 16 * 8;      // a full input block of doubles
 // bound of every mbarrier wait, in SM clock cycles (about a second)
@@ -452,14 +452,16 @@ __device__ __forceinline__ void consume_rows(const unsigned char* stage, int pst
     for (int c = 0; c < Tl::CPL; ++c) acc[i][c] += part[i][c];
 }
 
-template <typename T, typename TA, int RC>
+template <typename T, typename TA, int RC, bool kSkipRows = true>
 __device__ __forceinline__ void consume_stage(const unsigned char* stage, int rows, int npst, int p0,
                                               const TA* __restrict__ Xs, int rg, int cg,
                                               TA (&acc)[Tile<RC>::RPL][Tile<RC>::CPL]) {
   using Tl = Tile<RC>;
   const int pst = rows * 16;
   const int ni = (rows + Tl::RG - 1) / Tl::RG;  // row groups holding rows of the tile
-  if constexpr (Tl::RPL == 4) {
+  if constexpr (!kSkipRows) {
+    consume_rows<T, TA, RC, Tl::RPL>(stage, pst, npst, p0, Xs, rg, cg, acc);
+  } else if constexpr (Tl::RPL == 4) {
     if (ni >= 4)
       consume_rows<T, TA, RC, 4>(stage, pst, npst, p0, Xs, rg, cg, acc);
     else if (ni == 3)
@@ -1033,8 +1035,8 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
         } else if constexpr (kTC) {
           if (tc)
             mma_stage<RC>(stg, rows, npst, p0, reinterpret_cast<const float*>(Xs), lane, accm);
-          else
-            consume_stage<TN, TA, RC>(stg, rows, npst, p0, Xs, rg, cg, acc);
+          else  // the near field: leaf rows, one variant (keeps the kernel's code small)
+            consume_stage<TN, TA, RC, false>(stg, rows, npst, p0, Xs, rg, cg, acc);
         } else {
           if (is_near)
             consume_stage<TN, TA, RC>(stg, rows, npst, p0, Xs, rg, cg, acc);
