@@ -1158,7 +1158,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(TA) == 8 ? 1 : 2)
 // Claim order of the groups.  The emission order below is a valid
 // dependency order but makes warps claim groups long before their inputs
 // exist.  This list scheduler simulates the launch: kWorkers warps, a group
-// costs a fixed latency plus its bytes at a warp's share of HBM bandwidth, a
+// costs a fixed latency (its record, its inputs' signal path and the copy
+// latency; with the 2 us of a bare copy the simulated chain ran ahead of the
+// real one, and warps claimed chain groups long before their inputs were
+// complete) plus its bytes at a warp's share of HBM bandwidth, a
 // group is ready once every counter it waits for has seen all of its
 // contributions, and among ready groups the one with the longest remaining
 // dependency path (upward rank) starts first.  Groups are then claimed in
@@ -1172,7 +1175,7 @@ void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups
   start.assign(ng, 0.f);
   makespan = 0.f;
   if (ng < 1) return;
-  constexpr double kWorkers = 148 * 8, kLatency = 2.0e-6, kBandwidth = 6.0e12;  // s, B/s
+  constexpr double kWorkers = 148 * 8, kLatency = 10.0e-6, kBandwidth = 6.0e12;  // s, B/s
   std::vector<double> cost(ng);
   std::vector<int> sig(ng, -1);
   std::vector<std::vector<std::pair<int, int>>> waits(ng);
