@@ -104,9 +104,9 @@ TRAFFIC = {
     "green_aca": ("paper_1810_08429_b300/csrc/build.cu",
                   "44e68fc10fa230bed4647f73cdb392b198276e1ee26b782e4c38c37513b95713", 29.04e6 / 13),
     "mv_persistent.f32": ("paper_1810_08429_b300/csrc/matvec.cu",
-                          "90eeb48bee6df5ffa900f27387a66c7d74e28ecae1e7821bdf353a082dcff36d", 480.99e6),
+                          "fde4e836840b6a81776641bd075a418369aca1490b08cbadc3eaed066303fac8", 480.99e6),
     "mv_persistent.bf16": ("paper_1810_08429_b300/csrc/matvec.cu",
-                           "90eeb48bee6df5ffa900f27387a66c7d74e28ecae1e7821bdf353a082dcff36d", 270.84e6),
+                           "fde4e836840b6a81776641bd075a418369aca1490b08cbadc3eaed066303fac8", 272.54e6),
 }
 
 
