@@ -110,6 +110,24 @@ TRAFFIC = {
 }
 
 
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of a list of floats over all ranks of the default
+    process group (the values themselves when there is none)."""
+    import torch
+    import torch.distributed as dist
+    vals = [float(v) for v in values]
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return vals
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_gbs(bytes_per_rank, ms_max, world):
+    """Whole-job throughput: every rank's bytes over the slowest rank's time."""
+    return world * bytes_per_rank / (ms_max * 1e-3) / 1e9
+
+
 def captured_traffic(name):
     import hashlib
     if name not in TRAFFIC:
@@ -362,10 +380,6 @@ def main():
     gca.profile_enable(False)
     phases = gca.profile_read()
     total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
     clk = clocks.summary()
 
     agg = {}
@@ -377,7 +391,13 @@ def main():
     nm = len(MESHES)
     bytes_by = {p: sum(product_bytes(s, p if p != "f32T" else "f32", n, NRHS) for s in stats)
                 for p in ("f64", "f32", "bf16", "f32T")}
-    gbs = {p: bytes_by[p] * K / (agg[p] * 1e-3) / 1e9 for p in bytes_by}
+    # replicas: the slowest rank's times, every rank's bytes (`value` and the
+    # other throughputs below are whole-job figures)
+    keys = ["total"] + list(bytes_by) + ["build"]
+    worst = dict(zip(keys, max_over_ranks([total_ms] + [agg[p] for p in bytes_by] + [agg["build"]], dev)))
+    total_ms = worst["total"]
+    agg["build"] = worst["build"]
+    gbs = {p: whole_job_gbs(bytes_by[p] * K, worst[p], 1) for p in bytes_by}
     hbm_peak, peak_kind = measured_peaks()
 
     # accuracy of the reduced-precision products against the float64 product
@@ -446,7 +466,7 @@ def main():
             e2e_ms.append(a.elapsed_time(b))
     h2d = sum(x.numel() * 4 for x in xs32)
     d2h = h2d
-    e2e_val = bytes_by["f32"] / (statistics.median(e2e_ms) * 1e-3) / 1e9
+    e2e_val = whole_job_gbs(bytes_by["f32"], max_over_ranks([statistics.median(e2e_ms)], dev)[0], 1)
 
     launches_per_step = sum(l for (l, _) in phases.values()) / K
 
