@@ -24,8 +24,13 @@
  *     unspecified and no handle is returned.
  *   - Host pointers (meshes, trees, parameter structs, export buffers) are
  *     owned by the caller and only read/written during the call.
- *   - Device pointers (x, y of the products) are owned by the caller and
- *     must be valid device memory of the current device.
+ *   - The products' x and y are owned by the caller: memory of the current
+ *     device, or page-locked host memory mapped into the device's address
+ *     space (cudaHostAlloc, cudaMallocHost, or cudaHostRegister with
+ *     cudaHostRegisterMapped), which the product reads and writes in place
+ *     over the bus -- the transfer then happens inside the product's own
+ *     kernels.  Any other pointer (pageable host memory, another device's
+ *     memory) is refused with GCA_ERR_INVALID_ARG.
  *   - Handles own all of their device memory until gca_free().
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
  *     default stream.  Products are stream ordered and do not synchronise.
@@ -212,9 +217,10 @@ int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t max_clusters
 int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
               void* stream, gca_h2** out);
 
-/* y = G_H2 x for nrhs right-hand sides.  x: device, column-major n x nrhs
- * with leading dimension ldx >= n, rows in original triangle order; y:
- * device, same layout with ldy >= n, overwritten.  Element type float64
+/* y = G_H2 x for nrhs right-hand sides.  x: column-major n x nrhs with
+ * leading dimension ldx >= n, rows in original triangle order; y: same layout
+ * with ldy >= n, overwritten (device or mapped page-locked host memory, see
+ * the conventions above).  Element type float64
  * for GCA_F64, float32 otherwise.  x and y must not overlap.  The handle
  * keeps internal work buffers: calls on the same handle must be ordered on
  * one stream.  1 <= nrhs <= 4096.  Errors: INVALID_ARG, CUDA, OOM. */
@@ -273,7 +279,7 @@ int gca_peak_probe(double* fp64_flops, double* fp32_flops);
  * >= 1, meshes[i] with trees[i]); the batch owns the handles (read them with
  * gca_batch_handle, never free them individually).  The batched products take
  * per-mesh nrhs, x, ldx, y, ldy arrays (host arrays of length count; x, y
- * device pointers with the conventions of h2_matvec).  Calls on one batch must
+ * with the conventions of h2_matvec).  Calls on one batch must
  * be ordered on one stream.  Errors: as gca_build / h2_matvec. */
 int gca_build_batch(int32_t count, const gca_mesh* meshes, const gca_tree* trees,
                     const gca_params* params, void* stream, gca_h2_batch** out);

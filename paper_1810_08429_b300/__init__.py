@@ -257,19 +257,16 @@ class H2:
         return self.stats()["n"]
 
     def matvec(self, x, prec="f64", transpose=False, out=None, stream=None):
-        """y = G_H2 x (or G_H2^T x) for a CUDA tensor x of shape (n,) or (n, R)."""
+        """y = G_H2 x (or G_H2^T x) for x of shape (n,) or (n, R), a tensor on the
+        GPU or in page-locked host memory (read in place by the product); the
+        result is allocated beside x unless `out` is given."""
         import torch
         p = _PREC[prec]
         dt = torch.float64 if p == F64 else torch.float32
-        vec = x.dim() == 1
-        x2 = x[:, None] if vec else x
-        if x2.dtype != dt or not x2.is_cuda:
-            raise TypeError(f"x must be a CUDA {dt} tensor")
-        if x2.stride(0) != 1:
-            x2 = x2.t().contiguous().t()
+        x2, vec = _as_colmajor(x, dt)
         n, R = x2.shape
         if out is None:
-            out = torch.empty((R, n), dtype=dt, device=x2.device).t()
+            out = _empty_like_colmajor(x2, dt)
         y2 = out[:, None] if out.dim() == 1 else out
         if y2.stride(0) != 1 or y2.shape != (n, R):
             raise ValueError("out must be column-major (n, R)")
@@ -314,11 +311,21 @@ def build(vertices, triangles, tree, params, stream=None):
 def _as_colmajor(x, dt):
     vec = x.dim() == 1
     x2 = x[:, None] if vec else x
-    if x2.dtype != dt or not x2.is_cuda:
-        raise TypeError(f"x must be a CUDA {dt} tensor")
+    if x2.dtype != dt or not (x2.is_cuda or x2.is_pinned()):
+        raise TypeError(f"x must be a {dt} tensor on the GPU or in page-locked host memory")
     if x2.stride(0) != 1:
         x2 = x2.t().contiguous().t()
+        if not x2.is_cuda:
+            x2 = x2.pin_memory()
     return x2, vec
+
+
+def _empty_like_colmajor(x2, dt):
+    """A column-major (n, R) result beside x2: on its GPU, or page-locked."""
+    import torch
+    if x2.is_cuda:
+        return torch.empty((x2.shape[1], x2.shape[0]), dtype=dt, device=x2.device).t()
+    return torch.empty((x2.shape[1], x2.shape[0]), dtype=dt, pin_memory=True).t()
 
 
 class Batch:
@@ -363,7 +370,7 @@ class Batch:
             raise ValueError("one right-hand side block per mesh")
         xs2, vecs = zip(*[_as_colmajor(x, dt) for x in xs])
         if outs is None:
-            outs = [torch.empty((x2.shape[1], x2.shape[0]), dtype=dt, device=x2.device).t() for x2 in xs2]
+            outs = [_empty_like_colmajor(x2, dt) for x2 in xs2]
         ys2 = [o[:, None] if o.dim() == 1 else o for o in outs]
         nrhs = (ctypes.c_int32 * k)(*[x2.shape[1] for x2 in xs2])
         xp = (ctypes.c_void_p * k)(*[x2.data_ptr() for x2 in xs2])

@@ -179,6 +179,7 @@ struct gca_h2 {
 
   // device: geometry and tree
   gca::DevMem d_vert, d_tri, d_perm, d_begin, d_end, d_rank;
+  gca::DevMem d_iperm;  // inverse of perm: position in cluster order of each triangle
   // device: block lists (build kernels)
   gca::DevMem d_far_t, d_far_s, d_soff, d_near_t, d_near_s, d_noff;
   // device: coefficients, row-major float64 (as exported)

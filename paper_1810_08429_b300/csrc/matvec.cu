@@ -109,6 +109,7 @@ struct SlotArgs {
   TV* y;                       // caller's y, original order, column-major
   int64_t ldy;
   const int* perm;
+  const int* iperm;            // inverse of perm
   const TV* xp;                // x in cluster order [n][R]
   TV* yp;                      // y in cluster order [n][R] (zeroed)
   TV* xh;                      // [rank_sum][R]
@@ -328,29 +329,66 @@ __device__ __forceinline__ void add_row(double* p, const double* v, int valid_co
 }
 
 // x (original order) -> x in cluster order, all slots of a launch
-// (blockIdx.y = slot)
+// (blockIdx.y = slot).  The caller's x is read in its own order (coalesced,
+// 16 bytes a thread where the columns allow it: x may be page-locked host
+// memory read over the bus, where fewer, wider requests matter) and written
+// to its cluster-order position.
 template <typename TV>
 __global__ void k_gather(const SlotArgs<TV>* __restrict__ dslots, const __grid_constant__ SlotPack<TV> pack,
                          int inline_slots) {
   const SlotArgs<TV>& sa = inline_slots ? pack.s[blockIdx.y] : dslots[blockIdx.y];
+  constexpr int V = 16 / (int)sizeof(TV);
+  TV* xp = const_cast<TV*>(sa.xp);
+  if (sa.n % V == 0 && sa.ldx % V == 0 && (reinterpret_cast<uintptr_t>(sa.x) & 15) == 0) {
+    const int nv = sa.n / V;
+    const int64_t tot = (int64_t)nv * sa.R;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+      const int c = (int)(idx / nv), j = (int)(idx % nv) * V;
+      const uint4 u = *reinterpret_cast<const uint4*>(sa.x + j + (int64_t)c * sa.ldx);
+      TV v[V];
+      memcpy(v, &u, 16);
+#pragma unroll
+      for (int e = 0; e < V; ++e) xp[(int64_t)sa.iperm[j + e] * sa.R + c] = v[e];
+    }
+    return;
+  }
   const int64_t tot = (int64_t)sa.n * sa.R;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / sa.R), c = (int)(idx % sa.R);
-    const_cast<TV*>(sa.xp)[idx] = sa.x[sa.perm[i] + c * sa.ldx];
+    const int c = (int)(idx / sa.n), j = (int)(idx % sa.n);
+    xp[(int64_t)sa.iperm[j] * sa.R + c] = sa.x[j + c * sa.ldx];
   }
 }
 
-// y in cluster order -> caller's y (original order)
+// y in cluster order -> caller's y (original order), written in the
+// caller's order (coalesced, 16 bytes a thread where the columns allow it,
+// also into page-locked host memory)
 template <typename TV>
 __global__ void k_scatter(const SlotArgs<TV>* __restrict__ dslots, const __grid_constant__ SlotPack<TV> pack,
                           int inline_slots) {
   const SlotArgs<TV>& sa = inline_slots ? pack.s[blockIdx.y] : dslots[blockIdx.y];
+  constexpr int V = 16 / (int)sizeof(TV);
+  if (sa.n % V == 0 && sa.ldy % V == 0 && (reinterpret_cast<uintptr_t>(sa.y) & 15) == 0) {
+    const int nv = sa.n / V;
+    const int64_t tot = (int64_t)nv * sa.R;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+      const int c = (int)(idx / nv), j = (int)(idx % nv) * V;
+      TV v[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) v[e] = sa.yp[(int64_t)sa.iperm[j + e] * sa.R + c];
+      uint4 u;
+      memcpy(&u, v, 16);
+      *reinterpret_cast<uint4*>(sa.y + j + (int64_t)c * sa.ldy) = u;
+    }
+    return;
+  }
   const int64_t tot = (int64_t)sa.n * sa.R;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(idx / sa.n), i = (int)(idx % sa.n);
-    sa.y[sa.perm[i] + c * sa.ldy] = sa.yp[(int64_t)i * sa.R + c];
+    const int c = (int)(idx / sa.n), j = (int)(idx % sa.n);
+    sa.y[j + c * sa.ldy] = sa.yp[(int64_t)sa.iperm[j] * sa.R + c];
   }
 }
 
@@ -1431,6 +1469,11 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
 
 int finish_plan(gca_h2* h, cudaStream_t st) {
   h->max_rows = std::max(h->max_rank, h->max_leaf);
+  {
+    std::vector<int> iperm(h->n);
+    for (int i = 0; i < h->n; ++i) iperm[h->perm[i]] = i;
+    GCA_TRY(upload(h->d_iperm, iperm, st));
+  }
   GCA_TRY(build_items(h, 0, st));
   GCA_TRY(build_items(h, 1, st));
   GCA_TRY(h->d_status.alloc(sizeof(int)));
@@ -1497,6 +1540,7 @@ void fill_slot(SlotArgs<TV>& a, const gca_h2* h, int dir, int R, int RC, const v
   a.y = static_cast<TV*>(y);
   a.ldy = ldy;
   a.perm = h->d_perm.as<int>();
+  a.iperm = h->d_iperm.as<int>();
 }
 
 // Launches the persistent kernel with as many CTAs as fit on the device (found once per device and kernel, so that later launches
@@ -1698,9 +1742,49 @@ bool has_precision(const gca_h2* h, gca_prec prec) {
   return false;
 }
 
+// The address under which a kernel reads or writes a caller's x or y:
+// device memory of the current device as it is, page-locked host memory
+// mapped into the device's address space by its device alias; anything else
+// (pageable host memory, another device's memory) is refused rather than
+// handed to a kernel.
+int resolve_io(const void* p, const void** dev_p, const char* what, int i) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    a.type = cudaMemoryTypeUnregistered;
+  }
+  int dev = 0;
+  GCA_TRY_CUDA(cudaGetDevice(&dev));
+  if ((a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev) {
+    *dev_p = p;
+    return GCA_OK;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+    *dev_p = a.devicePointer;
+    return GCA_OK;
+  }
+  set_error(std::string("h2_matvec: ") + what + " of product " + std::to_string(i) +
+            " is neither memory of the current device nor mapped page-locked host memory");
+  return GCA_ERR_INVALID_ARG;
+}
+
 int launch_any(const gca_h2* const* hs, int count, gca_prec prec, bool trans, const int32_t* nrhs,
-               const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy,
+               const void* const* x_in, const int64_t* ldx, void* const* y_in, const int64_t* ldy,
                ProductCache& pc, int* status, cudaStream_t st) {
+  std::vector<const void*> xs(count);
+  std::vector<void*> ys(count);
+  for (int i = 0; i < count; ++i) {
+    if (!x_in[i] || !y_in[i]) {
+      set_error("h2_matvec: invalid arguments (handle " + std::to_string(i) + ")");
+      return GCA_ERR_INVALID_ARG;
+    }
+    const void* yd = nullptr;
+    GCA_TRY(resolve_io(x_in[i], &xs[i], "x", i));
+    GCA_TRY(resolve_io(y_in[i], &yd, "y", i));
+    ys[i] = const_cast<void*>(yd);
+  }
+  const void* const* x = xs.data();
+  void* const* y = ys.data();
   for (int i = 0; i < count; ++i) {
     if (!hs[i] || !x[i] || !y[i] || nrhs[i] < 1 || nrhs[i] > 4096 || ldx[i] < hs[i]->n ||
         ldy[i] < hs[i]->n) {
@@ -1902,6 +1986,12 @@ int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, 
     set_error("h2_matvec_noalloc: the handle was built without this precision");
     return GCA_ERR_UNSUPPORTED;
   }
+  const void* xd = nullptr;
+  const void* yd = nullptr;
+  GCA_TRY(resolve_io(x, &xd, "x", 0));
+  GCA_TRY(resolve_io(y, &yd, "y", 0));
+  x = xd;
+  y = const_cast<void*>(yd);
   unsigned char* base = nullptr;
   GCA_TRY(noalloc_scratch(&base));
   switch (prec) {

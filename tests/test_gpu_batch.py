@@ -60,3 +60,18 @@ def test_batch_matches_single(batch_case, prec):
         # same arithmetic; only the order of the atomic accumulations differs
         assert rel_cols(y.double().cpu().numpy(), single.double().cpu().numpy()) <= 1e-5
     assert b.status() == 0
+
+
+def test_batch_host_io(batch_case):
+    """A batched product with x and y in page-locked host memory (ragged R)
+    equals the same product on device buffers."""
+    gca, b, meshes, _ = batch_case
+    nrhs = [2, 16, 5]
+    xs = [synth.normal_rhs(len(t), r, seed=11 + i) for i, ((_, t), r) in enumerate(zip(meshes, nrhs))]
+    yd = b.matvec([torch.from_numpy(x).cuda() for x in xs], "f64")
+    yh = b.matvec([torch.from_numpy(x).pin_memory() for x in xs], "f64")
+    torch.cuda.synchronize()
+    for a, c in zip(yh, yd):
+        assert not a.is_cuda
+        c = c.cpu()
+        assert float((a - c).norm() / c.norm()) <= 1e-13

@@ -222,3 +222,36 @@ def test_invalid_matvec_arguments(gpu_1280):
         h.matvec_raw(0, 2, x.data_ptr(), 100, x.data_ptr(), 1280, None)
     with pytest.raises(gca.GCAError):
         h.matvec_raw(7, 2, x.data_ptr(), 1280, x.data_ptr(), 1280, None)
+
+
+def test_pageable_host_memory_refused(gpu_1280):
+    import paper_1810_08429_b300 as gca
+    h, _, _ = gpu_1280
+    x = np.zeros((2, 1280))  # pageable host memory: refused before any launch
+    y = torch.zeros(1280, 2, dtype=torch.float64, device="cuda")
+    with pytest.raises(gca.GCAError):
+        h.matvec_raw(0, 2, x.ctypes.data, 1280, y.data_ptr(), 1280, None)
+    with pytest.raises(gca.GCAError):
+        h.matvec_raw(0, 2, y.data_ptr(), 1280, x.ctypes.data, 1280, None)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_host_io_matches_device_io(gpu_1280, h2_1280, prec):
+    """x and y in page-locked host memory, read and written in place by the
+    product, give the product of device x and y (and the oracle's)."""
+    h, _, _ = gpu_1280
+    dt = torch.float64 if prec == "f64" else torch.float32
+    x = synth.normal_rhs(1280, 3, seed=4)
+    xd = torch.from_numpy(x).to("cuda", dt)
+    xh = torch.from_numpy(x).to(dt).pin_memory()
+    yd = h.matvec(xd, prec).cpu()
+    yh = h.matvec(xh, prec)
+    torch.cuda.synchronize()
+    assert not yh.is_cuda and yh.is_pinned()
+    assert rel_cols(yh.double().numpy(), yd.double().numpy()) <= (1e-13 if prec == "f64" else 1e-6)
+    if prec == "f64":
+        assert rel_cols(yh.numpy(), oh2.matvec(h2_1280, x)) <= TOL64
+    yt = h.matvec(xh, prec, transpose=True)
+    torch.cuda.synchronize()
+    assert rel_cols(yt.double().numpy(), h.matvec(xd, prec, transpose=True).cpu().double().numpy()) <= \
+        (1e-13 if prec == "f64" else 1e-6)
