@@ -294,6 +294,33 @@ int h2_matvec_transpose_batch(const gca_h2_batch* b, gca_prec prec, const int32_
 int gca_batch_status(const gca_h2_batch* b, int32_t* status);
 void gca_free_batch(gca_h2_batch* b);
 
+/* Autotuner of the products' tile width (not part of the method; a service
+ * to callers).  A product runs its right-hand sides in chunks of W columns,
+ * one warp tile per chunk, with W one of 1, 2, 4, 8, 16; by default W is the
+ * smallest of them at or above the largest nrhs (16 from 16 on).
+ * gca_tune_batch times the default W and its half and quarter on the given
+ * batched product (arguments as h2_matvec_batch / h2_matvec_transpose_batch;
+ * the product is run in place and y is overwritten), records the fastest in
+ * a process-wide table under the key (device name, precision, direction,
+ * largest nrhs, floor(log2(total rows))) and returns it in *width (may be
+ * NULL).  Later products (single or batched) whose key is in the table use
+ * that width; h2_matvec_noalloc always uses the default.  Synchronises the
+ * stream.  Errors: as h2_matvec_batch.
+ * gca_tune_save writes the table to a text file, one "key width" line per
+ * entry (key = device|precision|transpose|nrhs|log2rows, spaces in the device
+ * name written as '_'); gca_tune_load merges such a file into the table
+ * (INVALID_ARG on a malformed line, leaving the table unchanged);
+ * gca_tune_get reads the width recorded for a key (0: none); gca_tune_clear
+ * empties the table. */
+int gca_tune_batch(const gca_h2_batch* b, gca_prec prec, int32_t transpose, const int32_t* nrhs,
+                   const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy,
+                   void* stream, int32_t* width);
+int gca_tune_save(const char* path);
+int gca_tune_load(const char* path);
+int gca_tune_get(const char* device, gca_prec prec, int32_t transpose, int32_t nrhs, int64_t rows,
+                 int32_t* width);
+void gca_tune_clear(void);
+
 /* Sticky error bits of the products run on this handle so far (0: none;
  * 1: a bounded device-side wait of the persistent product kernel expired;
  * 2: the kernel met a malformed work record).  With any bit set the results

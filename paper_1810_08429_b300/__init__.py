@@ -107,6 +107,15 @@ def _load():
         "gca_profile_read": (ctypes.c_int, [ctypes.POINTER(_Phase), ctypes.c_int32,
                                             ctypes.POINTER(ctypes.c_int32)]),
         "gca_peak_probe": (ctypes.c_int, [_f64p, _f64p]),
+        "gca_tune_batch": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int64), vp,
+                                          ctypes.POINTER(ctypes.c_int32)]),
+        "gca_tune_save": (ctypes.c_int, [ctypes.c_char_p]),
+        "gca_tune_load": (ctypes.c_int, [ctypes.c_char_p]),
+        "gca_tune_get": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
+        "gca_tune_clear": (None, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -360,8 +369,18 @@ class Batch:
         _check(lib.gca_batch_status(self._b, ctypes.byref(v)), "gca_batch_status")
         return v.value
 
+    def tune(self, xs, prec="f32", transpose=False, outs=None, stream=None):
+        """Autotune the tile width of this product (``gca_tune_batch``): runs it
+        with each candidate width (outs are overwritten), records the fastest
+        for later products with the same key and returns it."""
+        return self._call(xs, prec, transpose, outs, stream, tune=True)
+
     def matvec(self, xs, prec="f32", transpose=False, outs=None, stream=None):
-        """[G_i x_i] (or transposes) for CUDA tensors x_i of shape (n_i,) or (n_i, R_i)."""
+        """[G_i x_i] (or transposes) for tensors x_i of shape (n_i,) or (n_i, R_i) on
+        the GPU or in page-locked host memory."""
+        return self._call(xs, prec, transpose, outs, stream, tune=False)
+
+    def _call(self, xs, prec, transpose, outs, stream, tune):
         import torch
         p = _PREC[prec]
         dt = torch.float64 if p == F64 else torch.float32
@@ -377,9 +396,37 @@ class Batch:
         yp = (ctypes.c_void_p * k)(*[y2.data_ptr() for y2 in ys2])
         ldx = (ctypes.c_int64 * k)(*[x2.stride(1) if x2.shape[1] > 1 else x2.shape[0] for x2 in xs2])
         ldy = (ctypes.c_int64 * k)(*[y2.stride(1) if y2.shape[1] > 1 else y2.shape[0] for y2 in ys2])
+        if tune:
+            w = ctypes.c_int32(0)
+            _check(lib.gca_tune_batch(self._b, p, 1 if transpose else 0, nrhs, xp, ldx, yp, ldy,
+                                      _stream_ptr(stream), ctypes.byref(w)), "gca_tune_batch")
+            return w.value
         fn = lib.h2_matvec_transpose_batch if transpose else lib.h2_matvec_batch
         _check(fn(self._b, p, nrhs, xp, ldx, yp, ldy, _stream_ptr(stream)), "h2_matvec_batch")
         return [o[:, 0] if v and o.dim() == 2 else o for o, v in zip(outs, vecs)]
+
+
+def tune_save(path):
+    """Write the tile-width table to a text file (``gca_tune_save``)."""
+    _check(lib.gca_tune_save(os.fsencode(path)), "gca_tune_save")
+
+
+def tune_load(path):
+    """Merge a table written by ``tune_save`` (``gca_tune_load``)."""
+    _check(lib.gca_tune_load(os.fsencode(path)), "gca_tune_load")
+
+
+def tune_get(device, prec, transpose, nrhs, rows):
+    """Tile width recorded for a key, 0 if none (``gca_tune_get``)."""
+    w = ctypes.c_int32(0)
+    _check(lib.gca_tune_get(device.encode(), _PREC.get(prec, prec), 1 if transpose else 0, nrhs, rows,
+                            ctypes.byref(w)), "gca_tune_get")
+    return w.value
+
+
+def tune_clear():
+    """Empty the tile-width table (``gca_tune_clear``)."""
+    lib.gca_tune_clear()
 
 
 def build_batch(meshes, trees, params, stream=None):

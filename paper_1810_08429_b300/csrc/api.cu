@@ -212,6 +212,30 @@ int gca_batch_status(const gca_h2_batch* b, int32_t* status) {
 
 void gca_free_batch(gca_h2_batch* b) { delete b; }
 
+int gca_tune_batch(const gca_h2_batch* b, gca_prec prec, int32_t transpose, const int32_t* nrhs,
+                   const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy, void* stream,
+                   int32_t* width) {
+  int w = 0;
+  const int st = gca::tune_batch(b, prec, transpose != 0, nrhs, x, ldx, y, ldy,
+                                 static_cast<cudaStream_t>(stream), &w);
+  if (st == GCA_OK && width) *width = w;
+  return st;
+}
+
+int gca_tune_save(const char* path) { return gca::tune_save(path); }
+
+int gca_tune_load(const char* path) { return gca::tune_load(path); }
+
+int gca_tune_get(const char* device, gca_prec prec, int32_t transpose, int32_t nrhs, int64_t rows,
+                 int32_t* width) {
+  int w = 0;
+  const int st = gca::tune_get(device, prec, transpose != 0, nrhs, rows, &w);
+  if (st == GCA_OK && width) *width = w;
+  return st;
+}
+
+void gca_tune_clear(void) { gca::tune_clear(); }
+
 const char* gca_strerror(int status) {
   switch (status) {
     case GCA_OK: return "ok";

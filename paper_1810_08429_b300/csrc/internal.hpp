@@ -121,6 +121,13 @@ int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, 
 int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* nrhs,
                  const void* const* x, const int64_t* ldx, void* const* y, const int64_t* ldy,
                  cudaStream_t st);
+// autotuner of the products' tile width (matvec.cu)
+int tune_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* nrhs, const void* const* x,
+               const int64_t* ldx, void* const* y, const int64_t* ldy, cudaStream_t st, int* rc_out);
+int tune_save(const char* path);
+int tune_load(const char* path);
+int tune_get(const char* device, gca_prec prec, bool trans, int32_t nrhs, int64_t rows, int* rc);
+void tune_clear();
 int matvec(const gca_h2* h, gca_prec prec, bool trans, int32_t nrhs, const void* x, int64_t ldx,
            void* y, int64_t ldy, cudaStream_t st);
 

@@ -43,6 +43,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <cstdio>
+#include <map>
 #include <mutex>
 #include <queue>
 #include <string>
@@ -1718,17 +1720,68 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   return GCA_OK;
 }
 
+// ------------------------------------------------------------- autotuner
+//
+// The tile width RC (right-hand sides of a warp tile; a product runs in
+// chunks of RC columns) is a per-launch choice among the compiled widths 1,
+// 2, 4, 8 and 16.  By default the smallest width at or above the largest R
+// (16 from R = 16 on).  gca_tune_batch times the candidate widths on a real
+// product and records the fastest per (device name, precision, direction,
+// largest R, log2 of the total rows); later products with that key use it.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+thread_local int g_force_rc = 0;  // width forced while tuning (0: none)
+
+int default_width(int R) { return R >= 16 ? 16 : (R > 4 ? 8 : (R > 2 ? 4 : (R > 1 ? 2 : 1))); }
+
+std::string device_name() {
+  int dev = 0;
+  cudaDeviceProp pr{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown";
+  }
+  std::string nm(pr.name);
+  for (char& c : nm)
+    if (c == '|' || c == ' ' || c == '\n') c = '_';
+  return nm;
+}
+
+std::string tune_key(const std::string& dev, int prec, int dir, int R, int64_t rows) {
+  int lg = 0;
+  while (lg < 62 && (int64_t(1) << (lg + 1)) <= rows) ++lg;
+  return dev + "|" + std::to_string(prec) + "|" + std::to_string(dir) + "|" + std::to_string(R) + "|" +
+         std::to_string(lg);
+}
+
+int tuned_width(int prec, int dir, int R, int64_t rows) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune.empty()) return 0;
+  const auto it = g_tune.find(tune_key(device_name(), prec, dir, R, rows));
+  return it == g_tune.end() ? 0 : it->second;
+}
+
 template <typename T, typename TN, typename TA, typename TV>
 int launch(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, const void* const* x,
            const int64_t* ldx, void* const* y, const int64_t* ldy, ProductCache& pc, int* status,
            cudaStream_t st) {
   int R = 1;
-  for (int i = 0; i < count; ++i) R = std::max(R, (int)nrhs[i]);
-  if (R >= 16) return launch_rc<T, TN, TA, TV, 16>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
-  if (R > 4) return launch_rc<T, TN, TA, TV, 8>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
-  if (R > 2) return launch_rc<T, TN, TA, TV, 4>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
-  if (R > 1) return launch_rc<T, TN, TA, TV, 2>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
-  return launch_rc<T, TN, TA, TV, 1>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+  int64_t rows = 0;
+  for (int i = 0; i < count; ++i) {
+    R = std::max(R, (int)nrhs[i]);
+    rows += hs[i]->n;
+  }
+  constexpr int prec = sizeof(T) == 8 ? GCA_F64 : (sizeof(T) == 4 ? GCA_F32 : GCA_BF16);
+  int rc = g_force_rc;
+  if (rc == 0) rc = tuned_width(prec, dir, R, rows);
+  if (rc == 0) rc = default_width(R);
+  switch (rc) {
+    case 16: return launch_rc<T, TN, TA, TV, 16>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+    case 8: return launch_rc<T, TN, TA, TV, 8>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+    case 4: return launch_rc<T, TN, TA, TV, 4>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+    case 2: return launch_rc<T, TN, TA, TV, 2>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+    default: return launch_rc<T, TN, TA, TV, 1>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+  }
 }
 
 // the handle kept the panels of this precision (gca_params.flags)
@@ -1858,6 +1911,132 @@ int matvec_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t
   std::vector<const gca_h2*> hs(b->h.begin(), b->h.end());
   return launch_any(hs.data(), (int)hs.size(), prec, trans, nrhs, x, ldx, y, ldy, b->pc,
                     b->d_status.as<int>(), st);
+}
+
+int tune_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* nrhs, const void* const* x,
+               const int64_t* ldx, void* const* y, const int64_t* ldy, cudaStream_t st, int* rc_out) {
+  if (!b || b->h.empty() || !nrhs || !x || !ldx || !y || !ldy || !rc_out) {
+    set_error("gca_tune_batch: invalid arguments");
+    return GCA_ERR_INVALID_ARG;
+  }
+  int R = 1;
+  int64_t rows = 0;
+  for (size_t i = 0; i < b->h.size(); ++i) {
+    R = std::max(R, (int)nrhs[i]);
+    rows += b->h[i]->n;
+  }
+  const int d = default_width(R);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GCA_TRY_CUDA(cudaEventCreate(&e0));
+  GCA_TRY_CUDA(cudaEventCreate(&e1));
+  struct Ev {
+    cudaEvent_t a, b;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev{e0, e1};
+  int best = 0;
+  float best_ms = 0.f;
+  for (int rc : {d, d / 2, d / 4}) {
+    if (rc < 1) continue;
+    g_force_rc = rc;
+    int s = GCA_OK;
+    for (int w = 0; w < 2 && s == GCA_OK; ++w) s = matvec_batch(b, prec, trans, nrhs, x, ldx, y, ldy, st);
+    std::vector<float> ms;
+    for (int r = 0; r < 5 && s == GCA_OK; ++r) {
+      cudaEventRecord(e0, st);
+      s = matvec_batch(b, prec, trans, nrhs, x, ldx, y, ldy, st);
+      cudaEventRecord(e1, st);
+      float t = 0.f;
+      if (s == GCA_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)) {
+        set_error("gca_tune_batch: timing failed");
+        s = GCA_ERR_CUDA;
+      }
+      ms.push_back(t);
+    }
+    g_force_rc = 0;
+    if (s != GCA_OK) return s;
+    std::sort(ms.begin(), ms.end());
+    const float med = ms[ms.size() / 2];
+    if (best == 0 || med < best_ms) {
+      best = rc;
+      best_ms = med;
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(device_name(), (int)prec, trans ? 1 : 0, R, rows)] = best;
+  }
+  *rc_out = best;
+  return GCA_OK;
+}
+
+int tune_save(const char* path) {
+  if (!path) {
+    set_error("gca_tune_save: NULL path");
+    return GCA_ERR_INVALID_ARG;
+  }
+  std::FILE* f = std::fopen(path, "w");
+  if (!f) {
+    set_error(std::string("gca_tune_save: cannot open ") + path);
+    return GCA_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : g_tune) std::fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+  const bool ok = std::fclose(f) == 0;
+  if (!ok) {
+    set_error(std::string("gca_tune_save: write failed: ") + path);
+    return GCA_ERR_INVALID_ARG;
+  }
+  return GCA_OK;
+}
+
+int tune_load(const char* path) {
+  if (!path) {
+    set_error("gca_tune_load: NULL path");
+    return GCA_ERR_INVALID_ARG;
+  }
+  std::FILE* f = std::fopen(path, "r");
+  if (!f) {
+    set_error(std::string("gca_tune_load: cannot open ") + path);
+    return GCA_ERR_INVALID_ARG;
+  }
+  std::map<std::string, int> add;
+  char key[512];
+  int rc = 0;
+  int st = GCA_OK;
+  for (;;) {
+    const int got = std::fscanf(f, "%511s %d", key, &rc);
+    if (got == EOF) break;
+    if (got != 2 || (rc != 1 && rc != 2 && rc != 4 && rc != 8 && rc != 16)) {
+      set_error(std::string("gca_tune_load: malformed line in ") + path);
+      st = GCA_ERR_INVALID_ARG;
+      break;
+    }
+    add[key] = rc;
+  }
+  std::fclose(f);
+  if (st != GCA_OK) return st;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : add) g_tune[kv.first] = kv.second;
+  return GCA_OK;
+}
+
+int tune_get(const char* device, gca_prec prec, bool trans, int32_t nrhs, int64_t rows, int* rc) {
+  if (!device || !rc || nrhs < 1 || rows < 1) {
+    set_error("gca_tune_get: invalid arguments");
+    return GCA_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const auto it = g_tune.find(tune_key(device, (int)prec, trans ? 1 : 0, nrhs, rows));
+  *rc = it == g_tune.end() ? 0 : it->second;
+  return GCA_OK;
+}
+
+void tune_clear() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
 }
 
 // ------------------------------------------------------- no-alloc product
