@@ -105,16 +105,20 @@ struct SlotArgs {
   int nchunk;                  // right-hand-side chunks of RC columns
   int R;
   int n;
-  int pad;
+  int rc;                      // RC: columns of a chunk
+  int rank_sum;                // rows of x-hat and y-hat
   const TV* x;                 // caller's x, original order, column-major
   int64_t ldx;
   TV* y;                       // caller's y, original order, column-major
   int64_t ldy;
   const int* perm;
   const int* iperm;            // inverse of perm
-  const TV* xp;                // x in cluster order [n][R]
-  TV* yp;                      // y in cluster order [n][R] (zeroed)
-  TV* xh;                      // [rank_sum][R]
+  // the vectors of the recursion, chunk-major: column c of row i at
+  // ((c / RC) * rows + i) * RC + c % RC, so that the rows of one chunk are
+  // contiguous (one bulk copy per input block, whatever R)
+  const TV* xp;                // x in cluster order [nchunk][n][RC]
+  TV* yp;                      // y in cluster order [nchunk][n][RC] (zeroed)
+  TV* xh;                      // [nchunk][rank_sum][RC]
   TV* yh;
   int* counters;               // [2 nc]
 };
@@ -351,7 +355,7 @@ __global__ void k_gather(const SlotArgs<TV>* __restrict__ dslots, const __grid_c
       TV v[V];
       memcpy(v, &u, 16);
 #pragma unroll
-      for (int e = 0; e < V; ++e) xp[(int64_t)sa.iperm[j + e] * sa.R + c] = v[e];
+      for (int e = 0; e < V; ++e) xp[((int64_t)(c / sa.rc) * sa.n + sa.iperm[j + e]) * sa.rc + c % sa.rc] = v[e];
     }
     return;
   }
@@ -359,7 +363,7 @@ __global__ void k_gather(const SlotArgs<TV>* __restrict__ dslots, const __grid_c
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(idx / sa.n), j = (int)(idx % sa.n);
-    xp[(int64_t)sa.iperm[j] * sa.R + c] = sa.x[j + c * sa.ldx];
+    xp[((int64_t)(c / sa.rc) * sa.n + sa.iperm[j]) * sa.rc + c % sa.rc] = sa.x[j + c * sa.ldx];
   }
 }
 
@@ -379,7 +383,7 @@ __global__ void k_scatter(const SlotArgs<TV>* __restrict__ dslots, const __grid_
       const int c = (int)(idx / nv), j = (int)(idx % nv) * V;
       TV v[V];
 #pragma unroll
-      for (int e = 0; e < V; ++e) v[e] = sa.yp[(int64_t)sa.iperm[j + e] * sa.R + c];
+      for (int e = 0; e < V; ++e) v[e] = sa.yp[((int64_t)(c / sa.rc) * sa.n + sa.iperm[j + e]) * sa.rc + c % sa.rc];
       uint4 u;
       memcpy(&u, v, 16);
       *reinterpret_cast<uint4*>(sa.y + j + (int64_t)c * sa.ldy) = u;
@@ -390,7 +394,7 @@ __global__ void k_scatter(const SlotArgs<TV>* __restrict__ dslots, const __grid_
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(idx / sa.n), j = (int)(idx % sa.n);
-    sa.y[j + c * sa.ldy] = sa.yp[(int64_t)sa.iperm[j] * sa.R + c];
+    sa.y[j + c * sa.ldy] = sa.yp[((int64_t)(c / sa.rc) * sa.n + sa.iperm[j]) * sa.rc + c % sa.rc];
   }
 }
 
@@ -674,7 +678,7 @@ __device__ __forceinline__ void seg_geom(const SlotArgs<TV>& sa, uint32_t a8, ui
 
 template <typename TV, int RC>
 __device__ __forceinline__ bool bulk_inputs(const SlotArgs<TV>& sa) {
-  return RC == sa.R && (RC * sizeof(TV)) % 16 == 0;
+  return (RC * sizeof(TV)) % 16 == 0;
 }
 
 // ------------------------------------------------------------- producer
@@ -949,7 +953,9 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
         const int xin = (fl >> 8) & 0xff;
         const int k = (int)(rk >> 16);
         const int xrow = __shfl_sync(FULL, d.x_row, s);
-        const TV* X = (xin == kInXh ? sa.xh : (xin == kInYh ? sa.yh : sa.xp)) + (int64_t)xrow * sa.R;
+        // rows [xrow, xrow + k) of chunk c0 / RC of the input vector
+        const TV* X = (xin == kInXh ? sa.xh : (xin == kInYh ? sa.yh : sa.xp)) +
+                      ((int64_t)(u.c0 / RC) * (xin == kInX ? sa.n : sa.rank_sum) + xrow) * RC;
         // rows past the block's columns meet zero panel columns (and, on the
         // tensor cores, the zeroed upper half of a last single panel): they
         // are copied in as zeros, so the buffer only ever gets bulk copies
@@ -970,7 +976,7 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
           const int kp = kz;
           for (int i = lane; i < kp * RC; i += 32) {
             const int r = i / RC, c = i % RC;
-            Xs[i] = (r < k && c0 + c < sa.R) ? (TA)__ldcg(X + (int64_t)r * sa.R + c0 + c) : (TA)0;
+            Xs[i] = (r < k && c0 + c < sa.R) ? (TA)__ldcg(X + (int64_t)r * RC + c) : (TA)0;
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(P.xfull(j));
@@ -1095,42 +1101,34 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
       const int out = (fl >> 16) & 0xff;
       TV* obase = out == kOutXh ? sa.xh : (out == kOutYh ? sa.yh : sa.yp);
       const int o_row = __shfl_sync(FULL, d.o_row, s);
-      const int R = sa.R;
+      // rows of this chunk of the output (chunk-major, RC columns a row; the
+      // columns past R are padding that nothing reads)
+      TV* const ochunk = obase + (int64_t)(c0 / RC) * (out == kOutY ? sa.n : sa.rank_sum) * RC;
       if constexpr (kTC) {
         if (tc) {
           // accumulator fragments: rows 16 mt + g (+ 8), columns 8 nt + 2t (+ 1)
           const int g = lane >> 2, t = lane & 3;
-          const bool even = (R % 2) == 0;
 #pragma unroll
           for (int mt = 0; mt < 4; ++mt)
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
-              const int col = c0 + 8 * nt + 2 * t;
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
                 const int r = 16 * mt + g + 8 * h;
-                float* o = reinterpret_cast<float*>(obase) + ((int64_t)o_row + r) * R + col;
-                if (r < rows && col < R) {
-                  if (even && col + 1 < R) {
-                    red_add2(o, accm[mt][nt][2 * h], accm[mt][nt][2 * h + 1]);
-                  } else {
-                    red_add(o, accm[mt][nt][2 * h]);
-                    if (col + 1 < R) red_add(o + 1, accm[mt][nt][2 * h + 1]);
-                  }
-                }
+                float* o = reinterpret_cast<float*>(ochunk) + ((int64_t)o_row + r) * RC + 8 * nt + 2 * t;
+                if (r < rows) red_add2(o, accm[mt][nt][2 * h], accm[mt][nt][2 * h + 1]);
                 accm[mt][nt][2 * h] = accm[mt][nt][2 * h + 1] = 0.f;
               }
             }
           continue;
         }
       }
-      const int col0 = c0 + cg * Tl::CPL;
-      const int vc = min(Tl::CPL, R - col0);
-      const bool aligned = (R % 4) == 0 && (col0 % 4) == 0;
+      const int col0 = cg * Tl::CPL;
+      const bool aligned = (Tl::CPL * sizeof(TV)) % 16 == 0;
 #pragma unroll
       for (int i = 0; i < Tl::RPL; ++i) {
         const int r = rg + Tl::RG * i;
-        if (r < rows && vc > 0) add_row<Tl::CPL>(obase + ((int64_t)o_row + r) * R + col0, acc[i], vc, aligned);
+        if (r < rows) add_row<Tl::CPL>(ochunk + ((int64_t)o_row + r) * RC + col0, acc[i], Tl::CPL, aligned);
       }
 #pragma unroll
       for (int i = 0; i < Tl::RPL; ++i)
@@ -1536,7 +1534,8 @@ void fill_slot(SlotArgs<TV>& a, const gca_h2* h, int dir, int R, int RC, const v
   a.R = R;
   a.nchunk = (R + RC - 1) / RC;
   a.n = h->n;
-  a.pad = 0;
+  a.rc = RC;
+  a.rank_sum = (int)h->rank_sum;
   a.x = static_cast<const TV*>(x);
   a.ldx = ldx;
   a.y = static_cast<TV*>(y);
@@ -1607,7 +1606,7 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   std::vector<size_t> o_xh(count), o_yh(count), o_yp(count), o_cnt(count), o_xp(count);
   for (int i = 0; i < count; ++i) {
     const gca_h2* h = hs[i];
-    const int R = nrhs[i];
+    const int R = (nrhs[i] + RC - 1) / RC * RC;  // chunk-major vectors: whole chunks
     o_xh[i] = off;
     off += up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * R);
     o_yh[i] = off;
@@ -1620,7 +1619,7 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   const size_t zeroed = off;
   for (int i = 0; i < count; ++i) {
     o_xp[i] = off;
-    off += up256(sizeof(TV) * (size_t)hs[i]->n * nrhs[i]);
+    off += up256(sizeof(TV) * (size_t)hs[i]->n * ((nrhs[i] + RC - 1) / RC * RC));
   }
   std::vector<int> nchunk(count);
   int64_t work = 0, free_work = 0;
@@ -2094,8 +2093,9 @@ __global__ void k_put_slot(SlotArgs<TV> a, SlotArgs<TV>* dst) { *dst = a; }
 template <typename T, typename TN, typename TA, typename TV, int RC>
 int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* y, int64_t ldy,
                       unsigned char* base, size_t cap, cudaStream_t st) {
-  const size_t b_xh = up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * R);
-  const size_t b_yp = up256(sizeof(TV) * (size_t)h->n * R);
+  const int Rp = (R + RC - 1) / RC * RC;  // chunk-major vectors: whole chunks
+  const size_t b_xh = up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * Rp);
+  const size_t b_yp = up256(sizeof(TV) * (size_t)h->n * Rp);
   const size_t b_cnt = up256(sizeof(int) * 2 * (size_t)h->nc);
   const size_t o_xh = 256 + kZeroBytes, o_yh = o_xh + b_xh, o_yp = o_yh + b_xh, o_cnt = o_yp + b_yp;
   const size_t zeroed = o_cnt + b_cnt;
