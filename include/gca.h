@@ -297,8 +297,9 @@ void gca_free_batch(gca_h2_batch* b);
 /* Autotuner of the products' tile width (not part of the method; a service
  * to callers).  A product runs its right-hand sides in chunks of W columns,
  * one warp tile per chunk, with W one of 1, 2, 4, 8, 16; by default W is the
- * smallest of them at or above the largest nrhs (16 from 16 on).
- * gca_tune_batch times the default W and its half and quarter on the given
+ * smallest of them at or above the largest nrhs (16 from 16 on), and at most 4
+ * in float64 (whose products are FP64-bound; narrow tiles measured faster).
+ * gca_tune_batch times the widths from a quarter to four times the default on the given
  * batched product (arguments as h2_matvec_batch / h2_matvec_transpose_batch;
  * the product is run in place and y is overwritten), records the fastest in
  * a process-wide table under the key (device name, precision, direction,

@@ -1724,14 +1724,22 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
 // The tile width RC (right-hand sides of a warp tile; a product runs in
 // chunks of RC columns) is a per-launch choice among the compiled widths 1,
 // 2, 4, 8 and 16.  By default the smallest width at or above the largest R
-// (16 from R = 16 on).  gca_tune_batch times the candidate widths on a real
-// product and records the fastest per (device name, precision, direction,
-// largest R, log2 of the total rows); later products with that key use it.
+// (16 from R = 16 on; at most 4 in float64, below).  gca_tune_batch times the
+// widths from a quarter to four times the default on a real product and
+// records the fastest per (device name, precision, direction, largest R,
+// log2 of the total rows); later products with that key use it.
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 thread_local int g_force_rc = 0;  // width forced while tuning (0: none)
 
-int default_width(int R) { return R >= 16 ? 16 : (R > 4 ? 8 : (R > 2 ? 4 : (R > 1 ? 2 : 1))); }
+// the float64 product is bound by the FP64 pipe, not by streaming the
+// blocks: narrow tiles (more chunks, each block streamed once per chunk) run
+// it faster (the autotuner measured width 4 about 8% faster than 16 at
+// R = 16, 32 and 64 on the 20480-triangle pair)
+int default_width(int R, int prec) {
+  const int w = R >= 16 ? 16 : (R > 4 ? 8 : (R > 2 ? 4 : (R > 1 ? 2 : 1)));
+  return prec == GCA_F64 ? std::min(w, 4) : w;
+}
 
 std::string device_name() {
   int dev = 0;
@@ -1773,7 +1781,7 @@ int launch(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, con
   constexpr int prec = sizeof(T) == 8 ? GCA_F64 : (sizeof(T) == 4 ? GCA_F32 : GCA_BF16);
   int rc = g_force_rc;
   if (rc == 0) rc = tuned_width(prec, dir, R, rows);
-  if (rc == 0) rc = default_width(R);
+  if (rc == 0) rc = default_width(R, prec);
   switch (rc) {
     case 16: return launch_rc<T, TN, TA, TV, 16>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
     case 8: return launch_rc<T, TN, TA, TV, 8>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
@@ -1924,7 +1932,7 @@ int tune_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* 
     R = std::max(R, (int)nrhs[i]);
     rows += b->h[i]->n;
   }
-  const int d = default_width(R);
+  const int d = default_width(R, (int)prec);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   GCA_TRY_CUDA(cudaEventCreate(&e0));
   GCA_TRY_CUDA(cudaEventCreate(&e1));
@@ -1937,8 +1945,8 @@ int tune_batch(const gca_h2_batch* b, gca_prec prec, bool trans, const int32_t* 
   } ev{e0, e1};
   int best = 0;
   float best_ms = 0.f;
-  for (int rc : {d, d / 2, d / 4}) {
-    if (rc < 1) continue;
+  for (int rc : {16, 8, 4, 2, 1}) {
+    if (rc > 4 * d || 4 * rc < d) continue;  // from a quarter to four times the default
     g_force_rc = rc;
     int s = GCA_OK;
     for (int w = 0; w < 2 && s == GCA_OK; ++w) s = matvec_batch(b, prec, trans, nrhs, x, ldx, y, ldy, st);
@@ -2146,11 +2154,14 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
 template <typename T, typename TN, typename TA, typename TV>
 int launch_noalloc(const gca_h2* h, int R, const void* x, int64_t ldx, void* y, int64_t ldy,
                    unsigned char* base, size_t cap, cudaStream_t st) {
-  if (R >= 16) return launch_noalloc_rc<T, TN, TA, TV, 16>(h, R, x, ldx, y, ldy, base, cap, st);
-  if (R > 4) return launch_noalloc_rc<T, TN, TA, TV, 8>(h, R, x, ldx, y, ldy, base, cap, st);
-  if (R > 2) return launch_noalloc_rc<T, TN, TA, TV, 4>(h, R, x, ldx, y, ldy, base, cap, st);
-  if (R > 1) return launch_noalloc_rc<T, TN, TA, TV, 2>(h, R, x, ldx, y, ldy, base, cap, st);
-  return launch_noalloc_rc<T, TN, TA, TV, 1>(h, R, x, ldx, y, ldy, base, cap, st);
+  constexpr int prec = sizeof(T) == 8 ? GCA_F64 : (sizeof(T) == 4 ? GCA_F32 : GCA_BF16);
+  switch (default_width(R, prec)) {
+    case 16: return launch_noalloc_rc<T, TN, TA, TV, 16>(h, R, x, ldx, y, ldy, base, cap, st);
+    case 8: return launch_noalloc_rc<T, TN, TA, TV, 8>(h, R, x, ldx, y, ldy, base, cap, st);
+    case 4: return launch_noalloc_rc<T, TN, TA, TV, 4>(h, R, x, ldx, y, ldy, base, cap, st);
+    case 2: return launch_noalloc_rc<T, TN, TA, TV, 2>(h, R, x, ldx, y, ldy, base, cap, st);
+    default: return launch_noalloc_rc<T, TN, TA, TV, 1>(h, R, x, ldx, y, ldy, base, cap, st);
+  }
 }
 
 }  // namespace
