@@ -450,7 +450,10 @@ __device__ __forceinline__ void load_row(const TA* __restrict__ p, TA (&x)[CPL])
 }
 
 // One panel (P columns) of the lane's rows in the first NI row groups times
-// the staged input rows.
+// the staged input rows.  In float the products run as packed pairs
+// (fma.rn.f32x2: two adjacent right-hand sides of a row per instruction,
+// each rounded as a scalar fma), which halves the FMA instructions of the
+// issue-bound inner loop.
 template <typename T, typename TA, int RC, int NI>
 __device__ __forceinline__ void panel_fma(const unsigned char* panel, const TA* __restrict__ xr, int rg, int cg,
                                           TA (&part)[Tile<RC>::RPL][Tile<RC>::CPL]) {
@@ -464,10 +467,23 @@ __device__ __forceinline__ void panel_fma(const unsigned char* panel, const TA* 
   for (int kk = 0; kk < P; ++kk) {
     TA x[Tl::CPL];
     load_row<TA, Tl::CPL>(xr + kk * RC + cg * Tl::CPL, x);
+    if constexpr (std::is_same<TA, float>::value && Tl::CPL % 2 == 0) {
 #pragma unroll
-    for (int i = 0; i < NI; ++i)
+      for (int i = 0; i < NI; ++i) {
+        const float2 vv = make_float2(v[i][kk], v[i][kk]);
 #pragma unroll
-      for (int c = 0; c < Tl::CPL; ++c) part[i][c] = fma(v[i][kk], x[c], part[i][c]);
+        for (int c = 0; c < Tl::CPL; c += 2) {
+          const float2 p = __ffma2_rn(vv, make_float2(x[c], x[c + 1]), make_float2(part[i][c], part[i][c + 1]));
+          part[i][c] = p.x;
+          part[i][c + 1] = p.y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+#pragma unroll
+        for (int c = 0; c < Tl::CPL; ++c) part[i][c] = fma(v[i][kk], x[c], part[i][c]);
+    }
   }
 }
 
