@@ -104,9 +104,9 @@ TRAFFIC = {
     "green_aca": ("paper_1810_08429_b300/csrc/build.cu",
                   "44e68fc10fa230bed4647f73cdb392b198276e1ee26b782e4c38c37513b95713", 29.04e6 / 13),
     "mv_persistent.f32": ("paper_1810_08429_b300/csrc/matvec.cu",
-                          "f950cc0627d60ceced0157e142f1892332868b7ec7747fe1fc4c8bac4b597c14", 480.83e6),
+                          "96a4dc6dc53f5c89cff31187d76d8a0674c4ac4c26a55b23fcd078277bd6f00b", 481.23e6),
     "mv_persistent.bf16": ("paper_1810_08429_b300/csrc/matvec.cu",
-                           "f950cc0627d60ceced0157e142f1892332868b7ec7747fe1fc4c8bac4b597c14", 272.33e6),
+                           "96a4dc6dc53f5c89cff31187d76d8a0674c4ac4c26a55b23fcd078277bd6f00b", 272.48e6),
 }
 
 
