@@ -25,7 +25,13 @@ Steps, in the paper's order:
    tilde-tau_1 u tilde-tau_2 of its children (child 0 first), giving
    tilde-tau and V^_tau, which splits into the transfer matrices
    E_{tau_1} = V^_tau|tilde-tau_1 x tilde-tau and E_{tau_2}.  Leaves keep
-   V_tau = V^_tau.  The root gets no basis.
+   V_tau = V^_tau.  Only clusters whose basis the H^2 matrix uses get one:
+   the bases enter through the admissible blocks, G|tau-hat x sigma-hat ~
+   V_tau G|tilde-tau x tilde-sigma V_sigma^* (Sect. 4), and a parent's basis
+   is built from its children's, so a cluster needs a basis iff it or one of
+   its ancestors is in an admissible block.  The others (the root, and the
+   coarse levels of a closed surface) get an empty one: rank 0, no pivots,
+   zero-size V and E, which add nothing to the products.
 5. ``build_h2`` (Sect. 4): coupling matrices S_{tau sigma} = G|tilde-tau x
    tilde-sigma for admissible blocks and near-field blocks G|tau-hat x
    sigma-hat for inadmissible leaf pairs, all from ``galerkin.entries``.
@@ -137,15 +143,38 @@ class Bases:
     rank: np.ndarray = None
 
 
-def build_bases(gal, tree, lo, hi, params):
-    """Nested cluster bases by Green cross approximation (Sect. 3, Sect. 4)."""
+def needed_clusters(tree, far):
+    """needed[c]: c or one of its ancestors is in an admissible block."""
+    nc = len(tree["begin"])
+    needed = np.zeros(nc, dtype=bool)
+    for (t, s) in far:
+        needed[t] = needed[s] = True
+    for c in np.argsort(tree["level"], kind="stable"):   # top-down
+        for ch in (tree["child0"][c], tree["child1"][c]):
+            if ch >= 0 and needed[c]:
+                needed[ch] = True
+    return needed
+
+
+def build_bases(gal, tree, lo, hi, params, far=None):
+    """Nested cluster bases by Green cross approximation (Sect. 3, Sect. 4),
+    for the clusters that need one (all non-root clusters when `far` is
+    None); the others get empty bases."""
     nc = len(tree["begin"])
     diam = cluster.diameter(lo, hi)
     bases = Bases(pivots=[None] * nc, rank=np.zeros(nc, dtype=np.int64))
     margin = params.margin()
+    needed = np.ones(nc, dtype=bool) if far is None else needed_clusters(tree, far)
+    needed[0] = False
     order = np.argsort(-tree["level"], kind="stable")   # deepest level first
     for c in order:
-        if c == 0:
+        if not needed[c]:
+            bases.pivots[c] = np.zeros(0, dtype=tree["perm"].dtype)
+            if cluster.is_leaf(tree, c):
+                bases.V[c] = np.zeros((tree["end"][c] - tree["begin"][c], 0))
+            elif c != 0:
+                for ch in (tree["child0"][c], tree["child1"][c]):
+                    bases.E[ch] = np.zeros((bases.rank[ch], 0))
             continue
         z, nrm, w = omega_rule(lo[c], hi[c], diam[c], margin, params.box_gauss_m)
         bases.omega[c] = (z, nrm, w)
@@ -187,7 +216,7 @@ def build_h2(vertices, triangles, params, tree=None):
         tree = cluster.build_tree(vertices, triangles, params.leaf_size)
     lo, hi = cluster.cluster_boxes(vertices, triangles, tree)
     far, near = cluster.block_tree(tree, lo, hi, params.eta)
-    bases = build_bases(gal, tree, lo, hi, params)
+    bases = build_bases(gal, tree, lo, hi, params, far)
     S = {}
     for (t, s) in far:
         S[(t, s)] = gal.block(bases.pivots[t], bases.pivots[s])

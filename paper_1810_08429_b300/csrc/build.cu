@@ -867,6 +867,15 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   }
   GCA_TRY_CUDA(cudaGetLastError());
 
+  // A cluster basis enters the matrix only through the admissible blocks of
+  // the cluster and, by nestedness, of its ancestors (Sect. 4); the bases of
+  // the other clusters are not built (rank 0).
+  std::vector<char> needed(nc, 0);
+  for (size_t b = 0; b < h->far_t.size(); ++b) needed[h->far_t[b]] = needed[h->far_s[b]] = 1;
+  for (int L = 0; L < h->depth; ++L)
+    for (int c : h->by_level[L])
+      if (needed[c] && h->child0[c] >= 0) needed[h->child0[c]] = needed[h->child1[c]] = 1;
+
   // nested bases, level by level from the deepest
   h->rank.assign(nc, 0);
   h->poff.assign(nc, -1);
@@ -908,6 +917,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   for (int L = h->depth; L >= 1; --L) {
     std::vector<AcaJob> jobs;
     for (int c : h->by_level[L]) {
+      if (!needed[c]) continue;
       AcaJob j{};
       j.c = c;
       j.leaf = h->child0[c] < 0;
@@ -1023,9 +1033,10 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   std::vector<Segment> vseg, eseg;
   for (int c = 1; c < nc; ++c) {
     const int r = h->rank[c];
+    if (r == 0) continue;  // unused basis
     if (h->child0[c] < 0) {
       vseg.push_back({vh_off[c], h->voff[c], (int64_t)rows_of[c] * r});
-    } else if (c != 0) {
+    } else {
       const int c0 = h->child0[c], c1 = h->child1[c];
       eseg.push_back({vh_off[c], h->eoff[c0], (int64_t)h->rank[c0] * r});
       eseg.push_back({vh_off[c] + (int64_t)h->rank[c0] * r, h->eoff[c1], (int64_t)h->rank[c1] * r});

@@ -93,7 +93,13 @@ def check_leaf_bases(dump, tree, lo, hi, gal, params, rng, leaves=6, tol=1e-8):
             at += (tree["end"][c] - tree["begin"][c]) * rank[c]
     poff = np.concatenate([[0], np.cumsum(rank)])
     diam = cluster.diameter(lo, hi)
-    cand = [c for c in voff]
+    # leaves whose basis the H^2 matrix uses (they or an ancestor in an
+    # admissible block); the others must have none
+    needed = ogca.needed_clusters(tree, [tuple(b) for b in dump["far"].tolist()])
+    for c in voff:
+        if not needed[c]:
+            assert rank[c] == 0, f"basis of unused leaf {c}"
+    cand = [c for c in voff if needed[c]]
     flips = 0
     for c in rng.choice(cand, size=min(leaves, len(cand)), replace=False):
         rows = tree["perm"][tree["begin"][c]:tree["end"][c]]

@@ -80,22 +80,28 @@ def compare_coefficients(h2o, dump, tree, tol, tol_basis=None):
     par = cluster.parents({k: np.asarray(v) for k, v in tree.items()})
     # leaf bases
     at = 0
-    scale = max(np.abs(m).max() for m in h2o.bases.V.values())
+    scale = max(np.abs(m).max() for m in h2o.bases.V.values() if m.size)
     for c in range(1, nc):
         if tree["child0"][c] >= 0:
             continue
         blk = dump["V"][at:at + sz(c) * rank[c]].reshape(sz(c), rank[c])
         at += sz(c) * rank[c]
+        if blk.size == 0:
+            assert h2o.bases.V[c].size == 0
+            continue
         assert np.abs(blk - h2o.bases.V[c]).max() <= tol_basis * scale, f"V of leaf {c}"
     assert at == len(dump["V"])
     # transfer matrices
     at = 0
-    scale = max([np.abs(m).max() for m in h2o.bases.E.values()] + [1.0])
+    scale = max([np.abs(m).max() for m in h2o.bases.E.values() if m.size] + [1.0])
     for c in range(1, nc):
         if par[c] <= 0:
             continue
         blk = dump["E"][at:at + rank[c] * rank[par[c]]].reshape(rank[c], rank[par[c]])
         at += rank[c] * rank[par[c]]
+        if blk.size == 0:  # a transfer into a cluster the H^2 matrix does not use
+            assert h2o.bases.E[c].size == 0
+            continue
         assert np.abs(blk - h2o.bases.E[c]).max() <= tol_basis * scale, f"E of cluster {c}"
     assert at == len(dump["E"])
     # coupling blocks
