@@ -16,6 +16,7 @@ namespace {
 thread_local std::string g_last_error;
 }
 void set_error(const std::string& msg) { g_last_error = msg; }
+std::string last_error() { return g_last_error; }
 }  // namespace gca
 
 extern "C" {

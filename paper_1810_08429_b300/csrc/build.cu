@@ -463,50 +463,64 @@ __global__ void k_to_panel(const PanelJob* __restrict__ jobs, const double* __re
   }
 }
 
-// Panels of V, V^T, E, E^T, S, S^T, N, N^T (index PanelKind) with their
-// element offsets per block (the same for all precisions).
-int make_panels(gca_h2* h, cudaStream_t st) {
+// Every stored block in panel form: f(kind, index, rows, columns, transposed)
+// for V, V^T, E, E^T, S, S^T, N, N^T (index PanelKind), in storage order.
+template <typename F>
+void for_each_panel(const gca_h2* h, F&& f) {
   const int nc = h->nc;
   const int nfar = (int)h->far_t.size(), nnear = (int)h->near_t.size();
-  std::vector<PanelJob> jobs[kPanelKinds];
-  int64_t size[kPanelKinds] = {0};
-  for (int q = 0; q < kPanelKinds; ++q) h->panel_off[q].clear();
-  h->panel_off[kV].assign(nc, -1);
-  h->panel_off[kVt].assign(nc, -1);
-  h->panel_off[kE].assign(nc, -1);
-  h->panel_off[kEt].assign(nc, -1);
-  h->panel_off[kS].assign(nfar, -1);
-  h->panel_off[kSt].assign(nfar, -1);
-  h->panel_off[kN].assign(nnear, -1);
-  h->panel_off[kNt].assign(nnear, -1);
-  auto add = [&](int kind, int idx, int64_t src, int m, int k, int trans) {
-    h->panel_off[kind][idx] = size[kind];
-    jobs[kind].push_back({src, size[kind], m, k, trans, 0});
-    size[kind] += (int64_t)m * pad8(k);
-  };
   for (int c = 1; c < nc; ++c) {
     if (h->child0[c] < 0) {
       const int nr = h->end[c] - h->begin[c], r = h->rank[c];
-      add(kV, c, h->voff[c], nr, r, 0);
-      add(kVt, c, h->voff[c], r, nr, 1);
+      f(kV, c, nr, r, 0);
+      f(kVt, c, r, nr, 1);
     }
     if (h->parent[c] > 0) {
       const int r = h->rank[c], rp = h->rank[h->parent[c]];
-      add(kE, c, h->eoff[c], r, rp, 0);
-      add(kEt, c, h->eoff[c], rp, r, 1);
+      f(kE, c, r, rp, 0);
+      f(kEt, c, rp, r, 1);
     }
   }
   for (int b = 0; b < nfar; ++b) {
     const int rt = h->rank[h->far_t[b]], rs = h->rank[h->far_s[b]];
-    add(kS, b, h->soff[b], rt, rs, 0);
-    add(kSt, b, h->soff[b], rs, rt, 1);
+    f(kS, b, rt, rs, 0);
+    f(kSt, b, rs, rt, 1);
   }
   for (int b = 0; b < nnear; ++b) {
     const int t = h->near_t[b], s = h->near_s[b];
     const int mt = h->end[t] - h->begin[t], ms = h->end[s] - h->begin[s];
-    add(kN, b, h->noff[b], mt, ms, 0);
-    add(kNt, b, h->noff[b], ms, mt, 1);
+    f(kN, b, mt, ms, 0);
+    f(kNt, b, ms, mt, 1);
   }
+}
+
+// Element offsets of every block in its panel array (the same for all
+// precisions) and the array sizes; needs only the ranks and block lists.
+void layout_panels(gca_h2* h) {
+  const int nc = h->nc;
+  const int nfar = (int)h->far_t.size(), nnear = (int)h->near_t.size();
+  const int count[kPanelKinds] = {nc, nc, nc, nc, nfar, nfar, nnear, nnear};
+  for (int q = 0; q < kPanelKinds; ++q) {
+    h->panel_off[q].assign(count[q], -1);
+    h->psize[q] = 0;
+  }
+  for_each_panel(h, [&](int kind, int idx, int m, int k, int) {
+    h->panel_off[kind][idx] = h->psize[kind];
+    h->psize[kind] += (int64_t)m * pad8(k);
+  });
+}
+
+// Panels of all stored blocks from the row-major float64 coefficients, at the
+// offsets of layout_panels.
+int make_panels(gca_h2* h, cudaStream_t st) {
+  std::vector<PanelJob> jobs[kPanelKinds];
+  for_each_panel(h, [&](int kind, int idx, int m, int k, int trans) {
+    const int64_t src = (kind == kV || kind == kVt)   ? h->voff[idx]
+                        : (kind == kE || kind == kEt) ? h->eoff[idx]
+                        : (kind == kS || kind == kSt) ? h->soff[idx]
+                                                      : h->noff[idx];
+    jobs[kind].push_back({src, h->panel_off[kind][idx], m, k, trans, 0});
+  });
   const DevMem* srcs[kPanelKinds] = {&h->V64, &h->V64, &h->E64, &h->E64,
                                      &h->S64, &h->S64, &h->N64, &h->N64};
   DevMem d_jobs;
@@ -517,10 +531,9 @@ int make_panels(gca_h2* h, cudaStream_t st) {
     // the float32 near field also serves the bfloat16 products
     const bool k32 = !(fl & GCA_DROP_F32) || (near && !(fl & GCA_DROP_BF16));
     const bool k16 = !near && !(fl & GCA_DROP_BF16);
-    if (k64) GCA_TRY(h->P64[q].alloc(sizeof(double) * size[q]));
-    if (k32) GCA_TRY(h->P32[q].alloc(sizeof(float) * size[q]));
-    if (k16) GCA_TRY(h->P16[q].alloc(sizeof(__nv_bfloat16) * size[q]));
-    h->psize[q] = size[q];
+    if (k64) GCA_TRY(h->P64[q].alloc(sizeof(double) * h->psize[q]));
+    if (k32) GCA_TRY(h->P32[q].alloc(sizeof(float) * h->psize[q]));
+    if (k16) GCA_TRY(h->P16[q].alloc(sizeof(__nv_bfloat16) * h->psize[q]));
     if (jobs[q].empty() || !(k64 || k32 || k16)) continue;
     GCA_TRY(d_jobs.reserve(sizeof(PanelJob) * jobs[q].size()));
     GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, jobs[q].data(), sizeof(PanelJob) * jobs[q].size(),
@@ -1061,6 +1074,12 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   }
   d_vh.release();
 
+  // The product plan needs only the ranks, the block lists and the panel
+  // offsets: it is computed on host threads while the device computes the
+  // coupling and near-field entries.
+  layout_panels(h.get());
+  PlanHandle plan = plan_start(h.get());
+
   // pivots (host copy) and the pivot pool for the entry kernels
   h->piv.resize(std::max<int64_t>(piv_used, 1));
   GCA_TRY_CUDA(cudaMemcpyAsync(h->piv.data(), d_piv.p, sizeof(int) * piv_used, cudaMemcpyDeviceToHost, st));
@@ -1177,7 +1196,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     GCA_TRY(make_panels(h.get(), st));
   }
 
-  GCA_TRY(finish_plan(h.get(), st));
+  GCA_TRY(finish_plan(h.get(), plan.get(), st));
   GCA_TRY_CUDA(cudaStreamSynchronize(st));
   if (prm->flags & GCA_DROP_EXPORT) {
     h->V64.release();

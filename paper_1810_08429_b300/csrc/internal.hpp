@@ -22,6 +22,7 @@ enum PanelKind { kV = 0, kVt, kE, kEt, kS, kSt, kN, kNt, kPanelKinds };
 
 // Last error text of the calling thread (returned by gca_last_error()).
 void set_error(const std::string& msg);
+std::string last_error();
 
 #define GCA_TRY_CUDA(expr)                                                      \
   do {                                                                          \
@@ -112,7 +113,19 @@ class PhaseScope {
 // Entry points of the translation units.
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
           gca_h2** out);
-int finish_plan(gca_h2* h, cudaStream_t st);
+// Product plan (matvec.cu): plan_start runs the host planning of both
+// directions on worker threads (it needs the ranks, block lists and panel
+// offsets); finish_plan joins it and uploads the plan with the inverse
+// permutation.  Destroying the handle joins the threads.
+struct PlanJob;
+struct PlanJobDelete {
+  void operator()(PlanJob* j) const;
+};
+using PlanHandle = std::unique_ptr<PlanJob, PlanJobDelete>;
+PlanHandle plan_start(const gca_h2* h);
+int finish_plan(gca_h2* h, PlanJob* job, cudaStream_t st);
+// Panel layout (build.cu): element offsets of every block, then the panels.
+void layout_panels(gca_h2* h);
 int make_panels(gca_h2* h, cudaStream_t st);
 int product_status(const gca_h2* h, int* out);
 int prepare_batch(gca_h2_batch* b, cudaStream_t st);

@@ -47,6 +47,8 @@
 #include <map>
 #include <mutex>
 #include <queue>
+#include <system_error>
+#include <thread>
 #include <string>
 #include <type_traits>
 
@@ -1332,7 +1334,18 @@ int to_seg(const MvItem& it, MvSeg& s) {
 // Work items of one direction (0: product, 1: transposed product).
 // Segments = (block, 64-row slice, 64-column chunk); groups = runs of
 // segments with the same output rows claimed and accumulated together.
-int build_items(gca_h2* h, int dir, cudaStream_t st) {
+// Host part of the product plan of one direction (pure host code, so that it
+// can run on a worker thread while the device computes the coefficients).
+struct DirPlan {
+  std::vector<MvSeg> segs;  // group records in claim order: chain, then free
+  int64_t n_chain = 0, n_free = 0;
+  std::vector<float> chain_t;
+  float makespan = 0.f;
+  int status = GCA_OK;
+  std::string error;
+};
+
+int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
   const int nc = h->nc;
   const bool trans = dir == 1;
   std::vector<MvItem> items;
@@ -1467,31 +1480,77 @@ int build_items(gca_h2* h, int dir, cudaStream_t st) {
         set_error("internal: work group longer than a group record");
         return GCA_ERR_UNSUPPORTED;
       }
-  schedule_groups(items, groups, 2 * nc, h->chain_t[dir], h->makespan[dir]);
-  h->n_chain[dir] = (int64_t)groups.size();
-  h->n_free[dir] = (int64_t)free_groups.size();
+  schedule_groups(items, groups, 2 * nc, P.chain_t, P.makespan);
+  P.n_chain = (int64_t)groups.size();
+  P.n_free = (int64_t)free_groups.size();
   // group records in claim order: chain groups, then free groups
-  std::vector<MvSeg> segs((groups.size() + free_groups.size()) * kMaxGroupSegs);
-  std::memset(segs.data(), 0, segs.size() * sizeof(MvSeg));
+  P.segs.assign((groups.size() + free_groups.size()) * kMaxGroupSegs, MvSeg{});
   size_t gi = 0;
   for (const auto* gl : {&groups, &free_groups})
     for (const int2& g : *gl) {
-      for (int j = g.x; j < g.y; ++j) GCA_TRY(to_seg(items[j], segs[gi * kMaxGroupSegs + (j - g.x)]));
+      for (int j = g.x; j < g.y; ++j) GCA_TRY(to_seg(items[j], P.segs[gi * kMaxGroupSegs + (j - g.x)]));
       ++gi;
     }
-  GCA_TRY(upload(h->d_segs[dir], segs, st));
   return GCA_OK;
 }
 
-int finish_plan(gca_h2* h, cudaStream_t st) {
+// Both directions planned on two worker threads.  The threads read the tree,
+// ranks, block lists and panel offsets of the handle, which the caller must
+// not change until the job is joined.
+struct PlanJob {
+  DirPlan p[2];
+  std::thread t[2];
+  void join() {
+    for (auto& th : t)
+      if (th.joinable()) th.join();
+  }
+  ~PlanJob() { join(); }
+};
+
+void PlanJobDelete::operator()(PlanJob* j) const { delete j; }
+
+PlanHandle plan_start(const gca_h2* h) {
+  PlanHandle j(new PlanJob);
+  for (int dir = 0; dir < 2; ++dir) {
+    DirPlan* P = &j->p[dir];
+    auto run = [h, dir, P]() {
+      try {
+        P->status = plan_dir(h, dir, *P);
+        if (P->status != GCA_OK) P->error = last_error();
+      } catch (const std::bad_alloc&) {
+        P->status = GCA_ERR_OOM;
+        P->error = "product plan: host allocation failed";
+      }
+    };
+    try {
+      j->t[dir] = std::thread(run);
+    } catch (const std::system_error&) {
+      run();  // no thread available: plan on the calling thread
+    }
+  }
+  return j;
+}
+
+int finish_plan(gca_h2* h, PlanJob* job, cudaStream_t st) {
   h->max_rows = std::max(h->max_rank, h->max_leaf);
   {
     std::vector<int> iperm(h->n);
     for (int i = 0; i < h->n; ++i) iperm[h->perm[i]] = i;
     GCA_TRY(upload(h->d_iperm, iperm, st));
   }
-  GCA_TRY(build_items(h, 0, st));
-  GCA_TRY(build_items(h, 1, st));
+  job->join();
+  for (int dir = 0; dir < 2; ++dir) {
+    DirPlan& P = job->p[dir];
+    if (P.status != GCA_OK) {
+      set_error(P.error);
+      return P.status;
+    }
+    h->n_chain[dir] = P.n_chain;
+    h->n_free[dir] = P.n_free;
+    h->chain_t[dir].swap(P.chain_t);
+    h->makespan[dir] = P.makespan;
+    GCA_TRY(upload(h->d_segs[dir], P.segs, st));
+  }
   GCA_TRY(h->d_status.alloc(sizeof(int)));
   GCA_TRY_CUDA(cudaMemsetAsync(h->d_status.p, 0, sizeof(int), st));
   return GCA_OK;
