@@ -77,6 +77,37 @@ __global__ void k_tri_geom(int nt, const double* __restrict__ vert, const int* _
   }
 }
 
+// A quadrature node as float pairs (value = hi + lo) for the coupling
+// entries.  The coordinates are taken relative to an origin o and the high
+// parts lie on a grid of step g = 2^(E - 22), where every |x - o| < 2^E: the
+// high parts are integers times g below 2^22 g, so the difference of two of
+// them is exact in float; the low parts hold the rest (|lo| <= g / 2, stored
+// to 2^-24 of that).  The weight is split the same way (hi = nearest float).
+struct __align__(16) SplitNode {
+  float4 hi;  // x, y, z, w
+  float4 lo;
+};
+
+__global__ void k_split_nodes(int64_t count, const P4* __restrict__ tq, double ox, double oy, double oz,
+                              double g, SplitNode* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const P4 p = tq[i];
+  const double inv_g = 1.0 / g;  // g is a power of two: exact
+  auto split = [&](double u, float& hi, float& lo) {
+    const double h = rint(u * inv_g) * g;  // on the grid, exact in float
+    hi = (float)h;
+    lo = (float)(u - h);  // u - h is exact in double
+  };
+  SplitNode n;
+  split(p.x - ox, n.hi.x, n.lo.x);
+  split(p.y - oy, n.hi.y, n.lo.y);
+  split(p.z - oz, n.hi.z, n.lo.z);
+  n.hi.w = (float)p.w;
+  n.lo.w = (float)(p.w - (double)n.hi.w);
+  out[i] = n;
+}
+
 // one warp per cluster: min / max over the vertices of its triangles
 __global__ void k_cluster_boxes(int nc, const int* __restrict__ begin, const int* __restrict__ end,
                                 const int* __restrict__ perm, const int* __restrict__ tri,
@@ -510,9 +541,39 @@ void layout_panels(gca_h2* h) {
   });
 }
 
+// Which precisions of panel kind q a handle keeps (the float32 near field
+// also serves the bfloat16 products).
+void panel_precisions(const gca_h2* h, int q, bool& k64, bool& k32, bool& k16) {
+  const uint32_t fl = h->params.flags;
+  const bool near = q == kN || q == kNt;
+  k64 = !(fl & GCA_DROP_F64);
+  k32 = !(fl & GCA_DROP_F32) || (near && !(fl & GCA_DROP_BF16));
+  k16 = !near && !(fl & GCA_DROP_BF16);
+}
+
+// Device arrays of the panels at the sizes of layout_panels.
+int alloc_panels(gca_h2* h) {
+  for (int q = 0; q < kPanelKinds; ++q) {
+    bool k64, k32, k16;
+    panel_precisions(h, q, k64, k32, k16);
+    if (k64) GCA_TRY(h->P64[q].alloc(sizeof(double) * h->psize[q]));
+    if (k32) GCA_TRY(h->P32[q].alloc(sizeof(float) * h->psize[q]));
+    if (k16) GCA_TRY(h->P16[q].alloc(sizeof(__nv_bfloat16) * h->psize[q]));
+  }
+  return GCA_OK;
+}
+
+// Number of panel jobs of make_panels (the size of its job buffer).
+int64_t panel_jobs(const gca_h2* h) {
+  int64_t n = 0;
+  for_each_panel(h, [&](int, int, int, int, int) { ++n; });
+  return n;
+}
+
 // Panels of all stored blocks from the row-major float64 coefficients, at the
-// offsets of layout_panels.
-int make_panels(gca_h2* h, cudaStream_t st) {
+// offsets of layout_panels, into the arrays of alloc_panels; `jobs_buf` holds
+// at least panel_jobs(h) jobs.
+int make_panels(gca_h2* h, DevMem& jobs_buf, cudaStream_t st) {
   std::vector<PanelJob> jobs[kPanelKinds];
   for_each_panel(h, [&](int kind, int idx, int m, int k, int trans) {
     const int64_t src = (kind == kV || kind == kVt)   ? h->voff[idx]
@@ -523,27 +584,25 @@ int make_panels(gca_h2* h, cudaStream_t st) {
   });
   const DevMem* srcs[kPanelKinds] = {&h->V64, &h->V64, &h->E64, &h->E64,
                                      &h->S64, &h->S64, &h->N64, &h->N64};
-  DevMem d_jobs;
-  const uint32_t fl = h->params.flags;
+  size_t at = 0;
   for (int q = 0; q < kPanelKinds; ++q) {
-    const bool near = q == kN || q == kNt;
-    const bool k64 = !(fl & GCA_DROP_F64);
-    // the float32 near field also serves the bfloat16 products
-    const bool k32 = !(fl & GCA_DROP_F32) || (near && !(fl & GCA_DROP_BF16));
-    const bool k16 = !near && !(fl & GCA_DROP_BF16);
-    if (k64) GCA_TRY(h->P64[q].alloc(sizeof(double) * h->psize[q]));
-    if (k32) GCA_TRY(h->P32[q].alloc(sizeof(float) * h->psize[q]));
-    if (k16) GCA_TRY(h->P16[q].alloc(sizeof(__nv_bfloat16) * h->psize[q]));
+    bool k64, k32, k16;
+    panel_precisions(h, q, k64, k32, k16);
     if (jobs[q].empty() || !(k64 || k32 || k16)) continue;
-    GCA_TRY(d_jobs.reserve(sizeof(PanelJob) * jobs[q].size()));
-    GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, jobs[q].data(), sizeof(PanelJob) * jobs[q].size(),
-                                 cudaMemcpyHostToDevice, st));
+    if ((at + jobs[q].size()) * sizeof(PanelJob) > jobs_buf.bytes) {
+      set_error("internal: panel job buffer too small");
+      return GCA_ERR_UNSUPPORTED;
+    }
+    PanelJob* dj = jobs_buf.as<PanelJob>() + at;
+    GCA_TRY_CUDA(cudaMemcpyAsync(dj, jobs[q].data(), sizeof(PanelJob) * jobs[q].size(), cudaMemcpyHostToDevice,
+                                 st));
     k_to_panel<<<(unsigned)jobs[q].size(), 256, 0, st>>>(
-        d_jobs.as<PanelJob>(), srcs[q]->as<double>(), k64 ? h->P64[q].as<double>() : nullptr,
-        k32 ? h->P32[q].as<float>() : nullptr, k16 ? h->P16[q].as<__nv_bfloat16>() : nullptr);
+        dj, srcs[q]->as<double>(), k64 ? h->P64[q].as<double>() : nullptr, k32 ? h->P32[q].as<float>() : nullptr,
+        k16 ? h->P16[q].as<__nv_bfloat16>() : nullptr);
     GCA_TRY_CUDA(cudaGetLastError());
-    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_jobs is reused
+    at += jobs[q].size();
   }
+  GCA_TRY_CUDA(cudaStreamSynchronize(st));  // the host job lists go out of scope
   return GCA_OK;
 }
 
@@ -570,6 +629,75 @@ __device__ __forceinline__ double regular_entry(const P4* __restrict__ xq,
   return s * kInv4Pi;
 }
 
+// Float-pair arithmetic (a value is hi + lo with |lo| <= ulp(hi)), after
+// Dekker's and Knuth's error-free transformations: the rounded sum or product
+// and its exact rounding error.  The _rn intrinsics are never contracted
+// into fused operations, which would break the transformations.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// One coupling entry, the 7 x 7 rule of regular_entry, evaluated on the FP32
+// pipe in float-pair arithmetic.  A term's relative error is about
+// 2^(E - 44) / |d| (2^E bounds |x - o|, d = x - y): 1e-12 and below for the
+// admissible pairs of the coupling blocks, whose nodes lie at least a
+// fraction of a cluster diameter apart.  The near field keeps float64.
+// Per node pair: d = (x_hi - y_hi) + (x_lo - y_lo) with an exact high part;
+// r^2 = |d|^2 as a float pair; 1/r from rsqrtf refined by one Newton step
+// whose residual 1 - y0^2 r^2 is formed exactly to first order; the weighted
+// terms are summed as float pairs and rounded to double once per entry.
+__device__ __forceinline__ double regular_entry_split(const SplitNode* __restrict__ xq,
+                                                      const SplitNode* __restrict__ yq) {
+  float sh = 0.f, sl = 0.f;
+#pragma unroll 1
+  for (int p = 0; p < 7; ++p) {
+    const SplitNode x = xq[p];
+    float ih = 0.f, il = 0.f;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const SplitNode y = yq[q];
+      const float dh0 = __fsub_rn(x.hi.x, y.hi.x), dl0 = __fsub_rn(x.lo.x, y.lo.x);
+      const float dh1 = __fsub_rn(x.hi.y, y.hi.y), dl1 = __fsub_rn(x.lo.y, y.lo.y);
+      const float dh2 = __fsub_rn(x.hi.z, y.hi.z), dl2 = __fsub_rn(x.lo.z, y.lo.z);
+      // |d|^2 = sum dh^2 + 2 dh dl (+ dl^2, below 2^-40 relative)
+      const float p0 = __fmul_rn(dh0, dh0), p1 = __fmul_rn(dh1, dh1), p2 = __fmul_rn(dh2, dh2);
+      float low = __fmaf_rn(dh0, dh0, -p0);
+      low = __fadd_rn(low, __fmaf_rn(dh1, dh1, -p1));
+      low = __fadd_rn(low, __fmaf_rn(dh2, dh2, -p2));
+      low = __fmaf_rn(__fadd_rn(dh0, dh0), dl0, low);
+      low = __fmaf_rn(__fadd_rn(dh1, dh1), dl1, low);
+      low = __fmaf_rn(__fadd_rn(dh2, dh2), dl2, low);
+      float s01, e01, rh, e2;
+      two_sum(p0, p1, s01, e01);
+      two_sum(s01, p2, rh, e2);
+      const float rl = __fadd_rn(low, __fadd_rn(e01, e2));
+      // 1/r = y0 (1 + rho / 2), rho = 1 - y0^2 r^2 (|rho| ~ 2^-22)
+      const float y0 = rsqrtf(rh);
+      const float u = __fmul_rn(y0, y0), uu = __fmaf_rn(y0, y0, -u);
+      const float m = __fmul_rn(u, rh), me = __fmaf_rn(u, rh, -m);
+      const float rho = __fmaf_rn(-uu, rh, __fmaf_rn(-u, rl, __fsub_rn(__fsub_rn(1.f, m), me)));
+      const float dy = __fmul_rn(__fmul_rn(0.5f, y0), rho);
+      // term w_q / r as a float pair, added to the inner sum
+      const float th = __fmul_rn(y.hi.w, y0);
+      const float tl = __fadd_rn(__fmaf_rn(y.hi.w, y0, -th), __fmaf_rn(y.hi.w, dy, __fmul_rn(y.lo.w, y0)));
+      float ns, ne;
+      two_sum(ih, th, ns, ne);
+      ih = ns;
+      il = __fadd_rn(il, __fadd_rn(ne, tl));
+    }
+    // outer sum += w_p * inner
+    const float th = __fmul_rn(x.hi.w, ih);
+    const float tl = __fadd_rn(__fmaf_rn(x.hi.w, ih, -th), __fmaf_rn(x.hi.w, il, __fmul_rn(x.lo.w, ih)));
+    float ns, ne;
+    two_sum(sh, th, ns, ne);
+    sh = ns;
+    sl = __fadd_rn(sl, __fadd_rn(ne, tl));
+  }
+  return ((double)sh + (double)sl) * kInv4Pi;
+}
+
 // One CTA per pair of mirrored admissible blocks (tau, sigma) and
 // (sigma, tau): G is symmetric (Eq. 1 with g(x, y) = g(y, x) and the same
 // rule on both triangles), so S_{sigma tau} = S_{tau sigma}^T and every
@@ -579,23 +707,23 @@ __device__ __forceinline__ double regular_entry(const P4* __restrict__ xq,
 __global__ void k_couple_entries(const int2* __restrict__ pairs, const int* __restrict__ far_t,
                                  const int* __restrict__ far_s, const int64_t* __restrict__ soff,
                                  const int* __restrict__ rank, const int64_t* __restrict__ poff,
-                                 const int* __restrict__ piv, const P4* __restrict__ tq,
+                                 const int* __restrict__ piv, const SplitNode* __restrict__ tn,
                                  double* __restrict__ S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  P4* ys = reinterpret_cast<P4*>(smem_raw);
+  SplitNode* ys = reinterpret_cast<SplitNode*>(smem_raw);
   const int2 bm = pairs[blockIdx.x];
   const int b = bm.x;
   const int t = far_t[b], s = far_s[b];
   const int rt = rank[t], rs = rank[s];
   const int* pt = piv + poff[t];
   const int* ps = piv + poff[s];
-  for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) ys[i] = tq[7 * (int64_t)ps[i / 7] + i % 7];
+  for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) ys[i] = tn[7 * (int64_t)ps[i / 7] + i % 7];
   __syncthreads();
   double* out = S + soff[b];
   double* mir = bm.y >= 0 ? S + soff[bm.y] : nullptr;
   for (int idx = threadIdx.x; idx < rt * rs; idx += blockDim.x) {
     const int a = idx / rs, c = idx % rs;
-    const double v = regular_entry(tq + 7 * (int64_t)pt[a], ys + 7 * c);
+    const double v = regular_entry_split(tn + 7 * (int64_t)pt[a], ys + 7 * c);
     out[idx] = v;
     if (mir) mir[(int64_t)c * rt + a] = v;
   }
@@ -867,6 +995,23 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY_CUDA(cudaMemcpyAsync(box.data(), d_box.p, box.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   GCA_TRY_CUDA(cudaStreamSynchronize(st));
   box_diameters(box, diam);
+  // split nodes of the coupling entries: origin at the root box's centre,
+  // grid step 2^(E - 22) with 2^E above the box's largest half width
+  DevMem d_tn;
+  {
+    double half = 0.0, o[3];
+    for (int d = 0; d < 3; ++d) {
+      o[d] = 0.5 * (box[d] + box[3 + d]);
+      half = std::max(half, 0.5 * (box[3 + d] - box[d]));
+    }
+    int E = 0;
+    std::frexp(std::max(half, 1e-300), &E);  // half < 2^E
+    const double g = std::ldexp(1.0, E - 22);
+    GCA_TRY(d_tn.alloc(sizeof(SplitNode) * 7 * (size_t)n));
+    PhaseScope ps__("split_nodes", st);
+    k_split_nodes<<<blocks_for(7LL * n, 256), 256, 0, st>>>(7LL * n, d_tq.as<P4>(), o[0], o[1], o[2], g,
+                                                            d_tn.as<SplitNode>());
+  }
   block_tree(h->child0, h->child1, box, diam, prm->eta, h->far_t, h->far_s, h->near_t, h->near_s);
   GCA_TRY(upload(d_diam, diam, st));
 
@@ -1074,21 +1219,16 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   }
   d_vh.release();
 
-  // The product plan needs only the ranks, the block lists and the panel
-  // offsets: it is computed on host threads while the device computes the
-  // coupling and near-field entries.
-  layout_panels(h.get());
-  PlanHandle plan = plan_start(h.get());
-
-  // pivots (host copy) and the pivot pool for the entry kernels
+  // Offsets of the coupling and near-field coefficients, the panel layout and
+  // every device buffer of the rest of the build are set up first, so that
+  // the host has nothing to do but the product plan while the device
+  // computes the entries.
+  const int nfar = (int)h->far_t.size(), nnear = (int)h->near_t.size();
   h->piv.resize(std::max<int64_t>(piv_used, 1));
   GCA_TRY_CUDA(cudaMemcpyAsync(h->piv.data(), d_piv.p, sizeof(int) * piv_used, cudaMemcpyDeviceToHost, st));
   GCA_TRY(upload(h->d_rank, h->rank, st));
   DevMem d_poff;
   GCA_TRY(upload(d_poff, h->poff, st));
-
-  // coupling matrices
-  const int nfar = (int)h->far_t.size(), nnear = (int)h->near_t.size();
   h->soff.assign(nfar + 1, 0);
   for (int b = 0; b < nfar; ++b)
     h->soff[b + 1] = h->soff[b] + (int64_t)h->rank[h->far_t[b]] * h->rank[h->far_s[b]];
@@ -1097,44 +1237,30 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY(upload(h->d_far_s, h->far_s, st));
   GCA_TRY(upload(h->d_soff, h->soff, st));
   GCA_TRY(h->S64.alloc(sizeof(double) * h->s_entries));
-  if (nfar > 0) {
-    // mirrored pairs: the block list is sorted by (row, column) cluster, and
-    // the block tree is symmetric (the admissibility condition and the
-    // splitting rule do not depend on the order of tau and sigma); a block
-    // whose mirror is missing is computed alone
-    std::vector<int2> pairs;
-    pairs.reserve(nfar / 2 + 1);
-    for (int b = 0; b < nfar; ++b) {
-      const int t = h->far_t[b], s = h->far_s[b];
-      int m = -1;
-      {
-        int lo = 0, hi = nfar;
-        while (lo < hi) {
-          const int mid = (lo + hi) / 2;
-          if (h->far_t[mid] < s || (h->far_t[mid] == s && h->far_s[mid] < t)) lo = mid + 1; else hi = mid;
-        }
-        if (lo < nfar && h->far_t[lo] == s && h->far_s[lo] == t) m = lo;
-      }
-      if (m < 0)
-        pairs.push_back(make_int2(b, -1));
-      else if (t < s)
-        pairs.push_back(make_int2(b, m));
-    }
-    DevMem d_pairs;
-    GCA_TRY(upload(d_pairs, pairs, st));
-    const size_t smem = sizeof(P4) * 7 * (size_t)std::max(h->max_rank, 1);
-    GCA_TRY_CUDA(cudaFuncSetAttribute(k_couple_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // mirrored pairs of coupling blocks: the block list is sorted by (row,
+  // column) cluster, and the block tree is symmetric (the admissibility
+  // condition and the splitting rule do not depend on the order of tau and
+  // sigma); a block whose mirror is missing is computed alone
+  std::vector<int2> pairs;
+  pairs.reserve(nfar / 2 + 1);
+  for (int b = 0; b < nfar; ++b) {
+    const int t = h->far_t[b], s = h->far_s[b];
+    int m = -1;
     {
-      PhaseScope ps__("couple_entries", st);
-      k_couple_entries<<<(unsigned)pairs.size(), 256, smem, st>>>(
-          d_pairs.as<int2>(), h->d_far_t.as<int>(), h->d_far_s.as<int>(), h->d_soff.as<int64_t>(),
-          h->d_rank.as<int>(), d_poff.as<int64_t>(), d_piv.as<int>(), d_tq.as<P4>(), h->S64.as<double>());
+      int lo = 0, hi = nfar;
+      while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (h->far_t[mid] < s || (h->far_t[mid] == s && h->far_s[mid] < t)) lo = mid + 1; else hi = mid;
+      }
+      if (lo < nfar && h->far_t[lo] == s && h->far_s[lo] == t) m = lo;
     }
-    GCA_TRY_CUDA(cudaGetLastError());
-    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_pairs is freed at the end of this scope
+    if (m < 0)
+      pairs.push_back(make_int2(b, -1));
+    else if (t < s)
+      pairs.push_back(make_int2(b, m));
   }
-
-  // near field
+  DevMem d_pairs;
+  GCA_TRY(upload(d_pairs, pairs, st));
   h->noff.assign(nnear + 1, 0);
   for (int b = 0; b < nnear; ++b) {
     const int t = h->near_t[b], s = h->near_s[b];
@@ -1154,6 +1280,27 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY(d_items.alloc(sizeof(SingularItem) * 3 * (size_t)cap));
   GCA_TRY(d_counts.alloc(sizeof(unsigned long long) * 4));
   GCA_TRY_CUDA(cudaMemsetAsync(d_counts.p, 0, sizeof(unsigned long long) * 4, st));
+  layout_panels(h.get());
+  GCA_TRY(alloc_panels(h.get()));
+  DevMem d_pjobs;
+  GCA_TRY(d_pjobs.alloc(sizeof(PanelJob) * (size_t)panel_jobs(h.get())));
+  GCA_TRY_CUDA(cudaStreamSynchronize(st));  // the host copy of the pivots
+
+  // coupling matrices
+  if (nfar > 0) {
+    const size_t smem = sizeof(SplitNode) * 7 * (size_t)std::max(h->max_rank, 1);
+    GCA_TRY_CUDA(cudaFuncSetAttribute(k_couple_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      PhaseScope ps__("couple_entries", st);
+      k_couple_entries<<<(unsigned)pairs.size(), 256, smem, st>>>(
+          d_pairs.as<int2>(), h->d_far_t.as<int>(), h->d_far_s.as<int>(), h->d_soff.as<int64_t>(),
+          h->d_rank.as<int>(), d_poff.as<int64_t>(), d_piv.as<int>(), d_tn.as<SplitNode>(),
+          h->S64.as<double>());
+    }
+    GCA_TRY_CUDA(cudaGetLastError());
+  }
+
+  // near field
   if (nnear > 0) {
     const size_t smem = sizeof(P4) * 7 * (size_t)h->max_leaf;
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1166,6 +1313,11 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
           d_status.as<int>());
     }
     GCA_TRY_CUDA(cudaGetLastError());
+  }
+  // the product plan needs only the ranks, the block lists and the panel
+  // offsets: the host computes it while the coupling and near-field kernels run
+  PlanHandle plan = plan_start(h.get());
+  if (nnear > 0) {
     GCA_TRY(check_status(d_status, st, "near field"));
     unsigned long long counts[4];
     GCA_TRY_CUDA(cudaMemcpyAsync(counts, d_counts.p, sizeof(counts), cudaMemcpyDeviceToHost, st));
@@ -1193,7 +1345,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   {
     PhaseScope ps_conv("to_panel", st);
     ps_conv.launches(kPanelKinds);
-    GCA_TRY(make_panels(h.get(), st));
+    GCA_TRY(make_panels(h.get(), d_pjobs, st));
   }
 
   GCA_TRY(finish_plan(h.get(), plan.get(), st));

@@ -114,9 +114,9 @@ class PhaseScope {
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
           gca_h2** out);
 // Product plan (matvec.cu): plan_start runs the host planning of both
-// directions on worker threads (it needs the ranks, block lists and panel
-// offsets); finish_plan joins it and uploads the plan with the inverse
-// permutation.  Destroying the handle joins the threads.
+// directions (it needs the ranks, block lists and panel offsets; the build
+// calls it while the entry kernels run); finish_plan uploads the plan with
+// the inverse permutation.
 struct PlanJob;
 struct PlanJobDelete {
   void operator()(PlanJob* j) const;
@@ -124,9 +124,12 @@ struct PlanJobDelete {
 using PlanHandle = std::unique_ptr<PlanJob, PlanJobDelete>;
 PlanHandle plan_start(const gca_h2* h);
 int finish_plan(gca_h2* h, PlanJob* job, cudaStream_t st);
-// Panel layout (build.cu): element offsets of every block, then the panels.
+// Panel layout (build.cu): element offsets of every block, the device
+// arrays, the number of panel jobs, then the panels themselves.
 void layout_panels(gca_h2* h);
-int make_panels(gca_h2* h, cudaStream_t st);
+int alloc_panels(gca_h2* h);
+int64_t panel_jobs(const gca_h2* h);
+int make_panels(gca_h2* h, DevMem& jobs_buf, cudaStream_t st);
 int product_status(const gca_h2* h, int* out);
 int prepare_batch(gca_h2_batch* b, cudaStream_t st);
 int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx, void* y,

@@ -47,8 +47,6 @@
 #include <map>
 #include <mutex>
 #include <queue>
-#include <system_error>
-#include <thread>
 #include <string>
 #include <type_traits>
 
@@ -1334,8 +1332,8 @@ int to_seg(const MvItem& it, MvSeg& s) {
 // Work items of one direction (0: product, 1: transposed product).
 // Segments = (block, 64-row slice, 64-column chunk); groups = runs of
 // segments with the same output rows claimed and accumulated together.
-// Host part of the product plan of one direction (pure host code, so that it
-// can run on a worker thread while the device computes the coefficients).
+// Host part of the product plan of one direction (pure host code: it runs
+// while the device computes the coefficients).
 struct DirPlan {
   std::vector<MvSeg> segs;  // group records in claim order: chain, then free
   int64_t n_chain = 0, n_free = 0;
@@ -1494,17 +1492,11 @@ int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
   return GCA_OK;
 }
 
-// Both directions planned on two worker threads.  The threads read the tree,
-// ranks, block lists and panel offsets of the handle, which the caller must
-// not change until the job is joined.
+// Both directions, planned on the calling thread.  (On worker threads the
+// planning ran several times slower than here, so the build instead calls
+// this with the entry kernels queued on the device.)
 struct PlanJob {
   DirPlan p[2];
-  std::thread t[2];
-  void join() {
-    for (auto& th : t)
-      if (th.joinable()) th.join();
-  }
-  ~PlanJob() { join(); }
 };
 
 void PlanJobDelete::operator()(PlanJob* j) const { delete j; }
@@ -1512,21 +1504,9 @@ void PlanJobDelete::operator()(PlanJob* j) const { delete j; }
 PlanHandle plan_start(const gca_h2* h) {
   PlanHandle j(new PlanJob);
   for (int dir = 0; dir < 2; ++dir) {
-    DirPlan* P = &j->p[dir];
-    auto run = [h, dir, P]() {
-      try {
-        P->status = plan_dir(h, dir, *P);
-        if (P->status != GCA_OK) P->error = last_error();
-      } catch (const std::bad_alloc&) {
-        P->status = GCA_ERR_OOM;
-        P->error = "product plan: host allocation failed";
-      }
-    };
-    try {
-      j->t[dir] = std::thread(run);
-    } catch (const std::system_error&) {
-      run();  // no thread available: plan on the calling thread
-    }
+    DirPlan& P = j->p[dir];
+    P.status = plan_dir(h, dir, P);
+    if (P.status != GCA_OK) P.error = last_error();
   }
   return j;
 }
@@ -1538,7 +1518,6 @@ int finish_plan(gca_h2* h, PlanJob* job, cudaStream_t st) {
     for (int i = 0; i < h->n; ++i) iperm[h->perm[i]] = i;
     GCA_TRY(upload(h->d_iperm, iperm, st));
   }
-  job->join();
   for (int dir = 0; dir < 2; ++dir) {
     DirPlan& P = job->p[dir];
     if (P.status != GCA_OK) {

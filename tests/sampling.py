@@ -74,6 +74,31 @@ def check_near_entries(dump, tree, gal, rng, blocks=64, per_block=16, tol=1e-10)
     return len(ref)
 
 
+def check_coupling_entries(dump, gal, rng, blocks=64, per_block=16, tol=1e-10):
+    """Sampled S entries against the oracle's Galerkin entries of the pivot
+    triangles, S_{tau sigma}[a, b] = g(tilde-tau_a, tilde-sigma_b) (Sect. 4);
+    relative per entry (all entries are positive)."""
+    rank = dump["rank"]
+    poff = np.concatenate([[0], np.cumsum(rank)])
+    far = dump["far"]
+    soff = np.concatenate([[0], np.cumsum(rank[far[:, 0]] * rank[far[:, 1]])])
+    assert soff[-1] == len(dump["S"])
+    pick = rng.choice(len(far), size=min(blocks, len(far)), replace=False)
+    ii, jj, got = [], [], []
+    for b in pick:
+        t, s = far[b]
+        a = rng.integers(0, rank[t], per_block)
+        c = rng.integers(0, rank[s], per_block)
+        ii.append(dump["pivots"][poff[t] + a])
+        jj.append(dump["pivots"][poff[s] + c])
+        got.append(dump["S"][soff[b] + a * rank[s] + c])
+    ii, jj, got = np.concatenate(ii), np.concatenate(jj), np.concatenate(got)
+    ref = gal.entries(ii, jj)
+    err = np.abs(got - ref) / np.abs(ref)
+    assert err.max() <= tol, (err.max(), ii[err.argmax()], jj[err.argmax()])
+    return float(err.max())
+
+
 def check_leaf_bases(dump, tree, lo, hi, gal, params, rng, leaves=6, tol=1e-8):
     """Leaf pivots and V from the oracle's own Green matrix and ACA.
 

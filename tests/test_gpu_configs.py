@@ -4,8 +4,8 @@
   20480-triangle sphere and its perturbed copy built together
   (gca_build_batch; leaf 64, eta 2, m 4, tol 1e-8) and applied in one
   persistent launch with 16 right-hand sides N(0, 1).  Tree and block tree
-  equal the oracle's; sampled near-field entries and leaf bases match the
-  oracle's; sampled rows of the float64 product match the dense G within
+  equal the oracle's; sampled coupling and near-field entries and leaf
+  bases match the oracle's; sampled rows of the float64 product match the dense G within
   the compression error; the adjoint identity holds; float32 and bfloat16
   products stay within their bounds of the float64 product.
 * The 81920-triangle sphere with 64 right-hand sides: float32 and bfloat16
@@ -73,6 +73,7 @@ def test_bench_workload_samples_match_oracle(bench_batch):
         sampling.check_blocks(dump, far, near)
         gal = Galerkin(v, t, p.sauter_q)
         sampling.check_near_entries(dump, tree, gal, rng)
+        sampling.check_coupling_entries(dump, gal, rng)
         sampling.check_leaf_bases(dump, tree, lo, hi, gal, p, rng)
 
 
