@@ -639,18 +639,21 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// One coupling entry, the 7 x 7 rule of regular_entry, evaluated on the FP32
-// pipe in float-pair arithmetic.  A term's relative error is about
-// 2^(E - 44) / |d| (2^E bounds |x - o|, d = x - y): 1e-12 and below for the
-// admissible pairs of the coupling blocks, whose nodes lie at least a
-// fraction of a cluster diameter apart.  The near field keeps float64.
-// Per node pair: d = (x_hi - y_hi) + (x_lo - y_lo) with an exact high part;
+// One entry by the 7 x 7 rule of regular_entry, evaluated on the FP32 pipe
+// in float-pair arithmetic.  A term's relative error is about
+// 2^(E - 45) / |d| (2^E bounds |x - o|, d = x - y; the rounding of the low
+// parts of the nodes): 1e-13 and below for the admissible pairs of the
+// coupling blocks, whose nodes lie at least a fraction of a cluster
+// diameter apart.  min_r2 returns the smallest |d|^2
+// (high part) met, so that callers with close pairs can fall back to
+// float64.  Per node pair: d = (x_hi - y_hi) + (x_lo - y_lo) with an exact high part;
 // r^2 = |d|^2 as a float pair; 1/r from rsqrtf refined by one Newton step
 // whose residual 1 - y0^2 r^2 is formed exactly to first order; the weighted
 // terms are summed as float pairs and rounded to double once per entry.
 __device__ __forceinline__ double regular_entry_split(const SplitNode* __restrict__ xq,
-                                                      const SplitNode* __restrict__ yq) {
+                                                      const SplitNode* __restrict__ yq, float& min_r2) {
   float sh = 0.f, sl = 0.f;
+  float mr = 3.0e38f;
 #pragma unroll 1
   for (int p = 0; p < 7; ++p) {
     const SplitNode x = xq[p];
@@ -661,20 +664,23 @@ __device__ __forceinline__ double regular_entry_split(const SplitNode* __restric
       const float dh0 = __fsub_rn(x.hi.x, y.hi.x), dl0 = __fsub_rn(x.lo.x, y.lo.x);
       const float dh1 = __fsub_rn(x.hi.y, y.hi.y), dl1 = __fsub_rn(x.lo.y, y.lo.y);
       const float dh2 = __fsub_rn(x.hi.z, y.hi.z), dl2 = __fsub_rn(x.lo.z, y.lo.z);
-      // |d|^2 = sum dh^2 + 2 dh dl (+ dl^2, below 2^-40 relative)
+      // |d|^2 = sum dh^2 + (2 dh + dl) dl; the dl^2 part matters: it is
+      // (g / |d|)^2 relative, 1e-10 at a few hundred grid steps
       const float p0 = __fmul_rn(dh0, dh0), p1 = __fmul_rn(dh1, dh1), p2 = __fmul_rn(dh2, dh2);
       float low = __fmaf_rn(dh0, dh0, -p0);
       low = __fadd_rn(low, __fmaf_rn(dh1, dh1, -p1));
       low = __fadd_rn(low, __fmaf_rn(dh2, dh2, -p2));
-      low = __fmaf_rn(__fadd_rn(dh0, dh0), dl0, low);
-      low = __fmaf_rn(__fadd_rn(dh1, dh1), dl1, low);
-      low = __fmaf_rn(__fadd_rn(dh2, dh2), dl2, low);
+      low = __fmaf_rn(__fadd_rn(__fadd_rn(dh0, dh0), dl0), dl0, low);
+      low = __fmaf_rn(__fadd_rn(__fadd_rn(dh1, dh1), dl1), dl1, low);
+      low = __fmaf_rn(__fadd_rn(__fadd_rn(dh2, dh2), dl2), dl2, low);
       float s01, e01, rh, e2;
       two_sum(p0, p1, s01, e01);
       two_sum(s01, p2, rh, e2);
       const float rl = __fadd_rn(low, __fadd_rn(e01, e2));
-      // 1/r = y0 (1 + rho / 2), rho = 1 - y0^2 r^2 (|rho| ~ 2^-22)
-      const float y0 = rsqrtf(rh);
+      mr = fminf(mr, rh);
+      // 1/r = y0 (1 + rho / 2), rho = 1 - y0^2 r^2 (|rho| ~ 2^-22: y0 must
+      // start from rh + rl, since the cross terms put r^2 - rh at 2 g / |d|)
+      const float y0 = rsqrtf(__fadd_rn(rh, rl));
       const float u = __fmul_rn(y0, y0), uu = __fmaf_rn(y0, y0, -u);
       const float m = __fmul_rn(u, rh), me = __fmaf_rn(u, rh, -m);
       const float rho = __fmaf_rn(-uu, rh, __fmaf_rn(-u, rl, __fsub_rn(__fsub_rn(1.f, m), me)));
@@ -695,6 +701,7 @@ __device__ __forceinline__ double regular_entry_split(const SplitNode* __restric
     sh = ns;
     sl = __fadd_rn(sl, __fadd_rn(ne, tl));
   }
+  min_r2 = mr;
   return ((double)sh + (double)sl) * kInv4Pi;
 }
 
@@ -723,7 +730,8 @@ __global__ void k_couple_entries(const int2* __restrict__ pairs, const int* __re
   double* mir = bm.y >= 0 ? S + soff[bm.y] : nullptr;
   for (int idx = threadIdx.x; idx < rt * rs; idx += blockDim.x) {
     const int a = idx / rs, c = idx % rs;
-    const double v = regular_entry_split(tn + 7 * (int64_t)pt[a], ys + 7 * c);
+    float mr;
+    const double v = regular_entry_split(tn + 7 * (int64_t)pt[a], ys + 7 * c, mr);
     out[idx] = v;
     if (mir) mir[(int64_t)c * rt + a] = v;
   }
@@ -737,21 +745,28 @@ struct SingularItem {
 
 // One CTA per near block: disjoint pairs by the 7 x 7 rule, touching pairs
 // appended to the list of their case (1 common vertex, 2 common edge,
-// 3 identical).
+// 3 identical).  A disjoint pair is evaluated in float-pair arithmetic and
+// again in float64 when two of its nodes are closer than sqrt(near_r2) =
+// 2^(E - 8) (so that the float-pair error stays below about 2^-37).
 __global__ void k_near_entries(const int* __restrict__ near_t, const int* __restrict__ near_s,
                                const int64_t* __restrict__ noff, const int* __restrict__ begin,
                                const int* __restrict__ end, const int* __restrict__ perm,
                                const int* __restrict__ tri, const P4* __restrict__ tq,
+                               const SplitNode* __restrict__ tn, float near_r2,
                                double* __restrict__ N, SingularItem* __restrict__ lists,
                                int64_t cap, unsigned long long* __restrict__ counts,
                                int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  P4* ys = reinterpret_cast<P4*>(smem_raw);
   const int b = blockIdx.x;
   const int t = near_t[b], s = near_s[b];
   const int bt = begin[t], nt = end[t] - bt, bs = begin[s], ns = end[s] - bs;
-  for (int i = threadIdx.x; i < ns * 7; i += blockDim.x)
-    ys[i] = tq[7 * (int64_t)perm[bs + i / 7] + i % 7];
+  P4* ys = reinterpret_cast<P4*>(smem_raw);
+  SplitNode* yn = reinterpret_cast<SplitNode*>(smem_raw + sizeof(P4) * 7 * (size_t)ns);
+  for (int i = threadIdx.x; i < ns * 7; i += blockDim.x) {
+    const int64_t src = 7 * (int64_t)perm[bs + i / 7] + i % 7;
+    ys[i] = tq[src];
+    yn[i] = tn[src];
+  }
   __syncthreads();
   const int64_t base = noff[b];
   for (int idx = threadIdx.x; idx < nt * ns; idx += blockDim.x) {
@@ -764,7 +779,10 @@ __global__ void k_near_entries(const int* __restrict__ near_t, const int* __rest
       shared += (va == tri[3 * tj]) + (va == tri[3 * tj + 1]) + (va == tri[3 * tj + 2]);
     }
     if (shared == 0) {
-      N[base + idx] = regular_entry(tq + 7 * (int64_t)ti, ys + 7 * j);
+      float mr;
+      double v = regular_entry_split(tn + 7 * (int64_t)ti, yn + 7 * j, mr);
+      if (mr < near_r2) v = regular_entry(tq + 7 * (int64_t)ti, ys + 7 * j);
+      N[base + idx] = v;
     } else {
       const unsigned long long slot = atomicAdd(&counts[shared], 1ull);
       if (slot < (unsigned long long)cap) {
@@ -998,6 +1016,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // split nodes of the coupling entries: origin at the root box's centre,
   // grid step 2^(E - 22) with 2^E above the box's largest half width
   DevMem d_tn;
+  float near_r2 = 0.f;  // float-pair entries of the near field need |d| >= 2^(E - 8)
   {
     double half = 0.0, o[3];
     for (int d = 0; d < 3; ++d) {
@@ -1007,6 +1026,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     int E = 0;
     std::frexp(std::max(half, 1e-300), &E);  // half < 2^E
     const double g = std::ldexp(1.0, E - 22);
+    near_r2 = (float)std::ldexp(1.0, 2 * (E - 8));
     GCA_TRY(d_tn.alloc(sizeof(SplitNode) * 7 * (size_t)n));
     PhaseScope ps__("split_nodes", st);
     k_split_nodes<<<blocks_for(7LL * n, 256), 256, 0, st>>>(7LL * n, d_tq.as<P4>(), o[0], o[1], o[2], g,
@@ -1302,14 +1322,15 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
 
   // near field
   if (nnear > 0) {
-    const size_t smem = sizeof(P4) * 7 * (size_t)h->max_leaf;
+    const size_t smem = (sizeof(P4) + sizeof(SplitNode)) * 7 * (size_t)h->max_leaf;
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
       PhaseScope ps__("near_entries", st);
       k_near_entries<<<nnear, 256, smem, st>>>(
           h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
           h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), d_tq.as<P4>(),
-          h->N64.as<double>(), d_items.as<SingularItem>(), cap, d_counts.as<unsigned long long>(),
+          d_tn.as<SplitNode>(), near_r2, h->N64.as<double>(), d_items.as<SingularItem>(), cap,
+          d_counts.as<unsigned long long>(),
           d_status.as<int>());
     }
     GCA_TRY_CUDA(cudaGetLastError());

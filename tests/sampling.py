@@ -71,7 +71,7 @@ def check_near_entries(dump, tree, gal, rng, blocks=64, per_block=16, tol=1e-10)
     ref = gal.entries(ii, jj)
     err = np.abs(got - ref) / np.abs(ref)
     assert err.max() <= tol, (err.max(), ii[err.argmax()], jj[err.argmax()])
-    return len(ref)
+    return float(err.max())
 
 
 def check_coupling_entries(dump, gal, rng, blocks=64, per_block=16, tol=1e-10):
