@@ -571,38 +571,43 @@ int64_t panel_jobs(const gca_h2* h) {
 }
 
 // Panels of all stored blocks from the row-major float64 coefficients, at the
-// offsets of layout_panels, into the arrays of alloc_panels; `jobs_buf` holds
-// at least panel_jobs(h) jobs.
-int make_panels(gca_h2* h, DevMem& jobs_buf, cudaStream_t st) {
-  std::vector<PanelJob> jobs[kPanelKinds];
-  for_each_panel(h, [&](int kind, int idx, int m, int k, int trans) {
-    const int64_t src = (kind == kV || kind == kVt)   ? h->voff[idx]
-                        : (kind == kE || kind == kEt) ? h->eoff[idx]
-                        : (kind == kS || kind == kSt) ? h->soff[idx]
-                                                      : h->noff[idx];
-    jobs[kind].push_back({src, h->panel_off[kind][idx], m, k, trans, 0});
-  });
+// offsets of layout_panels, into the arrays of alloc_panels.  `jobs_buf`
+// holds at least panel_jobs(h) jobs; `host_jobs` receives their host copy
+// and must outlive the next synchronisation of the stream (the launches are
+// asynchronous).
+int make_panels(gca_h2* h, DevMem& jobs_buf, std::vector<PanelJob>& host_jobs, cudaStream_t st) {
+  int64_t first[kPanelKinds + 1] = {0};
+  host_jobs.clear();
+  for (int q = 0; q < kPanelKinds; ++q) {
+    for_each_panel(h, [&](int kind, int idx, int m, int k, int trans) {
+      if (kind != q) return;
+      const int64_t src = (kind == kV || kind == kVt)   ? h->voff[idx]
+                          : (kind == kE || kind == kEt) ? h->eoff[idx]
+                          : (kind == kS || kind == kSt) ? h->soff[idx]
+                                                        : h->noff[idx];
+      host_jobs.push_back({src, h->panel_off[kind][idx], m, k, trans, 0});
+    });
+    first[q + 1] = (int64_t)host_jobs.size();
+  }
+  if (host_jobs.size() * sizeof(PanelJob) > jobs_buf.bytes) {
+    set_error("internal: panel job buffer too small");
+    return GCA_ERR_UNSUPPORTED;
+  }
+  if (host_jobs.empty()) return GCA_OK;
+  GCA_TRY_CUDA(cudaMemcpyAsync(jobs_buf.p, host_jobs.data(), sizeof(PanelJob) * host_jobs.size(),
+                               cudaMemcpyHostToDevice, st));
   const DevMem* srcs[kPanelKinds] = {&h->V64, &h->V64, &h->E64, &h->E64,
                                      &h->S64, &h->S64, &h->N64, &h->N64};
-  size_t at = 0;
   for (int q = 0; q < kPanelKinds; ++q) {
     bool k64, k32, k16;
     panel_precisions(h, q, k64, k32, k16);
-    if (jobs[q].empty() || !(k64 || k32 || k16)) continue;
-    if ((at + jobs[q].size()) * sizeof(PanelJob) > jobs_buf.bytes) {
-      set_error("internal: panel job buffer too small");
-      return GCA_ERR_UNSUPPORTED;
-    }
-    PanelJob* dj = jobs_buf.as<PanelJob>() + at;
-    GCA_TRY_CUDA(cudaMemcpyAsync(dj, jobs[q].data(), sizeof(PanelJob) * jobs[q].size(), cudaMemcpyHostToDevice,
-                                 st));
-    k_to_panel<<<(unsigned)jobs[q].size(), 256, 0, st>>>(
-        dj, srcs[q]->as<double>(), k64 ? h->P64[q].as<double>() : nullptr, k32 ? h->P32[q].as<float>() : nullptr,
-        k16 ? h->P16[q].as<__nv_bfloat16>() : nullptr);
+    const int64_t cnt = first[q + 1] - first[q];
+    if (cnt == 0 || !(k64 || k32 || k16)) continue;
+    k_to_panel<<<(unsigned)cnt, 256, 0, st>>>(
+        jobs_buf.as<PanelJob>() + first[q], srcs[q]->as<double>(), k64 ? h->P64[q].as<double>() : nullptr,
+        k32 ? h->P32[q].as<float>() : nullptr, k16 ? h->P16[q].as<__nv_bfloat16>() : nullptr);
     GCA_TRY_CUDA(cudaGetLastError());
-    at += jobs[q].size();
   }
-  GCA_TRY_CUDA(cudaStreamSynchronize(st));  // the host job lists go out of scope
   return GCA_OK;
 }
 
@@ -1336,8 +1341,10 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     GCA_TRY_CUDA(cudaGetLastError());
   }
   // the product plan needs only the ranks, the block lists and the panel
-  // offsets: the host computes it while the coupling and near-field kernels run
-  PlanHandle plan = plan_start(h.get());
+  // offsets: the host computes one direction while the coupling and
+  // near-field kernels run, the other while the singular and panel kernels run
+  PlanHandle plan = plan_new();
+  plan_direction(h.get(), 0, plan.get());
   if (nnear > 0) {
     GCA_TRY(check_status(d_status, st, "near field"));
     unsigned long long counts[4];
@@ -1363,11 +1370,13 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   }
 
   // panel layout for the products, three precisions
+  std::vector<PanelJob> panel_host_jobs;  // kept until the synchronisation below
   {
     PhaseScope ps_conv("to_panel", st);
     ps_conv.launches(kPanelKinds);
-    GCA_TRY(make_panels(h.get(), d_pjobs, st));
+    GCA_TRY(make_panels(h.get(), d_pjobs, panel_host_jobs, st));
   }
+  plan_direction(h.get(), 1, plan.get());
 
   GCA_TRY(finish_plan(h.get(), plan.get(), st));
   GCA_TRY_CUDA(cudaStreamSynchronize(st));

@@ -113,23 +113,25 @@ class PhaseScope {
 // Entry points of the translation units.
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
           gca_h2** out);
-// Product plan (matvec.cu): plan_start runs the host planning of both
-// directions (it needs the ranks, block lists and panel offsets; the build
-// calls it while the entry kernels run); finish_plan uploads the plan with
-// the inverse permutation.
+// Product plan (matvec.cu): plan_direction runs the host planning of one
+// direction (it needs the ranks, block lists and panel offsets; the build
+// calls it while its kernels run); finish_plan plans what is left and
+// uploads the plan with the inverse permutation.
 struct PlanJob;
 struct PlanJobDelete {
   void operator()(PlanJob* j) const;
 };
 using PlanHandle = std::unique_ptr<PlanJob, PlanJobDelete>;
-PlanHandle plan_start(const gca_h2* h);
+PlanHandle plan_new();
+void plan_direction(const gca_h2* h, int dir, PlanJob* job);
 int finish_plan(gca_h2* h, PlanJob* job, cudaStream_t st);
 // Panel layout (build.cu): element offsets of every block, the device
 // arrays, the number of panel jobs, then the panels themselves.
 void layout_panels(gca_h2* h);
 int alloc_panels(gca_h2* h);
 int64_t panel_jobs(const gca_h2* h);
-int make_panels(gca_h2* h, DevMem& jobs_buf, cudaStream_t st);
+struct PanelJob;
+int make_panels(gca_h2* h, DevMem& jobs_buf, std::vector<PanelJob>& host_jobs, cudaStream_t st);
 int product_status(const gca_h2* h, int* out);
 int prepare_batch(gca_h2_batch* b, cudaStream_t st);
 int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx, void* y,

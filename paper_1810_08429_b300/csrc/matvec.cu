@@ -1492,23 +1492,23 @@ int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
   return GCA_OK;
 }
 
-// Both directions, planned on the calling thread.  (On worker threads the
-// planning ran several times slower than here, so the build instead calls
-// this with the entry kernels queued on the device.)
+// The plans of both directions, each computed on the calling thread.  (On
+// worker threads the planning ran several times slower than here, so the
+// build instead plans while its kernels are queued on the device.)
 struct PlanJob {
   DirPlan p[2];
+  bool done[2] = {false, false};
 };
 
 void PlanJobDelete::operator()(PlanJob* j) const { delete j; }
 
-PlanHandle plan_start(const gca_h2* h) {
-  PlanHandle j(new PlanJob);
-  for (int dir = 0; dir < 2; ++dir) {
-    DirPlan& P = j->p[dir];
-    P.status = plan_dir(h, dir, P);
-    if (P.status != GCA_OK) P.error = last_error();
-  }
-  return j;
+PlanHandle plan_new() { return PlanHandle(new PlanJob); }
+
+void plan_direction(const gca_h2* h, int dir, PlanJob* job) {
+  DirPlan& P = job->p[dir];
+  P.status = plan_dir(h, dir, P);
+  if (P.status != GCA_OK) P.error = last_error();
+  job->done[dir] = true;
 }
 
 int finish_plan(gca_h2* h, PlanJob* job, cudaStream_t st) {
@@ -1519,6 +1519,7 @@ int finish_plan(gca_h2* h, PlanJob* job, cudaStream_t st) {
     GCA_TRY(upload(h->d_iperm, iperm, st));
   }
   for (int dir = 0; dir < 2; ++dir) {
+    if (!job->done[dir]) plan_direction(h, dir, job);
     DirPlan& P = job->p[dir];
     if (P.status != GCA_OK) {
       set_error(P.error);
