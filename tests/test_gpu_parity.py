@@ -218,6 +218,50 @@ def test_other_surfaces(lib, name, leaf, m, tol):
     assert rel_cols(y, oh2.matvec(ref, x)) <= TOL64
 
 
+def test_close_disjoint_pair_uses_float64(lib):
+    """Two disjoint triangles 5e-5 apart inside the icosahedron: their nodes are
+    far closer than the float-pair floor 2^(E-8) of the near field (E = 1
+    here), so their entries must have float64 accuracy (the float-pair rule
+    would be about 1e-9 off); the other disjoint entries stay within the
+    float-pair bound."""
+    v0, t0 = synth.icosahedron()
+    tiny = np.array([[0.0, 0.0, 0.0], [1e-3, 0.0, 0.0], [0.0, 1e-3, 0.0]])
+    v = np.vstack([v0, tiny, tiny + [0.0, 0.0, 5e-5]])
+    nv = len(v0)
+    t = np.vstack([t0, [[nv, nv + 1, nv + 2], [nv + 3, nv + 4, nv + 5]]]).astype(np.int32)
+    p = OParams(leaf_size=32, eta=2.0, box_gauss_m=3, aca_tol=1e-6, sauter_q=5)
+    ref = ogca.build_h2(v, t, p)
+    tree = lib.tree_build(v, t, 32)
+    h = lib.build(v, t, tree, _params(lib, p))
+    dump = h.export()
+    compare_structure(ref, dump, tree)
+    N = dump["N"].reshape(22, 22)
+    perm = np.asarray(tree["perm"])
+    R = ref.N[(0, 0)]
+    err = np.abs(N - R) / np.abs(R)
+    assert err.max() <= 1e-11
+    a, b = (int(np.nonzero(perm == k)[0][0]) for k in (20, 21))
+    assert err[a, b] <= 1e-13 and err[b, a] <= 1e-13
+
+
+def test_translated_scaled_mesh(lib):
+    """The 1280-triangle sphere scaled by 1000 and moved far from the origin:
+    the float-pair grid follows the mesh's box (origin at its centre, step
+    2^(E-22) from its half width), so the entries keep their accuracy."""
+    v, t = synth.mesh_for_config("sphere1280")
+    v = v * 1000.0 + np.array([3.0e4, -2.0e4, 5.0e3])
+    p = OParams(leaf_size=32, eta=2.0, box_gauss_m=3, aca_tol=1e-6, sauter_q=5)
+    ref = ogca.build_h2(v, t, p)
+    tree = lib.tree_build(v, t, 32)
+    h = lib.build(v, t, tree, _params(lib, p))
+    dump = h.export()
+    compare_structure(ref, dump, tree)
+    compare_coefficients(ref, dump, tree, TOL64)
+    x = synth.normal_rhs(len(t), 3, seed=2)
+    y = h.matvec(torch.from_numpy(x).cuda(), "f64").cpu().numpy()
+    assert rel_cols(y, oh2.matvec(ref, x)) <= TOL64
+
+
 def test_invalid_matvec_arguments(gpu_1280):
     import paper_1810_08429_b300 as gca
     h, _, _ = gpu_1280
