@@ -810,9 +810,8 @@ __global__ void k_near_entries(const int* __restrict__ near_t, const int* __rest
 // The xi-integral is therefore exactly 1/3 and only eta is sampled (q^3
 // Gauss points per piece).
 
-template <int CASE>
-__device__ __forceinline__ double sauter_piece(int piece, double e1, double e2, double e3,
-                                               double& u1, double& u2, double& v1, double& v2) {
+template <int CASE, typename R>
+R sauter_piece(int piece, R e1, R e2, R e3, R& u1, R& u2, R& v1, R& v2) {
   if (CASE == 3) {
     const double w = e1 * e1 * e2;
     switch (piece) {
@@ -843,12 +842,68 @@ __device__ __forceinline__ double sauter_piece(int piece, double e1, double e2, 
   }
 }
 
-// one warp per touching pair
+// One sample point of a Sauter-Schwab piece: h(eta) = sum_k c_k V_k over the
+// edge vectors V_k of the pair (case 1: e1, e2, f1, f2; case 2: e1, e2, f2
+// with c_0 = u1 - v1, since f1 = e1; case 3: e1, e2 with c = (u1 - v1,
+// u2 - v2)) and the weight W = w_a w_b w_c w^(eta), all as float pairs.
+// The table is computed on the host in long double, so the differences of
+// the identical-vertex cases are formed before any rounding.
+struct __align__(16) SSEntry {
+  float4 ch, cl;  // coefficients, high and low parts
+  float wh, wl;   // weight
+  float pad[2];
+};
+
+template <int CASE>
+void sauter_table(const Rules& rules, std::vector<SSEntry>& out) {
+  const int q = rules.q, q3 = q * q * q;
+  constexpr int pieces = CASE == 3 ? 6 : (CASE == 2 ? 5 : 2);
+  auto split = [](long double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (long double)hi);
+  };
+  for (int s = 0; s < pieces * q3; ++s) {
+    const int piece = s / q3, r = s % q3;
+    const int a = r / (q * q), b = (r / q) % q, c = r % q;
+    long double u1, u2, v1, v2;
+    const long double wj = sauter_piece<CASE, long double>(piece, rules.ss_t[a], rules.ss_t[b], rules.ss_t[c],
+                                                           u1, u2, v1, v2);
+    long double cf[4] = {0, 0, 0, 0};
+    if (CASE == 1) {
+      cf[0] = u1; cf[1] = u2; cf[2] = -v1; cf[3] = -v2;
+    } else if (CASE == 2) {
+      cf[0] = u1 - v1; cf[1] = u2; cf[2] = -v2;
+    } else {
+      cf[0] = u1 - v1; cf[1] = u2 - v2;
+    }
+    SSEntry e{};
+    split(cf[0], e.ch.x, e.cl.x);
+    split(cf[1], e.ch.y, e.cl.y);
+    split(cf[2], e.ch.z, e.cl.z);
+    split(cf[3], e.ch.w, e.cl.w);
+    split((long double)rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * wj, e.wh, e.wl);
+    out.push_back(e);
+  }
+}
+
+// c * (vh + vl) with c = ch + cl, added to the float pair (sh, sl)
+__device__ __forceinline__ void fp_mul_add(float ch, float cl, float vh, float vl, float& sh, float& sl) {
+  const float th = __fmul_rn(ch, vh);
+  const float tl = __fmaf_rn(ch, vl, __fmaf_rn(cl, vh, __fmaf_rn(ch, vh, -th)));
+  float ns, ne;
+  two_sum(sh, th, ns, ne);
+  sh = ns;
+  sl = __fadd_rn(sl, __fadd_rn(ne, tl));
+}
+
+// one warp per touching pair; the eta samples in float-pair arithmetic (the
+// regular rule's error-free sums, |h|^2 as a float pair and one Newton step
+// from rsqrtf), the pair's sum and its Jacobians in float64
 template <int CASE>
 __global__ void k_singular(const SingularItem* __restrict__ items,
                            const unsigned long long* __restrict__ counts, int64_t cap,
-                           const int* __restrict__ tri, const double* __restrict__ vert, Rules rules,
-                           double* __restrict__ N) {
+                           const int* __restrict__ tri, const double* __restrict__ vert,
+                           const SSEntry* __restrict__ table, int nsamples, double* __restrict__ N) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t count = min((long long)counts[CASE], (long long)cap);
@@ -898,20 +953,55 @@ __global__ void k_singular(const SingularItem* __restrict__ items,
     f1v[d] = qv[1][d] - qv[0][d];
     f2v[d] = qv[2][d] - qv[1][d];
   }
-  const int q = rules.q, q3 = q * q * q;
-  constexpr int pieces = CASE == 3 ? 6 : (CASE == 2 ? 5 : 2);
-  double acc = 0.0;
-  for (int s = lane; s < pieces * q3; s += 32) {
-    const int piece = s / q3, r = s % q3;
-    const int a = r / (q * q), b = (r / q) % q, c = r % q;
-    const double e1 = rules.ss_t[a], e2 = rules.ss_t[b], e3 = rules.ss_t[c];
-    double u1, u2, v1, v2;
-    const double wj = sauter_piece<CASE>(piece, e1, e2, e3, u1, u2, v1, v2);
-    double h[3];
-    for (int d = 0; d < 3; ++d) h[d] = u1 * e1v[d] + u2 * e2v[d] - v1 * f1v[d] - v2 * f2v[d];
-    const double r2 = h[0] * h[0] + h[1] * h[1] + h[2] * h[2];
-    acc += rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * wj * rsqrt(r2);
+  // the edge vectors of h as float pairs (case 2: f1 = e1; case 3: f = e)
+  constexpr int NT = CASE == 3 ? 2 : (CASE == 2 ? 3 : 4);
+  float vh[NT][3], vl[NT][3];
+  for (int d = 0; d < 3; ++d) {
+    const double src[4] = {e1v[d], e2v[d], CASE == 2 ? f2v[d] : f1v[d], f2v[d]};
+    for (int k = 0; k < NT; ++k) {
+      vh[k][d] = (float)src[k];
+      vl[k][d] = (float)(src[k] - (double)vh[k][d]);
+    }
   }
+  float ah = 0.f, al = 0.f;
+  for (int s = lane; s < nsamples; s += 32) {
+    const SSEntry e = table[s];
+    const float ch[4] = {e.ch.x, e.ch.y, e.ch.z, e.ch.w}, cl[4] = {e.cl.x, e.cl.y, e.cl.z, e.cl.w};
+    float hh[3], hl[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      hh[d] = 0.f;
+      hl[d] = 0.f;
+#pragma unroll
+      for (int k = 0; k < NT; ++k) fp_mul_add(ch[k], cl[k], vh[k][d], vl[k][d], hh[d], hl[d]);
+    }
+    // |h|^2 as a float pair
+    const float p0 = __fmul_rn(hh[0], hh[0]), p1 = __fmul_rn(hh[1], hh[1]), p2 = __fmul_rn(hh[2], hh[2]);
+    float low = __fmaf_rn(hh[0], hh[0], -p0);
+    low = __fadd_rn(low, __fmaf_rn(hh[1], hh[1], -p1));
+    low = __fadd_rn(low, __fmaf_rn(hh[2], hh[2], -p2));
+    low = __fmaf_rn(__fadd_rn(__fadd_rn(hh[0], hh[0]), hl[0]), hl[0], low);
+    low = __fmaf_rn(__fadd_rn(__fadd_rn(hh[1], hh[1]), hl[1]), hl[1], low);
+    low = __fmaf_rn(__fadd_rn(__fadd_rn(hh[2], hh[2]), hl[2]), hl[2], low);
+    float s01, e01, rh, e2;
+    two_sum(p0, p1, s01, e01);
+    two_sum(s01, p2, rh, e2);
+    const float rl = __fadd_rn(low, __fadd_rn(e01, e2));
+    // 1/|h| = y0 (1 + rho / 2), rho = 1 - y0^2 |h|^2
+    const float y0 = rsqrtf(__fadd_rn(rh, rl));
+    const float u = __fmul_rn(y0, y0), uu = __fmaf_rn(y0, y0, -u);
+    const float m = __fmul_rn(u, rh), me = __fmaf_rn(u, rh, -m);
+    const float rho = __fmaf_rn(-uu, rh, __fmaf_rn(-u, rl, __fsub_rn(__fsub_rn(1.f, m), me)));
+    const float dy = __fmul_rn(__fmul_rn(0.5f, y0), rho);
+    // acc += W / |h|
+    const float th = __fmul_rn(e.wh, y0);
+    const float tl = __fadd_rn(__fmaf_rn(e.wh, y0, -th), __fmaf_rn(e.wh, dy, __fmul_rn(e.wl, y0)));
+    float ns, ne;
+    two_sum(ah, th, ns, ne);
+    ah = ns;
+    al = __fadd_rn(al, __fadd_rn(ne, tl));
+  }
+  double acc = (double)ah + (double)al;
   for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   if (lane == 0) {
     double jp[3], jq[3];
@@ -1303,6 +1393,17 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   for (auto v : valence) cap += v * v;
   DevMem d_items, d_counts;
   GCA_TRY(d_items.alloc(sizeof(SingularItem) * 3 * (size_t)cap));
+  // sample tables of the three Sauter-Schwab cases (vertex, edge, identical)
+  std::vector<SSEntry> ss;
+  int ss_off[4] = {0, 0, 0, 0};
+  sauter_table<1>(rules, ss);
+  ss_off[1] = (int)ss.size();
+  sauter_table<2>(rules, ss);
+  ss_off[2] = (int)ss.size();
+  sauter_table<3>(rules, ss);
+  ss_off[3] = (int)ss.size();
+  DevMem d_ss;
+  GCA_TRY(upload(d_ss, ss, st));
   GCA_TRY(d_counts.alloc(sizeof(unsigned long long) * 4));
   GCA_TRY_CUDA(cudaMemsetAsync(d_counts.p, 0, sizeof(unsigned long long) * 4, st));
   layout_panels(h.get());
@@ -1356,16 +1457,19 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     const unsigned long long* cnt = d_counts.as<unsigned long long>();
     PhaseScope ps_sing("singular", st);
     ps_sing.launches((counts[1] > 0) + (counts[2] > 0) + (counts[3] > 0));
+    const SSEntry* tab = d_ss.as<SSEntry>();
     if (counts[1])
       k_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
-          items, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), rules, h->N64.as<double>());
+          items, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), tab + ss_off[0], ss_off[1] - ss_off[0],
+          h->N64.as<double>());
     if (counts[2])
       k_singular<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
-          items + cap, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), rules, h->N64.as<double>());
+          items + cap, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), tab + ss_off[1],
+          ss_off[2] - ss_off[1], h->N64.as<double>());
     if (counts[3])
       k_singular<3><<<blocks_for(32LL * counts[3], 256), 256, 0, st>>>(
-          items + 2 * cap, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), rules,
-          h->N64.as<double>());
+          items + 2 * cap, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), tab + ss_off[2],
+          ss_off[3] - ss_off[2], h->N64.as<double>());
     GCA_TRY_CUDA(cudaGetLastError());
   }
 
