@@ -54,7 +54,7 @@ constexpr int kStatusOverflow = 2;
 // ------------------------------------------------------------------ geometry
 
 __global__ void k_tri_geom(int nt, const double* __restrict__ vert, const int* __restrict__ tri,
-                           Rules rules, P4* __restrict__ tq) {
+                           Rules rules, P4* __restrict__ tq, double* __restrict__ area2) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const int ia = tri[3 * t], ib = tri[3 * t + 1], ic = tri[3 * t + 2];
@@ -69,7 +69,9 @@ __global__ void k_tri_geom(int nt, const double* __restrict__ vert, const int* _
   double cx = u[1] * v[2] - u[2] * v[1];
   double cy = u[2] * v[0] - u[0] * v[2];
   double cz = u[0] * v[1] - u[1] * v[0];
-  double area = 0.5 * sqrt(cx * cx + cy * cy + cz * cz);
+  const double a2 = sqrt(cx * cx + cy * cy + cz * cz);
+  area2[t] = a2;  // |(b - a) x (c - a)|, the Jacobian of the parametrisations of T
+  double area = 0.5 * a2;
   for (int q = 0; q < 7; ++q) {
     double l0 = rules.bary[q][0], l1 = rules.bary[q][1], l2 = rules.bary[q][2];
     tq[7 * t + q] = P4{l0 * a[0] + l1 * b[0] + l2 * c[0], l0 * a[1] + l1 * b[1] + l2 * c[1],
@@ -898,12 +900,13 @@ __device__ __forceinline__ void fp_mul_add(float ch, float cl, float vh, float v
 
 // one warp per touching pair; the eta samples in float-pair arithmetic (the
 // regular rule's error-free sums, |h|^2 as a float pair and one Newton step
-// from rsqrtf), the pair's sum and its Jacobians in float64
+// from rsqrtf), the pair's sum and its Jacobians (2 |T|) in float64
 template <int CASE>
 __global__ void k_singular(const SingularItem* __restrict__ items,
                            const unsigned long long* __restrict__ counts, int64_t cap,
                            const int* __restrict__ tri, const double* __restrict__ vert,
-                           const SSEntry* __restrict__ table, int nsamples, double* __restrict__ N) {
+                           const double* __restrict__ area2, const SSEntry* __restrict__ table, int nsamples,
+                           double* __restrict__ N) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t count = min((long long)counts[CASE], (long long)cap);
@@ -940,29 +943,30 @@ __global__ void k_singular(const SingularItem* __restrict__ items,
       Q[a] = tj[(pj + a) % 3];
     }
   }
-  double p[3][3], qv[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int d = 0; d < 3; ++d) {
-      p[a][d] = vert[3 * P[a] + d];
-      qv[a][d] = vert[3 * Q[a] + d];
-    }
-  double e1v[3], e2v[3], f1v[3], f2v[3];
-  for (int d = 0; d < 3; ++d) {
-    e1v[d] = p[1][d] - p[0][d];
-    e2v[d] = p[2][d] - p[1][d];
-    f1v[d] = qv[1][d] - qv[0][d];
-    f2v[d] = qv[2][d] - qv[1][d];
-  }
-  // the edge vectors of h as float pairs (case 2: f1 = e1; case 3: f = e)
+  // The edge vectors of h as float pairs (case 1: e1, e2, f1, f2; case 2: e1,
+  // e2, f2, since f1 = e1; case 3: e1, e2), e1 = P1 - P0, e2 = P2 - P1,
+  // f1 = Q1 - Q0, f2 = Q2 - Q1.  Lane 3k + d forms component d of vector k in
+  // float64 and splits it; the others receive it by shuffles.
   constexpr int NT = CASE == 3 ? 2 : (CASE == 2 ? 3 : 4);
-  float vh[NT][3], vl[NT][3];
-  for (int d = 0; d < 3; ++d) {
-    const double src[4] = {e1v[d], e2v[d], CASE == 2 ? f2v[d] : f1v[d], f2v[d]};
-    for (int k = 0; k < NT; ++k) {
-      vh[k][d] = (float)src[k];
-      vl[k][d] = (float)(src[k] - (double)vh[k][d]);
-    }
+  float my_h = 0.f, my_l = 0.f;
+  if (lane < 3 * NT) {
+    const int k = lane / 3, d = lane - 3 * k;
+    const bool useq = (CASE == 1 && k >= 2) || (CASE == 2 && k == 2);
+    const bool second = !(k == 0 || (CASE == 1 && k == 2));  // edge (1, 2) instead of (0, 1)
+    const int i0 = useq ? (second ? Q[1] : Q[0]) : (second ? P[1] : P[0]);
+    const int i1 = useq ? (second ? Q[2] : Q[1]) : (second ? P[2] : P[1]);
+    const double x = vert[3 * i1 + d] - vert[3 * i0 + d];
+    my_h = (float)x;
+    my_l = (float)(x - (double)my_h);
   }
+  float vh[NT][3], vl[NT][3];
+#pragma unroll
+  for (int k = 0; k < NT; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      vh[k][d] = __shfl_sync(0xffffffffu, my_h, 3 * k + d);
+      vl[k][d] = __shfl_sync(0xffffffffu, my_l, 3 * k + d);
+    }
   float ah = 0.f, al = 0.f;
   for (int s = lane; s < nsamples; s += 32) {
     const SSEntry e = table[s];
@@ -1003,18 +1007,8 @@ __global__ void k_singular(const SingularItem* __restrict__ items,
   }
   double acc = (double)ah + (double)al;
   for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if (lane == 0) {
-    double jp[3], jq[3];
-    jp[0] = e1v[1] * e2v[2] - e1v[2] * e2v[1];
-    jp[1] = e1v[2] * e2v[0] - e1v[0] * e2v[2];
-    jp[2] = e1v[0] * e2v[1] - e1v[1] * e2v[0];
-    jq[0] = f1v[1] * f2v[2] - f1v[2] * f2v[1];
-    jq[1] = f1v[2] * f2v[0] - f1v[0] * f2v[2];
-    jq[2] = f1v[0] * f2v[1] - f1v[1] * f2v[0];
-    const double JP = sqrt(jp[0] * jp[0] + jp[1] * jp[1] + jp[2] * jp[2]);
-    const double JQ = sqrt(jq[0] * jq[0] + jq[1] * jq[1] + jq[2] * jq[2]);
-    N[it.pos] = acc * JP * JQ * (kInv4Pi / 3.0);
-  }
+  // Jacobians |e1 x e2| and |f1 x f2|: twice the triangles' areas
+  if (lane == 0) N[it.pos] = acc * area2[it.ti] * area2[it.tj] * (kInv4Pi / 3.0);
 }
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -1087,15 +1081,16 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY(upload(h->d_perm, h->perm, st));
   GCA_TRY(upload(h->d_begin, h->begin, st));
   GCA_TRY(upload(h->d_end, h->end, st));
-  DevMem d_tq, d_box, d_diam, d_zq, d_status;
+  DevMem d_tq, d_area2, d_box, d_diam, d_zq, d_status;
   GCA_TRY(d_tq.alloc(sizeof(P4) * 7 * (size_t)n));
+  GCA_TRY(d_area2.alloc(sizeof(double) * (size_t)n));
   GCA_TRY(d_box.alloc(sizeof(double) * 6 * (size_t)nc));
   GCA_TRY(d_status.alloc(sizeof(int)));
   GCA_TRY_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), st));
   {
     PhaseScope ps__("tri_geom", st);
     k_tri_geom<<<blocks_for(n, 128), 128, 0, st>>>(n, h->d_vert.as<double>(), h->d_tri.as<int>(), rules,
-                                                  d_tq.as<P4>());
+                                                  d_tq.as<P4>(), d_area2.as<double>());
   }
   {
     PhaseScope ps__("cluster_boxes", st);
@@ -1458,18 +1453,19 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     PhaseScope ps_sing("singular", st);
     ps_sing.launches((counts[1] > 0) + (counts[2] > 0) + (counts[3] > 0));
     const SSEntry* tab = d_ss.as<SSEntry>();
+    const int* tri_d = h->d_tri.as<int>();
+    const double* vert_d = h->d_vert.as<double>();
+    const double* a2 = d_area2.as<double>();
+    double* N64 = h->N64.as<double>();
     if (counts[1])
       k_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
-          items, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), tab + ss_off[0], ss_off[1] - ss_off[0],
-          h->N64.as<double>());
+          items, cnt, cap, tri_d, vert_d, a2, tab + ss_off[0], ss_off[1] - ss_off[0], N64);
     if (counts[2])
       k_singular<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
-          items + cap, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), tab + ss_off[1],
-          ss_off[2] - ss_off[1], h->N64.as<double>());
+          items + cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[1], ss_off[2] - ss_off[1], N64);
     if (counts[3])
       k_singular<3><<<blocks_for(32LL * counts[3], 256), 256, 0, st>>>(
-          items + 2 * cap, cnt, cap, h->d_tri.as<int>(), h->d_vert.as<double>(), tab + ss_off[2],
-          ss_off[3] - ss_off[2], h->N64.as<double>());
+          items + 2 * cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[2], ss_off[3] - ss_off[2], N64);
     GCA_TRY_CUDA(cudaGetLastError());
   }
 
