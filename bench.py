@@ -349,6 +349,9 @@ def main():
 
     def step(record):
         nonlocal batch
+        # the previous step's batch is freed inside the step but outside the
+        # build's window (cudaFree of its buffers synchronises the device)
+        batch = None
         a = ev()
         batch = gca.build_batch(meshes, trees, prm)
         if record:

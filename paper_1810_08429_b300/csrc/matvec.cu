@@ -1232,34 +1232,47 @@ void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups
   constexpr double kWorkers = 148 * 8, kLatency = 10.0e-6, kBandwidth = 6.0e12;  // s, B/s
   std::vector<double> cost(ng);
   std::vector<int> sig(ng, -1);
-  std::vector<std::vector<std::pair<int, int>>> waits(ng);
-  std::vector<std::vector<int>> waiters(ncounters);
-  std::vector<int> total(ncounters, 0);
+  // the distinct counters each group waits for (wptr/wcnt, compressed by
+  // group) and the groups waiting for each counter (cptr/cgrp, by counter)
+  std::vector<int> wptr(ng + 1, 0), wctr;
+  wctr.reserve(ng);
+  std::vector<int> total(ncounters, 0), nwait(ncounters + 1, 0);
   for (int gi = 0; gi < ng; ++gi) {
     double bytes = 0;
+    int w[kMaxGroupSegs], nw = 0;
     for (int sgi = groups[gi].x; sgi < groups[gi].y; ++sgi) {
       const MvItem& it = items[sgi];
       bytes += 16.0 * std::min(kItemRows, it.m - it.a0) * (pad8(it.k) / 4);  // float panels
-      if (it.wait_idx >= 0) waits[gi].push_back({it.wait_idx, it.wait_cnt});
+      if (it.wait_idx >= 0 && nw < kMaxGroupSegs) w[nw++] = it.wait_idx;
     }
+    std::sort(w, w + nw);
+    nw = (int)(std::unique(w, w + nw) - w);
+    for (int j = 0; j < nw; ++j) {
+      wctr.push_back(w[j]);
+      ++nwait[w[j] + 1];
+    }
+    wptr[gi + 1] = (int)wctr.size();
     cost[gi] = kLatency + bytes / (kBandwidth / kWorkers);
     sig[gi] = items[groups[gi].y - 1].sig_idx;
     if (sig[gi] >= 0) total[sig[gi]]++;
-    std::sort(waits[gi].begin(), waits[gi].end());
-    waits[gi].erase(std::unique(waits[gi].begin(), waits[gi].end()), waits[gi].end());
-    for (auto& w : waits[gi]) waiters[w.first].push_back(gi);
   }
+  for (int c = 0; c < ncounters; ++c) nwait[c + 1] += nwait[c];
+  std::vector<int> cgrp(wctr.size()), cfill(nwait.begin(), nwait.end() - 1);
+  for (int gi = 0; gi < ng; ++gi)
+    for (int j = wptr[gi]; j < wptr[gi + 1]; ++j) cgrp[cfill[wctr[j]]++] = gi;
   // upward rank: emission order is topological, so one reverse sweep suffices
   std::vector<double> rank(ng, 0.0), cmax(ncounters, 0.0);
   for (int gi = ng - 1; gi >= 0; --gi) {
     rank[gi] = cost[gi] + (sig[gi] >= 0 ? cmax[sig[gi]] : 0.0);
-    for (auto& w : waits[gi]) cmax[w.first] = std::max(cmax[w.first], rank[gi]);
+    for (int j = wptr[gi]; j < wptr[gi + 1]; ++j) cmax[wctr[j]] = std::max(cmax[wctr[j]], rank[gi]);
   }
   std::vector<int> pending(ng), done(ncounters, 0);
   using Ready = std::pair<double, int>;  // (rank, group)
-  std::priority_queue<Ready> ready;
+  std::vector<Ready> ready_store;
+  ready_store.reserve(ng);
+  std::priority_queue<Ready> ready(std::less<Ready>(), std::move(ready_store));
   for (int gi = 0; gi < ng; ++gi) {
-    pending[gi] = (int)waits[gi].size();
+    pending[gi] = wptr[gi + 1] - wptr[gi];
     if (pending[gi] == 0) ready.push({rank[gi], gi});
   }
   using Run = std::pair<double, int>;  // (finish, group), earliest first
@@ -1286,8 +1299,9 @@ void schedule_groups(const std::vector<MvItem>& items, std::vector<int2>& groups
     ++free_workers;
     const int c = sig[r.second];
     if (c >= 0 && ++done[c] == total[c])
-      for (int gw : waiters[c]) {
+      for (int j = nwait[c]; j < nwait[c + 1]; ++j) {
         // a group waits for the counter to reach its full count
+        const int gw = cgrp[j];
         if (--pending[gw] == 0) ready.push({rank[gw], gw});
       }
   }
@@ -1350,6 +1364,11 @@ int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
   std::vector<int2> groups, free_groups;
   std::vector<int2>* target = &groups;  // list the groups being emitted go to
   std::vector<int> cx(nc, 0), cy(nc, 0);  // contributions (groups) to x-hat_c, y-hat_c
+  {
+    const size_t nblk = h->far_t.size() + h->near_t.size();
+    items.reserve(2 * nblk + 4 * (size_t)nc);
+    groups.reserve(nblk / 2 + 4 * (size_t)nc);
+  }
   struct Blk {
     int kind;
     int64_t a_off;
