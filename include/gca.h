@@ -212,8 +212,15 @@ int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t max_clusters
  * leaves (leaf bases V_tau, transfer matrices E_tau, pivot sets tilde-tau),
  * coupling matrices S = G|tilde-tau x tilde-sigma and near-field blocks
  * G|tau-hat x sigma-hat, plus float32 / bfloat16 copies for the reduced
- * precision products.  mesh/tree/params are copied; *out receives a new
- * handle.  Synchronises `stream`.  Errors: INVALID_ARG, OOM, CUDA, NUMERIC. */
+ * precision products.  The coefficients are stored in float64.  The Green
+ * matrices and the cross approximation are computed in float64; the 7 x 7
+ * and Sauter-Schwab quadratures of S and N in float-pair arithmetic (about
+ * 48 significant bits, 1e-13 relative or better; near-field pairs with
+ * nodes closer than 2^-8 of the mesh's half width fall back to float64).
+ * Cluster bases that no admissible block uses, directly or through an
+ * ancestor, are not built (rank 0).  mesh/tree/params are copied; *out
+ * receives a new handle.  Synchronises `stream`.  Errors: INVALID_ARG,
+ * OOM, CUDA, NUMERIC. */
 int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
               void* stream, gca_h2** out);
 
