@@ -220,7 +220,8 @@ int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t max_clusters
  * Cluster bases that no admissible block uses, directly or through an
  * ancestor, are not built (rank 0).  mesh/tree/params are copied; *out
  * receives a new handle.  Synchronises `stream`.  Errors: INVALID_ARG,
- * OOM, CUDA, NUMERIC. */
+ * OOM, CUDA, NUMERIC; UNSUPPORTED when the mesh's half width lies outside
+ * [2^-41, 2^40] (float exponent range of the float-pair quadrature). */
 int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
               void* stream, gca_h2** out);
 

@@ -1115,6 +1115,11 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     }
     int E = 0;
     std::frexp(std::max(half, 1e-300), &E);  // half < 2^E
+    if (E < -40 || E > 40) {
+      // |d|^2 and the grid must stay inside float's exponent range
+      set_error("gca_build: mesh half width outside [2^-41, 2^40]; rescale the coordinates");
+      return GCA_ERR_UNSUPPORTED;
+    }
     const double g = std::ldexp(1.0, E - 22);
     near_r2 = (float)std::ldexp(1.0, 2 * (E - 8));
     GCA_TRY(d_tn.alloc(sizeof(SplitNode) * 7 * (size_t)n));

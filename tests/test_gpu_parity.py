@@ -262,6 +262,17 @@ def test_translated_scaled_mesh(lib):
     assert rel_cols(y, oh2.matvec(ref, x)) <= TOL64
 
 
+def test_mesh_scale_outside_float_range_refused(lib):
+    """A mesh 1e-14 wide would underflow the float-pair quadrature: the build
+    refuses it with an error instead of returning wrong entries."""
+    v, t = synth.icosahedron()
+    v = v * 1e-14
+    p = OParams(leaf_size=32, eta=2.0, box_gauss_m=3, aca_tol=1e-6, sauter_q=5)
+    tree = lib.tree_build(v, t, 32)
+    with pytest.raises(Exception, match="half width"):
+        lib.build(v, t, tree, _params(lib, p))
+
+
 def test_invalid_matvec_arguments(gpu_1280):
     import paper_1810_08429_b300 as gca
     h, _, _ = gpu_1280
