@@ -241,3 +241,38 @@ def test_error_falls_with_tolerance(sphere1280, dense_1280, h2_1280):
     # the achieved accuracy tracks the requested tolerance
     for tol, e in zip((1e-2, 1e-3, 1e-4, 1e-6), errs):
         assert e < tol
+
+
+def test_needed_clusters_brute_force(h2_1280):
+    """needed(c) against its definition (Sect. 4: a basis enters the matrix
+    only through V_tau S V_sigma^T and, nested, through its ancestors'): c or
+    one of its ancestors is a row or column cluster of an admissible block.
+    The clusters without a basis are exactly the unneeded ones, and the
+    product still matches the one with every basis (checked elsewhere
+    against the dense G)."""
+    tree = h2_1280.tree
+    nc = len(tree["begin"])
+    parent = np.full(nc, -1)
+    for c in range(nc):
+        for ch in (tree["child0"][c], tree["child1"][c]):
+            if ch >= 0:
+                parent[ch] = c
+    in_far = set()
+    for (t, s) in h2_1280.far:
+        in_far.add(int(t))
+        in_far.add(int(s))
+    ref = np.zeros(nc, dtype=bool)
+    for c in range(nc):
+        a = c
+        while a >= 0:
+            if a in in_far:
+                ref[c] = True
+                break
+            a = parent[a]
+    got = gca.needed_clusters(tree, h2_1280.far)
+    assert np.array_equal(got, ref)
+    assert not got[0]                       # the root is in no admissible block
+    assert (~got).sum() > 1                 # the sphere's upper levels are unused
+    rank = h2_1280.bases.rank
+    assert np.all(rank[~got] == 0)
+    assert np.all(rank[got] > 0)
