@@ -647,16 +647,16 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // One entry by the 7 x 7 rule of regular_entry, evaluated on the FP32 pipe
-// in float-pair arithmetic.  A term's relative error is about
-// 2^(E - 45) / |d| (2^E bounds |x - o|, d = x - y; the rounding of the low
-// parts of the nodes): 1e-13 and below for the admissible pairs of the
-// coupling blocks, whose nodes lie at least a fraction of a cluster
-// diameter apart.  min_r2 returns the smallest |d|^2
-// (high part) met, so that callers with close pairs can fall back to
-// float64.  Per node pair: d = (x_hi - y_hi) + (x_lo - y_lo) with an exact high part;
-// r^2 = |d|^2 as a float pair; 1/r from rsqrtf refined by one Newton step
-// whose residual 1 - y0^2 r^2 is formed exactly to first order; the weighted
-// terms are summed as float pairs and rounded to double once per entry.
+// in float-pair arithmetic.  Per node pair: d = (x_hi - y_hi) + (x_lo - y_lo)
+// with an exact high part; r^2 = |d|^2 as a float pair; 1/r from rsqrtf
+// refined by one Newton step whose residual 1 - y0^2 r^2 is formed exactly
+// to first order; the weighted terms are summed as float pairs and rounded
+// to double once per entry.  A term's relative error is about
+// 2^(E - 45) / |d| (2^E bounds |x - o|, d = x - y; it comes from the
+// rounding of the nodes' low parts): 1e-13 and below for the admissible
+// pairs of the coupling blocks, whose nodes lie at least a fraction of a
+// cluster diameter apart.  min_r2 returns the smallest |d|^2 (high part)
+// met, so that callers with close pairs can fall back to float64.
 __device__ __forceinline__ double regular_entry_split(const SplitNode* __restrict__ xq,
                                                       const SplitNode* __restrict__ yq, float& min_r2) {
   float sh = 0.f, sl = 0.f;
