@@ -456,17 +456,31 @@ struct PanelJob {
 // moves with one contiguous copy.
 constexpr int kTileRows = 64, kTileCols = 64;
 
-__host__ __device__ inline int64_t tile_index(int m, int kp, int P, int64_t d, int* row, int* col) {
-  const int64_t slice_elems = (int64_t)kTileRows * kp;
-  const int i = (int)(d / slice_elems);
-  const int64_t e = d - i * slice_elems;
+// Element d of the panel layout of an m x kp block, split into the parts
+// that do not depend on the panel width P: its tile's first row and column,
+// the tile's row count ms and the offset f inside the tile.  Block-local
+// indices stay below 2^31, so 32-bit division suffices.
+struct TilePos {
+  int row0, col0, ms, f;
+};
+
+__device__ __forceinline__ TilePos tile_pos(int m, int kp, int d) {
+  const int slice = kTileRows * kp;
+  const int i = d / slice;
+  const int e = d - i * slice;
   const int ms = min(kTileRows, m - i * kTileRows);
-  const int j = (int)(e / ((int64_t)ms * kTileCols));
-  const int64_t f = e - (int64_t)j * ms * kTileCols;
-  const int p = (int)(f / (ms * P)), g = (int)(f % (ms * P));
-  *row = i * kTileRows + g / P;
-  *col = j * kTileCols + p * P + g % P;
-  return d;
+  const int tile = ms * kTileCols;
+  const int j = e / tile;
+  return TilePos{i * kTileRows, j * kTileCols, ms, e - j * tile};
+}
+
+// (row, column) of the entry at offset f of a tile with ms rows and panels of
+// P = 2^lgp entries per row
+__device__ __forceinline__ void tile_entry(const TilePos& t, int lgp, int& row, int& col) {
+  const int mp = t.ms << lgp;
+  const int p = t.f / mp, g = t.f - p * mp;
+  row = t.row0 + (g >> lgp);
+  col = t.col0 + (p << lgp) + (g & ((1 << lgp) - 1));
 }
 
 __global__ void k_to_panel(const PanelJob* __restrict__ jobs, const double* __restrict__ src,
@@ -474,23 +488,24 @@ __global__ void k_to_panel(const PanelJob* __restrict__ jobs, const double* __re
                            __nv_bfloat16* __restrict__ d16) {
   const PanelJob j = jobs[blockIdx.x];
   const int kp = pad8(j.k);
-  const int64_t total = (int64_t)j.m * kp;
+  const int total = j.m * kp;
   auto at = [&](int a, int kk) -> double {
     if (kk >= j.k) return 0.0;
     return j.trans ? src[j.src + (int64_t)kk * j.m + a] : src[j.src + (int64_t)a * j.k + kk];
   };
-  for (int64_t d = threadIdx.x; d < total; d += blockDim.x) {
+  for (int d = threadIdx.x; d < total; d += blockDim.x) {
+    const TilePos t = tile_pos(j.m, kp, d);
     int a, kk;
     if (d64) {
-      tile_index(j.m, kp, 2, d, &a, &kk);
+      tile_entry(t, 1, a, kk);
       d64[j.dst + d] = at(a, kk);
     }
     if (d32) {
-      tile_index(j.m, kp, 4, d, &a, &kk);
+      tile_entry(t, 2, a, kk);
       d32[j.dst + d] = (float)at(a, kk);
     }
     if (d16) {
-      tile_index(j.m, kp, 8, d, &a, &kk);
+      tile_entry(t, 3, a, kk);
       d16[j.dst + d] = __double2bfloat16(at(a, kk));
     }
   }
