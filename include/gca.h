@@ -31,7 +31,11 @@
  *     over the bus -- the transfer then happens inside the product's own
  *     kernels.  Any other pointer (pageable host memory, another device's
  *     memory) is refused with GCA_ERR_INVALID_ARG.
- *   - Handles own all of their device memory until gca_free().
+ *   - Handles own all of their device memory until gca_free().  A handle
+ *     (or batch) lives on the device that was current when it was built or
+ *     imported; every call that launches work on it checks that this device
+ *     is current and otherwise fails with GCA_ERR_INVALID_ARG, naming both
+ *     ordinals, before anything is launched.
  *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
  *     default stream.  Products are stream ordered and do not synchronise.
  *     gca_build synchronises the stream (it sizes its outputs from ranks
@@ -225,7 +229,13 @@ int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t max_clusters
 int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
               void* stream, gca_h2** out);
 
-/* y = G_H2 x for nrhs right-hand sides.  x: column-major n x nrhs with
+/* y = G_H2 x for nrhs right-hand sides, G_H2 the representation of Sect. 4:
+ * y|tau-hat = sum over admissible (tau, sigma) of V_tau S_{tau sigma}
+ * V_sigma^* x|sigma-hat plus sum over inadmissible leaf pairs of
+ * N_{tau sigma} x|sigma-hat, evaluated by the H^2 recursion (forward
+ * transform x-hat_sigma = V_sigma^* x up the tree through the transfer
+ * matrices E, coupling, backward transform down the tree, near field).
+ * x: column-major n x nrhs with
  * leading dimension ldx >= n, rows in original triangle order; y: same layout
  * with ldy >= n, overwritten (device or mapped page-locked host memory, see
  * the conventions above).  Element type float64
@@ -251,12 +261,19 @@ int h2_matvec(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64
  *     other threads, other handles) race and give wrong results; order them;
  *   - a product whose workspace exceeds the array is rejected with
  *     GCA_ERR_UNSUPPORTED and a message giving the bytes it would need (the
- *     20480-triangle workload fits with 16 float32 right-hand sides).
+ *     20480-triangle workload fits with 16 float32 right-hand sides);
+ *   - the address looked up on the first call is kept for the life of the
+ *     process: resetting the device (cudaDeviceReset) between calls is not
+ *     supported, since the library's device data is reloaded elsewhere;
+ *   - with tracing on its time is recorded as "mv_persistent_noalloc.<prec>".
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
 int h2_matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx,
                       void* y, int64_t ldy, void* stream);
 
-/* y = G_H2^T x, same conventions as h2_matvec. */
+/* y = G_H2^T x, same conventions as h2_matvec: the representation of
+ * Sect. 4 transposed, y|sigma-hat = sum V_sigma S_{tau sigma}^* V_tau^* x|tau-hat
+ * plus sum N_{tau sigma}^* x|tau-hat (for the symmetric Galerkin matrix of
+ * Eq. (1) it equals h2_matvec up to the order of floating-point sums). */
 int h2_matvec_transpose(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x,
                         int64_t ldx, void* y, int64_t ldy, void* stream);
 
@@ -266,7 +283,9 @@ int h2_matvec_transpose(const gca_h2* h, gca_prec prec, int32_t nrhs, const void
  * time and launch count per phase name (at most cap entries; *count gets
  * the number of phases) and clears the accumulators.  Phase names: build
  * phases ("green_aca", "couple_entries", ...) and product phases
- * "mv_<stage>.<f64|f32|bf16>[.T]". */
+ * "mv_<stage>.<f64|f32|bf16>[.T]".  on = 2 splits the per-level build
+ * phases by tree level L and thread-block cluster size C
+ * ("green_aca.L<L>.c<C>"); on = 0 stops recording. */
 typedef struct {
   char name[32];
   int64_t launches;
@@ -276,8 +295,10 @@ int gca_profile_enable(int on);
 int gca_profile_read(gca_phase* out, int32_t cap, int32_t* count);
 
 /* Arithmetic throughput probe (not part of the method): chains of fused
- * multiply-adds on every SM; FLOP/s in float64 and float32, 2 per FMA.
- * Used as the denominator of the ALU roofline of the build kernels. */
+ * multiply-adds on every SM; FLOP/s in float64 (scalar FMA) and float32
+ * (packed pairs, fma.rn.f32x2: the instruction the float kernels issue), 2
+ * per FMA.  Used as the denominator of the ALU roofline of the build
+ * kernels. */
 int gca_peak_probe(double* fp64_flops, double* fp32_flops);
 
 /* Batches: independent GCA-H^2 matrices (one per mesh) built with the same
@@ -336,10 +357,62 @@ void gca_tune_clear(void);
  * of that product are unreliable.  Synchronises the device. */
 int gca_h2_status(const gca_h2* h, int32_t* status);
 
+/* Synchronise `stream`, then turn the status bits of the products run on
+ * this handle (batch) so far into a return code: GCA_ERR_TIMEOUT when a
+ * bounded device-side wait expired (bit 1), GCA_ERR_INVALID_ARG when a
+ * product met a malformed work record (bit 2), GCA_OK when neither.  The
+ * bits stay set until gca_h2_clear_status (gca_batch_clear_status), which
+ * synchronises the device and clears them; a product after the clear runs
+ * normally (the expired product's results are unreliable, nothing else). */
+int gca_h2_check(const gca_h2* h, void* stream);
+int gca_h2_clear_status(const gca_h2* h);
+int gca_batch_check(const gca_h2_batch* b, void* stream);
+int gca_batch_clear_status(const gca_h2_batch* b);
+
+/* Handle from a host copy of an H^2 representation (Sect. 4) computed
+ * elsewhere, e.g. by another implementation of the construction, so that
+ * the products (h2_matvec, h2_matvec_transpose, h2_matvec_noalloc) run on
+ * it with the construction bypassed.  `tree` is the cluster tree over nt
+ * triangles (as for gca_build); `dump` holds the representation in the
+ * layout gca_h2_export writes, with nfar coupling and nnear near-field
+ * blocks (pairs in any order; every array but `pivots` is required, and
+ * `pivots` only when some rank is positive).  Requirements: rank 0 for the
+ * root, 0 <= r_tau <= |tau-hat| at leaves and <= r_tau1 + r_tau2 above;
+ * coupling blocks between non-root clusters; near-field blocks between
+ * leaves; finite coefficients.  `flags` selects the kept copies as in
+ * gca_params.flags; the stats' k and n_singular are 0.  The arrays are
+ * copied; synchronises `stream`.  Errors: INVALID_ARG (inconsistent input),
+ * NUMERIC (non-finite coefficient), OOM, CUDA. */
+int gca_h2_import(const gca_tree* tree, int32_t nt, int32_t nfar, int32_t nnear, const gca_host_dump* dump,
+                  uint32_t flags, void* stream, gca_h2** out);
+
 int gca_h2_stats(const gca_h2* h, gca_stats* out);
 int gca_h2_export(const gca_h2* h, gca_host_dump* out);
 void gca_free(gca_h2* h);
 const char* gca_strerror(int status);
+/* Text of the last error raised on the calling thread (empty if none); valid
+ * until the thread's next failing call. */
+const char* gca_last_error(void);
+
+/* Test hooks (not part of the method): process-wide settings that let tests
+ * reach the failure paths without faulting a GPU.  `name`:
+ *   "wait_cycles"  bound of every device-side wait of the product kernels,
+ *                  in SM clock cycles (default 2^31, about a second);
+ *                  value <= 0 restores the default.
+ *   "stall_chain"  value != 0: every dependency wait of later products
+ *                  needs one completion more than the plan provides (a
+ *                  count that nothing reaches), so the first producer that
+ *                  waits for an input runs out of its bounded wait, sets
+ *                  status bit 1 and the launch winds down; 0: off.
+ *   "fail_alloc"   value n > 0: the n-th device allocation of the library
+ *                  from now on fails as if the device were out of memory
+ *                  (the call then returns GCA_ERR_OOM and frees what it
+ *                  allocated); 0: off.
+ *   "device_skew"  handles and batches built or imported from now on record
+ *                  (current device + value) as their device, so that the
+ *                  wrong-device check can be exercised on one GPU; 0: off.
+ * Errors: INVALID_ARG for an unknown name. */
+int gca_test_hook(const char* name, int64_t value);
 
 #ifdef __cplusplus
 }

@@ -116,6 +116,14 @@ def _load():
         "gca_tune_get": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
         "gca_tune_clear": (None, []),
+        "gca_h2_check": (ctypes.c_int, [vp, vp]),
+        "gca_h2_clear_status": (ctypes.c_int, [vp]),
+        "gca_batch_check": (ctypes.c_int, [vp, vp]),
+        "gca_batch_clear_status": (ctypes.c_int, [vp]),
+        "gca_h2_import": (ctypes.c_int, [ctypes.POINTER(_Tree), ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.POINTER(_Dump), ctypes.c_uint32, vp,
+                                         ctypes.POINTER(vp)]),
+        "gca_test_hook": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -127,14 +135,21 @@ def _load():
 lib = _load()
 
 
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+
+
 class GCAError(RuntimeError):
-    pass
+    """A failed library call; ``status`` is the gca_status code."""
+
+    def __init__(self, msg, status=None):
+        super().__init__(msg)
+        self.status = status
 
 
 def _check(status, what):
     if status != 0:
         msg = lib.gca_last_error().decode(errors="replace")
-        raise GCAError(f"{what}: {lib.gca_strerror(status).decode()} ({status}): {msg}")
+        raise GCAError(f"{what}: {lib.gca_strerror(status).decode()} ({status}): {msg}", status)
 
 
 @dataclass
@@ -192,6 +207,8 @@ def _tree(tree):
 def _stream_ptr(stream):
     import torch
     if stream is None:
+        if not torch.cuda.is_available():
+            return ctypes.c_void_p(None)  # host-side validation fails before any device work
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
 
@@ -232,28 +249,52 @@ class H2:
         _check(lib.gca_h2_status(self._h, ctypes.byref(v)), "gca_h2_status")
         return v.value
 
-    def export(self):
-        """Host copy of the representation (layout documented in gca.h)."""
+    def check(self, stream=None):
+        """Raise GCAError (GCA_ERR_TIMEOUT, ...) if a product on this handle
+        recorded an error (gca_h2_check); synchronises the stream."""
+        _check(lib.gca_h2_check(self._h, _stream_ptr(stream)), "gca_h2_check")
+
+    def clear_status(self):
+        """Clear the sticky error bits (gca_h2_clear_status)."""
+        _check(lib.gca_h2_clear_status(self._h), "gca_h2_clear_status")
+
+    def matvec_noalloc(self, x, prec="f64", out=None, stream=None):
+        """y = G_H2 x through h2_matvec_noalloc (workspace from the library's
+        fixed device array; same conventions as ``matvec``)."""
+        import torch
+        p = _PREC[prec]
+        dt = torch.float64 if p == F64 else torch.float32
+        x2, vec = _as_colmajor(x, dt)
+        n, R = x2.shape
+        if out is None:
+            out = _empty_like_colmajor(x2, dt)
+        y2 = out[:, None] if out.dim() == 1 else out
+        _check(lib.h2_matvec_noalloc(self._h, p, R, ctypes.c_void_p(x2.data_ptr()),
+                                     x2.stride(1) if R > 1 else n, ctypes.c_void_p(y2.data_ptr()),
+                                     y2.stride(1) if R > 1 else n, _stream_ptr(stream)),
+               "h2_matvec_noalloc")
+        return out[:, 0] if vec and out.dim() == 2 else out
+
+    def export(self, parts=None):
+        """Host copy of the representation (layout documented in gca.h); with
+        `parts` (e.g. ("rank",)) only those arrays are copied."""
         s = self.stats()
-        d = {
-            "rank": np.zeros(s["nclusters"], dtype=np.int32),
-            "pivots": np.zeros(max(s["rank_sum"], 1), dtype=np.int32),
-            "far": np.zeros(2 * max(s["nfar"], 1), dtype=np.int32),
-            "near": np.zeros(2 * max(s["nnear"], 1), dtype=np.int32),
-            "V": np.zeros(max(s["v_entries"], 1)),
-            "E": np.zeros(max(s["e_entries"], 1)),
-            "S": np.zeros(max(s["s_entries"], 1)),
-            "N": np.zeros(max(s["n_entries"], 1)),
-        }
-        dump = _Dump(*[d[k].ctypes.data_as(_i32p if d[k].dtype == np.int32 else _f64p)
-                       for k in ("rank", "pivots", "far", "near", "V", "E", "S", "N")])
+        sizes = {"rank": s["nclusters"], "pivots": s["rank_sum"], "far": 2 * s["nfar"],
+                 "near": 2 * s["nnear"], "V": s["v_entries"], "E": s["e_entries"],
+                 "S": s["s_entries"], "N": s["n_entries"]}
+        keys = ("rank", "pivots", "far", "near", "V", "E", "S", "N")
+        want = set(keys if parts is None else parts)
+        d = {k: np.zeros(max(sizes[k], 1), dtype=np.int32 if k in ("rank", "pivots", "far", "near")
+                         else np.float64) for k in keys if k in want}
+        dump = _Dump(*[d[k].ctypes.data_as(_i32p if d[k].dtype == np.int32 else _f64p) if k in d
+                       else None for k in keys])
         _check(lib.gca_h2_export(self._h, ctypes.byref(dump)), "gca_h2_export")
-        d["pivots"] = d["pivots"][:s["rank_sum"]]
-        d["far"] = d["far"][:2 * s["nfar"]].reshape(-1, 2)
-        d["near"] = d["near"][:2 * s["nnear"]].reshape(-1, 2)
-        for k, key in (("V", "v_entries"), ("E", "e_entries"), ("S", "s_entries"),
-                       ("N", "n_entries")):
-            d[k] = d[k][:s[key]]
+        for k in d:
+            d[k] = d[k][:sizes[k]]
+        if "far" in d:
+            d["far"] = d["far"].reshape(-1, 2)
+        if "near" in d:
+            d["near"] = d["near"].reshape(-1, 2)
         return d
 
     def matvec_raw(self, prec, nrhs, x_ptr, ldx, y_ptr, ldy, stream_ptr, transpose=False):
@@ -285,9 +326,10 @@ class H2:
         return out[:, 0] if vec and out.dim() == 2 else out
 
 
-def profile_enable(on=True):
-    """Start / stop per-phase GPU event timing (gca_profile_enable)."""
-    _check(lib.gca_profile_enable(1 if on else 0), "gca_profile_enable")
+def profile_enable(on=True, detail=False):
+    """Start / stop per-phase GPU event timing (gca_profile_enable); with
+    `detail` the build's per-level phases are split by level and cluster size."""
+    _check(lib.gca_profile_enable((2 if detail else 1) if on else 0), "gca_profile_enable")
 
 
 def profile_read():
@@ -315,6 +357,43 @@ def build(vertices, triangles, tree, params, stream=None):
     _check(lib.gca_build(ctypes.byref(m), ctypes.byref(t), ctypes.byref(p), _stream_ptr(stream),
                          ctypes.byref(h)), "gca_build")
     return H2(h.value)
+
+
+def _dump_arrays(d):
+    """gca_host_dump over the arrays of `d` (keys as ``H2.export`` returns)."""
+    arrs = {
+        "rank": np.ascontiguousarray(d["rank"], dtype=np.int32),
+        "pivots": np.ascontiguousarray(d["pivots"], dtype=np.int32),
+        "far": np.ascontiguousarray(np.asarray(d["far"], dtype=np.int32).reshape(-1)),
+        "near": np.ascontiguousarray(np.asarray(d["near"], dtype=np.int32).reshape(-1)),
+    }
+    for k in ("V", "E", "S", "N"):
+        arrs[k] = np.ascontiguousarray(d[k], dtype=np.float64)
+    for k, a in arrs.items():
+        if a.size == 0:
+            arrs[k] = np.zeros(1, dtype=a.dtype)
+    dump = _Dump(*[arrs[k].ctypes.data_as(_i32p if arrs[k].dtype == np.int32 else _f64p)
+                   for k in ("rank", "pivots", "far", "near", "V", "E", "S", "N")])
+    return dump, arrs
+
+
+def import_h2(tree, n, rep, flags=0, stream=None):
+    """gca_h2_import: a handle from a host representation `rep` (dict with
+    rank, pivots, far [(tau, sigma)], near, V, E, S, N in the layout of
+    ``H2.export``) over the cluster tree `tree` of n triangles."""
+    t, keep_t = _tree(tree)
+    dump, keep_d = _dump_arrays(rep)
+    nfar = len(np.asarray(rep["far"]).reshape(-1)) // 2
+    nnear = len(np.asarray(rep["near"]).reshape(-1)) // 2
+    h = ctypes.c_void_p(None)
+    _check(lib.gca_h2_import(ctypes.byref(t), n, nfar, nnear, ctypes.byref(dump), flags,
+                             _stream_ptr(stream), ctypes.byref(h)), "gca_h2_import")
+    return H2(h.value)
+
+
+def test_hook(name, value):
+    """Set a failure-path test hook (gca_test_hook)."""
+    _check(lib.gca_test_hook(name.encode(), int(value)), "gca_test_hook")
 
 
 def _as_colmajor(x, dt):
@@ -368,6 +447,13 @@ class Batch:
         v = ctypes.c_int32(0)
         _check(lib.gca_batch_status(self._b, ctypes.byref(v)), "gca_batch_status")
         return v.value
+
+    def check(self, stream=None):
+        """Raise GCAError if a product on this batch recorded an error."""
+        _check(lib.gca_batch_check(self._b, _stream_ptr(stream)), "gca_batch_check")
+
+    def clear_status(self):
+        _check(lib.gca_batch_clear_status(self._b), "gca_batch_clear_status")
 
     def tune(self, xs, prec="f32", transpose=False, outs=None, stream=None):
         """Autotune the tile width of this product (``gca_tune_batch``): runs it

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <memory>
@@ -14,9 +15,36 @@
 namespace gca {
 namespace {
 thread_local std::string g_last_error;
-}
+std::atomic<long long> g_wait_cycles{kDefaultWaitCycles};
+std::atomic<int> g_stall_chain{0};
+std::atomic<int> g_device_skew{0};
+std::atomic<long long> g_fail_alloc{0};  // allocations left before the injected failure (0: off)
+}  // namespace
 void set_error(const std::string& msg) { g_last_error = msg; }
 std::string last_error() { return g_last_error; }
+
+TestHooks test_hooks() {
+  return TestHooks{g_wait_cycles.load(), g_stall_chain.load(), g_device_skew.load()};
+}
+
+bool alloc_should_fail() {
+  long long left = g_fail_alloc.load();
+  while (left > 0) {
+    if (g_fail_alloc.compare_exchange_weak(left, left - 1)) return left == 1;
+  }
+  return false;
+}
+
+int check_device(int device, const char* what) {
+  int cur = -1;
+  GCA_TRY_CUDA(cudaGetDevice(&cur));
+  if (cur != device) {
+    set_error(std::string(what) + ": built on device " + std::to_string(device) + ", but device " +
+              std::to_string(cur) + " is current (make the handle's device current first)");
+    return GCA_ERR_INVALID_ARG;
+  }
+  return GCA_OK;
+}
 }  // namespace gca
 
 extern "C" {
@@ -51,6 +79,21 @@ int h2_matvec_transpose(const gca_h2* h, gca_prec prec, int32_t nrhs, const void
 int h2_matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx,
                       void* y, int64_t ldy, void* stream) {
   return gca::matvec_noalloc(h, prec, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream));
+}
+
+int gca_h2_import(const gca_tree* tree, int32_t nt, int32_t nfar, int32_t nnear, const gca_host_dump* dump,
+                  uint32_t flags, void* stream, gca_h2** out) {
+  if (!out) {
+    gca::set_error("gca_h2_import: out is NULL");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    return gca::import_h2(tree, nt, nfar, nnear, dump, flags, static_cast<cudaStream_t>(stream), out);
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_h2_import: host allocation failed");
+    return GCA_ERR_OOM;
+  }
 }
 
 int gca_h2_stats(const gca_h2* h, gca_stats* o) {
@@ -131,6 +174,70 @@ int gca_h2_status(const gca_h2* h, int32_t* status) {
   return GCA_OK;
 }
 
+namespace {
+// the first error recorded in a product status word
+int status_error(int bits, const char* what) {
+  if (bits & 1) {
+    gca::set_error(std::string(what) + ": a bounded device-side wait of a product expired");
+    return GCA_ERR_TIMEOUT;
+  }
+  if (bits & 2) {
+    gca::set_error(std::string(what) + ": a product kernel met a malformed work record");
+    return GCA_ERR_INVALID_ARG;
+  }
+  return GCA_OK;
+}
+
+int sync_status(const gca::DevMem& st, void* stream, int* bits) {
+  GCA_TRY_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  GCA_TRY_CUDA(cudaMemcpy(bits, st.p, sizeof(int), cudaMemcpyDeviceToHost));
+  return GCA_OK;
+}
+}  // namespace
+
+int gca_h2_check(const gca_h2* h, void* stream) {
+  if (!h) {
+    gca::set_error("gca_h2_check: NULL handle");
+    return GCA_ERR_INVALID_ARG;
+  }
+  GCA_TRY(gca::check_device(h->device, "gca_h2_check"));
+  int bits = 0;
+  GCA_TRY(sync_status(h->d_status, stream, &bits));
+  return status_error(bits, "gca_h2_check");
+}
+
+int gca_h2_clear_status(const gca_h2* h) {
+  if (!h) {
+    gca::set_error("gca_h2_clear_status: NULL handle");
+    return GCA_ERR_INVALID_ARG;
+  }
+  GCA_TRY(gca::check_device(h->device, "gca_h2_clear_status"));
+  GCA_TRY_CUDA(cudaDeviceSynchronize());
+  GCA_TRY_CUDA(cudaMemset(h->d_status.p, 0, sizeof(int)));
+  return GCA_OK;
+}
+
+int gca_test_hook(const char* name, int64_t value) {
+  if (!name) {
+    gca::set_error("gca_test_hook: NULL name");
+    return GCA_ERR_INVALID_ARG;
+  }
+  const std::string n(name);
+  if (n == "wait_cycles") {
+    gca::g_wait_cycles = value > 0 ? (long long)value : gca::kDefaultWaitCycles;
+  } else if (n == "stall_chain") {
+    gca::g_stall_chain = value != 0 ? 1 : 0;
+  } else if (n == "fail_alloc") {
+    gca::g_fail_alloc = value > 0 ? (long long)value : 0;
+  } else if (n == "device_skew") {
+    gca::g_device_skew = (int)value;
+  } else {
+    gca::set_error("gca_test_hook: unknown hook " + n);
+    return GCA_ERR_INVALID_ARG;
+  }
+  return GCA_OK;
+}
+
 void gca_free(gca_h2* h) { delete h; }
 
 int gca_build_batch(int32_t count, const gca_mesh* meshes, const gca_tree* trees,
@@ -151,6 +258,7 @@ int gca_build_batch(int32_t count, const gca_mesh* meshes, const gca_tree* trees
       }
       b->h.push_back(h);
     }
+    b->device = b->h[0]->device;
     int st = b->d_status.alloc(sizeof(int));
     if (st != GCA_OK) return st;
     if (cudaMemset(b->d_status.p, 0, sizeof(int)) != cudaSuccess) {
@@ -208,6 +316,28 @@ int gca_batch_status(const gca_h2_batch* b, int32_t* status) {
     return GCA_ERR_CUDA;
   }
   *status = v;
+  return GCA_OK;
+}
+
+int gca_batch_check(const gca_h2_batch* b, void* stream) {
+  if (!b) {
+    gca::set_error("gca_batch_check: NULL batch");
+    return GCA_ERR_INVALID_ARG;
+  }
+  GCA_TRY(gca::check_device(b->device, "gca_batch_check"));
+  int bits = 0;
+  GCA_TRY(sync_status(b->d_status, stream, &bits));
+  return status_error(bits, "gca_batch_check");
+}
+
+int gca_batch_clear_status(const gca_h2_batch* b) {
+  if (!b) {
+    gca::set_error("gca_batch_clear_status: NULL batch");
+    return GCA_ERR_INVALID_ARG;
+  }
+  GCA_TRY(gca::check_device(b->device, "gca_batch_clear_status"));
+  GCA_TRY_CUDA(cudaDeviceSynchronize());
+  GCA_TRY_CUDA(cudaMemset(b->d_status.p, 0, sizeof(int)));
   return GCA_OK;
 }
 

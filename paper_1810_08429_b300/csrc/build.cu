@@ -628,6 +628,17 @@ int make_panels(gca_h2* h, DevMem& jobs_buf, std::vector<PanelJob>& host_jobs, c
   return GCA_OK;
 }
 
+// Panels of every stored block, synchronously (the imported handles, which
+// have no entry kernels to overlap with).
+int make_panels_sync(gca_h2* h, cudaStream_t st) {
+  DevMem jobs;
+  GCA_TRY(jobs.alloc(sizeof(PanelJob) * (size_t)std::max<int64_t>(panel_jobs(h), 1)));
+  std::vector<PanelJob> host_jobs;
+  GCA_TRY(make_panels(h, jobs, host_jobs, st));
+  GCA_TRY_CUDA(cudaStreamSynchronize(st));
+  return GCA_OK;
+}
+
 namespace {
 
 // ------------------------------------------------------ regular entries
@@ -1059,6 +1070,8 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     return GCA_ERR_INVALID_ARG;
   }
   auto h = std::make_unique<gca_h2>();
+  GCA_TRY_CUDA(cudaGetDevice(&h->device));
+  h->device += test_hooks().device_skew;
   h->params = *prm;
   h->n = mesh->nt;
   h->nv = mesh->nv;
@@ -1285,7 +1298,9 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      PhaseScope ps__("green_aca", st);
+      PhaseScope ps__(profile_detail() ? "green_aca.L" + std::to_string(L) + ".c" + std::to_string(C)
+                                       : std::string("green_aca"),
+                      st);
       GCA_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_aca, (const AcaJob*)dj, k, rows_cap, kw,
                                       (const int*)h->d_perm.as<int>(), (const P4*)d_tq.as<P4>(),
                                       (const P4*)d_zq.as<P4>(), d_piv.as<int>(), d_uscr.as<double>(),

@@ -39,6 +39,18 @@ std::string last_error();
     if (s__ != GCA_OK) return s__; \
   } while (0)
 
+// Test hooks (gca_test_hook, api.cu): settings that make failure paths
+// reachable without a GPU fault.  `alloc_should_fail` counts device
+// allocations and reports true for the one chosen by "fail_alloc".
+struct TestHooks {
+  long long wait_cycles;  // bound of every device-side wait of the products
+  int stall_chain;        // product dependency waits need one more completion than any plan gives
+  int device_skew;        // handles record (current device + skew) as their device
+};
+TestHooks test_hooks();
+bool alloc_should_fail();
+constexpr long long kDefaultWaitCycles = 1LL << 31;  // about a second at 2 GHz
+
 // Owning device allocation (cudaMalloc / cudaFree).
 struct DevMem {
   void* p = nullptr;
@@ -55,7 +67,7 @@ struct DevMem {
   int alloc(size_t nbytes) {
     release();
     if (nbytes == 0) nbytes = 16;
-    cudaError_t e = cudaMalloc(&p, nbytes);
+    cudaError_t e = alloc_should_fail() ? cudaErrorMemoryAllocation : cudaMalloc(&p, nbytes);
     if (e != cudaSuccess) {
       p = nullptr;
       set_error(std::string("cudaMalloc(") + std::to_string(nbytes) + "): " + cudaGetErrorString(e));
@@ -89,6 +101,10 @@ void block_tree(const std::vector<int>& child0, const std::vector<int>& child1,
                 const std::vector<double>& box, const std::vector<double>& diam, double eta,
                 std::vector<int>& far_t, std::vector<int>& far_s, std::vector<int>& near_t,
                 std::vector<int>& near_s);
+
+// Finer phase names requested (gca_profile_enable(2)): the build splits its
+// per-level phases by level and launch shape (profile.cu).
+bool profile_detail();
 
 // Event pair around a phase when profiling is enabled (profile.cu).
 class PhaseScope {
@@ -132,7 +148,14 @@ int alloc_panels(gca_h2* h);
 int64_t panel_jobs(const gca_h2* h);
 struct PanelJob;
 int make_panels(gca_h2* h, DevMem& jobs_buf, std::vector<PanelJob>& host_jobs, cudaStream_t st);
+int make_panels_sync(gca_h2* h, cudaStream_t st);
+// gca_h2_import (import.cpp)
+int import_h2(const gca_tree* tree, int32_t nt, int32_t nfar, int32_t nnear, const gca_host_dump* d,
+              uint32_t flags, cudaStream_t st, gca_h2** out);
 int product_status(const gca_h2* h, int* out);
+// GCA_OK when `device` is the current device, else INVALID_ARG with a message
+// naming both ordinals (the handle's memory would be another device's).
+int check_device(int device, const char* what);
 int prepare_batch(gca_h2_batch* b, cudaStream_t st);
 int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx, void* y,
                    int64_t ldy, cudaStream_t st);
@@ -230,6 +253,7 @@ struct gca_h2 {
   mutable gca::ProductCache pc;
   mutable gca::DevMem d_status;  // sticky error bits of the products
   int max_rows = 0;              // largest block dimension (bounds the staged X)
+  int device = -1;               // ordinal of the device that holds the handle's memory
 };
 
 // A batch of handles applied in one persistent launch.
@@ -237,6 +261,7 @@ struct gca_h2_batch {
   std::vector<gca_h2*> h;          // owned
   mutable gca::ProductCache pc;    // shared product workspace
   mutable gca::DevMem d_status;
+  int device = -1;                 // ordinal of the device that holds the batch
   ~gca_h2_batch() {
     for (auto* p : h) delete p;
   }

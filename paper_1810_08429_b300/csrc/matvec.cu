@@ -144,6 +144,8 @@ struct LaunchArgs {
   int* status;
   int* abort_flag;             // raised by any timed-out wait; every wait gives up
   const void* zeros;           // kZeroBytes of zeros (pads input blocks)
+  long long wait_cycles;       // bound of every wait, SM clock cycles
+  int wait_extra;              // added to every dependency count (0; 1 only in failure-path tests)
 };
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -177,8 +179,6 @@ constexpr int kStageBytes = kStagePanels * kItemRows * 16;  // 8 KB: one contigu
 constexpr int kStages = 2;
 constexpr int kDescSlots = 4;                               // records: chain 0, 1; free 2, 3
 constexpr size_t kZeroBytes = (size_t)kChunk * 16 * 8;      // a full input block of doubles
-// bound of every mbarrier wait, in SM clock cycles (about a second)
-constexpr long long kWaitCycles = 1LL << 31;
 // a waiting warp sleeps until the phase completes or this many ns pass
 constexpr unsigned kSuspendNs = 20000;
 
@@ -246,7 +246,7 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
 // poll.
 template <unsigned kMaxSleep = 128>
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile int* abort_flag,
-                                          int* status) {
+                                          int* status, long long wait_cycles) {
   if (mbar_try_wait(b, parity)) return true;
   const long long t0 = clock64();
   unsigned ns = 16;
@@ -256,7 +256,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity, volatile
     if (mbar_try_wait(b, parity)) return true;
     if ((it & 15) == 0) {
       if (*abort_flag) return false;
-      if (clock64() - t0 > kWaitCycles) break;
+      if (clock64() - t0 > wait_cycles) break;
     }
   }
   atomicOr(status, kStatusTimeout);
@@ -269,7 +269,7 @@ __device__ __forceinline__ void mbar_drain(uint64_t* b, unsigned parity) {
   const long long t0 = clock64();
   while (!mbar_try_wait(b, parity)) {
     __nanosleep(256);
-    if (clock64() - t0 > kWaitCycles) return;
+    if (clock64() - t0 > kDefaultWaitCycles) return;
   }
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
@@ -721,7 +721,7 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
     const int q = (int)(usig & 1);
     const unsigned par = (usig >> 1) & 1;
     if (block) {
-      if (!mbar_wait<512>(P.uempty(q), par, abort_flag, L.status)) {
+      if (!mbar_wait<512>(P.uempty(q), par, abort_flag, L.status, L.wait_cycles)) {
         ok = false;
         return false;
       }
@@ -751,7 +751,7 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
       if (mbar_try_wait(b, par)) return true;
       if ((it & 15) == 0) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > L.wait_cycles) {
           atomicOr(L.status, kStatusTimeout);
           *abort_flag = 1;
           return false;
@@ -804,7 +804,7 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
     pr.nseg = count_segs(pr.d, lane);
     const bool w = lane < pr.nseg && pr.d.wait_idx >= 0;
     bool nr = false;
-    if (w) nr = ld_acquire(sa.counters + pr.d.wait_idx) < pr.d.wait_cnt * sa.nchunk;
+    if (w) nr = ld_acquire(sa.counters + pr.d.wait_idx) < pr.d.wait_cnt * sa.nchunk + L.wait_extra;
     pr.notready = __ballot_sync(FULL, nr);
     pr.haswait = __ballot_sync(FULL, w);
     __syncwarp();
@@ -924,7 +924,7 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
         // flight, then wait for the input vector block to be complete
         while (p0 < np && stage_free_now()) issue_stage();
         const int widx = __shfl_sync(FULL, d.wait_idx, s);
-        const int need = __shfl_sync(FULL, d.wait_cnt, s) * sa.nchunk;
+        const int need = __shfl_sync(FULL, d.wait_cnt, s) * sa.nchunk + L.wait_extra;
         bool timeout = false;
         {
           const long long t0 = clock64();
@@ -943,7 +943,7 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
                 timeout = true;
                 break;
               }
-              if (clock64() - t0 > kWaitCycles) {
+              if (clock64() - t0 > L.wait_cycles) {
                 atomicOr(L.status, kStatusTimeout);
                 *abort_flag = 1;
                 timeout = true;
@@ -1057,7 +1057,7 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
       for (int e = 0; e < 4; ++e) accm[i][nt][e] = 0.f;
   while (true) {
     const int q = (int)(ucnt & 1);
-    if (!mbar_wait(P.ufull(q), (ucnt >> 1) & 1, abort_flag, L.status)) return;
+    if (!mbar_wait(P.ufull(q), (ucnt >> 1) & 1, abort_flag, L.status, L.wait_cycles)) return;
     const int4 msg = P.queue[q];
     ++ucnt;
     if (msg.x < 0) return;
@@ -1085,11 +1085,11 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
       const bool is_near = ain == kN || ain == kNt;
       const int np = kp / (is_near ? Panel<TN>::P : Panel<T>::P);
       const int j = (int)(xuse & 1);
-      if (!mbar_wait(P.xfull(j), (xuse >> 1) & 1, abort_flag, L.status)) return;
+      if (!mbar_wait(P.xfull(j), (xuse >> 1) & 1, abort_flag, L.status, L.wait_cycles)) return;
       const TA* Xs = P.xslot(j);  // padded with zero rows by the producer
       for (int p0 = 0; p0 < np; p0 += kStagePanels) {
         const int st = (int)(use % kStages);
-        if (!mbar_wait(P.full(st), (use / kStages) & 1, abort_flag, L.status)) return;
+        if (!mbar_wait(P.full(st), (use / kStages) & 1, abort_flag, L.status, L.wait_cycles)) return;
         const unsigned char* stg = P.ring + st * kStageBytes;
         const int npst = min(kStagePanels, np - p0);
         if constexpr (sizeof(T) == sizeof(TN)) {
@@ -1784,6 +1784,11 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   L.abort_flag = reinterpret_cast<int*>(base + 16);
   L.zeros = base + 256;
   L.status = status;
+  {
+    const TestHooks th = test_hooks();
+    L.wait_cycles = th.wait_cycles;
+    L.wait_extra = th.stall_chain;
+  }
   GCA_TRY_CUDA(cudaMemsetAsync(base, 0, zeroed, st));
   const unsigned gx = (unsigned)std::min<int64_t>(1024, (max_n + 255) / 256);
   k_gather<TV><<<dim3(std::max(1u, gx), count), 256, 0, st>>>(d_slots, pack, inline_slots ? 1 : 0);
@@ -1908,6 +1913,11 @@ int launch_any(const gca_h2* const* hs, int count, gca_prec prec, bool trans, co
   std::vector<const void*> xs(count);
   std::vector<void*> ys(count);
   for (int i = 0; i < count; ++i) {
+    if (!hs[i]) {
+      set_error("h2_matvec: NULL handle " + std::to_string(i));
+      return GCA_ERR_INVALID_ARG;
+    }
+    GCA_TRY(check_device(hs[i]->device, "h2_matvec"));
     if (!x_in[i] || !y_in[i]) {
       set_error("h2_matvec: invalid arguments (handle " + std::to_string(i) + ")");
       return GCA_ERR_INVALID_ARG;
@@ -2167,9 +2177,6 @@ int noalloc_scratch(unsigned char** out) {
   return GCA_OK;
 }
 
-template <typename TV>
-__global__ void k_put_slot(SlotArgs<TV> a, SlotArgs<TV>* dst) { *dst = a; }
-
 // h2_matvec's launch for one handle with the workspace carved out of `base`
 // (capacity `cap` bytes); nothing is allocated.
 template <typename T, typename TN, typename TA, typename TV, int RC>
@@ -2181,14 +2188,17 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   const size_t b_cnt = up256(sizeof(int) * 2 * (size_t)h->nc);
   const size_t o_xh = 256 + kZeroBytes, o_yh = o_xh + b_xh, o_yp = o_yh + b_xh, o_cnt = o_yp + b_yp;
   const size_t zeroed = o_cnt + b_cnt;
-  const size_t o_xp = zeroed, o_slot = o_xp + b_yp;
-  const size_t need = o_slot + up256(sizeof(SlotArgs<TV>));
+  const size_t o_xp = zeroed;
+  const size_t need = o_xp + b_yp;
   if (need > cap) {
     set_error("h2_matvec_noalloc: this product needs " + std::to_string(need) +
               " bytes of workspace, more than the " + std::to_string(cap) +
               "-byte scratch array (fewer right-hand sides or h2_matvec)");
     return GCA_ERR_UNSUPPORTED;
   }
+  const char* pn = sizeof(T) == 8 ? ".f64" : (sizeof(T) == 4 ? ".f32" : ".bf16");
+  PhaseScope ps(std::string("mv_persistent_noalloc") + pn, st);
+  ps.launches(3);
   SlotArgs<TV> a{};
   fill_slot<T, TN, TV>(a, h, 0, R, RC, x, ldx, y, ldy);
   a.xh = reinterpret_cast<TV*>(base + o_xh);
@@ -2197,7 +2207,7 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   a.counters = reinterpret_cast<int*>(base + o_cnt);
   a.xp = reinterpret_cast<TV*>(base + o_xp);
   LaunchArgs L;
-  L.slots = base + o_slot;
+  L.slots = nullptr;  // the descriptor travels inline as a kernel parameter
   L.nslots = 1;
   L.chain_map = nullptr;
   L.free_map = nullptr;
@@ -2208,19 +2218,23 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   L.abort_flag = reinterpret_cast<int*>(base + 16);
   L.zeros = base + 256;
   L.status = h->d_status.as<int>();
+  {
+    const TestHooks th = test_hooks();
+    L.wait_cycles = th.wait_cycles;
+    L.wait_extra = th.stall_chain;
+  }
   // the array keeps the previous call's contents: the claim counters, abort
   // flag, x-hat, y-hat, y and the counters must start at zero
   GCA_TRY_CUDA(cudaMemsetAsync(base, 0, zeroed, st));
-  // the descriptor travels as a kernel argument: no host buffer to keep alive
-  auto* d_slots = reinterpret_cast<SlotArgs<TV>*>(base + o_slot);
-  k_put_slot<TV><<<1, 1, 0, st>>>(a, d_slots);
+  // the descriptor travels as a kernel parameter: nothing to copy or keep alive
   const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, ((int64_t)h->n * R + 255) / 256));
   SlotPack<TV> pack;
   std::memset(&pack, 0, sizeof(pack));
-  k_gather<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots, pack, 0);
+  pack.s[0] = a;
+  k_gather<TV><<<dim3(gx, 1), 256, 0, st>>>(nullptr, pack, 1);
   if (L.total + L.total_free > 0)
     GCA_TRY((launch_persistent<T, TN, TA, TV, RC>(L, pack, L.total + L.total_free, st)));
-  k_scatter<TV><<<dim3(gx, 1), 256, 0, st>>>(d_slots, pack, 0);
+  k_scatter<TV><<<dim3(gx, 1), 256, 0, st>>>(nullptr, pack, 1);
   GCA_TRY_CUDA(cudaGetLastError());
   return GCA_OK;
 }
@@ -2246,6 +2260,7 @@ int matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, 
     set_error("h2_matvec_noalloc: invalid arguments");
     return GCA_ERR_INVALID_ARG;
   }
+  GCA_TRY(check_device(h->device, "h2_matvec_noalloc"));
   if (!has_precision(h, prec)) {
     set_error("h2_matvec_noalloc: the handle was built without this precision");
     return GCA_ERR_UNSUPPORTED;

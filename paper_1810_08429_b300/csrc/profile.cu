@@ -28,6 +28,7 @@ struct Pending {
 
 std::mutex g_mu;
 bool g_on = false;
+bool g_detail = false;
 std::vector<Pending> g_pending;
 std::map<std::string, std::pair<int64_t, double>> g_acc;  // launches, ms
 
@@ -46,6 +47,11 @@ void drain_locked() {
 }
 
 }  // namespace
+
+bool profile_detail() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_on && g_detail;
+}
 
 PhaseScope::PhaseScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -86,6 +92,23 @@ __global__ void k_fma_probe(T* out, int iters, T a, T b) {
   if (s == (T)-1.2345) out[0] = s;  // keep the chain alive
 }
 
+// The float32 chains as packed pairs (fma.rn.f32x2, the instruction of the
+// float product and entry kernels): 8 independent pair accumulators.
+__global__ void k_fma2_probe(float* out, int iters, float a, float b) {
+  float2 x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = make_float2((float)(threadIdx.x + j), (float)(threadIdx.x - j));
+  const float2 aa = make_float2(a, a), bb = make_float2(b, b);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = __ffma2_rn(x[j], aa, bb);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j].x + x[j].y;
+  if (s == -1.2345f) out[0] = s;  // keep the chain alive
+}
+
 template <typename T>
 double fma_probe_flops() {
   int dev = 0, sms = 0;
@@ -97,9 +120,16 @@ double fma_probe_flops() {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  k_fma_probe<T><<<blocks, threads>>>(out, 64, (T)0.999, (T)0.001);  // warm up
+  // float: packed pairs, two FMAs per instruction
+  auto run = [&](int it) {
+    if constexpr (sizeof(T) == 4)
+      k_fma2_probe<<<blocks, threads>>>(out, it, 0.999f, 0.001f);
+    else
+      k_fma_probe<T><<<blocks, threads>>>(out, it, (T)0.999, (T)0.001);
+  };
+  run(64);  // warm up
   cudaEventRecord(e0);
-  k_fma_probe<T><<<blocks, threads>>>(out, iters, (T)0.999, (T)0.001);
+  run(iters);
   cudaEventRecord(e1);
   cudaEventSynchronize(e1);
   float ms = 0.f;
@@ -107,7 +137,7 @@ double fma_probe_flops() {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(out);
-  const double flops = 2.0 * 8.0 * iters * (double)threads * blocks;
+  const double flops = 2.0 * 8.0 * (sizeof(T) == 4 ? 2.0 : 1.0) * iters * (double)threads * blocks;
   return ms > 0.f ? flops / (ms * 1e-3) : 0.0;
 }
 
@@ -120,6 +150,7 @@ extern "C" {
 int gca_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(gca::g_mu);
   gca::g_on = on != 0;
+  gca::g_detail = on >= 2;
   return GCA_OK;
 }
 

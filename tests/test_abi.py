@@ -126,3 +126,48 @@ def test_invalid_input_rejected_on_host():
     with pytest.raises(gca.GCAError):
         gca.tree_build(v, bad, 8)
     assert "vertex id" in gca.lib.gca_last_error().decode()
+
+
+def test_import_rejects_inconsistent_representation_on_host():
+    """gca_h2_import validates the tree, ranks, pivots and block lists before
+    any device work (so this runs without a GPU)."""
+    from oracle import gca as ogca
+    from oracle.params import Params as OParams
+    from oracle_dump import oracle_dump
+    v, t = synth.mesh_for_config("sphere320")
+    h2o = ogca.build_h2(v, t, OParams(leaf_size=16, eta=2.0, box_gauss_m=3, aca_tol=1e-6, sauter_q=5))
+    good = oracle_dump(h2o)
+    tree = h2o.tree
+
+    def status_of(rep):
+        with pytest.raises(gca.GCAError) as e:
+            gca.import_h2(tree, len(t), rep)
+        return e.value.status, str(e.value)
+
+    bad = dict(good, rank=good["rank"].copy())
+    bad["rank"][0] = 3
+    assert status_of(bad)[0] == gca.ERR_INVALID_ARG
+    leaf = int(np.nonzero(tree["child0"] < 0)[0][0])
+    bad = dict(good, rank=good["rank"].copy())
+    bad["rank"][leaf] = tree["end"][leaf] - tree["begin"][leaf] + 1
+    assert "rank of cluster" in status_of(bad)[1]
+    bad = dict(good, near=good["near"].copy())
+    bad["near"][0, 0] = 0  # the root is not a leaf
+    assert "near-field block" in status_of(bad)[1]
+    bad = dict(good, far=good["far"].copy())
+    bad["far"][0, 1] = len(tree["begin"])
+    assert "coupling block" in status_of(bad)[1]
+    bad = dict(good, pivots=good["pivots"].copy())
+    bad["pivots"][0] = len(t)
+    assert "pivot" in status_of(bad)[1]
+    bad = dict(good, S=good["S"].copy())
+    bad["S"][0] = np.nan
+    assert status_of(bad)[0] == gca.ERR_NUMERIC
+
+
+def test_test_hooks_reject_unknown_names():
+    with pytest.raises(gca.GCAError) as e:
+        gca.test_hook("no_such_hook", 1)
+    assert e.value.status == gca.ERR_INVALID_ARG
+    for name in ("wait_cycles", "stall_chain", "fail_alloc", "device_skew"):
+        gca.test_hook(name, 0)

@@ -97,3 +97,28 @@ def test_invalid_arguments(setup):
                                      ctypes.c_void_p(y.data_ptr()), n, null) == -1
     assert gca.lib.h2_matvec_noalloc(h._h, 0, 1, ctypes.c_void_p(x.data_ptr()), n - 1,
                                      ctypes.c_void_p(y.data_ptr()), n, null) == -1
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_allocates_no_device_memory(setup, prec):
+    """The point of the entry point: a product on a handle that never ran an
+    allocating product leaves the device's free memory unchanged.  A first
+    call on another handle loads the kernels (lazy module loading may place
+    code in device memory); the measured call is on a fresh handle."""
+    gca, h = setup
+    dt = torch.float64 if prec == "f64" else torch.float32
+    n = h.n
+    x = _colmajor(synth.uniform_rhs(n, 4, seed=21), dt)
+    y = torch.empty((4, n), dtype=dt, device="cuda").t()
+    assert _noalloc(gca, h, prec, x, y) == 0
+    v, t = synth.mesh_for_config("sphere1280")
+    fresh = gca.build(v, t, gca.tree_build(v, t, 32),
+                      gca.Params(leaf_size=32, eta=2.0, box_gauss_m=3, aca_tol=1e-6, sauter_q=5))
+    y2 = torch.empty((4, n), dtype=dt, device="cuda").t()
+    torch.cuda.synchronize()
+    before = torch.cuda.mem_get_info()[0]
+    assert _noalloc(gca, fresh, prec, x, y2) == 0
+    torch.cuda.synchronize()
+    after = torch.cuda.mem_get_info()[0]
+    assert after == before
+    assert _rel(y2, h.matvec(x, prec)).max() <= TOL[prec]
