@@ -73,16 +73,22 @@ FLOPS_PER_GREEN_EVAL = 20
 
 
 def green_aca_flops(tree, rank, k):
-    """FP64 work of the Green-matrix + ACA phase: 7 k rows evaluations per
-    cluster (rows = |tau-hat| at leaves, r_1 + r_2 above), the rank-one
-    updates of the rows x 2k residual (2 rows 2k flops per pivot) and the
-    triangular solve for V-hat (rows r^2)."""
+    """FP64 work of the Green-matrix + ACA phase, per cluster with a basis:
+    7 k rows evaluations of the Green matrix (rows = |tau-hat| at leaves,
+    r_1 + r_2 above) and, after pivot t, the rank-one update of the residual
+    over the rows and columns not yet eliminated, 2 (rows - t - 1)
+    (2k - t - 1) flops, plus the update of the interpolation matrix V^ on
+    the same rows, 2 (rows - t - 1) t flops (V^ = U L^-1 kept current)."""
     c0, c1 = tree["child0"], tree["child1"]
     total = 0
     for c in range(1, len(c0)):
-        rows = int(tree["end"][c] - tree["begin"][c]) if c0[c] < 0 else int(rank[c0[c]] + rank[c1[c]])
         r = int(rank[c])
-        total += FLOPS_PER_GREEN_EVAL * 7 * k * rows + 2 * rows * 2 * k * r + rows * r * r
+        if r == 0:
+            continue
+        rows = int(tree["end"][c] - tree["begin"][c]) if c0[c] < 0 else int(rank[c0[c]] + rank[c1[c]])
+        t = np.arange(r)
+        act = rows - t - 1
+        total += FLOPS_PER_GREEN_EVAL * 7 * k * rows + int(np.sum(2 * act * (2 * k - t - 1) + 2 * act * t))
     return int(total)
 
 
@@ -209,31 +215,96 @@ def blas_threads():
         info = threadpool_info()
         return max([i.get("num_threads", 1) for i in info] + [1])
     except Exception:
-        return os.cpu_count() or 1
+        env = os.environ.get("OMP_NUM_THREADS") or os.environ.get("OPENBLAS_NUM_THREADS")
+        return int(env) if env and env.isdigit() else (os.cpu_count() or 1)
 
 
-def oracle_sample(mesh="sphere1280", reps=5):
-    """The oracle on a bounded sample: its own GCA-H^2 of a smaller sphere with
-    the workload's parameters, then timed float64 products with 16 RHS."""
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def kernel_evals(tree, rank, k, n_entries, n_singular, s_entries, q):
+    """Kernel evaluations of a GCA-H^2 construction, the build's unit of work:
+    7 k per row of every Green matrix (g and dg/dn share one distance; rows =
+    |tau-hat| at leaves, r_1 + r_2 above, for every cluster with a basis),
+    49 per coupling entry and per disjoint near entry, and the Sauter-Schwab
+    points of every touching entry (q^3 per region: the integral over the
+    radial variable of each Sauter-Schwab region is exact, 1/3; 2, 5, 6
+    regions for a common vertex, a common edge, identical triangles)."""
+    c0, c1 = tree["child0"], tree["child1"]
+    green = 0
+    for c in range(1, len(c0)):
+        if rank[c] == 0:
+            continue
+        rows = int(tree["end"][c] - tree["begin"][c]) if c0[c] < 0 else int(rank[c0[c]] + rank[c1[c]])
+        green += 7 * k * rows
+    regular = 49 * (int(s_entries) + int(n_entries - sum(n_singular[1:])))
+    singular = q ** 3 * (2 * n_singular[1] + 5 * n_singular[2] + 6 * n_singular[3])
+    return int(green + regular + singular)
+
+
+def oracle_leg(mesh="sphere1280", reps=5):
+    """One timing of the oracle on a bounded sample (run in a child process
+    whose BLAS thread count the parent sets): its own GCA-H^2 of a smaller
+    sphere with the workload's parameters, then float64 products with 16
+    RHS.  Returns build and product seconds, bytes and kernel evaluations."""
     from oracle import gca as ogca, h2 as oh2
+    from oracle.galerkin import shared_vertices
     from oracle.params import Params as OParams
     v, t = synth.mesh_for_config(mesh)
     p = OParams(**PARAMS)
+    x = synth.normal_rhs(len(t), NRHS, seed=0)
     t0 = time.perf_counter()
     H = ogca.build_h2(v, t, p)
     tb = time.perf_counter() - t0
-    st = oh2.storage(H)
-    x = synth.normal_rhs(len(t), NRHS, seed=0)
     oh2.matvec(H, x)
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
         oh2.matvec(H, x)
         times.append(time.perf_counter() - t0)
+    st = oh2.storage(H)
     byt = 8 * st["total"] + 2 * 8 * len(t) * NRHS
-    return {"gbs": byt / statistics.median(times) / 1e9, "build_s": tb,
-            "matvec_s": statistics.median(times), "n": len(t), "mesh": mesh,
-            "cores": blas_threads()}
+    ii, jj = [], []
+    for (tt, ss) in H.near:
+        a = H.tree["perm"][H.tree["begin"][tt]:H.tree["end"][tt]]
+        b = H.tree["perm"][H.tree["begin"][ss]:H.tree["end"][ss]]
+        ii.append(np.repeat(a, len(b)))
+        jj.append(np.tile(b, len(a)))
+    sv = shared_vertices(np.asarray(t), np.concatenate(ii), np.concatenate(jj))
+    nsing = [int(np.sum(sv == c)) for c in range(4)]
+    evals = kernel_evals(H.tree, H.bases.rank, 6 * p.box_gauss_m ** 2, st["N"], nsing, st["S"], p.sauter_q)
+    return {"build_s": tb, "matvec_s": statistics.median(times), "bytes": byt, "evals": evals,
+            "n": len(t), "mesh": mesh, "threads": blas_threads()}
+
+
+def oracle_sample():
+    """The oracle timed on one thread (BLAS and OpenMP limited to 1 in a child
+    process) and on all of the host's cores (a child process with the
+    library defaults)."""
+    out = {"cores": os.cpu_count() or 1, "cpu_model": cpu_model()}
+    for label, limit in (("single_thread", "1"), ("all_cores", None)):
+        env = dict(os.environ)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            if limit:
+                env[var] = limit
+            else:
+                env.pop(var, None)
+        res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg"], env=env,
+                             capture_output=True, text=True, check=True)
+        leg = json.loads(res.stdout.strip().splitlines()[-1])
+        leg["gbs"] = leg["bytes"] / leg["matvec_s"] / 1e9
+        leg["build_evals_per_s"] = leg["evals"] / leg["build_s"]
+        out[label] = leg
+    out["n"] = out["all_cores"]["n"]
+    out["build_kernel_evals"] = out["all_cores"]["evals"]
+    return out
 
 
 def run_reference(args):
@@ -258,13 +329,15 @@ def run_reference(args):
     value = byt / dt / 1e9
     sample = (f"oracle float64 H2 product, 16 RHS, on its own GCA-H2 of the {len(t)}-triangle "
               f"sphere built with the workload's parameters (build not timed)")
+    threads = blas_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config({"sample_mesh": mesh}),
-            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": blas_threads(),
-                             "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads,
+                             "kind": "oracle", "sample": sample, "cpu_model": cpu_model(),
+                             "host_cores": os.cpu_count()},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -295,6 +368,76 @@ def run_profile(args):
     print(json.dumps({"profile": args.profile, "n": len(t), "status": h.status()}), flush=True)
 
 
+def time_products(fn, K, W, stream):
+    """Median device time (ms) of fn() over K runs after W warm-ups, CUDA
+    events on the launching stream."""
+    import torch
+    for _ in range(W):
+        fn()
+    ts = []
+    for _ in range(K):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def leg_errors(ys, ref):
+    """Largest relative 2-norm error per right-hand side against `ref`."""
+    return max(float(((y.double() - r).norm(dim=0) / r.norm(dim=0)).max()) for y, r in zip(ys, ref))
+
+
+def run_legs(gca, batch, meshes, stats, n, args, dev, stream, hbm_peak):
+    """Products outside the step: R = 1 and R = 4 on the bench's two meshes
+    (float32, bfloat16; where the product streams the blocks with little
+    arithmetic per byte), and the 81920-triangle sphere with 64 right-hand
+    sides in float64, float32 and bfloat16 (built with the bench parameters).
+    Each: median of K products after W warm-ups, algorithmic GB/s, fraction
+    of HBM, error against the float64 product of the same right-hand sides."""
+    import torch
+    K, W = max(args.steps, 3), max(args.warmup, 3)
+    legs = {}
+    for R in (1, 4):
+        x64 = [torch.from_numpy(synth.normal_rhs(len(t), R, seed=R)).to(dev) for _, t in meshes]
+        x32 = [x.float() for x in x64]
+        ref = batch.matvec(x64, "f64")
+        for prec in ("f32", "bf16"):
+            outs = [torch.empty((R, len(t)), dtype=torch.float32, device=dev).t() for _, t in meshes]
+            ms = time_products(lambda: batch.matvec(x32, prec, outs=outs), K, W, stream)
+            byt = sum(product_bytes(s, prec, n, R) for s in stats)
+            legs[f"{prec}.R{R}"] = {"GB/s": byt / ms / 1e6, "frac_hbm": byt / ms / 1e6 / hbm_peak,
+                                    "us_both_meshes": ms * 1e3, "err_vs_f64": leg_errors(outs, ref)}
+    v, t = synth.mesh_for_config("sphere81920")
+    tree = gca.tree_build(v, t, PARAMS["leaf_size"])
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    h = gca.build(v, t, tree, gca.Params(**PARAMS, flags=gca.DROP_EXPORT))
+    b.record(stream)
+    b.synchronize()
+    st = h.stats()
+    R = 64
+    x64 = torch.from_numpy(synth.normal_rhs(len(t), R, seed=0)).to(dev)
+    x32 = x64.float()
+    y64 = torch.empty((R, len(t)), dtype=torch.float64, device=dev).t()
+    cfg3 = {"workload": "sphere81920, leaf 64, eta 2, m 4, tol 1e-8, 64 RHS N(0,1)",
+            "build_s": a.elapsed_time(b) * 1e-3}
+    for prec in ("f64", "f32", "bf16"):
+        xin = x64 if prec == "f64" else x32
+        out = y64 if prec == "f64" else torch.empty((R, len(t)), dtype=torch.float32, device=dev).t()
+        ms = time_products(lambda: h.matvec(xin, prec, out=out), K, W, stream)
+        byt = product_bytes(st, prec, len(t), R)
+        cfg3[prec] = {"GB/s": byt / ms / 1e6, "frac_hbm": byt / ms / 1e6 / hbm_peak, "ms": ms,
+                      "err_vs_f64": 0.0 if prec == "f64" else leg_errors([out], [y64])}
+    h.check()
+    legs["sphere81920.R64"] = cfg3
+    return legs
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,9 +445,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile", choices=["f64", "f32", "bf16", "build"], default=None,
                     help="run the small single-mesh case used for kernel captures")
     args = ap.parse_args()
+    if args.oracle_leg:
+        print(json.dumps(oracle_leg()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -368,7 +515,10 @@ def main():
     for _ in range(args.warmup):
         hs = step(False)
     stats = [h.stats() for h in hs]
-    aca_flops = [green_aca_flops(tr, h.export()["rank"], s["k"]) for tr, h, s in zip(trees, hs, stats)]
+    ranks = [h.export(("rank",))["rank"] for h in hs]
+    aca_flops = [green_aca_flops(tr, r, s["k"]) for tr, r, s in zip(trees, ranks, stats)]
+    gpu_evals = sum(kernel_evals(tr, r, s["k"], s["n_entries"], s["n_singular"], s["s_entries"],
+                                 PARAMS["sauter_q"]) for tr, r, s in zip(trees, ranks, stats))
     fp64_peak, fp32_peak = gca.peak_probe()
     torch.cuda.synchronize()
 
@@ -482,24 +632,44 @@ def main():
 
     launches_per_step = sum(l for (l, _) in phases.values()) / K
 
+    # the other product legs: few right-hand sides on the same two meshes, and
+    # the 81920-triangle precision configuration (64 right-hand sides)
+    with ClockSampler(local) as clocks_legs:
+        legs = run_legs(gca, batch, meshes, stats, n, args, dev, stream, hbm_peak)
+    legs["clocks"] = clocks_legs.summary()
+
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline:
         o = oracle_sample()
-        cpu = {"value": o["gbs"], "unit": "GB/s", "cores": o["cores"], "kind": "oracle",
+        allc, one = o["all_cores"], o["single_thread"]
+        cpu = {"value": allc["gbs"], "unit": "GB/s", "cores": allc["threads"], "kind": "oracle",
                "sample": (f"oracle float64 H2 product (16 RHS) on its own GCA-H2 of the "
                           f"{o['n']}-triangle sphere built with the workload's parameters; "
-                          f"oracle build {o['build_s']:.1f} s, product {o['matvec_s']*1e3:.0f} ms")}
+                          f"timed on all cores ({allc['threads']} BLAS threads) and on one thread"),
+               "cpu_model": o["cpu_model"], "host_cores": o["cores"],
+               "single_thread": {"value": one["gbs"], "unit": "GB/s", "cores": 1,
+                                 "build_s": one["build_s"],
+                                 "build_evals_per_s": one["build_evals_per_s"]},
+               "all_cores": {"value": allc["gbs"], "unit": "GB/s", "cores": allc["threads"],
+                             "build_s": allc["build_s"],
+                             "build_evals_per_s": allc["build_evals_per_s"]},
+               "build_kernel_evals": o["build_kernel_evals"],
+               "build_unit": "kernel evaluations (7 k per Green-matrix row, 49 per regular entry, "
+                             "q^3 per Sauter-Schwab region)"}
     line = {
         "metric": METRIC, "value": gbs["f32"] * world, "unit": "GB/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": total_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config({"parallelism": f"replicas{world}"}),
         "build_s": agg["build"] / K * 1e-3,
+        "build_evals_per_s": gpu_evals / (agg["build"] / K * 1e-3),
+        "build_kernel_evals": gpu_evals,
         "matvec": {p: {"GB/s": gbs[p], "frac_hbm": gbs[p] / hbm_peak,
                        "ms_both_meshes": agg[p] / K} for p in gbs},
         "err_vs_f64": errs,
+        "matvec_legs": legs,
         "roofline": roofline_for(dom),
         "roofline_matvec": roofline_for(mv_dom),
         "peaks": {"hbm_gbs": hbm_peak, "hbm_kind": peak_kind, "fp64_tflops": fp64_peak / 1e12,

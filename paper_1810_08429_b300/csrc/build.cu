@@ -180,99 +180,195 @@ struct AcaJob {
   int rmax;       // min(rows, 2k)
   int tbegin;     // leaf: first position in perm
   int r0;         // non-leaf: rank of child0 (its pivots come first)
-  int r1;
+  int mesh;       // entry of the launch's mesh table
   int pad;
   int64_t piv0;   // non-leaf: pivot pool offsets of the children
   int64_t piv1;
-  int64_t m_off;  // matrix offset in global scratch (when not in shared memory)
-  int64_t u_off;  // column factors U (rows x rmax, column-major) in scratch
-  int64_t vh_off; // V^ (rows x r, row-major) in the V^ pool
-  int64_t p_off;  // this cluster's pivots in the pivot pool
+  int64_t vh_off; // V^ (rows x r, row-major) in the mesh's V^ pool
+  int64_t p_off;  // this cluster's pivots in the mesh's pivot pool
   double diam;    // d_tau
 };
 
-// Cross approximation of one job on a thread-block cluster of C CTAs
-// (C = 1 for small jobs).  CTA q owns the box points nu in [q kw, q kw + kw)
-// and keeps both of their columns of A^ (nu: g-column, nu + k: dg-column)
-// in shared memory, column-major.  One ACA step (Sect. 3):
-//   1. apply the previous rank-one update (one FMA per entry) while taking
-//      the largest |entry| as an IEEE bit pattern (integer max is exact for
-//      non-negative doubles and keeps the slow FP64 pipe free);
-//   2. cluster max -> stopping rule; threshold max (1 - tie);
-//   3. smallest column-major global index at or above the threshold
-//      (columns of a CTA are in increasing global order, so the first hit of
-//      each thread's strided sweep is its minimum) -> cluster min;
-//   4. the owner of the pivot column forms u = R[:, j*] / p, writes it to the
-//      U scratch and the other CTAs copy it through distributed shared memory;
-//      every CTA keeps its slice of the pivot row as v.
-// Afterwards V^ = U L^{-1} (L = U[P, :], unit lower triangular) is solved
-// row by row, the rows spread over the cluster.
-// doubles of the matrix region of k_aca's shared memory: the CTA's columns
-// of A^ during the cross approximation, then one row of V^ per warp (r <=
-// rows) during the triangular solve
-__host__ __device__ constexpr size_t aca_s_doubles(int rows_cap, int kw_cap) {
-  return (size_t)rows_cap * 2 * kw_cap > (size_t)(kAcaThreads / 32) * rows_cap
-             ? (size_t)rows_cap * 2 * kw_cap
-             : (size_t)(kAcaThreads / 32) * rows_cap;
-}
+// Per-mesh arrays of an ACA launch (one launch may serve several meshes).
+struct AcaMesh {
+  const int* perm;
+  const P4* tq;
+  const P4* zq;
+  int* piv_pool;
+  double* vh_pool;
+  int* rank_out;
+};
 
+// Cross approximation of one job on a thread-block cluster of C CTAs (C = 1
+// for small jobs).  CTA q owns the rows [q rpc, (q + 1) rpc) of A^ with all
+// 2k columns (nu: g-column, nu + k: dg-column), row-major in shared memory,
+// and the same rows of the interpolation matrix V^.  One step of the cross
+// approximation with complete pivoting (Sect. 3):
+//   1. the rank-one update R <- R - u v^T of the residual and the update of
+//      V^ below, over the rows and columns not yet eliminated;
+//   2. the CTA's largest |R| (IEEE bit patterns: an integer max is exact for
+//      non-negative doubles) and, among its entries within the tie window of
+//      that maximum, the smallest column-major index (column, then row);
+//   3. the CTA posts maximum, candidate and the candidate's residual row and
+//      V^ row into a double-buffered slot of its shared memory; one cluster
+//      barrier;
+//   4. every CTA reads all posts through distributed shared memory: the
+//      cluster maximum (stopping rule), the tie threshold and the winning
+//      candidate, whose posted rows give the pivot row v and w = V^[i*, :].
+//      The entries of a CTA within the cluster's tie window are a subset of
+//      those within its own, so its posted candidate is its answer whenever
+//      the candidate itself lies in the cluster's window; otherwise (a near
+//      tie straddling two CTAs' windows) one more round rescans at the
+//      cluster's threshold;
+//   5. u = R[:, j*] / p for the CTA's rows still in play; the pivot row and
+//      column leave the active region (swapped to its end, with the maps
+//      from storage positions to row and column indices of A^).
+// The pivot row and column of the residual are zero after their step (up to
+// rounding in an implementation that keeps updating them), so they never
+// hold a later pivot: the update skips them, which roughly halves its
+// float64 work.  V^ = A^[:, Q] A^[P, Q]^{-1} = U L^{-1} is kept up to date
+// instead of being solved at the end: with pivot row i* and u = R[:, j*] / p,
+//   V^ <- [V^ - u V^[i*, :], u],
+// since the new unit lower triangular factor's inverse adds the row
+// -U[i*, :] L^{-1} = -V^[i*, :]; so V^[P, :] = I exactly, and a pivot row's
+// V^ row is final when it leaves the active region.
+constexpr int kAcaPosts = 3;   // two alternating posts per step, one for rescans
 constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+struct AcaPost {
+  unsigned long long maxbits;  // the CTA's largest |R|
+  unsigned long long candbits; // |R| of its candidate
+  int key;                     // candidate's column-major index j * rows + i in A^ (INT_MAX: none)
+  int tri;                     // candidate row's triangle id
+  double pval;                 // candidate's signed value
+  int cslot;                   // candidate's column storage position (the same in every CTA)
+  int rslot;                   // candidate's row storage position in the posting CTA
+  int bad;                     // the candidate could not be certified (rescan)
+  int pad;
+};
+constexpr int kAcaMaxCluster = 16;
+
+// candidate rows posted by a CTA (residual row, then V^ row); the headers go
+// to every CTA of the cluster
+__host__ __device__ constexpr size_t aca_post_doubles(int k2, int rmax_cap) {
+  return (size_t)k2 + (size_t)rmax_cap;
+}
+
+// Summary of a set of residual entries for complete pivoting with a tie
+// window: its largest |R| (bits m), and the smallest key k among its entries
+// with |R| >= m (1 - tie), with that entry's |R| (bits v).  For any threshold
+// T >= m (1 - tie) the set's entries at or above T are a subset of those at
+// its own window, so k is their smallest key whenever v >= T; otherwise the
+// summary cannot answer (bad) and the entries are scanned again.  Merging two
+// summaries applies this to both sides at the merged window.
+struct Cand {
+  unsigned long long m, k, v;
+  int bad;
+};
+__device__ __forceinline__ unsigned long long tie_bits(unsigned long long m, double keep) {
+  return m > kInfBits ? m : (unsigned long long)__double_as_longlong(__longlong_as_double((long long)m) * keep);
+}
+__device__ __forceinline__ Cand cand_merge(const Cand& a, const Cand& b, double keep) {
+  Cand o;
+  o.m = a.m > b.m ? a.m : b.m;
+  o.k = ~0ull;
+  o.v = 0;
+  o.bad = 0;
+  const unsigned long long thr = tie_bits(o.m, keep);
+  if (a.m >= thr) {
+    if (a.bad || a.v < thr) o.bad = 1;
+    else if (a.k < o.k) { o.k = a.k; o.v = a.v; }
+  }
+  if (b.m >= thr) {
+    if (b.bad || b.v < thr) o.bad = 1;
+    else if (b.k < o.k) { o.k = b.k; o.v = b.v; }
+  }
+  return o;
+}
+__device__ __forceinline__ Cand cand_shfl(const Cand& a, int off) {
+  Cand o;
+  o.m = __shfl_xor_sync(0xffffffffu, a.m, off);
+  o.k = __shfl_xor_sync(0xffffffffu, a.k, off);
+  o.v = __shfl_xor_sync(0xffffffffu, a.v, off);
+  o.bad = __shfl_xor_sync(0xffffffffu, a.bad, off);
+  return o;
+}
+
+// shared memory of one CTA: residual rows, V^ rows, posts, u, v, w, the rows'
+// triangles and indices, the columns' indices and the pivots' triangles
+__host__ __device__ constexpr size_t aca_smem_bytes(int rpc_cap, int k2, int rmax_cap) {
+  return sizeof(double) * ((size_t)rpc_cap * k2 + (size_t)rpc_cap * rmax_cap +
+                           kAcaPosts * aca_post_doubles(k2, rmax_cap) + rpc_cap + k2 + rmax_cap) +
+         sizeof(int) * (2 * (size_t)rpc_cap + k2 + rmax_cap);
+}
+
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
   for (int off = 16; off; off >>= 1) {
     const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
-    v = o > v ? o : v;
+    v = o < v ? o : v;
   }
   return v;
 }
-__device__ __forceinline__ int warp_min_int(int v) {
-  for (int off = 16; off; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
-  return v;
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & kAbsMask;
 }
 
+// LC: columns of a lane in the row updates (2k <= 32 LC)
+template <int LC>
 __global__ void __launch_bounds__(kAcaThreads)
-k_aca(const AcaJob* __restrict__ jobs, int k, int rows_cap, int kw_cap, const int* __restrict__ perm,
-      const P4* __restrict__ tq, const P4* __restrict__ zq, int* __restrict__ piv_pool,
-      double* __restrict__ uscratch, double* __restrict__ vh_pool, int* __restrict__ rank_out,
+k_aca(const AcaJob* __restrict__ jobs, const AcaMesh* __restrict__ meshes, int k, int rpc_cap, int rmax_cap,
       double tol, double tie, int* __restrict__ status) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int q = (int)cluster.block_rank();
   const AcaJob job = jobs[blockIdx.x / C];
-  const int rows = job.rows;
-  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5;
-  const int kw = (k + C - 1) / C;
-  const int nu0 = q * kw;
-  const int nk = max(0, min(kw, k - nu0));  // box points of this CTA
-  const int ncol = 2 * nk;
+  const AcaMesh M = meshes[job.mesh];
+  const int rows = job.rows, k2 = 2 * k;
+  const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, wid = tid >> 5, nwarps = nth >> 5;
+  const int rpc = (rows + C - 1) / C;
+  const int row0 = q * rpc;
+  const int nr = max(0, min(rpc, rows - row0));  // rows of this CTA
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* S = reinterpret_cast<double*>(smem_raw);                  // rows_cap x 2 kw_cap
-  double* s_u = S + aca_s_doubles(rows_cap, kw_cap);                  // rows_cap
-  double* s_v = s_u + rows_cap;                                       // 2 kw_cap
-  int* s_rows = reinterpret_cast<int*>(s_v + 2 * kw_cap);             // rows_cap
-  int* s_prow = s_rows + rows_cap;                                    // rows_cap
-  __shared__ unsigned long long s_wmax[32];
-  __shared__ int s_wmin[32];
-  __shared__ unsigned long long s_max;  // cluster visible
-  __shared__ int s_idx;                 // cluster visible
+  double* S = reinterpret_cast<double*>(smem_raw);            // nr x k2, row-major (storage order)
+  double* W = S + (size_t)rpc_cap * k2;                       // nr x rmax, row-major: V^
+  double* posts = W + (size_t)rpc_cap * rmax_cap;             // kAcaPosts x post
+  double* s_u = posts + kAcaPosts * aca_post_doubles(k2, rmax_cap);  // rpc_cap
+  double* s_v = s_u + rpc_cap;                                // k2
+  double* s_w = s_v + k2;                                     // rmax_cap
+  int* s_tri = reinterpret_cast<int*>(s_w + rmax_cap);         // rpc_cap: triangle of each stored row
+  int* s_rid = s_tri + rpc_cap;                               // rpc_cap: row of A^ of each stored row
+  int* s_cid = s_rid + rpc_cap;                               // k2: column of A^ of each stored column
+  int* s_ptri = s_cid + k2;                                   // rmax_cap: pivots' triangles
+  __shared__ unsigned long long s_red[32];
+  __shared__ unsigned long long s_bcast;
+  __shared__ Cand s_cand[32];
+  __shared__ AcaPost s_hdr[kAcaPosts][kAcaMaxCluster];  // every CTA's header, pushed by its owner
+  const size_t post_stride = aca_post_doubles(k2, rmax_cap);
+  auto post_row = [&](double* base, int b) { return base + b * post_stride; };
+  const double keep = 1.0 - tie;
 
-  for (int i = tid; i < rows; i += nth)
-    s_rows[i] = job.leaf ? perm[job.tbegin + i]
-                         : (i < job.r0 ? piv_pool[job.piv0 + i] : piv_pool[job.piv1 + (i - job.r0)]);
+  for (int i = tid; i < nr; i += nth) {
+    const int g = row0 + i;
+    s_tri[i] = job.leaf ? M.perm[job.tbegin + g]
+                        : (g < job.r0 ? M.piv_pool[job.piv0 + g] : M.piv_pool[job.piv1 + (g - job.r0)]);
+    s_rid[i] = g;
+  }
+  for (int c = tid; c < k2; c += nth) s_cid[c] = c;
   __syncthreads();
 
-  // this CTA's columns of A^: nu (g) and nu + k (dg) for its box points
-  const P4* z = zq + (int64_t)job.c * k;
+  // own rows of A^ (Sect. 2): columns nu (g) and nu + k (dg) for every box point
+  const P4* z = M.zq + (int64_t)job.c * k;
   const int m2 = k / 6;
-  for (int idx = tid; idx < rows * nk; idx += nth) {
-    const int i = idx % rows, a = idx / rows, nu = nu0 + a;
+  for (int idx = tid; idx < nr * k; idx += nth) {
+    const int i = idx / k, nu = idx - i * k;
     const P4 zz = z[nu];
     const int face = nu / m2, d = face >> 1;
     const double sgn = (face & 1) ? 1.0 : -1.0;
-    const P4* xq = tq + 7 * (int64_t)s_rows[i];
+    const P4* xq = M.tq + 7 * (int64_t)s_tri[i];
     double gs = 0.0, ds = 0.0;
 #pragma unroll
     for (int qq = 0; qq < 7; ++qq) {
@@ -283,56 +379,255 @@ k_aca(const AcaJob* __restrict__ jobs, int k, int rows_cap, int kw_cap, const in
       gs += x.w * ir;
       ds += x.w * dn * ir * ir * ir;
     }
-    S[(int64_t)a * rows + i] = zz.w * gs * kInv4Pi;
-    S[(int64_t)(nk + a) * rows + i] = -job.diam * zz.w * ds * kInv4Pi;
+    S[(int64_t)i * k2 + nu] = zz.w * gs * kInv4Pi;
+    S[(int64_t)i * k2 + k + nu] = -job.diam * zz.w * ds * kInv4Pi;
   }
   __syncthreads();
 
-  const int total = rows * ncol;
-  double* U = uscratch + job.u_off;
-  int r = 0;
-  double first = 0.0;
-  bool have_update = false;
-  // (row, column) of a thread's entries idx = tid + nth m, advanced without
-  // division: idx -> idx + nth moves the row by di and the column by dj
-  const int i_first = tid % rows, j_first = tid / rows;
-  const int di = nth % rows, dj = nth / rows;
-  for (;;) {
-    // 1. update + local max of |R| (bit patterns)
-    unsigned long long lmax = 0;
-    if (have_update) {
-      int i = i_first, jj = j_first;
-      for (int idx = tid; idx < total; idx += nth) {
-        const double val = fma(-s_u[i], s_v[jj], S[idx]);
-        S[idx] = val;
-        const unsigned long long b = (unsigned long long)__double_as_longlong(val) & kAbsMask;
-        lmax = b > lmax ? b : lmax;
-        i += di;
-        jj += dj;
-        if (i >= rows) {
-          i -= rows;
-          ++jj;
+  // block-wide reductions (every thread gets the result)
+  auto block_min = [&](unsigned long long v) {
+    v = warp_min_u64(v);
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long m = lane < nwarps ? s_red[lane] : ~0ull;
+      m = warp_min_u64(m);
+      if (lane == 0) s_bcast = m;
+    }
+    __syncthreads();
+    return s_bcast;
+  };
+  auto block_cand = [&](Cand c) {
+    for (int off = 16; off; off >>= 1) c = cand_merge(c, cand_shfl(c, off), keep);
+    if (lane == 0) s_cand[wid] = c;
+    __syncthreads();
+    Cand o = s_cand[0];
+    for (int w = 1; w < nwarps; ++w) o = cand_merge(o, s_cand[w], keep);
+    __syncthreads();
+    return o;
+  };
+  // smallest (key << 32 | storage position) over the active entries with
+  // |R| >= thr; one warp per row, the lanes over the columns
+  int na = nr, nca = k2;
+  auto find_key = [&](unsigned long long thr) {
+    unsigned long long best = ~0ull;
+    int cid[LC];
+#pragma unroll
+    for (int m = 0; m < LC; ++m) cid[m] = lane + 32 * m < nca ? s_cid[lane + 32 * m] : 0;
+    for (int i = wid; i < na; i += nwarps) {
+      const double* Sr = S + (int64_t)i * k2;
+      const int rid = s_rid[i];
+#pragma unroll
+      for (int m = 0; m < LC; ++m) {
+        const int c = lane + 32 * m;
+        if (c < nca && abs_bits(Sr[c]) >= thr) {
+          const unsigned long long kk =
+              ((unsigned long long)(cid[m] * rows + rid) << 32) | (unsigned)(i * k2 + c);
+          best = kk < best ? kk : best;
         }
       }
-    } else {
-      for (int idx = tid; idx < total; idx += nth) {
-        const unsigned long long b = (unsigned long long)__double_as_longlong(S[idx]) & kAbsMask;
-        lmax = b > lmax ? b : lmax;
+    }
+    return block_min(best);
+  };
+  // post the CTA's summary into slot b: the candidate's residual and V^ rows
+  // stay in this CTA; the header goes to every CTA of the cluster
+  auto post = [&](int b, const Cand& cd, int r) {
+    double* prow = post_row(posts, b);
+    const bool has = cd.k != ~0ull && !cd.bad;
+    const int pos = has ? (int)(cd.k & 0xffffffffu) : 0;
+    const int i = pos / k2, c = pos - (pos / k2) * k2;
+    if (has) {
+      for (int cc = tid; cc < nca; cc += nth) prow[cc] = S[(int64_t)i * k2 + cc];
+      for (int cc = tid; cc < r; cc += nth) prow[k2 + cc] = W[(int64_t)i * rmax_cap + cc];
+    }
+    if (tid < C) {
+      AcaPost h;
+      h.maxbits = cd.m;
+      h.bad = cd.bad;
+      h.pad = 0;
+      if (has) {
+        const double pv = S[(int64_t)i * k2 + c];
+        h.candbits = abs_bits(pv);
+        h.key = (int)(cd.k >> 32);
+        h.pval = pv;
+        h.tri = s_tri[i];
+        h.cslot = c;
+        h.rslot = i;
+      } else {
+        h.candbits = 0;
+        h.key = INT_MAX;
+        h.pval = 0.0;
+        h.tri = -1;
+        h.cslot = -1;
+        h.rslot = -1;
       }
+      *cluster.map_shared_rank(&s_hdr[b][q], tid) = h;
     }
-    lmax = warp_max_u64(lmax);
-    if (lane == 0) s_wmax[wid] = lmax;
+  };
+
+  int r = 0;
+  double first = 0.0;
+  int jslot = -1, islot = -1;  // storage positions of the last pivot's column and (owner) row
+  bool own = false;            // this CTA holds the last pivot row
+  for (;;) {
+    Cand cd{0, ~0ull, 0, 0};        // this lane's running summary
+    unsigned long long wthr = 0;    // its window threshold
+    if (r > 0) {
+      const int t = r - 1;
+      // the pivot column leaves the active region: swap it with the last
+      // active column (every CTA; the same positions everywhere)
+      const int cl = nca - 1;
+      if (jslot != cl) {
+        for (int i = tid; i < na; i += nth) {
+          double* Sr = S + (int64_t)i * k2;
+          const double a = Sr[jslot];
+          Sr[jslot] = Sr[cl];
+          Sr[cl] = a;
+        }
+        if (tid == 0) {
+          const double a = s_v[jslot];
+          s_v[jslot] = s_v[cl];
+          s_v[cl] = a;
+          const int b = s_cid[jslot];
+          s_cid[jslot] = s_cid[cl];
+          s_cid[cl] = b;
+        }
+      }
+      __syncthreads();
+      nca = cl;
+      if (own) {
+        // the pivot row leaves too: swap with the last active row; its V^ row
+        // becomes the unit vector e_t
+        const int rl = na - 1;
+        if (islot != rl) {
+          double* A = S + (int64_t)islot * k2;
+          double* B = S + (int64_t)rl * k2;
+          for (int c = tid; c < nca; c += nth) {
+            const double a = A[c];
+            A[c] = B[c];
+            B[c] = a;
+          }
+          double* WA = W + (int64_t)islot * rmax_cap;
+          double* WB = W + (int64_t)rl * rmax_cap;
+          for (int c = tid; c < t; c += nth) WA[c] = WB[c];
+          if (tid == 0) {
+            s_u[islot] = s_u[rl];
+            const int a = s_tri[islot];
+            s_tri[islot] = s_tri[rl];
+            s_tri[rl] = a;
+            const int b = s_rid[islot];
+            s_rid[islot] = s_rid[rl];
+            s_rid[rl] = b;
+          }
+        }
+        __syncthreads();
+        double* WB = W + (int64_t)rl * rmax_cap;
+        for (int c = tid; c < job.rmax; c += nth) WB[c] = c == t ? 1.0 : 0.0;
+        na = rl;
+      }
+      // V^ and residual of the active rows, one warp per row: lane columns
+      // lane + 32 m of w and v in registers
+      double wr[LC], vr[LC];
+#pragma unroll
+      for (int m = 0; m < LC; ++m) {
+        const int c = lane + 32 * m;
+        wr[m] = c < t ? s_w[c] : 0.0;
+        vr[m] = c < nca ? s_v[c] : 0.0;
+      }
+      const bool last = r == job.rmax;
+      int cid[LC];
+#pragma unroll
+      for (int m = 0; m < LC; ++m) cid[m] = lane + 32 * m < nca ? s_cid[lane + 32 * m] : 0;
+      for (int i = wid; i < na; i += nwarps) {
+        const double ui = s_u[i];
+        double* Wr = W + (int64_t)i * rmax_cap;
+#pragma unroll
+        for (int m = 0; m < LC; ++m) {
+          const int c = lane + 32 * m;
+          if (c < t) Wr[c] = fma(-ui, wr[m], Wr[c]);
+        }
+        if (lane == 0) Wr[t] = ui;
+        if (last) continue;
+        double* Sr = S + (int64_t)i * k2;
+        const unsigned long long rk = (unsigned long long)s_rid[i];
+#pragma unroll
+        for (int m = 0; m < LC; ++m) {
+          const int c = lane + 32 * m;
+          if (c < nca) {
+            const double val = fma(-ui, vr[m], Sr[c]);
+            Sr[c] = val;
+            // running summary of this lane's entries (a new maximum resets
+            // the window; a rise within the window keeps a certified key)
+            const unsigned long long b = abs_bits(val);
+            const unsigned long long key =
+                ((unsigned long long)cid[m] * rows + rk) << 32 | (unsigned)(i * k2 + c);
+            if (b > cd.m) {
+              const unsigned long long thr = tie_bits(b, keep);
+              if (cd.m >= thr && (cd.bad || cd.v < thr)) cd.bad = 1;
+              if (cd.m < thr || cd.bad) {
+                cd.k = key;
+                cd.v = b;
+              } else if (key < cd.k) {
+                cd.k = key;
+                cd.v = b;
+              }
+              cd.m = b;
+              wthr = thr;
+            } else if (b >= wthr && key < cd.k) {
+              cd.k = key;
+              cd.v = b;
+            }
+          }
+        }
+      }
+      if (last) break;
+    } else {
+      for (int i = wid; i < na; i += nwarps)
+        for (int c = lane; c < nca; c += 32) {
+          const unsigned long long b = abs_bits(S[(int64_t)i * k2 + c]);
+          const unsigned long long key = ((unsigned long long)c * rows + s_rid[i]) << 32 | (unsigned)(i * k2 + c);
+          if (b > cd.m) {
+            const unsigned long long thr = tie_bits(b, keep);
+            if (cd.m >= thr && (cd.bad || cd.v < thr)) cd.bad = 1;
+            if (cd.m < thr || cd.bad) {
+              cd.k = key;
+              cd.v = b;
+            } else if (key < cd.k) {
+              cd.k = key;
+              cd.v = b;
+            }
+            cd.m = b;
+            wthr = thr;
+          } else if (b >= wthr && key < cd.k) {
+            cd.k = key;
+            cd.v = b;
+          }
+        }
+    }
+    Cand cc = block_cand(cd);
+    if (cc.bad && cc.m <= kInfBits) {
+      // a near tie the running summaries could not certify: scan again
+      const unsigned long long kp = find_key(tie_bits(cc.m, keep));
+      cc.k = kp;
+      cc.v = kp == ~0ull ? 0 : abs_bits(S[kp & 0xffffffffu]);
+      cc.bad = 0;
+    }
+    const int slot = r & 1;
+    post(slot, cc, r);
     __syncthreads();
-    if (tid == 0) {
-      unsigned long long m = 0;
-      for (int w = 0; w < nth / 32; ++w) m = s_wmax[w] > m ? s_wmax[w] : m;
-      s_max = m;
-    }
     cluster.sync();
-    // 2. cluster max (each warp reads the C CTAs' maxima)
-    unsigned long long gmax = 0;
-    if (lane < C) gmax = *cluster.map_shared_rank(&s_max, lane);
-    gmax = warp_max_u64(gmax);
+    // every warp takes the same decision from the same headers (lane p holds
+    // CTA p's)
+    Cand g{0, ~0ull, 0, 0};
+    if (lane < C) {
+      const AcaPost& h = s_hdr[slot][lane];
+      g.m = h.maxbits;
+      g.k = h.key == INT_MAX ? ~0ull : (unsigned long long)h.key;
+      g.v = h.candbits;
+      g.bad = h.bad;
+    }
+    for (int off = 16; off; off >>= 1) g = cand_merge(g, cand_shfl(g, off), keep);
+    const unsigned long long gmax = g.m;
     if (gmax > kInfBits) {
       if (tid == 0 && q == 0) atomicOr(status, kStatusNumeric);
       break;
@@ -340,82 +635,53 @@ k_aca(const AcaJob* __restrict__ jobs, int k, int rows_cap, int kw_cap, const in
     const double big = __longlong_as_double((long long)gmax);
     if (r == 0) first = big;
     if (big == 0.0 || (r > 0 && big <= tol * first)) break;
-    const unsigned long long thr = (unsigned long long)__double_as_longlong(big * (1.0 - tie));
-    // 3. smallest global column-major index at or above the threshold
-    int lidx = INT_MAX;
-    for (int idx = tid; idx < total; idx += nth) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(S[idx]) & kAbsMask;
-      if (b >= thr) {
-        const int i = idx % rows, jj = idx / rows;
-        const int j = jj < nk ? nu0 + jj : k + nu0 + (jj - nk);
-        lidx = j * rows + i;
-        break;
+    int pslot = slot;
+    unsigned long long kk = g.k;
+    if (g.bad) {
+      // a CTA's own window held a candidate outside the cluster's window:
+      // every CTA posts its smallest key at the cluster's threshold
+      const unsigned long long thr = tie_bits(gmax, keep);
+      Cand c2{cc.m, ~0ull, 0, 0};
+      if (cc.m >= thr) {
+        c2.k = find_key(thr);
+        c2.v = c2.k == ~0ull ? 0 : abs_bits(S[c2.k & 0xffffffffu]);
       }
+      post(2, c2, r);
+      __syncthreads();
+      cluster.sync();
+      unsigned long long k2s = ~0ull;
+      if (lane < C && s_hdr[2][lane].key != INT_MAX) k2s = (unsigned long long)s_hdr[2][lane].key;
+      kk = warp_min_u64(k2s);
+      pslot = 2;
     }
-    lidx = warp_min_int(lidx);
-    if (lane == 0) s_wmin[wid] = lidx;
-    __syncthreads();
-    if (tid == 0) {
-      int m = INT_MAX;
-      for (int w = 0; w < nth / 32; ++w) m = min(m, s_wmin[w]);
-      s_idx = m;
-    }
-    cluster.sync();
-    int gidx = INT_MAX;
-    if (lane < C) gidx = *cluster.map_shared_rank(&s_idx, lane);
-    gidx = warp_min_int(gidx);
-    const int ip = gidx % rows, jp = gidx / rows;
-    const int nup = jp < k ? jp : jp - k;
-    const int owner = nup / kw;
-    // 4. pivot row slice, pivot column from its owner
-    for (int jj = tid; jj < ncol; jj += nth) s_v[jj] = S[(int64_t)jj * rows + ip];
-    if (q == owner) {
-      const int ajj = jp < k ? (nup - nu0) : (nk + nup - nu0);
-      const double p = S[(int64_t)ajj * rows + ip];
-      for (int i = tid; i < rows; i += nth) {
-        const double u = S[(int64_t)ajj * rows + i] / p;
-        s_u[i] = u;
-        U[(int64_t)r * rows + i] = u;
-      }
-    }
-    if (tid == 0) s_prow[r] = ip;
-    cluster.sync();
-    if (q != owner) {
-      const double* ru = cluster.map_shared_rank(s_u, owner);
-      for (int i = tid; i < rows; i += nth) s_u[i] = ru[i];
-    }
-    __syncthreads();
+    const int owner = __ffs(__ballot_sync(0xffffffffu, lane < C && s_hdr[pslot][lane].key == (int)kk)) - 1;
+    // the pivot row v, w = V^[i*, :] and p from the winner's post; u for the
+    // CTA's active rows
+    const AcaPost* wh = &s_hdr[pslot][owner];
+    const double* wrow = post_row(cluster.map_shared_rank(posts, owner), pslot);
+    const double p = wh->pval;
+    jslot = wh->cslot;
+    own = owner == q;
+    islot = own ? wh->rslot : -1;
+    for (int c = tid; c < nca; c += nth) s_v[c] = wrow[c];
+    for (int c = tid; c < r; c += nth) s_w[c] = wrow[k2 + c];
+    for (int i = tid; i < na; i += nth) s_u[i] = S[(int64_t)i * k2 + jslot] / p;
+    if (tid == 0) s_ptri[r] = wh->tri;
     ++r;
-    have_update = true;
-    if (r == job.rmax) break;
+    __syncthreads();
   }
-  cluster.sync();  // every U column written, no CTA still reads a peer's u
-
-  // V^ = U L^{-1} (L = U[P, :], unit lower triangular): row a of V^
-  // solves v L = U[a, :] by back substitution, v_c = U[a, c] -
-  // sum_{d > c} v_d L_{dc}.  One warp per row (rows spread over the
-  // cluster), the sum over d split over the lanes; the row being solved
-  // lives in the warp's slice of S (the residual is no longer needed).
-  // V^ row-major rows x r.
-  double* Vh = vh_pool + job.vh_off;
-  const int rpc = (rows + C - 1) / C;
-  const int nwarps = nth / 32;
-  double* vrow = S + (size_t)wid * rows_cap;  // r <= rows doubles per warp
-  for (int a = q * rpc + wid; a < min(rows, (q + 1) * rpc); a += nwarps) {
-    for (int c = r - 1; c >= 0; --c) {
-      double part = 0.0;
-      const double* Lc = U + (int64_t)c * rows;
-      for (int d = c + 1 + lane; d < r; d += 32) part = fma(vrow[d], Lc[s_prow[d]], part);
-      for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-      if (lane == 0) vrow[c] = Lc[a] - part;
-      __syncwarp();
-    }
-    for (int c = lane; c < r; c += 32) Vh[(int64_t)a * r + c] = vrow[c];
-    __syncwarp();
+  cluster.sync();  // no CTA still reads a peer's posts
+  // V^ (rows x r, row-major by row of A^) and the pivots' triangles in
+  // selection order
+  double* Vh = M.vh_pool + job.vh_off;
+  for (int i = wid; i < nr; i += nwarps) {
+    const double* Wr = W + (int64_t)i * rmax_cap;
+    double* out = Vh + (int64_t)s_rid[i] * r;
+    for (int c = lane; c < r; c += 32) out[c] = Wr[c];
   }
   if (q == 0) {
-    for (int t = tid; t < r; t += nth) piv_pool[job.p_off + t] = s_rows[s_prow[t]];
-    if (tid == 0) rank_out[job.c] = r;
+    for (int t = tid; t < r; t += nth) M.piv_pool[job.p_off + t] = s_ptri[t];
+    if (tid == 0) M.rank_out[job.c] = r;
   }
 }
 
@@ -1054,6 +1320,91 @@ int check_status(DevMem& st, cudaStream_t s, const char* where) {
   return GCA_OK;
 }
 
+// Launches of k_aca for one level: jobs grouped by cluster size C (CTAs per
+// job).  A job takes the smallest C whose rows fit in shared memory; levels
+// with few jobs spread them over more CTAs (up to 16), so that the level
+// keeps the SMs busy and each CTA's share of the FP64 rank-one updates stays
+// small, as long as every CTA keeps at least kMinRowsPerCta rows.
+class AcaLauncher {
+ public:
+  int init(int k) {
+    k_ = k;
+    int dev = 0;
+    GCA_TRY_CUDA(cudaGetDevice(&dev));
+    int optin = 0;
+    GCA_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev));
+    kern_ = 2 * k <= 128 ? k_aca<4> : (2 * k <= 192 ? k_aca<6> : k_aca<14>);
+    cudaFuncAttributes fa{};
+    GCA_TRY_CUDA(cudaFuncGetAttributes(&fa, kern_));
+    budget_ = (size_t)optin - fa.sharedSizeBytes;
+    GCA_TRY_CUDA(cudaFuncSetAttribute(kern_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget_));
+    GCA_TRY_CUDA(cudaFuncSetAttribute(kern_, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    return GCA_OK;
+  }
+  size_t smem(int rows, int C) const {
+    const int rpc = (rows + C - 1) / C;
+    return aca_smem_bytes(rpc, 2 * k_, std::min(rows, 2 * k_));
+  }
+  int launch(const std::vector<AcaJob>& jobs, DevMem& d_jobs, const AcaMesh* d_mesh, int level, double tol,
+             double tie, int* d_status, cudaStream_t st) {
+    constexpr int kMinRowsPerCta = 16;
+    int spread = 1;
+    while (spread < 16 && (int64_t)jobs.size() * spread < sms_) spread *= 2;
+    std::vector<AcaJob> by_c[5];
+    for (const auto& j : jobs) {
+      int g = 0;
+      while (g < 5 && smem(j.rows, 1 << g) > budget_) ++g;
+      if (g == 5) {
+        set_error("gca_build: cross approximation matrix too large for the cluster kernel");
+        return GCA_ERR_UNSUPPORTED;
+      }
+      while (g < 4 && (1 << g) < spread && (j.rows >> (g + 1)) >= kMinRowsPerCta) ++g;
+      by_c[g].push_back(j);
+    }
+    GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * jobs.size()));
+    std::vector<AcaJob> host;  // grouped copy, uploaded at once
+    for (int g = 0; g < 5; ++g) host.insert(host.end(), by_c[g].begin(), by_c[g].end());
+    GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, host.data(), sizeof(AcaJob) * host.size(), cudaMemcpyHostToDevice, st));
+    size_t at = 0;
+    for (int g = 0; g < 5; ++g) {
+      if (by_c[g].empty()) continue;
+      const int C = 1 << g;
+      int rows_cap = 1;
+      for (const auto& j : by_c[g]) rows_cap = std::max(rows_cap, j.rows);
+      const int rpc_cap = (rows_cap + C - 1) / C;
+      const int rmax_cap = std::min(rows_cap, 2 * k_);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(by_c[g].size() * C));
+      cfg.blockDim = dim3(kAcaThreads);
+      cfg.dynamicSmemBytes = aca_smem_bytes(rpc_cap, 2 * k_, rmax_cap);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      PhaseScope ps__(profile_detail() ? "green_aca.L" + std::to_string(level) + ".c" + std::to_string(C)
+                                       : std::string("green_aca"),
+                      st);
+      GCA_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern_, (const AcaJob*)(d_jobs.as<AcaJob>() + at), d_mesh, k_,
+                                      rpc_cap, rmax_cap, tol, tie, d_status));
+      at += by_c[g].size();
+    }
+    // `host` must outlive the copy: the caller synchronises before the next level
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));
+    return GCA_OK;
+  }
+
+ private:
+  int k_ = 0;
+  int sms_ = 148;
+  size_t budget_ = 0;
+  void (*kern_)(const AcaJob*, const AcaMesh*, int, int, int, double, double, int*) = nullptr;
+};
+
 }  // namespace
 
 // The whole construction; see the header of this file.
@@ -1187,7 +1538,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     // upper bounds, refined per level below
     piv_cap += std::min<int64_t>(h->end[c] - h->begin[c], 2 * k);
   }
-  DevMem d_piv, d_rank, d_vh, d_uscr, d_jobs;
+  DevMem d_piv, d_rank, d_vh, d_jobs, d_mesh;
   GCA_TRY(d_piv.alloc(sizeof(int) * (size_t)std::max<int64_t>(piv_cap, 1)));
   GCA_TRY(d_rank.alloc(sizeof(int) * (size_t)nc));
   GCA_TRY_CUDA(cudaMemsetAsync(d_rank.p, 0, sizeof(int) * nc, st));
@@ -1199,22 +1550,16 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     vh_cap += rows * std::min<int64_t>(rows, 2 * k);
   }
   GCA_TRY(d_vh.alloc(sizeof(double) * (size_t)std::max<int64_t>(vh_cap, 1)));
-  int dev = 0;
-  GCA_TRY_CUDA(cudaGetDevice(&dev));
-  int smem_optin = 0;
-  GCA_TRY_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  cudaFuncAttributes aca_attr{};
-  GCA_TRY_CUDA(cudaFuncGetAttributes(&aca_attr, k_aca));
-  const int aca_dyn_max = smem_optin - (int)aca_attr.sharedSizeBytes;
-  GCA_TRY_CUDA(cudaFuncSetAttribute(k_aca, cudaFuncAttributeMaxDynamicSharedMemorySize, aca_dyn_max));
-  GCA_TRY_CUDA(cudaFuncSetAttribute(k_aca, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  {
+    const AcaMesh am{h->d_perm.as<int>(), d_tq.as<P4>(), d_zq.as<P4>(), d_piv.as<int>(), d_vh.as<double>(),
+                     d_rank.as<int>()};
+    GCA_TRY(d_mesh.alloc(sizeof(AcaMesh)));
+    GCA_TRY_CUDA(cudaMemcpyAsync(d_mesh.p, &am, sizeof(AcaMesh), cudaMemcpyHostToDevice, st));
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // am is a local
+  }
+  AcaLauncher aca;
+  GCA_TRY(aca.init(k));
   const double tie = std::ldexp(1.0, -40);
-  // shared memory of one CTA of k_aca for a job of `rows` rows on a C-CTA cluster
-  auto aca_smem = [&](int rows, int C) -> size_t {
-    const int kw = (k + C - 1) / C;
-    return sizeof(double) * (aca_s_doubles(rows, kw) + rows + 2 * kw) + sizeof(int) * 2 * (size_t)rows;
-  };
-  const size_t smem_budget = (size_t)aca_dyn_max;
   for (int L = h->depth; L >= 1; --L) {
     std::vector<AcaJob> jobs;
     for (int c : h->by_level[L]) {
@@ -1228,12 +1573,12 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
       } else {
         const int c0 = h->child0[c], c1 = h->child1[c];
         j.r0 = h->rank[c0];
-        j.r1 = h->rank[c1];
-        j.rows = j.r0 + j.r1;
+        j.rows = j.r0 + h->rank[c1];
         j.piv0 = h->poff[c0];
         j.piv1 = h->poff[c1];
       }
       j.rmax = std::min(j.rows, 2 * k);
+      j.mesh = 0;
       j.diam = diam[c];
       j.p_off = piv_used;
       h->poff[c] = piv_used;
@@ -1249,69 +1594,11 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
       set_error("gca_build: internal pool bound exceeded");
       return GCA_ERR_INVALID_ARG;
     }
-    int64_t u_used = 0;
-    for (auto& j : jobs) {
-      j.u_off = u_used;
-      u_used += (int64_t)j.rows * j.rmax;
-    }
-    GCA_TRY(d_uscr.reserve(sizeof(double) * (size_t)std::max<int64_t>(u_used, 1)));
-    // small jobs on one CTA, large ones on clusters of 8 or 16 CTAs whose
-    // column slices fit in shared memory
-    std::vector<AcaJob> by_c[3];
-    const int csize[3] = {1, 8, 16};
-    for (const auto& j : jobs) {
-      int pick = -1;
-      if ((size_t)j.rows * 2 * k * sizeof(double) <= 96 * 1024 && aca_smem(j.rows, 1) <= smem_budget)
-        pick = 0;
-      else if (aca_smem(j.rows, 8) <= smem_budget)
-        pick = 1;
-      else if (aca_smem(j.rows, 16) <= smem_budget)
-        pick = 2;
-      if (pick < 0) {
-        set_error("gca_build: cross approximation matrix too large for the cluster kernel");
-        return GCA_ERR_UNSUPPORTED;
-      }
-      by_c[pick].push_back(j);
-    }
-    GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * jobs.size()));
-    size_t at = 0;
-    for (int g = 0; g < 3; ++g) {
-      if (by_c[g].empty()) continue;
-      const int C = csize[g];
-      int rows_cap = 1;
-      for (const auto& j : by_c[g]) rows_cap = std::max(rows_cap, j.rows);
-      const int kw = (k + C - 1) / C;
-      const size_t smem = aca_smem(rows_cap, C);
-      AcaJob* dj = d_jobs.as<AcaJob>() + at;
-      GCA_TRY_CUDA(cudaMemcpyAsync(dj, by_c[g].data(), sizeof(AcaJob) * by_c[g].size(),
-                                   cudaMemcpyHostToDevice, st));
-      at += by_c[g].size();
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)(by_c[g].size() * C));
-      cfg.blockDim = dim3(kAcaThreads);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = C;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      PhaseScope ps__(profile_detail() ? "green_aca.L" + std::to_string(L) + ".c" + std::to_string(C)
-                                       : std::string("green_aca"),
-                      st);
-      GCA_TRY_CUDA(cudaLaunchKernelEx(&cfg, k_aca, (const AcaJob*)dj, k, rows_cap, kw,
-                                      (const int*)h->d_perm.as<int>(), (const P4*)d_tq.as<P4>(),
-                                      (const P4*)d_zq.as<P4>(), d_piv.as<int>(), d_uscr.as<double>(),
-                                      d_vh.as<double>(), d_rank.as<int>(), prm->aca_tol, tie,
-                                      d_status.as<int>()));
-    }
+    GCA_TRY(aca.launch(jobs, d_jobs, d_mesh.as<AcaMesh>(), L, prm->aca_tol, tie, d_status.as<int>(), st));
     GCA_TRY(check_status(d_status, st, "cross approximation"));
     GCA_TRY_CUDA(cudaMemcpyAsync(h->rank.data(), d_rank.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
     GCA_TRY_CUDA(cudaStreamSynchronize(st));
   }
-  d_uscr.release();
 
   // offsets of the stored coefficients
   h->xoff.assign(nc + 1, 0);

@@ -8,8 +8,10 @@
   bases match the oracle's; sampled rows of the float64 product match the dense G within
   the compression error; the adjoint identity holds; float32 and bfloat16
   products stay within their bounds of the float64 product.
-* The 81920-triangle sphere with 64 right-hand sides: float32 and bfloat16
-  products (and transposes) against float64 per right-hand side.
+* The 81920-triangle sphere (bench parameters): the oracle's tree and block
+  tree, sampled coupling and near-field entries, leaf bases and dense rows;
+  with 64 right-hand sides, float32 and bfloat16 products (and transposes)
+  against float64 per right-hand side.
 * 256 meshes of uneven size and type (1280-20480 triangles, 1-32
   right-hand sides each) in one persistent float32 launch, also replayed
   from a CUDA graph, against each mesh's own product; the float64 product
@@ -112,10 +114,38 @@ def test_adjoint_identity_full_size(bench_batch):
         assert ((lhs - rhs).abs() / scale).max() <= 1e-13, n
 
 
-def test_sphere81920_precision(lib):
+@pytest.fixture(scope="module")
+def sphere81920(lib):
     v, t = synth.mesh_for_config("sphere81920")
     tree = lib.tree_build(v, t, CFG2["leaf_size"])
-    h = lib.build(v, t, tree, lib.Params(**CFG2, flags=lib.DROP_EXPORT))
+    h = lib.build(v, t, tree, lib.Params(**CFG2))
+    return v, t, tree, h
+
+
+def test_sphere81920_samples_match_oracle(sphere81920):
+    """The precision configuration (81920 triangles, built with the bench
+    parameters) on samples the oracle computes one by one: its tree and block
+    tree, coupling and near-field entries, leaf bases, and rows of the dense
+    G against the float64 product."""
+    v, t, tr, h = sphere81920
+    p = OParams(**CFG2)
+    rng = np.random.default_rng(81920)
+    tree, lo, hi, far, near = sampling.oracle_geometry(v, t, p)
+    sampling.check_tree(tr, tree)
+    dump = h.export()
+    sampling.check_blocks(dump, far, near)
+    gal = Galerkin(v, t, p.sauter_q)
+    sampling.check_near_entries(dump, tree, gal, rng)
+    sampling.check_coupling_entries(dump, gal, rng)
+    sampling.check_leaf_bases(dump, tree, lo, hi, gal, p, rng)
+    del dump
+    x = synth.normal_rhs(len(t), 4, seed=3)
+    y = h.matvec(colmajor(x, torch.float64), "f64").cpu().numpy()
+    sampling.check_dense_rows(y, x, v, t, gal, rng, rows=3)
+
+
+def test_sphere81920_precision(sphere81920):
+    v, t, tree, h = sphere81920
     X = synth.normal_rhs(len(t), 64, seed=0)
     x64 = colmajor(X, torch.float64)
     x32 = colmajor(X, torch.float32)
