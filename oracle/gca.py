@@ -156,10 +156,14 @@ def needed_clusters(tree, far):
     return needed
 
 
-def build_bases(gal, tree, lo, hi, params, far=None):
+def build_bases(gal, tree, lo, hi, params, far=None, green=None):
     """Nested cluster bases by Green cross approximation (Sect. 3, Sect. 4),
     for the clusters that need one (all non-root clusters when `far` is
-    None); the others get empty bases."""
+    None); the others get empty bases.  `green(gal, rows, z, nrm, w, d)`
+    forms the thin matrix of a cluster (default: the Green quadrature matrix
+    A_tau of the single-layer kernel)."""
+    if green is None:
+        green = green_matrix
     nc = len(tree["begin"])
     diam = cluster.diameter(lo, hi)
     bases = Bases(pivots=[None] * nc, rank=np.zeros(nc, dtype=np.int64))
@@ -183,7 +187,7 @@ def build_bases(gal, tree, lo, hi, params, far=None):
         else:
             c0, c1 = tree["child0"][c], tree["child1"][c]
             rows = np.concatenate([bases.pivots[c0], bases.pivots[c1]])
-        A = green_matrix(gal, rows, z, nrm, w, diam[c])
+        A = green(gal, rows, z, nrm, w, diam[c])
         res = aca(A, params.aca_tol, params.tie_rel)
         bases.pivots[c] = rows[res.rows]
         bases.rank[c] = len(res.rows)
