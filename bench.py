@@ -435,6 +435,38 @@ def run_legs(gca, batch, meshes, stats, n, args, dev, stream, hbm_peak):
                       "err_vs_f64": 0.0 if prec == "f64" else leg_errors([out], [y64])}
     h.check()
     legs["sphere81920.R64"] = cfg3
+    del h
+    # the double-layer operator K on the perturbed 20480-triangle sphere (its
+    # row bases are the single layer's, its column bases its own)
+    v, t = meshes[1]
+    tree = gca.tree_build(v, t, PARAMS["leaf_size"])
+    a.record(stream)
+    hd = gca.build_double_layer(v, t, tree, gca.Params(**PARAMS, flags=gca.DROP_EXPORT))
+    b.record(stream)
+    b.synchronize()
+    st = hd.stats()
+    cs = hd.column_stats()
+    R = NRHS
+    x64 = torch.from_numpy(synth.normal_rhs(len(t), R, seed=0)).to(dev)
+    x32 = x64.float()
+    dlg = {"workload": "double layer, perturbed20480, leaf 64, eta 2, m 4, tol 1e-8, 16 RHS N(0,1)",
+           "build_s": a.elapsed_time(b) * 1e-3, "rank_sum_rows": st["rank_sum"], "rank_sum_cols": cs["rank_sum"]}
+    ref = {}
+    for tr in (False, True):
+        y64 = torch.empty((R, len(t)), dtype=torch.float64, device=dev).t()
+        for prec in ("f64", "f32", "bf16"):
+            xin = x64 if prec == "f64" else x32
+            out = y64 if prec == "f64" else torch.empty((R, len(t)), dtype=torch.float32, device=dev).t()
+            ms = time_products(lambda: hd.matvec(xin, prec, transpose=tr, out=out), K, W, stream)
+            sm = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+            sv = 8 if prec == "f64" else 4
+            byt = (sm * (st["v_entries"] + st["e_entries"] + cs["w_entries"] + cs["f_entries"] + st["s_entries"])
+                   + sv * st["n_entries"] + 2 * sv * len(t) * R)
+            key = prec + (".T" if tr else "")
+            dlg[key] = {"GB/s": byt / ms / 1e6, "frac_hbm": byt / ms / 1e6 / hbm_peak, "ms": ms,
+                        "err_vs_f64": 0.0 if prec == "f64" else leg_errors([out], [y64])}
+    hd.check()
+    legs["double_layer.perturbed20480.R16"] = dlg
     return legs
 
 

@@ -229,6 +229,52 @@ int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t max_clusters
 int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
               void* stream, gca_h2** out);
 
+/* The double-layer operator of the integral equation of Sect. 1: the
+ * Galerkin matrix K with k_ij = int_{T_i} int_{T_j} dg/dn_y(x, y) dy dx,
+ * dg/dn_y(x, y) = <n_y, x - y> / (4 pi |x - y|^3), n_y the outer unit normal
+ * of the flat triangle holding y (from its vertex order), and its GCA-H^2
+ * approximation K|tau x sigma ~ V_tau K|tilde-tau x tilde-sigma' W_sigma^*.
+ *   - rows: x -> dg/dn_y(x, y) is harmonic near tau, so Green's formula in x
+ *     (Sect. 2) gives the single layer's factors: V_tau, E_tau and
+ *     tilde-tau are those of gca_build;
+ *   - columns: applying <n_y, grad_y> to Green's formula for y -> g(x, y)
+ *     gives the column Green matrix
+ *       a'_{j nu}    =          sqrt(w_nu) int dg/dn_y(y, z_nu) phi_j(y) dy,
+ *       a'_{j nu+k}  = -d_sigma sqrt(w_nu) int d2g/dn_y dn_z(y, z_nu) phi_j(y) dy,
+ *     d2g/dn_y dn_z(y, z) = (<n_y, n_z> / r^3 - 3 <n_y, e><n_z, e> / r^5) / (4 pi),
+ *     e = z - y; its cross approximation (Sect. 3), nested as in Sect. 4,
+ *     gives tilde-sigma', the column bases W and transfer matrices F;
+ *   - entries in float64: the 7 x 7 rule for disjoint pairs, 0 for identical
+ *     flat triangles, Sauter-Schwab for a common edge or vertex (Sect. 8).
+ * The handle works with h2_matvec (K x), h2_matvec_transpose (K^T x, a
+ * genuinely different product), h2_matvec_noalloc, gca_h2_stats (S: the
+ * r_tau x r'_sigma couplings, N: the near field), gca_h2_export (row bases,
+ * couplings, near field) and gca_h2_export_columns.  Arguments, errors and
+ * synchronisation as gca_build. */
+int gca_build_double_layer(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
+                           void* stream, gca_h2** out);
+
+/* Sizes of the column side of a handle: op 0 (single layer: the row bases
+ * serve the columns, the values repeat those of gca_h2_stats) or op 1
+ * (double layer); max_rank and rank_sum of r'_sigma, coefficients of the
+ * column bases W and transfers F. */
+typedef struct {
+  int32_t op;
+  int32_t max_rank;
+  int64_t rank_sum;
+  int64_t w_entries;
+  int64_t f_entries;
+} gca_column_stats;
+int gca_h2_column_stats(const gca_h2* h, gca_column_stats* out);
+
+/* Host copy of the column side in the layout of gca_host_dump: rank
+ * [nclusters] (r'_sigma), pivots [rank_sum] (tilde-sigma'), V the column
+ * bases W (leaves, |sigma-hat| x r' row-major), E the transfers F
+ * (r'_child x r'_parent row-major); far, near, S and N must be NULL.  On a
+ * single-layer handle it returns the row bases.  Errors: INVALID_ARG,
+ * UNSUPPORTED (GCA_DROP_EXPORT), CUDA. */
+int gca_h2_export_columns(const gca_h2* h, gca_host_dump* out);
+
 /* y = G_H2 x for nrhs right-hand sides, G_H2 the representation of Sect. 4:
  * y|tau-hat = sum over admissible (tau, sigma) of V_tau S_{tau sigma}
  * V_sigma^* x|sigma-hat plus sum over inadmissible leaf pairs of

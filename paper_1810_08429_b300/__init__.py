@@ -62,6 +62,11 @@ class _Phase(ctypes.Structure):
                 ("ms", ctypes.c_double)]
 
 
+class _ColStats(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("max_rank", ctypes.c_int32), ("rank_sum", ctypes.c_int64),
+                ("w_entries", ctypes.c_int64), ("f_entries", ctypes.c_int64)]
+
+
 class _Dump(ctypes.Structure):
     _fields_ = [("rank", _i32p), ("pivots", _i32p), ("far", _i32p), ("near", _i32p),
                 ("V", _f64p), ("E", _f64p), ("S", _f64p), ("N", _f64p)]
@@ -124,6 +129,10 @@ def _load():
                                          ctypes.c_int32, ctypes.POINTER(_Dump), ctypes.c_uint32, vp,
                                          ctypes.POINTER(vp)]),
         "gca_test_hook": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64]),
+        "gca_build_double_layer": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
+                                                  ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+        "gca_h2_column_stats": (ctypes.c_int, [vp, ctypes.POINTER(_ColStats)]),
+        "gca_h2_export_columns": (ctypes.c_int, [vp, ctypes.POINTER(_Dump)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -297,6 +306,28 @@ class H2:
             d["near"] = d["near"].reshape(-1, 2)
         return d
 
+    def column_stats(self):
+        """Sizes of the column side (gca_h2_column_stats)."""
+        s = _ColStats()
+        _check(lib.gca_h2_column_stats(self._h, ctypes.byref(s)), "gca_h2_column_stats")
+        return {name: getattr(s, name) for name, _ in _ColStats._fields_}
+
+    def export_columns(self):
+        """Host copy of the column side: rank (r'), pivots, W (leaf column
+        bases) and F (column transfers) (gca_h2_export_columns)."""
+        s = self.stats()
+        c = self.column_stats()
+        d = {"rank": np.zeros(s["nclusters"], dtype=np.int32),
+             "pivots": np.zeros(max(c["rank_sum"], 1), dtype=np.int32),
+             "W": np.zeros(max(c["w_entries"], 1)), "F": np.zeros(max(c["f_entries"], 1))}
+        dump = _Dump(d["rank"].ctypes.data_as(_i32p), d["pivots"].ctypes.data_as(_i32p), None, None,
+                     d["W"].ctypes.data_as(_f64p), d["F"].ctypes.data_as(_f64p), None, None)
+        _check(lib.gca_h2_export_columns(self._h, ctypes.byref(dump)), "gca_h2_export_columns")
+        d["pivots"] = d["pivots"][:c["rank_sum"]]
+        d["W"] = d["W"][:c["w_entries"]]
+        d["F"] = d["F"][:c["f_entries"]]
+        return d
+
     def matvec_raw(self, prec, nrhs, x_ptr, ldx, y_ptr, ldy, stream_ptr, transpose=False):
         fn = lib.h2_matvec_transpose if transpose else lib.h2_matvec
         _check(fn(self._h, _PREC.get(prec, prec), nrhs, x_ptr, ldx, y_ptr, ldy, stream_ptr),
@@ -394,6 +425,18 @@ def import_h2(tree, n, rep, flags=0, stream=None):
 def test_hook(name, value):
     """Set a failure-path test hook (gca_test_hook)."""
     _check(lib.gca_test_hook(name.encode(), int(value)), "gca_test_hook")
+
+
+def build_double_layer(vertices, triangles, tree, params, stream=None):
+    """gca_build_double_layer on the current CUDA device; returns an ``H2``
+    whose products apply the double-layer matrix K (and K^T)."""
+    m, keep_m = _mesh(vertices, triangles)
+    t, keep_t = _tree(tree)
+    p = params._c()
+    h = ctypes.c_void_p(None)
+    _check(lib.gca_build_double_layer(ctypes.byref(m), ctypes.byref(t), ctypes.byref(p), _stream_ptr(stream),
+                                      ctypes.byref(h)), "gca_build_double_layer")
+    return H2(h.value)
 
 
 def _as_colmajor(x, dt):

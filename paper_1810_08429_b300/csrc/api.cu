@@ -66,6 +66,83 @@ int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* para
   }
 }
 
+int gca_build_double_layer(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params, void* stream,
+                           gca_h2** out) {
+  if (!out) {
+    gca::set_error("gca_build_double_layer: out is NULL");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    return gca::build(mesh, tree, params, static_cast<cudaStream_t>(stream), out, 1);
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_build_double_layer: host allocation failed");
+    return GCA_ERR_OOM;
+  }
+}
+
+int gca_h2_column_stats(const gca_h2* h, gca_column_stats* o) {
+  if (!h || !o) {
+    gca::set_error("gca_h2_column_stats: NULL argument");
+    return GCA_ERR_INVALID_ARG;
+  }
+  std::memset(o, 0, sizeof(*o));
+  o->op = h->op;
+  if (h->op == 1) {
+    o->max_rank = h->max_rank2;
+    o->rank_sum = h->rank_sum2;
+    o->w_entries = h->w_entries;
+    o->f_entries = h->f_entries;
+  } else {
+    o->max_rank = h->max_rank;
+    o->rank_sum = h->rank_sum;
+    o->w_entries = h->v_entries;
+    o->f_entries = h->e_entries;
+  }
+  return GCA_OK;
+}
+
+int gca_h2_export_columns(const gca_h2* h, gca_host_dump* o) {
+  if (!h || !o) {
+    gca::set_error("gca_h2_export_columns: NULL argument");
+    return GCA_ERR_INVALID_ARG;
+  }
+  if (h->op != 1) {
+    // one basis serves rows and columns
+    gca_host_dump d{o->rank, o->pivots, nullptr, nullptr, o->V, o->E, nullptr, nullptr};
+    return gca_h2_export(h, &d);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    gca::set_error("gca_h2_export_columns: device error before export");
+    return GCA_ERR_CUDA;
+  }
+  if (o->far || o->near || o->S || o->N) {
+    gca::set_error("gca_h2_export_columns: far, near, S and N belong to gca_h2_export");
+    return GCA_ERR_INVALID_ARG;
+  }
+  if (o->rank) std::memcpy(o->rank, h->rank2.data(), sizeof(int) * h->nc);
+  if (o->pivots) {
+    int64_t at = 0;
+    for (int c = 0; c < h->nc; ++c)
+      for (int t = 0; t < h->rank2[c]; ++t) o->pivots[at++] = h->piv2[h->poff2[c] + t];
+  }
+  if ((h->params.flags & GCA_DROP_EXPORT) && (o->V || o->E)) {
+    gca::set_error("gca_h2_export_columns: the handle was built with GCA_DROP_EXPORT");
+    return GCA_ERR_UNSUPPORTED;
+  }
+  struct Item { double* dst; const gca::DevMem* src; int64_t n; };
+  const Item items[2] = {{o->V, &h->W64, h->w_entries}, {o->E, &h->F64, h->f_entries}};
+  for (const auto& it : items)
+    if (it.dst && it.n > 0) {
+      cudaError_t e = cudaMemcpy(it.dst, it.src->p, sizeof(double) * it.n, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        gca::set_error(std::string("gca_h2_export_columns: ") + cudaGetErrorString(e));
+        return GCA_ERR_CUDA;
+      }
+    }
+  return GCA_OK;
+}
+
 int h2_matvec(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x, int64_t ldx, void* y,
               int64_t ldy, void* stream) {
   return gca::matvec(h, prec, false, nrhs, x, ldx, y, ldy, static_cast<cudaStream_t>(stream));

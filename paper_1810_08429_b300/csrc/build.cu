@@ -54,7 +54,8 @@ constexpr int kStatusOverflow = 2;
 // ------------------------------------------------------------------ geometry
 
 __global__ void k_tri_geom(int nt, const double* __restrict__ vert, const int* __restrict__ tri,
-                           Rules rules, P4* __restrict__ tq, double* __restrict__ area2) {
+                           Rules rules, P4* __restrict__ tq, double* __restrict__ area2,
+                           double* __restrict__ nrm) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   const int ia = tri[3 * t], ib = tri[3 * t + 1], ic = tri[3 * t + 2];
@@ -71,6 +72,11 @@ __global__ void k_tri_geom(int nt, const double* __restrict__ vert, const int* _
   double cz = u[0] * v[1] - u[1] * v[0];
   const double a2 = sqrt(cx * cx + cy * cy + cz * cz);
   area2[t] = a2;  // |(b - a) x (c - a)|, the Jacobian of the parametrisations of T
+  if (nrm) {      // outer unit normal (the orientation of the stored vertex order)
+    nrm[3 * t] = cx / a2;
+    nrm[3 * t + 1] = cy / a2;
+    nrm[3 * t + 2] = cz / a2;
+  }
   double area = 0.5 * a2;
   for (int q = 0; q < 7; ++q) {
     double l0 = rules.bary[q][0], l1 = rules.bary[q][1], l2 = rules.bary[q][2];
@@ -181,7 +187,7 @@ struct AcaJob {
   int tbegin;     // leaf: first position in perm
   int r0;         // non-leaf: rank of child0 (its pivots come first)
   int mesh;       // entry of the launch's mesh table
-  int pad;
+  int kind;       // 0: Green matrix A_tau of the single layer; 1: column matrix of the double layer
   int64_t piv0;   // non-leaf: pivot pool offsets of the children
   int64_t piv1;
   int64_t vh_off; // V^ (rows x r, row-major) in the mesh's V^ pool
@@ -197,6 +203,7 @@ struct AcaMesh {
   int* piv_pool;
   double* vh_pool;
   int* rank_out;
+  const double* nrm;  // outer unit normals per triangle (column matrices of the double layer)
 };
 
 // Cross approximation of one job on a thread-block cluster of C CTAs (C = 1
@@ -370,14 +377,35 @@ k_aca(const AcaJob* __restrict__ jobs, const AcaMesh* __restrict__ meshes, int k
     const double sgn = (face & 1) ? 1.0 : -1.0;
     const P4* xq = M.tq + 7 * (int64_t)s_tri[i];
     double gs = 0.0, ds = 0.0;
+    if (job.kind == 0) {
+      // a_{i nu} = sqrt(w) int g(x, z) phi_i, a_{i nu+k} = -d sqrt(w) int dg/dn_z(x, z) phi_i
 #pragma unroll
-    for (int qq = 0; qq < 7; ++qq) {
-      const P4 x = xq[qq];
-      const double dx = x.x - zz.x, dy = x.y - zz.y, dz = x.z - zz.z;
-      const double ir = rsqrt(dx * dx + dy * dy + dz * dz);
-      const double dn = sgn * (d == 0 ? dx : (d == 1 ? dy : dz));
-      gs += x.w * ir;
-      ds += x.w * dn * ir * ir * ir;
+      for (int qq = 0; qq < 7; ++qq) {
+        const P4 x = xq[qq];
+        const double dx = x.x - zz.x, dy = x.y - zz.y, dz = x.z - zz.z;
+        const double ir = rsqrt(dx * dx + dy * dy + dz * dz);
+        const double dn = sgn * (d == 0 ? dx : (d == 1 ? dy : dz));
+        gs += x.w * ir;
+        ds += x.w * dn * ir * ir * ir;
+      }
+    } else {
+      // the double layer's column matrix: a'_{j nu} = sqrt(w) int dg/dn_y(y, z) phi_j,
+      // a'_{j nu+k} = -d sqrt(w) int d2g/dn_y dn_z(y, z) phi_j, with e = z - y,
+      // dg/dn_y = <n_y, e> / (4 pi r^3), d2g = (<n_y, n_z> / r^3 - 3 <n_y, e> <n_z, e> / r^5) / (4 pi)
+      const double* ny = M.nrm + 3 * (int64_t)s_tri[i];
+      const double n0 = ny[0], n1 = ny[1], n2 = ny[2];
+      const double nn = sgn * (d == 0 ? n0 : (d == 1 ? n1 : n2));
+#pragma unroll
+      for (int qq = 0; qq < 7; ++qq) {
+        const P4 y = xq[qq];
+        const double ex = zz.x - y.x, ey = zz.y - y.y, ez = zz.z - y.z;
+        const double ir = rsqrt(ex * ex + ey * ey + ez * ez);
+        const double ir3 = ir * ir * ir;
+        const double nye = n0 * ex + n1 * ey + n2 * ez;
+        const double nze = sgn * (d == 0 ? ex : (d == 1 ? ey : ez));
+        gs += y.w * nye * ir3;
+        ds += y.w * (nn - 3.0 * nye * nze * ir * ir) * ir3;
+      }
     }
     S[(int64_t)i * k2 + nu] = zz.w * gs * kInv4Pi;
     S[(int64_t)i * k2 + k + nu] = -job.diam * zz.w * ds * kInv4Pi;
@@ -796,7 +824,8 @@ void for_each_panel(const gca_h2* h, F&& f) {
     }
   }
   for (int b = 0; b < nfar; ++b) {
-    const int rt = h->rank[h->far_t[b]], rs = h->rank[h->far_s[b]];
+    const int rt = h->rank[h->far_t[b]];
+    const int rs = h->op == 1 ? h->rank2[h->far_s[b]] : h->rank[h->far_s[b]];  // r'_sigma: column bases
     f(kS, b, rt, rs, 0);
     f(kSt, b, rs, rt, 1);
   }
@@ -806,6 +835,20 @@ void for_each_panel(const gca_h2* h, F&& f) {
     f(kN, b, mt, ms, 0);
     f(kNt, b, ms, mt, 1);
   }
+  if (h->op != 1) return;
+  // column bases W and transfers F (their own ranks r')
+  for (int c = 1; c < nc; ++c) {
+    if (h->child0[c] < 0) {
+      const int nr = h->end[c] - h->begin[c], r = h->rank2[c];
+      f(kW, c, nr, r, 0);
+      f(kWt, c, r, nr, 1);
+    }
+    if (h->parent[c] > 0) {
+      const int r = h->rank2[c], rp = h->rank2[h->parent[c]];
+      f(kF, c, r, rp, 0);
+      f(kFt, c, rp, r, 1);
+    }
+  }
 }
 
 // Element offsets of every block in its panel array (the same for all
@@ -813,7 +856,7 @@ void for_each_panel(const gca_h2* h, F&& f) {
 void layout_panels(gca_h2* h) {
   const int nc = h->nc;
   const int nfar = (int)h->far_t.size(), nnear = (int)h->near_t.size();
-  const int count[kPanelKinds] = {nc, nc, nc, nc, nfar, nfar, nnear, nnear};
+  const int count[kPanelKinds] = {nc, nc, nc, nc, nfar, nfar, nnear, nnear, nc, nc, nc, nc};
   for (int q = 0; q < kPanelKinds; ++q) {
     h->panel_off[q].assign(count[q], -1);
     h->psize[q] = 0;
@@ -867,7 +910,9 @@ int make_panels(gca_h2* h, DevMem& jobs_buf, std::vector<PanelJob>& host_jobs, c
       const int64_t src = (kind == kV || kind == kVt)   ? h->voff[idx]
                           : (kind == kE || kind == kEt) ? h->eoff[idx]
                           : (kind == kS || kind == kSt) ? h->soff[idx]
-                                                        : h->noff[idx];
+                          : (kind == kN || kind == kNt) ? h->noff[idx]
+                          : (kind == kW || kind == kWt) ? h->voff2[idx]
+                                                        : h->eoff2[idx];
       host_jobs.push_back({src, h->panel_off[kind][idx], m, k, trans, 0});
     });
     first[q + 1] = (int64_t)host_jobs.size();
@@ -879,8 +924,8 @@ int make_panels(gca_h2* h, DevMem& jobs_buf, std::vector<PanelJob>& host_jobs, c
   if (host_jobs.empty()) return GCA_OK;
   GCA_TRY_CUDA(cudaMemcpyAsync(jobs_buf.p, host_jobs.data(), sizeof(PanelJob) * host_jobs.size(),
                                cudaMemcpyHostToDevice, st));
-  const DevMem* srcs[kPanelKinds] = {&h->V64, &h->V64, &h->E64, &h->E64,
-                                     &h->S64, &h->S64, &h->N64, &h->N64};
+  const DevMem* srcs[kPanelKinds] = {&h->V64, &h->V64, &h->E64, &h->E64, &h->S64, &h->S64,
+                                     &h->N64, &h->N64, &h->W64, &h->W64, &h->F64, &h->F64};
   for (int q = 0; q < kPanelKinds; ++q) {
     bool k64, k32, k16;
     panel_precisions(h, q, k64, k32, k16);
@@ -1303,6 +1348,204 @@ __global__ void k_singular(const SingularItem* __restrict__ items,
   if (lane == 0) N[it.pos] = acc * area2[it.ti] * area2[it.tj] * (kInv4Pi / 3.0);
 }
 
+// ------------------------------------------------ double-layer entries
+//
+// k_ij = int_{T_i} int_{T_j} dg/dn_y(x, y) dy dx with dg/dn_y(x, y) =
+// <n_j, x - y> / (4 pi |x - y|^3), n_j the outer unit normal of T_j (the
+// kernel of the integral equation of Sect. 1), in float64: the 7 x 7 rule for
+// disjoint pairs, 0 for identical (flat) triangles, the Sauter-Schwab
+// substitutions for a common edge or vertex.
+
+__device__ __forceinline__ double dl_regular_entry(const P4* __restrict__ xq, const P4* __restrict__ yq,
+                                                   double n0, double n1, double n2) {
+  double s = 0.0;
+#pragma unroll 1
+  for (int p = 0; p < 7; ++p) {
+    const P4 x = xq[p];
+    double sp = 0.0;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const P4 y = yq[q];
+      const double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+      const double ir = rsqrt(dx * dx + dy * dy + dz * dz);
+      sp += y.w * (n0 * dx + n1 * dy + n2 * dz) * ir * ir * ir;
+    }
+    s += x.w * sp;
+  }
+  return s * kInv4Pi;
+}
+
+// One CTA per coupling block (tau, sigma): K|tilde-tau x tilde-sigma', the
+// row pivots of tau against the column pivots of sigma (r_tau x r'_sigma,
+// row-major).  K is not symmetric, so every block is computed.
+__global__ void k_dl_couple(const int* __restrict__ far_t, const int* __restrict__ far_s,
+                            const int64_t* __restrict__ soff, const int* __restrict__ rank,
+                            const int* __restrict__ rank2, const int64_t* __restrict__ poff,
+                            const int64_t* __restrict__ poff2, const int* __restrict__ piv,
+                            const int* __restrict__ piv2, const P4* __restrict__ tq,
+                            const double* __restrict__ nrm, double* __restrict__ S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  const int t = far_t[b], s = far_s[b];
+  const int rt = rank[t], rs = rank2[s];
+  P4* ys = reinterpret_cast<P4*>(smem_raw);
+  double* yn = reinterpret_cast<double*>(ys + 7 * (size_t)rs);
+  const int* pt = piv + poff[t];
+  const int* ps = piv2 + poff2[s];
+  for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) ys[i] = tq[7 * (int64_t)ps[i / 7] + i % 7];
+  for (int i = threadIdx.x; i < rs * 3; i += blockDim.x) yn[i] = nrm[3 * (int64_t)ps[i / 3] + i % 3];
+  __syncthreads();
+  double* out = S + soff[b];
+  for (int idx = threadIdx.x; idx < rt * rs; idx += blockDim.x) {
+    const int a = idx / rs, c = idx - (idx / rs) * rs;
+    out[idx] = dl_regular_entry(tq + 7 * (int64_t)pt[a], ys + 7 * c, yn[3 * c], yn[3 * c + 1], yn[3 * c + 2]);
+  }
+}
+
+// One CTA per near block of the double layer: disjoint pairs by the 7 x 7
+// rule, identical triangles 0, pairs with a common edge or vertex appended to
+// the list of their case (1 vertex, 2 edge).
+__global__ void k_dl_near_entries(const int* __restrict__ near_t, const int* __restrict__ near_s,
+                                  const int64_t* __restrict__ noff, const int* __restrict__ begin,
+                                  const int* __restrict__ end, const int* __restrict__ perm,
+                                  const int* __restrict__ tri, const P4* __restrict__ tq,
+                                  const double* __restrict__ nrm, double* __restrict__ N,
+                                  SingularItem* __restrict__ lists, int64_t cap,
+                                  unsigned long long* __restrict__ counts, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  const int t = near_t[b], s = near_s[b];
+  const int bt = begin[t], nt = end[t] - bt, bs = begin[s], ns = end[s] - bs;
+  P4* ys = reinterpret_cast<P4*>(smem_raw);
+  double* yn = reinterpret_cast<double*>(ys + 7 * (size_t)ns);
+  for (int i = threadIdx.x; i < ns * 7; i += blockDim.x) ys[i] = tq[7 * (int64_t)perm[bs + i / 7] + i % 7];
+  for (int i = threadIdx.x; i < ns * 3; i += blockDim.x) yn[i] = nrm[3 * (int64_t)perm[bs + i / 3] + i % 3];
+  __syncthreads();
+  const int64_t base = noff[b];
+  for (int idx = threadIdx.x; idx < nt * ns; idx += blockDim.x) {
+    const int i = idx / ns, j = idx - (idx / ns) * ns;
+    const int ti = perm[bt + i], tj = perm[bs + j];
+    int shared = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int va = tri[3 * ti + a];
+      shared += (va == tri[3 * tj]) + (va == tri[3 * tj + 1]) + (va == tri[3 * tj + 2]);
+    }
+    if (shared == 0) {
+      N[base + idx] = dl_regular_entry(tq + 7 * (int64_t)ti, ys + 7 * j, yn[3 * j], yn[3 * j + 1], yn[3 * j + 2]);
+    } else if (shared == 3) {
+      N[base + idx] = 0.0;  // x - y lies in the plane of T_j
+      atomicAdd(&counts[3], 1ull);
+    } else {
+      const unsigned long long slot = atomicAdd(&counts[shared], 1ull);
+      if (slot < (unsigned long long)cap) {
+        lists[(shared - 1) * cap + slot] = SingularItem{base + idx, ti, tj};
+      } else {
+        atomicOr(status, kStatusOverflow);
+      }
+    }
+  }
+}
+
+// A Sauter-Schwab sample of the double layer in float64: the coefficients of
+// h(eta) = (x - y) / xi in the edge vectors (as in SSEntry) and the weight
+// (Gauss weights times the piece's Jacobian without xi^3).
+struct __align__(16) SSEntry64 {
+  double c[4];
+  double w;
+  double pad;
+};
+
+template <int CASE>
+void sauter_table64(const Rules& rules, std::vector<SSEntry64>& out) {
+  const int q = rules.q, q3 = q * q * q;
+  constexpr int pieces = CASE == 2 ? 5 : 2;
+  for (int s = 0; s < pieces * q3; ++s) {
+    const int piece = s / q3, r = s % q3;
+    const int a = r / (q * q), b = (r / q) % q, c = r % q;
+    long double u1, u2, v1, v2;
+    const long double wj = sauter_piece<CASE, long double>(piece, rules.ss_t[a], rules.ss_t[b], rules.ss_t[c],
+                                                           u1, u2, v1, v2);
+    SSEntry64 e{};
+    if (CASE == 1) {
+      e.c[0] = (double)u1; e.c[1] = (double)u2; e.c[2] = (double)-v1; e.c[3] = (double)-v2;
+    } else {
+      e.c[0] = (double)(u1 - v1); e.c[1] = (double)u2; e.c[2] = (double)-v2; e.c[3] = 0.0;
+    }
+    e.w = (double)((long double)rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * wj);
+    out.push_back(e);
+  }
+}
+
+// one warp per pair with a common vertex (CASE 1) or edge (CASE 2): on each
+// piece x - y = xi h(eta), the kernel times the Jacobian xi^3 is
+// xi <n_j, h> / |h|^3, so the xi-integral is exactly 1/2 and eta is sampled
+template <int CASE>
+__global__ void k_dl_singular(const SingularItem* __restrict__ items,
+                              const unsigned long long* __restrict__ counts, int64_t cap,
+                              const int* __restrict__ tri, const double* __restrict__ vert,
+                              const double* __restrict__ area2, const double* __restrict__ nrm,
+                              const SSEntry64* __restrict__ table, int nsamples, double* __restrict__ N) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t count = min((long long)counts[CASE], (long long)cap);
+  if (w >= count) return;
+  const SingularItem it = items[w];
+  int ti[3], tj[3];
+  for (int a = 0; a < 3; ++a) {
+    ti[a] = tri[3 * it.ti + a];
+    tj[a] = tri[3 * it.tj + a];
+  }
+  int P[3], Q[3];
+  if (CASE == 2) {
+    int sh[2], ns = 0, oi = -1, oj = -1;
+    for (int a = 0; a < 3; ++a) {
+      const bool in_j = ti[a] == tj[0] || ti[a] == tj[1] || ti[a] == tj[2];
+      if (in_j) sh[ns++] = ti[a]; else oi = ti[a];
+    }
+    for (int a = 0; a < 3; ++a)
+      if (tj[a] != sh[0] && tj[a] != sh[1]) oj = tj[a];
+    P[0] = Q[0] = sh[0];
+    P[1] = Q[1] = sh[1];
+    P[2] = oi;
+    Q[2] = oj;
+  } else {
+    int pi = 0, pj = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (ti[a] == tj[b]) { pi = a; pj = b; }
+    for (int a = 0; a < 3; ++a) {
+      P[a] = ti[(pi + a) % 3];
+      Q[a] = tj[(pj + a) % 3];
+    }
+  }
+  // edge vectors: case 1 e1, e2, f1, f2; case 2 e1, e2, f2 (f1 = e1)
+  double V[4][3];
+  for (int d = 0; d < 3; ++d) {
+    V[0][d] = vert[3 * P[1] + d] - vert[3 * P[0] + d];
+    V[1][d] = vert[3 * P[2] + d] - vert[3 * P[1] + d];
+    if (CASE == 1) {
+      V[2][d] = vert[3 * Q[1] + d] - vert[3 * Q[0] + d];
+      V[3][d] = vert[3 * Q[2] + d] - vert[3 * Q[1] + d];
+    } else {
+      V[2][d] = vert[3 * Q[2] + d] - vert[3 * Q[1] + d];
+      V[3][d] = 0.0;
+    }
+  }
+  const double n0 = nrm[3 * (int64_t)it.tj], n1 = nrm[3 * (int64_t)it.tj + 1], n2 = nrm[3 * (int64_t)it.tj + 2];
+  double acc = 0.0;
+  for (int s = lane; s < nsamples; s += 32) {
+    const SSEntry64 e = table[s];
+    double h[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) h[d] = e.c[0] * V[0][d] + e.c[1] * V[1][d] + e.c[2] * V[2][d] + e.c[3] * V[3][d];
+    const double ir = rsqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    acc += e.w * (n0 * h[0] + n1 * h[1] + n2 * h[2]) * ir * ir * ir;
+  }
+  for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) N[it.pos] = acc * area2[it.ti] * area2[it.tj] * (kInv4Pi / 2.0);
+}
+
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 int check_status(DevMem& st, cudaStream_t s, const char* where) {
@@ -1409,7 +1652,7 @@ class AcaLauncher {
 
 // The whole construction; see the header of this file.
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
-          gca_h2** out) {
+          gca_h2** out, int op) {
   auto t0 = std::chrono::steady_clock::now();
   GCA_TRY(validate_mesh(mesh));
   GCA_TRY(validate_tree(mesh, tree, GCA_MAX_LEAF));
@@ -1423,6 +1666,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   auto h = std::make_unique<gca_h2>();
   GCA_TRY_CUDA(cudaGetDevice(&h->device));
   h->device += test_hooks().device_skew;
+  h->op = op;
   h->params = *prm;
   h->n = mesh->nt;
   h->nv = mesh->nv;
@@ -1460,8 +1704,9 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY(upload(h->d_perm, h->perm, st));
   GCA_TRY(upload(h->d_begin, h->begin, st));
   GCA_TRY(upload(h->d_end, h->end, st));
-  DevMem d_tq, d_area2, d_box, d_diam, d_zq, d_status;
+  DevMem d_tq, d_area2, d_box, d_diam, d_zq, d_status, d_nrm;
   GCA_TRY(d_tq.alloc(sizeof(P4) * 7 * (size_t)n));
+  if (op == 1) GCA_TRY(d_nrm.alloc(sizeof(double) * 3 * (size_t)n));
   GCA_TRY(d_area2.alloc(sizeof(double) * (size_t)n));
   GCA_TRY(d_box.alloc(sizeof(double) * 6 * (size_t)nc));
   GCA_TRY(d_status.alloc(sizeof(int)));
@@ -1469,7 +1714,8 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   {
     PhaseScope ps__("tri_geom", st);
     k_tri_geom<<<blocks_for(n, 128), 128, 0, st>>>(n, h->d_vert.as<double>(), h->d_tri.as<int>(), rules,
-                                                  d_tq.as<P4>(), d_area2.as<double>());
+                                                  d_tq.as<P4>(), d_area2.as<double>(),
+                                                  op == 1 ? d_nrm.as<double>() : nullptr);
   }
   {
     PhaseScope ps__("cluster_boxes", st);
@@ -1528,128 +1774,159 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     for (int c : h->by_level[L])
       if (needed[c] && h->child0[c] >= 0) needed[h->child0[c]] = needed[h->child1[c]] = 1;
 
-  // nested bases, level by level from the deepest
-  h->rank.assign(nc, 0);
-  h->poff.assign(nc, -1);
-  std::vector<int64_t> vh_off(nc, -1);
-  std::vector<int> rows_of(nc, 0);
-  int64_t piv_cap = 0, vh_cap = 0;
-  for (int c = 1; c < nc; ++c) {
-    // upper bounds, refined per level below
-    piv_cap += std::min<int64_t>(h->end[c] - h->begin[c], 2 * k);
-  }
-  DevMem d_piv, d_rank, d_vh, d_jobs, d_mesh;
-  GCA_TRY(d_piv.alloc(sizeof(int) * (size_t)std::max<int64_t>(piv_cap, 1)));
-  GCA_TRY(d_rank.alloc(sizeof(int) * (size_t)nc));
-  GCA_TRY_CUDA(cudaMemsetAsync(d_rank.p, 0, sizeof(int) * nc, st));
-  // V^ pool: rows <= min(|tau-hat|, 4k) for every cluster bounds its size
-  int64_t piv_used = 0, vh_used = 0;
-  for (int c = 1; c < nc; ++c) {
-    int64_t rows = h->child0[c] < 0 ? (h->end[c] - h->begin[c])
-                                    : std::min<int64_t>(h->end[c] - h->begin[c], 4 * k);
-    vh_cap += rows * std::min<int64_t>(rows, 2 * k);
-  }
-  GCA_TRY(d_vh.alloc(sizeof(double) * (size_t)std::max<int64_t>(vh_cap, 1)));
-  {
-    const AcaMesh am{h->d_perm.as<int>(), d_tq.as<P4>(), d_zq.as<P4>(), d_piv.as<int>(), d_vh.as<double>(),
-                     d_rank.as<int>()};
-    GCA_TRY(d_mesh.alloc(sizeof(AcaMesh)));
-    GCA_TRY_CUDA(cudaMemcpyAsync(d_mesh.p, &am, sizeof(AcaMesh), cudaMemcpyHostToDevice, st));
-    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // am is a local
-  }
+  // Nested bases, level by level from the deepest (kind 0: the cluster bases
+  // V, E of the rows from A_tau; kind 1: the double layer's column bases W, F
+  // from its column matrix): ranks, pivots in the pool d_piv (offsets poff),
+  // and the row-major float64 leaf bases and transfer matrices.
   AcaLauncher aca;
   GCA_TRY(aca.init(k));
   const double tie = std::ldexp(1.0, -40);
-  for (int L = h->depth; L >= 1; --L) {
-    std::vector<AcaJob> jobs;
-    for (int c : h->by_level[L]) {
-      if (!needed[c]) continue;
-      AcaJob j{};
-      j.c = c;
-      j.leaf = h->child0[c] < 0;
-      if (j.leaf) {
-        j.rows = h->end[c] - h->begin[c];
-        j.tbegin = h->begin[c];
+  struct BasisOut {
+    std::vector<int>* rank;
+    std::vector<int64_t>* poff;
+    std::vector<int64_t>* voff;
+    std::vector<int64_t>* eoff;
+    int64_t* v_entries;
+    int64_t* e_entries;
+    DevMem* V64;
+    DevMem* E64;
+  };
+  auto nested_bases = [&](int kind, const BasisOut& o, DevMem& d_piv, DevMem& d_rank, int64_t& piv_used) -> int {
+    std::vector<int>& rank = *o.rank;
+    std::vector<int64_t>& poff = *o.poff;
+    rank.assign(nc, 0);
+    poff.assign(nc, -1);
+    std::vector<int64_t> vh_off(nc, -1);
+    std::vector<int> rows_of(nc, 0);
+    int64_t piv_cap = 0, vh_cap = 0;
+    for (int c = 1; c < nc; ++c) {
+      // upper bounds, refined per level below
+      piv_cap += std::min<int64_t>(h->end[c] - h->begin[c], 2 * k);
+    }
+    DevMem d_vh, d_jobs, d_mesh;
+    GCA_TRY(d_piv.alloc(sizeof(int) * (size_t)std::max<int64_t>(piv_cap, 1)));
+    GCA_TRY(d_rank.alloc(sizeof(int) * (size_t)nc));
+    GCA_TRY_CUDA(cudaMemsetAsync(d_rank.p, 0, sizeof(int) * nc, st));
+    // V^ pool: rows <= min(|tau-hat|, 4k) for every cluster bounds its size
+    int64_t vh_used = 0;
+    piv_used = 0;
+    for (int c = 1; c < nc; ++c) {
+      int64_t rows = h->child0[c] < 0 ? (h->end[c] - h->begin[c])
+                                      : std::min<int64_t>(h->end[c] - h->begin[c], 4 * k);
+      vh_cap += rows * std::min<int64_t>(rows, 2 * k);
+    }
+    GCA_TRY(d_vh.alloc(sizeof(double) * (size_t)std::max<int64_t>(vh_cap, 1)));
+    {
+      const AcaMesh am{h->d_perm.as<int>(), d_tq.as<P4>(), d_zq.as<P4>(), d_piv.as<int>(), d_vh.as<double>(),
+                       d_rank.as<int>(), d_nrm.as<double>()};
+      GCA_TRY(d_mesh.alloc(sizeof(AcaMesh)));
+      GCA_TRY_CUDA(cudaMemcpyAsync(d_mesh.p, &am, sizeof(AcaMesh), cudaMemcpyHostToDevice, st));
+      GCA_TRY_CUDA(cudaStreamSynchronize(st));  // am is a local
+    }
+    for (int L = h->depth; L >= 1; --L) {
+      std::vector<AcaJob> jobs;
+      for (int c : h->by_level[L]) {
+        if (!needed[c]) continue;
+        AcaJob j{};
+        j.c = c;
+        j.kind = kind;
+        j.leaf = h->child0[c] < 0;
+        if (j.leaf) {
+          j.rows = h->end[c] - h->begin[c];
+          j.tbegin = h->begin[c];
+        } else {
+          const int c0 = h->child0[c], c1 = h->child1[c];
+          j.r0 = rank[c0];
+          j.rows = j.r0 + rank[c1];
+          j.piv0 = poff[c0];
+          j.piv1 = poff[c1];
+        }
+        j.rmax = std::min(j.rows, 2 * k);
+        j.mesh = 0;
+        j.diam = diam[c];
+        j.p_off = piv_used;
+        poff[c] = piv_used;
+        piv_used += j.rmax;
+        j.vh_off = vh_used;
+        vh_off[c] = vh_used;
+        vh_used += (int64_t)j.rows * j.rmax;
+        rows_of[c] = j.rows;
+        jobs.push_back(j);
+      }
+      if (jobs.empty()) continue;
+      if (piv_used > piv_cap || vh_used > vh_cap) {
+        set_error("gca_build: internal pool bound exceeded");
+        return GCA_ERR_INVALID_ARG;
+      }
+      GCA_TRY(aca.launch(jobs, d_jobs, d_mesh.as<AcaMesh>(), L, prm->aca_tol, tie, d_status.as<int>(), st));
+      GCA_TRY(check_status(d_status, st, "cross approximation"));
+      GCA_TRY_CUDA(cudaMemcpyAsync(rank.data(), d_rank.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
+      GCA_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    // row-major leaf bases and transfer matrices from the V^ pool
+    o.voff->assign(nc, -1);
+    o.eoff->assign(nc, -1);
+    *o.v_entries = 0;
+    *o.e_entries = 0;
+    for (int c = 1; c < nc; ++c)
+      if (h->child0[c] < 0) {
+        (*o.voff)[c] = *o.v_entries;
+        *o.v_entries += (int64_t)(h->end[c] - h->begin[c]) * rank[c];
+      }
+    for (int c = 1; c < nc; ++c)
+      if (h->parent[c] > 0) {
+        (*o.eoff)[c] = *o.e_entries;
+        *o.e_entries += (int64_t)rank[c] * rank[h->parent[c]];
+      }
+    std::vector<Segment> vseg, eseg;
+    for (int c = 1; c < nc; ++c) {
+      const int r = rank[c];
+      if (r == 0) continue;  // unused basis
+      if (h->child0[c] < 0) {
+        vseg.push_back({vh_off[c], (*o.voff)[c], (int64_t)rows_of[c] * r});
       } else {
         const int c0 = h->child0[c], c1 = h->child1[c];
-        j.r0 = h->rank[c0];
-        j.rows = j.r0 + h->rank[c1];
-        j.piv0 = h->poff[c0];
-        j.piv1 = h->poff[c1];
+        eseg.push_back({vh_off[c], (*o.eoff)[c0], (int64_t)rank[c0] * r});
+        eseg.push_back({vh_off[c] + (int64_t)rank[c0] * r, (*o.eoff)[c1], (int64_t)rank[c1] * r});
       }
-      j.rmax = std::min(j.rows, 2 * k);
-      j.mesh = 0;
-      j.diam = diam[c];
-      j.p_off = piv_used;
-      h->poff[c] = piv_used;
-      piv_used += j.rmax;
-      j.vh_off = vh_used;
-      vh_off[c] = vh_used;
-      vh_used += (int64_t)j.rows * j.rmax;
-      rows_of[c] = j.rows;
-      jobs.push_back(j);
     }
-    if (jobs.empty()) continue;
-    if (piv_used > piv_cap || vh_used > vh_cap) {
-      set_error("gca_build: internal pool bound exceeded");
-      return GCA_ERR_INVALID_ARG;
+    GCA_TRY(o.V64->alloc(sizeof(double) * *o.v_entries));
+    GCA_TRY(o.E64->alloc(sizeof(double) * *o.e_entries));
+    DevMem d_seg;
+    for (auto* sv : {&vseg, &eseg}) {
+      if (sv->empty()) continue;
+      GCA_TRY(d_seg.reserve(sizeof(Segment) * sv->size()));
+      GCA_TRY_CUDA(cudaMemcpyAsync(d_seg.p, sv->data(), sizeof(Segment) * sv->size(),
+                                   cudaMemcpyHostToDevice, st));
+      const bool isv = sv == &vseg;
+      {
+        PhaseScope ps__("pack", st);
+        k_pack<<<(unsigned)sv->size(), 256, 0, st>>>(d_seg.as<Segment>(), d_vh.as<double>(),
+                                                     isv ? o.V64->as<double>() : o.E64->as<double>());
+      }
+      GCA_TRY_CUDA(cudaGetLastError());
+      GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_seg is reused
     }
-    GCA_TRY(aca.launch(jobs, d_jobs, d_mesh.as<AcaMesh>(), L, prm->aca_tol, tie, d_status.as<int>(), st));
-    GCA_TRY(check_status(d_status, st, "cross approximation"));
-    GCA_TRY_CUDA(cudaMemcpyAsync(h->rank.data(), d_rank.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
-    GCA_TRY_CUDA(cudaStreamSynchronize(st));
-  }
-
-  // offsets of the stored coefficients
+    return GCA_OK;
+  };
+  DevMem d_piv, d_rank, d_piv2, d_rank2;
+  int64_t piv_used = 0, piv2_used = 0;
+  GCA_TRY(nested_bases(0, BasisOut{&h->rank, &h->poff, &h->voff, &h->eoff, &h->v_entries, &h->e_entries, &h->V64,
+                                   &h->E64},
+                       d_piv, d_rank, piv_used));
   h->xoff.assign(nc + 1, 0);
   for (int c = 0; c < nc; ++c) h->xoff[c + 1] = h->xoff[c] + h->rank[c];
   h->rank_sum = h->xoff[nc];
   h->max_rank = *std::max_element(h->rank.begin(), h->rank.end());
-  h->voff.assign(nc, -1);
-  h->eoff.assign(nc, -1);
-  std::vector<Segment> segs;
-  for (int c = 1; c < nc; ++c) {
-    if (h->child0[c] < 0) {
-      h->voff[c] = h->v_entries;
-      const int64_t len = (int64_t)(h->end[c] - h->begin[c]) * h->rank[c];
-      h->v_entries += len;
-    }
+  if (op == 1) {
+    GCA_TRY(nested_bases(1, BasisOut{&h->rank2, &h->poff2, &h->voff2, &h->eoff2, &h->w_entries, &h->f_entries,
+                                     &h->W64, &h->F64},
+                         d_piv2, d_rank2, piv2_used));
+    h->xoff2.assign(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) h->xoff2[c + 1] = h->xoff2[c] + h->rank2[c];
+    h->rank_sum2 = h->xoff2[nc];
+    h->max_rank2 = *std::max_element(h->rank2.begin(), h->rank2.end());
   }
-  for (int c = 1; c < nc; ++c)
-    if (h->parent[c] > 0) {
-      h->eoff[c] = h->e_entries;
-      h->e_entries += (int64_t)h->rank[c] * h->rank[h->parent[c]];
-    }
-  std::vector<Segment> vseg, eseg;
-  for (int c = 1; c < nc; ++c) {
-    const int r = h->rank[c];
-    if (r == 0) continue;  // unused basis
-    if (h->child0[c] < 0) {
-      vseg.push_back({vh_off[c], h->voff[c], (int64_t)rows_of[c] * r});
-    } else {
-      const int c0 = h->child0[c], c1 = h->child1[c];
-      eseg.push_back({vh_off[c], h->eoff[c0], (int64_t)h->rank[c0] * r});
-      eseg.push_back({vh_off[c] + (int64_t)h->rank[c0] * r, h->eoff[c1], (int64_t)h->rank[c1] * r});
-    }
-  }
-  GCA_TRY(h->V64.alloc(sizeof(double) * h->v_entries));
-  GCA_TRY(h->E64.alloc(sizeof(double) * h->e_entries));
-  DevMem d_seg;
-  for (auto* sv : {&vseg, &eseg}) {
-    if (sv->empty()) continue;
-    GCA_TRY(d_seg.reserve(sizeof(Segment) * sv->size()));
-    GCA_TRY_CUDA(cudaMemcpyAsync(d_seg.p, sv->data(), sizeof(Segment) * sv->size(),
-                                 cudaMemcpyHostToDevice, st));
-    const bool isv = sv == &vseg;
-    {
-      PhaseScope ps__("pack", st);
-      k_pack<<<(unsigned)sv->size(), 256, 0, st>>>(
-          d_seg.as<Segment>(), d_vh.as<double>(), isv ? h->V64.as<double>() : h->E64.as<double>());
-    }
-    GCA_TRY_CUDA(cudaGetLastError());
-    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_seg is reused
-  }
-  d_vh.release();
 
   // Offsets of the coupling and near-field coefficients, the panel layout and
   // every device buffer of the rest of the build are set up first, so that
@@ -1659,11 +1936,19 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   h->piv.resize(std::max<int64_t>(piv_used, 1));
   GCA_TRY_CUDA(cudaMemcpyAsync(h->piv.data(), d_piv.p, sizeof(int) * piv_used, cudaMemcpyDeviceToHost, st));
   GCA_TRY(upload(h->d_rank, h->rank, st));
-  DevMem d_poff;
+  DevMem d_poff, d_poff2, d_rank2v;
   GCA_TRY(upload(d_poff, h->poff, st));
+  if (op == 1) {
+    h->piv2.resize(std::max<int64_t>(piv2_used, 1));
+    GCA_TRY_CUDA(cudaMemcpyAsync(h->piv2.data(), d_piv2.p, sizeof(int) * piv2_used, cudaMemcpyDeviceToHost, st));
+    GCA_TRY(upload(d_poff2, h->poff2, st));
+    GCA_TRY(upload(d_rank2v, h->rank2, st));
+  }
+  // coupling blocks: r_tau x r_sigma (single layer) or r_tau x r'_sigma (double layer)
+  const std::vector<int>& rcol = op == 1 ? h->rank2 : h->rank;
   h->soff.assign(nfar + 1, 0);
   for (int b = 0; b < nfar; ++b)
-    h->soff[b + 1] = h->soff[b] + (int64_t)h->rank[h->far_t[b]] * h->rank[h->far_s[b]];
+    h->soff[b + 1] = h->soff[b] + (int64_t)h->rank[h->far_t[b]] * rcol[h->far_s[b]];
   h->s_entries = h->soff[nfar];
   GCA_TRY(upload(h->d_far_t, h->far_t, st));
   GCA_TRY(upload(h->d_far_s, h->far_s, st));
@@ -1675,7 +1960,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // sigma); a block whose mirror is missing is computed alone
   std::vector<int2> pairs;
   pairs.reserve(nfar / 2 + 1);
-  for (int b = 0; b < nfar; ++b) {
+  for (int b = 0; b < nfar && op == 0; ++b) {
     const int t = h->far_t[b], s = h->far_s[b];
     int m = -1;
     {
@@ -1719,8 +2004,18 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   ss_off[2] = (int)ss.size();
   sauter_table<3>(rules, ss);
   ss_off[3] = (int)ss.size();
-  DevMem d_ss;
+  DevMem d_ss, d_ss64;
   GCA_TRY(upload(d_ss, ss, st));
+  // the double layer's samples in float64 (vertex, edge)
+  std::vector<SSEntry64> ss64;
+  int ss64_off[3] = {0, 0, 0};
+  if (op == 1) {
+    sauter_table64<1>(rules, ss64);
+    ss64_off[1] = (int)ss64.size();
+    sauter_table64<2>(rules, ss64);
+    ss64_off[2] = (int)ss64.size();
+    GCA_TRY(upload(d_ss64, ss64, st));
+  }
   GCA_TRY(d_counts.alloc(sizeof(unsigned long long) * 4));
   GCA_TRY_CUDA(cudaMemsetAsync(d_counts.p, 0, sizeof(unsigned long long) * 4, st));
   layout_panels(h.get());
@@ -1730,7 +2025,18 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY_CUDA(cudaStreamSynchronize(st));  // the host copy of the pivots
 
   // coupling matrices
-  if (nfar > 0) {
+  if (nfar > 0 && op == 1) {
+    const size_t smem = (sizeof(P4) * 7 + sizeof(double) * 3) * (size_t)std::max(h->max_rank2, 1);
+    GCA_TRY_CUDA(cudaFuncSetAttribute(k_dl_couple, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      PhaseScope ps__("dl_couple_entries", st);
+      k_dl_couple<<<(unsigned)nfar, 256, smem, st>>>(
+          h->d_far_t.as<int>(), h->d_far_s.as<int>(), h->d_soff.as<int64_t>(), h->d_rank.as<int>(),
+          d_rank2v.as<int>(), d_poff.as<int64_t>(), d_poff2.as<int64_t>(), d_piv.as<int>(), d_piv2.as<int>(),
+          d_tq.as<P4>(), d_nrm.as<double>(), h->S64.as<double>());
+    }
+    GCA_TRY_CUDA(cudaGetLastError());
+  } else if (nfar > 0) {
     const size_t smem = sizeof(SplitNode) * 7 * (size_t)std::max(h->max_rank, 1);
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_couple_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
@@ -1744,7 +2050,19 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   }
 
   // near field
-  if (nnear > 0) {
+  if (nnear > 0 && op == 1) {
+    const size_t smem = (sizeof(P4) * 7 + sizeof(double) * 3) * (size_t)h->max_leaf;
+    GCA_TRY_CUDA(cudaFuncSetAttribute(k_dl_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      PhaseScope ps__("dl_near_entries", st);
+      k_dl_near_entries<<<nnear, 256, smem, st>>>(
+          h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
+          h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), d_tq.as<P4>(), d_nrm.as<double>(),
+          h->N64.as<double>(), d_items.as<SingularItem>(), cap, d_counts.as<unsigned long long>(),
+          d_status.as<int>());
+    }
+    GCA_TRY_CUDA(cudaGetLastError());
+  } else if (nnear > 0) {
     const size_t smem = (sizeof(P4) + sizeof(SplitNode)) * 7 * (size_t)h->max_leaf;
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
@@ -1779,6 +2097,16 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     const double* vert_d = h->d_vert.as<double>();
     const double* a2 = d_area2.as<double>();
     double* N64 = h->N64.as<double>();
+    if (op == 1) {
+      const SSEntry64* tab64 = d_ss64.as<SSEntry64>();
+      if (counts[1])
+        k_dl_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
+            items, cnt, cap, tri_d, vert_d, a2, d_nrm.as<double>(), tab64, ss64_off[1], N64);
+      if (counts[2])
+        k_dl_singular<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
+            items + cap, cnt, cap, tri_d, vert_d, a2, d_nrm.as<double>(), tab64 + ss64_off[1],
+            ss64_off[2] - ss64_off[1], N64);
+    } else {
     if (counts[1])
       k_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
           items, cnt, cap, tri_d, vert_d, a2, tab + ss_off[0], ss_off[1] - ss_off[0], N64);
@@ -1788,6 +2116,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     if (counts[3])
       k_singular<3><<<blocks_for(32LL * counts[3], 256), 256, 0, st>>>(
           items + 2 * cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[2], ss_off[3] - ss_off[2], N64);
+    }
     GCA_TRY_CUDA(cudaGetLastError());
   }
 
@@ -1807,6 +2136,8 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     h->E64.release();
     h->S64.release();
     h->N64.release();
+    h->W64.release();
+    h->F64.release();
   }
   h->build_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

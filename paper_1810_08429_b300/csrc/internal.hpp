@@ -17,8 +17,9 @@ struct gca_h2_batch;
 namespace gca {
 
 // Stored blocks in panel layout: leaf bases, transfers, couplings, near field,
-// each also transposed.
-enum PanelKind { kV = 0, kVt, kE, kEt, kS, kSt, kN, kNt, kPanelKinds };
+// each also transposed; the column bases and transfers of an operator whose
+// columns have bases of their own (the double layer).
+enum PanelKind { kV = 0, kVt, kE, kEt, kS, kSt, kN, kNt, kW, kWt, kF, kFt, kPanelKinds };
 
 // Last error text of the calling thread (returned by gca_last_error()).
 void set_error(const std::string& msg);
@@ -127,8 +128,9 @@ class PhaseScope {
 };
 
 // Entry points of the translation units.
+// op 0: the single-layer matrix G; op 1: the double-layer matrix K
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
-          gca_h2** out);
+          gca_h2** out, int op = 0);
 // Product plan (matvec.cu): plan_direction runs the host planning of one
 // direction (it needs the ranks, block lists and panel offsets; the build
 // calls it while its kernels run); finish_plan plans what is left and
@@ -254,6 +256,30 @@ struct gca_h2 {
   mutable gca::DevMem d_status;  // sticky error bits of the products
   int max_rows = 0;              // largest block dimension (bounds the staged X)
   int device = -1;               // ordinal of the device that holds the handle's memory
+
+  // The operator: 0 the single layer (one basis per cluster serves rows and
+  // columns), 1 the double layer (columns have bases W, transfers F and
+  // pivots tilde-sigma' of their own; the couplings are r_tau x r'_sigma).
+  int op = 0;
+  std::vector<int> rank2;              // r'_sigma (op 1)
+  std::vector<int64_t> xoff2;
+  int64_t rank_sum2 = 0;
+  int max_rank2 = 0;
+  std::vector<int> piv2;
+  std::vector<int64_t> poff2, voff2, eoff2;
+  int64_t w_entries = 0, f_entries = 0;
+  gca::DevMem W64, F64;                // row-major float64, as exported
+
+  // the bases a product direction (0: G x, 1: G^T x) transforms its input
+  // with and returns its output through
+  bool in_cols(int dir) const { return op == 1 && dir == 0; }
+  bool out_cols(int dir) const { return op == 1 && dir == 1; }
+  const std::vector<int>& rank_in(int dir) const { return in_cols(dir) ? rank2 : rank; }
+  const std::vector<int>& rank_out(int dir) const { return out_cols(dir) ? rank2 : rank; }
+  const std::vector<int64_t>& xoff_in(int dir) const { return in_cols(dir) ? xoff2 : xoff; }
+  const std::vector<int64_t>& xoff_out(int dir) const { return out_cols(dir) ? xoff2 : xoff; }
+  int64_t rank_sum_in(int dir) const { return in_cols(dir) ? rank_sum2 : rank_sum; }
+  int64_t rank_sum_out(int dir) const { return out_cols(dir) ? rank_sum2 : rank_sum; }
 };
 
 // A batch of handles applied in one persistent launch.

@@ -106,7 +106,8 @@ struct SlotArgs {
   int R;
   int n;
   int rc;                      // RC: columns of a chunk
-  int rank_sum;                // rows of x-hat and y-hat
+  int rs_in;                   // rows of x-hat (the input side's bases)
+  int rs_out;                  // rows of y-hat (the output side's bases)
   const TV* x;                 // caller's x, original order, column-major
   int64_t ldx;
   TV* y;                       // caller's y, original order, column-major
@@ -118,7 +119,7 @@ struct SlotArgs {
   // contiguous (one bulk copy per input block, whatever R)
   const TV* xp;                // x in cluster order [nchunk][n][RC]
   TV* yp;                      // y in cluster order [nchunk][n][RC] (zeroed)
-  TV* xh;                      // [nchunk][rank_sum][RC]
+  TV* xh;                      // [nchunk][rs_in][RC]
   TV* yh;
   int* counters;               // [2 nc]
 };
@@ -971,7 +972,8 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
         const int xrow = __shfl_sync(FULL, d.x_row, s);
         // rows [xrow, xrow + k) of chunk c0 / RC of the input vector
         const TV* X = (xin == kInXh ? sa.xh : (xin == kInYh ? sa.yh : sa.xp)) +
-                      ((int64_t)(u.c0 / RC) * (xin == kInX ? sa.n : sa.rank_sum) + xrow) * RC;
+                      ((int64_t)(u.c0 / RC) * (xin == kInX ? sa.n : (xin == kInXh ? sa.rs_in : sa.rs_out)) +
+                       xrow) * RC;
         // rows past the block's columns meet zero panel columns (and, on the
         // tensor cores, the zeroed upper half of a last single panel): they
         // are copied in as zeros, so the buffer only ever gets bulk copies
@@ -1119,7 +1121,8 @@ __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
       const int o_row = __shfl_sync(FULL, d.o_row, s);
       // rows of this chunk of the output (chunk-major, RC columns a row; the
       // columns past R are padding that nothing reads)
-      TV* const ochunk = obase + (int64_t)(c0 / RC) * (out == kOutY ? sa.n : sa.rank_sum) * RC;
+      TV* const ochunk =
+          obase + (int64_t)(c0 / RC) * (out == kOutY ? sa.n : (out == kOutXh ? sa.rs_in : sa.rs_out)) * RC;
       if constexpr (kTC) {
         if (tc) {
           // accumulator fragments: rows 16 mt + g (+ 8), columns 8 nt + 2t (+ 1)
@@ -1420,23 +1423,32 @@ int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
   };
   const auto& O = h->panel_off;
   const int kCoupleSegs = 8, kNearSegs = 8;
+  // input side (forward transform) and output side (backward transform) of
+  // this direction: the cluster bases V, E, or the column bases W, F of an
+  // operator that has them
+  const auto& rin = h->rank_in(dir);
+  const auto& rout = h->rank_out(dir);
+  const auto& xin = h->xoff_in(dir);
+  const auto& xout = h->xoff_out(dir);
+  const int kLeafIn = h->in_cols(dir) ? kWt : kVt, kUpIn = h->in_cols(dir) ? kFt : kEt;
+  const int kDownOut = h->out_cols(dir) ? kF : kE, kLeafOut = h->out_cols(dir) ? kW : kV;
   // segments of the transforms (the critical path of the product): one tile
   // each, every tile of a transfer block in a group of its own, so that each
   // step of the tree recursion is spread over many warps
   const int kChainPiece = kChunk;
   // forward transform: leaves
   for (int c : h->leaves)
-    if (c > 0 && h->rank[c] > 0)
-      emit({{kVt, O[kVt][c], h->rank[c], h->end[c] - h->begin[c], h->begin[c], -1, 0}}, kInX, kOutXh,
-           h->xoff[c], h->rank[c], c, &cx[c], 1, kChainPiece);
+    if (c > 0 && rin[c] > 0)
+      emit({{kLeafIn, O[kLeafIn][c], rin[c], h->end[c] - h->begin[c], h->begin[c], -1, 0}}, kInX, kOutXh,
+           xin[c], rin[c], c, &cx[c], 1, kChainPiece);
   // forward transform: up the tree, deepest level first (one segment per group:
   // the chain is latency bound, so its work is spread over many warps)
   for (int L = h->depth - 1; L >= 1; --L)
     for (int p : h->by_level[L]) {
       if (h->child0[p] < 0) continue;
       for (int ch : {h->child0[p], h->child1[p]})
-        emit({{kEt, O[kEt][ch], h->rank[p], h->rank[ch], h->xoff[ch], ch, cx[ch]}}, kInXh, kOutXh,
-             h->xoff[p], h->rank[p], p, &cx[p], 1, kChainPiece);
+        emit({{kUpIn, O[kUpIn][ch], rin[p], rin[ch], xin[ch], ch, cx[ch]}}, kInXh, kOutXh, xin[p], rin[p], p,
+             &cx[p], 1, kChainPiece);
     }
   // coupling: per output cluster, its blocks (deepest input first) in groups
   // of a few segments; clusters deepest first, since their inputs are ready
@@ -1457,10 +1469,9 @@ int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
     std::vector<Blk> blks;
     for (int b : bl) {
       const int in = trans ? h->far_t[b] : h->far_s[b];
-      blks.push_back({trans ? kSt : kS, O[trans ? kSt : kS][b], h->rank[own], h->rank[in], h->xoff[in], in,
-                      cx[in]});
+      blks.push_back({trans ? kSt : kS, O[trans ? kSt : kS][b], rout[own], rin[in], xin[in], in, cx[in]});
     }
-    emit(blks, kInXh, kOutYh, h->xoff[own], h->rank[own], nc + own, &cy[own], kCoupleSegs, kChunk);
+    emit(blks, kInXh, kOutYh, xout[own], rout[own], nc + own, &cy[own], kCoupleSegs, kChunk);
   }
   {
     target = &free_groups;
@@ -1482,14 +1493,14 @@ int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
   for (int L = 2; L <= h->depth; ++L)
     for (int c : h->by_level[L]) {
       const int p = h->parent[c];
-      if (cy[p] == 0 || h->rank[c] == 0) continue;  // y-hat_p = 0
-      emit({{kE, O[kE][c], h->rank[c], h->rank[p], h->xoff[p], nc + p, cy[p]}}, kInYh, kOutYh,
-           h->xoff[c], h->rank[c], nc + c, &cy[c], 1, kChainPiece);
+      if (cy[p] == 0 || rout[c] == 0) continue;  // y-hat_p = 0
+      emit({{kDownOut, O[kDownOut][c], rout[c], rout[p], xout[p], nc + p, cy[p]}}, kInYh, kOutYh, xout[c],
+           rout[c], nc + c, &cy[c], 1, kChainPiece);
     }
   // leaf bases
   for (int c : h->leaves)
-    if (c > 0 && h->rank[c] > 0 && cy[c] > 0)
-      emit({{kV, O[kV][c], h->end[c] - h->begin[c], h->rank[c], h->xoff[c], nc + c, cy[c]}}, kInYh,
+    if (c > 0 && rout[c] > 0 && cy[c] > 0)
+      emit({{kLeafOut, O[kLeafOut][c], h->end[c] - h->begin[c], rout[c], xout[c], nc + c, cy[c]}}, kInYh,
            kOutY, h->begin[c], h->end[c] - h->begin[c], -1, nullptr, 1, kChainPiece);
   for (const auto* gl : {&groups, &free_groups})
     for (const int2& g : *gl)
@@ -1531,7 +1542,7 @@ void plan_direction(const gca_h2* h, int dir, PlanJob* job) {
 }
 
 int finish_plan(gca_h2* h, PlanJob* job, cudaStream_t st) {
-  h->max_rows = std::max(h->max_rank, h->max_leaf);
+  h->max_rows = std::max(std::max(h->max_rank, h->max_rank2), h->max_leaf);
   {
     std::vector<int> iperm(h->n);
     for (int i = 0; i < h->n; ++i) iperm[h->perm[i]] = i;
@@ -1609,7 +1620,8 @@ void fill_slot(SlotArgs<TV>& a, const gca_h2* h, int dir, int R, int RC, const v
   a.nchunk = (R + RC - 1) / RC;
   a.n = h->n;
   a.rc = RC;
-  a.rank_sum = (int)h->rank_sum;
+  a.rs_in = (int)h->rank_sum_in(dir);
+  a.rs_out = (int)h->rank_sum_out(dir);
   a.x = static_cast<const TV*>(x);
   a.ldx = ldx;
   a.y = static_cast<TV*>(y);
@@ -1682,9 +1694,9 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
     const gca_h2* h = hs[i];
     const int R = (nrhs[i] + RC - 1) / RC * RC;  // chunk-major vectors: whole chunks
     o_xh[i] = off;
-    off += up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * R);
+    off += up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum_in(dir), 1) * R);
     o_yh[i] = off;
-    off += up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * R);
+    off += up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum_out(dir), 1) * R);
     o_yp[i] = off;
     off += up256(sizeof(TV) * (size_t)h->n * R);
     o_cnt[i] = off;
@@ -2183,10 +2195,11 @@ template <typename T, typename TN, typename TA, typename TV, int RC>
 int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* y, int64_t ldy,
                       unsigned char* base, size_t cap, cudaStream_t st) {
   const int Rp = (R + RC - 1) / RC * RC;  // chunk-major vectors: whole chunks
-  const size_t b_xh = up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum, 1) * Rp);
+  const size_t b_xh = up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum_in(0), 1) * Rp);
+  const size_t b_yh = up256(sizeof(TV) * (size_t)std::max<int64_t>(h->rank_sum_out(0), 1) * Rp);
   const size_t b_yp = up256(sizeof(TV) * (size_t)h->n * Rp);
   const size_t b_cnt = up256(sizeof(int) * 2 * (size_t)h->nc);
-  const size_t o_xh = 256 + kZeroBytes, o_yh = o_xh + b_xh, o_yp = o_yh + b_xh, o_cnt = o_yp + b_yp;
+  const size_t o_xh = 256 + kZeroBytes, o_yh = o_xh + b_xh, o_yp = o_yh + b_yh, o_cnt = o_yp + b_yp;
   const size_t zeroed = o_cnt + b_cnt;
   const size_t o_xp = zeroed;
   const size_t need = o_xp + b_yp;
