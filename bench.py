@@ -467,6 +467,47 @@ def run_legs(gca, batch, meshes, stats, n, args, dev, stream, hbm_peak):
                         "err_vs_f64": 0.0 if prec == "f64" else leg_errors([out], [y64])}
     hd.check()
     legs["double_layer.perturbed20480.R16"] = dlg
+    del hd
+    # the collocation variant on the 20480-triangle sphere: one integral per
+    # entry; its entry phases beside the Galerkin single layer's (same mesh)
+    v, t = meshes[0]
+    tree = gca.tree_build(v, t, PARAMS["leaf_size"])
+    gca.profile_enable(True)
+    hg = gca.build(v, t, tree, gca.Params(**PARAMS, flags=gca.DROP_EXPORT))
+    torch.cuda.synchronize()
+    ph_g = gca.profile_read()
+    del hg
+    a.record(stream)
+    hc = gca.build_collocation(v, t, tree, gca.Params(**PARAMS, flags=gca.DROP_EXPORT))
+    b.record(stream)
+    b.synchronize()
+    ph_c = gca.profile_read()
+    gca.profile_enable(False)
+    st = hc.stats()
+    cs = hc.column_stats()
+    ent = lambda ph, names: sum(ph.get(nm, (0, 0.0))[1] for nm in names)  # noqa: E731
+    colg = {"workload": "collocation at centroids, sphere20480, leaf 64, eta 2, m 4, tol 1e-8, 16 RHS N(0,1)",
+            "build_s": a.elapsed_time(b) * 1e-3,
+            "entries_ms": ent(ph_c, ("col_couple_entries", "col_near_entries")),
+            "galerkin_entries_ms": ent(ph_g, ("couple_entries", "near_entries", "singular")),
+            "green_aca_ms": ent(ph_c, ("green_aca",)), "galerkin_green_aca_ms": ent(ph_g, ("green_aca",))}
+    x64 = torch.from_numpy(synth.normal_rhs(len(t), NRHS, seed=0)).to(dev)
+    x32 = x64.float()
+    for tr in (False, True):
+        y64 = torch.empty((NRHS, len(t)), dtype=torch.float64, device=dev).t()
+        for prec in ("f64", "f32", "bf16"):
+            xin = x64 if prec == "f64" else x32
+            out = y64 if prec == "f64" else torch.empty((NRHS, len(t)), dtype=torch.float32, device=dev).t()
+            ms = time_products(lambda: hc.matvec(xin, prec, transpose=tr, out=out), K, W, stream)
+            sm = {"f64": 8, "f32": 4, "bf16": 2}[prec]
+            sv = 8 if prec == "f64" else 4
+            byt = (sm * (st["v_entries"] + st["e_entries"] + cs["w_entries"] + cs["f_entries"] + st["s_entries"])
+                   + sv * st["n_entries"] + 2 * sv * len(t) * NRHS)
+            colg[prec + (".T" if tr else "")] = {"GB/s": byt / ms / 1e6, "frac_hbm": byt / ms / 1e6 / hbm_peak,
+                                                  "ms": ms,
+                                                  "err_vs_f64": 0.0 if prec == "f64" else leg_errors([out], [y64])}
+    hc.check()
+    legs["collocation.sphere20480.R16"] = colg
     return legs
 
 

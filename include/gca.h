@@ -254,10 +254,32 @@ int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* para
 int gca_build_double_layer(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
                            void* stream, gca_h2** out);
 
+/* The collocation variant of the single layer (Sect. 6): a single integral
+ * per entry instead of the double integral of Eq. (1),
+ *   c_ij = int_{T_j} g(x_i, y) dy,
+ * with the centroid x_i of triangle i as collocation point (the
+ * piecewise-constant counterpart of the paper's vertices), and its GCA-H^2
+ * approximation C|tau x sigma ~ V_tau C|tilde-tau x tilde-sigma' W_sigma^*:
+ *   - rows: x -> g(x, y) is harmonic near tau, so Green's formula evaluated
+ *     at the collocation points gives a_{i nu} = sqrt(w_nu) g(x_i, z_nu),
+ *     a_{i nu+k} = -d_tau sqrt(w_nu) dg/dn_z(x_i, z_nu), cross-approximated
+ *     and nested into the row bases V, E;
+ *   - columns: the y-factors are the Galerkin ones, so the column bases W, F
+ *     are those of gca_build;
+ *   - entries in float64: the 7-point rule on T_j for j != i; for j = i a
+ *     Duffy transformation around x_i (three sub-triangles, the radial
+ *     integral exact, 4 sauter_q Gauss points along each edge).
+ * The handle works like a gca_build_double_layer handle (two-sided bases,
+ * h2_matvec for C x, h2_matvec_transpose for C^T x, gca_h2_export_columns);
+ * n_singular[3] of its stats counts the Duffy entries.  Arguments, errors
+ * and synchronisation as gca_build. */
+int gca_build_collocation(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
+                          void* stream, gca_h2** out);
+
 /* Sizes of the column side of a handle: op 0 (single layer: the row bases
- * serve the columns, the values repeat those of gca_h2_stats) or op 1
- * (double layer); max_rank and rank_sum of r'_sigma, coefficients of the
- * column bases W and transfers F. */
+ * serve the columns, the values repeat those of gca_h2_stats), op 1
+ * (double layer) or op 2 (collocation); max_rank and rank_sum of r'_sigma,
+ * coefficients of the column bases W and transfers F. */
 typedef struct {
   int32_t op;
   int32_t max_rank;

@@ -131,6 +131,8 @@ def _load():
         "gca_test_hook": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64]),
         "gca_build_double_layer": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
                                                   ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+        "gca_build_collocation": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
+                                                 ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
         "gca_h2_column_stats": (ctypes.c_int, [vp, ctypes.POINTER(_ColStats)]),
         "gca_h2_export_columns": (ctypes.c_int, [vp, ctypes.POINTER(_Dump)]),
     }
@@ -436,6 +438,18 @@ def build_double_layer(vertices, triangles, tree, params, stream=None):
     h = ctypes.c_void_p(None)
     _check(lib.gca_build_double_layer(ctypes.byref(m), ctypes.byref(t), ctypes.byref(p), _stream_ptr(stream),
                                       ctypes.byref(h)), "gca_build_double_layer")
+    return H2(h.value)
+
+
+def build_collocation(vertices, triangles, tree, params, stream=None):
+    """gca_build_collocation on the current CUDA device; returns an ``H2``
+    whose products apply the collocation matrix C (and C^T)."""
+    m, keep_m = _mesh(vertices, triangles)
+    t, keep_t = _tree(tree)
+    p = params._c()
+    h = ctypes.c_void_p(None)
+    _check(lib.gca_build_collocation(ctypes.byref(m), ctypes.byref(t), ctypes.byref(p), _stream_ptr(stream),
+                                     ctypes.byref(h)), "gca_build_collocation")
     return H2(h.value)
 
 

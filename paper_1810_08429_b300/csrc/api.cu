@@ -81,6 +81,21 @@ int gca_build_double_layer(const gca_mesh* mesh, const gca_tree* tree, const gca
   }
 }
 
+int gca_build_collocation(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params, void* stream,
+                          gca_h2** out) {
+  if (!out) {
+    gca::set_error("gca_build_collocation: out is NULL");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    return gca::build(mesh, tree, params, static_cast<cudaStream_t>(stream), out, 2);
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_build_collocation: host allocation failed");
+    return GCA_ERR_OOM;
+  }
+}
+
 int gca_h2_column_stats(const gca_h2* h, gca_column_stats* o) {
   if (!h || !o) {
     gca::set_error("gca_h2_column_stats: NULL argument");
@@ -88,7 +103,7 @@ int gca_h2_column_stats(const gca_h2* h, gca_column_stats* o) {
   }
   std::memset(o, 0, sizeof(*o));
   o->op = h->op;
-  if (h->op == 1) {
+  if (h->op != 0) {
     o->max_rank = h->max_rank2;
     o->rank_sum = h->rank_sum2;
     o->w_entries = h->w_entries;
@@ -107,7 +122,7 @@ int gca_h2_export_columns(const gca_h2* h, gca_host_dump* o) {
     gca::set_error("gca_h2_export_columns: NULL argument");
     return GCA_ERR_INVALID_ARG;
   }
-  if (h->op != 1) {
+  if (h->op == 0) {
     // one basis serves rows and columns
     gca_host_dump d{o->rank, o->pivots, nullptr, nullptr, o->V, o->E, nullptr, nullptr};
     return gca_h2_export(h, &d);

@@ -187,7 +187,8 @@ struct AcaJob {
   int tbegin;     // leaf: first position in perm
   int r0;         // non-leaf: rank of child0 (its pivots come first)
   int mesh;       // entry of the launch's mesh table
-  int kind;       // 0: Green matrix A_tau of the single layer; 1: column matrix of the double layer
+  int kind;       // 0: Green matrix A_tau of the single layer; 1: column matrix of the double
+                  // layer; 2: rows of the collocation matrix (values at the centroids)
   int64_t piv0;   // non-leaf: pivot pool offsets of the children
   int64_t piv1;
   int64_t vh_off; // V^ (rows x r, row-major) in the mesh's V^ pool
@@ -388,6 +389,15 @@ k_aca(const AcaJob* __restrict__ jobs, const AcaMesh* __restrict__ meshes, int k
         gs += x.w * ir;
         ds += x.w * dn * ir * ir * ir;
       }
+    } else if (job.kind == 2) {
+      // collocation rows: a_{i nu} = sqrt(w) g(x_i, z), a_{i nu+k} = -d sqrt(w)
+      // dg/dn_z(x_i, z) at the centroid x_i (the 7-point rule's centre)
+      const P4 x = xq[0];
+      const double dx = x.x - zz.x, dy = x.y - zz.y, dz = x.z - zz.z;
+      const double ir = rsqrt(dx * dx + dy * dy + dz * dz);
+      const double dn = sgn * (d == 0 ? dx : (d == 1 ? dy : dz));
+      gs = ir;
+      ds = dn * ir * ir * ir;
     } else {
       // the double layer's column matrix: a'_{j nu} = sqrt(w) int dg/dn_y(y, z) phi_j,
       // a'_{j nu+k} = -d sqrt(w) int d2g/dn_y dn_z(y, z) phi_j, with e = z - y,
@@ -825,7 +835,7 @@ void for_each_panel(const gca_h2* h, F&& f) {
   }
   for (int b = 0; b < nfar; ++b) {
     const int rt = h->rank[h->far_t[b]];
-    const int rs = h->op == 1 ? h->rank2[h->far_s[b]] : h->rank[h->far_s[b]];  // r'_sigma: column bases
+    const int rs = h->op != 0 ? h->rank2[h->far_s[b]] : h->rank[h->far_s[b]];  // r'_sigma: column bases
     f(kS, b, rt, rs, 0);
     f(kSt, b, rs, rt, 1);
   }
@@ -835,7 +845,7 @@ void for_each_panel(const gca_h2* h, F&& f) {
     f(kN, b, mt, ms, 0);
     f(kNt, b, ms, mt, 1);
   }
-  if (h->op != 1) return;
+  if (h->op == 0) return;
   // column bases W and transfers F (their own ranks r')
   for (int c = 1; c < nc; ++c) {
     if (h->child0[c] < 0) {
@@ -1546,6 +1556,102 @@ __global__ void k_dl_singular(const SingularItem* __restrict__ items,
   if (lane == 0) N[it.pos] = acc * area2[it.ti] * area2[it.tj] * (kInv4Pi / 2.0);
 }
 
+// ------------------------------------------------- collocation entries
+//
+// c_ij = int_{T_j} g(x_i, y) dy at the centroid x_i of T_i (the collocation
+// variant of Sect. 6 for the piecewise constant basis), in float64: the
+// 7-point rule on T_j for j != i; for j = i the Duffy transformation around
+// x_i: T_i splits into (x_i, P_k, P_k+1), on which y = x_i + s ((1 - t) P_k +
+// t P_k+1 - x_i) makes the integrand J_k / |(1 - t) P_k + t P_k+1 - x_i|
+// independent of s; t takes the rule `duffy` (nodes and weights on [0, 1]).
+
+__device__ __forceinline__ double col_regular_entry(const P4& x, const P4* __restrict__ yq) {
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    const P4 y = yq[q];
+    const double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+    s += y.w * rsqrt(dx * dx + dy * dy + dz * dz);
+  }
+  return s * kInv4Pi;
+}
+
+__device__ double col_duffy_entry(const P4& x, const double* __restrict__ vert, const int* __restrict__ tri, int t,
+                                  const double2* __restrict__ duffy, int nd) {
+  double P[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) P[a][d] = vert[3 * tri[3 * t + a] + d];
+  const double xc[3] = {x.x, x.y, x.z};
+  double total = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double* A = P[k];
+    const double* B = P[(k + 1) % 3];
+    const double a0 = A[0] - xc[0], a1 = A[1] - xc[1], a2 = A[2] - xc[2];
+    const double b0 = B[0] - xc[0], b1 = B[1] - xc[1], b2 = B[2] - xc[2];
+    const double c0 = a1 * b2 - a2 * b1, c1 = a2 * b0 - a0 * b2, c2 = a0 * b1 - a1 * b0;
+    const double jac = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+    double sk = 0.0;
+    for (int q = 0; q < nd; ++q) {
+      const double tq = duffy[q].x;
+      const double e0 = a0 + tq * (b0 - a0), e1 = a1 + tq * (b1 - a1), e2 = a2 + tq * (b2 - a2);
+      sk += duffy[q].y * rsqrt(e0 * e0 + e1 * e1 + e2 * e2);
+    }
+    total += jac * sk;
+  }
+  return total * kInv4Pi;
+}
+
+// One CTA per coupling block: C|tilde-tau x tilde-sigma', the centroids of the
+// row pivots against the 7-point rules of the column pivots.
+__global__ void k_col_couple(const int* __restrict__ far_t, const int* __restrict__ far_s,
+                             const int64_t* __restrict__ soff, const int* __restrict__ rank,
+                             const int* __restrict__ rank2, const int64_t* __restrict__ poff,
+                             const int64_t* __restrict__ poff2, const int* __restrict__ piv,
+                             const int* __restrict__ piv2, const P4* __restrict__ tq, double* __restrict__ S) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  const int t = far_t[b], s = far_s[b];
+  const int rt = rank[t], rs = rank2[s];
+  P4* ys = reinterpret_cast<P4*>(smem_raw);
+  const int* pt = piv + poff[t];
+  const int* ps = piv2 + poff2[s];
+  for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) ys[i] = tq[7 * (int64_t)ps[i / 7] + i % 7];
+  __syncthreads();
+  double* out = S + soff[b];
+  for (int idx = threadIdx.x; idx < rt * rs; idx += blockDim.x) {
+    const int a = idx / rs, c = idx - (idx / rs) * rs;
+    out[idx] = col_regular_entry(tq[7 * (int64_t)pt[a]], ys + 7 * c);
+  }
+}
+
+// One CTA per near block of the collocation matrix.
+__global__ void k_col_near_entries(const int* __restrict__ near_t, const int* __restrict__ near_s,
+                                   const int64_t* __restrict__ noff, const int* __restrict__ begin,
+                                   const int* __restrict__ end, const int* __restrict__ perm,
+                                   const int* __restrict__ tri, const double* __restrict__ vert,
+                                   const P4* __restrict__ tq, const double2* __restrict__ duffy, int nd,
+                                   double* __restrict__ N, unsigned long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int b = blockIdx.x;
+  const int t = near_t[b], s = near_s[b];
+  const int bt = begin[t], nt = end[t] - bt, bs = begin[s], ns = end[s] - bs;
+  P4* ys = reinterpret_cast<P4*>(smem_raw);
+  for (int i = threadIdx.x; i < ns * 7; i += blockDim.x) ys[i] = tq[7 * (int64_t)perm[bs + i / 7] + i % 7];
+  __syncthreads();
+  const int64_t base = noff[b];
+  for (int idx = threadIdx.x; idx < nt * ns; idx += blockDim.x) {
+    const int i = idx / ns, j = idx - (idx / ns) * ns;
+    const int ti = perm[bt + i], tj = perm[bs + j];
+    const P4 x = tq[7 * (int64_t)ti];
+    if (ti == tj) {
+      N[base + idx] = col_duffy_entry(x, vert, tri, ti, duffy, nd);
+      atomicAdd(&counts[3], 1ull);
+    } else {
+      N[base + idx] = col_regular_entry(x, ys + 7 * j);
+    }
+  }
+}
+
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 int check_status(DevMem& st, cudaStream_t s, const char* where) {
@@ -1911,16 +2017,21 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   };
   DevMem d_piv, d_rank, d_piv2, d_rank2;
   int64_t piv_used = 0, piv2_used = 0;
-  GCA_TRY(nested_bases(0, BasisOut{&h->rank, &h->poff, &h->voff, &h->eoff, &h->v_entries, &h->e_entries, &h->V64,
-                                   &h->E64},
+  // rows: the Galerkin single layer's bases (op 0, 1) or the collocation rows (op 2)
+  GCA_TRY(nested_bases(op == 2 ? 2 : 0,
+                       BasisOut{&h->rank, &h->poff, &h->voff, &h->eoff, &h->v_entries, &h->e_entries, &h->V64,
+                                &h->E64},
                        d_piv, d_rank, piv_used));
   h->xoff.assign(nc + 1, 0);
   for (int c = 0; c < nc; ++c) h->xoff[c + 1] = h->xoff[c] + h->rank[c];
   h->rank_sum = h->xoff[nc];
   h->max_rank = *std::max_element(h->rank.begin(), h->rank.end());
-  if (op == 1) {
-    GCA_TRY(nested_bases(1, BasisOut{&h->rank2, &h->poff2, &h->voff2, &h->eoff2, &h->w_entries, &h->f_entries,
-                                     &h->W64, &h->F64},
+  if (op != 0) {
+    // columns: the double layer's own bases (op 1) or the Galerkin single
+    // layer's (op 2)
+    GCA_TRY(nested_bases(op == 1 ? 1 : 0,
+                         BasisOut{&h->rank2, &h->poff2, &h->voff2, &h->eoff2, &h->w_entries, &h->f_entries,
+                                  &h->W64, &h->F64},
                          d_piv2, d_rank2, piv2_used));
     h->xoff2.assign(nc + 1, 0);
     for (int c = 0; c < nc; ++c) h->xoff2[c + 1] = h->xoff2[c] + h->rank2[c];
@@ -1938,14 +2049,14 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY(upload(h->d_rank, h->rank, st));
   DevMem d_poff, d_poff2, d_rank2v;
   GCA_TRY(upload(d_poff, h->poff, st));
-  if (op == 1) {
+  if (op != 0) {
     h->piv2.resize(std::max<int64_t>(piv2_used, 1));
     GCA_TRY_CUDA(cudaMemcpyAsync(h->piv2.data(), d_piv2.p, sizeof(int) * piv2_used, cudaMemcpyDeviceToHost, st));
     GCA_TRY(upload(d_poff2, h->poff2, st));
     GCA_TRY(upload(d_rank2v, h->rank2, st));
   }
   // coupling blocks: r_tau x r_sigma (single layer) or r_tau x r'_sigma (double layer)
-  const std::vector<int>& rcol = op == 1 ? h->rank2 : h->rank;
+  const std::vector<int>& rcol = op != 0 ? h->rank2 : h->rank;
   h->soff.assign(nfar + 1, 0);
   for (int b = 0; b < nfar; ++b)
     h->soff[b + 1] = h->soff[b] + (int64_t)h->rank[h->far_t[b]] * rcol[h->far_s[b]];
@@ -2025,7 +2136,27 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY_CUDA(cudaStreamSynchronize(st));  // the host copy of the pivots
 
   // coupling matrices
-  if (nfar > 0 && op == 1) {
+  std::vector<double2> duffy;  // the collocation's Duffy rule: 4q Gauss points on [0, 1]
+  DevMem d_duffy;
+  if (op == 2) {
+    const int nd = 4 * prm->sauter_q;
+    std::vector<double> xt(nd), wt(nd);
+    gauss_legendre(nd, xt.data(), wt.data());
+    for (int i = 0; i < nd; ++i) duffy.push_back(make_double2(0.5 * (xt[i] + 1.0), 0.5 * wt[i]));
+    GCA_TRY(upload(d_duffy, duffy, st));
+  }
+  if (nfar > 0 && op == 2) {
+    const size_t smem = sizeof(P4) * 7 * (size_t)std::max(h->max_rank2, 1);
+    GCA_TRY_CUDA(cudaFuncSetAttribute(k_col_couple, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      PhaseScope ps__("col_couple_entries", st);
+      k_col_couple<<<(unsigned)nfar, 256, smem, st>>>(
+          h->d_far_t.as<int>(), h->d_far_s.as<int>(), h->d_soff.as<int64_t>(), h->d_rank.as<int>(),
+          d_rank2v.as<int>(), d_poff.as<int64_t>(), d_poff2.as<int64_t>(), d_piv.as<int>(), d_piv2.as<int>(),
+          d_tq.as<P4>(), h->S64.as<double>());
+    }
+    GCA_TRY_CUDA(cudaGetLastError());
+  } else if (nfar > 0 && op == 1) {
     const size_t smem = (sizeof(P4) * 7 + sizeof(double) * 3) * (size_t)std::max(h->max_rank2, 1);
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_dl_couple, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
@@ -2050,7 +2181,18 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   }
 
   // near field
-  if (nnear > 0 && op == 1) {
+  if (nnear > 0 && op == 2) {
+    const size_t smem = sizeof(P4) * 7 * (size_t)h->max_leaf;
+    GCA_TRY_CUDA(cudaFuncSetAttribute(k_col_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+      PhaseScope ps__("col_near_entries", st);
+      k_col_near_entries<<<nnear, 256, smem, st>>>(
+          h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
+          h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), h->d_vert.as<double>(), d_tq.as<P4>(),
+          d_duffy.as<double2>(), (int)duffy.size(), h->N64.as<double>(), d_counts.as<unsigned long long>());
+    }
+    GCA_TRY_CUDA(cudaGetLastError());
+  } else if (nnear > 0 && op == 1) {
     const size_t smem = (sizeof(P4) * 7 + sizeof(double) * 3) * (size_t)h->max_leaf;
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_dl_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
@@ -2097,7 +2239,9 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     const double* vert_d = h->d_vert.as<double>();
     const double* a2 = d_area2.as<double>();
     double* N64 = h->N64.as<double>();
-    if (op == 1) {
+    if (op == 2) {
+      // the collocation's diagonal entries were integrated in place
+    } else if (op == 1) {
       const SSEntry64* tab64 = d_ss64.as<SSEntry64>();
       if (counts[1])
         k_dl_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(

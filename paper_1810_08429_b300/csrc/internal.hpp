@@ -128,7 +128,8 @@ class PhaseScope {
 };
 
 // Entry points of the translation units.
-// op 0: the single-layer matrix G; op 1: the double-layer matrix K
+// op 0: the single-layer matrix G; op 1: the double-layer matrix K; op 2: the
+// collocation matrix C of the single layer
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
           gca_h2** out, int op = 0);
 // Product plan (matvec.cu): plan_direction runs the host planning of one
@@ -258,8 +259,10 @@ struct gca_h2 {
   int device = -1;               // ordinal of the device that holds the handle's memory
 
   // The operator: 0 the single layer (one basis per cluster serves rows and
-  // columns), 1 the double layer (columns have bases W, transfers F and
-  // pivots tilde-sigma' of their own; the couplings are r_tau x r'_sigma).
+  // columns), 1 the double layer, 2 the collocated single layer.  For op 1 and
+  // 2 the columns have bases W, transfers F and pivots tilde-sigma' of their
+  // own (the double layer's; the Galerkin single layer's under the
+  // collocation rows) and the couplings are r_tau x r'_sigma.
   int op = 0;
   std::vector<int> rank2;              // r'_sigma (op 1)
   std::vector<int64_t> xoff2;
@@ -272,8 +275,8 @@ struct gca_h2 {
 
   // the bases a product direction (0: G x, 1: G^T x) transforms its input
   // with and returns its output through
-  bool in_cols(int dir) const { return op == 1 && dir == 0; }
-  bool out_cols(int dir) const { return op == 1 && dir == 1; }
+  bool in_cols(int dir) const { return op != 0 && dir == 0; }
+  bool out_cols(int dir) const { return op != 0 && dir == 1; }
   const std::vector<int>& rank_in(int dir) const { return in_cols(dir) ? rank2 : rank; }
   const std::vector<int>& rank_out(int dir) const { return out_cols(dir) ? rank2 : rank; }
   const std::vector<int64_t>& xoff_in(int dir) const { return in_cols(dir) ? xoff2 : xoff; }
