@@ -156,14 +156,19 @@ def needed_clusters(tree, far):
     return needed
 
 
-def build_bases(gal, tree, lo, hi, params, far=None, green=None):
+def build_bases(gal, tree, lo, hi, params, far=None, green=None, nested=True):
     """Nested cluster bases by Green cross approximation (Sect. 3, Sect. 4),
     for the clusters that need one (all non-root clusters when `far` is
     None); the others get empty bases.  `green(gal, rows, z, nrm, w, d)`
     forms the thin matrix of a cluster (default: the Green quadrature matrix
-    A_tau of the single-layer kernel)."""
+    A_tau of the single-layer kernel).  With nested=False every cluster that
+    is in an admissible block gets a basis V_tau of its own from the cross
+    approximation of A_tau on all of its triangles (the single-level GCA of
+    Sect. 3), and no transfer matrices."""
     if green is None:
         green = green_matrix
+    if not nested:
+        return _single_level_bases(gal, tree, lo, hi, params, far, green)
     nc = len(tree["begin"])
     diam = cluster.diameter(lo, hi)
     bases = Bases(pivots=[None] * nc, rank=np.zeros(nc, dtype=np.int64))
@@ -197,6 +202,28 @@ def build_bases(gal, tree, lo, hi, params, far=None, green=None):
             r0 = bases.rank[tree["child0"][c]]
             bases.E[tree["child0"][c]] = res.V[:r0, :]
             bases.E[tree["child1"][c]] = res.V[r0:, :]
+    return bases
+
+
+def _single_level_bases(gal, tree, lo, hi, params, far, green):
+    nc = len(tree["begin"])
+    diam = cluster.diameter(lo, hi)
+    bases = Bases(pivots=[None] * nc, rank=np.zeros(nc, dtype=np.int64))
+    inblock = np.zeros(nc, dtype=bool)
+    for (t, s) in far:
+        inblock[t] = inblock[s] = True
+    for c in range(nc):
+        rows = tree["perm"][tree["begin"][c]:tree["end"][c]]
+        if not inblock[c]:
+            bases.pivots[c] = np.zeros(0, dtype=tree["perm"].dtype)
+            bases.V[c] = np.zeros((len(rows), 0))
+            continue
+        z, nrm, w = omega_rule(lo[c], hi[c], diam[c], params.margin(), params.box_gauss_m)
+        bases.omega[c] = (z, nrm, w)
+        res = aca(green(gal, rows, z, nrm, w, diam[c]), params.aca_tol, params.tie_rel)
+        bases.pivots[c] = rows[res.rows]
+        bases.rank[c] = len(res.rows)
+        bases.V[c] = res.V
     return bases
 
 
