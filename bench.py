@@ -508,7 +508,65 @@ def run_legs(gca, batch, meshes, stats, n, args, dev, stream, hbm_peak):
                                                   "err_vs_f64": 0.0 if prec == "f64" else leg_errors([out], [y64])}
     hc.check()
     legs["collocation.sphere20480.R16"] = colg
+    del hc
+    legs["error_vs_storage.sphere5120"] = error_vs_storage(gca, dev)
     return legs
+
+
+def error_vs_storage(gca, dev, iters=25):
+    """The comparison of the paper's Fig. 1-3 on the 5120-triangle sphere
+    (leaf 32, eta 2): pure Green quadrature (m = 2, 3, 4), single-level GCA
+    and GCA-H^2 (m = 3, tolerances 1e-4, 1e-6, 1e-8).  Per run: stored
+    coefficients (bases, transfers, couplings or factors, near field), build
+    seconds (device stream), and ||G~ - G_ref||_2 / ||G_ref||_2 by power
+    iteration with the GPU products, G_ref the GCA-H^2 at m = 6, tolerance
+    1e-12 (its own error is far below the others')."""
+    import torch
+    v, t = synth.mesh_for_config("sphere5120")
+    tree = gca.tree_build(v, t, 32)
+    n = len(t)
+
+    def prm(m, tol):
+        return gca.Params(leaf_size=32, eta=2.0, box_gauss_m=m, aca_tol=tol, sauter_q=5, flags=gca.DROP_EXPORT)
+
+    def timed(fn, m, tol):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        h = fn(v, t, tree, prm(m, tol))
+        b.record()
+        b.synchronize()
+        return h, a.elapsed_time(b) * 1e-3
+
+    ref, _ = timed(gca.build, 6, 1e-12)
+
+    def err(h):
+        x = torch.randn(n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+        lam = 0.0
+        for _ in range(iters):
+            x = x / x.norm()
+            r = ref.matvec(x, "f64") - h.matvec(x, "f64")
+            y = ref.matvec(r, "f64", transpose=True) - h.matvec(r, "f64", transpose=True)
+            lam = float(y.norm())
+            x = y
+        z = torch.randn(n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
+        for _ in range(iters):
+            z = z / z.norm()
+            z = ref.matvec(ref.matvec(z, "f64"), "f64", transpose=True)
+        return (lam / float(z.norm())) ** 0.5
+
+    rows = []
+    runs = [("green_quadrature", gca.build_green_quadrature, m, 1e-6) for m in (2, 3, 4)]
+    runs += [(kind, fn, 3, tol) for tol in (1e-4, 1e-6, 1e-8)
+             for kind, fn in (("single_level_gca", gca.build_single_level), ("gca_h2", gca.build))]
+    for kind, fn, m, tol in runs:
+        h, bs = timed(fn, m, tol)
+        st = h.stats()
+        rows.append({"method": kind, "m": m, "tol": tol if kind != "green_quadrature" else None,
+                     "stored_entries": st["v_entries"] + st["e_entries"] + st["s_entries"] + st["n_entries"],
+                     "build_s": bs, "rel_spectral_error": err(h)})
+        del h
+    return rows
 
 
 def main():

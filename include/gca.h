@@ -276,6 +276,31 @@ int gca_build_double_layer(const gca_mesh* mesh, const gca_tree* tree, const gca
 int gca_build_collocation(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
                           void* stream, gca_h2** out);
 
+/* The two approximations of the single-layer matrix that GCA-H^2 improves
+ * on, for the error-versus-storage comparison of the paper (Sect. 2 - 4):
+ *   - gca_build_single_level: single-level GCA (Sect. 3),
+ *     G|tau x sigma ~ V_tau G|tilde-tau x tilde-sigma V_sigma^*, with V_tau
+ *     from the cross approximation of A_tau on all of tau's triangles for
+ *     every cluster of an admissible block, and no transfer matrices.
+ *     Export: V holds |tau-hat| x r_tau for every cluster 1..nclusters-1 in
+ *     increasing id (not only the leaves); E is empty.  The cross
+ *     approximation of a cluster's whole A_tau must fit the cluster kernel's
+ *     shared memory (GCA_ERR_UNSUPPORTED otherwise: about 1000 triangles at
+ *     m = 4, 1800 at m = 3).
+ *   - gca_build_green_quadrature: pure Green quadrature (Sect. 2, Eq. (2)),
+ *     G|tau x sigma ~ A_tau B_{tau sigma}^*, A_tau the Green quadrature
+ *     matrix of tau (|tau-hat| x 2k) and B_{tau sigma} the factor of sigma on
+ *     tau's box.  Export: rank = 2k for the clusters of the blocks (-1 as
+ *     pivots: there are none), V = A_tau for those clusters in increasing id,
+ *     S = B_{tau sigma}^* (2k x |sigma-hat| row-major) per block.
+ * Both: float64 Green and coupling matrices, the near field as gca_build,
+ * products (and transposes) with h2_matvec; arguments and errors as
+ * gca_build. */
+int gca_build_single_level(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
+                           void* stream, gca_h2** out);
+int gca_build_green_quadrature(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
+                               void* stream, gca_h2** out);
+
 /* Sizes of the column side of a handle: op 0 (single layer: the row bases
  * serve the columns, the values repeat those of gca_h2_stats), op 1
  * (double layer) or op 2 (collocation); max_rank and rank_sum of r'_sigma,

@@ -133,6 +133,10 @@ def _load():
                                                   ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
         "gca_build_collocation": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
                                                  ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+        "gca_build_single_level": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
+                                                  ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+        "gca_build_green_quadrature": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
+                                                      ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
         "gca_h2_column_stats": (ctypes.c_int, [vp, ctypes.POINTER(_ColStats)]),
         "gca_h2_export_columns": (ctypes.c_int, [vp, ctypes.POINTER(_Dump)]),
     }
@@ -439,6 +443,27 @@ def build_double_layer(vertices, triangles, tree, params, stream=None):
     _check(lib.gca_build_double_layer(ctypes.byref(m), ctypes.byref(t), ctypes.byref(p), _stream_ptr(stream),
                                       ctypes.byref(h)), "gca_build_double_layer")
     return H2(h.value)
+
+
+def _build_with(fn, name, vertices, triangles, tree, params, stream):
+    m, keep_m = _mesh(vertices, triangles)
+    t, keep_t = _tree(tree)
+    p = params._c()
+    h = ctypes.c_void_p(None)
+    _check(fn(ctypes.byref(m), ctypes.byref(t), ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)), name)
+    return H2(h.value)
+
+
+def build_single_level(vertices, triangles, tree, params, stream=None):
+    """Single-level GCA of G (gca_build_single_level); returns an ``H2``."""
+    return _build_with(lib.gca_build_single_level, "gca_build_single_level", vertices, triangles, tree, params,
+                       stream)
+
+
+def build_green_quadrature(vertices, triangles, tree, params, stream=None):
+    """Pure Green quadrature of G (gca_build_green_quadrature); returns an ``H2``."""
+    return _build_with(lib.gca_build_green_quadrature, "gca_build_green_quadrature", vertices, triangles, tree,
+                       params, stream)
 
 
 def build_collocation(vertices, triangles, tree, params, stream=None):

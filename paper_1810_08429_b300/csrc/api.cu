@@ -96,6 +96,36 @@ int gca_build_collocation(const gca_mesh* mesh, const gca_tree* tree, const gca_
   }
 }
 
+int gca_build_single_level(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params, void* stream,
+                           gca_h2** out) {
+  if (!out) {
+    gca::set_error("gca_build_single_level: out is NULL");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    return gca::build(mesh, tree, params, static_cast<cudaStream_t>(stream), out, 3);
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_build_single_level: host allocation failed");
+    return GCA_ERR_OOM;
+  }
+}
+
+int gca_build_green_quadrature(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params, void* stream,
+                               gca_h2** out) {
+  if (!out) {
+    gca::set_error("gca_build_green_quadrature: out is NULL");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    return gca::build(mesh, tree, params, static_cast<cudaStream_t>(stream), out, 4);
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_build_green_quadrature: host allocation failed");
+    return GCA_ERR_OOM;
+  }
+}
+
 int gca_h2_column_stats(const gca_h2* h, gca_column_stats* o) {
   if (!h || !o) {
     gca::set_error("gca_h2_column_stats: NULL argument");
@@ -103,7 +133,7 @@ int gca_h2_column_stats(const gca_h2* h, gca_column_stats* o) {
   }
   std::memset(o, 0, sizeof(*o));
   o->op = h->op;
-  if (h->op != 0) {
+  if (h->two_sided()) {
     o->max_rank = h->max_rank2;
     o->rank_sum = h->rank_sum2;
     o->w_entries = h->w_entries;
@@ -122,7 +152,7 @@ int gca_h2_export_columns(const gca_h2* h, gca_host_dump* o) {
     gca::set_error("gca_h2_export_columns: NULL argument");
     return GCA_ERR_INVALID_ARG;
   }
-  if (h->op == 0) {
+  if (!h->two_sided()) {
     // one basis serves rows and columns
     gca_host_dump d{o->rank, o->pivots, nullptr, nullptr, o->V, o->E, nullptr, nullptr};
     return gca_h2_export(h, &d);
@@ -224,7 +254,8 @@ int gca_h2_export(const gca_h2* h, gca_host_dump* o) {
   if (o->pivots) {
     int64_t at = 0;
     for (int c = 0; c < h->nc; ++c)
-      for (int t = 0; t < h->rank[c]; ++t) o->pivots[at++] = h->piv[h->poff[c] + t];
+      for (int t = 0; t < h->rank[c]; ++t)
+        o->pivots[at++] = h->op == 4 ? -1 : h->piv[h->poff[c] + t];  // Green quadrature: no pivots
   }
   if (o->far)
     for (size_t b = 0; b < h->far_t.size(); ++b) {

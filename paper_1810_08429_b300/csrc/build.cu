@@ -821,13 +821,14 @@ template <typename F>
 void for_each_panel(const gca_h2* h, F&& f) {
   const int nc = h->nc;
   const int nfar = (int)h->far_t.size(), nnear = (int)h->near_t.size();
+  const bool single = h->single_level();  // bases of every cluster, no transfers
   for (int c = 1; c < nc; ++c) {
-    if (h->child0[c] < 0) {
+    if (h->child0[c] < 0 || single) {
       const int nr = h->end[c] - h->begin[c], r = h->rank[c];
       f(kV, c, nr, r, 0);
       f(kVt, c, r, nr, 1);
     }
-    if (h->parent[c] > 0) {
+    if (h->parent[c] > 0 && !single) {
       const int r = h->rank[c], rp = h->rank[h->parent[c]];
       f(kE, c, r, rp, 0);
       f(kEt, c, rp, r, 1);
@@ -835,7 +836,10 @@ void for_each_panel(const gca_h2* h, F&& f) {
   }
   for (int b = 0; b < nfar; ++b) {
     const int rt = h->rank[h->far_t[b]];
-    const int rs = h->op != 0 ? h->rank2[h->far_s[b]] : h->rank[h->far_s[b]];  // r'_sigma: column bases
+    // r'_sigma (column bases), r_sigma, or |sigma-hat| (Green quadrature: B^*)
+    const int rs = h->two_sided() ? h->rank2[h->far_s[b]]
+                   : h->op == 4   ? h->end[h->far_s[b]] - h->begin[h->far_s[b]]
+                                  : h->rank[h->far_s[b]];
     f(kS, b, rt, rs, 0);
     f(kSt, b, rs, rt, 1);
   }
@@ -845,7 +849,7 @@ void for_each_panel(const gca_h2* h, F&& f) {
     f(kN, b, mt, ms, 0);
     f(kNt, b, ms, mt, 1);
   }
-  if (h->op == 0) return;
+  if (!h->two_sided()) return;
   // column bases W and transfers F (their own ranks r')
   for (int c = 1; c < nc; ++c) {
     if (h->child0[c] < 0) {
@@ -1556,6 +1560,78 @@ __global__ void k_dl_singular(const SingularItem* __restrict__ items,
   if (lane == 0) N[it.pos] = acc * area2[it.ti] * area2[it.tj] * (kInv4Pi / 2.0);
 }
 
+// ----------------------------------------------- Green quadrature factors
+//
+// The pure Green quadrature of Sect. 2: G|tau-hat x sigma-hat ~ A_tau B^*,
+//   a_{i nu}   =        sqrt(w) int g(x, z_nu) phi_i,   a_{i nu+k} = -d_tau sqrt(w) int dg/dn_z(x, z_nu) phi_i,
+//   b_{j nu}   =        sqrt(w) int dg/dn_z(z_nu, y) phi_j,  b_{j nu+k} = sqrt(w) / d_tau int g(z_nu, y) phi_j,
+// with the box rule z_nu, n_nu, w_nu of omega_tau (Eq. (2)); float64.
+
+struct GqJob {
+  int c;          // the cluster whose box carries the rule
+  int s;          // the cluster whose triangles are integrated
+  int64_t off;    // output offset
+};
+
+// A_tau of every listed cluster (row-major |tau-hat| x 2k), one CTA each
+__global__ void k_gq_rows(const GqJob* __restrict__ jobs, int k, const int* __restrict__ begin,
+                          const int* __restrict__ end, const int* __restrict__ perm, const P4* __restrict__ tq,
+                          const P4* __restrict__ zq, const double* __restrict__ diam, double* __restrict__ out) {
+  const GqJob jb = jobs[blockIdx.x];
+  const int c = jb.c, b0 = begin[c], nr = end[c] - b0, m2 = k / 6;
+  const P4* z = zq + (int64_t)c * k;
+  double* A = out + jb.off;
+  for (int idx = threadIdx.x; idx < nr * k; idx += blockDim.x) {
+    const int i = idx / k, nu = idx - i * k;
+    const P4 zz = z[nu];
+    const int face = nu / m2, d = face >> 1;
+    const double sgn = (face & 1) ? 1.0 : -1.0;
+    const P4* xq = tq + 7 * (int64_t)perm[b0 + i];
+    double gs = 0.0, ds = 0.0;
+#pragma unroll
+    for (int qq = 0; qq < 7; ++qq) {
+      const P4 x = xq[qq];
+      const double dx = x.x - zz.x, dy = x.y - zz.y, dz = x.z - zz.z;
+      const double ir = rsqrt(dx * dx + dy * dy + dz * dz);
+      const double dn = sgn * (d == 0 ? dx : (d == 1 ? dy : dz));
+      gs += x.w * ir;
+      ds += x.w * dn * ir * ir * ir;
+    }
+    A[(int64_t)i * 2 * k + nu] = zz.w * gs * kInv4Pi;
+    A[(int64_t)i * 2 * k + k + nu] = -diam[c] * zz.w * ds * kInv4Pi;
+  }
+}
+
+// B_{tau sigma}^* of every coupling block (row-major 2k x |sigma-hat|), one CTA each
+__global__ void k_gq_factors(const GqJob* __restrict__ jobs, int k, const int* __restrict__ begin,
+                             const int* __restrict__ end, const int* __restrict__ perm, const P4* __restrict__ tq,
+                             const P4* __restrict__ zq, const double* __restrict__ diam, double* __restrict__ out) {
+  const GqJob jb = jobs[blockIdx.x];
+  const int c = jb.c, s = jb.s, b0 = begin[s], ns = end[s] - b0, m2 = k / 6;
+  const P4* z = zq + (int64_t)c * k;
+  const double inv_d = 1.0 / diam[c];
+  double* B = out + jb.off;
+  for (int idx = threadIdx.x; idx < ns * k; idx += blockDim.x) {
+    const int j = idx / k, nu = idx - j * k;
+    const P4 zz = z[nu];
+    const int face = nu / m2, d = face >> 1;
+    const double sgn = (face & 1) ? 1.0 : -1.0;
+    const P4* yq = tq + 7 * (int64_t)perm[b0 + j];
+    double dn_s = 0.0, g_s = 0.0;
+#pragma unroll
+    for (int qq = 0; qq < 7; ++qq) {
+      const P4 y = yq[qq];
+      const double ex = y.x - zz.x, ey = y.y - zz.y, ez = y.z - zz.z;
+      const double ir = rsqrt(ex * ex + ey * ey + ez * ez);
+      const double dn = sgn * (d == 0 ? ex : (d == 1 ? ey : ez));
+      dn_s += y.w * dn * ir * ir * ir;
+      g_s += y.w * ir;
+    }
+    B[(int64_t)nu * ns + j] = zz.w * dn_s * kInv4Pi;
+    B[(int64_t)(k + nu) * ns + j] = zz.w * inv_d * g_s * kInv4Pi;
+  }
+}
+
 // ------------------------------------------------- collocation entries
 //
 // c_ij = int_{T_j} g(x_i, y) dy at the centroid x_i of T_i (the collocation
@@ -1876,7 +1952,10 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // the other clusters are not built (rank 0).
   std::vector<char> needed(nc, 0);
   for (size_t b = 0; b < h->far_t.size(); ++b) needed[h->far_t[b]] = needed[h->far_s[b]] = 1;
-  for (int L = 0; L < h->depth; ++L)
+  // single-level bases (op 3) and Green quadrature (op 4) serve only the
+  // clusters of the blocks themselves; nested bases also their descendants
+  const bool single = op == 3 || op == 4;
+  for (int L = 0; L < h->depth && !single; ++L)
     for (int c : h->by_level[L])
       if (needed[c] && h->child0[c] >= 0) needed[h->child0[c]] = needed[h->child1[c]] = 1;
 
@@ -1917,8 +1996,8 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     int64_t vh_used = 0;
     piv_used = 0;
     for (int c = 1; c < nc; ++c) {
-      int64_t rows = h->child0[c] < 0 ? (h->end[c] - h->begin[c])
-                                      : std::min<int64_t>(h->end[c] - h->begin[c], 4 * k);
+      int64_t rows = (h->child0[c] < 0 || single) ? (h->end[c] - h->begin[c])
+                                                  : std::min<int64_t>(h->end[c] - h->begin[c], 4 * k);
       vh_cap += rows * std::min<int64_t>(rows, 2 * k);
     }
     GCA_TRY(d_vh.alloc(sizeof(double) * (size_t)std::max<int64_t>(vh_cap, 1)));
@@ -1936,7 +2015,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
         AcaJob j{};
         j.c = c;
         j.kind = kind;
-        j.leaf = h->child0[c] < 0;
+        j.leaf = h->child0[c] < 0 || single;  // single-level: A_tau on all of tau's triangles
         if (j.leaf) {
           j.rows = h->end[c] - h->begin[c];
           j.tbegin = h->begin[c];
@@ -1975,12 +2054,12 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     *o.v_entries = 0;
     *o.e_entries = 0;
     for (int c = 1; c < nc; ++c)
-      if (h->child0[c] < 0) {
+      if (h->child0[c] < 0 || single) {
         (*o.voff)[c] = *o.v_entries;
         *o.v_entries += (int64_t)(h->end[c] - h->begin[c]) * rank[c];
       }
     for (int c = 1; c < nc; ++c)
-      if (h->parent[c] > 0) {
+      if (h->parent[c] > 0 && !single) {
         (*o.eoff)[c] = *o.e_entries;
         *o.e_entries += (int64_t)rank[c] * rank[h->parent[c]];
       }
@@ -1988,7 +2067,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     for (int c = 1; c < nc; ++c) {
       const int r = rank[c];
       if (r == 0) continue;  // unused basis
-      if (h->child0[c] < 0) {
+      if (h->child0[c] < 0 || single) {
         vseg.push_back({vh_off[c], (*o.voff)[c], (int64_t)rows_of[c] * r});
       } else {
         const int c0 = h->child0[c], c1 = h->child1[c];
@@ -2017,16 +2096,47 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   };
   DevMem d_piv, d_rank, d_piv2, d_rank2;
   int64_t piv_used = 0, piv2_used = 0;
-  // rows: the Galerkin single layer's bases (op 0, 1) or the collocation rows (op 2)
-  GCA_TRY(nested_bases(op == 2 ? 2 : 0,
-                       BasisOut{&h->rank, &h->poff, &h->voff, &h->eoff, &h->v_entries, &h->e_entries, &h->V64,
-                                &h->E64},
-                       d_piv, d_rank, piv_used));
+  // rows: the Galerkin single layer's bases (op 0, 1; single level for op 3),
+  // the collocation rows (op 2), or the Green quadrature matrices A_tau of
+  // the clusters of the blocks (op 4: "rank" 2k, no pivots)
+  if (op == 4) {
+    h->rank.assign(nc, 0);
+    h->voff.assign(nc, -1);
+    h->eoff.assign(nc, -1);
+    h->v_entries = 0;
+    std::vector<GqJob> gj;
+    for (int c = 1; c < nc; ++c)
+      if (needed[c]) {
+        h->rank[c] = 2 * k;
+        h->voff[c] = h->v_entries;
+        gj.push_back({c, c, h->v_entries});
+        h->v_entries += (int64_t)(h->end[c] - h->begin[c]) * 2 * k;
+      }
+    GCA_TRY(h->V64.alloc(sizeof(double) * (size_t)std::max<int64_t>(h->v_entries, 1)));
+    GCA_TRY(h->E64.alloc(sizeof(double)));
+    DevMem d_gj;
+    GCA_TRY(upload(d_gj, gj, st));
+    if (!gj.empty()) {
+      PhaseScope ps__("gq_rows", st);
+      k_gq_rows<<<(unsigned)gj.size(), 256, 0, st>>>(d_gj.as<GqJob>(), k, h->d_begin.as<int>(), h->d_end.as<int>(),
+                                                    h->d_perm.as<int>(), d_tq.as<P4>(), d_zq.as<P4>(),
+                                                    d_diam.as<double>(), h->V64.as<double>());
+      GCA_TRY_CUDA(cudaGetLastError());
+    }
+    h->poff.assign(nc, 0);
+    GCA_TRY(d_piv.alloc(sizeof(int)));
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // gj is a local
+  } else {
+    GCA_TRY(nested_bases(op == 2 ? 2 : 0,
+                         BasisOut{&h->rank, &h->poff, &h->voff, &h->eoff, &h->v_entries, &h->e_entries, &h->V64,
+                                  &h->E64},
+                         d_piv, d_rank, piv_used));
+  }
   h->xoff.assign(nc + 1, 0);
   for (int c = 0; c < nc; ++c) h->xoff[c + 1] = h->xoff[c] + h->rank[c];
   h->rank_sum = h->xoff[nc];
   h->max_rank = *std::max_element(h->rank.begin(), h->rank.end());
-  if (op != 0) {
+  if (h->two_sided()) {
     // columns: the double layer's own bases (op 1) or the Galerkin single
     // layer's (op 2)
     GCA_TRY(nested_bases(op == 1 ? 1 : 0,
@@ -2045,21 +2155,23 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // computes the entries.
   const int nfar = (int)h->far_t.size(), nnear = (int)h->near_t.size();
   h->piv.resize(std::max<int64_t>(piv_used, 1));
-  GCA_TRY_CUDA(cudaMemcpyAsync(h->piv.data(), d_piv.p, sizeof(int) * piv_used, cudaMemcpyDeviceToHost, st));
+  if (piv_used > 0)
+    GCA_TRY_CUDA(cudaMemcpyAsync(h->piv.data(), d_piv.p, sizeof(int) * piv_used, cudaMemcpyDeviceToHost, st));
   GCA_TRY(upload(h->d_rank, h->rank, st));
   DevMem d_poff, d_poff2, d_rank2v;
   GCA_TRY(upload(d_poff, h->poff, st));
-  if (op != 0) {
+  if (h->two_sided()) {
     h->piv2.resize(std::max<int64_t>(piv2_used, 1));
     GCA_TRY_CUDA(cudaMemcpyAsync(h->piv2.data(), d_piv2.p, sizeof(int) * piv2_used, cudaMemcpyDeviceToHost, st));
     GCA_TRY(upload(d_poff2, h->poff2, st));
     GCA_TRY(upload(d_rank2v, h->rank2, st));
   }
   // coupling blocks: r_tau x r_sigma (single layer) or r_tau x r'_sigma (double layer)
-  const std::vector<int>& rcol = op != 0 ? h->rank2 : h->rank;
+  const std::vector<int>& rcol = h->two_sided() ? h->rank2 : h->rank;
   h->soff.assign(nfar + 1, 0);
   for (int b = 0; b < nfar; ++b)
-    h->soff[b + 1] = h->soff[b] + (int64_t)h->rank[h->far_t[b]] * rcol[h->far_s[b]];
+    h->soff[b + 1] = h->soff[b] + (int64_t)h->rank[h->far_t[b]] *
+                                      (op == 4 ? h->end[h->far_s[b]] - h->begin[h->far_s[b]] : rcol[h->far_s[b]]);
   h->s_entries = h->soff[nfar];
   GCA_TRY(upload(h->d_far_t, h->far_t, st));
   GCA_TRY(upload(h->d_far_s, h->far_s, st));
@@ -2071,7 +2183,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // sigma); a block whose mirror is missing is computed alone
   std::vector<int2> pairs;
   pairs.reserve(nfar / 2 + 1);
-  for (int b = 0; b < nfar && op == 0; ++b) {
+  for (int b = 0; b < nfar && (op == 0 || op == 3); ++b) {
     const int t = h->far_t[b], s = h->far_s[b];
     int m = -1;
     {
@@ -2145,7 +2257,20 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     for (int i = 0; i < nd; ++i) duffy.push_back(make_double2(0.5 * (xt[i] + 1.0), 0.5 * wt[i]));
     GCA_TRY(upload(d_duffy, duffy, st));
   }
-  if (nfar > 0 && op == 2) {
+  if (nfar > 0 && op == 4) {
+    std::vector<GqJob> gj;
+    for (int b = 0; b < nfar; ++b) gj.push_back({h->far_t[b], h->far_s[b], h->soff[b]});
+    DevMem d_gj;
+    GCA_TRY(upload(d_gj, gj, st));
+    {
+      PhaseScope ps__("gq_factors", st);
+      k_gq_factors<<<(unsigned)nfar, 256, 0, st>>>(d_gj.as<GqJob>(), k, h->d_begin.as<int>(), h->d_end.as<int>(),
+                                                  h->d_perm.as<int>(), d_tq.as<P4>(), d_zq.as<P4>(),
+                                                  d_diam.as<double>(), h->S64.as<double>());
+    }
+    GCA_TRY_CUDA(cudaGetLastError());
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // gj is a local
+  } else if (nfar > 0 && op == 2) {
     const size_t smem = sizeof(P4) * 7 * (size_t)std::max(h->max_rank2, 1);
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_col_couple, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {

@@ -129,7 +129,8 @@ class PhaseScope {
 
 // Entry points of the translation units.
 // op 0: the single-layer matrix G; op 1: the double-layer matrix K; op 2: the
-// collocation matrix C of the single layer
+// collocation matrix C of the single layer; op 3: G by single-level GCA; op 4:
+// G by Green quadrature
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
           gca_h2** out, int op = 0);
 // Product plan (matvec.cu): plan_direction runs the host planning of one
@@ -275,8 +276,13 @@ struct gca_h2 {
 
   // the bases a product direction (0: G x, 1: G^T x) transforms its input
   // with and returns its output through
-  bool in_cols(int dir) const { return op != 0 && dir == 0; }
-  bool out_cols(int dir) const { return op != 0 && dir == 1; }
+  // op 3: single-level GCA (a basis V_tau for every cluster of a block, on
+  // all of its triangles, no transfers); op 4: Green quadrature (A_tau per
+  // cluster, the factors B_{tau sigma}^* as the blocks' couplings)
+  bool two_sided() const { return op == 1 || op == 2; }
+  bool single_level() const { return op == 3 || op == 4; }
+  bool in_cols(int dir) const { return two_sided() && dir == 0; }
+  bool out_cols(int dir) const { return two_sided() && dir == 1; }
   const std::vector<int>& rank_in(int dir) const { return in_cols(dir) ? rank2 : rank; }
   const std::vector<int>& rank_out(int dir) const { return out_cols(dir) ? rank2 : rank; }
   const std::vector<int64_t>& xoff_in(int dir) const { return in_cols(dir) ? xoff2 : xoff; }

@@ -1436,14 +1436,19 @@ int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
   // each, every tile of a transfer block in a group of its own, so that each
   // step of the tree recursion is spread over many warps
   const int kChainPiece = kChunk;
-  // forward transform: leaves
-  for (int c : h->leaves)
-    if (c > 0 && rin[c] > 0)
+  // Single-level bases (op 3) and Green quadrature (op 4) have a basis for
+  // every cluster of a block and no transfers; Green quadrature's couplings
+  // B^* read x itself in the product and write y itself in the transposed one.
+  const bool single = h->single_level();
+  const bool gq = h->op == 4;
+  // forward transform: leaves (every cluster with a basis when single)
+  for (int c = 1; c < nc; ++c)
+    if ((h->child0[c] < 0 || single) && rin[c] > 0 && !(gq && !trans))
       emit({{kLeafIn, O[kLeafIn][c], rin[c], h->end[c] - h->begin[c], h->begin[c], -1, 0}}, kInX, kOutXh,
            xin[c], rin[c], c, &cx[c], 1, kChainPiece);
   // forward transform: up the tree, deepest level first (one segment per group:
   // the chain is latency bound, so its work is spread over many warps)
-  for (int L = h->depth - 1; L >= 1; --L)
+  for (int L = h->depth - 1; L >= 1 && !single; --L)
     for (int p : h->by_level[L]) {
       if (h->child0[p] < 0) continue;
       for (int ch : {h->child0[p], h->child1[p]})
@@ -1467,11 +1472,27 @@ int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
       return h->level[iu] > h->level[iv];
     });
     std::vector<Blk> blks;
-    for (int b : bl) {
-      const int in = trans ? h->far_t[b] : h->far_s[b];
-      blks.push_back({trans ? kSt : kS, O[trans ? kSt : kS][b], rout[own], rin[in], xin[in], in, cx[in]});
+    if (gq && !trans) {
+      // y-hat_tau += B_{tau sigma}^* x|sigma-hat
+      for (int b : bl) {
+        const int in = h->far_s[b];
+        blks.push_back({kS, O[kS][b], rout[own], h->end[in] - h->begin[in], h->begin[in], -1, 0});
+      }
+      emit(blks, kInX, kOutYh, xout[own], rout[own], nc + own, &cy[own], kCoupleSegs, kChunk);
+    } else if (gq) {
+      // y|sigma-hat += B_{tau sigma} x-hat_tau, x-hat_tau = A_tau^* x|tau-hat
+      for (int b : bl) {
+        const int in = h->far_t[b];
+        blks.push_back({kSt, O[kSt][b], h->end[own] - h->begin[own], rin[in], xin[in], in, cx[in]});
+      }
+      emit(blks, kInXh, kOutY, h->begin[own], h->end[own] - h->begin[own], -1, nullptr, kCoupleSegs, kChunk);
+    } else {
+      for (int b : bl) {
+        const int in = trans ? h->far_t[b] : h->far_s[b];
+        blks.push_back({trans ? kSt : kS, O[trans ? kSt : kS][b], rout[own], rin[in], xin[in], in, cx[in]});
+      }
+      emit(blks, kInXh, kOutYh, xout[own], rout[own], nc + own, &cy[own], kCoupleSegs, kChunk);
     }
-    emit(blks, kInXh, kOutYh, xout[own], rout[own], nc + own, &cy[own], kCoupleSegs, kChunk);
   }
   {
     target = &free_groups;
@@ -1490,16 +1511,16 @@ int plan_dir(const gca_h2* h, int dir, DirPlan& P) {
     target = &groups;
   }
   // backward transform, level by level down (y-hat of the parent must be final)
-  for (int L = 2; L <= h->depth; ++L)
+  for (int L = 2; L <= h->depth && !single; ++L)
     for (int c : h->by_level[L]) {
       const int p = h->parent[c];
       if (cy[p] == 0 || rout[c] == 0) continue;  // y-hat_p = 0
       emit({{kDownOut, O[kDownOut][c], rout[c], rout[p], xout[p], nc + p, cy[p]}}, kInYh, kOutYh, xout[c],
            rout[c], nc + c, &cy[c], 1, kChainPiece);
     }
-  // leaf bases
-  for (int c : h->leaves)
-    if (c > 0 && rout[c] > 0 && cy[c] > 0)
+  // leaf bases (every cluster with a basis when single)
+  for (int c = 1; c < nc; ++c)
+    if ((h->child0[c] < 0 || single) && rout[c] > 0 && cy[c] > 0)
       emit({{kLeafOut, O[kLeafOut][c], h->end[c] - h->begin[c], rout[c], xout[c], nc + c, cy[c]}}, kInYh,
            kOutY, h->begin[c], h->end[c] - h->begin[c], -1, nullptr, 1, kChainPiece);
   for (const auto* gl : {&groups, &free_groups})
