@@ -24,6 +24,7 @@ meshes.  Under torchrun every rank runs the same workload on its own GPU
 """
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -628,7 +629,12 @@ def main():
     def step(record):
         nonlocal batch
         # the previous step's batch is freed inside the step but outside the
-        # build's window (cudaFree of its buffers synchronises the device)
+        # build's window (cudaFree of its buffers synchronises the device);
+        # explicitly, since the batch and its handle views form a reference
+        # cycle that the garbage collector would otherwise break at a random
+        # point (inside some other timed window)
+        if batch is not None:
+            batch.free()
         batch = None
         a = ev()
         batch = gca.build_batch(meshes, trees, prm)
@@ -643,6 +649,7 @@ def main():
         return batch.handles
 
     hs = None
+    gc.disable()  # no collection inside the timed windows (the batches are freed explicitly)
     for _ in range(args.warmup):
         hs = step(False)
     stats = [h.stats() for h in hs]
@@ -668,6 +675,7 @@ def main():
     torch.cuda.synchronize()
     gca.profile_enable(False)
     phases = gca.profile_read()
+    gc.enable()
     total_ms = t_start.elapsed_time(t_end)
     clk = clocks.summary()
 
