@@ -110,15 +110,15 @@ def build_evals(st, q):
 TRAFFIC = {
     "couple_entries": ("paper_1810_08429_b300/csrc/build.cu",
                        "ec912a73524dfc2f5deeb36d59ea99ab9d978611e3556ec5ba9c22ea25c64021", 583.32e6),
-    # 10 level launches of one mesh move 26.87 MB in all: the average per launch
+    # launches 4-6 of one mesh's build move 7.83 MB in all: the average per launch
     "green_aca": ("paper_1810_08429_b300/csrc/build.cu",
-                  "ec912a73524dfc2f5deeb36d59ea99ab9d978611e3556ec5ba9c22ea25c64021", 26.87e6 / 10),
+                  "829acb3736ad60ebad42a591e4c232080d0c441059af28f845711561a281dd4e", 7.832e6 / 3),
     "near_entries": ("paper_1810_08429_b300/csrc/build.cu",
                      "ec912a73524dfc2f5deeb36d59ea99ab9d978611e3556ec5ba9c22ea25c64021", 24.62e6),
     "mv_persistent.f32": ("paper_1810_08429_b300/csrc/matvec.cu",
-                          "03beadad4213a75b189180d438b506c2421e7251b43987a9b93c18c9579dda55", 475.92e6),
+                          "7f46538d2225f94780454d9b77d5730c1c3b3126cac83cee24a1b4a32b001b2b", 475.40e6),
     "mv_persistent.bf16": ("paper_1810_08429_b300/csrc/matvec.cu",
-                           "03beadad4213a75b189180d438b506c2421e7251b43987a9b93c18c9579dda55", 269.69e6),
+                           "7f46538d2225f94780454d9b77d5730c1c3b3126cac83cee24a1b4a32b001b2b", 269.56e6),
 }
 
 
