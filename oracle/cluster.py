@@ -33,8 +33,14 @@ import numpy as np
 def build_tree(vertices, triangles, leaf_size):
     v = np.asarray(vertices, dtype=np.float64)
     t = np.asarray(triangles, dtype=np.int64)
-    n = t.shape[0]
     cent = (v[t[:, 0]] + v[t[:, 1]] + v[t[:, 2]]) / 3.0
+    return build_tree_from_centers(cent, leaf_size)
+
+
+def build_tree_from_centers(cent, leaf_size):
+    """The bisection above on given points (one per index)."""
+    cent = np.asarray(cent, dtype=np.float64)
+    n = cent.shape[0]
     perm = np.arange(n, dtype=np.int64)
     begin, end, child0, child1, level = [0], [n], [-1], [-1], [0]
     queue = [0]
