@@ -96,25 +96,45 @@ class ACAResult:
     cols: np.ndarray      # pivot column positions, in selection order
     U: np.ndarray         # column factors (nrows x r)
     V: np.ndarray         # interpolation matrix V^ (nrows x r)
+    gap: float = 0.0      # replay: largest 1 - |R_ij| / max|R| over the steps
+    stop: tuple = None    # replay: (smallest max|R| / (tol first) before a step,
+                          #          max|R| / (tol first) after the last step)
 
 
-def aca(A, tol, tie_rel=2.0 ** -40):
-    """Cross approximation with complete pivoting (Sect. 3)."""
+def aca(A, tol, tie_rel=2.0 ** -40, follow=None):
+    """Cross approximation with complete pivoting (Sect. 3).
+
+    ``follow`` (test infrastructure): a sequence of row positions to take
+    as the pivot rows instead of the argmax, each with the column that
+    complete pivoting would take within that row.  It replays a pivot
+    sequence found elsewhere (late pivots whose residuals are equal to
+    rounding can be taken in either order); ``gap`` and ``stop`` then tell
+    how far each replayed pivot fell below the largest residual and whether
+    the stopping rule agrees with the replayed rank."""
     R = np.array(A, dtype=np.float64, copy=True)
     nr, nc = R.shape
-    rmax = min(nr, nc)
+    rmax = min(nr, nc) if follow is None else len(follow)
     prow, pcol, ucols = [], [], []
     first = None
+    gap, low = 0.0, np.inf
     while len(prow) < rmax:
         absR = np.abs(R)
         big = absR.max()
         if first is None:
             first = big
-        if big == 0.0 or (prow and big <= tol * first):
+        if follow is None and (big == 0.0 or (prow and big <= tol * first)):
             break
-        cand = absR >= big * (1.0 - tie_rel)
-        j = int(np.nonzero(cand.any(axis=0))[0][0])
-        i = int(np.nonzero(cand[:, j])[0][0])
+        if follow is None:
+            cand = absR >= big * (1.0 - tie_rel)
+            j = int(np.nonzero(cand.any(axis=0))[0][0])
+            i = int(np.nonzero(cand[:, j])[0][0])
+        else:
+            i = int(follow[len(prow)])
+            rowbig = absR[i].max()
+            j = int(np.nonzero(absR[i] >= rowbig * (1.0 - tie_rel))[0][0])
+            gap = max(gap, 1.0 - absR[i, j] / big)
+            if prow:
+                low = min(low, big / (tol * first))
         p = R[i, j]
         u = R[:, j] / p
         v = R[i, :].copy()
@@ -131,7 +151,10 @@ def aca(A, tol, tie_rel=2.0 ** -40):
         Vh = scipy.linalg.solve_triangular(L.T, U.T, lower=False, unit_diagonal=True).T
     else:
         Vh = np.zeros((nr, 0))
-    return ACAResult(np.array(prow, dtype=np.int64), np.array(pcol, dtype=np.int64), U, Vh)
+    stop = None
+    if follow is not None and first:
+        stop = (low, np.abs(R).max() / (tol * first) if r < min(nr, nc) else 0.0)
+    return ACAResult(np.array(prow, dtype=np.int64), np.array(pcol, dtype=np.int64), U, Vh, gap, stop)
 
 
 @dataclass
@@ -141,6 +164,7 @@ class Bases:
     E: dict = field(default_factory=dict)        # child -> (r_child x r_parent)
     omega: dict = field(default_factory=dict)    # cluster -> (z, n, w)
     rank: np.ndarray = None
+    replay: dict = field(default_factory=dict)   # cluster -> (gap, stop) of a replayed ACA
 
 
 def needed_clusters(tree, far):
@@ -156,7 +180,7 @@ def needed_clusters(tree, far):
     return needed
 
 
-def build_bases(gal, tree, lo, hi, params, far=None, green=None, nested=True):
+def build_bases(gal, tree, lo, hi, params, far=None, green=None, nested=True, follow=None):
     """Nested cluster bases by Green cross approximation (Sect. 3, Sect. 4),
     for the clusters that need one (all non-root clusters when `far` is
     None); the others get empty bases.  `green(gal, rows, z, nrm, w, d)`
@@ -164,7 +188,10 @@ def build_bases(gal, tree, lo, hi, params, far=None, green=None, nested=True):
     A_tau of the single-layer kernel).  With nested=False every cluster that
     is in an admissible block gets a basis V_tau of its own from the cross
     approximation of A_tau on all of its triangles (the single-level GCA of
-    Sect. 3), and no transfer matrices."""
+    Sect. 3), and no transfer matrices.  ``follow`` (test infrastructure):
+    cluster -> pivot ids to replay in the cross approximations (see ``aca``);
+    the largest gap and the stopping ratios are collected in
+    ``bases.replay``."""
     if green is None:
         green = green_matrix
     if not nested:
@@ -193,7 +220,13 @@ def build_bases(gal, tree, lo, hi, params, far=None, green=None, nested=True):
             c0, c1 = tree["child0"][c], tree["child1"][c]
             rows = np.concatenate([bases.pivots[c0], bases.pivots[c1]])
         A = green(gal, rows, z, nrm, w, diam[c])
-        res = aca(A, params.aca_tol, params.tie_rel)
+        fol = None
+        if follow is not None:
+            pos = {int(q): a for a, q in enumerate(rows)}
+            fol = [pos[int(q)] for q in follow[c]]
+        res = aca(A, params.aca_tol, params.tie_rel, follow=fol)
+        if fol is not None:
+            bases.replay[c] = (res.gap, res.stop)
         bases.pivots[c] = rows[res.rows]
         bases.rank[c] = len(res.rows)
         if cluster.is_leaf(tree, c):

@@ -303,14 +303,16 @@ def cluster_boxes_p1(vertices, triangles, supports, tree):
     return lo, hi
 
 
-def build_p1_h2(vertices, triangles, params, tree=None):
-    """GCA-H^2 of the single-layer matrix in the nodal basis."""
+def build_p1_h2(vertices, triangles, params, tree=None, follow=None):
+    """GCA-H^2 of the single-layer matrix in the nodal basis.  ``follow``
+    (test infrastructure): cluster -> pivot vertex ids to replay in the cross
+    approximations (``gca.aca``)."""
     gal = P1Galerkin(vertices, triangles, params.sauter_q)
     if tree is None:
         tree = build_tree_points(vertices, params.leaf_size)
     lo, hi = cluster_boxes_p1(vertices, triangles, gal.supports, tree)
     far, near = cluster.block_tree(tree, lo, hi, params.eta)
-    bases = build_bases(gal, tree, lo, hi, params, far, green=green_matrix_p1)
+    bases = build_bases(gal, tree, lo, hi, params, far, green=green_matrix_p1, follow=follow)
     S = {}
     for (t, s) in far:
         S[(t, s)] = gal.block(bases.pivots[t], bases.pivots[s])

@@ -276,3 +276,23 @@ def test_needed_clusters_brute_force(h2_1280):
     rank = h2_1280.bases.rank
     assert np.all(rank[~got] == 0)
     assert np.all(rank[got] > 0)
+
+
+def test_aca_replay_of_its_own_pivots():
+    """The replay mode (test infrastructure for rounding-level pivot ties):
+    replaying the cross approximation's own pivot rows reproduces it exactly
+    with no gap and a consistent stop; another order shows up as a gap."""
+    rng = np.random.default_rng(3)
+    sv = 10.0 ** -np.arange(12)
+    A = (rng.normal(size=(40, 12)) * sv) @ rng.normal(size=(12, 30))
+    res = gca.aca(A, 1e-6)
+    rep = gca.aca(A, 1e-6, follow=res.rows)
+    assert np.array_equal(rep.rows, res.rows) and np.array_equal(rep.cols, res.cols)
+    assert np.array_equal(rep.V, res.V)
+    assert rep.gap == 0.0
+    low, after = rep.stop
+    assert low > 1.0 and after <= 1.0
+    swapped = list(res.rows)
+    swapped[0], swapped[1] = swapped[1], swapped[0]
+    assert gca.aca(A, 1e-6, follow=swapped).gap > 0.5
+    assert gca.aca(A, 1e-6, follow=list(res.rows) + [int(np.setdiff1d(np.arange(40), res.rows)[0])]).stop[0] <= 1.0
