@@ -510,6 +510,37 @@ def run_legs(gca, batch, meshes, stats, n, args, dev, stream, hbm_peak):
     hc.check()
     legs["collocation.sphere20480.R16"] = colg
     del hc
+    # the nodal (piecewise linear) basis of Sect. 5 on the 20480-triangle
+    # sphere: 10242 vertex indices, entries summed over triangle pairs of the
+    # support unions
+    v, t = meshes[0]
+    tree = gca.tree_build_points(v, PARAMS["leaf_size"])
+    gca.profile_enable(True)
+    a.record(stream)
+    hp = gca.build_p1(v, t, tree, gca.Params(**PARAMS, flags=gca.DROP_EXPORT))
+    b.record(stream)
+    b.synchronize()
+    ph_p = gca.profile_read()
+    gca.profile_enable(False)
+    st = hp.stats()
+    p1g = {"workload": "nodal basis, sphere20480 (10242 vertices), leaf 64, eta 2, m 4, tol 1e-8, 16 RHS N(0,1)",
+           "build_s": a.elapsed_time(b) * 1e-3, "rank_sum": st["rank_sum"],
+           "phases_ms": {k: round(ms, 3) for k, (_, ms) in ph_p.items()},
+           "regular_pairs": st["n_singular"][0], "touching_pairs": st["n_singular"][1:]}
+    nv = len(v)
+    x64 = torch.from_numpy(synth.normal_rhs(nv, NRHS, seed=0)).to(dev)
+    x32 = x64.float()
+    y64 = torch.empty((NRHS, nv), dtype=torch.float64, device=dev).t()
+    for prec in ("f64", "f32", "bf16"):
+        xin = x64 if prec == "f64" else x32
+        out = y64 if prec == "f64" else torch.empty((NRHS, nv), dtype=torch.float32, device=dev).t()
+        ms = time_products(lambda: hp.matvec(xin, prec, out=out), K, W, stream)
+        byt = product_bytes(st, prec, nv, NRHS)
+        p1g[prec] = {"GB/s": byt / ms / 1e6, "frac_hbm": byt / ms / 1e6 / hbm_peak, "ms": ms,
+                     "err_vs_f64": 0.0 if prec == "f64" else leg_errors([out], [y64])}
+    hp.check()
+    legs["p1.sphere20480.R16"] = p1g
+    del hp
     legs["error_vs_storage.sphere5120"] = error_vs_storage(gca, dev)
     return legs
 

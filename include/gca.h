@@ -210,6 +210,14 @@ int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t max_clusters
                    int32_t* perm, int32_t* begin, int32_t* end, int32_t* child0,
                    int32_t* child1, int32_t* level, int32_t* nclusters);
 
+/* The same bisection on n given points (x, y, z per index, host, [n][3]),
+ * e.g. the vertices of a mesh for the nodal basis of gca_build_p1.
+ * Outputs and errors as gca_tree_build (NUMERIC for a non-finite
+ * coordinate). */
+int gca_tree_build_points(int32_t n, const double* points, int32_t leaf_size, int32_t max_clusters,
+                          int32_t* perm, int32_t* begin, int32_t* end, int32_t* child0,
+                          int32_t* child1, int32_t* level, int32_t* nclusters);
+
 /* Build the GCA-H^2 representation of G on the current device (Sect. 2 -
  * Sect. 4, Sect. 8): cluster boxes, box quadrature, Green quadrature
  * matrices, complete-pivoting cross approximation level by level from the
@@ -300,6 +308,57 @@ int gca_build_single_level(const gca_mesh* mesh, const gca_tree* tree, const gca
                            void* stream, gca_h2** out);
 int gca_build_green_quadrature(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
                                void* stream, gca_h2** out);
+
+/* The single-layer matrix in the continuous piecewise linear (nodal) basis
+ * of Sect. 5: phi_i is linear on every triangle, 1 in vertex i and 0 in
+ * the other vertices, so its support T_i is the fan of triangles around i
+ * and
+ *   g_ij = sum_{t in T_i} sum_{s in T_j} int_t phi_i(x) int_s g(x, y) phi_j(y) dy dx.
+ * Indices are the mesh's VERTICES: the tree is a tree over vertex ids
+ * (e.g. gca_tree_build_points on the vertex positions), n = nv, and the
+ * products take x and y of nv rows in the caller's vertex order.  Every
+ * vertex must belong to a triangle (INVALID_ARG otherwise).
+ *   - cluster boxes: bounding boxes of all triangles in the supports of the
+ *     cluster's basis functions (Sect. 2: the box must contain the
+ *     supports);
+ *   - Green matrices: a_{i nu} = sqrt(w_nu) int g(x, z_nu) phi_i(x) dx and
+ *     a_{i nu+k} = -d_tau sqrt(w_nu) int dg/dn_z(x, z_nu) phi_i(x) dx, the
+ *     7-point rule on every triangle of T_i weighted by the barycentric
+ *     coordinate of vertex i; cross approximation and nesting as gca_build;
+ *   - entries (couplings G|tilde-tau x tilde-sigma, near field
+ *     G|tau-hat x sigma-hat) assembled triangle pair by triangle pair over
+ *     the support unions of the two index lists (the mergesort of Sect. 5,
+ *     gca_support_union): every pair's 3 x 3 matrix
+ *     M_ab = int_t lambda_a int_s g lambda_b (barycentric lambda) is
+ *     computed once and added to the entries of the corners in the lists;
+ *     disjoint pairs by the 7 x 7 rule, touching pairs by Sauter-Schwab
+ *     (order sauter_q) with the barycentric weights of both sample points,
+ *     all in float64.
+ * The matrix is symmetric; the handle works like a gca_build handle
+ * (h2_matvec, h2_matvec_transpose, h2_matvec_noalloc, stats, export with
+ * vertex ids as pivots and vertex order in V and N).  n_singular of the
+ * stats counts touching triangle pairs by case (index 1 vertex, 2 edge,
+ * 3 identical; index 0 the disjoint pairs).  Arguments, errors and
+ * synchronisation as gca_build. */
+int gca_build_p1(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
+                 void* stream, gca_h2** out);
+
+/* The support unions of Sect. 5 on the device, for inspection and tests:
+ * for each of nlists lists of vertex ids (host CSR: list l is
+ * lists[list_ptr[l] .. list_ptr[l + 1]), no repeated id within a list) the
+ * union of the supports T_i of its vertices, one row per triangle in
+ * ascending triangle id: (triangle, l0, l1, l2) with l_c the position in
+ * the list of the triangle's corner c, or -1 when that corner is not in
+ * the list.  Each vertex contributes its support as a list sorted by
+ * triangle; the lists are merged (a bitonic sort of the entries in shared
+ * memory, one CTA per list) and the rows of one triangle combined.
+ * Output (host): rows [cap][4] packed list after list, counts [nlists] the
+ * rows of each list.  cap must be at least sum over the lists of
+ * sum_{i in list} |T_i| (the rows before merging).  Errors: INVALID_ARG
+ * (bad mesh, ids out of range, cap too small), UNSUPPORTED (a list with
+ * more than 16384 support entries), CUDA.  Synchronises `stream`. */
+int gca_support_union(const gca_mesh* mesh, int32_t nlists, const int32_t* list_ptr, const int32_t* lists,
+                      int32_t* rows, int64_t cap, int32_t* counts, void* stream);
 
 /* Sizes of the column side of a handle: op 0 (single layer: the row bases
  * serve the columns, the values repeat those of gca_h2_stats), op 1

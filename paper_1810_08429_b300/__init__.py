@@ -137,6 +137,12 @@ def _load():
                                                   ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
         "gca_build_green_quadrature": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
                                                       ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+        "gca_build_p1": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
+                                        ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+        "gca_tree_build_points": (ctypes.c_int, [ctypes.c_int32, _f64p, ctypes.c_int32, ctypes.c_int32,
+                                                 _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
+        "gca_support_union": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.c_int32, _i32p, _i32p, _i32p,
+                                             ctypes.c_int64, _i32p, vp]),
         "gca_h2_column_stats": (ctypes.c_int, [vp, ctypes.POINTER(_ColStats)]),
         "gca_h2_export_columns": (ctypes.c_int, [vp, ctypes.POINTER(_Dump)]),
     }
@@ -208,6 +214,55 @@ def tree_build(vertices, triangles, leaf_size):
     _check(st, "gca_tree_build")
     for k in ("begin", "end", "child0", "child1", "level"):
         out[k] = out[k][:nc.value].copy()
+    return out
+
+
+def tree_build_points(points, leaf_size):
+    """Cluster tree by recursive bisection of given points
+    (``gca_tree_build_points``, e.g. the vertices for ``build_p1``)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    if pts.ndim != 2 or pts.shape[1] != 3:
+        raise ValueError("points must be (n, 3)")
+    n = pts.shape[0]
+    cap = max(2 * n - 1, 1)
+    out = {k: np.zeros(n if k == "perm" else cap, dtype=np.int32)
+           for k in ("perm", "begin", "end", "child0", "child1", "level")}
+    nc = ctypes.c_int32(0)
+    st = lib.gca_tree_build_points(n, pts.ctypes.data_as(_f64p), leaf_size, cap,
+                                   *[out[k].ctypes.data_as(_i32p)
+                                     for k in ("perm", "begin", "end", "child0", "child1", "level")],
+                                   ctypes.byref(nc))
+    _check(st, "gca_tree_build_points")
+    for k in ("begin", "end", "child0", "child1", "level"):
+        out[k] = out[k][:nc.value].copy()
+    return out
+
+
+def support_union(vertices, triangles, lists, stream=None):
+    """The support unions of Sect. 5 computed on the device
+    (``gca_support_union``): for each list of vertex ids a list of rows
+    (triangle, (l0, l1, l2)) in ascending triangle id, l_c the position of
+    the triangle's corner c in the list or -1."""
+    m, keep_m = _mesh(vertices, triangles)
+    lists = [np.ascontiguousarray(a, dtype=np.int32).reshape(-1) for a in lists]
+    ptr = np.zeros(len(lists) + 1, dtype=np.int32)
+    for i, a in enumerate(lists):
+        ptr[i + 1] = ptr[i] + len(a)
+    flat = np.ascontiguousarray(np.concatenate(lists + [np.zeros(1, np.int32)]), dtype=np.int32)
+    nv = keep_m[0].shape[0]
+    val = np.bincount(np.clip(keep_m[1].reshape(-1), 0, nv), minlength=nv + 1)
+    # ids out of range are refused by the library; they count 0 here
+    cap = int(sum(int(val[np.where((a >= 0) & (a < nv), a, nv)].sum()) for a in lists))
+    rows = np.zeros((max(cap, 1), 4), dtype=np.int32)
+    counts = np.zeros(max(len(lists), 1), dtype=np.int32)
+    _check(lib.gca_support_union(ctypes.byref(m), len(lists), ptr.ctypes.data_as(_i32p), flat.ctypes.data_as(_i32p),
+                                 rows.ctypes.data_as(_i32p), cap, counts.ctypes.data_as(_i32p),
+                                 _stream_ptr(stream)), "gca_support_union")
+    out, at = [], 0
+    for i in range(len(lists)):
+        r = rows[at:at + counts[i]]
+        at += counts[i]
+        out.append([(int(a[0]), (int(a[1]), int(a[2]), int(a[3]))) for a in r])
     return out
 
 
@@ -464,6 +519,14 @@ def build_green_quadrature(vertices, triangles, tree, params, stream=None):
     """Pure Green quadrature of G (gca_build_green_quadrature); returns an ``H2``."""
     return _build_with(lib.gca_build_green_quadrature, "gca_build_green_quadrature", vertices, triangles, tree,
                        params, stream)
+
+
+def build_p1(vertices, triangles, tree, params, stream=None):
+    """gca_build_p1: the single-layer matrix in the continuous piecewise
+    linear (nodal) basis of Sect. 5 over a tree of the VERTICES (e.g.
+    ``tree_build_points(vertices, leaf)``); returns an ``H2`` whose products
+    take x and y with one row per vertex."""
+    return _build_with(lib.gca_build_p1, "gca_build_p1", vertices, triangles, tree, params, stream)
 
 
 def build_collocation(vertices, triangles, tree, params, stream=None):

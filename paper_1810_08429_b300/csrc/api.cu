@@ -81,6 +81,31 @@ int gca_build_double_layer(const gca_mesh* mesh, const gca_tree* tree, const gca
   }
 }
 
+int gca_build_p1(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params, void* stream,
+                 gca_h2** out) {
+  if (!out) {
+    gca::set_error("gca_build_p1: out is NULL");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    return gca::build(mesh, tree, params, static_cast<cudaStream_t>(stream), out, 5);
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_build_p1: host allocation failed");
+    return GCA_ERR_OOM;
+  }
+}
+
+int gca_support_union(const gca_mesh* mesh, int32_t nlists, const int32_t* list_ptr, const int32_t* lists,
+                      int32_t* rows, int64_t cap, int32_t* counts, void* stream) {
+  try {
+    return gca::support_union(mesh, nlists, list_ptr, lists, rows, cap, counts, static_cast<cudaStream_t>(stream));
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_support_union: host allocation failed");
+    return GCA_ERR_OOM;
+  }
+}
+
 int gca_build_collocation(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params, void* stream,
                           gca_h2** out) {
   if (!out) {

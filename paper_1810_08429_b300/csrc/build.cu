@@ -188,7 +188,8 @@ struct AcaJob {
   int r0;         // non-leaf: rank of child0 (its pivots come first)
   int mesh;       // entry of the launch's mesh table
   int kind;       // 0: Green matrix A_tau of the single layer; 1: column matrix of the double
-                  // layer; 2: rows of the collocation matrix (values at the centroids)
+                  // layer; 2: rows of the collocation matrix (values at the centroids);
+                  // 3: rows of the nodal basis (Sect. 5)
   int64_t piv0;   // non-leaf: pivot pool offsets of the children
   int64_t piv1;
   int64_t vh_off; // V^ (rows x r, row-major) in the mesh's V^ pool
@@ -205,6 +206,9 @@ struct AcaMesh {
   double* vh_pool;
   int* rank_out;
   const double* nrm;  // outer unit normals per triangle (column matrices of the double layer)
+  const int* sup_ptr;   // nodal basis: support of vertex v = sup_item[sup_ptr[v] .. sup_ptr[v + 1])
+  const int* sup_item;  // (triangle << 2) | corner of the vertex
+  double bary[7][3];    // barycentric coordinates of the 7-point rule's nodes
 };
 
 // Cross approximation of one job on a thread-block cluster of C CTAs (C = 1
@@ -388,6 +392,25 @@ k_aca(const AcaJob* __restrict__ jobs, const AcaMesh* __restrict__ meshes, int k
         const double dn = sgn * (d == 0 ? dx : (d == 1 ? dy : dz));
         gs += x.w * ir;
         ds += x.w * dn * ir * ir * ir;
+      }
+    } else if (job.kind == 3) {
+      // nodal rows (Sect. 5): the 7-point rule on every triangle of the
+      // vertex's support, each node weighted by the barycentric coordinate of
+      // the vertex's corner
+      const int v = s_tri[i];
+      for (int e = M.sup_ptr[v]; e < M.sup_ptr[v + 1]; ++e) {
+        const int it = M.sup_item[e], cn = it & 3;
+        const P4* xt = M.tq + 7 * (int64_t)(it >> 2);
+#pragma unroll
+        for (int qq = 0; qq < 7; ++qq) {
+          const P4 x = xt[qq];
+          const double wl = x.w * M.bary[qq][cn];
+          const double dx = x.x - zz.x, dy = x.y - zz.y, dz = x.z - zz.z;
+          const double ir = rsqrt(dx * dx + dy * dy + dz * dz);
+          const double dn = sgn * (d == 0 ? dx : (d == 1 ? dy : dz));
+          gs += wl * ir;
+          ds += wl * dn * ir * ir * ir;
+        }
       }
     } else if (job.kind == 2) {
       // collocation rows: a_{i nu} = sqrt(w) g(x_i, z), a_{i nu+k} = -d sqrt(w)
@@ -1730,6 +1753,8 @@ __global__ void k_col_near_entries(const int* __restrict__ near_t, const int* __
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+#include "p1.cuh"
+
 int check_status(DevMem& st, cudaStream_t s, const char* where) {
   int h = 0;
   GCA_TRY_CUDA(cudaMemcpyAsync(&h, st.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1832,12 +1857,41 @@ class AcaLauncher {
 
 }  // namespace
 
+// Supports of the nodal basis functions (Sect. 5): for vertex v the
+// triangles containing it in ascending order, item[ptr[v] .. ptr[v + 1]) =
+// (triangle << 2) | corner.  Every vertex must belong to a triangle.
+int node_supports(const gca_mesh* mesh, std::vector<int>& ptr, std::vector<int>& item, const char* who) {
+  const int nv = mesh->nv, nt = mesh->nt;
+  if (nt >= (1 << 29)) {
+    set_error(std::string(who) + ": too many triangles for the support encoding");
+    return GCA_ERR_UNSUPPORTED;
+  }
+  ptr.assign(nv + 1, 0);
+  for (int64_t e = 0; e < 3LL * nt; ++e) ptr[mesh->triangles[e] + 1]++;
+  for (int v = 0; v < nv; ++v) {
+    if (ptr[v + 1] == 0) {
+      set_error(std::string(who) + ": vertex " + std::to_string(v) + " belongs to no triangle");
+      return GCA_ERR_INVALID_ARG;
+    }
+    ptr[v + 1] += ptr[v];
+  }
+  item.resize(3 * (size_t)nt);
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (int t = 0; t < nt; ++t)
+    for (int c = 0; c < 3; ++c) item[fill[mesh->triangles[3 * (size_t)t + c]]++] = (t << 2) | c;
+  return GCA_OK;
+}
+
 // The whole construction; see the header of this file.
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
           gca_h2** out, int op) {
   auto t0 = std::chrono::steady_clock::now();
   GCA_TRY(validate_mesh(mesh));
-  GCA_TRY(validate_tree(mesh, tree, GCA_MAX_LEAF));
+  // op 5 (nodal basis, Sect. 5): the indices are the vertices
+  const bool p1 = op == 5;
+  gca_mesh shape = *mesh;
+  if (p1) shape.nt = mesh->nv;
+  GCA_TRY(validate_tree(&shape, tree, GCA_MAX_LEAF));
   if (!prm || !(prm->eta > 0.0) || prm->box_gauss_m < 1 || prm->box_gauss_m > GCA_MAX_BOX_M ||
       !(prm->aca_tol >= 0.0) || prm->tri_rule != 7 || prm->sauter_q < 1 ||
       prm->sauter_q > GCA_MAX_SAUTER_Q ||
@@ -1845,17 +1899,22 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     set_error("gca_build: invalid parameters");
     return GCA_ERR_INVALID_ARG;
   }
+  // supports of the nodal basis functions: the triangles at each vertex in
+  // ascending order, as (triangle << 2) | corner
+  std::vector<int> sup_ptr, sup_item;
+  if (p1) GCA_TRY(node_supports(mesh, sup_ptr, sup_item, "gca_build_p1"));
   auto h = std::make_unique<gca_h2>();
   GCA_TRY_CUDA(cudaGetDevice(&h->device));
   h->device += test_hooks().device_skew;
   h->op = op;
   h->params = *prm;
-  h->n = mesh->nt;
+  h->n = p1 ? mesh->nv : mesh->nt;
   h->nv = mesh->nv;
   h->nc = tree->nclusters;
   h->m = prm->box_gauss_m;
   h->k = 6 * h->m * h->m;
   const int n = h->n, nc = h->nc, k = h->k;
+  const int ntri = mesh->nt;  // triangles (n: indices, the vertices for op 5)
   const double margin = prm->omega_margin < 0.0 ? 1.0 / (4.0 * prm->eta) : prm->omega_margin;
   const Rules rules = make_rules(h->m, prm->sauter_q);
 
@@ -1880,30 +1939,39 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
 
   // geometry upload
   std::vector<double> vert(mesh->vertices, mesh->vertices + 3LL * mesh->nv);
-  std::vector<int> tri(mesh->triangles, mesh->triangles + 3LL * n);
+  std::vector<int> tri(mesh->triangles, mesh->triangles + 3LL * ntri);
   GCA_TRY(upload(h->d_vert, vert, st));
   GCA_TRY(upload(h->d_tri, tri, st));
   GCA_TRY(upload(h->d_perm, h->perm, st));
   GCA_TRY(upload(h->d_begin, h->begin, st));
   GCA_TRY(upload(h->d_end, h->end, st));
-  DevMem d_tq, d_area2, d_box, d_diam, d_zq, d_status, d_nrm;
-  GCA_TRY(d_tq.alloc(sizeof(P4) * 7 * (size_t)n));
-  if (op == 1) GCA_TRY(d_nrm.alloc(sizeof(double) * 3 * (size_t)n));
-  GCA_TRY(d_area2.alloc(sizeof(double) * (size_t)n));
+  DevMem d_tq, d_area2, d_box, d_diam, d_zq, d_status, d_nrm, d_sup_ptr, d_sup_item;
+  GCA_TRY(d_tq.alloc(sizeof(P4) * 7 * (size_t)ntri));
+  if (op == 1) GCA_TRY(d_nrm.alloc(sizeof(double) * 3 * (size_t)ntri));
+  GCA_TRY(d_area2.alloc(sizeof(double) * (size_t)ntri));
+  if (p1) {
+    GCA_TRY(upload(d_sup_ptr, sup_ptr, st));
+    GCA_TRY(upload(d_sup_item, sup_item, st));
+  }
   GCA_TRY(d_box.alloc(sizeof(double) * 6 * (size_t)nc));
   GCA_TRY(d_status.alloc(sizeof(int)));
   GCA_TRY_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), st));
   {
     PhaseScope ps__("tri_geom", st);
-    k_tri_geom<<<blocks_for(n, 128), 128, 0, st>>>(n, h->d_vert.as<double>(), h->d_tri.as<int>(), rules,
+    k_tri_geom<<<blocks_for(ntri, 128), 128, 0, st>>>(ntri, h->d_vert.as<double>(), h->d_tri.as<int>(), rules,
                                                   d_tq.as<P4>(), d_area2.as<double>(),
                                                   op == 1 ? d_nrm.as<double>() : nullptr);
   }
   {
     PhaseScope ps__("cluster_boxes", st);
-    k_cluster_boxes<<<blocks_for(32LL * nc, 128), 128, 0, st>>>(
-        nc, h->d_begin.as<int>(), h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(),
-        h->d_vert.as<double>(), d_box.as<double>());
+    if (p1)
+      k_p1_boxes<<<blocks_for(32LL * nc, 128), 128, 0, st>>>(
+          nc, h->d_begin.as<int>(), h->d_end.as<int>(), h->d_perm.as<int>(), d_sup_ptr.as<int>(),
+          d_sup_item.as<int>(), h->d_tri.as<int>(), h->d_vert.as<double>(), d_box.as<double>());
+    else
+      k_cluster_boxes<<<blocks_for(32LL * nc, 128), 128, 0, st>>>(
+          nc, h->d_begin.as<int>(), h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(),
+          h->d_vert.as<double>(), d_box.as<double>());
   }
   GCA_TRY_CUDA(cudaGetLastError());
   std::vector<double> box(6 * (size_t)nc), diam;
@@ -1929,10 +1997,10 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     }
     const double g = std::ldexp(1.0, E - 22);
     near_r2 = (float)std::ldexp(1.0, 2 * (E - 8));
-    GCA_TRY(d_tn.alloc(sizeof(SplitNode) * 7 * (size_t)n));
+    GCA_TRY(d_tn.alloc(sizeof(SplitNode) * 7 * (size_t)ntri));
     PhaseScope ps__("split_nodes", st);
-    k_split_nodes<<<blocks_for(7LL * n, 256), 256, 0, st>>>(7LL * n, d_tq.as<P4>(), o[0], o[1], o[2], g,
-                                                            d_tn.as<SplitNode>());
+    k_split_nodes<<<blocks_for(7LL * ntri, 256), 256, 0, st>>>(7LL * ntri, d_tq.as<P4>(), o[0], o[1], o[2], g,
+                                                               d_tn.as<SplitNode>());
   }
   block_tree(h->child0, h->child1, box, diam, prm->eta, h->far_t, h->far_s, h->near_t, h->near_s);
   GCA_TRY(upload(d_diam, diam, st));
@@ -2002,8 +2070,9 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     }
     GCA_TRY(d_vh.alloc(sizeof(double) * (size_t)std::max<int64_t>(vh_cap, 1)));
     {
-      const AcaMesh am{h->d_perm.as<int>(), d_tq.as<P4>(), d_zq.as<P4>(), d_piv.as<int>(), d_vh.as<double>(),
-                       d_rank.as<int>(), d_nrm.as<double>()};
+      AcaMesh am{h->d_perm.as<int>(), d_tq.as<P4>(), d_zq.as<P4>(), d_piv.as<int>(), d_vh.as<double>(),
+                 d_rank.as<int>(), d_nrm.as<double>(), d_sup_ptr.as<int>(), d_sup_item.as<int>(), {}};
+      std::memcpy(am.bary, rules.bary, sizeof(am.bary));
       GCA_TRY(d_mesh.alloc(sizeof(AcaMesh)));
       GCA_TRY_CUDA(cudaMemcpyAsync(d_mesh.p, &am, sizeof(AcaMesh), cudaMemcpyHostToDevice, st));
       GCA_TRY_CUDA(cudaStreamSynchronize(st));  // am is a local
@@ -2127,7 +2196,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     GCA_TRY(d_piv.alloc(sizeof(int)));
     GCA_TRY_CUDA(cudaStreamSynchronize(st));  // gj is a local
   } else {
-    GCA_TRY(nested_bases(op == 2 ? 2 : 0,
+    GCA_TRY(nested_bases(op == 2 ? 2 : (p1 ? 3 : 0),
                          BasisOut{&h->rank, &h->poff, &h->voff, &h->eoff, &h->v_entries, &h->e_entries, &h->V64,
                                   &h->E64},
                          d_piv, d_rank, piv_used));
@@ -2183,7 +2252,7 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // sigma); a block whose mirror is missing is computed alone
   std::vector<int2> pairs;
   pairs.reserve(nfar / 2 + 1);
-  for (int b = 0; b < nfar && (op == 0 || op == 3); ++b) {
+  for (int b = 0; b < nfar && (op == 0 || op == 3 || p1); ++b) {
     const int t = h->far_t[b], s = h->far_s[b];
     int m = -1;
     {
@@ -2213,11 +2282,14 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   GCA_TRY(h->N64.alloc(sizeof(double) * h->n_entries));
   // bound on touching ordered pairs: sum over vertices of (triangles at v)^2
   std::vector<int64_t> valence(mesh->nv, 0);
-  for (int t = 0; t < 3 * n; ++t) valence[tri[t]]++;
+  for (int64_t t = 0; t < 3LL * ntri; ++t) valence[tri[t]]++;
   int64_t cap = 0;
   for (auto v : valence) cap += v * v;
   DevMem d_items, d_counts;
-  GCA_TRY(d_items.alloc(sizeof(SingularItem) * 3 * (size_t)cap));
+  // the nodal basis: a touching pair occurs in the unions of at most three
+  // row and three column leaves
+  if (p1) cap *= 9;
+  GCA_TRY(d_items.alloc((p1 ? sizeof(P1Item) : sizeof(SingularItem) * 3) * (size_t)cap));
   // sample tables of the three Sauter-Schwab cases (vertex, edge, identical)
   std::vector<SSEntry> ss;
   int ss_off[4] = {0, 0, 0, 0};
@@ -2239,8 +2311,25 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     ss64_off[2] = (int)ss64.size();
     GCA_TRY(upload(d_ss64, ss64, st));
   }
-  GCA_TRY(d_counts.alloc(sizeof(unsigned long long) * 4));
-  GCA_TRY_CUDA(cudaMemsetAsync(d_counts.p, 0, sizeof(unsigned long long) * 4, st));
+  GCA_TRY(d_counts.alloc(sizeof(unsigned long long) * 10));
+  GCA_TRY_CUDA(cudaMemsetAsync(d_counts.p, 0, sizeof(unsigned long long) * 10, st));
+  // the nodal basis: entries are sums over triangle pairs
+  std::vector<SSEntryP1> ssp1;
+  int3 ssp1_off{0, 0, 0}, ssp1_cnt{0, 0, 0};
+  DevMem d_ssp1;
+  if (p1) {
+    GCA_TRY_CUDA(cudaMemsetAsync(h->S64.p, 0, sizeof(double) * h->s_entries, st));
+    GCA_TRY_CUDA(cudaMemsetAsync(h->N64.p, 0, sizeof(double) * h->n_entries, st));
+    sauter_table_p1<1>(rules, ssp1);
+    ssp1_cnt.x = (int)ssp1.size();
+    sauter_table_p1<2>(rules, ssp1);
+    ssp1_off.y = ssp1_cnt.x;
+    ssp1_cnt.y = (int)ssp1.size() - ssp1_off.y;
+    sauter_table_p1<3>(rules, ssp1);
+    ssp1_off.z = ssp1_off.y + ssp1_cnt.y;
+    ssp1_cnt.z = (int)ssp1.size() - ssp1_off.z;
+    GCA_TRY(upload(d_ssp1, ssp1, st));
+  }
   layout_panels(h.get());
   GCA_TRY(alloc_panels(h.get()));
   DevMem d_pjobs;
@@ -2257,7 +2346,98 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     for (int i = 0; i < nd; ++i) duffy.push_back(make_double2(0.5 * (xt[i] + 1.0), 0.5 * wt[i]));
     GCA_TRY(upload(d_duffy, duffy, st));
   }
-  if (nfar > 0 && op == 4) {
+  // nodal basis (Sect. 5): support unions of the pivot lists of the
+  // clusters in admissible blocks and of the leaves in near blocks, then the
+  // pair-by-pair assembly of couplings and near field (mirrored blocks
+  // together)
+  std::vector<UnionJob> ujobs;
+  std::vector<P1Block> p1far, p1near;
+  DevMem d_ujobs, d_ucount, d_urows, d_p1far, d_p1near;
+  if (p1) {
+    std::vector<int> upiv(nc, -1), uleaf(nc, -1);
+    int64_t rows_total = 0;
+    int64_t max_m = 1;
+    int max_len = 1;
+    auto add_union = [&](const int* dlist, const int* hlist, int len) {
+      int64_t m = 0;
+      for (int a = 0; a < len; ++a) m += valence[hlist[a]];
+      ujobs.push_back(UnionJob{dlist, len, 0, rows_total});
+      rows_total += m;
+      max_m = std::max(max_m, m);
+      max_len = std::max(max_len, len);
+      return (int)ujobs.size() - 1;
+    };
+    for (int b = 0; b < nfar; ++b)
+      for (int c : {h->far_t[b], h->far_s[b]})
+        if (upiv[c] < 0)
+          upiv[c] = add_union(d_piv.as<int>() + h->poff[c], h->piv.data() + h->poff[c], h->rank[c]);
+    for (int b = 0; b < nnear; ++b)
+      for (int c : {h->near_t[b], h->near_s[b]})
+        if (uleaf[c] < 0)
+          uleaf[c] = add_union(h->d_perm.as<int>() + h->begin[c], h->perm.data() + h->begin[c],
+                               h->end[c] - h->begin[c]);
+    int pcap = 1;
+    while (pcap < max_m) pcap <<= 1;
+    if (pcap > kUnionMax) {
+      set_error("gca_build_p1: a support union has more than 16384 entries");
+      return GCA_ERR_UNSUPPORTED;
+    }
+    for (const int2& pr : pairs) {
+      const int b = pr.x, m = pr.y, t = h->far_t[b], s = h->far_s[b];
+      p1far.push_back(P1Block{h->soff[b], m >= 0 ? h->soff[m] : -1, h->rank[s], h->rank[t], upiv[t], upiv[s]});
+    }
+    for (int b = 0; b < nnear; ++b) {
+      const int t = h->near_t[b], s = h->near_s[b];
+      int m = -1;
+      if (t != s) {
+        int lo = 0, hi = nnear;
+        while (lo < hi) {
+          const int mid = (lo + hi) / 2;
+          if (h->near_t[mid] < s || (h->near_t[mid] == s && h->near_s[mid] < t)) lo = mid + 1; else hi = mid;
+        }
+        if (lo < nnear && h->near_t[lo] == s && h->near_s[lo] == t) m = lo;
+      }
+      if (t > s && m >= 0) continue;  // computed with its mirror
+      const int nt_ = h->end[t] - h->begin[t], ns_ = h->end[s] - h->begin[s];
+      p1near.push_back(P1Block{h->noff[b], m >= 0 ? h->noff[m] : -1, ns_, nt_, uleaf[t], uleaf[s]});
+    }
+    GCA_TRY(upload(d_ujobs, ujobs, st));
+    GCA_TRY(d_ucount.alloc(sizeof(int) * std::max<size_t>(ujobs.size(), 1)));
+    GCA_TRY(d_urows.alloc(sizeof(int4) * (size_t)std::max<int64_t>(rows_total, 1)));
+    GCA_TRY(upload(d_p1far, p1far, st));
+    GCA_TRY(upload(d_p1near, p1near, st));
+    if (!ujobs.empty()) {
+      const size_t smem = sizeof(unsigned long long) * (size_t)pcap + sizeof(int) * (size_t)(max_len + 1);
+      GCA_TRY_CUDA(cudaFuncSetAttribute(k_support_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      PhaseScope ps__("p1_union", st);
+      k_support_union<<<(unsigned)ujobs.size(), 256, smem, st>>>(d_ujobs.as<UnionJob>(), d_sup_ptr.as<int>(),
+                                                                d_sup_item.as<int>(), pcap, d_urows.as<int4>(),
+                                                                d_ucount.as<int>(), d_status.as<int>());
+      GCA_TRY_CUDA(cudaGetLastError());
+    }
+    BarySplit bs{};
+    for (int i = 0; i < 7; ++i)
+      for (int a = 0; a < 3; ++a) {
+        bs.h[i][a] = (float)rules.bary[i][a];
+        bs.l[i][a] = (float)(rules.bary[i][a] - (double)bs.h[i][a]);
+      }
+    if (!p1far.empty()) {
+      PhaseScope ps__("p1_couple_entries", st);
+      k_p1_entries<false><<<(unsigned)p1far.size(), 256, 0, st>>>(
+          d_p1far.as<P1Block>(), d_ujobs.as<UnionJob>(), d_ucount.as<int>(), d_urows.as<int4>(),
+          h->d_tri.as<int>(), d_tq.as<P4>(), d_tn.as<SplitNode>(), rules, bs, near_r2, h->S64.as<double>(),
+          d_items.as<P1Item>(), cap, d_counts.as<unsigned long long>() + 5, d_status.as<int>());
+      GCA_TRY_CUDA(cudaGetLastError());
+    }
+    if (!p1near.empty()) {
+      PhaseScope ps__("p1_near_entries", st);
+      k_p1_entries<true><<<(unsigned)p1near.size(), 256, 0, st>>>(
+          d_p1near.as<P1Block>(), d_ujobs.as<UnionJob>(), d_ucount.as<int>(), d_urows.as<int4>(),
+          h->d_tri.as<int>(), d_tq.as<P4>(), d_tn.as<SplitNode>(), rules, bs, near_r2, h->N64.as<double>(),
+          d_items.as<P1Item>(), cap, d_counts.as<unsigned long long>(), d_status.as<int>());
+      GCA_TRY_CUDA(cudaGetLastError());
+    }
+  } else if (nfar > 0 && op == 4) {
     std::vector<GqJob> gj;
     for (int b = 0; b < nfar; ++b) gj.push_back({h->far_t[b], h->far_s[b], h->soff[b]});
     DevMem d_gj;
@@ -2306,7 +2486,9 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   }
 
   // near field
-  if (nnear > 0 && op == 2) {
+  if (p1) {
+    // launched with the couplings above
+  } else if (nnear > 0 && op == 2) {
     const size_t smem = sizeof(P4) * 7 * (size_t)h->max_leaf;
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_col_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
@@ -2348,7 +2530,21 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // near-field kernels run, the other while the singular and panel kernels run
   PlanHandle plan = plan_new();
   plan_direction(h.get(), 0, plan.get());
-  if (nnear > 0) {
+  if (p1) {
+    GCA_TRY(check_status(d_status, st, "near field"));
+    unsigned long long counts[5];
+    GCA_TRY_CUDA(cudaMemcpyAsync(counts, d_counts.p, sizeof(counts), cudaMemcpyDeviceToHost, st));
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));
+    for (int c = 0; c <= 3; ++c) h->n_singular[c] = (int64_t)counts[c];
+    if (counts[4] > 0) {
+      PhaseScope ps_sing("p1_singular", st);
+      k_p1_singular<<<blocks_for(32LL * (int64_t)counts[4], 256), 256, 0, st>>>(
+          d_items.as<P1Item>(), d_counts.as<unsigned long long>(), cap, h->d_tri.as<int>(),
+          h->d_vert.as<double>(), d_area2.as<double>(), d_ssp1.as<SSEntryP1>(), ssp1_off, ssp1_cnt,
+          h->N64.as<double>());
+      GCA_TRY_CUDA(cudaGetLastError());
+    }
+  } else if (nnear > 0) {
     GCA_TRY(check_status(d_status, st, "near field"));
     unsigned long long counts[4];
     GCA_TRY_CUDA(cudaMemcpyAsync(counts, d_counts.p, sizeof(counts), cudaMemcpyDeviceToHost, st));
@@ -2411,6 +2607,100 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   h->build_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = h.release();
+  return GCA_OK;
+}
+
+// gca_support_union: the lists' unions on the device, copied back compacted.
+int support_union(const gca_mesh* mesh, int nlists, const int32_t* list_ptr, const int32_t* lists,
+                  int32_t* rows, int64_t cap, int32_t* counts, cudaStream_t st) {
+  GCA_TRY(validate_mesh(mesh));
+  if (nlists < 0 || (nlists > 0 && (!list_ptr || !lists || !rows || !counts)) || cap < 0) {
+    set_error("gca_support_union: bad arguments");
+    return GCA_ERR_INVALID_ARG;
+  }
+  if (nlists == 0) return GCA_OK;
+  std::vector<int> sup_ptr, sup_item;
+  GCA_TRY(node_supports(mesh, sup_ptr, sup_item, "gca_support_union"));
+  if (list_ptr[0] != 0) {
+    set_error("gca_support_union: list_ptr[0] must be 0");
+    return GCA_ERR_INVALID_ARG;
+  }
+  const int64_t total = list_ptr[nlists];
+  std::vector<char> seen(mesh->nv, 0);
+  std::vector<int64_t> bound(nlists + 1, 0);
+  int64_t max_m = 1;
+  int max_len = 1;
+  for (int l = 0; l < nlists; ++l) {
+    if (list_ptr[l + 1] < list_ptr[l]) {
+      set_error("gca_support_union: list_ptr not ascending");
+      return GCA_ERR_INVALID_ARG;
+    }
+    int64_t m = 0;
+    for (int64_t a = list_ptr[l]; a < list_ptr[l + 1]; ++a) {
+      const int v = lists[a];
+      if (v < 0 || v >= mesh->nv || seen[v]) {
+        set_error("gca_support_union: vertex id out of range or repeated in list " + std::to_string(l));
+        return GCA_ERR_INVALID_ARG;
+      }
+      seen[v] = 1;
+      m += sup_ptr[v + 1] - sup_ptr[v];
+    }
+    for (int64_t a = list_ptr[l]; a < list_ptr[l + 1]; ++a) seen[lists[a]] = 0;
+    bound[l + 1] = bound[l] + m;
+    max_m = std::max(max_m, m);
+    max_len = std::max<int>(max_len, (int)(list_ptr[l + 1] - list_ptr[l]));
+  }
+  if (bound[nlists] > cap) {
+    set_error("gca_support_union: cap below the support entries of the lists");
+    return GCA_ERR_INVALID_ARG;
+  }
+  int pcap = 1;
+  while (pcap < max_m) pcap <<= 1;
+  if (pcap > kUnionMax) {
+    set_error("gca_support_union: a list has more than 16384 support entries");
+    return GCA_ERR_UNSUPPORTED;
+  }
+  DevMem d_ptr, d_item, d_lists, d_jobs, d_rows, d_counts, d_status;
+  GCA_TRY(upload(d_ptr, sup_ptr, st));
+  GCA_TRY(upload(d_item, sup_item, st));
+  std::vector<int> hl(lists, lists + total);
+  GCA_TRY(upload(d_lists, hl, st));
+  std::vector<UnionJob> jobs(nlists);
+  for (int l = 0; l < nlists; ++l)
+    jobs[l] = UnionJob{d_lists.as<int>() + list_ptr[l], (int)(list_ptr[l + 1] - list_ptr[l]), 0, bound[l]};
+  GCA_TRY(upload(d_jobs, jobs, st));
+  GCA_TRY(d_rows.alloc(sizeof(int4) * (size_t)std::max<int64_t>(bound[nlists], 1)));
+  GCA_TRY(d_counts.alloc(sizeof(int) * (size_t)nlists));
+  GCA_TRY(d_status.alloc(sizeof(int)));
+  GCA_TRY_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), st));
+  const size_t smem = sizeof(unsigned long long) * (size_t)pcap + sizeof(int) * (size_t)(max_len + 1);
+  GCA_TRY_CUDA(cudaFuncSetAttribute(k_support_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_support_union<<<(unsigned)nlists, 256, smem, st>>>(d_jobs.as<UnionJob>(), d_ptr.as<int>(), d_item.as<int>(),
+                                                       pcap, d_rows.as<int4>(), d_counts.as<int>(),
+                                                       d_status.as<int>());
+  GCA_TRY_CUDA(cudaGetLastError());
+  std::vector<int4> hrows((size_t)std::max<int64_t>(bound[nlists], 1));
+  std::vector<int> hc(nlists);
+  int hs = 0;
+  GCA_TRY_CUDA(cudaMemcpyAsync(hrows.data(), d_rows.p, sizeof(int4) * hrows.size(), cudaMemcpyDeviceToHost, st));
+  GCA_TRY_CUDA(cudaMemcpyAsync(hc.data(), d_counts.p, sizeof(int) * nlists, cudaMemcpyDeviceToHost, st));
+  GCA_TRY_CUDA(cudaMemcpyAsync(&hs, d_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GCA_TRY_CUDA(cudaStreamSynchronize(st));
+  if (hs) {
+    set_error("gca_support_union: internal capacity exceeded");
+    return GCA_ERR_INVALID_ARG;
+  }
+  int64_t at = 0;
+  for (int l = 0; l < nlists; ++l) {
+    counts[l] = hc[l];
+    for (int r = 0; r < hc[l]; ++r, ++at) {
+      const int4 v = hrows[bound[l] + r];
+      rows[4 * at] = v.x;
+      rows[4 * at + 1] = v.y;
+      rows[4 * at + 2] = v.z;
+      rows[4 * at + 3] = v.w;
+    }
+  }
   return GCA_OK;
 }
 

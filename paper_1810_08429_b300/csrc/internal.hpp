@@ -130,9 +130,12 @@ class PhaseScope {
 // Entry points of the translation units.
 // op 0: the single-layer matrix G; op 1: the double-layer matrix K; op 2: the
 // collocation matrix C of the single layer; op 3: G by single-level GCA; op 4:
-// G by Green quadrature
+// G by Green quadrature; op 5: G in the nodal (piecewise linear) basis
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
           gca_h2** out, int op = 0);
+// gca_support_union (build.cu)
+int support_union(const gca_mesh* mesh, int nlists, const int32_t* list_ptr, const int32_t* lists,
+                  int32_t* rows, int64_t cap, int32_t* counts, cudaStream_t st);
 // Product plan (matvec.cu): plan_direction runs the host planning of one
 // direction (it needs the ranks, block lists and panel offsets; the build
 // calls it while its kernels run); finish_plan plans what is left and
@@ -263,7 +266,8 @@ struct gca_h2 {
   // columns), 1 the double layer, 2 the collocated single layer.  For op 1 and
   // 2 the columns have bases W, transfers F and pivots tilde-sigma' of their
   // own (the double layer's; the Galerkin single layer's under the
-  // collocation rows) and the couplings are r_tau x r'_sigma.
+  // collocation rows) and the couplings are r_tau x r'_sigma.  Op 5 (the
+  // nodal basis) is one-sided like op 0 with the vertices as indices.
   int op = 0;
   std::vector<int> rank2;              // r'_sigma (op 1)
   std::vector<int64_t> xoff2;

@@ -1,0 +1,613 @@
+// Continuous piecewise linear (nodal) basis functions, Sect. 5: kernels of
+// gca_build_p1 and gca_support_union.  Included by build.cu inside its
+// anonymous namespace (P4, Rules, kInv4Pi and sauter_piece come from there).
+//
+// The basis function phi_i of vertex i is linear on every triangle of its
+// support T_i (the fan around i), so every integral over T_i is a sum over
+// triangles t with the barycentric coordinate lambda_c of i's corner c in t
+// as weight.  A support entry packs (t << 2) | c.
+//
+//   k_p1_boxes      bounding box of the supports of a cluster's vertices
+//   k_aca kind 3    Green matrix rows: the 7-point rule on every t in T_i,
+//                   each node weighted by lambda_c (in build.cu)
+//   k_support_union the union of the supports of an index list (Sect. 5),
+//                   one row (t, l0, l1, l2) per triangle: the entries
+//                   (t, c, position) of all supports are sorted by (t, c) in
+//                   shared memory and the entries of one triangle combined
+//   k_p1_entries    one CTA per block: every triangle pair of the two unions
+//                   gives a 3 x 3 matrix M_ab = int_t lambda_a int_s g
+//                   lambda_b, added to the entries (l_a, l_b) of the block
+//                   (and to the mirrored block); disjoint pairs by the 7 x 7
+//                   rule in float-pair arithmetic on the FP32 pipe (float64
+//                   for close pairs), touching pairs handed to
+//   k_p1_singular   Sauter-Schwab with barycentric weights, one warp per
+//                   ordered pair (a mirrored block's pair is integrated in
+//                   its own order, as the rule is not symmetric in rounding
+//                   and quadrature error)
+#pragma once
+
+constexpr int kUnionMax = 16384;  // support entries of one list (shared-memory sort)
+
+// one warp per cluster: min / max over the vertices of the triangles in the
+// supports of the cluster's vertices
+__global__ void k_p1_boxes(int nc, const int* __restrict__ begin, const int* __restrict__ end,
+                           const int* __restrict__ perm, const int* __restrict__ sup_ptr,
+                           const int* __restrict__ sup_item, const int* __restrict__ tri,
+                           const double* __restrict__ vert, double* __restrict__ box) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nc) return;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = begin[warp] + lane; i < end[warp]; i += 32) {
+    const int v = perm[i];
+    for (int e = sup_ptr[v]; e < sup_ptr[v + 1]; ++e) {
+      const int t = sup_item[e] >> 2;
+      for (int a = 0; a < 3; ++a) {
+        const int w = tri[3 * t + a];
+        for (int d = 0; d < 3; ++d) {
+          const double x = vert[3 * w + d];
+          lo[d] = fmin(lo[d], x);
+          hi[d] = fmax(hi[d], x);
+        }
+      }
+    }
+  }
+  for (int off = 16; off; off >>= 1)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
+      hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+    }
+  if (lane == 0)
+    for (int d = 0; d < 3; ++d) {
+      box[6 * warp + d] = lo[d];
+      box[6 * warp + 3 + d] = hi[d];
+    }
+}
+
+// One support union: the list's vertex ids, its length and the first row of
+// its output in the row pool (room for the sum of the list's support sizes).
+struct UnionJob {
+  const int* list;
+  int len;
+  int pad;
+  int64_t out;
+};
+
+// One CTA per list.  Shared memory: `pcap` 64-bit keys (a power of two at
+// least the list's support entries) and len + 1 offsets.  Key of an entry:
+// triangle (bits 32..63), corner (30..31), position in the list (0..29).
+// After the bitonic sort the entries of a triangle are adjacent (at most
+// three, one per corner); the first of them writes the row.
+__global__ void __launch_bounds__(256)
+k_support_union(const UnionJob* __restrict__ jobs, const int* __restrict__ sup_ptr,
+                const int* __restrict__ sup_item, int pcap, int4* __restrict__ rows, int* __restrict__ counts,
+                int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);
+  const UnionJob job = jobs[blockIdx.x];
+  int* off = reinterpret_cast<int*>(key + pcap);  // len + 1
+  __shared__ int s_part[256];
+  __shared__ int s_total;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int a = tid; a < job.len; a += nth) {
+    const int v = job.list[a];
+    off[a + 1] = sup_ptr[v + 1] - sup_ptr[v];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    off[0] = 0;
+    for (int a = 0; a < job.len; ++a) off[a + 1] += off[a];
+  }
+  __syncthreads();
+  const int m = off[job.len];
+  if (m > pcap) {  // the host sizes pcap from the same counts; never taken
+    if (tid == 0) {
+      atomicOr(status, 2);
+      counts[blockIdx.x] = 0;
+    }
+    return;
+  }
+  int P = 1;
+  while (P < m) P <<= 1;
+  for (int a = tid; a < job.len; a += nth) {
+    const int v = job.list[a];
+    const int e0 = sup_ptr[v];
+    for (int e = e0; e < sup_ptr[v + 1]; ++e) {
+      const int it = sup_item[e];
+      key[off[a] + (e - e0)] = ((unsigned long long)(unsigned)(it >> 2) << 32) |
+                               ((unsigned long long)(it & 3) << 30) | (unsigned long long)a;
+    }
+  }
+  for (int i = m + tid; i < P; i += nth) key[i] = ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < P; i += nth) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned long long x = key[i], y = key[l];
+          if ((x > y) == ((i & k) == 0)) {
+            key[i] = y;
+            key[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // rows: one per run of equal triangles; a chunk of the sorted entries per
+  // thread, the heads counted, scanned over the threads, then written
+  const int chunk = (m + nth - 1) / nth;
+  const int c0 = min(m, tid * chunk), c1 = min(m, c0 + chunk);
+  auto head = [&](int i) { return i == 0 || (key[i] >> 32) != (key[i - 1] >> 32); };
+  int cnt = 0;
+  for (int i = c0; i < c1; ++i) cnt += head(i);
+  s_part[tid] = cnt;
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int t = 0; t < nth; ++t) {
+      const int c = s_part[t];
+      s_part[t] = acc;
+      acc += c;
+    }
+    s_total = acc;
+  }
+  __syncthreads();
+  int r = s_part[tid];
+  for (int i = c0; i < c1; ++i) {
+    if (!head(i)) continue;
+    const unsigned t = (unsigned)(key[i] >> 32);
+    int loc[3] = {-1, -1, -1};
+    for (int j = i; j < m && (unsigned)(key[j] >> 32) == t; ++j)
+      loc[(key[j] >> 30) & 3] = (int)(key[j] & 0x3fffffffu);
+    rows[job.out + r] = make_int4((int)t, loc[0], loc[1], loc[2]);
+    ++r;
+  }
+  if (tid == 0) counts[blockIdx.x] = s_total;
+}
+
+// A block of the nodal matrix: the rows' and the columns' support unions
+// (indices into the union jobs), the block's first entry and row stride, and
+// the mirrored block (G is symmetric: base2 < 0 when there is none).
+struct P1Block {
+  int64_t base;
+  int64_t base2;
+  int ld;
+  int ld2;
+  int ut;
+  int us;
+};
+
+// A touching triangle pair of one block for k_p1_singular.
+struct P1Item {
+  int64_t base;
+  int64_t base2;
+  int ld;
+  int ld2;
+  int ti;
+  int tj;
+  int lr[3];  // positions of ti's corners in the row list (-1: none)
+  int lc[3];  // positions of tj's corners in the column list
+  int cs;     // shared vertices: 1 vertex, 2 edge, 3 identical
+  int pad;
+};
+
+__device__ __forceinline__ void p1_scatter(double* __restrict__ out, int64_t base, int ld, int64_t base2, int ld2,
+                                           const int lr[3], const int lc[3], const double M[3][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (lr[a] < 0) continue;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (lc[b] < 0) continue;
+      atomicAdd(out + base + (int64_t)lr[a] * ld + lc[b], M[a][b]);
+      if (base2 >= 0) atomicAdd(out + base2 + (int64_t)lc[b] * ld2 + lr[a], M[a][b]);
+    }
+  }
+}
+
+// 3 x 3 matrix of a disjoint pair in float64 (7 x 7 rule): the kernel
+// values contracted with the barycentric weights of both nodes as they are
+// formed, c_a(y_j) = sum_i w_i lambda_a(x_i) / |x_i - y_j| and
+// M_ab += c_a w_j lambda_b(y_j).  Used for pairs whose nodes come closer
+// than the float-pair arithmetic below resolves.
+__device__ __noinline__ void p1_pair64(const P4* __restrict__ xq, const P4* __restrict__ yq, const Rules& rules,
+                                       double (*M)[3]) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) M[a][b] = 0.0;
+  for (int j = 0; j < 7; ++j) {
+    const P4 y = yq[j];
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      const P4 x = xq[i];
+      const double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+      const double t = x.w * rsqrt(dx * dx + dy * dy + dz * dz);
+      c0 += t * rules.bary[i][0];
+      c1 += t * rules.bary[i][1];
+      c2 += t * rules.bary[i][2];
+    }
+    const double wy = y.w * kInv4Pi;
+    for (int b = 0; b < 3; ++b) {
+      const double wb = wy * rules.bary[j][b];
+      M[0][b] += c0 * wb;
+      M[1][b] += c1 * wb;
+      M[2][b] += c2 * wb;
+    }
+  }
+}
+
+// The barycentric coordinates of the 7-point rule's nodes as float pairs.
+struct BarySplit {
+  float h[7][3];
+  float l[7][3];
+};
+
+// Node weights of one triangle times the barycentric coordinates, as float
+// pairs: W_ia = w_i lambda_a(x_i) = (w_h + w_l)(b_h + b_l) to first order.
+__device__ __forceinline__ void p1_weights(const SplitNode* __restrict__ nd, const BarySplit& bs, float (*wh)[3],
+                                           float (*wl)[3]) {
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    const float w = nd[i].hi.w, wlo = nd[i].lo.w;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float h = __fmul_rn(w, bs.h[i][a]);
+      wh[i][a] = h;
+      wl[i][a] = __fadd_rn(__fmaf_rn(w, bs.h[i][a], -h), __fmaf_rn(w, bs.l[i][a], __fmul_rn(wlo, bs.h[i][a])));
+    }
+  }
+}
+
+// 1 / |x - y| of two split nodes as a float pair y0 + dy (the recipe of
+// regular_entry_split: exact high differences, |d|^2 as a float pair,
+// rsqrtf refined by one Newton step); r2 receives the high part of |d|^2.
+__device__ __forceinline__ void inv_dist_split(float xh0, float xh1, float xh2, float xl0, float xl1, float xl2,
+                                               const float4& yh, const float4& yl, float& y0, float& dy,
+                                               float& r2) {
+  const float dh0 = __fsub_rn(xh0, yh.x), dl0 = __fsub_rn(xl0, yl.x);
+  const float dh1 = __fsub_rn(xh1, yh.y), dl1 = __fsub_rn(xl1, yl.y);
+  const float dh2 = __fsub_rn(xh2, yh.z), dl2 = __fsub_rn(xl2, yl.z);
+  const float p0 = __fmul_rn(dh0, dh0), p1 = __fmul_rn(dh1, dh1), p2 = __fmul_rn(dh2, dh2);
+  float low = __fmaf_rn(dh0, dh0, -p0);
+  low = __fadd_rn(low, __fmaf_rn(dh1, dh1, -p1));
+  low = __fadd_rn(low, __fmaf_rn(dh2, dh2, -p2));
+  low = __fmaf_rn(__fadd_rn(__fadd_rn(dh0, dh0), dl0), dl0, low);
+  low = __fmaf_rn(__fadd_rn(__fadd_rn(dh1, dh1), dl1), dl1, low);
+  low = __fmaf_rn(__fadd_rn(__fadd_rn(dh2, dh2), dl2), dl2, low);
+  float s01, e01, rh, e2;
+  two_sum(p0, p1, s01, e01);
+  two_sum(s01, p2, rh, e2);
+  const float rl = __fadd_rn(low, __fadd_rn(e01, e2));
+  r2 = rh;
+  y0 = rsqrtf(__fadd_rn(rh, rl));
+  const float u = __fmul_rn(y0, y0), uu = __fmaf_rn(y0, y0, -u);
+  const float m = __fmul_rn(u, rh), me = __fmaf_rn(u, rh, -m);
+  const float rho = __fmaf_rn(-uu, rh, __fmaf_rn(-u, rl, __fsub_rn(__fsub_rn(1.f, m), me)));
+  dy = __fmul_rn(__fmul_rn(0.5f, y0), rho);
+}
+
+// s + (th + tl) for float pairs s = (sh, sl)
+__device__ __forceinline__ void pair_acc(float& sh, float& sl, float th, float tl) {
+  float ns, ne;
+  two_sum(sh, th, ns, ne);
+  sh = ns;
+  sl = __fadd_rn(sl, __fadd_rn(ne, tl));
+}
+
+// (ah + al)(bh + bl) as a float pair to first order
+__device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl, float& th, float& tl) {
+  th = __fmul_rn(ah, bh);
+  tl = __fadd_rn(__fmaf_rn(ah, bh, -th), __fmaf_rn(ah, bl, __fmul_rn(al, bh)));
+}
+
+constexpr int kP1Chunk = 64;  // column triangles staged in shared memory at a time
+
+// One CTA per block.  Columns are staged in chunks (split nodes and weights
+// W'_jb in shared memory); a work item is a row triangle p with a residue g
+// of the chunk's columns modulo G (G groups when the rows are fewer than the
+// threads) and keeps p's split nodes and weights W_ia in registers.  A pair's
+// 3 x 3 matrix is formed on the FP32 pipe in float-pair arithmetic (about
+// 48 significant bits, as the single layer's coupling entries):
+//   c_a(y_j) = sum_i W_ia / |x_i - y_j|,  M_ab += c_a W'_jb,
+// and rounded to float64 once.  NEAR blocks test every pair for shared
+// vertices first and append touching pairs to the singular list; a disjoint
+// pair with nodes closer than sqrt(near_r2) is computed again in float64.
+// The output is zero on entry (atomic sums).
+template <bool NEAR>
+__global__ void __launch_bounds__(256)
+k_p1_entries(const P1Block* __restrict__ blocks, const UnionJob* __restrict__ ujobs,
+             const int* __restrict__ ucount, const int4* __restrict__ urows, const int* __restrict__ tri,
+             const P4* __restrict__ tq, const SplitNode* __restrict__ tn, Rules rules, BarySplit bs,
+             float near_r2, double* __restrict__ out, P1Item* __restrict__ items, int64_t cap,
+             unsigned long long* __restrict__ counts, int* __restrict__ status) {
+  __shared__ float4 ysh[kP1Chunk * 7];
+  __shared__ float4 ysl[kP1Chunk * 7];
+  __shared__ float2 ysw[kP1Chunk * 21];  // W'_jb (hi, lo), j-major
+  __shared__ int4 cr[kP1Chunk];
+  __shared__ int cv[kP1Chunk * 3];
+  const P1Block B = blocks[blockIdx.x];
+  const int4* R = urows + ujobs[B.ut].out;
+  const int4* C = urows + ujobs[B.us].out;
+  const int nr = ucount[B.ut], ncol = ucount[B.us];
+  const int tid = threadIdx.x, nth = blockDim.x;
+  int G = 1;
+  while (G < 32 && nr * G * 2 <= nth) G *= 2;
+  unsigned long long regular = 0;
+  for (int q0 = 0; q0 < ncol; q0 += kP1Chunk) {
+    const int cn = min(kP1Chunk, ncol - q0);
+    __syncthreads();
+    for (int i = tid; i < cn * 7; i += nth) {
+      const SplitNode nd = tn[7 * (int64_t)C[q0 + i / 7].x + i % 7];
+      ysh[i] = nd.hi;
+      ysl[i] = nd.lo;
+    }
+    for (int i = tid; i < cn; i += nth) {
+      const int4 c = C[q0 + i];
+      cr[i] = c;
+      if (NEAR)
+        for (int a = 0; a < 3; ++a) cv[3 * i + a] = tri[3 * c.x + a];
+      float wh[7][3], wl[7][3];
+      p1_weights(tn + 7 * (int64_t)c.x, bs, wh, wl);
+      for (int j = 0; j < 7; ++j)
+        for (int b = 0; b < 3; ++b) ysw[21 * i + 3 * j + b] = make_float2(wh[j][b], wl[j][b]);
+    }
+    __syncthreads();
+    for (int w = tid; w < nr * G; w += nth) {
+      const int p = w / G, g = w - (w / G) * G;
+      const int4 rp = R[p];
+      const int lr[3] = {rp.y, rp.z, rp.w};
+      const SplitNode* xn = tn + 7 * (int64_t)rp.x;
+      float xh[7][3], xl[7][3], Wh[7][3], Wl[7][3];
+#pragma unroll
+      for (int i = 0; i < 7; ++i) {
+        const SplitNode nd = xn[i];
+        xh[i][0] = nd.hi.x; xh[i][1] = nd.hi.y; xh[i][2] = nd.hi.z;
+        xl[i][0] = nd.lo.x; xl[i][1] = nd.lo.y; xl[i][2] = nd.lo.z;
+      }
+      p1_weights(xn, bs, Wh, Wl);
+      int tv[3] = {0, 0, 0};
+      if (NEAR)
+        for (int a = 0; a < 3; ++a) tv[a] = tri[3 * rp.x + a];
+      for (int q = g; q < cn; q += G) {
+        const int4 cq = cr[q];
+        const int lc[3] = {cq.y, cq.z, cq.w};
+        if (NEAR) {
+          int sh = 0;
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            sh += (tv[a] == cv[3 * q]) + (tv[a] == cv[3 * q + 1]) + (tv[a] == cv[3 * q + 2]);
+          if (sh) {
+            // The Sauter-Schwab rule depends on the order of the pair (the
+            // vertex orders follow the first triangle), so the mirrored
+            // block's pair (s, t) is integrated as a pair of its own.
+            const int nit = B.base2 >= 0 ? 2 : 1;
+            const unsigned long long slot = atomicAdd(&counts[4], (unsigned long long)nit);
+            atomicAdd(&counts[sh], (unsigned long long)nit);
+            if (slot + nit <= (unsigned long long)cap) {
+              for (int m = 0; m < nit; ++m) {
+                P1Item it;
+                it.base = m ? B.base2 : B.base;
+                it.base2 = -1;
+                it.ld = m ? B.ld2 : B.ld;
+                it.ld2 = 0;
+                it.ti = m ? cq.x : rp.x;
+                it.tj = m ? rp.x : cq.x;
+                for (int a = 0; a < 3; ++a) {
+                  it.lr[a] = m ? lc[a] : lr[a];
+                  it.lc[a] = m ? lr[a] : lc[a];
+                }
+                it.cs = sh;
+                it.pad = 0;
+                items[slot + m] = it;
+              }
+            } else {
+              atomicOr(status, 2);
+            }
+            continue;
+          }
+        }
+        float Mh[3][3], Ml[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) Mh[a][b] = Ml[a][b] = 0.f;
+        float mr = 3.0e38f;
+#pragma unroll 1
+        for (int j = 0; j < 7; ++j) {
+          const float4 yh = ysh[7 * q + j], yl = ysl[7 * q + j];
+          float ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+          for (int i = 0; i < 7; ++i) {
+            float y0, dy, r2;
+            inv_dist_split(xh[i][0], xh[i][1], xh[i][2], xl[i][0], xl[i][1], xl[i][2], yh, yl, y0, dy, r2);
+            mr = fminf(mr, r2);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              float th, tl;
+              pair_mul(Wh[i][a], Wl[i][a], y0, dy, th, tl);
+              pair_acc(ch[a], cl[a], th, tl);
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const float2 wy = ysw[21 * q + 3 * j + b];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              float th, tl;
+              pair_mul(ch[a], cl[a], wy.x, wy.y, th, tl);
+              pair_acc(Mh[a][b], Ml[a][b], th, tl);
+            }
+          }
+        }
+        double M[3][3];
+        if (NEAR && mr < near_r2) {
+          p1_pair64(tq + 7 * (int64_t)rp.x, tq + 7 * (int64_t)cq.x, rules, M);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) M[a][b] = ((double)Mh[a][b] + (double)Ml[a][b]) * kInv4Pi;
+        }
+        p1_scatter(out, B.base, B.ld, B.base2, B.ld2, lr, lc, M);
+        ++regular;
+      }
+    }
+  }
+  for (int o = 16; o; o >>= 1) regular += __shfl_xor_sync(0xffffffffu, regular, o);
+  if ((tid & 31) == 0 && regular) atomicAdd(&counts[0], regular);
+}
+
+// A Sauter-Schwab sample of the nodal basis: the coefficients of
+// h(eta) = (x - y) / xi in the edge vectors (as SSEntry64), the weight
+// (Gauss weights times the piece's Jacobian without xi^3) and the reference
+// coordinates u^(eta), v^(eta) of both points (u = xi u^, v = xi v^).
+struct __align__(16) SSEntryP1 {
+  double c[4];
+  double w;
+  double uh[2];
+  double vh[2];
+  double pad;
+};
+
+template <int CASE>
+void sauter_table_p1(const Rules& rules, std::vector<SSEntryP1>& out) {
+  const int q = rules.q, q3 = q * q * q;
+  constexpr int pieces = CASE == 3 ? 6 : (CASE == 2 ? 5 : 2);
+  for (int s = 0; s < pieces * q3; ++s) {
+    const int piece = s / q3, r = s % q3;
+    const int a = r / (q * q), b = (r / q) % q, c = r % q;
+    long double u1, u2, v1, v2;
+    const long double wj = sauter_piece<CASE, long double>(piece, rules.ss_t[a], rules.ss_t[b], rules.ss_t[c],
+                                                           u1, u2, v1, v2);
+    SSEntryP1 e{};
+    if (CASE == 1) {
+      e.c[0] = (double)u1; e.c[1] = (double)u2; e.c[2] = (double)-v1; e.c[3] = (double)-v2;
+    } else if (CASE == 2) {
+      e.c[0] = (double)(u1 - v1); e.c[1] = (double)u2; e.c[2] = (double)-v2; e.c[3] = 0.0;
+    } else {
+      e.c[0] = (double)(u1 - v1); e.c[1] = (double)(u2 - v2); e.c[2] = 0.0; e.c[3] = 0.0;
+    }
+    e.w = (double)((long double)rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * wj);
+    e.uh[0] = (double)u1;
+    e.uh[1] = (double)u2;
+    e.vh[0] = (double)v1;
+    e.vh[1] = (double)v2;
+    out.push_back(e);
+  }
+}
+
+// One warp per touching pair.  On each piece x - y = xi h(eta) and the
+// barycentric coordinates of both points (in the ordered vertices) are
+// alpha + xi beta with alpha = (1, 0, 0) and beta(u^) = (-u^1, u^1 - u^2, u^2),
+// so with f = w / |h| the xi-integral of xi^2 (alpha_a + xi beta_a)
+// (alpha_b + xi beta'_b) is exact:
+//   M_ab = sum f [alpha_a alpha_b / 3 + (alpha_a beta'_b + beta_a alpha_b) / 4 + beta_a beta'_b / 5],
+// formed from the sums of f, f beta_a, f beta'_b and f beta_a beta'_b.
+__global__ void __launch_bounds__(256)
+k_p1_singular(const P1Item* __restrict__ items, const unsigned long long* __restrict__ counts, int64_t cap,
+              const int* __restrict__ tri, const double* __restrict__ vert, const double* __restrict__ area2,
+              const SSEntryP1* __restrict__ table, int3 toff, int3 tcnt, double* __restrict__ out) {
+  const int64_t wi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t count = min((long long)counts[4], (long long)cap);
+  if (wi >= count) return;
+  const P1Item it = items[wi];
+  int ti[3], tj[3];
+  for (int a = 0; a < 3; ++a) {
+    ti[a] = tri[3 * it.ti + a];
+    tj[a] = tri[3 * it.tj + a];
+  }
+  // vertex orders of the rules (identical: stored; edge: shared ids in the
+  // order of ti, then the others; vertex: the shared id first, then
+  // cyclically) and the stored corner of each ordered vertex
+  int P[3], Q[3], ci[3], cj[3];
+  const int cs = it.cs;
+  if (cs == 3) {
+    for (int a = 0; a < 3; ++a) {
+      P[a] = Q[a] = ti[a];
+      ci[a] = a;
+      for (int b = 0; b < 3; ++b)
+        if (tj[b] == ti[a]) cj[a] = b;
+    }
+  } else if (cs == 2) {
+    int sh[2], ns = 0, oi = -1, oj = -1;
+    for (int a = 0; a < 3; ++a) {
+      const bool in_j = ti[a] == tj[0] || ti[a] == tj[1] || ti[a] == tj[2];
+      if (in_j) sh[ns++] = ti[a]; else oi = ti[a];
+    }
+    for (int a = 0; a < 3; ++a)
+      if (tj[a] != sh[0] && tj[a] != sh[1]) oj = tj[a];
+    P[0] = Q[0] = sh[0];
+    P[1] = Q[1] = sh[1];
+    P[2] = oi;
+    Q[2] = oj;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        if (ti[b] == P[a]) ci[a] = b;
+        if (tj[b] == Q[a]) cj[a] = b;
+      }
+  } else {
+    int pi = 0, pj = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (ti[a] == tj[b]) { pi = a; pj = b; }
+    for (int a = 0; a < 3; ++a) {
+      ci[a] = (pi + a) % 3;
+      cj[a] = (pj + a) % 3;
+      P[a] = ti[ci[a]];
+      Q[a] = tj[cj[a]];
+    }
+  }
+  double V[4][3];
+  for (int d = 0; d < 3; ++d) {
+    V[0][d] = vert[3 * P[1] + d] - vert[3 * P[0] + d];
+    V[1][d] = vert[3 * P[2] + d] - vert[3 * P[1] + d];
+    V[2][d] = cs == 1 ? vert[3 * Q[1] + d] - vert[3 * Q[0] + d] : (cs == 2 ? vert[3 * Q[2] + d] - vert[3 * Q[1] + d] : 0.0);
+    V[3][d] = cs == 1 ? vert[3 * Q[2] + d] - vert[3 * Q[1] + d] : 0.0;
+  }
+  const int t0 = cs == 1 ? toff.x : (cs == 2 ? toff.y : toff.z);
+  const int tn = cs == 1 ? tcnt.x : (cs == 2 ? tcnt.y : tcnt.z);
+  double s0 = 0.0, sa[3] = {0, 0, 0}, sb[3] = {0, 0, 0}, sab[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int s = lane; s < tn; s += 32) {
+    const SSEntryP1 e = table[t0 + s];
+    double h[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) h[d] = e.c[0] * V[0][d] + e.c[1] * V[1][d] + e.c[2] * V[2][d] + e.c[3] * V[3][d];
+    const double f = e.w * rsqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    const double ba[3] = {-e.uh[0], e.uh[0] - e.uh[1], e.uh[1]};
+    const double bb[3] = {-e.vh[0], e.vh[0] - e.vh[1], e.vh[1]};
+    s0 += f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      sa[a] += f * ba[a];
+      sb[a] += f * bb[a];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) sab[a][b] += f * ba[a] * bb[b];
+    }
+  }
+  for (int o = 16; o; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      sa[a] += __shfl_xor_sync(0xffffffffu, sa[a], o);
+      sb[a] += __shfl_xor_sync(0xffffffffu, sb[a], o);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) sab[a][b] += __shfl_xor_sync(0xffffffffu, sab[a][b], o);
+    }
+  }
+  if (lane != 0) return;
+  const double jac = area2[it.ti] * area2[it.tj] * kInv4Pi;
+  double M[3][3];  // stored corners
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double v = sab[a][b] / 5.0;
+      if (a == 0) v += sb[b] / 4.0;
+      if (b == 0) v += sa[a] / 4.0;
+      if (a == 0 && b == 0) v += s0 / 3.0;
+      M[ci[a]][cj[b]] = v * jac;
+    }
+  p1_scatter(out, it.base, it.ld, it.base2, it.ld2, it.lr, it.lc, M);
+}

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "internal.hpp"
@@ -193,26 +194,13 @@ BlockIndex index_blocks(int nclusters, const std::vector<int>& key) {
 
 }  // namespace gca
 
-extern "C" int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t max_clusters,
-                              int32_t* perm, int32_t* begin, int32_t* end, int32_t* child0,
-                              int32_t* child1, int32_t* level, int32_t* nclusters) {
+namespace {
+
+// The bisection of gca_tree_build on n points (x, y, z per index).
+int bisect(int n, const std::vector<double>& cent, int32_t leaf_size, int32_t max_clusters,
+           int32_t* perm, int32_t* begin, int32_t* end, int32_t* child0, int32_t* child1,
+           int32_t* level, int32_t* nclusters, const char* who) {
   using namespace gca;
-  int st = validate_mesh(mesh);
-  if (st != GCA_OK) return st;
-  if (leaf_size < 1 || !perm || !begin || !end || !child0 || !child1 || !level || !nclusters) {
-    set_error("gca_tree_build: bad arguments");
-    return GCA_ERR_INVALID_ARG;
-  }
-  const int n = mesh->nt;
-  std::vector<double> cent(3 * (size_t)n);
-  for (int t = 0; t < n; ++t) {
-    const int32_t* tri = mesh->triangles + 3LL * t;
-    for (int d = 0; d < 3; ++d) {
-      double s = mesh->vertices[3LL * tri[0] + d] + mesh->vertices[3LL * tri[1] + d];
-      s = s + mesh->vertices[3LL * tri[2] + d];
-      cent[3 * (size_t)t + d] = s / 3.0;
-    }
-  }
   std::vector<int> p(n);
   std::iota(p.begin(), p.end(), 0);
   std::vector<int> B{0}, E{n}, C0{-1}, C1{-1}, L{0};
@@ -249,7 +237,7 @@ extern "C" int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t m
     }
     std::copy(tmp.begin(), tmp.end(), p.begin() + b);
     if ((int)B.size() + 2 > max_clusters) {
-      set_error("gca_tree_build: max_clusters too small");
+      set_error(std::string(who) + ": max_clusters too small");
       return GCA_ERR_INVALID_ARG;
     }
     for (auto [cb, ce] : {std::pair<int, int>{b, b + nlow}, std::pair<int, int>{b + nlow, e}}) {
@@ -266,4 +254,49 @@ extern "C" int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t m
   std::copy(L.begin(), L.end(), level);
   *nclusters = (int32_t)B.size();
   return GCA_OK;
+}
+
+}  // namespace
+
+extern "C" int gca_tree_build(const gca_mesh* mesh, int32_t leaf_size, int32_t max_clusters,
+                              int32_t* perm, int32_t* begin, int32_t* end, int32_t* child0,
+                              int32_t* child1, int32_t* level, int32_t* nclusters) {
+  using namespace gca;
+  int st = validate_mesh(mesh);
+  if (st != GCA_OK) return st;
+  if (leaf_size < 1 || !perm || !begin || !end || !child0 || !child1 || !level || !nclusters) {
+    set_error("gca_tree_build: bad arguments");
+    return GCA_ERR_INVALID_ARG;
+  }
+  const int n = mesh->nt;
+  std::vector<double> cent(3 * (size_t)n);
+  for (int t = 0; t < n; ++t) {
+    const int32_t* tri = mesh->triangles + 3LL * t;
+    for (int d = 0; d < 3; ++d) {
+      double s = mesh->vertices[3LL * tri[0] + d] + mesh->vertices[3LL * tri[1] + d];
+      s = s + mesh->vertices[3LL * tri[2] + d];
+      cent[3 * (size_t)t + d] = s / 3.0;
+    }
+  }
+  return bisect(n, cent, leaf_size, max_clusters, perm, begin, end, child0, child1, level, nclusters,
+                "gca_tree_build");
+}
+
+extern "C" int gca_tree_build_points(int32_t n, const double* points, int32_t leaf_size, int32_t max_clusters,
+                                     int32_t* perm, int32_t* begin, int32_t* end, int32_t* child0,
+                                     int32_t* child1, int32_t* level, int32_t* nclusters) {
+  using namespace gca;
+  if (n < 1 || !points || leaf_size < 1 || !perm || !begin || !end || !child0 || !child1 || !level ||
+      !nclusters) {
+    set_error("gca_tree_build_points: bad arguments");
+    return GCA_ERR_INVALID_ARG;
+  }
+  for (int64_t i = 0; i < 3LL * n; ++i)
+    if (!std::isfinite(points[i])) {
+      set_error("gca_tree_build_points: non-finite coordinate");
+      return GCA_ERR_NUMERIC;
+    }
+  std::vector<double> cent(points, points + 3LL * n);
+  return bisect(n, cent, leaf_size, max_clusters, perm, begin, end, child0, child1, level, nclusters,
+                "gca_tree_build_points");
 }

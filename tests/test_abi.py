@@ -13,7 +13,7 @@ import pytest
 
 import synth
 import paper_1810_08429_b300 as gca
-from oracle import cluster
+from oracle import cluster, p1
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "gca.h")
@@ -67,6 +67,34 @@ def test_tree_build_matches_oracle(name, leaf):
     ref = cluster.build_tree(v, t, leaf)
     for key in ("perm", "begin", "end", "child0", "child1", "level"):
         assert np.array_equal(ours[key], ref[key]), key
+
+
+@pytest.mark.parametrize("name,leaf", [("sphere1280", 32), ("sphere20480", 64), ("ellipsoid1280", 16),
+                                       ("perturbed20480", 64)])
+def test_point_tree_matches_oracle(name, leaf):
+    """The vertex tree of the nodal basis (gca_tree_build_points)."""
+    v, t = synth.mesh_for_config(name)
+    ours = gca.tree_build_points(v, leaf)
+    ref = p1.build_tree_points(v, leaf)
+    for key in ("perm", "begin", "end", "child0", "child1", "level"):
+        assert np.array_equal(ours[key], ref[key]), key
+
+
+def test_p1_input_rejected_on_host():
+    """gca_build_p1: a vertex outside every triangle, a tree over the
+    triangles instead of the vertices, and a non-finite point."""
+    v, t = synth.icosphere(1)
+    p = gca.Params(leaf_size=8)
+    vx = np.vstack([v, [[2.0, 0.0, 0.0]]])
+    tree = gca.tree_build_points(vx, 8)
+    with pytest.raises(gca.GCAError, match="belongs to no triangle"):
+        gca.build_p1(vx, t, tree, p)
+    with pytest.raises(gca.GCAError):
+        gca.build_p1(v, t, gca.tree_build(v, t, 8), p)
+    vn = v.copy()
+    vn[2, 1] = np.inf
+    with pytest.raises(gca.GCAError):
+        gca.tree_build_points(vn, 8)
 
 
 def test_tree_build_degenerate_split():
