@@ -8,6 +8,7 @@
 #include <cstring>
 #include <string>
 #include <memory>
+#include <algorithm>
 #include <vector>
 
 #include "internal.hpp"
@@ -397,14 +398,20 @@ int gca_build_batch(int32_t count, const gca_mesh* meshes, const gca_tree* trees
   *out = nullptr;
   try {
     auto b = std::make_unique<gca_h2_batch>();
-    for (int32_t i = 0; i < count; ++i) {
-      gca_h2* h = nullptr;
-      int st = gca::build(meshes + i, trees + i, params, static_cast<cudaStream_t>(stream), &h);
+    // groups of up to 8 meshes share their cross approximation launches (the
+    // temporaries of a group's constructions are alive together)
+    constexpr int32_t kGroup = 8;
+    for (int32_t i0 = 0; i0 < count; i0 += kGroup) {
+      const int32_t g = std::min(kGroup, count - i0);
+      std::vector<gca_h2*> hs(g, nullptr);
+      int st = gca::build_group(g, meshes + i0, trees + i0, params, static_cast<cudaStream_t>(stream), hs.data());
+      for (gca_h2* h : hs)
+        if (h) b->h.push_back(h);  // owned by the batch from here on, freed with it on error
       if (st != GCA_OK) {
-        gca::set_error("gca_build_batch: mesh " + std::to_string(i) + ": " + gca_last_error());
+        gca::set_error("gca_build_batch: meshes " + std::to_string(i0) + ".." + std::to_string(i0 + g - 1) +
+                       ": " + gca_last_error());
         return st;
       }
-      b->h.push_back(h);
     }
     b->device = b->h[0]->device;
     int st = b->d_status.alloc(sizeof(int));

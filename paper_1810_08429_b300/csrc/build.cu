@@ -209,6 +209,7 @@ struct AcaMesh {
   const int* sup_ptr;   // nodal basis: support of vertex v = sup_item[sup_ptr[v] .. sup_ptr[v + 1])
   const int* sup_item;  // (triangle << 2) | corner of the vertex
   double bary[7][3];    // barycentric coordinates of the 7-point rule's nodes
+  int* status;          // the mesh's sticky error bits (NaN in a Green matrix)
 };
 
 // Cross approximation of one job on a thread-block cluster of C CTAs (C = 1
@@ -331,7 +332,7 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 template <int LC>
 __global__ void __launch_bounds__(kAcaThreads)
 k_aca(const AcaJob* __restrict__ jobs, const AcaMesh* __restrict__ meshes, int k, int rpc_cap, int rmax_cap,
-      double tol, double tie, int* __restrict__ status) {
+      double tol, double tie) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -690,7 +691,7 @@ k_aca(const AcaJob* __restrict__ jobs, const AcaMesh* __restrict__ meshes, int k
     for (int off = 16; off; off >>= 1) g = cand_merge(g, cand_shfl(g, off), keep);
     const unsigned long long gmax = g.m;
     if (gmax > kInfBits) {
-      if (tid == 0 && q == 0) atomicOr(status, kStatusNumeric);
+      if (tid == 0 && q == 0) atomicOr(M.status, kStatusNumeric);
       break;
     }
     const double big = __longlong_as_double((long long)gmax);
@@ -1777,6 +1778,16 @@ int check_status(DevMem& st, cudaStream_t s, const char* where) {
 // small, as long as every CTA keeps at least kMinRowsPerCta rows.
 class AcaLauncher {
  public:
+  AcaLauncher() = default;
+  AcaLauncher(const AcaLauncher&) = delete;
+  AcaLauncher& operator=(const AcaLauncher&) = delete;
+  ~AcaLauncher() {
+    for (int i = 0; i < 5; ++i) {
+      if (side_[i]) cudaStreamDestroy(side_[i]);
+      if (join_[i]) cudaEventDestroy(join_[i]);
+    }
+    if (fork_) cudaEventDestroy(fork_);
+  }
   int init(int k) {
     k_ = k;
     int dev = 0;
@@ -1797,7 +1808,7 @@ class AcaLauncher {
     return aca_smem_bytes(rpc, 2 * k_, std::min(rows, 2 * k_));
   }
   int launch(const std::vector<AcaJob>& jobs, DevMem& d_jobs, const AcaMesh* d_mesh, int level, double tol,
-             double tie, int* d_status, cudaStream_t st) {
+             double tie, cudaStream_t st) {
     constexpr int kMinRowsPerCta = 16;
     int spread = 1;
     while (spread < 16 && (int64_t)jobs.size() * spread < sms_) spread *= 2;
@@ -1816,10 +1827,34 @@ class AcaLauncher {
     std::vector<AcaJob> host;  // grouped copy, uploaded at once
     for (int g = 0; g < 5; ++g) host.insert(host.end(), by_c[g].begin(), by_c[g].end());
     GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, host.data(), sizeof(AcaJob) * host.size(), cudaMemcpyHostToDevice, st));
+    // the groups of one level are independent: with more than one, each runs
+    // on a side stream forked from and joined back into `st`
+    int ngroups = 0;
+    for (int g = 0; g < 5; ++g) ngroups += !by_c[g].empty();
+    const bool fork = ngroups > 1;
+    if (fork) {
+      for (int i = 0; i < 5; ++i)
+        if (!side_[i]) {
+          GCA_TRY_CUDA(cudaStreamCreateWithFlags(&side_[i], cudaStreamNonBlocking));
+          GCA_TRY_CUDA(cudaEventCreateWithFlags(&join_[i], cudaEventDisableTiming));
+        }
+      if (!fork_) GCA_TRY_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
+      GCA_TRY_CUDA(cudaEventRecord(fork_, st));
+    }
+    std::unique_ptr<PhaseScope> level_scope;
+    if (!profile_detail()) {
+      level_scope = std::make_unique<PhaseScope>("green_aca", st);
+      level_scope->launches(ngroups);
+    }
     size_t at = 0;
     for (int g = 0; g < 5; ++g) {
       if (by_c[g].empty()) continue;
       const int C = 1 << g;
+      cudaStream_t gs = st;
+      if (fork) {
+        gs = side_[g];
+        GCA_TRY_CUDA(cudaStreamWaitEvent(gs, fork_, 0));
+      }
       int rows_cap = 1;
       for (const auto& j : by_c[g]) rows_cap = std::max(rows_cap, j.rows);
       const int rpc_cap = (rows_cap + C - 1) / C;
@@ -1828,7 +1863,7 @@ class AcaLauncher {
       cfg.gridDim = dim3((unsigned)(by_c[g].size() * C));
       cfg.blockDim = dim3(kAcaThreads);
       cfg.dynamicSmemBytes = aca_smem_bytes(rpc_cap, 2 * k_, rmax_cap);
-      cfg.stream = st;
+      cfg.stream = gs;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
       attr[0].val.clusterDim.x = C;
@@ -1836,13 +1871,20 @@ class AcaLauncher {
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      PhaseScope ps__(profile_detail() ? "green_aca.L" + std::to_string(level) + ".c" + std::to_string(C)
-                                       : std::string("green_aca"),
-                      st);
-      GCA_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern_, (const AcaJob*)(d_jobs.as<AcaJob>() + at), d_mesh, k_,
-                                      rpc_cap, rmax_cap, tol, tie, d_status));
+      {
+        std::unique_ptr<PhaseScope> ps;
+        if (profile_detail())
+          ps = std::make_unique<PhaseScope>("green_aca.L" + std::to_string(level) + ".c" + std::to_string(C), gs);
+        GCA_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern_, (const AcaJob*)(d_jobs.as<AcaJob>() + at), d_mesh, k_,
+                                        rpc_cap, rmax_cap, tol, tie));
+      }
+      if (fork) {
+        GCA_TRY_CUDA(cudaEventRecord(join_[g], gs));
+        GCA_TRY_CUDA(cudaStreamWaitEvent(st, join_[g], 0));
+      }
       at += by_c[g].size();
     }
+    level_scope.reset();
     // `host` must outlive the copy: the caller synchronises before the next level
     GCA_TRY_CUDA(cudaStreamSynchronize(st));
     return GCA_OK;
@@ -1851,8 +1893,11 @@ class AcaLauncher {
  private:
   int k_ = 0;
   int sms_ = 148;
+  cudaStream_t side_[5] = {};
+  cudaEvent_t join_[5] = {};
+  cudaEvent_t fork_ = nullptr;
   size_t budget_ = 0;
-  void (*kern_)(const AcaJob*, const AcaMesh*, int, int, int, double, double, int*) = nullptr;
+  void (*kern_)(const AcaJob*, const AcaMesh*, int, int, int, double, double) = nullptr;
 };
 
 }  // namespace
@@ -1882,13 +1927,113 @@ int node_supports(const gca_mesh* mesh, std::vector<int>& ptr, std::vector<int>&
   return GCA_OK;
 }
 
-// The whole construction; see the header of this file.
-int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
-          gca_h2** out, int op) {
-  auto t0 = std::chrono::steady_clock::now();
+// One construction (see the header of this file) in stages, so that a batch
+// can run the cross approximations of several meshes level by level in
+// common launches: prepare() (geometry, block tree, box rules), rows() (the
+// row bases: one BasisPass, or the Green quadrature matrices), finish() (the
+// column bases of two-sided operators, entries, panels, product plan).
+struct BasisOut {
+  std::vector<int>* rank;
+  std::vector<int64_t>* poff;
+  std::vector<int64_t>* voff;
+  std::vector<int64_t>* eoff;
+  int64_t* v_entries;
+  int64_t* e_entries;
+  DevMem* V64;
+  DevMem* E64;
+};
+class Builder;
+
+// One side's nested bases (Sect. 3, Sect. 4), level by level from the
+// deepest (kind 0: the cluster bases V, E of the rows from A_tau; 1: the
+// double layer's column bases W, F from its column matrix; 2: the
+// collocation rows; 3: the nodal rows): ranks, pivots in the pool d_piv
+// (offsets poff), and the row-major float64 leaf bases and transfer
+// matrices.  begin() sizes the pools, jobs(L) appends level L's cross
+// approximations (job.mesh: the caller's index of this mesh in the launch's
+// mesh table, whose entry is `am`), after() reads the level's ranks back
+// once its launch is done, end() packs V and E.
+struct BasisPass {
+  BasisPass(Builder& b_, int kind_, const BasisOut& o_, DevMem& piv, DevMem& rank, int64_t& used)
+      : b(b_), kind(kind_), o(o_), d_piv(piv), d_rank(rank), piv_used(used) {}
+  int begin();
+  int jobs(int L, int mesh_index, std::vector<AcaJob>& out);
+  int after();
+  int end();
+  Builder& b;
+  int kind;
+  BasisOut o;
+  DevMem& d_piv;
+  DevMem& d_rank;
+  int64_t& piv_used;
+  std::vector<int64_t> vh_off;
+  std::vector<int> rows_of;
+  int64_t piv_cap = 0, vh_cap = 0, vh_used = 0;
+  DevMem d_vh;
+  AcaMesh am{};
+};
+
+class Builder {
+ public:
+  Builder(const gca_mesh* mesh_, const gca_tree* tree_, const gca_params* prm_, cudaStream_t st_, int op_)
+      : mesh(mesh_), tree(tree_), prm(prm_), st(st_), op(op_) {}
+  int prepare();
+  int rows();
+  int finish(gca_h2** out);
+  // the pass of the row bases (the single layer's, op 0, 1, 3; the
+  // collocation rows, op 2; the nodal rows, op 5)
+  std::unique_ptr<BasisPass> rows_pass() {
+    return std::make_unique<BasisPass>(*this, op == 2 ? 2 : (p1 ? 3 : 0),
+                                       BasisOut{&h->rank, &h->poff, &h->voff, &h->eoff, &h->v_entries,
+                                                &h->e_entries, &h->V64, &h->E64},
+                                       d_piv, d_rank, piv_used);
+  }
+  // a pass on this mesh alone: one launch per level
+  int run_pass(BasisPass& pass) {
+    GCA_TRY(pass.begin());
+    DevMem d_mesh, d_jobs;
+    GCA_TRY(d_mesh.alloc(sizeof(AcaMesh)));
+    GCA_TRY_CUDA(cudaMemcpyAsync(d_mesh.p, &pass.am, sizeof(AcaMesh), cudaMemcpyHostToDevice, st));
+    std::vector<AcaJob> js;
+    for (int L = h->depth; L >= 1; --L) {
+      js.clear();
+      GCA_TRY(pass.jobs(L, 0, js));
+      if (js.empty()) continue;
+      GCA_TRY(aca.launch(js, d_jobs, d_mesh.as<AcaMesh>(), L, prm->aca_tol, tie, st));
+      GCA_TRY(pass.after());
+    }
+    return pass.end();
+  }
+
+  const gca_mesh* mesh;
+  const gca_tree* tree;
+  const gca_params* prm;
+  cudaStream_t st;
+  int op;
+  std::chrono::steady_clock::time_point t0;
+  bool p1 = false, single = false;
+  std::vector<int> sup_ptr, sup_item;
+  std::unique_ptr<gca_h2> h;
+  int n = 0, nc = 0, k = 0, ntri = 0;
+  double margin = 0.0;
+  Rules rules{};
+  std::vector<double> vert;
+  std::vector<int> tri;
+  DevMem d_tq, d_area2, d_box, d_diam, d_zq, d_status, d_nrm, d_sup_ptr, d_sup_item, d_tn;
+  std::vector<double> box, diam;
+  float near_r2 = 0.f;
+  std::vector<char> needed;
+  AcaLauncher aca;
+  double tie = std::ldexp(1.0, -40);
+  DevMem d_piv, d_rank, d_piv2, d_rank2;
+  int64_t piv_used = 0, piv2_used = 0;
+};
+
+int Builder::prepare() {
+  t0 = std::chrono::steady_clock::now();
   GCA_TRY(validate_mesh(mesh));
   // op 5 (nodal basis, Sect. 5): the indices are the vertices
-  const bool p1 = op == 5;
+  p1 = op == 5;
   gca_mesh shape = *mesh;
   if (p1) shape.nt = mesh->nv;
   GCA_TRY(validate_tree(&shape, tree, GCA_MAX_LEAF));
@@ -1901,9 +2046,8 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   }
   // supports of the nodal basis functions: the triangles at each vertex in
   // ascending order, as (triangle << 2) | corner
-  std::vector<int> sup_ptr, sup_item;
   if (p1) GCA_TRY(node_supports(mesh, sup_ptr, sup_item, "gca_build_p1"));
-  auto h = std::make_unique<gca_h2>();
+  h = std::make_unique<gca_h2>();
   GCA_TRY_CUDA(cudaGetDevice(&h->device));
   h->device += test_hooks().device_skew;
   h->op = op;
@@ -1913,10 +2057,12 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   h->nc = tree->nclusters;
   h->m = prm->box_gauss_m;
   h->k = 6 * h->m * h->m;
-  const int n = h->n, nc = h->nc, k = h->k;
-  const int ntri = mesh->nt;  // triangles (n: indices, the vertices for op 5)
-  const double margin = prm->omega_margin < 0.0 ? 1.0 / (4.0 * prm->eta) : prm->omega_margin;
-  const Rules rules = make_rules(h->m, prm->sauter_q);
+  n = h->n;
+  nc = h->nc;
+  k = h->k;
+  ntri = mesh->nt;
+  margin = prm->omega_margin < 0.0 ? 1.0 / (4.0 * prm->eta) : prm->omega_margin;
+  rules = make_rules(h->m, prm->sauter_q);
 
   h->perm.assign(tree->perm, tree->perm + n);
   h->begin.assign(tree->begin, tree->begin + nc);
@@ -1938,14 +2084,13 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   }
 
   // geometry upload
-  std::vector<double> vert(mesh->vertices, mesh->vertices + 3LL * mesh->nv);
-  std::vector<int> tri(mesh->triangles, mesh->triangles + 3LL * ntri);
+  vert.assign(mesh->vertices, mesh->vertices + 3LL * mesh->nv);
+  tri.assign(mesh->triangles, mesh->triangles + 3LL * ntri);
   GCA_TRY(upload(h->d_vert, vert, st));
   GCA_TRY(upload(h->d_tri, tri, st));
   GCA_TRY(upload(h->d_perm, h->perm, st));
   GCA_TRY(upload(h->d_begin, h->begin, st));
   GCA_TRY(upload(h->d_end, h->end, st));
-  DevMem d_tq, d_area2, d_box, d_diam, d_zq, d_status, d_nrm, d_sup_ptr, d_sup_item;
   GCA_TRY(d_tq.alloc(sizeof(P4) * 7 * (size_t)ntri));
   if (op == 1) GCA_TRY(d_nrm.alloc(sizeof(double) * 3 * (size_t)ntri));
   GCA_TRY(d_area2.alloc(sizeof(double) * (size_t)ntri));
@@ -1974,14 +2119,13 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
           h->d_vert.as<double>(), d_box.as<double>());
   }
   GCA_TRY_CUDA(cudaGetLastError());
-  std::vector<double> box(6 * (size_t)nc), diam;
+  box.assign(6 * (size_t)nc, 0.0);
   GCA_TRY_CUDA(cudaMemcpyAsync(box.data(), d_box.p, box.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   GCA_TRY_CUDA(cudaStreamSynchronize(st));
   box_diameters(box, diam);
   // split nodes of the coupling entries: origin at the root box's centre,
   // grid step 2^(E - 22) with 2^E above the box's largest half width
-  DevMem d_tn;
-  float near_r2 = 0.f;  // float-pair entries of the near field need |d| >= 2^(E - 8)
+  near_r2 = 0.f;  // float-pair entries of the near field need |d| >= 2^(E - 8)
   {
     double half = 0.0, o[3];
     for (int d = 0; d < 3; ++d) {
@@ -2018,11 +2162,11 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // A cluster basis enters the matrix only through the admissible blocks of
   // the cluster and, by nestedness, of its ancestors (Sect. 4); the bases of
   // the other clusters are not built (rank 0).
-  std::vector<char> needed(nc, 0);
+  needed.assign(nc, 0);
   for (size_t b = 0; b < h->far_t.size(); ++b) needed[h->far_t[b]] = needed[h->far_s[b]] = 1;
   // single-level bases (op 3) and Green quadrature (op 4) serve only the
   // clusters of the blocks themselves; nested bases also their descendants
-  const bool single = op == 3 || op == 4;
+  single = op == 3 || op == 4;
   for (int L = 0; L < h->depth && !single; ++L)
     for (int c : h->by_level[L])
       if (needed[c] && h->child0[c] >= 0) needed[h->child0[c]] = needed[h->child1[c]] = 1;
@@ -2031,60 +2175,57 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   // V, E of the rows from A_tau; kind 1: the double layer's column bases W, F
   // from its column matrix): ranks, pivots in the pool d_piv (offsets poff),
   // and the row-major float64 leaf bases and transfer matrices.
-  AcaLauncher aca;
   GCA_TRY(aca.init(k));
-  const double tie = std::ldexp(1.0, -40);
-  struct BasisOut {
-    std::vector<int>* rank;
-    std::vector<int64_t>* poff;
-    std::vector<int64_t>* voff;
-    std::vector<int64_t>* eoff;
-    int64_t* v_entries;
-    int64_t* e_entries;
-    DevMem* V64;
-    DevMem* E64;
-  };
-  auto nested_bases = [&](int kind, const BasisOut& o, DevMem& d_piv, DevMem& d_rank, int64_t& piv_used) -> int {
+  return GCA_OK;
+}
+
+int BasisPass::begin() {
+    const int nc = b.nc, k = b.k;
+    gca_h2* h = b.h.get();
     std::vector<int>& rank = *o.rank;
     std::vector<int64_t>& poff = *o.poff;
     rank.assign(nc, 0);
     poff.assign(nc, -1);
-    std::vector<int64_t> vh_off(nc, -1);
-    std::vector<int> rows_of(nc, 0);
-    int64_t piv_cap = 0, vh_cap = 0;
+    vh_off.assign(nc, -1);
+    rows_of.assign(nc, 0);
+    piv_cap = 0;
+    vh_cap = 0;
     for (int c = 1; c < nc; ++c) {
       // upper bounds, refined per level below
       piv_cap += std::min<int64_t>(h->end[c] - h->begin[c], 2 * k);
     }
-    DevMem d_vh, d_jobs, d_mesh;
+    cudaStream_t st = b.st;
     GCA_TRY(d_piv.alloc(sizeof(int) * (size_t)std::max<int64_t>(piv_cap, 1)));
     GCA_TRY(d_rank.alloc(sizeof(int) * (size_t)nc));
     GCA_TRY_CUDA(cudaMemsetAsync(d_rank.p, 0, sizeof(int) * nc, st));
     // V^ pool: rows <= min(|tau-hat|, 4k) for every cluster bounds its size
-    int64_t vh_used = 0;
+    vh_used = 0;
     piv_used = 0;
     for (int c = 1; c < nc; ++c) {
-      int64_t rows = (h->child0[c] < 0 || single) ? (h->end[c] - h->begin[c])
+      int64_t rows = (h->child0[c] < 0 || b.single) ? (h->end[c] - h->begin[c])
                                                   : std::min<int64_t>(h->end[c] - h->begin[c], 4 * k);
       vh_cap += rows * std::min<int64_t>(rows, 2 * k);
     }
     GCA_TRY(d_vh.alloc(sizeof(double) * (size_t)std::max<int64_t>(vh_cap, 1)));
-    {
-      AcaMesh am{h->d_perm.as<int>(), d_tq.as<P4>(), d_zq.as<P4>(), d_piv.as<int>(), d_vh.as<double>(),
-                 d_rank.as<int>(), d_nrm.as<double>(), d_sup_ptr.as<int>(), d_sup_item.as<int>(), {}};
-      std::memcpy(am.bary, rules.bary, sizeof(am.bary));
-      GCA_TRY(d_mesh.alloc(sizeof(AcaMesh)));
-      GCA_TRY_CUDA(cudaMemcpyAsync(d_mesh.p, &am, sizeof(AcaMesh), cudaMemcpyHostToDevice, st));
-      GCA_TRY_CUDA(cudaStreamSynchronize(st));  // am is a local
-    }
-    for (int L = h->depth; L >= 1; --L) {
-      std::vector<AcaJob> jobs;
+    am = AcaMesh{h->d_perm.as<int>(), b.d_tq.as<P4>(), b.d_zq.as<P4>(), d_piv.as<int>(), d_vh.as<double>(),
+                 d_rank.as<int>(), b.d_nrm.as<double>(), b.d_sup_ptr.as<int>(), b.d_sup_item.as<int>(), {},
+                 b.d_status.as<int>()};
+    std::memcpy(am.bary, b.rules.bary, sizeof(am.bary));
+    return GCA_OK;
+}
+
+int BasisPass::jobs(int L, int mesh_index, std::vector<AcaJob>& out) {
+      const int k = b.k;
+      gca_h2* h = b.h.get();
+      std::vector<int>& rank = *o.rank;
+      std::vector<int64_t>& poff = *o.poff;
+      if (L > h->depth) return GCA_OK;
       for (int c : h->by_level[L]) {
-        if (!needed[c]) continue;
+        if (!b.needed[c]) continue;
         AcaJob j{};
         j.c = c;
         j.kind = kind;
-        j.leaf = h->child0[c] < 0 || single;  // single-level: A_tau on all of tau's triangles
+        j.leaf = h->child0[c] < 0 || b.single;  // single-level: A_tau on all of tau's triangles
         if (j.leaf) {
           j.rows = h->end[c] - h->begin[c];
           j.tbegin = h->begin[c];
@@ -2096,8 +2237,8 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
           j.piv1 = poff[c1];
         }
         j.rmax = std::min(j.rows, 2 * k);
-        j.mesh = 0;
-        j.diam = diam[c];
+        j.mesh = mesh_index;
+        j.diam = b.diam[c];
         j.p_off = piv_used;
         poff[c] = piv_used;
         piv_used += j.rmax;
@@ -2105,18 +2246,28 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
         vh_off[c] = vh_used;
         vh_used += (int64_t)j.rows * j.rmax;
         rows_of[c] = j.rows;
-        jobs.push_back(j);
+        out.push_back(j);
       }
-      if (jobs.empty()) continue;
       if (piv_used > piv_cap || vh_used > vh_cap) {
         set_error("gca_build: internal pool bound exceeded");
         return GCA_ERR_INVALID_ARG;
       }
-      GCA_TRY(aca.launch(jobs, d_jobs, d_mesh.as<AcaMesh>(), L, prm->aca_tol, tie, d_status.as<int>(), st));
-      GCA_TRY(check_status(d_status, st, "cross approximation"));
-      GCA_TRY_CUDA(cudaMemcpyAsync(rank.data(), d_rank.p, sizeof(int) * nc, cudaMemcpyDeviceToHost, st));
-      GCA_TRY_CUDA(cudaStreamSynchronize(st));
-    }
+      return GCA_OK;
+}
+
+int BasisPass::after() {
+    GCA_TRY(check_status(b.d_status, b.st, "cross approximation"));
+    GCA_TRY_CUDA(cudaMemcpyAsync(o.rank->data(), d_rank.p, sizeof(int) * b.nc, cudaMemcpyDeviceToHost, b.st));
+    GCA_TRY_CUDA(cudaStreamSynchronize(b.st));
+    return GCA_OK;
+}
+
+int BasisPass::end() {
+    const int nc = b.nc;
+    const bool single = b.single;
+    gca_h2* h = b.h.get();
+    cudaStream_t st = b.st;
+    std::vector<int>& rank = *o.rank;
     // row-major leaf bases and transfer matrices from the V^ pool
     o.voff->assign(nc, -1);
     o.eoff->assign(nc, -1);
@@ -2162,9 +2313,9 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
       GCA_TRY_CUDA(cudaStreamSynchronize(st));  // d_seg is reused
     }
     return GCA_OK;
-  };
-  DevMem d_piv, d_rank, d_piv2, d_rank2;
-  int64_t piv_used = 0, piv2_used = 0;
+}
+
+int Builder::rows() {
   // rows: the Galerkin single layer's bases (op 0, 1; single level for op 3),
   // the collocation rows (op 2), or the Green quadrature matrices A_tau of
   // the clusters of the blocks (op 4: "rank" 2k, no pivots)
@@ -2196,11 +2347,12 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
     GCA_TRY(d_piv.alloc(sizeof(int)));
     GCA_TRY_CUDA(cudaStreamSynchronize(st));  // gj is a local
   } else {
-    GCA_TRY(nested_bases(op == 2 ? 2 : (p1 ? 3 : 0),
-                         BasisOut{&h->rank, &h->poff, &h->voff, &h->eoff, &h->v_entries, &h->e_entries, &h->V64,
-                                  &h->E64},
-                         d_piv, d_rank, piv_used));
+    GCA_TRY(run_pass(*rows_pass()));
   }
+  return GCA_OK;
+}
+
+int Builder::finish(gca_h2** out) {
   h->xoff.assign(nc + 1, 0);
   for (int c = 0; c < nc; ++c) h->xoff[c + 1] = h->xoff[c] + h->rank[c];
   h->rank_sum = h->xoff[nc];
@@ -2208,10 +2360,11 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   if (h->two_sided()) {
     // columns: the double layer's own bases (op 1) or the Galerkin single
     // layer's (op 2)
-    GCA_TRY(nested_bases(op == 1 ? 1 : 0,
-                         BasisOut{&h->rank2, &h->poff2, &h->voff2, &h->eoff2, &h->w_entries, &h->f_entries,
-                                  &h->W64, &h->F64},
-                         d_piv2, d_rank2, piv2_used));
+    BasisPass pass(*this, op == 1 ? 1 : 0,
+                   BasisOut{&h->rank2, &h->poff2, &h->voff2, &h->eoff2, &h->w_entries, &h->f_entries, &h->W64,
+                            &h->F64},
+                   d_piv2, d_rank2, piv2_used);
+    GCA_TRY(run_pass(pass));
     h->xoff2.assign(nc + 1, 0);
     for (int c = 0; c < nc; ++c) h->xoff2[c + 1] = h->xoff2[c] + h->rank2[c];
     h->rank_sum2 = h->xoff2[nc];
@@ -2607,6 +2760,52 @@ int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cud
   h->build_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = h.release();
+  return GCA_OK;
+}
+
+
+// The whole construction of one mesh.
+int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
+          gca_h2** out, int op) {
+  Builder b(mesh, tree, prm, st, op);
+  GCA_TRY(b.prepare());
+  GCA_TRY(b.rows());
+  return b.finish(out);
+}
+
+// The single layer of several meshes (gca_build_batch) in groups: the
+// cross approximations of a group's meshes share one launch per tree level
+// (job.mesh selects the mesh), so the coarse levels, which hold few
+// clusters per mesh, fill more of the device.  Each mesh is otherwise built
+// as by build().
+int build_group(int count, const gca_mesh* meshes, const gca_tree* trees, const gca_params* prm, cudaStream_t st,
+                gca_h2** out) {
+  std::vector<std::unique_ptr<Builder>> bs;
+  for (int i = 0; i < count; ++i) {
+    bs.push_back(std::make_unique<Builder>(meshes + i, trees + i, prm, st, 0));
+    GCA_TRY(bs.back()->prepare());
+  }
+  std::vector<std::unique_ptr<BasisPass>> passes;
+  int depth = 0;
+  for (auto& b : bs) {
+    passes.push_back(b->rows_pass());
+    GCA_TRY(passes.back()->begin());
+    depth = std::max(depth, b->h->depth);
+  }
+  std::vector<AcaMesh> table;
+  for (auto& p : passes) table.push_back(p->am);
+  DevMem d_table, d_jobs;
+  GCA_TRY(upload(d_table, table, st));
+  std::vector<AcaJob> js;
+  for (int L = depth; L >= 1; --L) {
+    js.clear();
+    for (int i = 0; i < count; ++i) GCA_TRY(passes[i]->jobs(L, i, js));
+    if (js.empty()) continue;
+    GCA_TRY(bs[0]->aca.launch(js, d_jobs, d_table.as<AcaMesh>(), L, prm->aca_tol, bs[0]->tie, st));
+    for (auto& p : passes) GCA_TRY(p->after());
+  }
+  for (auto& p : passes) GCA_TRY(p->end());
+  for (int i = 0; i < count; ++i) GCA_TRY(bs[i]->finish(out + i));
   return GCA_OK;
 }
 

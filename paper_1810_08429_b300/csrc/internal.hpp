@@ -133,6 +133,10 @@ class PhaseScope {
 // G by Green quadrature; op 5: G in the nodal (piecewise linear) basis
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
           gca_h2** out, int op = 0);
+// gca_build_batch (build.cu): `count` single-layer meshes whose cross
+// approximations share one launch per tree level
+int build_group(int count, const gca_mesh* meshes, const gca_tree* trees, const gca_params* prm, cudaStream_t st,
+                gca_h2** out);
 // gca_support_union (build.cu)
 int support_union(const gca_mesh* mesh, int nlists, const int32_t* list_ptr, const int32_t* lists,
                   int32_t* rows, int64_t cap, int32_t* counts, cudaStream_t st);
