@@ -20,10 +20,10 @@
 //                   (and to the mirrored block); disjoint pairs by the 7 x 7
 //                   rule in float-pair arithmetic on the FP32 pipe (float64
 //                   for close pairs), touching pairs handed to
-//   k_p1_singular   Sauter-Schwab with barycentric weights, one warp per
-//                   ordered pair (a mirrored block's pair is integrated in
-//                   its own order, as the rule is not symmetric in rounding
-//                   and quadrature error)
+//   k_p1_singular   Sauter-Schwab with barycentric weights in float-pair
+//                   arithmetic, one warp per ordered pair (a mirrored
+//                   block's pair is integrated in its own order, as the rule
+//                   is not symmetric in rounding and quadrature error)
 #pragma once
 
 constexpr int kUnionMax = 16384;  // support entries of one list (shared-memory sort)
@@ -458,52 +458,66 @@ k_p1_entries(const P1Block* __restrict__ blocks, const UnionJob* __restrict__ uj
   if ((tid & 31) == 0 && regular) atomicAdd(&counts[0], regular);
 }
 
-// A Sauter-Schwab sample of the nodal basis: the coefficients of
-// h(eta) = (x - y) / xi in the edge vectors (as SSEntry64), the weight
-// (Gauss weights times the piece's Jacobian without xi^3) and the reference
-// coordinates u^(eta), v^(eta) of both points (u = xi u^, v = xi v^).
+// A Sauter-Schwab sample of the nodal basis as float pairs (computed on the
+// host in long double): the coefficients of h(eta) = (x - y) / xi in the
+// edge vectors (as SSEntry), the weight (Gauss weights times the piece's
+// Jacobian without xi^3), and the slopes of the barycentric coordinates of
+// both points in the ordered vertices, u = xi u^, v = xi v^:
+// beta = (-u^1, u^1 - u^2, u^2) (beta_2 = -beta_0 - beta_1), beta' likewise.
 struct __align__(16) SSEntryP1 {
-  double c[4];
-  double w;
-  double uh[2];
-  double vh[2];
-  double pad;
+  float4 ch, cl;  // h coefficients, high and low parts
+  float4 ba;      // beta_0 (hi, lo), beta_1 (hi, lo)
+  float4 bb;      // beta'_0 (hi, lo), beta'_1 (hi, lo)
+  float wh, wl;   // weight
+  float pad[2];
 };
 
 template <int CASE>
 void sauter_table_p1(const Rules& rules, std::vector<SSEntryP1>& out) {
   const int q = rules.q, q3 = q * q * q;
   constexpr int pieces = CASE == 3 ? 6 : (CASE == 2 ? 5 : 2);
+  auto split = [](long double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (long double)hi);
+  };
   for (int s = 0; s < pieces * q3; ++s) {
     const int piece = s / q3, r = s % q3;
     const int a = r / (q * q), b = (r / q) % q, c = r % q;
     long double u1, u2, v1, v2;
     const long double wj = sauter_piece<CASE, long double>(piece, rules.ss_t[a], rules.ss_t[b], rules.ss_t[c],
                                                            u1, u2, v1, v2);
-    SSEntryP1 e{};
+    long double cf[4] = {0, 0, 0, 0};
     if (CASE == 1) {
-      e.c[0] = (double)u1; e.c[1] = (double)u2; e.c[2] = (double)-v1; e.c[3] = (double)-v2;
+      cf[0] = u1; cf[1] = u2; cf[2] = -v1; cf[3] = -v2;
     } else if (CASE == 2) {
-      e.c[0] = (double)(u1 - v1); e.c[1] = (double)u2; e.c[2] = (double)-v2; e.c[3] = 0.0;
+      cf[0] = u1 - v1; cf[1] = u2; cf[2] = -v2;
     } else {
-      e.c[0] = (double)(u1 - v1); e.c[1] = (double)(u2 - v2); e.c[2] = 0.0; e.c[3] = 0.0;
+      cf[0] = u1 - v1; cf[1] = u2 - v2;
     }
-    e.w = (double)((long double)rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * wj);
-    e.uh[0] = (double)u1;
-    e.uh[1] = (double)u2;
-    e.vh[0] = (double)v1;
-    e.vh[1] = (double)v2;
+    SSEntryP1 e{};
+    split(cf[0], e.ch.x, e.cl.x);
+    split(cf[1], e.ch.y, e.cl.y);
+    split(cf[2], e.ch.z, e.cl.z);
+    split(cf[3], e.ch.w, e.cl.w);
+    split(-u1, e.ba.x, e.ba.y);
+    split(u1 - u2, e.ba.z, e.ba.w);
+    split(-v1, e.bb.x, e.bb.y);
+    split(v1 - v2, e.bb.z, e.bb.w);
+    split((long double)rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * wj, e.wh, e.wl);
     out.push_back(e);
   }
 }
 
 // One warp per touching pair.  On each piece x - y = xi h(eta) and the
 // barycentric coordinates of both points (in the ordered vertices) are
-// alpha + xi beta with alpha = (1, 0, 0) and beta(u^) = (-u^1, u^1 - u^2, u^2),
-// so with f = w / |h| the xi-integral of xi^2 (alpha_a + xi beta_a)
-// (alpha_b + xi beta'_b) is exact:
-//   M_ab = sum f [alpha_a alpha_b / 3 + (alpha_a beta'_b + beta_a alpha_b) / 4 + beta_a beta'_b / 5],
-// formed from the sums of f, f beta_a, f beta'_b and f beta_a beta'_b.
+// alpha + xi beta with alpha = (1, 0, 0), so with f = w / |h| the
+// xi-integral of xi^2 (alpha_a + xi beta_a)(alpha_b + xi beta'_b) is exact:
+//   M_ab = sum f [alpha_a alpha_b / 3 + (alpha_a beta'_b + beta_a alpha_b) / 4 + beta_a beta'_b / 5].
+// The samples run in float-pair arithmetic on the FP32 pipe (the single
+// layer's Sauter-Schwab recipe: h from split edge vectors, |h|^2 as a float
+// pair, one Newton step from rsqrtf) and accumulate the sums of f, f beta_a,
+// f beta'_b and f beta_a beta'_b for a, b < 2 as float pairs; the third
+// components follow from beta_2 = -beta_0 - beta_1, in float64.
 __global__ void __launch_bounds__(256)
 k_p1_singular(const P1Item* __restrict__ items, const unsigned long long* __restrict__ counts, int64_t cap,
               const int* __restrict__ tri, const double* __restrict__ vert, const double* __restrict__ area2,
@@ -559,44 +573,102 @@ k_p1_singular(const P1Item* __restrict__ items, const unsigned long long* __rest
       Q[a] = tj[cj[a]];
     }
   }
-  double V[4][3];
-  for (int d = 0; d < 3; ++d) {
-    V[0][d] = vert[3 * P[1] + d] - vert[3 * P[0] + d];
-    V[1][d] = vert[3 * P[2] + d] - vert[3 * P[1] + d];
-    V[2][d] = cs == 1 ? vert[3 * Q[1] + d] - vert[3 * Q[0] + d] : (cs == 2 ? vert[3 * Q[2] + d] - vert[3 * Q[1] + d] : 0.0);
-    V[3][d] = cs == 1 ? vert[3 * Q[2] + d] - vert[3 * Q[1] + d] : 0.0;
+  // edge vectors as float pairs (case 1: e1, e2, f1, f2; case 2: e1, e2, f2;
+  // case 3: e1, e2): lane 3k + d forms component d of vector k in float64
+  // and splits it, the others receive it by shuffles
+  const int nt = cs == 3 ? 2 : (cs == 2 ? 3 : 4);
+  float my_h = 0.f, my_l = 0.f;
+  if (lane < 3 * nt) {
+    const int k = lane / 3, d = lane - 3 * k;
+    const bool useq = (cs == 1 && k >= 2) || (cs == 2 && k == 2);
+    const bool second = !(k == 0 || (cs == 1 && k == 2));  // edge (1, 2) instead of (0, 1)
+    const int i0 = useq ? (second ? Q[1] : Q[0]) : (second ? P[1] : P[0]);
+    const int i1 = useq ? (second ? Q[2] : Q[1]) : (second ? P[2] : P[1]);
+    const double x = vert[3 * i1 + d] - vert[3 * i0 + d];
+    my_h = (float)x;
+    my_l = (float)(x - (double)my_h);
   }
+  float vh[4][3], vl[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      vh[k][d] = __shfl_sync(0xffffffffu, my_h, 3 * k + d);  // lanes >= 3 nt hold zeros
+      vl[k][d] = __shfl_sync(0xffffffffu, my_l, 3 * k + d);
+    }
   const int t0 = cs == 1 ? toff.x : (cs == 2 ? toff.y : toff.z);
   const int tn = cs == 1 ? tcnt.x : (cs == 2 ? tcnt.y : tcnt.z);
-  double s0 = 0.0, sa[3] = {0, 0, 0}, sb[3] = {0, 0, 0}, sab[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  // float-pair sums: 0 f, 1-2 f beta_a, 3-4 f beta'_b, 5-8 f beta_a beta'_b
+  float sh[9], sl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) sh[i] = sl[i] = 0.f;
   for (int s = lane; s < tn; s += 32) {
     const SSEntryP1 e = table[t0 + s];
-    double h[3];
+    const float ch[4] = {e.ch.x, e.ch.y, e.ch.z, e.ch.w}, cl[4] = {e.cl.x, e.cl.y, e.cl.z, e.cl.w};
+    float hh[3], hl[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) h[d] = e.c[0] * V[0][d] + e.c[1] * V[1][d] + e.c[2] * V[2][d] + e.c[3] * V[3][d];
-    const double f = e.w * rsqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
-    const double ba[3] = {-e.uh[0], e.uh[0] - e.uh[1], e.uh[1]};
-    const double bb[3] = {-e.vh[0], e.vh[0] - e.vh[1], e.vh[1]};
-    s0 += f;
+    for (int d = 0; d < 3; ++d) {
+      hh[d] = 0.f;
+      hl[d] = 0.f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      sa[a] += f * ba[a];
-      sb[a] += f * bb[a];
+      for (int k = 0; k < 4; ++k)
+        if (k < nt) fp_mul_add(ch[k], cl[k], vh[k][d], vl[k][d], hh[d], hl[d]);
+    }
+    const float p0 = __fmul_rn(hh[0], hh[0]), p1 = __fmul_rn(hh[1], hh[1]), p2 = __fmul_rn(hh[2], hh[2]);
+    float low = __fmaf_rn(hh[0], hh[0], -p0);
+    low = __fadd_rn(low, __fmaf_rn(hh[1], hh[1], -p1));
+    low = __fadd_rn(low, __fmaf_rn(hh[2], hh[2], -p2));
+    low = __fmaf_rn(__fadd_rn(__fadd_rn(hh[0], hh[0]), hl[0]), hl[0], low);
+    low = __fmaf_rn(__fadd_rn(__fadd_rn(hh[1], hh[1]), hl[1]), hl[1], low);
+    low = __fmaf_rn(__fadd_rn(__fadd_rn(hh[2], hh[2]), hl[2]), hl[2], low);
+    float s01, e01, rh, e2;
+    two_sum(p0, p1, s01, e01);
+    two_sum(s01, p2, rh, e2);
+    const float rl = __fadd_rn(low, __fadd_rn(e01, e2));
+    const float y0 = rsqrtf(__fadd_rn(rh, rl));
+    const float u = __fmul_rn(y0, y0), uu = __fmaf_rn(y0, y0, -u);
+    const float m = __fmul_rn(u, rh), me = __fmaf_rn(u, rh, -m);
+    const float rho = __fmaf_rn(-uu, rh, __fmaf_rn(-u, rl, __fsub_rn(__fsub_rn(1.f, m), me)));
+    const float dy = __fmul_rn(__fmul_rn(0.5f, y0), rho);
+    float fh, fl;  // f = w / |h|
+    pair_mul(e.wh, e.wl, y0, dy, fh, fl);
+    pair_acc(sh[0], sl[0], fh, fl);
+    float gh[2], gl[2];  // f beta_a
+    pair_mul(fh, fl, e.ba.x, e.ba.y, gh[0], gl[0]);
+    pair_mul(fh, fl, e.ba.z, e.ba.w, gh[1], gl[1]);
+    pair_acc(sh[1], sl[1], gh[0], gl[0]);
+    pair_acc(sh[2], sl[2], gh[1], gl[1]);
+    const float bh[2] = {e.bb.x, e.bb.z}, bl[2] = {e.bb.y, e.bb.w};
 #pragma unroll
-      for (int b = 0; b < 3; ++b) sab[a][b] += f * ba[a] * bb[b];
+    for (int b = 0; b < 2; ++b) {
+      float th, tl;
+      pair_mul(fh, fl, bh[b], bl[b], th, tl);
+      pair_acc(sh[3 + b], sl[3 + b], th, tl);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        pair_mul(gh[a], gl[a], bh[b], bl[b], th, tl);
+        pair_acc(sh[5 + 2 * a + b], sl[5 + 2 * a + b], th, tl);
+      }
     }
   }
-  for (int o = 16; o; o >>= 1) {
-    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+  double S[9];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      sa[a] += __shfl_xor_sync(0xffffffffu, sa[a], o);
-      sb[a] += __shfl_xor_sync(0xffffffffu, sb[a], o);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) sab[a][b] += __shfl_xor_sync(0xffffffffu, sab[a][b], o);
-    }
+  for (int i = 0; i < 9; ++i) {
+    double v = (double)sh[i] + (double)sl[i];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    S[i] = v;
   }
   if (lane != 0) return;
+  const double s0 = S[0];
+  const double sa[3] = {S[1], S[2], -(S[1] + S[2])};
+  const double sb[3] = {S[3], S[4], -(S[3] + S[4])};
+  double sab[3][3];
+  sab[0][0] = S[5];
+  sab[0][1] = S[6];
+  sab[1][0] = S[7];
+  sab[1][1] = S[8];
+  for (int a = 0; a < 2; ++a) sab[a][2] = -(sab[a][0] + sab[a][1]);
+  for (int b = 0; b < 3; ++b) sab[2][b] = -(sab[0][b] + sab[1][b]);
   const double jac = area2[it.ti] * area2[it.tj] * kInv4Pi;
   double M[3][3];  // stored corners
 #pragma unroll
