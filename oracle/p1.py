@@ -193,6 +193,10 @@ class P1Galerkin:
     def n(self):
         return self.v.shape[0]
 
+    def regular_pairs(self, ti, si):
+        """3 x 3 matrices of disjoint triangle pairs (triangle ids)."""
+        return local_regular(self.v, self.t[ti], self.t[si])
+
     def pair(self, ti, si):
         """3 x 3 matrix of the triangle pair (ti, si), cached."""
         key = (ti, si)
@@ -227,7 +231,7 @@ class P1Galerkin:
             nsh = (tr[:, None, :, None] == tc[None, :, None, :]).sum(axis=(2, 3))
             ii, jj = np.nonzero(nsh == 0)
             if len(ii):
-                M = local_regular(self.v, tr[ii], tc[jj])
+                M = self.regular_pairs(ti[ii], ct[jj])
                 self._scatter(out, rl[s0 + ii], cl[jj], M)
             for i, j in zip(*np.nonzero(nsh > 0)):
                 M = self.pair(int(ti[i]), int(ct[j]))[None]

@@ -15,6 +15,7 @@ from .meshes import (  # noqa: F401
     perturb_sphere,
     scale_axes,
     mesh_for_config,
+    edge_midpoints_for_config,
     batch_meshes,
 )
 from .rhs import uniform_rhs, normal_rhs, exterior_points  # noqa: F401

@@ -208,3 +208,26 @@ def batch_meshes(count, seed=0, s_min=8, s_max=32):
             v = perturb_sphere(v, 0.1)
         out.append((np.ascontiguousarray(v), t.copy()))
     return out
+
+
+def edge_midpoints_for_config(name):
+    """Surface points at the edge midpoints of the mesh ``mesh_for_config(name)``
+    (the quadratic nodes of curved triangles): for each triangle the points
+    over its edges (0, 1), (1, 2), (2, 0), shape (nt, 3, 3).  The midpoint of
+    the two unit-sphere vertices is projected onto the unit sphere and then
+    perturbed and scaled like the vertices."""
+    table = {"sphere80": (1, None, None), "sphere320": (2, None, None), "sphere1280": (3, None, None),
+             "sphere5120": (4, None, None), "sphere20480": (5, None, None),
+             "perturbed320": (2, 0.1, None), "perturbed1280": (3, 0.1, None),
+             "perturbed20480": (5, 0.1, None), "ellipsoid1280": (3, None, (1.0, 1.5, 2.5))}
+    level, amp, axes = table[name]
+    v, t = icosphere(level)
+    a = v[t]                                  # (nt, 3, 3) unit-sphere corners
+    m = 0.5 * (a + a[:, [1, 2, 0], :])        # edges (0, 1), (1, 2), (2, 0)
+    m = m / np.sqrt((m * m).sum(axis=2))[:, :, None]
+    m = m.reshape(-1, 3)
+    if amp is not None:
+        m = perturb_sphere(m, amp)
+    if axes is not None:
+        m = scale_axes(m, axes)
+    return m.reshape(-1, 3, 3)
