@@ -448,6 +448,23 @@ def run_legs(gca, batch, meshes, stats, n, args, dev, stream, hbm_peak):
     h.check()
     legs["sphere81920.R64"] = cfg3
     del h
+    # the single layer's entries in float64 arithmetic (GCA_F64_ENTRIES, the
+    # paper's precision for the near-singular quadrature) beside the float-pair
+    # default: the same batch build of the bench's two meshes
+    trees = [gca.tree_build(v, t, PARAMS["leaf_size"]) for v, t in meshes]
+    gca.profile_enable(True)
+    a.record(stream)
+    b64 = gca.build_batch(meshes, trees, gca.Params(**PARAMS, flags=gca.F64_ENTRIES))
+    b.record(stream)
+    b.synchronize()
+    ph64 = gca.profile_read()
+    gca.profile_enable(False)
+    legs["f64_entries.sphere20480x2"] = {
+        "workload": "the bench's two meshes, gca_build_batch with GCA_F64_ENTRIES",
+        "build_s": a.elapsed_time(b) * 1e-3,
+        "phases_ms": {k: round(ph64[k][1], 3) for k in ("couple_entries", "near_entries", "singular") if k in ph64}}
+    b64.free()
+    del b64
     # the double-layer operator K on the perturbed 20480-triangle sphere (its
     # row bases are the single layer's, its column bases its own)
     v, t = meshes[1]
@@ -552,6 +569,33 @@ def run_legs(gca, batch, meshes, stats, n, args, dev, stream, hbm_peak):
     hp.check()
     legs["p1.sphere20480.R16"] = p1g
     del hp
+    # the nodal basis on curved triangles (Sect. 6): the same mesh with the
+    # surface points over its edges
+    mids = synth.edge_midpoints_for_config(MESHES[0])
+    gca.profile_enable(True)
+    a.record(stream)
+    hq = gca.build_p1_curved(v, t, mids, tree, gca.Params(**PARAMS, flags=gca.DROP_EXPORT))
+    b.record(stream)
+    b.synchronize()
+    ph_q = gca.profile_read()
+    gca.profile_enable(False)
+    st = hq.stats()
+    p1c = {"workload": "nodal basis on curved triangles, sphere20480 (10242 vertices), leaf 64, eta 2, m 4, "
+                       "tol 1e-8, 16 RHS N(0,1)",
+           "build_s": a.elapsed_time(b) * 1e-3, "rank_sum": st["rank_sum"],
+           "phases_ms": {k: round(ms, 3) for k, (_, ms) in ph_q.items()},
+           "touching_pairs": st["n_singular"][1:]}
+    y64 = torch.empty((NRHS, nv), dtype=torch.float64, device=dev).t()
+    for prec in ("f64", "f32", "bf16"):
+        xin = x64 if prec == "f64" else x32
+        out = y64 if prec == "f64" else torch.empty((NRHS, nv), dtype=torch.float32, device=dev).t()
+        ms = time_products(lambda: hq.matvec(xin, prec, out=out), K, W, stream)
+        byt = product_bytes(st, prec, nv, NRHS)
+        p1c[prec] = {"GB/s": byt / ms / 1e6, "frac_hbm": byt / ms / 1e6 / hbm_peak, "ms": ms,
+                     "err_vs_f64": 0.0 if prec == "f64" else leg_errors([out], [y64])}
+    hq.check()
+    legs["p1_curved.sphere20480.R16"] = p1c
+    del hq
     legs["error_vs_storage.sphere5120"] = error_vs_storage(gca, dev)
     return legs
 

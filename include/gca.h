@@ -130,8 +130,15 @@ enum {
                           rejected (the float32 near field stays while
                           GCA_BF16 products are kept)                      */
   GCA_DROP_BF16 = 4,   /* no bfloat16 panels: GCA_BF16 products rejected    */
-  GCA_DROP_EXPORT = 8  /* free the row-major float64 V, E, S, N after the
+  GCA_DROP_EXPORT = 8, /* free the row-major float64 V, E, S, N after the
                           build: gca_h2_export of them is rejected          */
+  GCA_F64_ENTRIES = 16 /* single layer (gca_build, gca_build_batch,
+                          gca_build_single_level, gca_build_green_quadrature):
+                          coupling and near-field entries and the
+                          Sauter-Schwab samples in float64 arithmetic
+                          instead of float-pair arithmetic on the FP32 pipe
+                          (the paper's precision for the near-singular
+                          quadrature; slower on this GPU's FP64 pipe)      */
 };
 
 enum {
@@ -342,6 +349,26 @@ int gca_build_green_quadrature(const gca_mesh* mesh, const gca_tree* tree, const
  * synchronisation as gca_build. */
 int gca_build_p1(const gca_mesh* mesh, const gca_tree* tree, const gca_params* params,
                  void* stream, gca_h2** out);
+
+/* The nodal basis of gca_build_p1 on curved triangles (Sect. 6): every
+ * triangle t is the quadratic map Phi_t of the reference triangle through
+ * its vertices and the surface points over its edges,
+ *   Phi_t(lambda) = sum_a lambda_a (2 lambda_a - 1) X_a
+ *                   + 4 (lambda_0 lambda_1 M01 + lambda_1 lambda_2 M12 + lambda_2 lambda_0 M20),
+ * the basis functions are mapped nodal ones (phi_i o Phi_t = lambda_c),
+ * and integrals over t carry the Gramian |d1 Phi_t x d2 Phi_t|.
+ *   midpoints  host [nt][3][3], caller-owned, read during the call: for
+ *              triangle t the points M01, M12, M20 over its edges (0, 1),
+ *              (1, 2), (2, 0) (e.g. the edge midpoints projected onto the
+ *              surface; the flat midpoints give gca_build_p1's matrix).
+ * Cluster boxes hold all six nodes of every support triangle; the 7-point
+ * rule takes nodes Phi(lambda_q) with weights w_q |Phi|'(lambda_q) / 2;
+ * touching pairs use the Sauter-Schwab maps with all four variables sampled
+ * (q^4 samples per piece, float64; the map is not affine).  Otherwise as
+ * gca_build_p1.  Errors additionally: INVALID_ARG (midpoints NULL),
+ * NUMERIC (a non-finite edge point). */
+int gca_build_p1_curved(const gca_mesh* mesh, const double* midpoints, const gca_tree* tree,
+                        const gca_params* params, void* stream, gca_h2** out);
 
 /* The support unions of Sect. 5 on the device, for inspection and tests:
  * for each of nlists lists of vertex ids (host CSR: list l is

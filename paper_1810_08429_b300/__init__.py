@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgca.so")
 
 F64, F32, BF16 = 0, 1, 2
-DROP_F64, DROP_F32, DROP_BF16, DROP_EXPORT = 1, 2, 4, 8  # gca_params.flags
+DROP_F64, DROP_F32, DROP_BF16, DROP_EXPORT, F64_ENTRIES = 1, 2, 4, 8, 16  # gca_params.flags
 _PREC = {"f64": F64, "f32": F32, "bf16": BF16, F64: F64, F32: F32, BF16: BF16}
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -139,6 +139,8 @@ def _load():
                                                       ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
         "gca_build_p1": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
                                         ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
+        "gca_build_p1_curved": (ctypes.c_int, [ctypes.POINTER(_Mesh), _f64p, ctypes.POINTER(_Tree),
+                                               ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
         "gca_tree_build_points": (ctypes.c_int, [ctypes.c_int32, _f64p, ctypes.c_int32, ctypes.c_int32,
                                                  _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
         "gca_support_union": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.c_int32, _i32p, _i32p, _i32p,
@@ -527,6 +529,22 @@ def build_p1(vertices, triangles, tree, params, stream=None):
     ``tree_build_points(vertices, leaf)``); returns an ``H2`` whose products
     take x and y with one row per vertex."""
     return _build_with(lib.gca_build_p1, "gca_build_p1", vertices, triangles, tree, params, stream)
+
+
+def build_p1_curved(vertices, triangles, midpoints, tree, params, stream=None):
+    """gca_build_p1_curved: the nodal basis on curved triangles (Sect. 6);
+    `midpoints` (nt, 3, 3) holds the surface points over the edges (0, 1),
+    (1, 2), (2, 0) of every triangle."""
+    m, keep_m = _mesh(vertices, triangles)
+    mid = np.ascontiguousarray(midpoints, dtype=np.float64)
+    if mid.shape != (m.nt, 3, 3):
+        raise ValueError("midpoints must be (nt, 3, 3)")
+    t, keep_t = _tree(tree)
+    p = params._c()
+    h = ctypes.c_void_p(None)
+    _check(lib.gca_build_p1_curved(ctypes.byref(m), mid.ctypes.data_as(_f64p), ctypes.byref(t), ctypes.byref(p),
+                                   _stream_ptr(stream), ctypes.byref(h)), "gca_build_p1_curved")
+    return H2(h.value)
 
 
 def build_collocation(vertices, triangles, tree, params, stream=None):

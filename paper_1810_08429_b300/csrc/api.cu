@@ -97,6 +97,21 @@ int gca_build_p1(const gca_mesh* mesh, const gca_tree* tree, const gca_params* p
   }
 }
 
+int gca_build_p1_curved(const gca_mesh* mesh, const double* midpoints, const gca_tree* tree,
+                        const gca_params* params, void* stream, gca_h2** out) {
+  if (!out) {
+    gca::set_error("gca_build_p1_curved: out is NULL");
+    return GCA_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    return gca::build(mesh, tree, params, static_cast<cudaStream_t>(stream), out, 6, midpoints);
+  } catch (const std::bad_alloc&) {
+    gca::set_error("gca_build_p1_curved: host allocation failed");
+    return GCA_ERR_OOM;
+  }
+}
+
 int gca_support_union(const gca_mesh* mesh, int32_t nlists, const int32_t* list_ptr, const int32_t* lists,
                       int32_t* rows, int64_t cap, int32_t* counts, void* stream) {
   try {

@@ -1093,31 +1093,45 @@ __device__ __forceinline__ double regular_entry_split(const SplitNode* __restric
 // entry is computed once and stored twice.  pairs[i] = (b, m): block b and
 // its mirror m (-1: b is computed alone).  The column pivots' nodes are
 // staged in shared memory.  S is row-major r_tau x r_sigma per block.
+// F64: the same entries by the float64 rule of regular_entry (GCA_F64_ENTRIES).
+template <bool F64>
 __global__ void k_couple_entries(const int2* __restrict__ pairs, const int* __restrict__ far_t,
                                  const int* __restrict__ far_s, const int64_t* __restrict__ soff,
                                  const int* __restrict__ rank, const int64_t* __restrict__ poff,
                                  const int* __restrict__ piv, const SplitNode* __restrict__ tn,
-                                 double* __restrict__ S) {
+                                 const P4* __restrict__ tq, double* __restrict__ S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SplitNode* ys = reinterpret_cast<SplitNode*>(smem_raw);
+  P4* yq = reinterpret_cast<P4*>(smem_raw);  // F64: the same bytes (sizeof(P4) == sizeof(SplitNode))
   const int2 bm = pairs[blockIdx.x];
   const int b = bm.x;
   const int t = far_t[b], s = far_s[b];
   const int rt = rank[t], rs = rank[s];
   const int* pt = piv + poff[t];
   const int* ps = piv + poff[s];
-  for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) ys[i] = tn[7 * (int64_t)ps[i / 7] + i % 7];
+  for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) {
+    if (F64)
+      yq[i] = tq[7 * (int64_t)ps[i / 7] + i % 7];
+    else
+      ys[i] = tn[7 * (int64_t)ps[i / 7] + i % 7];
+  }
   __syncthreads();
   double* out = S + soff[b];
   double* mir = bm.y >= 0 ? S + soff[bm.y] : nullptr;
   for (int idx = threadIdx.x; idx < rt * rs; idx += blockDim.x) {
     const int a = idx / rs, c = idx % rs;
-    float mr;
-    const double v = regular_entry_split(tn + 7 * (int64_t)pt[a], ys + 7 * c, mr);
+    double v;
+    if (F64) {
+      v = regular_entry(tq + 7 * (int64_t)pt[a], yq + 7 * c);
+    } else {
+      float mr;
+      v = regular_entry_split(tn + 7 * (int64_t)pt[a], ys + 7 * c, mr);
+    }
     out[idx] = v;
     if (mir) mir[(int64_t)c * rt + a] = v;
   }
 }
+static_assert(sizeof(P4) == sizeof(SplitNode), "k_couple_entries stages either kind of node in the same bytes");
 
 struct SingularItem {
   int64_t pos;  // position in N
@@ -1130,6 +1144,7 @@ struct SingularItem {
 // 3 identical).  A disjoint pair is evaluated in float-pair arithmetic and
 // again in float64 when two of its nodes are closer than sqrt(near_r2) =
 // 2^(E - 8) (so that the float-pair error stays below about 2^-37).
+template <bool F64>
 __global__ void k_near_entries(const int* __restrict__ near_t, const int* __restrict__ near_s,
                                const int64_t* __restrict__ noff, const int* __restrict__ begin,
                                const int* __restrict__ end, const int* __restrict__ perm,
@@ -1161,9 +1176,14 @@ __global__ void k_near_entries(const int* __restrict__ near_t, const int* __rest
       shared += (va == tri[3 * tj]) + (va == tri[3 * tj + 1]) + (va == tri[3 * tj + 2]);
     }
     if (shared == 0) {
-      float mr;
-      double v = regular_entry_split(tn + 7 * (int64_t)ti, yn + 7 * j, mr);
-      if (mr < near_r2) v = regular_entry(tq + 7 * (int64_t)ti, ys + 7 * j);
+      double v;
+      if (F64) {
+        v = regular_entry(tq + 7 * (int64_t)ti, ys + 7 * j);
+      } else {
+        float mr;
+        v = regular_entry_split(tn + 7 * (int64_t)ti, yn + 7 * j, mr);
+        if (mr < near_r2) v = regular_entry(tq + 7 * (int64_t)ti, ys + 7 * j);
+      }
       N[base + idx] = v;
     } else {
       const unsigned long long slot = atomicAdd(&counts[shared], 1ull);
@@ -1497,7 +1517,7 @@ struct __align__(16) SSEntry64 {
 template <int CASE>
 void sauter_table64(const Rules& rules, std::vector<SSEntry64>& out) {
   const int q = rules.q, q3 = q * q * q;
-  constexpr int pieces = CASE == 2 ? 5 : 2;
+  constexpr int pieces = CASE == 3 ? 6 : (CASE == 2 ? 5 : 2);
   for (int s = 0; s < pieces * q3; ++s) {
     const int piece = s / q3, r = s % q3;
     const int a = r / (q * q), b = (r / q) % q, c = r % q;
@@ -1507,12 +1527,77 @@ void sauter_table64(const Rules& rules, std::vector<SSEntry64>& out) {
     SSEntry64 e{};
     if (CASE == 1) {
       e.c[0] = (double)u1; e.c[1] = (double)u2; e.c[2] = (double)-v1; e.c[3] = (double)-v2;
-    } else {
+    } else if (CASE == 2) {
       e.c[0] = (double)(u1 - v1); e.c[1] = (double)u2; e.c[2] = (double)-v2; e.c[3] = 0.0;
+    } else {
+      e.c[0] = (double)(u1 - v1); e.c[1] = (double)(u2 - v2); e.c[2] = 0.0; e.c[3] = 0.0;
     }
     e.w = (double)((long double)rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * wj);
     out.push_back(e);
   }
+}
+
+// The single layer's touching pairs in float64 (GCA_F64_ENTRIES): one warp
+// per pair, the vertex orders and edge vectors of k_singular, 1 / |h| summed
+// over the eta samples of a float64 table (the xi-integral exactly 1/3).
+template <int CASE>
+__global__ void k_singular64(const SingularItem* __restrict__ items, const unsigned long long* __restrict__ counts,
+                             int64_t cap, const int* __restrict__ tri, const double* __restrict__ vert,
+                             const double* __restrict__ area2, const SSEntry64* __restrict__ table, int nsamples,
+                             double* __restrict__ N) {
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t count = min((long long)counts[CASE], (long long)cap);
+  if (w >= count) return;
+  const SingularItem it = items[w];
+  int ti[3], tj[3];
+  for (int a = 0; a < 3; ++a) {
+    ti[a] = tri[3 * it.ti + a];
+    tj[a] = tri[3 * it.tj + a];
+  }
+  int P[3], Q[3];
+  if (CASE == 3) {
+    for (int a = 0; a < 3; ++a) P[a] = Q[a] = ti[a];
+  } else if (CASE == 2) {
+    int sh[2], ns = 0, oi = -1, oj = -1;
+    for (int a = 0; a < 3; ++a) {
+      const bool in_j = ti[a] == tj[0] || ti[a] == tj[1] || ti[a] == tj[2];
+      if (in_j) sh[ns++] = ti[a]; else oi = ti[a];
+    }
+    for (int a = 0; a < 3; ++a)
+      if (tj[a] != sh[0] && tj[a] != sh[1]) oj = tj[a];
+    P[0] = Q[0] = sh[0];
+    P[1] = Q[1] = sh[1];
+    P[2] = oi;
+    Q[2] = oj;
+  } else {
+    int pi = 0, pj = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (ti[a] == tj[b]) { pi = a; pj = b; }
+    for (int a = 0; a < 3; ++a) {
+      P[a] = ti[(pi + a) % 3];
+      Q[a] = tj[(pj + a) % 3];
+    }
+  }
+  double V[4][3];
+  for (int d = 0; d < 3; ++d) {
+    V[0][d] = vert[3 * P[1] + d] - vert[3 * P[0] + d];
+    V[1][d] = vert[3 * P[2] + d] - vert[3 * P[1] + d];
+    V[2][d] = CASE == 1 ? vert[3 * Q[1] + d] - vert[3 * Q[0] + d]
+                        : (CASE == 2 ? vert[3 * Q[2] + d] - vert[3 * Q[1] + d] : 0.0);
+    V[3][d] = CASE == 1 ? vert[3 * Q[2] + d] - vert[3 * Q[1] + d] : 0.0;
+  }
+  double acc = 0.0;
+  for (int s = lane; s < nsamples; s += 32) {
+    const SSEntry64 e = table[s];
+    double h[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) h[d] = e.c[0] * V[0][d] + e.c[1] * V[1][d] + e.c[2] * V[2][d] + e.c[3] * V[3][d];
+    acc += e.w * rsqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+  }
+  for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) N[it.pos] = acc * area2[it.ti] * area2[it.tj] * (kInv4Pi / 3.0);
 }
 
 // one warp per pair with a common vertex (CASE 1) or edge (CASE 2): on each
@@ -1975,8 +2060,9 @@ struct BasisPass {
 
 class Builder {
  public:
-  Builder(const gca_mesh* mesh_, const gca_tree* tree_, const gca_params* prm_, cudaStream_t st_, int op_)
-      : mesh(mesh_), tree(tree_), prm(prm_), st(st_), op(op_) {}
+  Builder(const gca_mesh* mesh_, const gca_tree* tree_, const gca_params* prm_, cudaStream_t st_, int op_,
+          const double* midpoints_ = nullptr)
+      : mesh(mesh_), tree(tree_), prm(prm_), st(st_), op(op_), midpoints(midpoints_) {}
   int prepare();
   int rows();
   int finish(gca_h2** out);
@@ -2010,8 +2096,10 @@ class Builder {
   const gca_params* prm;
   cudaStream_t st;
   int op;
+  const double* midpoints;  // op 6: [nt][3][3] surface points over the edges
   std::chrono::steady_clock::time_point t0;
-  bool p1 = false, single = false;
+  bool p1 = false, single = false, curved = false;
+  DevMem d_mid;
   std::vector<int> sup_ptr, sup_item;
   std::unique_ptr<gca_h2> h;
   int n = 0, nc = 0, k = 0, ntri = 0;
@@ -2033,20 +2121,33 @@ int Builder::prepare() {
   t0 = std::chrono::steady_clock::now();
   GCA_TRY(validate_mesh(mesh));
   // op 5 (nodal basis, Sect. 5): the indices are the vertices
-  p1 = op == 5;
+  p1 = op == 5 || op == 6;
+  curved = op == 6;
   gca_mesh shape = *mesh;
   if (p1) shape.nt = mesh->nv;
   GCA_TRY(validate_tree(&shape, tree, GCA_MAX_LEAF));
   if (!prm || !(prm->eta > 0.0) || prm->box_gauss_m < 1 || prm->box_gauss_m > GCA_MAX_BOX_M ||
       !(prm->aca_tol >= 0.0) || prm->tri_rule != 7 || prm->sauter_q < 1 ||
       prm->sauter_q > GCA_MAX_SAUTER_Q ||
-      (prm->flags & ~(uint32_t)(GCA_DROP_F64 | GCA_DROP_F32 | GCA_DROP_BF16 | GCA_DROP_EXPORT)) != 0) {
+      (prm->flags & ~(uint32_t)(GCA_DROP_F64 | GCA_DROP_F32 | GCA_DROP_BF16 | GCA_DROP_EXPORT | GCA_F64_ENTRIES)) !=
+          0) {
     set_error("gca_build: invalid parameters");
     return GCA_ERR_INVALID_ARG;
   }
   // supports of the nodal basis functions: the triangles at each vertex in
   // ascending order, as (triangle << 2) | corner
-  if (p1) GCA_TRY(node_supports(mesh, sup_ptr, sup_item, "gca_build_p1"));
+  if (p1) GCA_TRY(node_supports(mesh, sup_ptr, sup_item, curved ? "gca_build_p1_curved" : "gca_build_p1"));
+  if (curved) {
+    if (!midpoints) {
+      set_error("gca_build_p1_curved: midpoints is NULL");
+      return GCA_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < 9LL * mesh->nt; ++i)
+      if (!std::isfinite(midpoints[i])) {
+        set_error("gca_build_p1_curved: non-finite edge point");
+        return GCA_ERR_NUMERIC;
+      }
+  }
   h = std::make_unique<gca_h2>();
   GCA_TRY_CUDA(cudaGetDevice(&h->device));
   h->device += test_hooks().device_skew;
@@ -2098,18 +2199,33 @@ int Builder::prepare() {
     GCA_TRY(upload(d_sup_ptr, sup_ptr, st));
     GCA_TRY(upload(d_sup_item, sup_item, st));
   }
+  if (curved) {
+    std::vector<double> mids(midpoints, midpoints + 9LL * ntri);
+    GCA_TRY(upload(d_mid, mids, st));
+    GCA_TRY_CUDA(cudaStreamSynchronize(st));  // mids is a local
+  }
   GCA_TRY(d_box.alloc(sizeof(double) * 6 * (size_t)nc));
   GCA_TRY(d_status.alloc(sizeof(int)));
   GCA_TRY_CUDA(cudaMemsetAsync(d_status.p, 0, sizeof(int), st));
   {
     PhaseScope ps__("tri_geom", st);
-    k_tri_geom<<<blocks_for(ntri, 128), 128, 0, st>>>(ntri, h->d_vert.as<double>(), h->d_tri.as<int>(), rules,
-                                                  d_tq.as<P4>(), d_area2.as<double>(),
-                                                  op == 1 ? d_nrm.as<double>() : nullptr);
+    if (curved)
+      k_tri_geom_curved<<<blocks_for(ntri, 128), 128, 0, st>>>(ntri, h->d_vert.as<double>(), h->d_tri.as<int>(),
+                                                               d_mid.as<double>(), rules, d_tq.as<P4>(),
+                                                               d_area2.as<double>());
+    else
+      k_tri_geom<<<blocks_for(ntri, 128), 128, 0, st>>>(ntri, h->d_vert.as<double>(), h->d_tri.as<int>(), rules,
+                                                    d_tq.as<P4>(), d_area2.as<double>(),
+                                                    op == 1 ? d_nrm.as<double>() : nullptr);
   }
   {
     PhaseScope ps__("cluster_boxes", st);
-    if (p1)
+    if (curved)
+      k_p1c_boxes<<<blocks_for(32LL * nc, 128), 128, 0, st>>>(
+          nc, h->d_begin.as<int>(), h->d_end.as<int>(), h->d_perm.as<int>(), d_sup_ptr.as<int>(),
+          d_sup_item.as<int>(), h->d_tri.as<int>(), h->d_vert.as<double>(), d_mid.as<double>(),
+          d_box.as<double>());
+    else if (p1)
       k_p1_boxes<<<blocks_for(32LL * nc, 128), 128, 0, st>>>(
           nc, h->d_begin.as<int>(), h->d_end.as<int>(), h->d_perm.as<int>(), d_sup_ptr.as<int>(),
           d_sup_item.as<int>(), h->d_tri.as<int>(), h->d_vert.as<double>(), d_box.as<double>());
@@ -2455,13 +2571,18 @@ int Builder::finish(gca_h2** out) {
   DevMem d_ss, d_ss64;
   GCA_TRY(upload(d_ss, ss, st));
   // the double layer's samples in float64 (vertex, edge)
+  // the double layer's samples in float64 (vertex, edge), or the single
+  // layer's (vertex, edge, identical) with GCA_F64_ENTRIES
+  const bool f64_entries = (prm->flags & GCA_F64_ENTRIES) && (op == 0 || op == 3 || op == 4);
   std::vector<SSEntry64> ss64;
-  int ss64_off[3] = {0, 0, 0};
-  if (op == 1) {
+  int ss64_off[4] = {0, 0, 0, 0};
+  if (op == 1 || f64_entries) {
     sauter_table64<1>(rules, ss64);
     ss64_off[1] = (int)ss64.size();
     sauter_table64<2>(rules, ss64);
     ss64_off[2] = (int)ss64.size();
+    if (f64_entries) sauter_table64<3>(rules, ss64);
+    ss64_off[3] = (int)ss64.size();
     GCA_TRY(upload(d_ss64, ss64, st));
   }
   GCA_TRY(d_counts.alloc(sizeof(unsigned long long) * 10));
@@ -2627,12 +2748,13 @@ int Builder::finish(gca_h2** out) {
     GCA_TRY_CUDA(cudaGetLastError());
   } else if (nfar > 0) {
     const size_t smem = sizeof(SplitNode) * 7 * (size_t)std::max(h->max_rank, 1);
-    GCA_TRY_CUDA(cudaFuncSetAttribute(k_couple_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = f64_entries ? k_couple_entries<true> : k_couple_entries<false>;
+    GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
       PhaseScope ps__("couple_entries", st);
-      k_couple_entries<<<(unsigned)pairs.size(), 256, smem, st>>>(
+      kern<<<(unsigned)pairs.size(), 256, smem, st>>>(
           d_pairs.as<int2>(), h->d_far_t.as<int>(), h->d_far_s.as<int>(), h->d_soff.as<int64_t>(),
-          h->d_rank.as<int>(), d_poff.as<int64_t>(), d_piv.as<int>(), d_tn.as<SplitNode>(),
+          h->d_rank.as<int>(), d_poff.as<int64_t>(), d_piv.as<int>(), d_tn.as<SplitNode>(), d_tq.as<P4>(),
           h->S64.as<double>());
     }
     GCA_TRY_CUDA(cudaGetLastError());
@@ -2666,10 +2788,11 @@ int Builder::finish(gca_h2** out) {
     GCA_TRY_CUDA(cudaGetLastError());
   } else if (nnear > 0) {
     const size_t smem = (sizeof(P4) + sizeof(SplitNode)) * 7 * (size_t)h->max_leaf;
-    GCA_TRY_CUDA(cudaFuncSetAttribute(k_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = f64_entries ? k_near_entries<true> : k_near_entries<false>;
+    GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
       PhaseScope ps__("near_entries", st);
-      k_near_entries<<<nnear, 256, smem, st>>>(
+      kern<<<nnear, 256, smem, st>>>(
           h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
           h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), d_tq.as<P4>(),
           d_tn.as<SplitNode>(), near_r2, h->N64.as<double>(), d_items.as<SingularItem>(), cap,
@@ -2689,7 +2812,29 @@ int Builder::finish(gca_h2** out) {
     GCA_TRY_CUDA(cudaMemcpyAsync(counts, d_counts.p, sizeof(counts), cudaMemcpyDeviceToHost, st));
     GCA_TRY_CUDA(cudaStreamSynchronize(st));
     for (int c = 0; c <= 3; ++c) h->n_singular[c] = (int64_t)counts[c];
-    if (counts[4] > 0) {
+    if (counts[4] > 0 && curved) {
+      // the curved rule's samples (xi sampled too)
+      std::vector<SSEntryCurved> tab;
+      int3 off{0, 0, 0}, cnt{0, 0, 0};
+      sauter_table_curved<1>(rules, tab);
+      cnt.x = (int)tab.size();
+      sauter_table_curved<2>(rules, tab);
+      off.y = cnt.x;
+      cnt.y = (int)tab.size() - off.y;
+      sauter_table_curved<3>(rules, tab);
+      off.z = off.y + cnt.y;
+      cnt.z = (int)tab.size() - off.z;
+      DevMem d_tab;
+      GCA_TRY(upload(d_tab, tab, st));
+      {
+        PhaseScope ps_sing("p1_singular", st);
+        k_p1c_singular<<<blocks_for(32LL * (int64_t)counts[4], 256), 256, 0, st>>>(
+            d_items.as<P1Item>(), d_counts.as<unsigned long long>(), cap, h->d_tri.as<int>(),
+            h->d_vert.as<double>(), d_mid.as<double>(), d_tab.as<SSEntryCurved>(), off, cnt, h->N64.as<double>());
+        GCA_TRY_CUDA(cudaGetLastError());
+      }
+      GCA_TRY_CUDA(cudaStreamSynchronize(st));  // tab and d_tab are locals
+    } else if (counts[4] > 0) {
       PhaseScope ps_sing("p1_singular", st);
       k_p1_singular<<<blocks_for(32LL * (int64_t)counts[4], 256), 256, 0, st>>>(
           d_items.as<P1Item>(), d_counts.as<unsigned long long>(), cap, h->d_tri.as<int>(),
@@ -2724,16 +2869,27 @@ int Builder::finish(gca_h2** out) {
         k_dl_singular<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
             items + cap, cnt, cap, tri_d, vert_d, a2, d_nrm.as<double>(), tab64 + ss64_off[1],
             ss64_off[2] - ss64_off[1], N64);
+    } else if (f64_entries) {
+      const SSEntry64* tab64 = d_ss64.as<SSEntry64>();
+      if (counts[1])
+        k_singular64<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
+            items, cnt, cap, tri_d, vert_d, a2, tab64, ss64_off[1], N64);
+      if (counts[2])
+        k_singular64<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
+            items + cap, cnt, cap, tri_d, vert_d, a2, tab64 + ss64_off[1], ss64_off[2] - ss64_off[1], N64);
+      if (counts[3])
+        k_singular64<3><<<blocks_for(32LL * counts[3], 256), 256, 0, st>>>(
+            items + 2 * cap, cnt, cap, tri_d, vert_d, a2, tab64 + ss64_off[2], ss64_off[3] - ss64_off[2], N64);
     } else {
-    if (counts[1])
-      k_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
-          items, cnt, cap, tri_d, vert_d, a2, tab + ss_off[0], ss_off[1] - ss_off[0], N64);
-    if (counts[2])
-      k_singular<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
-          items + cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[1], ss_off[2] - ss_off[1], N64);
-    if (counts[3])
-      k_singular<3><<<blocks_for(32LL * counts[3], 256), 256, 0, st>>>(
-          items + 2 * cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[2], ss_off[3] - ss_off[2], N64);
+      if (counts[1])
+        k_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
+            items, cnt, cap, tri_d, vert_d, a2, tab + ss_off[0], ss_off[1] - ss_off[0], N64);
+      if (counts[2])
+        k_singular<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
+            items + cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[1], ss_off[2] - ss_off[1], N64);
+      if (counts[3])
+        k_singular<3><<<blocks_for(32LL * counts[3], 256), 256, 0, st>>>(
+            items + 2 * cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[2], ss_off[3] - ss_off[2], N64);
     }
     GCA_TRY_CUDA(cudaGetLastError());
   }
@@ -2766,8 +2922,8 @@ int Builder::finish(gca_h2** out) {
 
 // The whole construction of one mesh.
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
-          gca_h2** out, int op) {
-  Builder b(mesh, tree, prm, st, op);
+          gca_h2** out, int op, const double* midpoints) {
+  Builder b(mesh, tree, prm, st, op, midpoints);
   GCA_TRY(b.prepare());
   GCA_TRY(b.rows());
   return b.finish(out);

@@ -130,9 +130,10 @@ class PhaseScope {
 // Entry points of the translation units.
 // op 0: the single-layer matrix G; op 1: the double-layer matrix K; op 2: the
 // collocation matrix C of the single layer; op 3: G by single-level GCA; op 4:
-// G by Green quadrature; op 5: G in the nodal (piecewise linear) basis
+// G by Green quadrature; op 5: G in the nodal (piecewise linear) basis;
+// op 6: the nodal basis on curved triangles (midpoints: [nt][3][3])
 int build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* prm, cudaStream_t st,
-          gca_h2** out, int op = 0);
+          gca_h2** out, int op = 0, const double* midpoints = nullptr);
 // gca_build_batch (build.cu): `count` single-layer meshes whose cross
 // approximations share one launch per tree level
 int build_group(int count, const gca_mesh* meshes, const gca_tree* trees, const gca_params* prm, cudaStream_t st,
@@ -270,8 +271,9 @@ struct gca_h2 {
   // columns), 1 the double layer, 2 the collocated single layer.  For op 1 and
   // 2 the columns have bases W, transfers F and pivots tilde-sigma' of their
   // own (the double layer's; the Galerkin single layer's under the
-  // collocation rows) and the couplings are r_tau x r'_sigma.  Op 5 (the
-  // nodal basis) is one-sided like op 0 with the vertices as indices.
+  // collocation rows) and the couplings are r_tau x r'_sigma.  Ops 5 and 6
+  // (the nodal basis on flat and on curved triangles) are one-sided like
+  // op 0 with the vertices as indices.
   int op = 0;
   std::vector<int> rank2;              // r'_sigma (op 1)
   std::vector<int64_t> xoff2;

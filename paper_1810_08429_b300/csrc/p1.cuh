@@ -683,3 +683,227 @@ k_p1_singular(const P1Item* __restrict__ items, const unsigned long long* __rest
     }
   p1_scatter(out, it.base, it.ld, it.base2, it.ld2, it.lr, it.lc, M);
 }
+
+// ----------------------------------------------- curved triangles (Sect. 6)
+//
+// A curved triangle is the quadratic map Phi of the reference triangle
+// through its vertices X0, X1, X2 and the surface points M01, M12, M20 over
+// its edges (the midpoints array: [nt][3][3], edges (0, 1), (1, 2), (2, 0)):
+//   Phi(lambda) = sum_a lambda_a (2 lambda_a - 1) X_a + 4 (lambda_0 lambda_1 M01
+//                 + lambda_1 lambda_2 M12 + lambda_2 lambda_0 M20),
+// with the Gramian gamma = |d1 Phi x d2 Phi| for x^ = (lambda_1, lambda_2).
+// The mapped nodal basis keeps the barycentric weights of the flat case.
+
+// Phi and gamma at lambda for six nodes X[6][3] (vertices, then edge points)
+__device__ __forceinline__ void curved_eval(const double (*X)[3], double l0, double l1, double l2, double* x,
+                                            double& gamma) {
+  const double N[6] = {l0 * (2.0 * l0 - 1.0), l1 * (2.0 * l1 - 1.0), l2 * (2.0 * l2 - 1.0),
+                       4.0 * l0 * l1,        4.0 * l1 * l2,        4.0 * l2 * l0};
+  // d/dx^_1 = d/dlambda_1 - d/dlambda_0, d/dx^_2 = d/dlambda_2 - d/dlambda_0
+  const double d1[6] = {-(4.0 * l0 - 1.0), 4.0 * l1 - 1.0, 0.0, 4.0 * (l0 - l1), 4.0 * l2, -4.0 * l2};
+  const double d2[6] = {-(4.0 * l0 - 1.0), 0.0, 4.0 * l2 - 1.0, -4.0 * l1, 4.0 * l1, 4.0 * (l0 - l2)};
+  double t1[3] = {0, 0, 0}, t2[3] = {0, 0, 0};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      s += N[k] * X[k][d];
+      t1[d] += d1[k] * X[k][d];
+      t2[d] += d2[k] * X[k][d];
+    }
+    x[d] = s;
+  }
+  const double n0 = t1[1] * t2[2] - t1[2] * t2[1];
+  const double n1 = t1[2] * t2[0] - t1[0] * t2[2];
+  const double n2 = t1[0] * t2[1] - t1[1] * t2[0];
+  gamma = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+}
+
+// The 7-point rule on curved triangles: nodes Phi(lambda_q), weights
+// w_q gamma(lambda_q) / 2 (the flat case: w_q |T|); area2 receives twice the
+// rule's area of the triangle.
+__global__ void k_tri_geom_curved(int nt, const double* __restrict__ vert, const int* __restrict__ tri,
+                                  const double* __restrict__ mid, Rules rules, P4* __restrict__ tq,
+                                  double* __restrict__ area2) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double X[6][3];
+  for (int a = 0; a < 3; ++a)
+    for (int d = 0; d < 3; ++d) {
+      X[a][d] = vert[3 * tri[3 * t + a] + d];
+      X[3 + a][d] = mid[9 * (int64_t)t + 3 * a + d];
+    }
+  double area = 0.0;
+  for (int q = 0; q < 7; ++q) {
+    double x[3], g;
+    curved_eval(X, rules.bary[q][0], rules.bary[q][1], rules.bary[q][2], x, g);
+    const double w = rules.w7[q] * g * 0.5;
+    tq[7 * t + q] = P4{x[0], x[1], x[2], w};
+    area += w;
+  }
+  area2[t] = 2.0 * area;
+}
+
+// one warp per cluster: min / max over the six nodes of the curved triangles
+// in the supports of the cluster's vertices
+__global__ void k_p1c_boxes(int nc, const int* __restrict__ begin, const int* __restrict__ end,
+                            const int* __restrict__ perm, const int* __restrict__ sup_ptr,
+                            const int* __restrict__ sup_item, const int* __restrict__ tri,
+                            const double* __restrict__ vert, const double* __restrict__ mid,
+                            double* __restrict__ box) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nc) return;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = begin[warp] + lane; i < end[warp]; i += 32) {
+    const int v = perm[i];
+    for (int e = sup_ptr[v]; e < sup_ptr[v + 1]; ++e) {
+      const int t = sup_item[e] >> 2;
+      for (int a = 0; a < 6; ++a)
+        for (int d = 0; d < 3; ++d) {
+          const double x = a < 3 ? vert[3 * tri[3 * t + a] + d] : mid[9 * (int64_t)t + 3 * (a - 3) + d];
+          lo[d] = fmin(lo[d], x);
+          hi[d] = fmax(hi[d], x);
+        }
+    }
+  }
+  for (int off = 16; off; off >>= 1)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fmin(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], off));
+      hi[d] = fmax(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], off));
+    }
+  if (lane == 0)
+    for (int d = 0; d < 3; ++d) {
+      box[6 * warp + d] = lo[d];
+      box[6 * warp + 3 + d] = hi[d];
+    }
+}
+
+// A sample of the curved Sauter-Schwab rule: the reference coordinates of
+// both points (u = xi u^(eta), v = xi v^(eta)) and the weight (Gauss weights
+// of all four variables times xi^3 and the piece's eta-Jacobian); the map is
+// not affine, so xi is sampled like eta.
+struct __align__(16) SSEntryCurved {
+  double u1, u2, v1, v2;
+  double w;
+  double pad;
+};
+
+template <int CASE>
+void sauter_table_curved(const Rules& rules, std::vector<SSEntryCurved>& out) {
+  const int q = rules.q, q3 = q * q * q;
+  constexpr int pieces = CASE == 3 ? 6 : (CASE == 2 ? 5 : 2);
+  for (int s = 0; s < pieces * q3; ++s) {
+    const int piece = s / q3, r = s % q3;
+    const int a = r / (q * q), b = (r / q) % q, c = r % q;
+    long double u1, u2, v1, v2;
+    const long double wj = sauter_piece<CASE, long double>(piece, rules.ss_t[a], rules.ss_t[b], rules.ss_t[c],
+                                                           u1, u2, v1, v2);
+    for (int x = 0; x < q; ++x) {
+      const long double xi = rules.ss_t[x];
+      SSEntryCurved e{};
+      e.u1 = (double)(xi * u1);
+      e.u2 = (double)(xi * u2);
+      e.v1 = (double)(xi * v1);
+      e.v2 = (double)(xi * v2);
+      e.w = (double)((long double)rules.ss_w[x] * rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * xi * xi * xi * wj);
+      out.push_back(e);
+    }
+  }
+}
+
+// One warp per ordered touching pair of curved triangles, in float64: the
+// vertex orders of the flat rules (the stored midpoints follow their edges),
+// Phi and gamma of both triangles at every sample, and the sums of
+// f lambda_a(u) lambda_b(v) with f = w gamma_t gamma_s / |Phi_t - Phi_s|.
+__global__ void __launch_bounds__(256)
+k_p1c_singular(const P1Item* __restrict__ items, const unsigned long long* __restrict__ counts, int64_t cap,
+               const int* __restrict__ tri, const double* __restrict__ vert, const double* __restrict__ mid,
+               const SSEntryCurved* __restrict__ table, int3 toff, int3 tcnt, double* __restrict__ out) {
+  const int64_t wi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t count = min((long long)counts[4], (long long)cap);
+  if (wi >= count) return;
+  const P1Item it = items[wi];
+  int ti[3], tj[3];
+  for (int a = 0; a < 3; ++a) {
+    ti[a] = tri[3 * it.ti + a];
+    tj[a] = tri[3 * it.tj + a];
+  }
+  int ci[3], cj[3];
+  const int cs = it.cs;
+  if (cs == 3) {
+    for (int a = 0; a < 3; ++a) {
+      ci[a] = a;
+      for (int b = 0; b < 3; ++b)
+        if (tj[b] == ti[a]) cj[a] = b;
+    }
+  } else if (cs == 2) {
+    int sh[2], ns = 0, oi = -1, oj = -1;
+    for (int a = 0; a < 3; ++a) {
+      const bool in_j = ti[a] == tj[0] || ti[a] == tj[1] || ti[a] == tj[2];
+      if (in_j) sh[ns++] = ti[a]; else oi = ti[a];
+    }
+    for (int a = 0; a < 3; ++a)
+      if (tj[a] != sh[0] && tj[a] != sh[1]) oj = tj[a];
+    const int P[3] = {sh[0], sh[1], oi}, Q[3] = {sh[0], sh[1], oj};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        if (ti[b] == P[a]) ci[a] = b;
+        if (tj[b] == Q[a]) cj[a] = b;
+      }
+  } else {
+    int pi = 0, pj = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (ti[a] == tj[b]) { pi = a; pj = b; }
+    for (int a = 0; a < 3; ++a) {
+      ci[a] = (pi + a) % 3;
+      cj[a] = (pj + a) % 3;
+    }
+  }
+  // ordered nodes: vertices, then the edge points of the ordered edges
+  // (0, 1), (1, 2), (2, 0); stored slot of edge {a, b}: 0 for {0, 1}, 1 for
+  // {1, 2}, 2 for {0, 2}
+  auto slot = [](int a, int b) { return a + b == 1 ? 0 : (a + b == 3 ? 1 : 2); };
+  double XP[6][3], XQ[6][3];
+  for (int a = 0; a < 3; ++a) {
+    const int e = slot(ci[a], ci[(a + 1) % 3]), f = slot(cj[a], cj[(a + 1) % 3]);
+    for (int d = 0; d < 3; ++d) {
+      XP[a][d] = vert[3 * ti[ci[a]] + d];
+      XQ[a][d] = vert[3 * tj[cj[a]] + d];
+      XP[3 + a][d] = mid[9 * (int64_t)it.ti + 3 * e + d];
+      XQ[3 + a][d] = mid[9 * (int64_t)it.tj + 3 * f + d];
+    }
+  }
+  const int t0 = cs == 1 ? toff.x : (cs == 2 ? toff.y : toff.z);
+  const int tn = cs == 1 ? tcnt.x : (cs == 2 ? tcnt.y : tcnt.z);
+  double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int s = lane; s < tn; s += 32) {
+    const SSEntryCurved e = table[t0 + s];
+    const double lu[3] = {1.0 - e.u1, e.u1 - e.u2, e.u2};
+    const double lv[3] = {1.0 - e.v1, e.v1 - e.v2, e.v2};
+    double x[3], y[3], gx, gy;
+    curved_eval(XP, lu[0], lu[1], lu[2], x, gx);
+    curved_eval(XQ, lv[0], lv[1], lv[2], y, gy);
+    const double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+    const double f = e.w * gx * gy * rsqrt(dx * dx + dy * dy + dz * dz);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc[a][b] += f * lu[a] * lv[b];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      for (int o = 16; o; o >>= 1) acc[a][b] += __shfl_xor_sync(0xffffffffu, acc[a][b], o);
+  if (lane != 0) return;
+  double M[3][3];  // stored corners
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) M[ci[a]][cj[b]] = acc[a][b] * kInv4Pi;
+  p1_scatter(out, it.base, it.ld, it.base2, it.ld2, it.lr, it.lc, M);
+}

@@ -316,3 +316,26 @@ def test_host_io_matches_device_io(gpu_1280, h2_1280, prec):
     torch.cuda.synchronize()
     assert rel_cols(yt.double().numpy(), h.matvec(xd, prec, transpose=True).cpu().double().numpy()) <= \
         (1e-13 if prec == "f64" else 1e-6)
+
+
+def test_float64_entries(lib, gpu_1280, h2_1280, sphere1280, small_params):
+    """GCA_F64_ENTRIES: couplings, near field and Sauter-Schwab samples in
+    float64 (the paper's precision) instead of float-pair arithmetic.  The
+    bases are the same (the entries do not enter the cross approximation);
+    the float64 entries match the oracle to 1e-12 of the largest entry and
+    the float-pair ones to 1e-12 of each other's."""
+    v, t = sphere1280
+    h, d, tree = gpu_1280
+    p = small_params
+    h64 = lib.build(v, t, tree, lib.Params(leaf_size=p.leaf_size, eta=p.eta, box_gauss_m=p.box_gauss_m,
+                                           aca_tol=p.aca_tol, sauter_q=p.sauter_q, flags=lib.F64_ENTRIES))
+    d64 = h64.export()
+    for k in ("rank", "pivots", "far", "near", "V", "E"):
+        assert np.array_equal(d64[k], d[k]), k
+    compare_coefficients(h2_1280, d64, tree, 1e-12, tol_basis=TOL64)
+    for k in ("S", "N"):
+        assert np.abs(d64[k] - d[k]).max() <= 1e-12 * np.abs(d64[k]).max(), k
+    st, st64 = h.stats(), h64.stats()
+    assert st["n_singular"] == st64["n_singular"]
+    x = torch.from_numpy(synth.normal_rhs(len(t), 3, seed=5)).cuda()
+    assert rel_cols(h64.matvec(x, "f64").cpu().numpy(), oh2.matvec(h2_1280, x.cpu().numpy())).max() <= 1e-10
