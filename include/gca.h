@@ -130,8 +130,10 @@ enum {
                           rejected (the float32 near field stays while
                           GCA_BF16 products are kept)                      */
   GCA_DROP_BF16 = 4,   /* no bfloat16 panels: GCA_BF16 products rejected    */
-  GCA_DROP_EXPORT = 8, /* free the row-major float64 V, E, S, N after the
-                          build: gca_h2_export of them is rejected          */
+  GCA_DROP_EXPORT = 8, /* gca_h2_export of V, E, S, N is rejected (a handle
+                          keeps no row-major float64 copy of them unless it
+                          has no float64 panels, GCA_DROP_F64: export
+                          rebuilds them from the float64 panels)           */
   GCA_F64_ENTRIES = 16 /* single layer (gca_build, gca_build_batch,
                           gca_build_single_level, gca_build_green_quadrature):
                           coupling and near-field entries and the
@@ -566,6 +568,11 @@ int gca_h2_import(const gca_tree* tree, int32_t nt, int32_t nfar, int32_t nnear,
                   uint32_t flags, void* stream, gca_h2** out);
 
 int gca_h2_stats(const gca_h2* h, gca_stats* out);
+/* Host copy of a handle in the layout of gca_host_dump.  V, E, S and N are
+ * rebuilt from the float64 panels (a handle keeps no second, row-major copy
+ * of them unless it was built with GCA_DROP_F64); this allocates a device
+ * buffer of the largest requested array for the call.  Synchronises the
+ * device.  Errors: UNSUPPORTED (GCA_DROP_EXPORT), OOM, CUDA. */
 int gca_h2_export(const gca_h2* h, gca_host_dump* out);
 void gca_free(gca_h2* h);
 const char* gca_strerror(int status);

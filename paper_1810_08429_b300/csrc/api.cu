@@ -216,10 +216,15 @@ int gca_h2_export_columns(const gca_h2* h, gca_host_dump* o) {
     gca::set_error("gca_h2_export_columns: the handle was built with GCA_DROP_EXPORT");
     return GCA_ERR_UNSUPPORTED;
   }
-  struct Item { double* dst; const gca::DevMem* src; int64_t n; };
-  const Item items[2] = {{o->V, &h->W64, h->w_entries}, {o->E, &h->F64, h->f_entries}};
+  struct Item { double* dst; const gca::DevMem* src; int64_t n; int kind; };
+  const Item items[2] = {{o->V, &h->W64, h->w_entries, gca::kW}, {o->E, &h->F64, h->f_entries, gca::kF}};
   for (const auto& it : items)
     if (it.dst && it.n > 0) {
+      if (!it.src->p) {
+        const int st = gca::export_from_panels(h, it.kind, it.dst, it.n);
+        if (st != GCA_OK) return st;
+        continue;
+      }
       cudaError_t e = cudaMemcpy(it.dst, it.src->p, sizeof(double) * it.n, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) {
         gca::set_error(std::string("gca_h2_export_columns: ") + cudaGetErrorString(e));
@@ -312,11 +317,17 @@ int gca_h2_export(const gca_h2* h, gca_host_dump* o) {
     gca::set_error("gca_h2_export: the handle was built with GCA_DROP_EXPORT");
     return GCA_ERR_UNSUPPORTED;
   }
-  struct Item { double* dst; const gca::DevMem* src; int64_t n; };
-  const Item items[4] = {{o->V, &h->V64, h->v_entries}, {o->E, &h->E64, h->e_entries},
-                         {o->S, &h->S64, h->s_entries}, {o->N, &h->N64, h->n_entries}};
+  // the row-major copy where the handle keeps one, else the float64 panels
+  struct Item { double* dst; const gca::DevMem* src; int64_t n; int kind; };
+  const Item items[4] = {{o->V, &h->V64, h->v_entries, gca::kV}, {o->E, &h->E64, h->e_entries, gca::kE},
+                         {o->S, &h->S64, h->s_entries, gca::kS}, {o->N, &h->N64, h->n_entries, gca::kN}};
   for (const auto& it : items)
     if (it.dst && it.n > 0) {
+      if (!it.src->p) {
+        const int st = gca::export_from_panels(h, it.kind, it.dst, it.n);
+        if (st != GCA_OK) return st;
+        continue;
+      }
       cudaError_t e = cudaMemcpy(it.dst, it.src->p, sizeof(double) * it.n, cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) {
         gca::set_error(std::string("gca_h2_export: ") + cudaGetErrorString(e));

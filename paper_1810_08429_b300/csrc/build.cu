@@ -839,6 +839,21 @@ __global__ void k_to_panel(const PanelJob* __restrict__ jobs, const double* __re
   }
 }
 
+// Row-major float64 blocks back from the float64 panels (the inverse of
+// k_to_panel on an untransposed kind, panels of P = 2): one CTA per block.
+__global__ void k_from_panel(const PanelJob* __restrict__ jobs, const double* __restrict__ p64,
+                             double* __restrict__ dst) {
+  const PanelJob j = jobs[blockIdx.x];
+  const int kp = pad8(j.k);
+  const int total = j.m * kp;
+  for (int d = threadIdx.x; d < total; d += blockDim.x) {
+    const TilePos t = tile_pos(j.m, kp, d);
+    int a, kk;
+    tile_entry(t, 1, a, kk);
+    if (kk < j.k) dst[j.dst + (int64_t)a * j.k + kk] = p64[j.src + d];
+  }
+}
+
 // Every stored block in panel form: f(kind, index, rows, columns, transposed)
 // for V, V^T, E, E^T, S, S^T, N, N^T (index PanelKind), in storage order.
 template <typename F>
@@ -974,6 +989,38 @@ int make_panels(gca_h2* h, DevMem& jobs_buf, std::vector<PanelJob>& host_jobs, c
         k32 ? h->P32[q].as<float>() : nullptr, k16 ? h->P16[q].as<__nv_bfloat16>() : nullptr);
     GCA_TRY_CUDA(cudaGetLastError());
   }
+  return GCA_OK;
+}
+
+// The row-major float64 coefficients of panel kind q (kV, kE, kS, kN, kW or
+// kF) in the export layout, rebuilt from the float64 panels into the host
+// array `host` of n doubles.  Synchronous; allocates a device buffer of n
+// doubles for the call.
+int export_from_panels(const gca_h2* h, int q, double* host, int64_t n) {
+  if (n <= 0) return GCA_OK;
+  if (!h->P64[q].p) {
+    set_error("gca_h2_export: no float64 panels and no row-major copy (GCA_DROP_F64)");
+    return GCA_ERR_UNSUPPORTED;
+  }
+  std::vector<PanelJob> jobs;
+  for_each_panel(h, [&](int kind, int idx, int m, int k, int) {
+    if (kind != q || (int64_t)m * k == 0) return;
+    const int64_t off = q == kV ? h->voff[idx]
+                        : q == kE ? h->eoff[idx]
+                        : q == kS ? h->soff[idx]
+                        : q == kN ? h->noff[idx]
+                        : q == kW ? h->voff2[idx]
+                                  : h->eoff2[idx];
+    jobs.push_back(PanelJob{h->panel_off[q][idx], off, m, k, 0, 0});
+  });
+  DevMem d_jobs, d_out;
+  GCA_TRY(upload(d_jobs, jobs, 0));
+  GCA_TRY(d_out.alloc(sizeof(double) * (size_t)n));
+  if (!jobs.empty()) {
+    k_from_panel<<<(unsigned)jobs.size(), 256>>>(d_jobs.as<PanelJob>(), h->P64[q].as<double>(), d_out.as<double>());
+    GCA_TRY_CUDA(cudaGetLastError());
+  }
+  GCA_TRY_CUDA(cudaMemcpy(host, d_out.p, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost));
   return GCA_OK;
 }
 
@@ -2905,7 +2952,10 @@ int Builder::finish(gca_h2** out) {
 
   GCA_TRY(finish_plan(h.get(), plan.get(), st));
   GCA_TRY_CUDA(cudaStreamSynchronize(st));
-  if (prm->flags & GCA_DROP_EXPORT) {
+  // the float64 panels hold the exported coefficients too (gca_h2_export
+  // rebuilds the row-major layout from them), so the row-major copies stay
+  // only where there are no float64 panels
+  if ((prm->flags & GCA_DROP_EXPORT) || !(prm->flags & GCA_DROP_F64)) {
     h->V64.release();
     h->E64.release();
     h->S64.release();

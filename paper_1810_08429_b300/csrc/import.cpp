@@ -159,7 +159,8 @@ int import_h2(const gca_tree* tree, int32_t nt, int32_t nfar, int32_t nnear, con
   PlanHandle plan = plan_new();
   GCA_TRY(finish_plan(h.get(), plan.get(), st));
   GCA_TRY_CUDA(cudaStreamSynchronize(st));
-  if (flags & GCA_DROP_EXPORT) {
+  // as gca_build: the float64 panels serve gca_h2_export when they exist
+  if ((flags & GCA_DROP_EXPORT) || !(flags & GCA_DROP_F64)) {
     h->V64.release();
     h->E64.release();
     h->S64.release();

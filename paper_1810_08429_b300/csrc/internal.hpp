@@ -161,6 +161,9 @@ int64_t panel_jobs(const gca_h2* h);
 struct PanelJob;
 int make_panels(gca_h2* h, DevMem& jobs_buf, std::vector<PanelJob>& host_jobs, cudaStream_t st);
 int make_panels_sync(gca_h2* h, cudaStream_t st);
+// gca_h2_export of panel kind q (kV, kE, kS, kN, kW, kF) from the float64
+// panels into a host array of n doubles, in the export layout (build.cu)
+int export_from_panels(const gca_h2* h, int q, double* host, int64_t n);
 // gca_h2_import (import.cpp)
 int import_h2(const gca_tree* tree, int32_t nt, int32_t nfar, int32_t nnear, const gca_host_dump* d,
               uint32_t flags, cudaStream_t st, gca_h2** out);

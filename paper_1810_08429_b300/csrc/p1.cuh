@@ -815,8 +815,9 @@ void sauter_table_curved(const Rules& rules, std::vector<SSEntryCurved>& out) {
 
 // One warp per ordered touching pair of curved triangles, in float64: the
 // vertex orders of the flat rules (the stored midpoints follow their edges),
-// Phi and gamma of both triangles at every sample, and the sums of
-// f lambda_a(u) lambda_b(v) with f = w gamma_t gamma_s / |Phi_t - Phi_s|.
+// x - y and the Gramians of both triangles at every sample from the maps'
+// monomial coefficients, and the sums of f lambda_a(u) lambda_b(v) with
+// f = w gamma_t gamma_s / |Phi_t - Phi_s|.
 __global__ void __launch_bounds__(256)
 k_p1c_singular(const P1Item* __restrict__ items, const unsigned long long* __restrict__ counts, int64_t cap,
                const int* __restrict__ tri, const double* __restrict__ vert, const double* __restrict__ mid,
@@ -877,18 +878,57 @@ k_p1c_singular(const P1Item* __restrict__ items, const unsigned long long* __res
       XQ[3 + a][d] = mid[9 * (int64_t)it.tj + 3 * f + d];
     }
   }
+  // The map in the reference coordinates u (lambda = (1 - u1, u1 - u2, u2)):
+  //   Phi(u) = X0 + B1 u1 + B2 u2 + C11 u1^2 + C12 u1 u2 + C22 u2^2,
+  //   B1 = 4 M01 - 3 X0 - X1,         B2 = X1 - X2 - 4 M01 + 4 M20,
+  //   C11 = 2 X0 + 2 X1 - 4 M01,      C12 = 4 (M01 + M12 - M20 - X1),
+  //   C22 = 2 X1 + 2 X2 - 4 M12.
+  // Both triangles start at the shared vertex (X0 of P is X0 of Q), so
+  // x - y is formed from the u- and v-terms alone; d Phi/du1 x d Phi/du2 has
+  // the Gramian's length (x^ = (u1 - u2, u2) has Jacobian 1).
+  double KP[5][3], KQ[5][3];
+  for (int d = 0; d < 3; ++d) {
+    KP[0][d] = 4.0 * XP[3][d] - 3.0 * XP[0][d] - XP[1][d];
+    KP[1][d] = XP[1][d] - XP[2][d] - 4.0 * XP[3][d] + 4.0 * XP[5][d];
+    KP[2][d] = 2.0 * XP[0][d] + 2.0 * XP[1][d] - 4.0 * XP[3][d];
+    KP[3][d] = 4.0 * (XP[3][d] + XP[4][d] - XP[5][d] - XP[1][d]);
+    KP[4][d] = 2.0 * XP[1][d] + 2.0 * XP[2][d] - 4.0 * XP[4][d];
+    KQ[0][d] = 4.0 * XQ[3][d] - 3.0 * XQ[0][d] - XQ[1][d];
+    KQ[1][d] = XQ[1][d] - XQ[2][d] - 4.0 * XQ[3][d] + 4.0 * XQ[5][d];
+    KQ[2][d] = 2.0 * XQ[0][d] + 2.0 * XQ[1][d] - 4.0 * XQ[3][d];
+    KQ[3][d] = 4.0 * (XQ[3][d] + XQ[4][d] - XQ[5][d] - XQ[1][d]);
+    KQ[4][d] = 2.0 * XQ[1][d] + 2.0 * XQ[2][d] - 4.0 * XQ[4][d];
+  }
+  auto gram = [](const double (*K)[3], double u1, double u2) {
+    double t1[3], t2[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      t1[d] = K[0][d] + 2.0 * K[2][d] * u1 + K[3][d] * u2;
+      t2[d] = K[1][d] + K[3][d] * u1 + 2.0 * K[4][d] * u2;
+    }
+    const double n0 = t1[1] * t2[2] - t1[2] * t2[1];
+    const double n1 = t1[2] * t2[0] - t1[0] * t2[2];
+    const double n2 = t1[0] * t2[1] - t1[1] * t2[0];
+    return sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+  };
   const int t0 = cs == 1 ? toff.x : (cs == 2 ? toff.y : toff.z);
   const int tn = cs == 1 ? tcnt.x : (cs == 2 ? tcnt.y : tcnt.z);
   double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   for (int s = lane; s < tn; s += 32) {
     const SSEntryCurved e = table[t0 + s];
+    const double mu[5] = {e.u1, e.u2, e.u1 * e.u1, e.u1 * e.u2, e.u2 * e.u2};
+    const double mv[5] = {e.v1, e.v2, e.v1 * e.v1, e.v1 * e.v2, e.v2 * e.v2};
+    double r2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double dd = 0.0;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) dd += KP[k][d] * mu[k] - KQ[k][d] * mv[k];
+      r2 += dd * dd;
+    }
+    const double f = e.w * gram(KP, e.u1, e.u2) * gram(KQ, e.v1, e.v2) * rsqrt(r2);
     const double lu[3] = {1.0 - e.u1, e.u1 - e.u2, e.u2};
     const double lv[3] = {1.0 - e.v1, e.v1 - e.v2, e.v2};
-    double x[3], y[3], gx, gy;
-    curved_eval(XP, lu[0], lu[1], lu[2], x, gx);
-    curved_eval(XQ, lv[0], lv[1], lv[2], y, gy);
-    const double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
-    const double f = e.w * gx * gy * rsqrt(dx * dx + dy * dy + dz * dz);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
