@@ -352,6 +352,20 @@ def run_profile(args):
 
     import paper_1810_08429_b300 as gca
     prm = gca.Params(**PARAMS)
+    if args.profile in ("p1", "p1c"):
+        # the nodal basis on the 20480-triangle sphere (flat or curved triangles)
+        v, t = synth.mesh_for_config(MESHES[0])
+        tree = gca.tree_build_points(v, PARAMS["leaf_size"])
+        mids = synth.edge_midpoints_for_config(MESHES[0])
+        for _ in range(max(args.steps, 1)):
+            if args.profile == "p1":
+                h = gca.build_p1(v, t, tree, gca.Params(**PARAMS, flags=gca.DROP_EXPORT))
+            else:
+                h = gca.build_p1_curved(v, t, mids, tree, gca.Params(**PARAMS, flags=gca.DROP_EXPORT))
+            h.free()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": args.profile, "n": len(v)}), flush=True)
+        return
     if args.profile == "build2":
         # the bench's two meshes as one batch (their cross approximations share
         # the level launches)
@@ -664,7 +678,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-leg", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--profile", choices=["f64", "f32", "bf16", "build", "build2"], default=None,
+    ap.add_argument("--profile", choices=["f64", "f32", "bf16", "build", "build2", "p1", "p1c"], default=None,
                     help="run the small single-mesh case used for kernel captures")
     args = ap.parse_args()
     if args.oracle_leg:

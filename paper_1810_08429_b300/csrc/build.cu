@@ -1959,15 +1959,21 @@ class AcaLauncher {
     std::vector<AcaJob> host;  // grouped copy, uploaded at once
     for (int g = 0; g < 5; ++g) host.insert(host.end(), by_c[g].begin(), by_c[g].end());
     GCA_TRY_CUDA(cudaMemcpyAsync(d_jobs.p, host.data(), sizeof(AcaJob) * host.size(), cudaMemcpyHostToDevice, st));
-    // the groups of one level are independent: with more than one, each runs
-    // on a side stream forked from and joined back into `st`
+    // the groups of one level are independent: each runs on a side stream
+    // forked from and joined back into `st`
     int ngroups = 0;
     for (int g = 0; g < 5; ++g) ngroups += !by_c[g].empty();
-    const bool fork = ngroups > 1;
+    // The side streams have the device's highest priority, so that the
+    // level's CTAs take the SMs ahead of the near field's (which runs on a
+    // lowest-priority stream beside the levels and fills the SMs they leave
+    // idle); every level runs on them.
+    const bool fork = true;
     if (fork) {
+      int least = 0, greatest = 0;
+      GCA_TRY_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
       for (int i = 0; i < 5; ++i)
         if (!side_[i]) {
-          GCA_TRY_CUDA(cudaStreamCreateWithFlags(&side_[i], cudaStreamNonBlocking));
+          GCA_TRY_CUDA(cudaStreamCreateWithPriority(&side_[i], cudaStreamNonBlocking, greatest));
           GCA_TRY_CUDA(cudaEventCreateWithFlags(&join_[i], cudaEventDisableTiming));
         }
       if (!fork_) GCA_TRY_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
@@ -2110,9 +2116,30 @@ class Builder {
   Builder(const gca_mesh* mesh_, const gca_tree* tree_, const gca_params* prm_, cudaStream_t st_, int op_,
           const double* midpoints_ = nullptr)
       : mesh(mesh_), tree(tree_), prm(prm_), st(st_), op(op_), midpoints(midpoints_) {}
+  ~Builder() {
+    if (near_st_) {
+      cudaStreamSynchronize(near_st_);
+      cudaStreamDestroy(near_st_);
+    }
+    if (near_ready_) cudaEventDestroy(near_ready_);
+    if (near_done_) cudaEventDestroy(near_done_);
+  }
+  Builder(const Builder&) = delete;
+  Builder& operator=(const Builder&) = delete;
   int prepare();
+  int near_field();
   int rows();
   int finish(gca_h2** out);
+  // the barycentric coordinates of the 7-point rule as float pairs
+  BarySplit bary_split() const {
+    BarySplit bs{};
+    for (int i = 0; i < 7; ++i)
+      for (int a = 0; a < 3; ++a) {
+        bs.h[i][a] = (float)rules.bary[i][a];
+        bs.l[i][a] = (float)(rules.bary[i][a] - (double)bs.h[i][a]);
+      }
+    return bs;
+  }
   // the pass of the row bases (the single layer's, op 0, 1, 3; the
   // collocation rows, op 2; the nodal rows, op 5)
   std::unique_ptr<BasisPass> rows_pass() {
@@ -2121,12 +2148,18 @@ class Builder {
                                                 &h->e_entries, &h->V64, &h->E64},
                                        d_piv, d_rank, piv_used);
   }
-  // a pass on this mesh alone: one launch per level
-  int run_pass(BasisPass& pass) {
+  // a pass on this mesh alone: one launch per level; `fork_near` launches the
+  // near field once the pass's pools are allocated (an allocation can wait
+  // for all work on the device, the side stream's included)
+  int run_pass(BasisPass& pass, bool fork_near = false) {
     GCA_TRY(pass.begin());
     DevMem d_mesh, d_jobs;
+    // room for every level's jobs at once: a reallocation between levels
+    // would free device memory and so wait for the near-field stream
+    GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * (size_t)nc));
     GCA_TRY(d_mesh.alloc(sizeof(AcaMesh)));
     GCA_TRY_CUDA(cudaMemcpyAsync(d_mesh.p, &pass.am, sizeof(AcaMesh), cudaMemcpyHostToDevice, st));
+    if (fork_near) GCA_TRY(near_field());
     std::vector<AcaJob> js;
     for (int L = h->depth; L >= 1; --L) {
       js.clear();
@@ -2162,6 +2195,15 @@ class Builder {
   double tie = std::ldexp(1.0, -40);
   DevMem d_piv, d_rank, d_piv2, d_rank2;
   int64_t piv_used = 0, piv2_used = 0;
+  // the near field (near_field()): touching-pair lists and their bound, the
+  // counts by case, its status word, the sample table, the nodal basis's
+  // near unions and blocks, and the side stream it runs on
+  std::vector<int64_t> valence;
+  int64_t cap = 0;
+  bool f64_entries = false;
+  DevMem d_items, d_counts, d_status_near, d_tab, d_nujobs, d_nucount, d_nurows, d_p1near;
+  cudaStream_t near_st_ = nullptr;
+  cudaEvent_t near_ready_ = nullptr, near_done_ = nullptr;
 };
 
 int Builder::prepare() {
@@ -2483,6 +2525,7 @@ int Builder::rows() {
   // the collocation rows (op 2), or the Green quadrature matrices A_tau of
   // the clusters of the blocks (op 4: "rank" 2k, no pivots)
   if (op == 4) {
+    GCA_TRY(near_field());
     h->rank.assign(nc, 0);
     h->voff.assign(nc, -1);
     h->eoff.assign(nc, -1);
@@ -2510,8 +2553,250 @@ int Builder::rows() {
     GCA_TRY(d_piv.alloc(sizeof(int)));
     GCA_TRY_CUDA(cudaStreamSynchronize(st));  // gj is a local
   } else {
-    GCA_TRY(run_pass(*rows_pass()));
+    GCA_TRY(run_pass(*rows_pass(), true));
   }
+  return GCA_OK;
+}
+
+// The near field (Sect. 8) needs the block tree and the quadrature nodes but
+// no basis.  Its entry and Sauter-Schwab kernels run on a side stream forked
+// from the build stream after the geometry, beside the cross approximation,
+// and finish() joins them back before the panels.  The touching-pair kernels
+// are launched for the bound `cap` of their lists (warps beyond the count
+// found on the device return at once), so no host read-back sits between
+// the entry kernels and them.
+int Builder::near_field() {
+  const int nnear = (int)h->near_t.size();
+  h->noff.assign(nnear + 1, 0);
+  for (int b = 0; b < nnear; ++b) {
+    const int t = h->near_t[b], s = h->near_s[b];
+    h->noff[b + 1] = h->noff[b] + (int64_t)(h->end[t] - h->begin[t]) * (h->end[s] - h->begin[s]);
+  }
+  h->n_entries = h->noff[nnear];
+  GCA_TRY(upload(h->d_near_t, h->near_t, st));
+  GCA_TRY(upload(h->d_near_s, h->near_s, st));
+  GCA_TRY(upload(h->d_noff, h->noff, st));
+  GCA_TRY(h->N64.alloc(sizeof(double) * h->n_entries));
+  // bound on touching ordered pairs: sum over vertices of (triangles at v)^2
+  valence.assign(mesh->nv, 0);
+  for (int64_t t = 0; t < 3LL * ntri; ++t) valence[tri[t]]++;
+  cap = 0;
+  for (auto v : valence) cap += v * v;
+  // the nodal basis: a touching pair occurs in the unions of at most three
+  // row and three column leaves
+  if (p1) cap *= 9;
+  GCA_TRY(d_items.alloc((p1 ? sizeof(P1Item) : sizeof(SingularItem) * 3) * (size_t)std::max<int64_t>(cap, 1)));
+  GCA_TRY(d_counts.alloc(sizeof(unsigned long long) * 5));
+  GCA_TRY(d_status_near.alloc(sizeof(int)));
+  f64_entries = (prm->flags & GCA_F64_ENTRIES) && (op == 0 || op == 3 || op == 4);
+  // sample tables: the single layer's (float pairs, or float64 with
+  // GCA_F64_ENTRIES), the double layer's (float64, vertex and edge), the
+  // nodal basis's (float pairs with the barycentric slopes; curved: float64
+  // with xi sampled); the collocation's Duffy rule (4q Gauss points on [0, 1])
+  std::vector<SSEntry> ss;
+  std::vector<SSEntry64> ss64;
+  std::vector<SSEntryP1> ssp1;
+  std::vector<SSEntryCurvedSplit> ssc;
+  std::vector<double2> duffy;
+  int ss_off[4] = {0, 0, 0, 0}, ss64_off[4] = {0, 0, 0, 0};
+  int3 t_off{0, 0, 0}, t_cnt{0, 0, 0};
+  if (p1 && curved) {
+    sauter_table_curved_split<1>(rules, ssc);
+    t_cnt.x = (int)ssc.size();
+    sauter_table_curved_split<2>(rules, ssc);
+    t_off.y = t_cnt.x;
+    t_cnt.y = (int)ssc.size() - t_off.y;
+    sauter_table_curved_split<3>(rules, ssc);
+    t_off.z = t_off.y + t_cnt.y;
+    t_cnt.z = (int)ssc.size() - t_off.z;
+    GCA_TRY(upload(d_tab, ssc, st));
+  } else if (p1) {
+    sauter_table_p1<1>(rules, ssp1);
+    t_cnt.x = (int)ssp1.size();
+    sauter_table_p1<2>(rules, ssp1);
+    t_off.y = t_cnt.x;
+    t_cnt.y = (int)ssp1.size() - t_off.y;
+    sauter_table_p1<3>(rules, ssp1);
+    t_off.z = t_off.y + t_cnt.y;
+    t_cnt.z = (int)ssp1.size() - t_off.z;
+    GCA_TRY(upload(d_tab, ssp1, st));
+  } else if (op == 1 || f64_entries) {
+    sauter_table64<1>(rules, ss64);
+    ss64_off[1] = (int)ss64.size();
+    sauter_table64<2>(rules, ss64);
+    ss64_off[2] = (int)ss64.size();
+    if (f64_entries) sauter_table64<3>(rules, ss64);
+    ss64_off[3] = (int)ss64.size();
+    GCA_TRY(upload(d_tab, ss64, st));
+  } else if (op == 2) {
+    const int nd = 4 * prm->sauter_q;
+    std::vector<double> xt(nd), wt(nd);
+    gauss_legendre(nd, xt.data(), wt.data());
+    for (int i = 0; i < nd; ++i) duffy.push_back(make_double2(0.5 * (xt[i] + 1.0), 0.5 * wt[i]));
+    GCA_TRY(upload(d_tab, duffy, st));
+  } else {
+    sauter_table<1>(rules, ss);
+    ss_off[1] = (int)ss.size();
+    sauter_table<2>(rules, ss);
+    ss_off[2] = (int)ss.size();
+    sauter_table<3>(rules, ss);
+    ss_off[3] = (int)ss.size();
+    GCA_TRY(upload(d_tab, ss, st));
+  }
+  // the nodal basis: the support unions of the near-field leaves and the
+  // near blocks, mirrored pairs together
+  std::vector<UnionJob> ujobs;
+  std::vector<P1Block> p1near;
+  int pcap = 1, max_len = 1;
+  if (p1) {
+    std::vector<int> uleaf(nc, -1);
+    int64_t rows_total = 0, max_m = 1;
+    for (int b = 0; b < nnear; ++b)
+      for (int c : {h->near_t[b], h->near_s[b]})
+        if (uleaf[c] < 0) {
+          int64_t m = 0;
+          for (int i = h->begin[c]; i < h->end[c]; ++i) m += valence[h->perm[i]];
+          ujobs.push_back(UnionJob{h->d_perm.as<int>() + h->begin[c], h->end[c] - h->begin[c], 0, rows_total});
+          uleaf[c] = (int)ujobs.size() - 1;
+          rows_total += m;
+          max_m = std::max(max_m, m);
+          max_len = std::max(max_len, h->end[c] - h->begin[c]);
+        }
+    while (pcap < max_m) pcap <<= 1;
+    if (pcap > kUnionMax) {
+      set_error("gca_build_p1: a support union has more than 16384 entries");
+      return GCA_ERR_UNSUPPORTED;
+    }
+    for (int b = 0; b < nnear; ++b) {
+      const int t = h->near_t[b], s = h->near_s[b];
+      int m = -1;
+      if (t != s) {
+        int lo = 0, hi = nnear;
+        while (lo < hi) {
+          const int mid = (lo + hi) / 2;
+          if (h->near_t[mid] < s || (h->near_t[mid] == s && h->near_s[mid] < t)) lo = mid + 1; else hi = mid;
+        }
+        if (lo < nnear && h->near_t[lo] == s && h->near_s[lo] == t) m = lo;
+      }
+      if (t > s && m >= 0) continue;  // computed with its mirror
+      const int nt_ = h->end[t] - h->begin[t], ns_ = h->end[s] - h->begin[s];
+      p1near.push_back(P1Block{h->noff[b], m >= 0 ? h->noff[m] : -1, ns_, nt_, uleaf[t], uleaf[s]});
+    }
+    GCA_TRY(upload(d_nujobs, ujobs, st));
+    GCA_TRY(d_nucount.alloc(sizeof(int) * std::max<size_t>(ujobs.size(), 1)));
+    GCA_TRY(d_nurows.alloc(sizeof(int4) * (size_t)std::max<int64_t>(rows_total, 1)));
+    GCA_TRY(upload(d_p1near, p1near, st));
+  }
+  // fork: the side stream waits for everything enqueued so far on the build
+  // stream (geometry, split nodes, the uploads above)
+  {
+    int least = 0, greatest = 0;
+    GCA_TRY_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    GCA_TRY_CUDA(cudaStreamCreateWithPriority(&near_st_, cudaStreamNonBlocking, least));
+  }
+  GCA_TRY_CUDA(cudaEventCreateWithFlags(&near_ready_, cudaEventDisableTiming));
+  GCA_TRY_CUDA(cudaEventCreateWithFlags(&near_done_, cudaEventDisableTiming));
+  GCA_TRY_CUDA(cudaEventRecord(near_ready_, st));
+  cudaStream_t ns = near_st_;
+  GCA_TRY_CUDA(cudaStreamWaitEvent(ns, near_ready_, 0));
+  GCA_TRY_CUDA(cudaMemsetAsync(d_counts.p, 0, sizeof(unsigned long long) * 5, ns));
+  GCA_TRY_CUDA(cudaMemsetAsync(d_status_near.p, 0, sizeof(int), ns));
+  const int* tri_d = h->d_tri.as<int>();
+  const double* vert_d = h->d_vert.as<double>();
+  const double* a2 = d_area2.as<double>();
+  double* N64 = h->N64.as<double>();
+  unsigned long long* cnt = d_counts.as<unsigned long long>();
+  int* nstat = d_status_near.as<int>();
+  const unsigned sing_blocks = blocks_for(32LL * std::max<int64_t>(cap, 1), 256);
+  if (nnear == 0) {
+    // nothing to integrate
+  } else if (p1) {
+    GCA_TRY_CUDA(cudaMemsetAsync(N64, 0, sizeof(double) * h->n_entries, ns));
+    if (!ujobs.empty()) {
+      const size_t smem = sizeof(unsigned long long) * (size_t)pcap + sizeof(int) * (size_t)(max_len + 1);
+      GCA_TRY_CUDA(cudaFuncSetAttribute(k_support_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      PhaseScope ps__("p1_union", ns);
+      k_support_union<<<(unsigned)ujobs.size(), 256, smem, ns>>>(d_nujobs.as<UnionJob>(), d_sup_ptr.as<int>(),
+                                                                d_sup_item.as<int>(), pcap, d_nurows.as<int4>(),
+                                                                d_nucount.as<int>(), nstat);
+      GCA_TRY_CUDA(cudaGetLastError());
+    }
+    if (!p1near.empty()) {
+      PhaseScope ps__("p1_near_entries", ns);
+      k_p1_entries<true><<<(unsigned)p1near.size(), 256, 0, ns>>>(
+          d_p1near.as<P1Block>(), d_nujobs.as<UnionJob>(), d_nucount.as<int>(), d_nurows.as<int4>(), tri_d,
+          d_tq.as<P4>(), d_tn.as<SplitNode>(), rules, bary_split(), near_r2, N64, d_items.as<P1Item>(), cap, cnt,
+          nstat);
+      GCA_TRY_CUDA(cudaGetLastError());
+    }
+    PhaseScope ps__("p1_singular", ns);
+    if (curved)
+      k_p1c_singular_split<<<sing_blocks, 256, 0, ns>>>(d_items.as<P1Item>(), cnt, cap, tri_d, vert_d,
+                                                         d_mid.as<double>(), d_tab.as<SSEntryCurvedSplit>(), t_off,
+                                                         t_cnt, N64);
+    else
+      k_p1_singular<<<sing_blocks, 256, 0, ns>>>(d_items.as<P1Item>(), cnt, cap, tri_d, vert_d, a2,
+                                                  d_tab.as<SSEntryP1>(), t_off, t_cnt, N64);
+    GCA_TRY_CUDA(cudaGetLastError());
+  } else if (op == 2) {
+    const size_t smem = sizeof(P4) * 7 * (size_t)h->max_leaf;
+    GCA_TRY_CUDA(cudaFuncSetAttribute(k_col_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PhaseScope ps__("col_near_entries", ns);
+    // the collocation's diagonal entries are integrated in place
+    k_col_near_entries<<<nnear, 256, smem, ns>>>(
+        h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
+        h->d_end.as<int>(), h->d_perm.as<int>(), tri_d, vert_d, d_tq.as<P4>(), d_tab.as<double2>(),
+        (int)duffy.size(), N64, cnt);
+    GCA_TRY_CUDA(cudaGetLastError());
+  } else {
+    const SingularItem* items = d_items.as<SingularItem>();
+    if (op == 1) {
+      const size_t smem = (sizeof(P4) * 7 + sizeof(double) * 3) * (size_t)h->max_leaf;
+      GCA_TRY_CUDA(cudaFuncSetAttribute(k_dl_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      PhaseScope ps__("dl_near_entries", ns);
+      k_dl_near_entries<<<nnear, 256, smem, ns>>>(
+          h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
+          h->d_end.as<int>(), h->d_perm.as<int>(), tri_d, d_tq.as<P4>(), d_nrm.as<double>(), N64,
+          d_items.as<SingularItem>(), cap, cnt, nstat);
+      GCA_TRY_CUDA(cudaGetLastError());
+    } else {
+      const size_t smem = (sizeof(P4) + sizeof(SplitNode)) * 7 * (size_t)h->max_leaf;
+      auto kern = f64_entries ? k_near_entries<true> : k_near_entries<false>;
+      GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      PhaseScope ps__("near_entries", ns);
+      kern<<<nnear, 256, smem, ns>>>(h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(),
+                                     h->d_begin.as<int>(), h->d_end.as<int>(), h->d_perm.as<int>(), tri_d,
+                                     d_tq.as<P4>(), d_tn.as<SplitNode>(), near_r2, N64, d_items.as<SingularItem>(),
+                                     cap, cnt, nstat);
+      GCA_TRY_CUDA(cudaGetLastError());
+    }
+    PhaseScope ps_sing("singular", ns);
+    ps_sing.launches(op == 1 ? 2 : 3);
+    if (op == 1) {
+      const SSEntry64* tab64 = d_tab.as<SSEntry64>();
+      k_dl_singular<1><<<sing_blocks, 256, 0, ns>>>(items, cnt, cap, tri_d, vert_d, a2, d_nrm.as<double>(), tab64,
+                                                     ss64_off[1], N64);
+      k_dl_singular<2><<<sing_blocks, 256, 0, ns>>>(items + cap, cnt, cap, tri_d, vert_d, a2, d_nrm.as<double>(),
+                                                     tab64 + ss64_off[1], ss64_off[2] - ss64_off[1], N64);
+    } else if (f64_entries) {
+      const SSEntry64* tab64 = d_tab.as<SSEntry64>();
+      k_singular64<1><<<sing_blocks, 256, 0, ns>>>(items, cnt, cap, tri_d, vert_d, a2, tab64, ss64_off[1], N64);
+      k_singular64<2><<<sing_blocks, 256, 0, ns>>>(items + cap, cnt, cap, tri_d, vert_d, a2, tab64 + ss64_off[1],
+                                                    ss64_off[2] - ss64_off[1], N64);
+      k_singular64<3><<<sing_blocks, 256, 0, ns>>>(items + 2 * cap, cnt, cap, tri_d, vert_d, a2, tab64 + ss64_off[2],
+                                                    ss64_off[3] - ss64_off[2], N64);
+    } else {
+      const SSEntry* tab = d_tab.as<SSEntry>();
+      k_singular<1><<<sing_blocks, 256, 0, ns>>>(items, cnt, cap, tri_d, vert_d, a2, tab, ss_off[1], N64);
+      k_singular<2><<<sing_blocks, 256, 0, ns>>>(items + cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[1],
+                                                  ss_off[2] - ss_off[1], N64);
+      k_singular<3><<<sing_blocks, 256, 0, ns>>>(items + 2 * cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[2],
+                                                  ss_off[3] - ss_off[2], N64);
+    }
+    GCA_TRY_CUDA(cudaGetLastError());
+  }
+  GCA_TRY_CUDA(cudaEventRecord(near_done_, ns));
+  // the host tables above are pageable and were copied when upload returned
   return GCA_OK;
 }
 
@@ -2586,70 +2871,11 @@ int Builder::finish(gca_h2** out) {
   }
   DevMem d_pairs;
   GCA_TRY(upload(d_pairs, pairs, st));
-  h->noff.assign(nnear + 1, 0);
-  for (int b = 0; b < nnear; ++b) {
-    const int t = h->near_t[b], s = h->near_s[b];
-    h->noff[b + 1] = h->noff[b] + (int64_t)(h->end[t] - h->begin[t]) * (h->end[s] - h->begin[s]);
-  }
-  h->n_entries = h->noff[nnear];
-  GCA_TRY(upload(h->d_near_t, h->near_t, st));
-  GCA_TRY(upload(h->d_near_s, h->near_s, st));
-  GCA_TRY(upload(h->d_noff, h->noff, st));
-  GCA_TRY(h->N64.alloc(sizeof(double) * h->n_entries));
-  // bound on touching ordered pairs: sum over vertices of (triangles at v)^2
-  std::vector<int64_t> valence(mesh->nv, 0);
-  for (int64_t t = 0; t < 3LL * ntri; ++t) valence[tri[t]]++;
-  int64_t cap = 0;
-  for (auto v : valence) cap += v * v;
-  DevMem d_items, d_counts;
-  // the nodal basis: a touching pair occurs in the unions of at most three
-  // row and three column leaves
-  if (p1) cap *= 9;
-  GCA_TRY(d_items.alloc((p1 ? sizeof(P1Item) : sizeof(SingularItem) * 3) * (size_t)cap));
-  // sample tables of the three Sauter-Schwab cases (vertex, edge, identical)
-  std::vector<SSEntry> ss;
-  int ss_off[4] = {0, 0, 0, 0};
-  sauter_table<1>(rules, ss);
-  ss_off[1] = (int)ss.size();
-  sauter_table<2>(rules, ss);
-  ss_off[2] = (int)ss.size();
-  sauter_table<3>(rules, ss);
-  ss_off[3] = (int)ss.size();
-  DevMem d_ss, d_ss64;
-  GCA_TRY(upload(d_ss, ss, st));
-  // the double layer's samples in float64 (vertex, edge)
-  // the double layer's samples in float64 (vertex, edge), or the single
-  // layer's (vertex, edge, identical) with GCA_F64_ENTRIES
-  const bool f64_entries = (prm->flags & GCA_F64_ENTRIES) && (op == 0 || op == 3 || op == 4);
-  std::vector<SSEntry64> ss64;
-  int ss64_off[4] = {0, 0, 0, 0};
-  if (op == 1 || f64_entries) {
-    sauter_table64<1>(rules, ss64);
-    ss64_off[1] = (int)ss64.size();
-    sauter_table64<2>(rules, ss64);
-    ss64_off[2] = (int)ss64.size();
-    if (f64_entries) sauter_table64<3>(rules, ss64);
-    ss64_off[3] = (int)ss64.size();
-    GCA_TRY(upload(d_ss64, ss64, st));
-  }
-  GCA_TRY(d_counts.alloc(sizeof(unsigned long long) * 10));
-  GCA_TRY_CUDA(cudaMemsetAsync(d_counts.p, 0, sizeof(unsigned long long) * 10, st));
-  // the nodal basis: entries are sums over triangle pairs
-  std::vector<SSEntryP1> ssp1;
-  int3 ssp1_off{0, 0, 0}, ssp1_cnt{0, 0, 0};
-  DevMem d_ssp1;
+  DevMem d_counts_far;  // the nodal basis's couplings: count of regular pairs
   if (p1) {
     GCA_TRY_CUDA(cudaMemsetAsync(h->S64.p, 0, sizeof(double) * h->s_entries, st));
-    GCA_TRY_CUDA(cudaMemsetAsync(h->N64.p, 0, sizeof(double) * h->n_entries, st));
-    sauter_table_p1<1>(rules, ssp1);
-    ssp1_cnt.x = (int)ssp1.size();
-    sauter_table_p1<2>(rules, ssp1);
-    ssp1_off.y = ssp1_cnt.x;
-    ssp1_cnt.y = (int)ssp1.size() - ssp1_off.y;
-    sauter_table_p1<3>(rules, ssp1);
-    ssp1_off.z = ssp1_off.y + ssp1_cnt.y;
-    ssp1_cnt.z = (int)ssp1.size() - ssp1_off.z;
-    GCA_TRY(upload(d_ssp1, ssp1, st));
+    GCA_TRY(d_counts_far.alloc(sizeof(unsigned long long) * 5));
+    GCA_TRY_CUDA(cudaMemsetAsync(d_counts_far.p, 0, sizeof(unsigned long long) * 5, st));
   }
   layout_panels(h.get());
   GCA_TRY(alloc_panels(h.get()));
@@ -2658,24 +2884,14 @@ int Builder::finish(gca_h2** out) {
   GCA_TRY_CUDA(cudaStreamSynchronize(st));  // the host copy of the pivots
 
   // coupling matrices
-  std::vector<double2> duffy;  // the collocation's Duffy rule: 4q Gauss points on [0, 1]
-  DevMem d_duffy;
-  if (op == 2) {
-    const int nd = 4 * prm->sauter_q;
-    std::vector<double> xt(nd), wt(nd);
-    gauss_legendre(nd, xt.data(), wt.data());
-    for (int i = 0; i < nd; ++i) duffy.push_back(make_double2(0.5 * (xt[i] + 1.0), 0.5 * wt[i]));
-    GCA_TRY(upload(d_duffy, duffy, st));
-  }
   // nodal basis (Sect. 5): support unions of the pivot lists of the
-  // clusters in admissible blocks and of the leaves in near blocks, then the
-  // pair-by-pair assembly of couplings and near field (mirrored blocks
-  // together)
+  // clusters in admissible blocks, then the pair-by-pair assembly of the
+  // couplings (mirrored blocks together; the near field runs in near_field())
   std::vector<UnionJob> ujobs;
-  std::vector<P1Block> p1far, p1near;
-  DevMem d_ujobs, d_ucount, d_urows, d_p1far, d_p1near;
+  std::vector<P1Block> p1far;
+  DevMem d_ujobs, d_ucount, d_urows, d_p1far;
   if (p1) {
-    std::vector<int> upiv(nc, -1), uleaf(nc, -1);
+    std::vector<int> upiv(nc, -1);
     int64_t rows_total = 0;
     int64_t max_m = 1;
     int max_len = 1;
@@ -2692,11 +2908,6 @@ int Builder::finish(gca_h2** out) {
       for (int c : {h->far_t[b], h->far_s[b]})
         if (upiv[c] < 0)
           upiv[c] = add_union(d_piv.as<int>() + h->poff[c], h->piv.data() + h->poff[c], h->rank[c]);
-    for (int b = 0; b < nnear; ++b)
-      for (int c : {h->near_t[b], h->near_s[b]})
-        if (uleaf[c] < 0)
-          uleaf[c] = add_union(h->d_perm.as<int>() + h->begin[c], h->perm.data() + h->begin[c],
-                               h->end[c] - h->begin[c]);
     int pcap = 1;
     while (pcap < max_m) pcap <<= 1;
     if (pcap > kUnionMax) {
@@ -2707,26 +2918,10 @@ int Builder::finish(gca_h2** out) {
       const int b = pr.x, m = pr.y, t = h->far_t[b], s = h->far_s[b];
       p1far.push_back(P1Block{h->soff[b], m >= 0 ? h->soff[m] : -1, h->rank[s], h->rank[t], upiv[t], upiv[s]});
     }
-    for (int b = 0; b < nnear; ++b) {
-      const int t = h->near_t[b], s = h->near_s[b];
-      int m = -1;
-      if (t != s) {
-        int lo = 0, hi = nnear;
-        while (lo < hi) {
-          const int mid = (lo + hi) / 2;
-          if (h->near_t[mid] < s || (h->near_t[mid] == s && h->near_s[mid] < t)) lo = mid + 1; else hi = mid;
-        }
-        if (lo < nnear && h->near_t[lo] == s && h->near_s[lo] == t) m = lo;
-      }
-      if (t > s && m >= 0) continue;  // computed with its mirror
-      const int nt_ = h->end[t] - h->begin[t], ns_ = h->end[s] - h->begin[s];
-      p1near.push_back(P1Block{h->noff[b], m >= 0 ? h->noff[m] : -1, ns_, nt_, uleaf[t], uleaf[s]});
-    }
     GCA_TRY(upload(d_ujobs, ujobs, st));
     GCA_TRY(d_ucount.alloc(sizeof(int) * std::max<size_t>(ujobs.size(), 1)));
     GCA_TRY(d_urows.alloc(sizeof(int4) * (size_t)std::max<int64_t>(rows_total, 1)));
     GCA_TRY(upload(d_p1far, p1far, st));
-    GCA_TRY(upload(d_p1near, p1near, st));
     if (!ujobs.empty()) {
       const size_t smem = sizeof(unsigned long long) * (size_t)pcap + sizeof(int) * (size_t)(max_len + 1);
       GCA_TRY_CUDA(cudaFuncSetAttribute(k_support_union, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -2736,26 +2931,12 @@ int Builder::finish(gca_h2** out) {
                                                                 d_ucount.as<int>(), d_status.as<int>());
       GCA_TRY_CUDA(cudaGetLastError());
     }
-    BarySplit bs{};
-    for (int i = 0; i < 7; ++i)
-      for (int a = 0; a < 3; ++a) {
-        bs.h[i][a] = (float)rules.bary[i][a];
-        bs.l[i][a] = (float)(rules.bary[i][a] - (double)bs.h[i][a]);
-      }
     if (!p1far.empty()) {
       PhaseScope ps__("p1_couple_entries", st);
       k_p1_entries<false><<<(unsigned)p1far.size(), 256, 0, st>>>(
           d_p1far.as<P1Block>(), d_ujobs.as<UnionJob>(), d_ucount.as<int>(), d_urows.as<int4>(),
-          h->d_tri.as<int>(), d_tq.as<P4>(), d_tn.as<SplitNode>(), rules, bs, near_r2, h->S64.as<double>(),
-          d_items.as<P1Item>(), cap, d_counts.as<unsigned long long>() + 5, d_status.as<int>());
-      GCA_TRY_CUDA(cudaGetLastError());
-    }
-    if (!p1near.empty()) {
-      PhaseScope ps__("p1_near_entries", st);
-      k_p1_entries<true><<<(unsigned)p1near.size(), 256, 0, st>>>(
-          d_p1near.as<P1Block>(), d_ujobs.as<UnionJob>(), d_ucount.as<int>(), d_urows.as<int4>(),
-          h->d_tri.as<int>(), d_tq.as<P4>(), d_tn.as<SplitNode>(), rules, bs, near_r2, h->N64.as<double>(),
-          d_items.as<P1Item>(), cap, d_counts.as<unsigned long long>(), d_status.as<int>());
+          h->d_tri.as<int>(), d_tq.as<P4>(), d_tn.as<SplitNode>(), rules, bary_split(), near_r2,
+          h->S64.as<double>(), nullptr, 0, d_counts_far.as<unsigned long long>(), d_status.as<int>());
       GCA_TRY_CUDA(cudaGetLastError());
     }
   } else if (nfar > 0 && op == 4) {
@@ -2807,138 +2988,21 @@ int Builder::finish(gca_h2** out) {
     GCA_TRY_CUDA(cudaGetLastError());
   }
 
-  // near field
-  if (p1) {
-    // launched with the couplings above
-  } else if (nnear > 0 && op == 2) {
-    const size_t smem = sizeof(P4) * 7 * (size_t)h->max_leaf;
-    GCA_TRY_CUDA(cudaFuncSetAttribute(k_col_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    {
-      PhaseScope ps__("col_near_entries", st);
-      k_col_near_entries<<<nnear, 256, smem, st>>>(
-          h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
-          h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), h->d_vert.as<double>(), d_tq.as<P4>(),
-          d_duffy.as<double2>(), (int)duffy.size(), h->N64.as<double>(), d_counts.as<unsigned long long>());
-    }
-    GCA_TRY_CUDA(cudaGetLastError());
-  } else if (nnear > 0 && op == 1) {
-    const size_t smem = (sizeof(P4) * 7 + sizeof(double) * 3) * (size_t)h->max_leaf;
-    GCA_TRY_CUDA(cudaFuncSetAttribute(k_dl_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    {
-      PhaseScope ps__("dl_near_entries", st);
-      k_dl_near_entries<<<nnear, 256, smem, st>>>(
-          h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
-          h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), d_tq.as<P4>(), d_nrm.as<double>(),
-          h->N64.as<double>(), d_items.as<SingularItem>(), cap, d_counts.as<unsigned long long>(),
-          d_status.as<int>());
-    }
-    GCA_TRY_CUDA(cudaGetLastError());
-  } else if (nnear > 0) {
-    const size_t smem = (sizeof(P4) + sizeof(SplitNode)) * 7 * (size_t)h->max_leaf;
-    auto kern = f64_entries ? k_near_entries<true> : k_near_entries<false>;
-    GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    {
-      PhaseScope ps__("near_entries", st);
-      kern<<<nnear, 256, smem, st>>>(
-          h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
-          h->d_end.as<int>(), h->d_perm.as<int>(), h->d_tri.as<int>(), d_tq.as<P4>(),
-          d_tn.as<SplitNode>(), near_r2, h->N64.as<double>(), d_items.as<SingularItem>(), cap,
-          d_counts.as<unsigned long long>(),
-          d_status.as<int>());
-    }
-    GCA_TRY_CUDA(cudaGetLastError());
-  }
   // the product plan needs only the ranks, the block lists and the panel
   // offsets: the host computes one direction while the coupling and
   // near-field kernels run, the other while the singular and panel kernels run
   PlanHandle plan = plan_new();
   plan_direction(h.get(), 0, plan.get());
-  if (p1) {
-    GCA_TRY(check_status(d_status, st, "near field"));
+  // the near field: joined back into the build stream; its sticky status and
+  // the counts of its pairs by case
+  if (near_st_) {
+    GCA_TRY_CUDA(cudaStreamWaitEvent(st, near_done_, 0));
+    GCA_TRY(check_status(d_status_near, st, "near field"));
     unsigned long long counts[5];
     GCA_TRY_CUDA(cudaMemcpyAsync(counts, d_counts.p, sizeof(counts), cudaMemcpyDeviceToHost, st));
     GCA_TRY_CUDA(cudaStreamSynchronize(st));
     for (int c = 0; c <= 3; ++c) h->n_singular[c] = (int64_t)counts[c];
-    if (counts[4] > 0 && curved) {
-      // the curved rule's samples (xi sampled too)
-      std::vector<SSEntryCurved> tab;
-      int3 off{0, 0, 0}, cnt{0, 0, 0};
-      sauter_table_curved<1>(rules, tab);
-      cnt.x = (int)tab.size();
-      sauter_table_curved<2>(rules, tab);
-      off.y = cnt.x;
-      cnt.y = (int)tab.size() - off.y;
-      sauter_table_curved<3>(rules, tab);
-      off.z = off.y + cnt.y;
-      cnt.z = (int)tab.size() - off.z;
-      DevMem d_tab;
-      GCA_TRY(upload(d_tab, tab, st));
-      {
-        PhaseScope ps_sing("p1_singular", st);
-        k_p1c_singular<<<blocks_for(32LL * (int64_t)counts[4], 256), 256, 0, st>>>(
-            d_items.as<P1Item>(), d_counts.as<unsigned long long>(), cap, h->d_tri.as<int>(),
-            h->d_vert.as<double>(), d_mid.as<double>(), d_tab.as<SSEntryCurved>(), off, cnt, h->N64.as<double>());
-        GCA_TRY_CUDA(cudaGetLastError());
-      }
-      GCA_TRY_CUDA(cudaStreamSynchronize(st));  // tab and d_tab are locals
-    } else if (counts[4] > 0) {
-      PhaseScope ps_sing("p1_singular", st);
-      k_p1_singular<<<blocks_for(32LL * (int64_t)counts[4], 256), 256, 0, st>>>(
-          d_items.as<P1Item>(), d_counts.as<unsigned long long>(), cap, h->d_tri.as<int>(),
-          h->d_vert.as<double>(), d_area2.as<double>(), d_ssp1.as<SSEntryP1>(), ssp1_off, ssp1_cnt,
-          h->N64.as<double>());
-      GCA_TRY_CUDA(cudaGetLastError());
-    }
-  } else if (nnear > 0) {
-    GCA_TRY(check_status(d_status, st, "near field"));
-    unsigned long long counts[4];
-    GCA_TRY_CUDA(cudaMemcpyAsync(counts, d_counts.p, sizeof(counts), cudaMemcpyDeviceToHost, st));
-    GCA_TRY_CUDA(cudaStreamSynchronize(st));
-    for (int c = 1; c <= 3; ++c) h->n_singular[c] = (int64_t)counts[c];
-    h->n_singular[0] = h->n_entries - (h->n_singular[1] + h->n_singular[2] + h->n_singular[3]);
-    const SingularItem* items = d_items.as<SingularItem>();
-    const unsigned long long* cnt = d_counts.as<unsigned long long>();
-    PhaseScope ps_sing("singular", st);
-    ps_sing.launches((counts[1] > 0) + (counts[2] > 0) + (counts[3] > 0));
-    const SSEntry* tab = d_ss.as<SSEntry>();
-    const int* tri_d = h->d_tri.as<int>();
-    const double* vert_d = h->d_vert.as<double>();
-    const double* a2 = d_area2.as<double>();
-    double* N64 = h->N64.as<double>();
-    if (op == 2) {
-      // the collocation's diagonal entries were integrated in place
-    } else if (op == 1) {
-      const SSEntry64* tab64 = d_ss64.as<SSEntry64>();
-      if (counts[1])
-        k_dl_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
-            items, cnt, cap, tri_d, vert_d, a2, d_nrm.as<double>(), tab64, ss64_off[1], N64);
-      if (counts[2])
-        k_dl_singular<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
-            items + cap, cnt, cap, tri_d, vert_d, a2, d_nrm.as<double>(), tab64 + ss64_off[1],
-            ss64_off[2] - ss64_off[1], N64);
-    } else if (f64_entries) {
-      const SSEntry64* tab64 = d_ss64.as<SSEntry64>();
-      if (counts[1])
-        k_singular64<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
-            items, cnt, cap, tri_d, vert_d, a2, tab64, ss64_off[1], N64);
-      if (counts[2])
-        k_singular64<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
-            items + cap, cnt, cap, tri_d, vert_d, a2, tab64 + ss64_off[1], ss64_off[2] - ss64_off[1], N64);
-      if (counts[3])
-        k_singular64<3><<<blocks_for(32LL * counts[3], 256), 256, 0, st>>>(
-            items + 2 * cap, cnt, cap, tri_d, vert_d, a2, tab64 + ss64_off[2], ss64_off[3] - ss64_off[2], N64);
-    } else {
-      if (counts[1])
-        k_singular<1><<<blocks_for(32LL * counts[1], 256), 256, 0, st>>>(
-            items, cnt, cap, tri_d, vert_d, a2, tab + ss_off[0], ss_off[1] - ss_off[0], N64);
-      if (counts[2])
-        k_singular<2><<<blocks_for(32LL * counts[2], 256), 256, 0, st>>>(
-            items + cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[1], ss_off[2] - ss_off[1], N64);
-      if (counts[3])
-        k_singular<3><<<blocks_for(32LL * counts[3], 256), 256, 0, st>>>(
-            items + 2 * cap, cnt, cap, tri_d, vert_d, a2, tab + ss_off[2], ss_off[3] - ss_off[2], N64);
-    }
-    GCA_TRY_CUDA(cudaGetLastError());
+    if (!p1) h->n_singular[0] = h->n_entries - (h->n_singular[1] + h->n_singular[2] + h->n_singular[3]);
   }
 
   // panel layout for the products, three precisions
@@ -3002,6 +3066,11 @@ int build_group(int count, const gca_mesh* meshes, const gca_tree* trees, const 
   for (auto& p : passes) table.push_back(p->am);
   DevMem d_table, d_jobs;
   GCA_TRY(upload(d_table, table, st));
+  size_t all_clusters = 0;
+  for (auto& b : bs) all_clusters += (size_t)b->nc;
+  GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * all_clusters));  // no reallocation between levels
+  // the near fields, once every allocation before the levels is made
+  for (auto& b : bs) GCA_TRY(b->near_field());
   std::vector<AcaJob> js;
   for (int L = depth; L >= 1; --L) {
     js.clear();

@@ -947,3 +947,260 @@ k_p1c_singular(const P1Item* __restrict__ items, const unsigned long long* __res
     for (int b = 0; b < 3; ++b) M[ci[a]][cj[b]] = acc[a][b] * kInv4Pi;
   p1_scatter(out, it.base, it.ld, it.base2, it.ld2, it.lr, it.lc, M);
 }
+
+// ------------------------------- curved pairs in float-pair arithmetic
+//
+// The samples of k_p1c_singular as float pairs (hi, lo), computed on the
+// host in long double: the monomials (u1, u2, u1^2, u1 u2, u2^2) of both
+// points, the first two barycentric coordinates of both (the third follows
+// from their sum being one), and the weight.
+struct __align__(16) SSEntryCurvedSplit {
+  float mu[5][2];
+  float mv[5][2];
+  float lu[2][2];
+  float lv[2][2];
+  float w[2];
+};
+
+template <int CASE>
+void sauter_table_curved_split(const Rules& rules, std::vector<SSEntryCurvedSplit>& out) {
+  const int q = rules.q, q3 = q * q * q;
+  constexpr int pieces = CASE == 3 ? 6 : (CASE == 2 ? 5 : 2);
+  auto split = [](long double x, float* hl) {
+    hl[0] = (float)x;
+    hl[1] = (float)(x - (long double)hl[0]);
+  };
+  for (int s = 0; s < pieces * q3; ++s) {
+    const int piece = s / q3, r = s % q3;
+    const int a = r / (q * q), b = (r / q) % q, c = r % q;
+    long double u1, u2, v1, v2;
+    const long double wj = sauter_piece<CASE, long double>(piece, rules.ss_t[a], rules.ss_t[b], rules.ss_t[c],
+                                                           u1, u2, v1, v2);
+    for (int x = 0; x < q; ++x) {
+      const long double xi = rules.ss_t[x];
+      const long double U1 = xi * u1, U2 = xi * u2, V1 = xi * v1, V2 = xi * v2;
+      SSEntryCurvedSplit e{};
+      const long double mu[5] = {U1, U2, U1 * U1, U1 * U2, U2 * U2};
+      const long double mv[5] = {V1, V2, V1 * V1, V1 * V2, V2 * V2};
+      for (int k = 0; k < 5; ++k) {
+        split(mu[k], e.mu[k]);
+        split(mv[k], e.mv[k]);
+      }
+      split(1.0L - U1, e.lu[0]);
+      split(U1 - U2, e.lu[1]);
+      split(1.0L - V1, e.lv[0]);
+      split(V1 - V2, e.lv[1]);
+      split((long double)rules.ss_w[x] * rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * xi * xi * xi * wj, e.w);
+      out.push_back(e);
+    }
+  }
+}
+
+// a - b for float pairs, to first order
+__device__ __forceinline__ void pair_sub(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  float e;
+  two_sum(ah, -bh, sh, e);
+  sl = __fadd_rn(e, __fsub_rn(al, bl));
+}
+
+// sqrt of a float pair a > 0: y = sqrtf(a_h), then one Newton step on the
+// exact residual a - y^2
+__device__ __forceinline__ void pair_sqrt(float ah, float al, float& sh, float& sl) {
+  const float y = sqrtf(ah);
+  const float p = __fmul_rn(y, y), pe = __fmaf_rn(y, y, -p);
+  const float res = __fadd_rn(__fsub_rn(__fsub_rn(ah, p), pe), al);
+  sh = y;
+  sl = __fdiv_rn(res, __fmul_rn(2.f, y));
+}
+
+// One warp per ordered touching pair of curved triangles in float-pair
+// arithmetic on the FP32 pipe (the curved rule of k_p1c_singular): the maps'
+// monomial coefficients are formed in float64 per pair and split into float
+// pairs; per sample x - y (the shared vertex cancelling), the tangents, the
+// normals, the Gramians (a float-pair square root), 1 / |x - y| (rsqrtf and
+// one Newton step) and f = w gamma_t gamma_s / |x - y| are float pairs, and
+// the sums of f, f lambda_a(u), f lambda_b(v) and f lambda_a(u) lambda_b(v)
+// for a, b < 2 are kept as float pairs (the third coordinates follow from
+// lambda_0 + lambda_1 + lambda_2 = 1, in float64).
+__global__ void __launch_bounds__(256)
+k_p1c_singular_split(const P1Item* __restrict__ items, const unsigned long long* __restrict__ counts,
+                     int64_t cap, const int* __restrict__ tri, const double* __restrict__ vert,
+                     const double* __restrict__ mid, const SSEntryCurvedSplit* __restrict__ table, int3 toff,
+                     int3 tcnt, double* __restrict__ out) {
+  const int64_t wi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t count = min((long long)counts[4], (long long)cap);
+  if (wi >= count) return;
+  const P1Item it = items[wi];
+  int ti[3], tj[3];
+  for (int a = 0; a < 3; ++a) {
+    ti[a] = tri[3 * it.ti + a];
+    tj[a] = tri[3 * it.tj + a];
+  }
+  int ci[3], cj[3];
+  const int cs = it.cs;
+  if (cs == 3) {
+    for (int a = 0; a < 3; ++a) {
+      ci[a] = a;
+      for (int b = 0; b < 3; ++b)
+        if (tj[b] == ti[a]) cj[a] = b;
+    }
+  } else if (cs == 2) {
+    int sh[2], ns = 0, oi = -1, oj = -1;
+    for (int a = 0; a < 3; ++a) {
+      const bool in_j = ti[a] == tj[0] || ti[a] == tj[1] || ti[a] == tj[2];
+      if (in_j) sh[ns++] = ti[a]; else oi = ti[a];
+    }
+    for (int a = 0; a < 3; ++a)
+      if (tj[a] != sh[0] && tj[a] != sh[1]) oj = tj[a];
+    const int P[3] = {sh[0], sh[1], oi}, Q[3] = {sh[0], sh[1], oj};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        if (ti[b] == P[a]) ci[a] = b;
+        if (tj[b] == Q[a]) cj[a] = b;
+      }
+  } else {
+    int pi = 0, pj = 0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        if (ti[a] == tj[b]) { pi = a; pj = b; }
+    for (int a = 0; a < 3; ++a) {
+      ci[a] = (pi + a) % 3;
+      cj[a] = (pj + a) % 3;
+    }
+  }
+  auto slot = [](int a, int b) { return a + b == 1 ? 0 : (a + b == 3 ? 1 : 2); };
+  double XP[6][3], XQ[6][3];
+  for (int a = 0; a < 3; ++a) {
+    const int e = slot(ci[a], ci[(a + 1) % 3]), f = slot(cj[a], cj[(a + 1) % 3]);
+    for (int d = 0; d < 3; ++d) {
+      XP[a][d] = vert[3 * ti[ci[a]] + d];
+      XQ[a][d] = vert[3 * tj[cj[a]] + d];
+      XP[3 + a][d] = mid[9 * (int64_t)it.ti + 3 * e + d];
+      XQ[3 + a][d] = mid[9 * (int64_t)it.tj + 3 * f + d];
+    }
+  }
+  // monomial coefficients (as in k_p1c_singular) split into float pairs
+  float kp[5][3][2], kq[5][3][2];
+  for (int d = 0; d < 3; ++d) {
+    const double cp[5] = {4.0 * XP[3][d] - 3.0 * XP[0][d] - XP[1][d],
+                          XP[1][d] - XP[2][d] - 4.0 * XP[3][d] + 4.0 * XP[5][d],
+                          2.0 * XP[0][d] + 2.0 * XP[1][d] - 4.0 * XP[3][d],
+                          4.0 * (XP[3][d] + XP[4][d] - XP[5][d] - XP[1][d]),
+                          2.0 * XP[1][d] + 2.0 * XP[2][d] - 4.0 * XP[4][d]};
+    const double cq[5] = {4.0 * XQ[3][d] - 3.0 * XQ[0][d] - XQ[1][d],
+                          XQ[1][d] - XQ[2][d] - 4.0 * XQ[3][d] + 4.0 * XQ[5][d],
+                          2.0 * XQ[0][d] + 2.0 * XQ[1][d] - 4.0 * XQ[3][d],
+                          4.0 * (XQ[3][d] + XQ[4][d] - XQ[5][d] - XQ[1][d]),
+                          2.0 * XQ[1][d] + 2.0 * XQ[2][d] - 4.0 * XQ[4][d]};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      kp[k][d][0] = (float)cp[k];
+      kp[k][d][1] = (float)(cp[k] - (double)kp[k][d][0]);
+      kq[k][d][0] = (float)cq[k];
+      kq[k][d][1] = (float)(cq[k] - (double)kq[k][d][0]);
+    }
+  }
+  // Gramian |d Phi/du1 x d Phi/du2| at the monomials m = (u1, u2, ...)
+  auto gram = [](const float (*K)[3][2], const float (*m)[2], float& gh, float& gl) {
+    float t1[3][2], t2[3][2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      // t1 = K0 + 2 K2 u1 + K3 u2, t2 = K1 + K3 u1 + 2 K4 u2 (doubling is exact)
+      t1[d][0] = K[0][d][0];
+      t1[d][1] = K[0][d][1];
+      fp_mul_add(2.f * K[2][d][0], 2.f * K[2][d][1], m[0][0], m[0][1], t1[d][0], t1[d][1]);
+      fp_mul_add(K[3][d][0], K[3][d][1], m[1][0], m[1][1], t1[d][0], t1[d][1]);
+      t2[d][0] = K[1][d][0];
+      t2[d][1] = K[1][d][1];
+      fp_mul_add(K[3][d][0], K[3][d][1], m[0][0], m[0][1], t2[d][0], t2[d][1]);
+      fp_mul_add(2.f * K[4][d][0], 2.f * K[4][d][1], m[1][0], m[1][1], t2[d][0], t2[d][1]);
+    }
+    float n2h = 0.f, n2l = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int e = (d + 1) % 3, f = (d + 2) % 3;
+      float ah, al, bh, bl, nh, nl;
+      pair_mul(t1[e][0], t1[e][1], t2[f][0], t2[f][1], ah, al);
+      pair_mul(t1[f][0], t1[f][1], t2[e][0], t2[e][1], bh, bl);
+      pair_sub(ah, al, bh, bl, nh, nl);
+      fp_mul_add(nh, nl, nh, nl, n2h, n2l);
+    }
+    pair_sqrt(n2h, n2l, gh, gl);
+  };
+  const int t0 = cs == 1 ? toff.x : (cs == 2 ? toff.y : toff.z);
+  const int tn = cs == 1 ? tcnt.x : (cs == 2 ? tcnt.y : tcnt.z);
+  // float-pair sums: 0 f, 1-2 f lambda_a(u), 3-4 f lambda_b(v), 5-8 f lambda_a(u) lambda_b(v)
+  float sh[9], sl[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) sh[i] = sl[i] = 0.f;
+  for (int s = lane; s < tn; s += 32) {
+    const SSEntryCurvedSplit e = table[t0 + s];
+    float r2h = 0.f, r2l = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float dh = 0.f, dl = 0.f;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        fp_mul_add(kp[k][d][0], kp[k][d][1], e.mu[k][0], e.mu[k][1], dh, dl);
+        fp_mul_add(-kq[k][d][0], -kq[k][d][1], e.mv[k][0], e.mv[k][1], dh, dl);
+      }
+      fp_mul_add(dh, dl, dh, dl, r2h, r2l);
+    }
+    // 1 / |x - y|: rsqrtf and one Newton step on the exact residual
+    const float y0 = rsqrtf(__fadd_rn(r2h, r2l));
+    const float u = __fmul_rn(y0, y0), uu = __fmaf_rn(y0, y0, -u);
+    const float mm = __fmul_rn(u, r2h), me = __fmaf_rn(u, r2h, -mm);
+    const float rho = __fmaf_rn(-uu, r2h, __fmaf_rn(-u, r2l, __fsub_rn(__fsub_rn(1.f, mm), me)));
+    const float dy = __fmul_rn(__fmul_rn(0.5f, y0), rho);
+    float gth, gtl, gsh, gsl;
+    gram(kp, e.mu, gth, gtl);
+    gram(kq, e.mv, gsh, gsl);
+    float fh, fl;
+    pair_mul(e.w[0], e.w[1], y0, dy, fh, fl);
+    pair_mul(fh, fl, gth, gtl, fh, fl);
+    pair_mul(fh, fl, gsh, gsl, fh, fl);
+    pair_acc(sh[0], sl[0], fh, fl);
+    float gh[2], gl[2];  // f lambda_a(u)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      pair_mul(fh, fl, e.lu[a][0], e.lu[a][1], gh[a], gl[a]);
+      pair_acc(sh[1 + a], sl[1 + a], gh[a], gl[a]);
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      float th, tl;
+      pair_mul(fh, fl, e.lv[b][0], e.lv[b][1], th, tl);
+      pair_acc(sh[3 + b], sl[3 + b], th, tl);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        pair_mul(gh[a], gl[a], e.lv[b][0], e.lv[b][1], th, tl);
+        pair_acc(sh[5 + 2 * a + b], sl[5 + 2 * a + b], th, tl);
+      }
+    }
+  }
+  double S[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    double v = (double)sh[i] + (double)sl[i];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    S[i] = v;
+  }
+  if (lane != 0) return;
+  // sums with lambda_2 = 1 - lambda_0 - lambda_1 on either side
+  double acc[3][3];
+  const double su[3] = {S[1], S[2], S[0] - S[1] - S[2]};
+  const double sv[3] = {S[3], S[4], S[0] - S[3] - S[4]};
+  acc[0][0] = S[5];
+  acc[0][1] = S[6];
+  acc[1][0] = S[7];
+  acc[1][1] = S[8];
+  for (int a = 0; a < 2; ++a) acc[a][2] = su[a] - acc[a][0] - acc[a][1];
+  for (int b = 0; b < 3; ++b) acc[2][b] = sv[b] - acc[0][b] - acc[1][b];
+  double M[3][3];  // stored corners
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) M[ci[a]][cj[b]] = acc[a][b] * kInv4Pi;
+  p1_scatter(out, it.base, it.ld, it.base2, it.ld2, it.lr, it.lc, M);
+}
