@@ -780,180 +780,15 @@ __global__ void k_p1c_boxes(int nc, const int* __restrict__ begin, const int* __
     }
 }
 
-// A sample of the curved Sauter-Schwab rule: the reference coordinates of
-// both points (u = xi u^(eta), v = xi v^(eta)) and the weight (Gauss weights
-// of all four variables times xi^3 and the piece's eta-Jacobian); the map is
-// not affine, so xi is sampled like eta.
-struct __align__(16) SSEntryCurved {
-  double u1, u2, v1, v2;
-  double w;
-  double pad;
-};
-
-template <int CASE>
-void sauter_table_curved(const Rules& rules, std::vector<SSEntryCurved>& out) {
-  const int q = rules.q, q3 = q * q * q;
-  constexpr int pieces = CASE == 3 ? 6 : (CASE == 2 ? 5 : 2);
-  for (int s = 0; s < pieces * q3; ++s) {
-    const int piece = s / q3, r = s % q3;
-    const int a = r / (q * q), b = (r / q) % q, c = r % q;
-    long double u1, u2, v1, v2;
-    const long double wj = sauter_piece<CASE, long double>(piece, rules.ss_t[a], rules.ss_t[b], rules.ss_t[c],
-                                                           u1, u2, v1, v2);
-    for (int x = 0; x < q; ++x) {
-      const long double xi = rules.ss_t[x];
-      SSEntryCurved e{};
-      e.u1 = (double)(xi * u1);
-      e.u2 = (double)(xi * u2);
-      e.v1 = (double)(xi * v1);
-      e.v2 = (double)(xi * v2);
-      e.w = (double)((long double)rules.ss_w[x] * rules.ss_w[a] * rules.ss_w[b] * rules.ss_w[c] * xi * xi * xi * wj);
-      out.push_back(e);
-    }
-  }
-}
-
-// One warp per ordered touching pair of curved triangles, in float64: the
-// vertex orders of the flat rules (the stored midpoints follow their edges),
-// x - y and the Gramians of both triangles at every sample from the maps'
-// monomial coefficients, and the sums of f lambda_a(u) lambda_b(v) with
-// f = w gamma_t gamma_s / |Phi_t - Phi_s|.
-__global__ void __launch_bounds__(256)
-k_p1c_singular(const P1Item* __restrict__ items, const unsigned long long* __restrict__ counts, int64_t cap,
-               const int* __restrict__ tri, const double* __restrict__ vert, const double* __restrict__ mid,
-               const SSEntryCurved* __restrict__ table, int3 toff, int3 tcnt, double* __restrict__ out) {
-  const int64_t wi = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int64_t count = min((long long)counts[4], (long long)cap);
-  if (wi >= count) return;
-  const P1Item it = items[wi];
-  int ti[3], tj[3];
-  for (int a = 0; a < 3; ++a) {
-    ti[a] = tri[3 * it.ti + a];
-    tj[a] = tri[3 * it.tj + a];
-  }
-  int ci[3], cj[3];
-  const int cs = it.cs;
-  if (cs == 3) {
-    for (int a = 0; a < 3; ++a) {
-      ci[a] = a;
-      for (int b = 0; b < 3; ++b)
-        if (tj[b] == ti[a]) cj[a] = b;
-    }
-  } else if (cs == 2) {
-    int sh[2], ns = 0, oi = -1, oj = -1;
-    for (int a = 0; a < 3; ++a) {
-      const bool in_j = ti[a] == tj[0] || ti[a] == tj[1] || ti[a] == tj[2];
-      if (in_j) sh[ns++] = ti[a]; else oi = ti[a];
-    }
-    for (int a = 0; a < 3; ++a)
-      if (tj[a] != sh[0] && tj[a] != sh[1]) oj = tj[a];
-    const int P[3] = {sh[0], sh[1], oi}, Q[3] = {sh[0], sh[1], oj};
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        if (ti[b] == P[a]) ci[a] = b;
-        if (tj[b] == Q[a]) cj[a] = b;
-      }
-  } else {
-    int pi = 0, pj = 0;
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b)
-        if (ti[a] == tj[b]) { pi = a; pj = b; }
-    for (int a = 0; a < 3; ++a) {
-      ci[a] = (pi + a) % 3;
-      cj[a] = (pj + a) % 3;
-    }
-  }
-  // ordered nodes: vertices, then the edge points of the ordered edges
-  // (0, 1), (1, 2), (2, 0); stored slot of edge {a, b}: 0 for {0, 1}, 1 for
-  // {1, 2}, 2 for {0, 2}
-  auto slot = [](int a, int b) { return a + b == 1 ? 0 : (a + b == 3 ? 1 : 2); };
-  double XP[6][3], XQ[6][3];
-  for (int a = 0; a < 3; ++a) {
-    const int e = slot(ci[a], ci[(a + 1) % 3]), f = slot(cj[a], cj[(a + 1) % 3]);
-    for (int d = 0; d < 3; ++d) {
-      XP[a][d] = vert[3 * ti[ci[a]] + d];
-      XQ[a][d] = vert[3 * tj[cj[a]] + d];
-      XP[3 + a][d] = mid[9 * (int64_t)it.ti + 3 * e + d];
-      XQ[3 + a][d] = mid[9 * (int64_t)it.tj + 3 * f + d];
-    }
-  }
-  // The map in the reference coordinates u (lambda = (1 - u1, u1 - u2, u2)):
-  //   Phi(u) = X0 + B1 u1 + B2 u2 + C11 u1^2 + C12 u1 u2 + C22 u2^2,
-  //   B1 = 4 M01 - 3 X0 - X1,         B2 = X1 - X2 - 4 M01 + 4 M20,
-  //   C11 = 2 X0 + 2 X1 - 4 M01,      C12 = 4 (M01 + M12 - M20 - X1),
-  //   C22 = 2 X1 + 2 X2 - 4 M12.
-  // Both triangles start at the shared vertex (X0 of P is X0 of Q), so
-  // x - y is formed from the u- and v-terms alone; d Phi/du1 x d Phi/du2 has
-  // the Gramian's length (x^ = (u1 - u2, u2) has Jacobian 1).
-  double KP[5][3], KQ[5][3];
-  for (int d = 0; d < 3; ++d) {
-    KP[0][d] = 4.0 * XP[3][d] - 3.0 * XP[0][d] - XP[1][d];
-    KP[1][d] = XP[1][d] - XP[2][d] - 4.0 * XP[3][d] + 4.0 * XP[5][d];
-    KP[2][d] = 2.0 * XP[0][d] + 2.0 * XP[1][d] - 4.0 * XP[3][d];
-    KP[3][d] = 4.0 * (XP[3][d] + XP[4][d] - XP[5][d] - XP[1][d]);
-    KP[4][d] = 2.0 * XP[1][d] + 2.0 * XP[2][d] - 4.0 * XP[4][d];
-    KQ[0][d] = 4.0 * XQ[3][d] - 3.0 * XQ[0][d] - XQ[1][d];
-    KQ[1][d] = XQ[1][d] - XQ[2][d] - 4.0 * XQ[3][d] + 4.0 * XQ[5][d];
-    KQ[2][d] = 2.0 * XQ[0][d] + 2.0 * XQ[1][d] - 4.0 * XQ[3][d];
-    KQ[3][d] = 4.0 * (XQ[3][d] + XQ[4][d] - XQ[5][d] - XQ[1][d]);
-    KQ[4][d] = 2.0 * XQ[1][d] + 2.0 * XQ[2][d] - 4.0 * XQ[4][d];
-  }
-  auto gram = [](const double (*K)[3], double u1, double u2) {
-    double t1[3], t2[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      t1[d] = K[0][d] + 2.0 * K[2][d] * u1 + K[3][d] * u2;
-      t2[d] = K[1][d] + K[3][d] * u1 + 2.0 * K[4][d] * u2;
-    }
-    const double n0 = t1[1] * t2[2] - t1[2] * t2[1];
-    const double n1 = t1[2] * t2[0] - t1[0] * t2[2];
-    const double n2 = t1[0] * t2[1] - t1[1] * t2[0];
-    return sqrt(n0 * n0 + n1 * n1 + n2 * n2);
-  };
-  const int t0 = cs == 1 ? toff.x : (cs == 2 ? toff.y : toff.z);
-  const int tn = cs == 1 ? tcnt.x : (cs == 2 ? tcnt.y : tcnt.z);
-  double acc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  for (int s = lane; s < tn; s += 32) {
-    const SSEntryCurved e = table[t0 + s];
-    const double mu[5] = {e.u1, e.u2, e.u1 * e.u1, e.u1 * e.u2, e.u2 * e.u2};
-    const double mv[5] = {e.v1, e.v2, e.v1 * e.v1, e.v1 * e.v2, e.v2 * e.v2};
-    double r2 = 0.0;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      double dd = 0.0;
-#pragma unroll
-      for (int k = 0; k < 5; ++k) dd += KP[k][d] * mu[k] - KQ[k][d] * mv[k];
-      r2 += dd * dd;
-    }
-    const double f = e.w * gram(KP, e.u1, e.u2) * gram(KQ, e.v1, e.v2) * rsqrt(r2);
-    const double lu[3] = {1.0 - e.u1, e.u1 - e.u2, e.u2};
-    const double lv[3] = {1.0 - e.v1, e.v1 - e.v2, e.v2};
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) acc[a][b] += f * lu[a] * lv[b];
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-      for (int o = 16; o; o >>= 1) acc[a][b] += __shfl_xor_sync(0xffffffffu, acc[a][b], o);
-  if (lane != 0) return;
-  double M[3][3];  // stored corners
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) M[ci[a]][cj[b]] = acc[a][b] * kInv4Pi;
-  p1_scatter(out, it.base, it.ld, it.base2, it.ld2, it.lr, it.lc, M);
-}
-
 // ------------------------------- curved pairs in float-pair arithmetic
 //
-// The samples of k_p1c_singular as float pairs (hi, lo), computed on the
-// host in long double: the monomials (u1, u2, u1^2, u1 u2, u2^2) of both
-// points, the first two barycentric coordinates of both (the third follows
-// from their sum being one), and the weight.
+// A sample of the curved Sauter-Schwab rule as float pairs (hi, lo),
+// computed on the host in long double: the map is not affine, so xi is
+// sampled like eta (u = xi u^(eta), v = xi v^(eta)); the monomials (u1, u2,
+// u1^2, u1 u2, u2^2) of both points, the first two barycentric coordinates
+// of both (the third follows from their sum being one), and the weight (the
+// Gauss weights of all four variables times xi^3 and the piece's
+// eta-Jacobian).
 struct __align__(16) SSEntryCurvedSplit {
   float mu[5][2];
   float mv[5][2];
@@ -1014,8 +849,16 @@ __device__ __forceinline__ void pair_sqrt(float ah, float al, float& sh, float& 
 }
 
 // One warp per ordered touching pair of curved triangles in float-pair
-// arithmetic on the FP32 pipe (the curved rule of k_p1c_singular): the maps'
-// monomial coefficients are formed in float64 per pair and split into float
+// arithmetic on the FP32 pipe: the vertex orders of the flat rules (the
+// stored edge points follow their edges); the maps in the reference
+// coordinates u (lambda = (1 - u1, u1 - u2, u2)),
+//   Phi(u) = X0 + B1 u1 + B2 u2 + C11 u1^2 + C12 u1 u2 + C22 u2^2,
+//   B1 = 4 M01 - 3 X0 - X1,         B2 = X1 - X2 - 4 M01 + 4 M20,
+//   C11 = 2 X0 + 2 X1 - 4 M01,      C12 = 4 (M01 + M12 - M20 - X1),
+//   C22 = 2 X1 + 2 X2 - 4 M12,
+// have |d Phi/du1 x d Phi/du2| as Gramian (x^ = (u1 - u2, u2) has Jacobian
+// 1), and both start at the shared vertex.  The monomial coefficients are
+// formed in float64 per pair and split into float
 // pairs; per sample x - y (the shared vertex cancelling), the tangents, the
 // normals, the Gramians (a float-pair square root), 1 / |x - y| (rsqrtf and
 // one Newton step) and f = w gamma_t gamma_s / |x - y| are float pairs, and
@@ -1080,7 +923,7 @@ k_p1c_singular_split(const P1Item* __restrict__ items, const unsigned long long*
       XQ[3 + a][d] = mid[9 * (int64_t)it.tj + 3 * f + d];
     }
   }
-  // monomial coefficients (as in k_p1c_singular) split into float pairs
+  // monomial coefficients split into float pairs
   float kp[5][3][2], kq[5][3][2];
   for (int d = 0; d < 3; ++d) {
     const double cp[5] = {4.0 * XP[3][d] - 3.0 * XP[0][d] - XP[1][d],
