@@ -315,7 +315,7 @@ constexpr int kP1Chunk = 64;  // column triangles staged in shared memory at a t
 // pair with nodes closer than sqrt(near_r2) is computed again in float64.
 // The output is zero on entry (atomic sums).
 template <bool NEAR>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, NEAR ? 1 : 2)
 k_p1_entries(const P1Block* __restrict__ blocks, const UnionJob* __restrict__ ujobs,
              const int* __restrict__ ucount, const int4* __restrict__ urows, const int* __restrict__ tri,
              const P4* __restrict__ tq, const SplitNode* __restrict__ tn, Rules rules, BarySplit bs,
@@ -865,7 +865,7 @@ __device__ __forceinline__ void pair_sqrt(float ah, float al, float& sh, float& 
 // the sums of f, f lambda_a(u), f lambda_b(v) and f lambda_a(u) lambda_b(v)
 // for a, b < 2 are kept as float pairs (the third coordinates follow from
 // lambda_0 + lambda_1 + lambda_2 = 1, in float64).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_p1c_singular_split(const P1Item* __restrict__ items, const unsigned long long* __restrict__ counts,
                      int64_t cap, const int* __restrict__ tri, const double* __restrict__ vert,
                      const double* __restrict__ mid, const SSEntryCurvedSplit* __restrict__ table, int3 toff,
