@@ -261,8 +261,11 @@ int gca_build(const gca_mesh* mesh, const gca_tree* tree, const gca_params* para
  *     d2g/dn_y dn_z(y, z) = (<n_y, n_z> / r^3 - 3 <n_y, e><n_z, e> / r^5) / (4 pi),
  *     e = z - y; its cross approximation (Sect. 3), nested as in Sect. 4,
  *     gives tilde-sigma', the column bases W and transfer matrices F;
- *   - entries in float64: the 7 x 7 rule for disjoint pairs, 0 for identical
- *     flat triangles, Sauter-Schwab for a common edge or vertex (Sect. 8).
+ *   - entries: the 7 x 7 rule for disjoint pairs in float-pair arithmetic
+ *     (about 48 significant bits; near-field pairs with nodes closer than
+ *     2^-8 of the mesh's half width in float64), 0 for identical flat
+ *     triangles, Sauter-Schwab in float64 for a common edge or vertex
+ *     (Sect. 8).
  * The handle works with h2_matvec (K x), h2_matvec_transpose (K^T x, a
  * genuinely different product), h2_matvec_noalloc, gca_h2_stats (S: the
  * r_tau x r'_sigma couplings, N: the near field), gca_h2_export (row bases,

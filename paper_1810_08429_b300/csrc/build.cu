@@ -1340,6 +1340,20 @@ __device__ __forceinline__ void fp_mul_add(float ch, float cl, float vh, float v
   sl = __fadd_rn(sl, __fadd_rn(ne, tl));
 }
 
+// s + (th + tl) for float pairs s = (sh, sl)
+__device__ __forceinline__ void pair_acc(float& sh, float& sl, float th, float tl) {
+  float ns, ne;
+  two_sum(sh, th, ns, ne);
+  sh = ns;
+  sl = __fadd_rn(sl, __fadd_rn(ne, tl));
+}
+
+// (ah + al)(bh + bl) as a float pair to first order
+__device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl, float& th, float& tl) {
+  th = __fmul_rn(ah, bh);
+  tl = __fadd_rn(__fmaf_rn(ah, bh, -th), __fmaf_rn(ah, bl, __fmul_rn(al, bh)));
+}
+
 // one warp per touching pair; the eta samples in float-pair arithmetic (the
 // regular rule's error-free sums, |h|^2 as a float pair and one Newton step
 // from rsqrtf), the pair's sum and its Jacobians (2 |T|) in float64
@@ -1480,30 +1494,96 @@ __device__ __forceinline__ double dl_regular_entry(const P4* __restrict__ xq, co
   return s * kInv4Pi;
 }
 
+// The double layer's 7 x 7 rule in float-pair arithmetic on the FP32 pipe
+// (the recipe of regular_entry_split): per node pair d = x - y with exact
+// high differences, |d|^2 and 1/|d| as float pairs, <n_y, d> with the
+// normal split into float pairs (nh + nl), the term w_q <n_y, d> / |d|^3
+// summed as float pairs and rounded to float64 once.  min_r2 returns the
+// smallest |d|^2 (high part) met, for the near field's float64 fallback.
+__device__ __forceinline__ double dl_entry_split(const SplitNode* __restrict__ xq, const SplitNode* __restrict__ yq,
+                                                 const float* nh, const float* nl, float& min_r2) {
+  float sh = 0.f, sl = 0.f;
+  float mr = 3.0e38f;
+#pragma unroll 1
+  for (int p = 0; p < 7; ++p) {
+    const SplitNode x = xq[p];
+    float ih = 0.f, il = 0.f;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      const SplitNode y = yq[q];
+      const float dh0 = __fsub_rn(x.hi.x, y.hi.x), dl0 = __fsub_rn(x.lo.x, y.lo.x);
+      const float dh1 = __fsub_rn(x.hi.y, y.hi.y), dl1 = __fsub_rn(x.lo.y, y.lo.y);
+      const float dh2 = __fsub_rn(x.hi.z, y.hi.z), dl2 = __fsub_rn(x.lo.z, y.lo.z);
+      const float p0 = __fmul_rn(dh0, dh0), p1 = __fmul_rn(dh1, dh1), p2 = __fmul_rn(dh2, dh2);
+      float low = __fmaf_rn(dh0, dh0, -p0);
+      low = __fadd_rn(low, __fmaf_rn(dh1, dh1, -p1));
+      low = __fadd_rn(low, __fmaf_rn(dh2, dh2, -p2));
+      low = __fmaf_rn(__fadd_rn(__fadd_rn(dh0, dh0), dl0), dl0, low);
+      low = __fmaf_rn(__fadd_rn(__fadd_rn(dh1, dh1), dl1), dl1, low);
+      low = __fmaf_rn(__fadd_rn(__fadd_rn(dh2, dh2), dl2), dl2, low);
+      float s01, e01, rh, e2;
+      two_sum(p0, p1, s01, e01);
+      two_sum(s01, p2, rh, e2);
+      const float rl = __fadd_rn(low, __fadd_rn(e01, e2));
+      mr = fminf(mr, rh);
+      const float y0 = rsqrtf(__fadd_rn(rh, rl));
+      const float u = __fmul_rn(y0, y0), uu = __fmaf_rn(y0, y0, -u);
+      const float m = __fmul_rn(u, rh), me = __fmaf_rn(u, rh, -m);
+      const float rho = __fmaf_rn(-uu, rh, __fmaf_rn(-u, rl, __fsub_rn(__fsub_rn(1.f, m), me)));
+      const float dy = __fmul_rn(__fmul_rn(0.5f, y0), rho);
+      // <n_y, d>
+      float ndh = 0.f, ndl = 0.f;
+      fp_mul_add(nh[0], nl[0], dh0, dl0, ndh, ndl);
+      fp_mul_add(nh[1], nl[1], dh1, dl1, ndh, ndl);
+      fp_mul_add(nh[2], nl[2], dh2, dl2, ndh, ndl);
+      // w_q <n_y, d> / |d|^3
+      float ah, al, bh, bl;
+      pair_mul(y0, dy, y0, dy, ah, al);
+      pair_mul(ah, al, y0, dy, bh, bl);
+      pair_mul(ndh, ndl, bh, bl, ah, al);
+      pair_mul(y.hi.w, y.lo.w, ah, al, bh, bl);
+      pair_acc(ih, il, bh, bl);
+    }
+    float th, tl;
+    pair_mul(x.hi.w, x.lo.w, ih, il, th, tl);
+    pair_acc(sh, sl, th, tl);
+  }
+  min_r2 = mr;
+  return ((double)sh + (double)sl) * kInv4Pi;
+}
+
 // One CTA per coupling block (tau, sigma): K|tilde-tau x tilde-sigma', the
 // row pivots of tau against the column pivots of sigma (r_tau x r'_sigma,
-// row-major).  K is not symmetric, so every block is computed.
+// row-major), in float-pair arithmetic (admissible pairs lie a fraction of
+// a cluster diameter apart).  K is not symmetric, so every block is
+// computed.
 __global__ void k_dl_couple(const int* __restrict__ far_t, const int* __restrict__ far_s,
                             const int64_t* __restrict__ soff, const int* __restrict__ rank,
                             const int* __restrict__ rank2, const int64_t* __restrict__ poff,
                             const int64_t* __restrict__ poff2, const int* __restrict__ piv,
-                            const int* __restrict__ piv2, const P4* __restrict__ tq,
+                            const int* __restrict__ piv2, const SplitNode* __restrict__ tn,
                             const double* __restrict__ nrm, double* __restrict__ S) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int b = blockIdx.x;
   const int t = far_t[b], s = far_s[b];
   const int rt = rank[t], rs = rank2[s];
-  P4* ys = reinterpret_cast<P4*>(smem_raw);
-  double* yn = reinterpret_cast<double*>(ys + 7 * (size_t)rs);
+  SplitNode* ys = reinterpret_cast<SplitNode*>(smem_raw);
+  float* yn = reinterpret_cast<float*>(ys + 7 * (size_t)rs);  // per column: 3 high, then 3 low parts
   const int* pt = piv + poff[t];
   const int* ps = piv2 + poff2[s];
-  for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) ys[i] = tq[7 * (int64_t)ps[i / 7] + i % 7];
-  for (int i = threadIdx.x; i < rs * 3; i += blockDim.x) yn[i] = nrm[3 * (int64_t)ps[i / 3] + i % 3];
+  for (int i = threadIdx.x; i < rs * 7; i += blockDim.x) ys[i] = tn[7 * (int64_t)ps[i / 7] + i % 7];
+  for (int i = threadIdx.x; i < rs * 3; i += blockDim.x) {
+    const double n = nrm[3 * (int64_t)ps[i / 3] + i % 3];
+    const float h = (float)n;
+    yn[6 * (i / 3) + i % 3] = h;
+    yn[6 * (i / 3) + 3 + i % 3] = (float)(n - (double)h);
+  }
   __syncthreads();
   double* out = S + soff[b];
   for (int idx = threadIdx.x; idx < rt * rs; idx += blockDim.x) {
     const int a = idx / rs, c = idx - (idx / rs) * rs;
-    out[idx] = dl_regular_entry(tq + 7 * (int64_t)pt[a], ys + 7 * c, yn[3 * c], yn[3 * c + 1], yn[3 * c + 2]);
+    float mr;
+    out[idx] = dl_entry_split(tn + 7 * (int64_t)pt[a], ys + 7 * c, yn + 6 * c, yn + 6 * c + 3, mr);
   }
 }
 
@@ -1514,6 +1594,7 @@ __global__ void k_dl_near_entries(const int* __restrict__ near_t, const int* __r
                                   const int64_t* __restrict__ noff, const int* __restrict__ begin,
                                   const int* __restrict__ end, const int* __restrict__ perm,
                                   const int* __restrict__ tri, const P4* __restrict__ tq,
+                                  const SplitNode* __restrict__ tn, float near_r2,
                                   const double* __restrict__ nrm, double* __restrict__ N,
                                   SingularItem* __restrict__ lists, int64_t cap,
                                   unsigned long long* __restrict__ counts, int* __restrict__ status) {
@@ -1522,9 +1603,21 @@ __global__ void k_dl_near_entries(const int* __restrict__ near_t, const int* __r
   const int t = near_t[b], s = near_s[b];
   const int bt = begin[t], nt = end[t] - bt, bs = begin[s], ns = end[s] - bs;
   P4* ys = reinterpret_cast<P4*>(smem_raw);
-  double* yn = reinterpret_cast<double*>(ys + 7 * (size_t)ns);
-  for (int i = threadIdx.x; i < ns * 7; i += blockDim.x) ys[i] = tq[7 * (int64_t)perm[bs + i / 7] + i % 7];
-  for (int i = threadIdx.x; i < ns * 3; i += blockDim.x) yn[i] = nrm[3 * (int64_t)perm[bs + i / 3] + i % 3];
+  SplitNode* yt = reinterpret_cast<SplitNode*>(ys + 7 * (size_t)ns);
+  double* yn = reinterpret_cast<double*>(yt + 7 * (size_t)ns);
+  float* yf = reinterpret_cast<float*>(yn + 3 * (size_t)ns);  // per column: 3 high, then 3 low parts
+  for (int i = threadIdx.x; i < ns * 7; i += blockDim.x) {
+    const int64_t src = 7 * (int64_t)perm[bs + i / 7] + i % 7;
+    ys[i] = tq[src];
+    yt[i] = tn[src];
+  }
+  for (int i = threadIdx.x; i < ns * 3; i += blockDim.x) {
+    const double n = nrm[3 * (int64_t)perm[bs + i / 3] + i % 3];
+    const float h = (float)n;
+    yn[i] = n;
+    yf[6 * (i / 3) + i % 3] = h;
+    yf[6 * (i / 3) + 3 + i % 3] = (float)(n - (double)h);
+  }
   __syncthreads();
   const int64_t base = noff[b];
   for (int idx = threadIdx.x; idx < nt * ns; idx += blockDim.x) {
@@ -1537,7 +1630,11 @@ __global__ void k_dl_near_entries(const int* __restrict__ near_t, const int* __r
       shared += (va == tri[3 * tj]) + (va == tri[3 * tj + 1]) + (va == tri[3 * tj + 2]);
     }
     if (shared == 0) {
-      N[base + idx] = dl_regular_entry(tq + 7 * (int64_t)ti, ys + 7 * j, yn[3 * j], yn[3 * j + 1], yn[3 * j + 2]);
+      // float pairs, or float64 for nodes closer than sqrt(near_r2)
+      float mr;
+      double v = dl_entry_split(tn + 7 * (int64_t)ti, yt + 7 * j, yf + 6 * j, yf + 6 * j + 3, mr);
+      if (mr < near_r2) v = dl_regular_entry(tq + 7 * (int64_t)ti, ys + 7 * j, yn[3 * j], yn[3 * j + 1], yn[3 * j + 2]);
+      N[base + idx] = v;
     } else if (shared == 3) {
       N[base + idx] = 0.0;  // x - y lies in the plane of T_j
       atomicAdd(&counts[3], 1ull);
@@ -2751,13 +2848,14 @@ int Builder::near_field() {
   } else {
     const SingularItem* items = d_items.as<SingularItem>();
     if (op == 1) {
-      const size_t smem = (sizeof(P4) * 7 + sizeof(double) * 3) * (size_t)h->max_leaf;
+      const size_t smem =
+          ((sizeof(P4) + sizeof(SplitNode)) * 7 + sizeof(double) * 3 + sizeof(float) * 6) * (size_t)h->max_leaf;
       GCA_TRY_CUDA(cudaFuncSetAttribute(k_dl_near_entries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       PhaseScope ps__("dl_near_entries", ns);
       k_dl_near_entries<<<nnear, 256, smem, ns>>>(
           h->d_near_t.as<int>(), h->d_near_s.as<int>(), h->d_noff.as<int64_t>(), h->d_begin.as<int>(),
-          h->d_end.as<int>(), h->d_perm.as<int>(), tri_d, d_tq.as<P4>(), d_nrm.as<double>(), N64,
-          d_items.as<SingularItem>(), cap, cnt, nstat);
+          h->d_end.as<int>(), h->d_perm.as<int>(), tri_d, d_tq.as<P4>(), d_tn.as<SplitNode>(), near_r2,
+          d_nrm.as<double>(), N64, d_items.as<SingularItem>(), cap, cnt, nstat);
       GCA_TRY_CUDA(cudaGetLastError());
     } else {
       const size_t smem = (sizeof(P4) + sizeof(SplitNode)) * 7 * (size_t)h->max_leaf;
@@ -2964,14 +3062,14 @@ int Builder::finish(gca_h2** out) {
     }
     GCA_TRY_CUDA(cudaGetLastError());
   } else if (nfar > 0 && op == 1) {
-    const size_t smem = (sizeof(P4) * 7 + sizeof(double) * 3) * (size_t)std::max(h->max_rank2, 1);
+    const size_t smem = (sizeof(SplitNode) * 7 + sizeof(float) * 6) * (size_t)std::max(h->max_rank2, 1);
     GCA_TRY_CUDA(cudaFuncSetAttribute(k_dl_couple, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
       PhaseScope ps__("dl_couple_entries", st);
       k_dl_couple<<<(unsigned)nfar, 256, smem, st>>>(
           h->d_far_t.as<int>(), h->d_far_s.as<int>(), h->d_soff.as<int64_t>(), h->d_rank.as<int>(),
           d_rank2v.as<int>(), d_poff.as<int64_t>(), d_poff2.as<int64_t>(), d_piv.as<int>(), d_piv2.as<int>(),
-          d_tq.as<P4>(), d_nrm.as<double>(), h->S64.as<double>());
+          d_tn.as<SplitNode>(), d_nrm.as<double>(), h->S64.as<double>());
     }
     GCA_TRY_CUDA(cudaGetLastError());
   } else if (nfar > 0) {

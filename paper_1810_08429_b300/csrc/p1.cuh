@@ -287,20 +287,6 @@ __device__ __forceinline__ void inv_dist_split(float xh0, float xh1, float xh2, 
   dy = __fmul_rn(__fmul_rn(0.5f, y0), rho);
 }
 
-// s + (th + tl) for float pairs s = (sh, sl)
-__device__ __forceinline__ void pair_acc(float& sh, float& sl, float th, float tl) {
-  float ns, ne;
-  two_sum(sh, th, ns, ne);
-  sh = ns;
-  sl = __fadd_rn(sl, __fadd_rn(ne, tl));
-}
-
-// (ah + al)(bh + bl) as a float pair to first order
-__device__ __forceinline__ void pair_mul(float ah, float al, float bh, float bl, float& th, float& tl) {
-  th = __fmul_rn(ah, bh);
-  tl = __fadd_rn(__fmaf_rn(ah, bh, -th), __fmaf_rn(ah, bl, __fmul_rn(al, bh)));
-}
-
 constexpr int kP1Chunk = 64;  // column triangles staged in shared memory at a time
 
 // One CTA per block.  Columns are staged in chunks (split nodes and weights
