@@ -31,6 +31,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <numeric>
 
 #include "internal.hpp"
@@ -2245,27 +2246,35 @@ class Builder {
                                                 &h->e_entries, &h->V64, &h->E64},
                                        d_piv, d_rank, piv_used);
   }
-  // a pass on this mesh alone: one launch per level; `fork_near` launches the
-  // near field once the pass's pools are allocated (an allocation can wait
-  // for all work on the device, the side stream's included)
-  int run_pass(BasisPass& pass, bool fork_near = false) {
-    GCA_TRY(pass.begin());
+  // passes on this mesh (the rows, and the columns of a two-sided
+  // operator, which do not depend on each other): one launch per level
+  // holds the jobs of all of them (job.mesh selects the pass's table entry);
+  // `fork_near` launches the near field once the passes' pools are allocated
+  // (an allocation can wait for all work on the device, the side stream's
+  // included)
+  int run_passes(std::initializer_list<BasisPass*> passes, bool fork_near) {
+    std::vector<AcaMesh> table;
+    for (BasisPass* p : passes) {
+      GCA_TRY(p->begin());
+      table.push_back(p->am);
+    }
     DevMem d_mesh, d_jobs;
     // room for every level's jobs at once: a reallocation between levels
     // would free device memory and so wait for the near-field stream
-    GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * (size_t)nc));
-    GCA_TRY(d_mesh.alloc(sizeof(AcaMesh)));
-    GCA_TRY_CUDA(cudaMemcpyAsync(d_mesh.p, &pass.am, sizeof(AcaMesh), cudaMemcpyHostToDevice, st));
+    GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * (size_t)nc * passes.size()));
+    GCA_TRY(upload(d_mesh, table, st));
     if (fork_near) GCA_TRY(near_field());
     std::vector<AcaJob> js;
     for (int L = h->depth; L >= 1; --L) {
       js.clear();
-      GCA_TRY(pass.jobs(L, 0, js));
+      int i = 0;
+      for (BasisPass* p : passes) GCA_TRY(p->jobs(L, i++, js));
       if (js.empty()) continue;
       GCA_TRY(aca.launch(js, d_jobs, d_mesh.as<AcaMesh>(), L, prm->aca_tol, tie, st));
-      GCA_TRY(pass.after());
+      for (BasisPass* p : passes) GCA_TRY(p->after());
     }
-    return pass.end();
+    for (BasisPass* p : passes) GCA_TRY(p->end());
+    return GCA_OK;
   }
 
   const gca_mesh* mesh;
@@ -2649,8 +2658,17 @@ int Builder::rows() {
     h->poff.assign(nc, 0);
     GCA_TRY(d_piv.alloc(sizeof(int)));
     GCA_TRY_CUDA(cudaStreamSynchronize(st));  // gj is a local
+  } else if (h->two_sided()) {
+    // columns: the double layer's own bases (op 1) or the Galerkin single
+    // layer's (op 2), in the same launches as the rows
+    auto rp = rows_pass();
+    BasisPass cp(*this, op == 1 ? 1 : 0,
+                 BasisOut{&h->rank2, &h->poff2, &h->voff2, &h->eoff2, &h->w_entries, &h->f_entries, &h->W64,
+                          &h->F64},
+                 d_piv2, d_rank2, piv2_used);
+    GCA_TRY(run_passes({rp.get(), &cp}, true));
   } else {
-    GCA_TRY(run_pass(*rows_pass(), true));
+    GCA_TRY(run_passes({rows_pass().get()}, true));
   }
   return GCA_OK;
 }
@@ -2904,13 +2922,7 @@ int Builder::finish(gca_h2** out) {
   h->rank_sum = h->xoff[nc];
   h->max_rank = *std::max_element(h->rank.begin(), h->rank.end());
   if (h->two_sided()) {
-    // columns: the double layer's own bases (op 1) or the Galerkin single
-    // layer's (op 2)
-    BasisPass pass(*this, op == 1 ? 1 : 0,
-                   BasisOut{&h->rank2, &h->poff2, &h->voff2, &h->eoff2, &h->w_entries, &h->f_entries, &h->W64,
-                            &h->F64},
-                   d_piv2, d_rank2, piv2_used);
-    GCA_TRY(run_pass(pass));
+    // the column bases were built with the rows (rows())
     h->xoff2.assign(nc + 1, 0);
     for (int c = 0; c < nc; ++c) h->xoff2[c + 1] = h->xoff2[c] + h->rank2[c];
     h->rank_sum2 = h->xoff2[nc];
