@@ -309,10 +309,11 @@ __device__ __forceinline__ Cand cand_shfl(const Cand& a, int off) {
   return o;
 }
 
-// shared memory of one CTA: residual rows, V^ rows, posts, u, v, w, the rows'
+// shared memory of one CTA: residual rows, posts, u, v, w, the rows'
 // triangles and indices, the columns' indices and the pivots' triangles
+// (V^ of the rows lives in a global scratch array of the launch)
 __host__ __device__ constexpr size_t aca_smem_bytes(int rpc_cap, int k2, int rmax_cap) {
-  return sizeof(double) * ((size_t)rpc_cap * k2 + (size_t)rpc_cap * rmax_cap +
+  return sizeof(double) * ((size_t)rpc_cap * k2 +
                            kAcaPosts * aca_post_doubles(k2, rmax_cap) + rpc_cap + k2 + rmax_cap) +
          sizeof(int) * (2 * (size_t)rpc_cap + k2 + rmax_cap);
 }
@@ -333,7 +334,7 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 template <int LC>
 __global__ void __launch_bounds__(kAcaThreads)
 k_aca(const AcaJob* __restrict__ jobs, const AcaMesh* __restrict__ meshes, int k, int rpc_cap, int rmax_cap,
-      double tol, double tie) {
+      double tol, double tie, double* __restrict__ wbuf) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -348,8 +349,10 @@ k_aca(const AcaJob* __restrict__ jobs, const AcaMesh* __restrict__ meshes, int k
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* S = reinterpret_cast<double*>(smem_raw);            // nr x k2, row-major (storage order)
-  double* W = S + (size_t)rpc_cap * k2;                       // nr x rmax, row-major: V^
-  double* posts = W + (size_t)rpc_cap * rmax_cap;             // kAcaPosts x post
+  // V^ of the CTA's rows (nr x rmax, row-major) in global memory: shared
+  // memory holds the residual rows only, so that two CTAs fit on an SM
+  double* W = wbuf + (size_t)blockIdx.x * rpc_cap * rmax_cap;
+  double* posts = S + (size_t)rpc_cap * k2;                   // kAcaPosts x post
   double* s_u = posts + kAcaPosts * aca_post_doubles(k2, rmax_cap);  // rpc_cap
   double* s_v = s_u + rpc_cap;                                // k2
   double* s_w = s_v + k2;                                     // rmax_cap
@@ -2033,6 +2036,14 @@ class AcaLauncher {
     GCA_TRY_CUDA(cudaFuncSetAttribute(kern_, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     return GCA_OK;
   }
+  // room for the V^ scratch of a level of the given rows (the clusters of a
+  // level cover at most `rows` rows, each job at most 2k columns, plus the
+  // rounding of every job up to its group's largest), so that the levels do
+  // not reallocate it (a reallocation frees device memory and so waits for
+  // every stream); launch() grows it where this bound falls short
+  int reserve_scratch(size_t rows, size_t jobs) {
+    return wbuf_.reserve(sizeof(double) * (rows + (size_t)GCA_MAX_LEAF * jobs) * 2 * (size_t)k_);
+  }
   size_t smem(int rows, int C) const {
     const int rpc = (rows + C - 1) / C;
     return aca_smem_bytes(rpc, 2 * k_, std::min(rows, 2 * k_));
@@ -2077,6 +2088,19 @@ class AcaLauncher {
       if (!fork_) GCA_TRY_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
       GCA_TRY_CUDA(cudaEventRecord(fork_, st));
     }
+    // V^ scratch of every CTA of the level: rpc_cap x rmax_cap per CTA, the
+    // groups one after the other (they run concurrently)
+    size_t wtotal = 0;
+    size_t woff[5] = {0, 0, 0, 0, 0};
+    for (int g = 0; g < 5; ++g) {
+      if (by_c[g].empty()) continue;
+      const int C = 1 << g;
+      int rows_cap = 1;
+      for (const auto& j : by_c[g]) rows_cap = std::max(rows_cap, j.rows);
+      woff[g] = wtotal;
+      wtotal += by_c[g].size() * C * (size_t)((rows_cap + C - 1) / C) * std::min(rows_cap, 2 * k_);
+    }
+    GCA_TRY(wbuf_.reserve(sizeof(double) * std::max<size_t>(wtotal, 1)));
     std::unique_ptr<PhaseScope> level_scope;
     if (!profile_detail()) {
       level_scope = std::make_unique<PhaseScope>("green_aca", st);
@@ -2098,7 +2122,7 @@ class AcaLauncher {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)(by_c[g].size() * C));
       cfg.blockDim = dim3(kAcaThreads);
-      cfg.dynamicSmemBytes = aca_smem_bytes(rpc_cap, 2 * k_, rmax_cap);
+      cfg.dynamicSmemBytes = smem(rows_cap, C);
       cfg.stream = gs;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -2112,7 +2136,7 @@ class AcaLauncher {
         if (profile_detail())
           ps = std::make_unique<PhaseScope>("green_aca.L" + std::to_string(level) + ".c" + std::to_string(C), gs);
         GCA_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern_, (const AcaJob*)(d_jobs.as<AcaJob>() + at), d_mesh, k_,
-                                        rpc_cap, rmax_cap, tol, tie));
+                                        rpc_cap, rmax_cap, tol, tie, wbuf_.as<double>() + woff[g]));
       }
       if (fork) {
         GCA_TRY_CUDA(cudaEventRecord(join_[g], gs));
@@ -2133,7 +2157,8 @@ class AcaLauncher {
   cudaEvent_t join_[5] = {};
   cudaEvent_t fork_ = nullptr;
   size_t budget_ = 0;
-  void (*kern_)(const AcaJob*, const AcaMesh*, int, int, int, double, double) = nullptr;
+  void (*kern_)(const AcaJob*, const AcaMesh*, int, int, int, double, double, double*) = nullptr;
+  DevMem wbuf_;  // V^ scratch of the launches (grow-only)
 };
 
 }  // namespace
@@ -2262,6 +2287,7 @@ class Builder {
     // room for every level's jobs at once: a reallocation between levels
     // would free device memory and so wait for the near-field stream
     GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * (size_t)nc * passes.size()));
+    GCA_TRY(aca.reserve_scratch((size_t)n * passes.size(), (size_t)nc * passes.size()));
     GCA_TRY(upload(d_mesh, table, st));
     if (fork_near) GCA_TRY(near_field());
     std::vector<AcaJob> js;
@@ -3176,8 +3202,12 @@ int build_group(int count, const gca_mesh* meshes, const gca_tree* trees, const 
   for (auto& p : passes) table.push_back(p->am);
   DevMem d_table, d_jobs;
   GCA_TRY(upload(d_table, table, st));
-  size_t all_clusters = 0;
-  for (auto& b : bs) all_clusters += (size_t)b->nc;
+  size_t all_clusters = 0, all_rows = 0;
+  for (auto& b : bs) {
+    all_clusters += (size_t)b->nc;
+    all_rows += (size_t)b->n;
+  }
+  GCA_TRY(bs[0]->aca.reserve_scratch(all_rows, all_clusters));
   GCA_TRY(d_jobs.reserve(sizeof(AcaJob) * all_clusters));  // no reallocation between levels
   // the near fields, once every allocation before the levels is made
   for (auto& b : bs) GCA_TRY(b->near_field());
