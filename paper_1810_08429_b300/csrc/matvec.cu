@@ -138,6 +138,9 @@ struct LaunchArgs {
   int nslots;
   const int2* chain_map;       // claim -> (slot, claim within the slot); null: one slot
   const int2* free_map;
+  int map_rep;                 // > 1: the maps hold one entry per group, and claim c is
+                               // chunk c % map_rep of entry c / map_rep (every slot has
+                               // map_rep chunks)
   int64_t total;               // chain claims over all slots
   int64_t total_free;          // free claims over all slots
   unsigned long long* next;    // chain claim counter
@@ -777,9 +780,10 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
     int64_t loc = c;
     const int2* map = chain ? L.chain_map : L.free_map;
     if (map) {
-      const int2 m = map[c];
+      const int rep = L.map_rep;
+      const int2 m = map[rep > 1 ? c / rep : c];
       s = m.x;
-      loc = m.y;
+      loc = rep > 1 ? (int64_t)m.y * rep + c % rep : m.y;
     }
     const SlotArgs<TV>& sa = slots[s];
     const int64_t g = loc / sa.nchunk + (chain ? 0 : sa.n_chain);
@@ -1731,10 +1735,8 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   std::vector<int> nchunk(count);
   int64_t work = 0, free_work = 0;
   int max_n = 0;
-  bool one_chunk = true;
   for (int i = 0; i < count; ++i) {
     nchunk[i] = (nrhs[i] + RC - 1) / RC;
-    one_chunk = one_chunk && nchunk[i] == 1;
     work += hs[i]->n_chain[dir] * nchunk[i];
     free_work += hs[i]->n_free[dir] * nchunk[i];
     max_n = std::max(max_n, hs[i]->n * nrhs[i]);
@@ -1751,8 +1753,13 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
     a.xp = reinterpret_cast<TV*>(base + o_xp[i]);
   }
   const bool inline_slots = count <= kInlineSlots;
-  const bool pre_maps = count > 1 && one_chunk && pc.maps1[dir].p && pc.maps1_chain[dir] == work &&
-                        pc.maps1_free[dir] == free_work;
+  // the batch's one-chunk claim orders serve every product whose meshes all
+  // take the same number of chunks: each group's claim is repeated per chunk
+  bool same_chunks = true;
+  for (int i = 1; i < count; ++i) same_chunks = same_chunks && nchunk[i] == nchunk[0];
+  const int rep = count > 0 ? nchunk[0] : 1;
+  const bool pre_maps = count > 1 && same_chunks && pc.maps1[dir].p && pc.maps1_chain[dir] * rep == work &&
+                        pc.maps1_free[dir] * rep == free_work;
   const bool dev_maps = count > 1 && !pre_maps;
   SlotPack<TV> pack;
   std::memset(&pack, 0, sizeof(pack));
@@ -1760,11 +1767,13 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   L.slots = nullptr;
   L.chain_map = nullptr;
   L.free_map = nullptr;
+  L.map_rep = 1;
   if (inline_slots)
     for (int i = 0; i < count; ++i) pack.s[i] = sl[i];
   if (pre_maps) {
     L.chain_map = pc.maps1[dir].as<int2>();
-    L.free_map = L.chain_map + work;
+    L.free_map = L.chain_map + work / rep;
+    L.map_rep = rep;
   }
   const SlotArgs<TV>* d_slots = nullptr;
   if (!inline_slots || dev_maps) {
@@ -2243,6 +2252,7 @@ int launch_noalloc_rc(const gca_h2* h, int R, const void* x, int64_t ldx, void* 
   LaunchArgs L;
   L.slots = nullptr;  // the descriptor travels inline as a kernel parameter
   L.nslots = 1;
+  L.map_rep = 1;
   L.chain_map = nullptr;
   L.free_map = nullptr;
   L.total = a.n_chain * a.nchunk;

@@ -48,6 +48,22 @@ def test_batch_f64_matches_oracle(batch_case, transpose):
     assert b.status() == 0
 
 
+@pytest.mark.parametrize("transpose", [False, True])
+@pytest.mark.parametrize("prec,R", [("f64", 12), ("f32", 32)])
+def test_batch_equal_chunks(batch_case, prec, R, transpose):
+    """Every mesh with the same number of right-hand-side chunks (3 of width 4
+    in float64, 2 of width 16 in float32): the claim orders come from the
+    batch's one-chunk orders, each claim repeated per chunk."""
+    gca, b, meshes, refs = batch_case
+    dt = torch.float64 if prec == "f64" else torch.float32
+    xs = [synth.normal_rhs(len(t), R, seed=21 + i) for i, (_, t) in enumerate(meshes)]
+    ys = b.matvec([torch.from_numpy(x).to(dt).cuda() for x in xs], prec, transpose=transpose)
+    for y, x, ref in zip(ys, xs, refs):
+        want = oh2.matvec_t(ref, x) if transpose else oh2.matvec(ref, x)
+        assert rel_cols(y.double().cpu().numpy(), want) <= (1e-10 if prec == "f64" else 1e-6)
+    assert b.status() == 0
+
+
 @pytest.mark.parametrize("prec", ["f32", "bf16"])
 def test_batch_matches_single(batch_case, prec):
     gca, b, meshes, refs = batch_case
