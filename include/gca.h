@@ -59,7 +59,9 @@ typedef enum {
   GCA_ERR_OOM = -3,         /* device or host allocation failed           */
   GCA_ERR_NUMERIC = -4,     /* NaN/Inf in the input or in an intermediate */
   GCA_ERR_TIMEOUT = -5,     /* a bounded device-side wait expired         */
-  GCA_ERR_UNSUPPORTED = -6  /* valid request outside the built limits     */
+  GCA_ERR_UNSUPPORTED = -6, /* valid request outside the built limits     */
+  GCA_ERR_IO = -7           /* a file could not be read or written, or is
+                               not a complete checkpoint                  */
 } gca_status;
 
 /* Surface mesh (Sect. 2): nv vertices, nt flat triangles.  vertices is
@@ -569,6 +571,36 @@ int gca_batch_clear_status(const gca_h2_batch* b);
  * NUMERIC (non-finite coefficient), OOM, CUDA. */
 int gca_h2_import(const gca_tree* tree, int32_t nt, int32_t nfar, int32_t nnear, const gca_host_dump* dump,
                   uint32_t flags, void* stream, gca_h2** out);
+
+/* Checkpoint of a handle (the paper has no counterpart; a service so that
+ * a program can skip the construction): gca_h2_save writes the cluster tree
+ * and the representation of Sect. 4 as gca_h2_export gives it (ranks,
+ * pivots, block lists, V, E, S, N in float64) with the construction's
+ * parameters and counts to the file `path`, and gca_h2_load rebuilds a
+ * device handle from such a file through gca_h2_import, whose products
+ * equal those of the saved handle (the float32 and bfloat16 copies are
+ * rounded again from the float64 coefficients, to the same values).
+ *
+ * gca_h2_save: handles of gca_build, gca_build_batch, gca_h2_import,
+ * gca_build_p1 and gca_build_p1_curved (one basis serving rows and
+ * columns); the two-sided and single-level handles give UNSUPPORTED, as
+ * does a handle built with GCA_DROP_EXPORT.  The file is written under
+ * `path` + ".tmp" and renamed to `path`, replacing it; on failure nothing
+ * is left under either name.  It is read back on a host of the same byte
+ * order.  Synchronises the device.  Errors: INVALID_ARG (NULL handle, empty
+ * path), UNSUPPORTED, OOM, IO, CUDA.
+ *
+ * gca_h2_load: `flags` selects the kept precisions as in gca_params.flags;
+ * the other parameters and the stats' k and n_singular are those of the
+ * saved handle.  A loaded nodal-basis handle multiplies like the saved one
+ * (its indices are the vertices).  The file's magic, sizes, length and
+ * checksum are checked before anything is allocated on the device.  The
+ * handle is created on the current device; synchronises `stream`.  Errors:
+ * INVALID_ARG (NULL out, empty path, a file whose representation the import
+ * rejects), IO (missing, unreadable, truncated or corrupted file), NUMERIC,
+ * OOM, CUDA. */
+int gca_h2_save(const gca_h2* h, const char* path);
+int gca_h2_load(const char* path, uint32_t flags, void* stream, gca_h2** out);
 
 int gca_h2_stats(const gca_h2* h, gca_stats* out);
 /* Host copy of a handle in the layout of gca_host_dump.  V, E, S and N are

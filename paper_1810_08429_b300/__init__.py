@@ -129,6 +129,8 @@ def _load():
                                          ctypes.c_int32, ctypes.POINTER(_Dump), ctypes.c_uint32, vp,
                                          ctypes.POINTER(vp)]),
         "gca_test_hook": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int64]),
+        "gca_h2_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "gca_h2_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_uint32, vp, ctypes.POINTER(vp)]),
         "gca_build_double_layer": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
                                                   ctypes.POINTER(_Params), vp, ctypes.POINTER(vp)]),
         "gca_build_collocation": (ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Tree),
@@ -158,7 +160,7 @@ def _load():
 lib = _load()
 
 
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_IO = 0, -1, -2, -3, -4, -5, -6, -7
 
 
 class GCAError(RuntimeError):
@@ -369,6 +371,11 @@ class H2:
             d["near"] = d["near"].reshape(-1, 2)
         return d
 
+    def save(self, path):
+        """Write a checkpoint of this handle to `path` (gca_h2_save); ``load``
+        reads it back."""
+        _check(lib.gca_h2_save(self._h, os.fsencode(path)), "gca_h2_save")
+
     def column_stats(self):
         """Sizes of the column side (gca_h2_column_stats)."""
         s = _ColStats()
@@ -482,6 +489,14 @@ def import_h2(tree, n, rep, flags=0, stream=None):
     h = ctypes.c_void_p(None)
     _check(lib.gca_h2_import(ctypes.byref(t), n, nfar, nnear, ctypes.byref(dump), flags,
                              _stream_ptr(stream), ctypes.byref(h)), "gca_h2_import")
+    return H2(h.value)
+
+
+def load(path, flags=0, stream=None):
+    """gca_h2_load: a handle on the current CUDA device from a checkpoint
+    written by ``H2.save``."""
+    h = ctypes.c_void_p(None)
+    _check(lib.gca_h2_load(os.fsencode(path), flags, _stream_ptr(stream), ctypes.byref(h)), "gca_h2_load")
     return H2(h.value)
 
 

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgca.so")
-SOURCES = ["tree.cpp", "build.cu", "matvec.cu", "api.cu", "profile.cu", "import.cpp"]
+SOURCES = ["tree.cpp", "build.cu", "matvec.cu", "api.cu", "profile.cu", "import.cpp", "checkpoint.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -557,6 +557,7 @@ const char* gca_strerror(int status) {
     case GCA_ERR_NUMERIC: return "non-finite value";
     case GCA_ERR_TIMEOUT: return "device wait timed out";
     case GCA_ERR_UNSUPPORTED: return "unsupported size or option";
+    case GCA_ERR_IO: return "file error or not a checkpoint";
     default: return "unknown status";
   }
 }

@@ -199,3 +199,67 @@ def test_test_hooks_reject_unknown_names():
     assert e.value.status == gca.ERR_INVALID_ARG
     for name in ("wait_cycles", "stall_chain", "fail_alloc", "device_skew"):
         gca.test_hook(name, 0)
+
+
+class _CheckpointHeader(ctypes.Structure):
+    """The header of a gca_h2_save file (after its 8-byte magic)."""
+    _fields_ = [("n", ctypes.c_int32), ("nc", ctypes.c_int32), ("nfar", ctypes.c_int32),
+                ("nnear", ctypes.c_int32), ("op", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("m", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rank_sum", ctypes.c_int64),
+                ("v_entries", ctypes.c_int64), ("e_entries", ctypes.c_int64), ("s_entries", ctypes.c_int64),
+                ("n_entries", ctypes.c_int64), ("n_singular", ctypes.c_int64 * 4), ("params", gca._Params)]
+
+
+def _fnv1a(data):
+    h = 1469598103934665603
+    for b in data:
+        h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def test_checkpoint_files_checked_on_host(tmp_path):
+    """gca_h2_load reads the documented layout and checks magic, length and
+    checksum before any device work: a file in that layout whose
+    representation is inconsistent (root rank 3) reaches the import's
+    validation (INVALID_ARG); the same file truncated, with a flipped byte or
+    a wrong magic, and a missing file, give ERR_IO."""
+    from oracle import gca as ogca
+    from oracle.params import Params as OParams
+    from oracle_dump import oracle_dump
+    v, t = synth.mesh_for_config("sphere80")
+    h2o = ogca.build_h2(v, t, OParams(leaf_size=16, eta=2.0, box_gauss_m=2, aca_tol=1e-4, sauter_q=3))
+    d = oracle_dump(h2o)
+    tr = h2o.tree
+    d["rank"] = d["rank"].copy()
+    d["rank"][0] = 3
+    hd = _CheckpointHeader(n=len(t), nc=len(tr["begin"]), nfar=len(d["far"]), nnear=len(d["near"]), op=0,
+                           k=0, m=0, rank_sum=len(d["pivots"]), v_entries=len(d["V"]), e_entries=len(d["E"]),
+                           s_entries=len(d["S"]), n_entries=len(d["N"]))
+    parts = [b"GCAH2CK1", bytes(hd)]
+    for key in ("perm", "begin", "end", "child0", "child1", "level"):
+        parts.append(np.asarray(tr[key], dtype=np.int32).tobytes())
+    for key in ("rank", "pivots", "far", "near"):
+        parts.append(np.asarray(d[key], dtype=np.int32).tobytes())
+    for key in ("V", "E", "S", "N"):
+        parts.append(np.asarray(d[key], dtype=np.float64).tobytes())
+    body = b"".join(parts)
+    data = body + _fnv1a(body).to_bytes(8, "little")
+
+    def status_of(blob, name):
+        p = tmp_path / name
+        p.write_bytes(blob)
+        with pytest.raises(gca.GCAError) as e:
+            gca.load(str(p))
+        return e.value.status, str(e.value)
+
+    st, msg = status_of(data, "inconsistent.gca")
+    assert st == gca.ERR_INVALID_ARG and "gca_h2_import" in msg and "rank" in msg, msg
+    assert status_of(data[:-9], "truncated.gca")[0] == gca.ERR_IO
+    flipped = bytearray(data)
+    flipped[len(data) // 2] ^= 0x10
+    st, msg = status_of(bytes(flipped), "flipped.gca")
+    assert st == gca.ERR_IO and "checksum" in msg
+    assert status_of(b"GCAH2CK0" + data[8:], "magic.gca")[0] == gca.ERR_IO
+    with pytest.raises(gca.GCAError) as e:
+        gca.load(str(tmp_path / "missing.gca"))
+    assert e.value.status == gca.ERR_IO
