@@ -48,7 +48,13 @@ constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
 struct __align__(32) P4 {
   double x, y, z, w;
 };
+// threads of a cross approximation CTA: 512 for jobs on clusters of 2 or 4
+// CTAs (about 60-150 rows per CTA: more warps in flight hide the update's
+// latency), 256 otherwise (a few rows per warp on 8 or 16 CTAs, where the
+// per-pivot barriers and reductions over more warps cost more than they hide)
 constexpr int kAcaThreads = 256;
+constexpr int kAcaThreadsWide = 512;
+inline bool aca_wide(int C) { return C == 2 || C == 4; }
 constexpr int kStatusNumeric = 1;
 constexpr int kStatusOverflow = 2;
 
@@ -331,8 +337,8 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
 }
 
 // LC: columns of a lane in the row updates (2k <= 32 LC)
-template <int LC>
-__global__ void __launch_bounds__(kAcaThreads)
+template <int LC, int NT>
+__global__ void __launch_bounds__(NT)
 k_aca(const AcaJob* __restrict__ jobs, const AcaMesh* __restrict__ meshes, int k, int rpc_cap, int rmax_cap,
       double tol, double tie, double* __restrict__ wbuf) {
   namespace cg = cooperative_groups;
@@ -2028,12 +2034,20 @@ class AcaLauncher {
     int optin = 0;
     GCA_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     GCA_TRY_CUDA(cudaDeviceGetAttribute(&sms_, cudaDevAttrMultiProcessorCount, dev));
-    kern_ = 2 * k <= 128 ? k_aca<4> : (2 * k <= 192 ? k_aca<6> : k_aca<14>);
-    cudaFuncAttributes fa{};
-    GCA_TRY_CUDA(cudaFuncGetAttributes(&fa, kern_));
-    budget_ = (size_t)optin - fa.sharedSizeBytes;
-    GCA_TRY_CUDA(cudaFuncSetAttribute(kern_, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget_));
-    GCA_TRY_CUDA(cudaFuncSetAttribute(kern_, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    kern_[0] = 2 * k <= 128 ? k_aca<4, kAcaThreads>
+                            : (2 * k <= 192 ? k_aca<6, kAcaThreads> : k_aca<14, kAcaThreads>);
+    kern_[1] = 2 * k <= 128 ? k_aca<4, kAcaThreadsWide>
+                            : (2 * k <= 192 ? k_aca<6, kAcaThreadsWide> : k_aca<14, kAcaThreadsWide>);
+    budget_ = (size_t)optin;
+    for (auto* kern : kern_) {
+      cudaFuncAttributes fa{};
+      GCA_TRY_CUDA(cudaFuncGetAttributes(&fa, kern));
+      budget_ = std::min(budget_, (size_t)optin - fa.sharedSizeBytes);
+    }
+    for (auto* kern : kern_) {
+      GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)budget_));
+      GCA_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    }
     return GCA_OK;
   }
   // room for the V^ scratch of a level of the given rows (the clusters of a
@@ -2121,7 +2135,8 @@ class AcaLauncher {
       const int rmax_cap = std::min(rows_cap, 2 * k_);
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)(by_c[g].size() * C));
-      cfg.blockDim = dim3(kAcaThreads);
+      const int wide = aca_wide(C) ? 1 : 0;
+      cfg.blockDim = dim3(wide ? kAcaThreadsWide : kAcaThreads);
       cfg.dynamicSmemBytes = smem(rows_cap, C);
       cfg.stream = gs;
       cudaLaunchAttribute attr[1];
@@ -2135,7 +2150,7 @@ class AcaLauncher {
         std::unique_ptr<PhaseScope> ps;
         if (profile_detail())
           ps = std::make_unique<PhaseScope>("green_aca.L" + std::to_string(level) + ".c" + std::to_string(C), gs);
-        GCA_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern_, (const AcaJob*)(d_jobs.as<AcaJob>() + at), d_mesh, k_,
+        GCA_TRY_CUDA(cudaLaunchKernelEx(&cfg, kern_[wide], (const AcaJob*)(d_jobs.as<AcaJob>() + at), d_mesh, k_,
                                         rpc_cap, rmax_cap, tol, tie, wbuf_.as<double>() + woff[g]));
       }
       if (fork) {
@@ -2157,7 +2172,7 @@ class AcaLauncher {
   cudaEvent_t join_[5] = {};
   cudaEvent_t fork_ = nullptr;
   size_t budget_ = 0;
-  void (*kern_)(const AcaJob*, const AcaMesh*, int, int, int, double, double, double*) = nullptr;
+  void (*kern_[2])(const AcaJob*, const AcaMesh*, int, int, int, double, double, double*) = {nullptr, nullptr};
   DevMem wbuf_;  // V^ scratch of the launches (grow-only)
 };
 
