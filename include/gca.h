@@ -458,8 +458,14 @@ int h2_matvec_noalloc(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* 
 
 /* y = G_H2^T x, same conventions as h2_matvec: the representation of
  * Sect. 4 transposed, y|sigma-hat = sum V_sigma S_{tau sigma}^* V_tau^* x|tau-hat
- * plus sum N_{tau sigma}^* x|tau-hat (for the symmetric Galerkin matrix of
- * Eq. (1) it equals h2_matvec up to the order of floating-point sums). */
+ * plus sum N_{tau sigma}^* x|tau-hat.  A handle of a symmetric operator
+ * (gca_build, gca_build_batch, gca_build_single_level, gca_build_p1,
+ * gca_build_p1_curved: G of Eq. (1), whose coupling blocks come in mirrored
+ * pairs S_{sigma tau} = S_{tau sigma}^T, evaluated once) keeps no transposed
+ * couplings and no transposed plan: this runs h2_matvec's plan with the
+ * mirrored near-field blocks transposed (their singular rules are not
+ * symmetric in the two triangles, so they are kept).  Handles from
+ * gca_h2_import and gca_h2_load keep both orientations. */
 int h2_matvec_transpose(const gca_h2* h, gca_prec prec, int32_t nrhs, const void* x,
                         int64_t ldx, void* y, int64_t ldy, void* stream);
 

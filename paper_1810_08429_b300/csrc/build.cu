@@ -864,8 +864,28 @@ __global__ void k_from_panel(const PanelJob* __restrict__ jobs, const double* __
   }
 }
 
+// Does every block (t[b], s[b]) of a list have its mirror (s[b], t[b]) in
+// the list?  If so, mir[b] = index of the mirror.
+bool blocks_mirrored(const std::vector<int>& t, const std::vector<int>& s, std::vector<int>& mir) {
+  const size_t n = t.size();
+  std::vector<std::pair<std::pair<int, int>, int>> a(n);
+  for (size_t i = 0; i < n; ++i) a[i] = {{t[i], s[i]}, (int)i};
+  std::sort(a.begin(), a.end());
+  mir.assign(n, -1);
+  for (size_t i = 0; i < n; ++i) {
+    const std::pair<int, int> want{s[i], t[i]};
+    auto it = std::lower_bound(a.begin(), a.end(), std::make_pair(want, INT_MIN));
+    if (it == a.end() || it->first != want) return false;
+    mir[i] = it->second;
+  }
+  return true;
+}
+
 // Every stored block in panel form: f(kind, index, rows, columns, transposed)
 // for V, V^T, E, E^T, S, S^T, N, N^T (index PanelKind), in storage order.
+// A mirrored handle stores no S^T; its N^T array holds, at block b's
+// offset, N_{mirror(b)}^T (the shape of N_b), read by the product's own plan
+// in the transposed product.
 template <typename F>
 void for_each_panel(const gca_h2* h, F&& f) {
   const int nc = h->nc;
@@ -890,13 +910,16 @@ void for_each_panel(const gca_h2* h, F&& f) {
                    : h->op == 4   ? h->end[h->far_s[b]] - h->begin[h->far_s[b]]
                                   : h->rank[h->far_s[b]];
     f(kS, b, rt, rs, 0);
-    f(kSt, b, rs, rt, 1);
+    if (!h->mirrored) f(kSt, b, rs, rt, 1);
   }
   for (int b = 0; b < nnear; ++b) {
     const int t = h->near_t[b], s = h->near_s[b];
     const int mt = h->end[t] - h->begin[t], ms = h->end[s] - h->begin[s];
     f(kN, b, mt, ms, 0);
-    f(kNt, b, ms, mt, 1);
+    if (h->mirrored)
+      f(kNt, b, mt, ms, 1);
+    else
+      f(kNt, b, ms, mt, 1);
   }
   if (!h->two_sided()) return;
   // column bases W and transfers F (their own ranks r')
@@ -973,7 +996,8 @@ int make_panels(gca_h2* h, DevMem& jobs_buf, std::vector<PanelJob>& host_jobs, c
       const int64_t src = (kind == kV || kind == kVt)   ? h->voff[idx]
                           : (kind == kE || kind == kEt) ? h->eoff[idx]
                           : (kind == kS || kind == kSt) ? h->soff[idx]
-                          : (kind == kN || kind == kNt) ? h->noff[idx]
+                          : kind == kN                  ? h->noff[idx]
+                          : kind == kNt ? h->noff[h->mirrored ? h->near_mirror[idx] : idx]
                           : (kind == kW || kind == kWt) ? h->voff2[idx]
                                                         : h->eoff2[idx];
       host_jobs.push_back({src, h->panel_off[kind][idx], m, k, trans, 0});
@@ -2500,6 +2524,14 @@ int Builder::prepare() {
   }
   block_tree(h->child0, h->child1, box, diam, prm->eta, h->far_t, h->far_s, h->near_t, h->near_s);
   GCA_TRY(upload(d_diam, diam, st));
+  // the symmetric operators (G of Eq. 1 in either basis, its single-level
+  // GCA) on a block tree whose blocks all come with their mirrors
+  {
+    std::vector<int> far_mirror;
+    h->mirrored = (op == 0 || op == 3 || p1) && blocks_mirrored(h->far_t, h->far_s, far_mirror) &&
+                  blocks_mirrored(h->near_t, h->near_s, h->near_mirror);
+    if (!h->mirrored) h->near_mirror.clear();
+  }
 
   // box quadrature
   GCA_TRY(d_zq.alloc(sizeof(P4) * (size_t)nc * k));
@@ -3163,7 +3195,7 @@ int Builder::finish(gca_h2** out) {
     ps_conv.launches(kPanelKinds);
     GCA_TRY(make_panels(h.get(), d_pjobs, panel_host_jobs, st));
   }
-  plan_direction(h.get(), 1, plan.get());
+  if (!h->mirrored) plan_direction(h.get(), 1, plan.get());
 
   GCA_TRY(finish_plan(h.get(), plan.get(), st));
   GCA_TRY_CUDA(cudaStreamSynchronize(st));

@@ -278,6 +278,20 @@ struct gca_h2 {
   // (the nodal basis on flat and on curved triangles) are one-sided like
   // op 0 with the vertices as indices.
   int op = 0;
+  // Built symmetric operator (the single layer G in either basis, and its
+  // single-level GCA): one basis per cluster and every block (tau, sigma)
+  // has its mirror (sigma, tau).  The couplings of a mirrored pair are
+  // evaluated once (S_{sigma tau} = S_{tau sigma}^T exactly), so the
+  // transposed product runs the product's own plan and S panels; only the
+  // near field, whose mirrored blocks are integrated separately (singular
+  // rules are not symmetric in the two triangles), gets a second panel
+  // array: at the offset of block b, N_{mirror(b)}^T, so that the plan's
+  // near-field segments read the transposed entries.  No S^T panels and no
+  // transposed plan are kept.  Imported handles keep both orientations.
+  bool mirrored = false;
+  std::vector<int> near_mirror;  // mirrored: index of each near block's mirror
+  // the plan direction that serves a product of direction `dir`
+  int served_dir(int dir) const { return mirrored ? 0 : dir; }
   std::vector<int> rank2;              // r'_sigma (op 1)
   std::vector<int64_t> xoff2;
   int64_t rank_sum2 = 0;

@@ -1574,6 +1574,7 @@ int finish_plan(gca_h2* h, PlanJob* job, cudaStream_t st) {
     GCA_TRY(upload(h->d_iperm, iperm, st));
   }
   for (int dir = 0; dir < 2; ++dir) {
+    if (h->served_dir(dir) != dir) continue;  // mirrored: no transposed plan
     if (!job->done[dir]) plan_direction(h, dir, job);
     DirPlan& P = job->p[dir];
     if (P.status != GCA_OK) {
@@ -1634,10 +1635,13 @@ void merge_claims(const gca_h2* const* hs, int count, int dir, const std::vector
 
 template <typename T, typename TN, typename TV>
 void fill_slot(SlotArgs<TV>& a, const gca_h2* h, int dir, int R, int RC, const void* x, int64_t ldx,
-               void* y, int64_t ldy) {
+               void* y, int64_t ldy, bool trans = false) {
   const DevMem* P = sizeof(T) == 8 ? h->P64 : (sizeof(T) == 4 ? h->P32 : h->P16);
   const DevMem* PN = sizeof(TN) == 8 ? h->P64 : h->P32;
   for (int q = 0; q < kPanelKinds; ++q) a.A[q] = (q == kN || q == kNt) ? PN[q].p : P[q].p;
+  // a mirrored handle's transposed product: the product's plan, whose
+  // near-field segments then read N_{mirror(b)}^T at block b's offset
+  if (trans && h->mirrored) a.A[kN] = PN[kNt].p;
   a.segs = h->d_segs[dir].as<MvSeg>();
   a.n_chain = h->n_chain[dir];
   a.n_free = h->n_free[dir];
@@ -1705,11 +1709,11 @@ int launch_persistent(const LaunchArgs& L, const SlotPack<TV>& pack, int64_t uni
 // descriptors (and claim orders) in the device cache of the precision and
 // direction, uploaded when the arguments change.
 template <typename T, typename TN, typename TA, typename TV, int RC>
-int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, const void* const* x,
+int launch_rc(const gca_h2* const* hs, int count, int dir, bool trans, const int32_t* nrhs, const void* const* x,
               const int64_t* ldx, void* const* y, const int64_t* ldy, ProductCache& pc, int* status,
               cudaStream_t st) {
   const char* pn = sizeof(T) == 8 ? ".f64" : (sizeof(T) == 4 ? ".f32" : ".bf16");
-  PhaseScope ps(std::string("mv_persistent") + pn + (dir ? ".T" : ""), st);
+  PhaseScope ps(std::string("mv_persistent") + pn + (trans ? ".T" : ""), st);
   ps.launches(3);
   DevMem& ws = pc.ws;
   std::vector<SlotArgs<TV>> sl(count);
@@ -1745,7 +1749,7 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   unsigned char* base = ws.as<unsigned char>();
   for (int i = 0; i < count; ++i) {
     SlotArgs<TV>& a = sl[i];
-    fill_slot<T, TN, TV>(a, hs[i], dir, nrhs[i], RC, x[i], ldx[i], y[i], ldy[i]);
+    fill_slot<T, TN, TV>(a, hs[i], dir, nrhs[i], RC, x[i], ldx[i], y[i], ldy[i], trans);
     a.xh = reinterpret_cast<TV*>(base + o_xh[i]);
     a.yh = reinterpret_cast<TV*>(base + o_yh[i]);
     a.yp = reinterpret_cast<TV*>(base + o_yp[i]);
@@ -1777,7 +1781,7 @@ int launch_rc(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, 
   }
   const SlotArgs<TV>* d_slots = nullptr;
   if (!inline_slots || dev_maps) {
-    DescCache& dc = pc.desc[(sizeof(T) == 8 ? 0 : (sizeof(T) == 4 ? 1 : 2)) * 2 + dir];
+    DescCache& dc = pc.desc[(sizeof(T) == 8 ? 0 : (sizeof(T) == 4 ? 1 : 2)) * 2 + (trans ? 1 : 0)];
     size_t doff = up256(sizeof(SlotArgs<TV>) * count);
     const size_t o_cmap = doff;
     if (dev_maps) doff += up256(sizeof(int2) * (size_t)std::max<int64_t>(work, 1));
@@ -1890,7 +1894,7 @@ int tuned_width(int prec, int dir, int R, int64_t rows) {
 }
 
 template <typename T, typename TN, typename TA, typename TV>
-int launch(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, const void* const* x,
+int launch(const gca_h2* const* hs, int count, int dir, bool trans, const int32_t* nrhs, const void* const* x,
            const int64_t* ldx, void* const* y, const int64_t* ldy, ProductCache& pc, int* status,
            cudaStream_t st) {
   int R = 1;
@@ -1904,11 +1908,11 @@ int launch(const gca_h2* const* hs, int count, int dir, const int32_t* nrhs, con
   if (rc == 0) rc = tuned_width(prec, dir, R, rows);
   if (rc == 0) rc = default_width(R, prec);
   switch (rc) {
-    case 16: return launch_rc<T, TN, TA, TV, 16>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
-    case 8: return launch_rc<T, TN, TA, TV, 8>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
-    case 4: return launch_rc<T, TN, TA, TV, 4>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
-    case 2: return launch_rc<T, TN, TA, TV, 2>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
-    default: return launch_rc<T, TN, TA, TV, 1>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+    case 16: return launch_rc<T, TN, TA, TV, 16>(hs, count, dir, trans, nrhs, x, ldx, y, ldy, pc, status, st);
+    case 8: return launch_rc<T, TN, TA, TV, 8>(hs, count, dir, trans, nrhs, x, ldx, y, ldy, pc, status, st);
+    case 4: return launch_rc<T, TN, TA, TV, 4>(hs, count, dir, trans, nrhs, x, ldx, y, ldy, pc, status, st);
+    case 2: return launch_rc<T, TN, TA, TV, 2>(hs, count, dir, trans, nrhs, x, ldx, y, ldy, pc, status, st);
+    default: return launch_rc<T, TN, TA, TV, 1>(hs, count, dir, trans, nrhs, x, ldx, y, ldy, pc, status, st);
   }
 }
 
@@ -1982,14 +1986,21 @@ int launch_any(const gca_h2* const* hs, int count, gca_prec prec, bool trans, co
       return GCA_ERR_UNSUPPORTED;
     }
   }
-  const int dir = trans ? 1 : 0;
+  // plan direction: a mirrored (symmetric) handle serves G^T x with the
+  // plan of G x (and its transposed near-field panels)
+  const int dir = hs[0]->served_dir(trans ? 1 : 0);
+  for (int i = 1; i < count; ++i)
+    if (hs[i]->served_dir(trans ? 1 : 0) != dir) {
+      set_error("h2_matvec: a launch mixes symmetric and non-symmetric handles");
+      return GCA_ERR_UNSUPPORTED;
+    }
   switch (prec) {
     case GCA_F64:
-      return launch<double, double, double, double>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+      return launch<double, double, double, double>(hs, count, dir, trans, nrhs, x, ldx, y, ldy, pc, status, st);
     case GCA_F32:
-      return launch<float, float, float, float>(hs, count, dir, nrhs, x, ldx, y, ldy, pc, status, st);
+      return launch<float, float, float, float>(hs, count, dir, trans, nrhs, x, ldx, y, ldy, pc, status, st);
     case GCA_BF16:
-      return launch<__nv_bfloat16, float, float, float>(hs, count, dir, nrhs, x, ldx, y, ldy, pc,
+      return launch<__nv_bfloat16, float, float, float>(hs, count, dir, trans, nrhs, x, ldx, y, ldy, pc,
                                                         status, st);
   }
   set_error("h2_matvec: unknown precision");
@@ -2006,6 +2017,7 @@ int prepare_batch(gca_h2_batch* b, cudaStream_t st) {
   std::vector<const gca_h2*> hs(b->h.begin(), b->h.end());
   std::vector<int> nchunk(count, 1);
   for (int dir = 0; dir < 2; ++dir) {
+    if (hs[0]->served_dir(dir) != dir) continue;  // mirrored: the transposed product runs plan 0
     std::vector<int2> cmap, fmap;
     merge_claims(hs.data(), count, dir, nchunk, cmap, fmap);
     cmap.insert(cmap.end(), fmap.begin(), fmap.end());

@@ -146,6 +146,42 @@ def test_stats_consistent(gpu_1280, h2_1280):
     assert s["n_singular"][3] == 1280 and s["n_singular"][2] == 3 * 1280
 
 
+def test_single_layer_couplings_mirrored(gpu_1280):
+    """The transposed product of the single layer runs the product's own plan
+    and coupling panels (the handle keeps no S^T).  That rests on the
+    coupling blocks coming in mirrored pairs with transposed entries: G is
+    symmetric (Eq. 1, g(x, y) = g(y, x), the same 7-point rule on both
+    triangles) and a mirrored pair is evaluated once.  The near field keeps
+    its transposed entries (Sauter-Schwab rules are not symmetric in the two
+    triangles), checked by the transposed products against the oracle."""
+    h, dump, tree = gpu_1280
+    rank = dump["rank"]
+    blocks, at = {}, 0
+    for (t, s) in map(tuple, dump["far"].tolist()):
+        blocks[(t, s)] = dump["S"][at:at + rank[t] * rank[s]].reshape(rank[t], rank[s])
+        at += rank[t] * rank[s]
+    for (t, s), b in blocks.items():
+        assert np.array_equal(b, blocks[(s, t)].T), f"S of {(t, s)} and its mirror"
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 1e-6)])
+def test_symmetric_transpose_adjoint(gpu_1280, prec, tol):
+    """<G^T x, z> = <x, G z> (float64), and the float32 transposed product
+    against the float64 one, for the symmetric handle whose transposed
+    product reuses the product's plan."""
+    h, _, _ = gpu_1280
+    x = torch.from_numpy(synth.normal_rhs(1280, 4, seed=3)).cuda()
+    z = torch.from_numpy(synth.normal_rhs(1280, 4, seed=4)).cuda()
+    ref = h.matvec(x, "f64", transpose=True)
+    if prec == "f64":
+        lhs = (ref * z).sum(0)
+        rhs = (x * h.matvec(z, "f64")).sum(0)
+        assert ((lhs - rhs).abs() / rhs.abs()).max().item() <= tol
+    else:
+        yt = h.matvec(x.float(), prec, transpose=True).double()
+        assert ((yt - ref).norm(dim=0) / ref.norm(dim=0)).max().item() <= tol
+
+
 @pytest.mark.parametrize("nrhs", [1, 3, 17])
 def test_matvec_f64(gpu_1280, h2_1280, nrhs):
     h, _, _ = gpu_1280
