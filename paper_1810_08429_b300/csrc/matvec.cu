@@ -180,7 +180,12 @@ constexpr int kItemRows = 64;                               // rows per segment 
 constexpr int kChunk = 64;                                  // columns per segment
 constexpr int kStagePanels = 8;
 constexpr int kStageBytes = kStagePanels * kItemRows * 16;  // 8 KB: one contiguous copy
-constexpr int kStages = 2;
+// ring stages of a pair: two at wide tiles (shared memory for two CTAs per
+// SM), three for the float-staged products at up to 4 right-hand sides per
+// tile, whose input blocks are small (more bytes in flight per pair where
+// each stage's compute is short)
+template <typename TA, int RC>
+constexpr int kStagesOf = (RC <= 4 && sizeof(TA) <= 4) ? 3 : 2;
 constexpr int kDescSlots = 4;                               // records: chain 0, 1; free 2, 3
 constexpr size_t kZeroBytes = (size_t)kChunk * 16 * 8;      // a full input block of doubles
 // a waiting warp sleeps until the phase completes or this many ns pass
@@ -192,6 +197,7 @@ template <typename TA, int RC>
 struct PairSmem {
   static constexpr size_t kXSlot = sizeof(TA) * (size_t)kChunk * RC;
   static constexpr size_t kRing = 0;
+  static constexpr int kStages = kStagesOf<TA, RC>;
   static constexpr size_t kX = (size_t)kStages * kStageBytes;
   static constexpr size_t kDesc = kX + 2 * kXSlot;
   static constexpr size_t kQueue = kDesc + (size_t)kDescSlots * kRecordBytes;
@@ -628,6 +634,7 @@ __device__ __forceinline__ void red_add2(float* p, float a, float b) {
 // Shared-memory regions and mbarriers of one pair.
 template <typename TA, int RC>
 struct Pair {
+  static constexpr int kStages = kStagesOf<TA, RC>;
   unsigned char* ring;
   TA* xb;
   MvSeg* rec;
@@ -705,6 +712,7 @@ __device__ __forceinline__ bool bulk_inputs(const SlotArgs<TV>& sa) {
 template <typename T, typename TN, typename TA, typename TV, int RC>
 __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, const Pair<TA, RC>& P, int lane) {
   constexpr unsigned FULL = 0xffffffffu;
+  constexpr int kStages = kStagesOf<TA, RC>;
   volatile int* abort_flag = L.abort_flag;
   uint32_t fill = 0, xfill = 0, uhand = 0;
   uint32_t dland_par = 0, dland_pend = 0, dfree_par = 0, dused = 0;
@@ -1042,6 +1050,7 @@ __device__ void producer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, co
 // ------------------------------------------------------------- consumer
 template <typename T, typename TN, typename TA, typename TV, int RC>
 __device__ void consumer_loop(const LaunchArgs& L, const SlotArgs<TV>* slots, const Pair<TA, RC>& P, int lane) {
+  constexpr int kStages = kStagesOf<TA, RC>;
   using Tl = Tile<RC>;
   constexpr unsigned FULL = 0xffffffffu;
   volatile int* abort_flag = L.abort_flag;
