@@ -118,9 +118,9 @@ TRAFFIC = {
     "near_entries": ("paper_1810_08429_b300/csrc/build.cu",
                      "923b1a936e03ad55214e453c632ecbec573480ead4ab6c8f2d834eff239e2297", 27.44e6),
     "mv_persistent.f32": ("paper_1810_08429_b300/csrc/matvec.cu",
-                          "5066ea961d4eb5e1ef1ff104b33259e00ccbacba7b7e9811fa91119ace633561", 475.84e6),
+                          "177d261423f17106e9d2afd0c473640d5af76e944c2005cb84a51af853f8f854", 476.10e6),
     "mv_persistent.bf16": ("paper_1810_08429_b300/csrc/matvec.cu",
-                           "5066ea961d4eb5e1ef1ff104b33259e00ccbacba7b7e9811fa91119ace633561", 269.91e6),
+                           "177d261423f17106e9d2afd0c473640d5af76e944c2005cb84a51af853f8f854", 270.15e6),
 }
 
 
