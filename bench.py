@@ -118,9 +118,9 @@ TRAFFIC = {
     "near_entries": ("paper_1810_08429_b300/csrc/build.cu",
                      "923b1a936e03ad55214e453c632ecbec573480ead4ab6c8f2d834eff239e2297", 27.44e6),
     "mv_persistent.f32": ("paper_1810_08429_b300/csrc/matvec.cu",
-                          "177d261423f17106e9d2afd0c473640d5af76e944c2005cb84a51af853f8f854", 476.10e6),
+                          "25516c3710cefbe2a445b57e64cca9b76d169bc949d6a3f85171933ff6d8c049", 476.22e6),
     "mv_persistent.bf16": ("paper_1810_08429_b300/csrc/matvec.cu",
-                           "177d261423f17106e9d2afd0c473640d5af76e944c2005cb84a51af853f8f854", 270.15e6),
+                           "25516c3710cefbe2a445b57e64cca9b76d169bc949d6a3f85171933ff6d8c049", 269.98e6),
 }
 
 

@@ -1914,7 +1914,9 @@ int launch(const gca_h2* const* hs, int count, int dir, bool trans, const int32_
   }
   constexpr int prec = sizeof(T) == 8 ? GCA_F64 : (sizeof(T) == 4 ? GCA_F32 : GCA_BF16);
   int rc = g_force_rc;
-  if (rc == 0) rc = tuned_width(prec, dir, R, rows);
+  // the tuner's key holds the caller's direction (a mirrored handle's
+  // transposed product runs plan 0 but keeps its own tuned width)
+  if (rc == 0) rc = tuned_width(prec, trans ? 1 : 0, R, rows);
   if (rc == 0) rc = default_width(R, prec);
   switch (rc) {
     case 16: return launch_rc<T, TN, TA, TV, 16>(hs, count, dir, trans, nrhs, x, ldx, y, ldy, pc, status, st);
